@@ -1,0 +1,303 @@
+"""FP64 CPU oracle for the baryon pasting method (Osato & Nagai 2022).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / ``--impl reference`` legs of ``bench.py`` are the only
+callers.  The product path (``paper_2201_02632_gb300``) never imports this
+package, and this package never imports the product path.
+
+The arithmetic lives in ``bp_oracle.c`` (plain C, FP64, compiled with
+``-ffp-contract=off``); this module builds it with gcc and marshals numpy
+arrays through ctypes.  Parity pins for every function are in
+``tests/test_oracle_*.py``.  Functions with no pin are listed in the
+module-level ``UNPINNED`` tuple (empty: every function is pinned).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bp_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+UNPINNED: tuple = ()
+
+# Field order of the oracle's per-halo model record (mirrors the enum in bp_oracle.c).
+FIELDS = (
+    "M", "c", "z", "rho_cr", "Delta_vir", "r_vir", "r_s", "rho_s", "m_c", "Phi0",
+    "r500", "M500", "M_star", "r_star", "E_gi", "E_dm", "P_s", "T", "rho0", "P0",
+    "r_f", "A_nt", "D_A", "tau", "res_m", "res_e", "status",
+)
+F = {name: i for i, name in enumerate(FIELDS)}
+
+
+class Cosmo(C.Structure):
+    _fields_ = [("Om", C.c_double), ("Ob", C.c_double), ("h", C.c_double),
+                ("Tcmb", C.c_double), ("XH", C.c_double)]
+
+
+class ICM(C.Structure):
+    _fields_ = [("Gamma", C.c_double), ("eps_dm", C.c_double), ("eps_star", C.c_double),
+                ("f_star", C.c_double), ("S_star", C.c_double), ("alpha_nt", C.c_double),
+                ("beta_nt", C.c_double), ("n_nt", C.c_double), ("energy_sign", C.c_int),
+                ("field_fb", C.c_int)]
+
+
+class Geom(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("n_maps", C.c_int),
+                ("theta0_x", C.c_double), ("theta0_y", C.c_double), ("dtheta", C.c_double)]
+
+
+def cosmo_default() -> Cosmo:
+    """WMAP9 flat LCDM of Section 1; T_CMB and X of Section 3.2."""
+    return Cosmo(Om=0.279, Ob=0.046, h=0.7, Tcmb=2.726, XH=0.76)
+
+
+def icm_default(**kw) -> ICM:
+    """Table 1 of the paper."""
+    p = dict(Gamma=1.2, eps_dm=0.0, eps_star=3.97e-6, f_star=0.026, S_star=0.12,
+             alpha_nt=0.18, beta_nt=0.5, n_nt=0.8, energy_sign=0, field_fb=0)
+    p.update(kw)
+    return ICM(**p)
+
+
+def geom(nx, ny, theta0_x, theta0_y, dtheta, n_maps=1) -> Geom:
+    return Geom(nx=int(nx), ny=int(ny), n_maps=int(n_maps), theta0_x=float(theta0_x),
+                theta0_y=float(theta0_y), dtheta=float(dtheta))
+
+
+def build(force: bool = False) -> str:
+    """Compile bp_oracle.c into _build/liboracle.so (gcc, FP64, no contraction)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = C.CDLL(path)
+            d, i64, i32 = C.c_double, C.c_int64, C.c_int
+            P = C.c_void_p
+            pc, pi, pg = C.POINTER(Cosmo), C.POINTER(ICM), C.POINTER(Geom)
+            sig = {
+                "orc_model_nfields": (i32, []),
+                "orc_rho_cr": (d, [pc, d]),
+                "orc_delta_vir": (d, [pc, d]),
+                "orc_chi": (d, [pc, d]),
+                "orc_z_of_chi": (d, [pc, d]),
+                "orc_DA": (d, [pc, d]),
+                "orc_tau": (d, [pc, d]),
+                "orc_m_of": (d, [d]),
+                "orc_sigma2": (d, [pc, d, d, d, d]),
+                "orc_halo_solve": (None, [pc, pi, d, d, d, i32, P]),
+                "orc_solve_halos": (None, [pc, pi, i64, P, P, P, i32, P, i32]),
+                "orc_profile": (None, [pc, pi, P, i64, P, P, P, P]),
+                "orc_nfw_eval": (None, [pc, d, d, d, i64, P, P, P, P]),
+                "orc_const_CP": (d, []),
+                "orc_const_CN": (d, [pc]),
+                "orc_los_integral": (d, [pc, pi, P, d, i32, d]),
+                "orc_hp_map": (None, [pc, pi, i64, P, P, P, P, P, pg, d, d, P, P, i32]),
+                "orc_w_sph": (d, [d]),
+                "orc_pp_assign": (None, [pc, pi, i64, P, P, P, P, P, P, P, P, d, i64, P, P, pg,
+                                         P, P, P, P, P, P, i32]),
+                "orc_pp_deposit": (None, [i64, P, P, P, P, P, P, pg, i32, P, P, i32]),
+                "orc_pp_deposit_pixels": (None, [i64, P, P, P, P, P, P, pg, i32, i64, P, P, P,
+                                                 P, i32]),
+                "orc_pp_pairs": (i64, [i64, P, P, P, P, i32, i32, i32, i32, i32, P, P]),
+                "orc_hp_pairs": (i64, [i64, P, P, P, P, pg, d, i32, i32, P, P]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            assert L.orc_model_nfields() == len(FIELDS)
+            _lib = L
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def _i32(a):
+    return np.ascontiguousarray(a, dtype=np.int32)
+
+
+# ---------------------------------------------------------------- cosmology
+def rho_cr(z, cp=None):
+    return lib().orc_rho_cr(C.byref(cp or cosmo_default()), float(z))
+
+
+def delta_vir(z, cp=None):
+    return lib().orc_delta_vir(C.byref(cp or cosmo_default()), float(z))
+
+
+def chi(z, cp=None):
+    return lib().orc_chi(C.byref(cp or cosmo_default()), float(z))
+
+
+def z_of_chi(x, cp=None):
+    return lib().orc_z_of_chi(C.byref(cp or cosmo_default()), float(x))
+
+
+def tau(z, cp=None):
+    return lib().orc_tau(C.byref(cp or cosmo_default()), float(z))
+
+
+def m_of(x):
+    return lib().orc_m_of(float(x))
+
+
+def sigma2(M_hinv, c, z, r, cp=None):
+    return lib().orc_sigma2(C.byref(cp or cosmo_default()), float(M_hinv), float(c), float(z),
+                            float(r))
+
+
+def nfw_eval(M_hinv, c, z, r, cp=None):
+    r = _f64(r)
+    rho, Menc, phi = (np.empty_like(r) for _ in range(3))
+    lib().orc_nfw_eval(C.byref(cp or cosmo_default()), float(M_hinv), float(c), float(z),
+                       r.size, _p(r), _p(rho), _p(Menc), _p(phi))
+    return rho, Menc, phi
+
+
+def const_CP():
+    return lib().orc_const_CP()
+
+
+def const_CN(cp=None):
+    return lib().orc_const_CN(C.byref(cp or cosmo_default()))
+
+
+# ---------------------------------------------------------------- halo solve
+def solve_halos(M_hinv, c, z, cp=None, ip=None, n_scan=48, nthreads=0):
+    """Per-halo ICM solve (Section 2).  Returns an [n, len(FIELDS)] FP64 array."""
+    M, c, z = _f64(M_hinv), _f64(c), _f64(z)
+    out = np.zeros((M.size, len(FIELDS)), np.float64)
+    lib().orc_solve_halos(C.byref(cp or cosmo_default()), C.byref(ip or icm_default()), M.size,
+                          _p(M), _p(c), _p(z), int(n_scan), _p(out), int(nthreads))
+    return out
+
+
+def profile(model_row, r, cp=None, ip=None):
+    """(P_e, rho_g, P_tot) of one solved halo at physical radii r."""
+    m, r = _f64(model_row), _f64(r)
+    Pe, rg, Pt = (np.empty_like(r) for _ in range(3))
+    lib().orc_profile(C.byref(cp or cosmo_default()), C.byref(ip or icm_default()), _p(m),
+                      r.size, _p(r), _p(Pe), _p(rg), _p(Pt))
+    return Pe, rg, Pt
+
+
+def los_integral(model_row, rperp, which=0, rtol=1e-12, cp=None, ip=None):
+    m = _f64(model_row)
+    return lib().orc_los_integral(C.byref(cp or cosmo_default()), C.byref(ip or icm_default()),
+                                  _p(m), float(rperp), int(which), float(rtol))
+
+
+# ---------------------------------------------------------------- HP
+def hp_map(thx, thy, vlos, models, g: Geom, ap_r500=0.0, map_id=None, rtol=1e-10, cp=None,
+           ip=None, nthreads=0):
+    thx, thy, vlos, models = _f64(thx), _f64(thy), _f64(vlos), _f64(models)
+    mid = None if map_id is None else _i32(map_id)
+    shape = (g.n_maps, g.ny, g.nx)
+    ym, bm = np.zeros(shape), np.zeros(shape)
+    lib().orc_hp_map(C.byref(cp or cosmo_default()), C.byref(ip or icm_default()), thx.size,
+                     _p(thx), _p(thy), _p(vlos), _p(mid), _p(models), C.byref(g),
+                     float(ap_r500), float(rtol), _p(ym), _p(bm), int(nthreads))
+    return ym, bm
+
+
+def hp_pairs(thx, thy, models, g: Geom, ap_r500, tw, th, map_id=None):
+    thx, thy, models = _f64(thx), _f64(thy), _f64(models)
+    mid = None if map_id is None else _i32(map_id)
+    L = lib()
+    n = L.orc_hp_pairs(thx.size, _p(thx), _p(thy), _p(mid), _p(models), C.byref(g),
+                       float(ap_r500), int(tw), int(th), None, None)
+    keys = np.empty(n, np.uint32)
+    vals = np.empty(n, np.uint32)
+    L.orc_hp_pairs(thx.size, _p(thx), _p(thy), _p(mid), _p(models), C.byref(g), float(ap_r500),
+                   int(tw), int(th), _p(keys), _p(vals))
+    return keys, vals
+
+
+# ---------------------------------------------------------------- PP
+def w_sph(x):
+    return lib().orc_w_sph(float(x))
+
+
+def pp_assign(parts: dict, Mp_hinv, halo_pos, models, g: Geom, cp=None, ip=None, nthreads=0):
+    """Per-particle signals.  parts: x,y,z,vx,vy,vz,hsml (float32), hid (int32).
+    halo_pos: float32 [3, nh].  Returns dict px,py,hp,Y,B (FP64) and kind (int32)."""
+    x, y, z = _f32(parts["x"]), _f32(parts["y"]), _f32(parts["z"])
+    vx, vy, vz = _f32(parts["vx"]), _f32(parts["vy"]), _f32(parts["vz"])
+    hs, hid = _f32(parts["hsml"]), _i32(parts["hid"])
+    hpos = _f32(halo_pos)
+    models = _f64(models)
+    n = x.size
+    out = {k: np.empty(n, np.float64) for k in ("px", "py", "hp", "Y", "B")}
+    kind = np.empty(n, np.int32)
+    nh = hpos.shape[1] if hpos.ndim == 2 else 0
+    lib().orc_pp_assign(C.byref(cp or cosmo_default()), C.byref(ip or icm_default()), n, _p(x),
+                        _p(y), _p(z), _p(vx), _p(vy), _p(vz), _p(hs), _p(hid), float(Mp_hinv),
+                        nh, _p(hpos), _p(models), C.byref(g), _p(out["px"]), _p(out["py"]),
+                        _p(out["hp"]), _p(out["Y"]), _p(out["B"]), _p(kind), int(nthreads))
+    out["kind"] = kind
+    return out
+
+
+def pp_deposit(a: dict, g: Geom, select=0, nthreads=0):
+    px, py, hp, Y, B = (_f64(a[k]) for k in ("px", "py", "hp", "Y", "B"))
+    kind = _i32(a["kind"])
+    ym = np.zeros((g.ny, g.nx))
+    bm = np.zeros((g.ny, g.nx))
+    lib().orc_pp_deposit(px.size, _p(px), _p(py), _p(hp), _p(Y), _p(B), _p(kind), C.byref(g),
+                         int(select), _p(ym), _p(bm), int(nthreads))
+    return ym, bm
+
+
+def pp_deposit_pixels(a: dict, g: Geom, pix_i, pix_j, select=0, nthreads=0):
+    px, py, hp, Y, B = (_f64(a[k]) for k in ("px", "py", "hp", "Y", "B"))
+    kind = _i32(a["kind"])
+    pi_, pj_ = _i32(pix_i), _i32(pix_j)
+    yv = np.zeros(pi_.size)
+    bv = np.zeros(pi_.size)
+    lib().orc_pp_deposit_pixels(px.size, _p(px), _p(py), _p(hp), _p(Y), _p(B), _p(kind),
+                                C.byref(g), int(select), pi_.size, _p(pi_), _p(pj_), _p(yv),
+                                _p(bv), int(nthreads))
+    return yv, bv
+
+
+def pp_pairs(px, py, hp, kind, nx, ny, tw, th, select=0):
+    """(key, particle) pairs of the tile membership, decided in FP32, ordered by key
+    then particle index."""
+    px, py, hp, kind = _f32(px), _f32(py), _f32(hp), _i32(kind)
+    L = lib()
+    n = L.orc_pp_pairs(px.size, _p(px), _p(py), _p(hp), _p(kind), nx, ny, tw, th, select, None,
+                       None)
+    keys = np.empty(n, np.uint32)
+    vals = np.empty(n, np.uint32)
+    L.orc_pp_pairs(px.size, _p(px), _p(py), _p(hp), _p(kind), nx, ny, tw, th, select, _p(keys),
+                   _p(vals))
+    return keys, vals

@@ -1,0 +1,258 @@
+"""Seeded synthetic inputs shaped like the paper's workloads.
+
+This module draws INPUTS only: halo catalogues (mass, concentration, redshift,
+sky position, line-of-sight velocity) and light-cone particles (comoving
+positions, velocities, smoothing lengths, halo membership).  It contains none
+of the pasting method's arithmetic (no ICM model, no projection, no kernel
+weights); both the CUDA path and the CPU oracle consume what it produces.
+
+The paper's inputs are N-body light-cones and Rockstar/SubFind catalogues
+(Section 3.1), which are not available; these generators stand in for them:
+
+* halo catalogue (HP, 1x1 deg^2): log-uniform mass in [1e13, 1e15] h^-1 Msun,
+  c = 5 (M/1e14)^-0.1 with 0.1 dex lognormal scatter, z ~ U(0.05, 1),
+  positions uniform in the patch, v_los ~ N(0, 300 km/s).
+* light-cone (PP): particles in a square cone around +z.  A fraction comes
+  from truncated-NFW halos with triaxial axis ratios U(0.5, 1) and random
+  orientation; the rest are field particles uniform in comoving volume.
+  Velocities N(0, 300 km/s) per component.  Smoothing lengths follow the
+  N_ngb = 64 neighbour rule applied to the local density of the generating
+  distribution (NFW density for halo particles, mean field density for field
+  particles).  Particle order is a seeded random permutation.
+
+Geometry of the generator (its own, used only to place objects): the
+comoving-distance/redshift relation is a trapezoid table of 1/E(z) for the
+same flat LCDM; halo particle clouds extend to a comoving radius enclosing
+200 times the mean matter density.  Nothing computed here is compared
+against anything.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+SEED_BASE = 20220108
+DEG = math.pi / 180.0
+OMEGA_M = 0.279
+C_KMS = 299792.458
+RHO_CRIT0_H2 = 2.77536627e11  # h^2 Msun / Mpc^3 (critical density today)
+
+
+@dataclass
+class MapGeom:
+    nx: int
+    ny: int
+    theta0_x: float  # rad, lower-left pixel edge
+    theta0_y: float
+    dtheta: float    # rad per pixel
+    n_maps: int = 1
+
+
+@dataclass
+class HaloCatalog:
+    M: np.ndarray      # f64 h^-1 Msun
+    c: np.ndarray      # f64
+    z: np.ndarray      # f64
+    thx: np.ndarray    # f64 rad
+    thy: np.ndarray    # f64 rad
+    vlos: np.ndarray   # f32 km/s
+    pos: np.ndarray | None = None  # f32 [3, n] comoving h^-1 Mpc
+    map_id: np.ndarray | None = None  # i32
+
+
+@dataclass
+class LightCone:
+    parts: dict                     # x,y,z,vx,vy,vz,hsml (f32), hid (i32)
+    halos: HaloCatalog
+    Mp: float                       # particle mass, h^-1 Msun
+    geom: MapGeom
+    info: dict = field(default_factory=dict)
+
+
+def _chi_table(zmax: float, n: int = 20001):
+    """Generator's own comoving distance table [h^-1 Mpc] (trapezoid on 1/E)."""
+    z = np.linspace(0.0, zmax, n)
+    inv_e = 1.0 / np.sqrt(OMEGA_M * (1 + z) ** 3 + 1 - OMEGA_M)
+    chi = np.concatenate([[0.0], np.cumsum(0.5 * (inv_e[1:] + inv_e[:-1]) * np.diff(z))])
+    return z, chi * C_KMS / 100.0
+
+
+def _concentration(rng, M):
+    return 5.0 * (M / 1e14) ** -0.1 * 10.0 ** rng.normal(0.0, 0.1, M.size)
+
+
+def halo_catalog(n=1000, seed=SEED_BASE, side_deg=1.0, logm=(13.0, 15.0), zr=(0.05, 1.0),
+                 npix=256) -> tuple[HaloCatalog, MapGeom]:
+    """HP catalogue on a side_deg x side_deg flat patch centred on the origin."""
+    rng = np.random.default_rng(seed)
+    M = 10.0 ** rng.uniform(logm[0], logm[1], n)
+    c = _concentration(rng, M)
+    z = rng.uniform(zr[0], zr[1], n)
+    half = 0.5 * side_deg * DEG
+    thx = rng.uniform(-half, half, n)
+    thy = rng.uniform(-half, half, n)
+    vlos = rng.normal(0.0, 300.0, n).astype(np.float32)
+    g = MapGeom(npix, npix, -half, -half, 2 * half / npix)
+    return HaloCatalog(M, c, z, thx, thy, vlos), g
+
+
+def powerlaw_masses(rng, n, mmin=1e12, mmax=1e15, slope=-0.9):
+    """dN/dlnM ~ M^slope on [mmin, mmax] by inverse CDF."""
+    u = rng.uniform(0.0, 1.0, n)
+    a, b = mmin ** slope, mmax ** slope
+    return (a + u * (b - a)) ** (1.0 / slope)
+
+
+def batched_catalog(n_maps=108, mean_halos=5e4, seed=SEED_BASE + 3, side_deg=5.0, npix=2048,
+                    zr=(0.01, 3.0)) -> tuple[HaloCatalog, MapGeom]:
+    """Many independent flat maps, Poisson halo counts per map."""
+    rng = np.random.default_rng(seed)
+    counts = rng.poisson(mean_halos, n_maps)
+    n = int(counts.sum())
+    M = powerlaw_masses(rng, n)
+    c = _concentration(rng, M)
+    z = rng.uniform(zr[0], zr[1], n)
+    half = 0.5 * side_deg * DEG
+    thx = rng.uniform(-half, half, n)
+    thy = rng.uniform(-half, half, n)
+    vlos = rng.normal(0.0, 300.0, n).astype(np.float32)
+    map_id = np.repeat(np.arange(n_maps, dtype=np.int32), counts)
+    g = MapGeom(npix, npix, -half, -half, 2 * half / npix, n_maps)
+    return HaloCatalog(M, c, z, thx, thy, vlos, map_id=map_id), g
+
+
+def _cone_points(rng, n, tan_half, chi_lo, chi_hi):
+    """Points uniform in comoving volume with |x/z|,|y/z| <= tan_half and chi in range."""
+    out = np.empty((0, 3))
+    while out.shape[0] < n:
+        m = int((n - out.shape[0]) * 3.2) + 1024
+        zc = chi_hi * rng.uniform(0.0, 1.0, m) ** (1.0 / 3.0)  # density ~ z^2 in the pyramid
+        xx = rng.uniform(-1.0, 1.0, m) * tan_half * zc
+        yy = rng.uniform(-1.0, 1.0, m) * tan_half * zc
+        r = np.sqrt(xx * xx + yy * yy + zc * zc)
+        ok = (r >= chi_lo) & (r <= chi_hi)
+        out = np.concatenate([out, np.stack([xx[ok], yy[ok], zc[ok]], 1)])
+    return out[:n]
+
+
+def _nfw_radii(rng, c, n_each):
+    """Radii in units of the cloud radius from a truncated NFW (inverse CDF, bisection)."""
+    cc = np.repeat(c, n_each)
+    u = rng.uniform(0.0, 1.0, cc.size)
+    mc = np.log1p(cc) - cc / (1 + cc)
+    lo = np.zeros_like(cc)
+    hi = cc.copy()
+    for _ in range(48):
+        mid = 0.5 * (lo + hi)
+        f = (np.log1p(mid) - mid / (1 + mid)) / mc - u
+        lo = np.where(f < 0, mid, lo)
+        hi = np.where(f < 0, hi, mid)
+    return 0.5 * (lo + hi) / cc  # x / c = r / R
+
+
+def _rotations(rng, n):
+    q = rng.normal(size=(n, 4))
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    w, x, y, z = q.T
+    return np.stack([
+        np.stack([1 - 2 * (y * y + z * z), 2 * (x * y - z * w), 2 * (x * z + y * w)], -1),
+        np.stack([2 * (x * y + z * w), 1 - 2 * (x * x + z * z), 2 * (y * z - x * w)], -1),
+        np.stack([2 * (x * z - y * w), 2 * (y * z + x * w), 1 - 2 * (x * x + y * y)], -1),
+    ], 1)  # [n, 3, 3]
+
+
+def lightcone(n_part=4_000_000, n_halo=3000, side_deg=2.0, zr=(0.05, 1.5), halo_frac=0.6,
+              npix=1024, seed=SEED_BASE + 1, mass="loguniform", n_ngb=64) -> LightCone:
+    """Light-cone particles + the catalogue of their halos."""
+    rng = np.random.default_rng(seed)
+    ztab, chitab = _chi_table(max(zr[1], 3.0) * 1.2)
+    chi_lo, chi_hi = np.interp(zr, ztab, chitab)
+    half = 0.5 * side_deg * DEG
+    tan_half = math.tan(half)
+    vol = (2 * tan_half) ** 2 * (chi_hi ** 3 - chi_lo ** 3) / 3.0  # pyramid shell (approx.)
+
+    # halos
+    if mass == "loguniform":
+        M = 10.0 ** rng.uniform(13.0, 15.0, n_halo)
+    else:
+        M = powerlaw_masses(rng, n_halo)
+    c = _concentration(rng, M)
+    hp = _cone_points(rng, n_halo, tan_half, chi_lo, chi_hi)
+    hchi = np.linalg.norm(hp, axis=1)
+    hz = np.interp(hchi, chitab, ztab)
+    thx = np.arctan2(hp[:, 0], hp[:, 2])
+    thy = np.arctan2(hp[:, 1], hp[:, 2])
+    hv = rng.normal(0.0, 300.0, n_halo).astype(np.float32)
+
+    # particles per halo proportional to mass (largest remainder)
+    n_h = int(round(halo_frac * n_part))
+    share = M / M.sum() * n_h
+    cnt = np.floor(share).astype(np.int64)
+    rem = n_h - int(cnt.sum())
+    if rem > 0:
+        cnt[np.argsort(-(share - cnt), kind="stable")[:rem]] += 1
+    Mp = float(M.sum() / n_h)
+
+    R = (3.0 * M / (4.0 * math.pi * 200.0 * OMEGA_M * RHO_CRIT0_H2)) ** (1.0 / 3.0)
+    rad = _nfw_radii(rng, c, cnt) * np.repeat(R, cnt)
+    d = rng.normal(size=(n_h, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    q = rng.uniform(0.5, 1.0, n_halo)
+    s = rng.uniform(0.5, 1.0, n_halo)
+    scale = np.stack([np.ones(n_halo), q, s], 1) / np.cbrt(q * s)[:, None]
+    off = d * rad[:, None] * np.repeat(scale, cnt, axis=0)
+    rot = _rotations(rng, n_halo)
+    off = np.einsum("nij,nj->ni", np.repeat(rot, cnt, axis=0), off)
+    hpos_p = np.repeat(hp, cnt, axis=0) + off
+    hid_h = np.repeat(np.arange(n_halo, dtype=np.int32), cnt)
+
+    # field particles
+    n_f = n_part - n_h
+    fpos = _cone_points(rng, n_f, tan_half, chi_lo, chi_hi)
+    n_field = n_f / vol
+
+    # smoothing lengths from the neighbour rule
+    rs = np.repeat(R / c, cnt)
+    mcv = np.repeat(np.log1p(c) - c / (1 + c), cnt)
+    x = rad / rs
+    rho = np.repeat(M, cnt) / (4 * math.pi * rs ** 3 * mcv) / (x * (1 + x) ** 2)
+    h_field = (3.0 * n_ngb / (4.0 * math.pi * n_field)) ** (1.0 / 3.0)
+    h_halo = np.minimum((3.0 * n_ngb / (4.0 * math.pi * (rho / Mp))) ** (1.0 / 3.0), h_field)
+
+    pos = np.concatenate([hpos_p, fpos])
+    hs = np.concatenate([h_halo, np.full(n_f, h_field)])
+    hid = np.concatenate([hid_h, np.full(n_f, -1, np.int32)])
+    vel = rng.normal(0.0, 300.0, (n_part, 3))
+    perm = rng.permutation(n_part)
+    parts = {
+        "x": pos[perm, 0].astype(np.float32), "y": pos[perm, 1].astype(np.float32),
+        "z": pos[perm, 2].astype(np.float32),
+        "vx": vel[perm, 0].astype(np.float32), "vy": vel[perm, 1].astype(np.float32),
+        "vz": vel[perm, 2].astype(np.float32),
+        "hsml": hs[perm].astype(np.float32), "hid": hid[perm].astype(np.int32),
+    }
+    cat = HaloCatalog(M, c, hz, thx, thy, hv, pos=hp.T.astype(np.float32).copy())
+    g = MapGeom(npix, npix, -half, -half, 2 * half / npix)
+    return LightCone(parts, cat, Mp, g, {"h_field": h_field, "n_halo_particles": n_h})
+
+
+def assigned_particles(n=20000, npix=96, seed=SEED_BASE + 11, hmax=24.0, frac_field=0.4,
+                       margin=8.0):
+    """Directly drawn per-particle deposit inputs (pixel coordinates, kernel radius in
+    pixels, signals) for testing the deposit alone.  Mixes tiny (sub-pixel), medium and
+    large kernels, particles straddling the map edge, h = 0, and signed B."""
+    rng = np.random.default_rng(seed)
+    px = rng.uniform(-margin, npix + margin, n).astype(np.float32)
+    py = rng.uniform(-margin, npix + margin, n).astype(np.float32)
+    u = rng.uniform(0, 1, n)
+    hp = np.where(u < 0.3, rng.uniform(0.0, 1.0, n),
+                  np.where(u < 0.8, rng.uniform(1.0, 6.0, n), rng.uniform(6.0, hmax, n)))
+    hp[rng.uniform(0, 1, n) < 0.02] = 0.0
+    kind = (rng.uniform(0, 1, n) < frac_field).astype(np.int32)
+    kind[rng.uniform(0, 1, n) < 0.05] = 2
+    Y = np.where(kind == 0, 10.0 ** rng.uniform(-9, -6, n), 0.0)
+    B = np.where(kind == 2, 0.0, rng.normal(0.0, 1e-7, n))
+    return {"px": px, "py": py, "hp": hp.astype(np.float32), "Y": Y.astype(np.float32),
+            "B": B.astype(np.float32), "kind": kind}
