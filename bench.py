@@ -1,0 +1,379 @@
+#!/usr/bin/env python
+"""Benchmark of the baryon pasting hot path on the light-cone workload.
+
+Workload (one step): 4e6 particles in a 2x2 deg^2 cone (z 0.05-1.5; 60% from 3000
+truncated-NFW halos, 40% field), 1024^2 maps.  A step solves the ICM model of the
+3000 halos, assigns the particle signals, pastes them (pair list, radix sort,
+tiled deposit, partial-tile reduction), pastes the 3000 halos' projected profiles
+onto their own 1024^2 maps, and finalises both map pairs.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on a bounded
+sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pasted particles/s (PP), halos/s (HP), frac of HBM roofline; surrogate vs solve"
+UNIT = "particles/s"
+WORKLOAD = ("PP plain, FP32 deposit: 4M particles, 2x2 deg^2 light-cone z 0.05-1.5, 3000 "
+            "halos (60% halo / 40% field particles), 1024^2 y and kSZ maps; plus HP of the "
+            "3000 halos on 1024^2 maps")
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def rank_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock, utilisation and throttle reasons."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,utilization.gpu,power.draw,"
+              "clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 10:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        load = [r for r in rows if num(r[3]) >= 50] or rows
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i] == "Active"})
+        return {"sm_mhz": statistics.median(num(r[1]) for r in load),
+                "sm_max_mhz": max(num(r[2]) for r in rows), "reasons": reasons,
+                "samples": len(rows), "samples_under_load": len(load)}
+
+
+def deposit_flops(rec_np, nx, ny):
+    """Algorithmic FP32 flops of one deposit launch: 2 per pixel update (one FMA per map)
+    over every particle's clipped 2h x 2h footprint; field particles update one map."""
+    px, py, hp, Y, kind = (rec_np[:, 0], rec_np[:, 1], rec_np[:, 2], rec_np[:, 3],
+                           rec_np[:, 5].astype(np.int32))
+    with np.errstate(invalid="ignore"):
+        i0 = np.floor(px - hp)
+        i1 = np.floor(px + hp)
+        j0 = np.floor(py - hp)
+        j1 = np.floor(py + hp)
+    ok = (kind != 2) & (i1 >= 0) & (i0 <= nx - 1) & (j1 >= 0) & (j0 <= ny - 1)
+    w = np.clip(i1, 0, nx - 1) - np.clip(i0, 0, nx - 1) + 1
+    h = np.clip(j1, 0, ny - 1) - np.clip(j0, 0, ny - 1) + 1
+    upd = (w * h)[ok].astype(np.float64)
+    maps = np.where(Y[ok] != 0, 2.0, 1.0)
+    return float(2.0 * np.sum(upd * maps)), float(np.sum(upd))
+
+
+def ncu_traffic(kernel_key):
+    """DRAM bytes per launch of a kernel from the committed ncu summary, if it was
+    captured on the current source of that kernel (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_counters.json")
+    try:
+        d = json.load(open(path))[kernel_key]
+    except Exception:
+        return None
+    src = open(os.path.join(ROOT, "paper_2201_02632_gb300", "csrc", d["source"]), "rb").read()
+    if hashlib.sha256(src).hexdigest()[:16] != d.get("source_sha256_16"):
+        return None
+    return d.get("dram_bytes_per_launch_scaled")
+
+
+# ------------------------------------------------------------------ CPU oracle legs
+def oracle_sample(lc, n_part_sample, n_halo_sample, threads):
+    """Times the FP64 oracle on a bounded sample of the workload; returns
+    (seconds extrapolated to the full step, detail dict)."""
+    import oracle as O
+
+    O.build()
+    g = O.geom(lc.geom.nx, lc.geom.ny, lc.geom.theta0_x, lc.geom.theta0_y, lc.geom.dtheta)
+    cat = lc.halos
+    t0 = time.perf_counter()
+    mo = O.solve_halos(cat.M, cat.c, cat.z, nthreads=threads)
+    t_solve = time.perf_counter() - t0
+    sub = {k: v[:n_part_sample] for k, v in lc.parts.items()}
+    t0 = time.perf_counter()
+    a = O.pp_assign(sub, lc.Mp, cat.pos, mo, g, nthreads=threads)
+    O.pp_deposit(a, g, nthreads=threads)
+    t_pp = time.perf_counter() - t0
+    hs = slice(0, n_halo_sample)
+    t0 = time.perf_counter()
+    O.hp_map(cat.thx[hs], cat.thy[hs], cat.vlos[hs], mo[hs], g, rtol=1e-8, nthreads=threads)
+    t_hp = time.perf_counter() - t0
+    n = lc.parts["x"].size
+    nh = cat.M.size
+    t_full = t_solve + t_pp * n / n_part_sample + t_hp * nh / n_halo_sample
+    det = {"t_solve_all_halos_s": round(t_solve, 3), "t_pp_sample_s": round(t_pp, 3),
+           "t_hp_sample_s": round(t_hp, 3), "n_part_sample": n_part_sample,
+           "n_halo_sample": n_halo_sample}
+    return t_full, det
+
+
+def run_reference(args):
+    rank, world, _ = rank_env()
+    if rank != 0:
+        return 0
+    from paper_2201_02632_gb300 import inputs as I
+
+    lc = I.lightcone()
+    threads = os.cpu_count() or 1
+    times = []
+    for k in range(args.warmup + args.steps):
+        t, det = oracle_sample(lc, args.ref_particles, args.ref_halos, threads)
+        if k >= args.warmup:
+            times.append(t)
+    t_step = statistics.mean(times)
+    n = lc.parts["x"].size
+    v = n / t_step
+    sample = (f"per step: FP64 oracle solve of all {lc.halos.M.size} halos, assign+deposit of "
+              f"{args.ref_particles} particles and HP of {args.ref_halos} halos, extrapolated "
+              f"linearly to the full step")
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "none (CPU)"},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                            "sample": sample},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU leg
+def run_ours(args):
+    import torch
+
+    rank, world, local = rank_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_2201_02632_gb300 import api
+    from paper_2201_02632_gb300 import build as B
+    from paper_2201_02632_gb300 import inputs as I
+
+    B.build()
+    # each rank pastes its own light-cone realisation (independent maps, no collective)
+    lc = I.lightcone(n_part=args.particles, seed=I.SEED_BASE + 1 + rank)
+    n = lc.parts["x"].size
+    cat = lc.halos
+    nh = cat.M.size
+    dev = torch.device("cuda", local)
+    ctx = api.Context()
+    g = api.geom(lc.geom.nx, lc.geom.ny, lc.geom.theta0_x, lc.geom.theta0_y, lc.geom.dtheta)
+
+    host = {k: torch.from_numpy(v).pin_memory() for k, v in lc.parts.items()}
+    hM = torch.from_numpy(cat.M).pin_memory()
+    hc = torch.from_numpy(cat.c).pin_memory()
+    hz = torch.from_numpy(cat.z).pin_memory()
+    hpos = torch.from_numpy(cat.pos).pin_memory()
+    hthx = torch.from_numpy(cat.thx).pin_memory()
+    hthy = torch.from_numpy(cat.thy).pin_memory()
+    hv = torch.from_numpy(cat.vlos).pin_memory()
+    h_in = list(host.values()) + [hM, hc, hz, hpos, hthx, hthy, hv]
+    d_in = [t.to(dev) for t in h_in]
+    parts_d = dict(zip(host.keys(), d_in[:len(host)]))
+    M, c, z, pos, thx, thy, vl = d_in[len(host):]
+    rec = torch.empty((n, api.ASSIGNED_STRIDE), dtype=torch.float32, device=dev)
+    pp = api.Maps.zeros(g, dev)
+    hp = api.Maps.zeros(g, dev)
+    out_host = [torch.empty((g.ny, g.nx), dtype=torch.float32).pin_memory() for _ in range(4)]
+    h2d_bytes = sum(t.numel() * t.element_size() for t in h_in)
+    d2h_bytes = sum(t.numel() * t.element_size() for t in out_host)
+
+    def step():
+        pp.zero_()
+        hp.zero_()
+        model, status = ctx.solve_halos(M, c, z)
+        ctx.assign_particles(parts_d, lc.Mp, pos, model, status, g, out=rec)
+        ctx.paste_particles(rec, g, pp)
+        ctx.paste_halos(thx, thy, vl, model, status, g, hp)
+        ctx.finalize(g, pp)
+        ctx.finalize(g, hp)
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    flops, updates = deposit_flops(rec.cpu().numpy(), g.nx, g.ny)
+    ctx.set_timing(True)
+    ctx.phase_times()
+
+    sampler = ClockSampler(local)
+    barrier()
+    if rank == 0:
+        sampler.start()
+    launches0 = ctx.kernel_launches()
+    step_ms, dep_ms, phases = [], [], []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        ph = ctx.phase_times()  # synchronises the stream
+        step_ms.append(e0.elapsed_time(e1))
+        dep_ms.append(ph["deposit"])
+        phases.append(ph)
+    barrier()
+    launches = ctx.kernel_launches() - launches0
+    clocks = sampler.stop() if rank == 0 else None
+    ctx.set_timing(False)
+    t_step = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([t_step], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_step = float(t.item())
+
+    # end to end through the public API: inputs from pinned host memory, maps back
+    e2e_ms = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for hsrc, ddst in zip(h_in, d_in):
+            ddst.copy_(hsrc, non_blocking=True)
+        step()
+        for hdst, dsrc in zip(out_host, (pp.y[0], pp.b[0], hp.y[0], hp.b[0])):
+            hdst.copy_(dsrc, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    t_e2e = sum(e2e_ms) / len(e2e_ms)
+    if world > 1:
+        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_e2e = float(t.item())
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    mean_ph = {k: round(sum(p[k] for p in phases) / len(phases), 4) for k in phases[0]}
+    dep = sum(dep_ms) / len(dep_ms)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    achieved = flops / (dep * 1e-3) / 1e12
+    traffic = ncu_traffic("k_deposit_c1")
+    hp_ms = mean_ph["solve"] + mean_ph["hp_table"] + mean_ph["hp_pairs"] + mean_ph["hp_paste"]
+    res = {
+        "metric": METRIC, "value": n * world / (t_step * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "particles": n, "halos": nh,
+                   "maps": f"{g.nx}x{g.ny}", "pp_tile": 64, "l2": "flushed: 256 MB write "
+                   "between timed steps", "parallelism": f"replicas x{world} (weak)"},
+        "hp_halos_per_s": nh / (hp_ms * 1e-3) if hp_ms > 0 else None,
+        "phase_ms": mean_ph,
+        "roofline": {"kernel": "k_deposit<64>", "bound": "alu", "achieved": achieved,
+                     "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                     "traffic": traffic, "deposit_ms": dep,
+                     "algorithmic_flops_per_launch": flops, "pixel_updates": updates,
+                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"},
+        "e2e": {"value": n * world / (t_e2e * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes,
+                "ms_per_step": t_e2e},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        threads = os.cpu_count() or 1
+        t_full, det = oracle_sample(lc, args.ref_particles, args.ref_halos, threads)
+        res["cpu_baseline"] = {
+            "value": n / t_full, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": (f"FP64 oracle: solve of all {nh} halos, assign+deposit of "
+                       f"{det['n_part_sample']} particles, HP of {det['n_halo_sample']} "
+                       f"halos, extrapolated linearly to the full step"), "detail": det}
+    print(json.dumps(res))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--particles", type=int, default=4_000_000)
+    ap.add_argument("--ref-particles", type=int, default=100_000)
+    ap.add_argument("--ref-halos", type=int, default=40)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,245 @@
+/*
+ * bp.h -- C ABI of the GB300 baryon pasting library (libbp.so).
+ *
+ * Method: Osato & Nagai, "Baryon pasting algorithm: halo-based and particle-based
+ * pasting methods" (arXiv:2201.02632).  The library computes, on one GPU:
+ *   bp_solve_halos       the per-halo analytic ICM model (Section 2, Eqs. of the
+ *                        polytrope, energy conservation, surface pressure, gas mass);
+ *   bp_assign_particles  per-particle tSZ/kSZ signals (Section 3.4, Eqs. y_i^PP,h,
+ *                        b_i^PP,h, field_y, field_b);
+ *   bp_paste_particles   the separable pixel-integrated SPH deposit (Section 3.4,
+ *                        Eqs. f_ij and integrated kernel);
+ *   bp_paste_halos       halo-based pasting of projected profiles (Section 3.3,
+ *                        Eqs. y^HP and b^HP);
+ *   bp_finalize_map      folding of the compensation planes and the conversion to
+ *                        temperature (Section 3.2).
+ *
+ * Conventions shared by every call:
+ *   - Units: masses in h^-1 Msun, positions and smoothing lengths in comoving
+ *     h^-1 Mpc, velocities in km/s (as in N-body catalogues).  Internally the
+ *     library works in physical Mpc, Msun and km/s with the cosmology's h.
+ *   - Flat sky: observer at the origin, line of sight +z; a position (x, y, z)
+ *     has sky angles theta_x = atan2(x, z), theta_y = atan2(y, z) [rad].
+ *   - Maps are FP32, row-major [n_maps][ny][nx]; pixel (i, j) spans
+ *     [theta0_x + i dtheta, theta0_x + (i+1) dtheta] x [theta0_y + j dtheta, ...].
+ *     Every map comes with a same-shaped FP32 "lo" plane holding the running
+ *     compensation (hi + lo is the value); paste calls ACCUMULATE into both, the
+ *     caller zeroes them first.  bp_finalize_map folds lo into hi.
+ *   - All array arguments are DEVICE pointers owned by the caller; the library
+ *     never frees them, never keeps them after a call returns, and never writes
+ *     an input.  Scratch memory (pair lists, sort buffers, tables) belongs to the
+ *     context and grows on demand.
+ *   - Every call is asynchronous on the context's stream, except where a call
+ *     documents a host synchronisation.
+ *   - Return value: BP_OK (0) or a negative error code; bp_last_error() gives a
+ *     message.  Invalid arguments are rejected before any work is queued.
+ */
+#ifndef BP_H
+#define BP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BP_OK 0
+#define BP_EINVAL (-1)    /* bad argument (null pointer, size, geometry) */
+#define BP_ECUDA (-2)     /* a CUDA runtime call failed */
+#define BP_ERANGE (-3)    /* input outside the supported range (z, map size, ids) */
+#define BP_ENOCONV (-4)   /* at least one halo did not converge (see status) */
+#define BP_ETIMEOUT (-5)  /* a bounded device wait gave up */
+#define BP_ENOMEM (-6)    /* scratch allocation failed */
+
+/* Flat LCDM background (Section 1) plus T_CMB and the hydrogen fraction X
+ * (Section 3.2).  Defaults: Om 0.279, Ob 0.046, h 0.7, Tcmb 2.726, XH 0.76. */
+typedef struct {
+  double Om, Ob, h, Tcmb, XH;
+} bp_cosmology;
+
+/* ICM model parameters (Table 1).  energy_sign selects the arrangement of the
+ * energy condition: 0 = E_g,f = E_g,i + eps_DM |E_DM| + eps_* M_* c^2 + dE_p
+ * (the gas gains the injected energy and does the surface work; gives r_f > r_vir
+ * as Section 2.2 states), 1 = the arrangement as printed.  field_fb = 1 multiplies
+ * the field-particle electron count by f_b (printed form: 0). */
+typedef struct {
+  double Gamma, eps_dm, eps_star, f_star, S_star, alpha_nt, beta_nt, n_nt;
+  int energy_sign;
+  int field_fb;
+} bp_icm_params;
+
+/* Flat-sky pixel grid.  theta0_* is the lower-left pixel EDGE in radians. */
+typedef struct {
+  int nx, ny, n_maps;
+  double theta0_x, theta0_y, dtheta;
+} bp_map_geom;
+
+/* Solved halo model record: FP64 device array laid out field-major,
+ * model[f * n + i] for halo i and field f below.  Physical units: Msun, Mpc,
+ * km/s; pressures Msun (km/s)^2 Mpc^-3; densities Msun Mpc^-3. */
+enum {
+  BP_M_MVIR = 0, /* virial mass [Msun] */
+  BP_M_C,        /* concentration */
+  BP_M_Z,        /* redshift */
+  BP_M_RVIR,     /* virial radius [Mpc] */
+  BP_M_RS,       /* NFW scale radius */
+  BP_M_RHOS,     /* NFW scale density */
+  BP_M_MC,       /* m(c) = ln(1+c) - c/(1+c) */
+  BP_M_PHI0,     /* central potential [(km/s)^2] */
+  BP_M_R500,
+  BP_M_M500,
+  BP_M_MSTAR,    /* stellar mass */
+  BP_M_RSTAR,    /* stellar radius */
+  BP_M_EGI,      /* initial gas energy */
+  BP_M_EDM,      /* dark-matter energy */
+  BP_M_PS,       /* surface pressure */
+  BP_M_T,        /* P0 / rho0 */
+  BP_M_RHO0,     /* central gas density */
+  BP_M_P0,       /* central total pressure */
+  BP_M_RF,       /* gas boundary radius r_f */
+  BP_M_ANT,      /* alpha_nt f(z) */
+  BP_M_DA,       /* angular-diameter distance [Mpc] */
+  BP_M_TAU,      /* mean optical depth to z */
+  BP_M_RESM,     /* gas-mass condition residual at the solution */
+  BP_M_RESE,     /* energy condition residual at the solution */
+  BP_M_NFIELDS
+};
+
+/* per-halo status codes written by bp_solve_halos */
+#define BP_HALO_OK 0
+#define BP_HALO_NOBRACKET 1  /* no r_f bracket found in [0.5, 10] r_vir */
+#define BP_HALO_BADSTAR 2    /* M_* >= f_b M_vir: no stellar radius */
+#define BP_HALO_THETA 3      /* theta(r_f) <= 0 */
+#define BP_HALO_MAXIT 4      /* Newton iteration limit reached */
+#define BP_HALO_BADINPUT 5   /* M, c or z not finite / out of range */
+
+/* particle record written by bp_assign_particles: BP_ASSIGNED_STRIDE floats per
+ * particle (32 bytes, 16-byte aligned):
+ *   [0] px   pixel-unit x coordinate measured from the map's lower-left edge
+ *   [1] py   pixel-unit y coordinate
+ *   [2] hp   kernel radius h in pixels (2h x 2h support square)
+ *   [3] Y    y_i: the particle's Compton-y in pixel units (Eq. y_i^PP,h)
+ *   [4] B    b_i: the particle's kSZ b in pixel units (Eqs. b_i^PP,h, field_b)
+ *   [5] kind 0 halo particle, 1 field particle, 2 contributes nothing
+ *   [6],[7]  zero */
+#define BP_ASSIGNED_STRIDE 8
+#define BP_KIND_HALO 0
+#define BP_KIND_FIELD 1
+#define BP_KIND_NONE 2
+
+#define BP_SELECT_ALL 0
+#define BP_SELECT_HALO 1
+#define BP_SELECT_FIELD 2
+
+#define BP_SOLVE_FP64 0
+
+#define BP_OUT_YB 0     /* maps hold y and b */
+#define BP_OUT_DT 1     /* maps hold Delta T / T_CMB: g_nu(x) y and -b */
+
+typedef struct bp_ctx bp_ctx;
+
+/* Create a context on the current CUDA device.  stream: a cudaStream_t (NULL = the
+ * legacy default stream).  Builds the background tables (chi(z), tau(z), z(chi)) on
+ * the host in FP64 and uploads them (synchronous).  Returns BP_EINVAL for
+ * non-physical parameters. */
+int bp_create(bp_ctx** ctx, const bp_cosmology* cosmo, const bp_icm_params* icm, void* stream);
+/* Free the context and its scratch (synchronises its stream). */
+int bp_destroy(bp_ctx* ctx);
+/* Message of the last error on this context (never NULL). */
+const char* bp_last_error(const bp_ctx* ctx);
+/* Change the stream later calls are queued on. */
+int bp_set_stream(bp_ctx* ctx, void* stream);
+/* Tile sizes: PP deposit tile (pixels per side: 32 or 64) and HP tile (32 or 64);
+ * pp_unit: maximum particles per deposit work unit (>= 256).  0 keeps a value. */
+int bp_set_tiling(bp_ctx* ctx, int pp_tile, int hp_tile, int pp_unit);
+/* Bytes of scratch the context currently holds. */
+int64_t bp_workspace_bytes(const bp_ctx* ctx);
+
+/* Phase timing: when on, each call records CUDA events around its kernels on the
+ * context's stream.  bp_phase_times synchronises the stream and writes, for every
+ * phase index below, the milliseconds accumulated since the previous call to it
+ * (then resets).  n: length of ms (>= BP_NPHASES). */
+#define BP_PH_SOLVE 0
+#define BP_PH_ASSIGN 1
+#define BP_PH_PAIRS 2     /* pair count, scan and emit */
+#define BP_PH_SORT 3      /* radix sort and tile ranges */
+#define BP_PH_DEPOSIT 4   /* work units + the deposit kernel */
+#define BP_PH_REDUCE 5    /* partial-tile reduction */
+#define BP_PH_HP_TABLE 6  /* HP per-halo tables */
+#define BP_PH_HP_PAIRS 7  /* HP (halo, tile) list and sort */
+#define BP_PH_HP_PASTE 8  /* HP paste and reduction */
+#define BP_PH_FINALIZE 9
+#define BP_NPHASES 10
+int bp_set_timing(bp_ctx* ctx, int on);
+int bp_phase_times(bp_ctx* ctx, double* ms, int n);
+/* Number of kernels this context has launched since it was created. */
+int64_t bp_kernel_launches(const bp_ctx* ctx);
+
+/* Section 2: solve the ICM model of n halos.
+ *   Mvir [n] FP64 h^-1 Msun, c [n] FP64, z [n] FP64 (0 <= z <= 10)
+ *   model [BP_M_NFIELDS * n] FP64 (field-major, written), status [n] int32 (written)
+ *   mode: BP_SOLVE_FP64.  resid_tol: convergence tolerance on the normalised
+ *   gas-mass and energy residuals (<= 0 selects 1e-10).
+ * Returns BP_ENOCONV if any halo's status is not BP_HALO_OK (this reads back one
+ * counter: the call synchronises the stream).  Halos are independent. */
+int bp_solve_halos(bp_ctx* ctx, int64_t n, const double* Mvir, const double* c, const double* z,
+                   double* model, int32_t* status, int mode, double resid_tol);
+
+/* Section 3.4: per-particle signals.
+ *   x,y,z [n] FP32 comoving h^-1 Mpc; vx,vy,vz [n] FP32 km/s (peculiar);
+ *   hsml [n] FP32 comoving h^-1 Mpc; halo_id [n] int32 (-1 = field particle);
+ *   Mp: particle mass in h^-1 Msun;
+ *   halo_pos [3 * n_halos] FP32 comoving h^-1 Mpc, layout [3][n_halos];
+ *   model/status: output of bp_solve_halos for those n_halos halos;
+ *   out [BP_ASSIGNED_STRIDE * n] FP32 (written, see the record layout above).
+ * A halo particle gets P_e, n_e of its halo's profile at its halo-centric distance
+ * and the volume V_i = Mp / rho_NFW(r_i); one beyond r_f, or of a halo whose status
+ * is not OK, gets kind BP_KIND_NONE.  halo_id >= n_halos: BP_ERANGE is NOT checked
+ * on the device; such particles get kind BP_KIND_NONE. */
+int bp_assign_particles(bp_ctx* ctx, int64_t n, const float* x, const float* y, const float* z,
+                        const float* vx, const float* vy, const float* vz, const float* hsml,
+                        const int32_t* halo_id, double Mp, int64_t n_halos,
+                        const float* halo_pos, const double* model, const int32_t* status,
+                        const bp_map_geom* geom, float* out);
+
+/* Section 3.4: deposit assigned particles through the separable pixel-integrated
+ * SPH kernel, f_ij = [w((x_i+ - x_p)/h) - w((x_i- - x_p)/h)] [same in y].
+ *   assigned [BP_ASSIGNED_STRIDE * n] FP32 (from bp_assign_particles or the caller)
+ *   select: BP_SELECT_ALL / HALO / FIELD
+ *   ymap, bmap, ylo, blo: [ny][nx] FP32, accumulated (geom->n_maps must be 1).
+ * Kernel support outside the map is dropped.  h = 0 deposits to the nearest grid
+ * point.  Deterministic: particles are summed per tile in index order with
+ * compensated FP32 sums.  Synchronises once to size the pair list. */
+int bp_paste_particles(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_geom* geom,
+                       int select, float* ymap, float* bmap, float* ylo, float* blo);
+
+/* The tile pair list of the deposit (for tests): keys (tile index ty*ntx+tx) and
+ * particle indices ordered by key then index.  capacity: entries the caller
+ * allocated; n_pairs (host pointer) receives the count.  BP_ERANGE if capacity
+ * is too small (nothing written).  Synchronises. */
+int bp_pp_pairs(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_geom* geom,
+                int select, int tile, uint32_t* keys, uint32_t* vals, int64_t capacity,
+                int64_t* n_pairs);
+
+/* Section 3.3: halo-based pasting.  For every pixel centre at projected radius
+ * r_perp < r_ap of halo h, add sigma_T/(m_e c^2) 2 int P_e dx to y and
+ * sigma_T (v_h/c) e^{-tau_h} 2 int n_e dx to b, the line of sight bounded by r_f.
+ *   th_x, th_y [n] FP64 rad; v_los [n] FP32 km/s; map_id [n] int32 or NULL (all 0);
+ *   model/status from bp_solve_halos; ap_r500 > 0 sets r_ap = min(r_f, ap_r500 r500),
+ *   0 sets r_ap = r_f; maps [n_maps][ny][nx] FP32 accumulated.
+ * Synchronises once to size the (halo, tile) list. */
+int bp_paste_halos(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_y,
+                   const float* v_los, const int32_t* map_id, const double* model,
+                   const int32_t* status, const bp_map_geom* geom, double ap_r500, float* ymap,
+                   float* bmap, float* ylo, float* blo);
+
+/* Section 3.2: fold lo into hi (hi <- fl(hi + lo), lo <- 0) for all n_maps maps;
+ * out_kind BP_OUT_DT then converts to Delta T/T_CMB: g_nu(x) y (x = h nu/k T_CMB,
+ * nu_ghz > 0) and -b.  ymap or bmap may be NULL (with its lo plane). */
+int bp_finalize_map(bp_ctx* ctx, const bp_map_geom* geom, float* ymap, float* bmap, float* ylo,
+                    float* blo, int out_kind, double nu_ghz);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BP_H */

@@ -119,6 +119,7 @@ def lib():
                                                  P, i32]),
                 "orc_pp_pairs": (i64, [i64, P, P, P, P, i32, i32, i32, i32, i32, P, P]),
                 "orc_hp_pairs": (i64, [i64, P, P, P, P, pg, d, i32, i32, P, P]),
+                "orc_energy_residual": (d, [pc, pi, d, d, d, d]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -199,6 +200,13 @@ def solve_halos(M_hinv, c, z, cp=None, ip=None, n_scan=48, nthreads=0):
     lib().orc_solve_halos(C.byref(cp or cosmo_default()), C.byref(ip or icm_default()), M.size,
                           _p(M), _p(c), _p(z), int(n_scan), _p(out), int(nthreads))
     return out
+
+
+def energy_residual(M_hinv, c, z, rf_over_rvir, cp=None, ip=None):
+    """Energy condition residual at r_f = rf_over_rvir * r_vir, with T set by the gas-mass
+    condition at that r_f."""
+    return lib().orc_energy_residual(C.byref(cp or cosmo_default()), C.byref(ip or icm_default()),
+                                     float(M_hinv), float(c), float(z), float(rf_over_rvir))
 
 
 def profile(model_row, r, cp=None, ip=None):

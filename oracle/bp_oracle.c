@@ -847,6 +847,7 @@ void orc_pp_deposit(int64_t n, const double* px, const double* py, const double*
       if (select == 1 && kind[k] != 0) continue;
       if (select == 2 && kind[k] != 1) continue;
       double h = hp[k];
+      if (!(h >= 0.0)) continue; /* a negative or NaN radius covers nothing */
       int ilo = (int)fmax(0.0, floor(px[k] - h)), ihi = (int)fmin(g->nx - 1.0, floor(px[k] + h));
       int jlo = (int)fmax((double)j0, floor(py[k] - h)), jhi = (int)fmin((double)j1, floor(py[k] + h));
       if (floor(px[k] + h) < 0 || floor(px[k] - h) > g->nx - 1) continue;
@@ -886,6 +887,7 @@ void orc_pp_deposit_pixels(int64_t n, const double* px, const double* py, const 
       if (select == 1 && kind[k] != 0) continue;
       if (select == 2 && kind[k] != 1) continue;
       double h = hp[k];
+      if (!(h >= 0.0)) continue;
       if (floor(px[k] - h) > i || floor(px[k] + h) < i) continue;
       if (floor(py[k] - h) > j || floor(py[k] + h) < j) continue;
       double a, b;
@@ -908,6 +910,7 @@ void orc_pp_deposit_pixels(int64_t n, const double* px, const double* py, const 
  * key = ty * ntx + tx.  Output: (key, particle index) pairs ordered by key,
  * ties by particle index.  Returns the pair count; if keys==NULL only counts. */
 static int o_span32(float c, float h, int n, int* lo, int* hi) {
+  if (!(h >= 0.0f)) return 0; /* a negative or NaN radius covers nothing */
   volatile float a = c - h, b = c + h; /* single-precision rounding, no fusion */
   if (!(a == a) || !(b == b)) return 0;
   float fa = floorf(a), fb = floorf(b);
@@ -987,4 +990,24 @@ int64_t orc_hp_pairs(int64_t nh, const double* thx, const double* thy, const int
   }
   free(cnt);
   return total;
+}
+
+/* Energy residual as a function of r_f, with T from the gas-mass condition at that
+ * r_f (the reduced one-dimensional problem of Section 2.2).  NAN where no T exists. */
+double orc_energy_residual(const orc_cosmo* cp, const orc_icm* ip, double M_hinv, double c,
+                           double z, double rf_over_rvir) {
+  double out[OF_N];
+  orc_halo_solve(cp, ip, M_hinv, c, z, 8, out);
+  o_solver s;
+  s.cp = cp;
+  s.ip = ip;
+  o_nfw_init(&s.h, cp, M_hinv / cp->h, c, z);
+  s.fb = cp->Ob / cp->Om;
+  s.n = 1.0 / (ip->Gamma - 1.0);
+  s.phi0 = o_phi0(&s.h);
+  s.Mstar = out[OF_MSTAR];
+  s.Egi = out[OF_EGI];
+  s.Edm = out[OF_EDM];
+  s.Ps = out[OF_PS];
+  return f_rese_rf(rf_over_rvir * s.h.rvir, &s);
 }

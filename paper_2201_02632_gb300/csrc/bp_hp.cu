@@ -1,0 +1,625 @@
+// bp_hp.cu -- halo-based pasting (Section 3.3) and map finalisation (Section 3.2).
+//
+//  k_hp_prep    per halo: FP64 centre in pixel units, aperture, FP32 profile constants
+//  k_hp_table   per halo and table node u = r_perp / r_f: the line-of-sight integrals
+//               of the dimensionless pressure and density profiles, divided by the
+//               chord sqrt(1 - u^2) so that the tabulated function is smooth at the
+//               edge (Eqs. y^HP, b^HP); 16-point Gauss-Legendre per segment after
+//               t = u sinh(s), split where the 3-D radius crosses r_vir and the zero
+//               of the thermal fraction
+//  k_hp_count / (map, tile, halo) pairs from the FP64 pixel-centre bounding box of the
+//  k_hp_emit    aperture disc
+//  k_hp_paste   persistent over work units; each pixel centre inside the aperture adds
+//               the interpolated projected profile with Kahan compensation
+//  k_hp_reduce  partial tiles of multi-unit tiles, in unit order
+//  k_finalize   hi + lo folding and the conversion to Delta T / T_CMB
+#include "bp_internal.cuh"
+
+#define HP_NT 256          // table intervals on u in [0, 1]
+#define HP_ROW (HP_NT + 3) // with one ghost node at each end
+#define HP_NGL 16
+
+__constant__ float c_hgx[HP_NGL];
+__constant__ float c_hgw[HP_NGL];
+
+namespace {
+
+bool g_hp_const = false;
+
+int hp_constants(bp_ctx* ctx) {
+  if (g_hp_const) return BP_OK;
+  float x[HP_NGL], w[HP_NGL];
+  for (int i = 0; i < HP_NGL; ++i) {
+    double z = cos(bpc::PI * (i + 0.75) / (HP_NGL + 0.5));
+    double dp = 0, p1 = 0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0;
+      p1 = z;
+      for (int k = 2; k <= HP_NGL; ++k) {
+        double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = HP_NGL * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[i] = (float)(-z);
+    w[i] = (float)(2.0 / ((1.0 - z * z) * dp * dp));
+  }
+  BP_CUDA(ctx, cudaMemcpyToSymbol(c_hgx, x, sizeof(x)));
+  BP_CUDA(ctx, cudaMemcpyToSymbol(c_hgw, w, sizeof(w)));
+  g_hp_const = true;
+  return BP_OK;
+}
+
+// Per-halo HP record.
+struct HpHalo {
+  double cx, cy;     // centre in pixel units from the lower-left edge
+  double rad_px;     // aperture radius [px]
+  float inv_rf_px;   // 1 / r_f [px]
+  float Ay, Ab;      // amplitude of y and b per unit chord (u = 0 edge chord 1)
+  int map, ok;
+  // profile constants for the tables (same meaning as the PP halo block)
+  float xf, c, q500, psi, A0, A1, ant, xnt;  // xnt: r_nt1 / r_s (R_nt = 1) or huge
+};
+
+__global__ void k_hp_prep(BpParams P, int64_t nh, const double* __restrict__ thx,
+                          const double* __restrict__ thy, const float* __restrict__ vlos,
+                          const int32_t* __restrict__ map_id, const double* __restrict__ model,
+                          const int32_t* __restrict__ status, bp_map_geom g, double ap_r500,
+                          HpHalo* out) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nh) return;
+  auto F = [&](int f) { return model[(int64_t)f * nh + k]; };
+  HpHalo H;
+  int mp = map_id ? map_id[k] : 0;
+  double rs = F(BP_M_RS), rf = F(BP_M_RF), T = F(BP_M_T), DA = F(BP_M_DA);
+  bool ok = status[k] == BP_HALO_OK && rs > 0 && rf > 0 && T > 0 && DA > 0 && mp >= 0 &&
+            mp < g.n_maps;
+  double rap = rf;
+  if (ap_r500 > 0) rap = fmin(rap, ap_r500 * F(BP_M_R500));
+  double px = DA * g.dtheta;  // Mpc per pixel at the halo
+  H.cx = (thx[k] - g.theta0_x) / g.dtheta;
+  H.cy = (thy[k] - g.theta0_y) / g.dtheta;
+  H.rad_px = rap / DA / g.dtheta;
+  H.inv_rf_px = (float)(px / rf);
+  double n1T = (P.n_poly + 1.0) * T, GM = bpc::G * F(BP_M_MVIR);
+  H.Ay = (float)(P.CP * P.pe_frac * F(BP_M_P0) * 2.0 * rf);
+  H.Ab = (float)(P.CN * F(BP_M_RHO0) * 2.0 * rf * ((double)vlos[k] / bpc::C_KMS) *
+                 exp(-F(BP_M_TAU)));
+  H.map = mp;
+  H.ok = ok ? 1 : 0;
+  H.xf = (float)(rf / rs);
+  H.c = (float)F(BP_M_C);
+  H.q500 = (float)(rs / F(BP_M_R500));
+  H.psi = (float)(GM / (F(BP_M_MC) * rs * n1T));
+  H.A0 = (float)(-F(BP_M_PHI0) / n1T);
+  H.A1 = (float)(GM / (rs * n1T));
+  H.ant = (float)F(BP_M_ANT);
+  double xnt = (F(BP_M_ANT) > 0) ? F(BP_M_R500) * pow(1.0 / F(BP_M_ANT), 1.0 / P.n_nt) / rs : 1e30;
+  H.xnt = (float)fmin(xnt, 1e30);
+  out[k] = H;
+}
+
+__device__ __forceinline__ float g_in(float x) {
+  if (x < 2e-2f) return x * (0.5f - x * (1.0f / 3.0f - x * (0.25f - x * 0.2f)));
+  return 1.0f - log1pf(x) / x;
+}
+
+// dimensionless pressure (thermal part) and density at x = r / r_s
+__device__ __forceinline__ void profile_pn(const HpHalo& H, float x, float n_poly, int n_int,
+                                           float n_nt, float& p, float& d) {
+  if (x >= H.xf) {
+    p = d = 0.f;
+    return;
+  }
+  float th = (x <= H.c) ? 1.0f - H.psi * g_in(x) : 1.0f - H.A0 + H.A1 / x;
+  th = fmaxf(th, 0.f);
+  float tn;
+  if (n_int > 0) {
+    float r = 1.f, b = th;
+    int e = n_int;
+    while (e) {
+      if (e & 1) r *= b;
+      b *= b;
+      e >>= 1;
+    }
+    tn = r;
+  } else {
+    tn = powf(th, n_poly);
+  }
+  float Rnt = H.ant * __powf(x * H.q500, n_nt);
+  d = tn;
+  p = tn * th * fmaxf(0.f, 1.0f - Rnt);
+}
+
+__global__ void __launch_bounds__(256) k_hp_table(const HpHalo* __restrict__ halos, int64_t nh,
+                                                  float n_poly, int n_int, float n_nt,
+                                                  float* tab) {
+  int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int64_t k = gid / (HP_NT + 1);
+  int node = (int)(gid % (HP_NT + 1));
+  if (k >= nh) return;
+  const HpHalo H = halos[k];
+  float* ty = tab + k * 2 * HP_ROW;
+  float* tb = ty + HP_ROW;
+  if (!H.ok) {
+    ty[node + 1] = tb[node + 1] = 0.f;
+    return;
+  }
+  float u = (float)node / HP_NT;
+  float Gy = 0.f, Gb = 0.f;
+  if (node == HP_NT) {  // limit u -> 1: the profile at r_f
+    float p, d;
+    profile_pn(H, H.xf * 0.99999994f, n_poly, n_int, n_nt, p, d);
+    Gy = p;
+    Gb = d;
+  } else {
+    float L = sqrtf(fmaxf(0.f, 1.0f - u * u));  // chord half-length in units of r_f
+    // radii (in units of r_f) where the integrand has a kink
+    float kinks[2] = {H.c / H.xf, H.xnt / H.xf};
+    float segs[4];
+    int ns = 0;
+    if (node == 0) {
+      // u = 0: integrate in t directly
+      segs[ns++] = 0.f;
+      for (int q = 0; q < 2; ++q)
+        if (kinks[q] > 0.f && kinks[q] < 1.0f) segs[ns++] = kinks[q];
+      segs[ns++] = 1.0f;
+      if (ns == 4 && segs[1] > segs[2]) { float t = segs[1]; segs[1] = segs[2]; segs[2] = t; }
+      float sy = 0.f, sb = 0.f;
+      for (int s = 0; s + 1 < ns; ++s) {
+        float a = segs[s], b = segs[s + 1], mid = 0.5f * (a + b), hw = 0.5f * (b - a);
+        for (int j = 0; j < HP_NGL; ++j) {
+          float t = mid + hw * c_hgx[j];
+          float p, d;
+          profile_pn(H, t * H.xf, n_poly, n_int, n_nt, p, d);
+          sy += hw * c_hgw[j] * p;
+          sb += hw * c_hgw[j] * d;
+        }
+      }
+      Gy = sy;
+      Gb = sb;
+    } else {
+      // t = u sinh(s): r/r_f = u cosh(s); s in [0, asinh(L/u)]
+      float smax = asinhf(L / u);
+      segs[ns++] = 0.f;
+      for (int q = 0; q < 2; ++q)
+        if (kinks[q] > u && kinks[q] < 1.0f) {
+          float sk = acoshf(kinks[q] / u);
+          if (sk > 0.f && sk < smax) segs[ns++] = sk;
+        }
+      segs[ns++] = smax;
+      if (ns == 4 && segs[1] > segs[2]) { float t = segs[1]; segs[1] = segs[2]; segs[2] = t; }
+      float sy = 0.f, sb = 0.f;
+      for (int s = 0; s + 1 < ns; ++s) {
+        float a = segs[s], b = segs[s + 1], mid = 0.5f * (a + b), hw = 0.5f * (b - a);
+        for (int j = 0; j < HP_NGL; ++j) {
+          float sv = mid + hw * c_hgx[j];
+          float ch = coshf(sv);
+          float p, d;
+          profile_pn(H, u * ch * H.xf, n_poly, n_int, n_nt, p, d);
+          float wj = hw * c_hgw[j] * u * ch;
+          sy += wj * p;
+          sb += wj * d;
+        }
+      }
+      Gy = sy / L;
+      Gb = sb / L;
+    }
+  }
+  ty[node + 1] = Gy;
+  tb[node + 1] = Gb;
+}
+
+// ghost nodes: G(-h) = G(h) (even in u), G(1+h) = 2 G(1) - G(1-h)
+__global__ void k_hp_ghosts(const HpHalo* __restrict__ halos, int64_t nh, float* tab) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nh) return;
+  for (int q = 0; q < 2; ++q) {
+    float* t = tab + k * 2 * HP_ROW + q * HP_ROW;
+    t[0] = t[2];
+    t[HP_NT + 2] = 2.f * t[HP_NT + 1] - t[HP_NT];
+  }
+}
+
+__device__ __forceinline__ bool hp_box(const HpHalo& H, const bp_map_geom& g, int& i0, int& i1,
+                                       int& j0, int& j1) {
+  if (!H.ok) return false;
+  double rad = H.rad_px;
+  double cx = H.cx - 0.5, cy = H.cy - 0.5;  // pixel-centre index units
+  double fa = floor(cx - rad), fb = floor(cx + rad);
+  double ga = floor(cy - rad), gb = floor(cy + rad);
+  if (fb < 0 || fa > g.nx - 1 || gb < 0 || ga > g.ny - 1) return false;
+  i0 = fa < 0 ? 0 : (int)fa;
+  i1 = fb > g.nx - 1 ? g.nx - 1 : (int)fb;
+  j0 = ga < 0 ? 0 : (int)ga;
+  j1 = gb > g.ny - 1 ? g.ny - 1 : (int)gb;
+  return true;
+}
+
+__global__ void k_hp_count(const HpHalo* __restrict__ halos, int64_t nh, bp_map_geom g, int ts,
+                           uint32_t* counts) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nh) return;
+  int i0, i1, j0, j1;
+  uint32_t c = 0;
+  if (hp_box(halos[k], g, i0, i1, j0, j1))
+    c = (uint32_t)((i1 / ts - i0 / ts + 1) * (j1 / ts - j0 / ts + 1));
+  counts[k] = c;
+}
+
+__global__ void k_hp_emit(const HpHalo* __restrict__ halos, int64_t nh, bp_map_geom g, int ts,
+                          const int64_t* __restrict__ offs, uint32_t* keys, uint32_t* vals) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nh) return;
+  int i0, i1, j0, j1;
+  const HpHalo H = halos[k];
+  if (!hp_box(H, g, i0, i1, j0, j1)) return;
+  int ntx = (g.nx + ts - 1) / ts, nty = (g.ny + ts - 1) / ts;
+  int64_t o = offs[k];
+  for (int ty = j0 / ts; ty <= j1 / ts; ++ty)
+    for (int tx = i0 / ts; tx <= i1 / ts; ++tx) {
+      keys[o] = (uint32_t)(((int64_t)H.map * nty + ty) * ntx + tx);
+      vals[o] = (uint32_t)k;
+      ++o;
+    }
+}
+
+struct HpUnit {
+  int64_t tile;
+  int64_t begin, end;
+  int64_t slot;
+};
+
+__global__ void k_hp_ucount(const int64_t* __restrict__ tstart, int64_t n_tiles, int unit,
+                            uint32_t* uc) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tiles) return;
+  uc[t] = (uint32_t)((tstart[t + 1] - tstart[t] + unit - 1) / unit);
+}
+__global__ void k_hp_uemit(const int64_t* __restrict__ tstart, int64_t n_tiles, int unit,
+                           const int64_t* __restrict__ uoff, HpUnit* units) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tiles) return;
+  int64_t b = tstart[t], e = tstart[t + 1], nu = (e - b + unit - 1) / unit, u0 = uoff[t];
+  for (int64_t q = 0; q < nu; ++q) {
+    HpUnit U;
+    U.tile = t;
+    U.slot = nu > 1 ? u0 + q : -1;
+    U.begin = b + q * unit;
+    U.end = min(e, b + (q + 1) * unit);
+    units[u0 + q] = U;
+  }
+}
+
+constexpr int HP_THREADS = 256;
+constexpr int HCH = 32;
+
+__device__ __forceinline__ float catmull(const float* __restrict__ t, float uu) {
+  // t: table row with ghosts; node k at t[k + 1]; uu in [0, 1)
+  float x = uu * HP_NT;
+  int i = (int)x;
+  if (i > HP_NT - 1) i = HP_NT - 1;
+  float f = x - (float)i;
+  float p0 = __ldg(t + i), p1 = __ldg(t + i + 1), p2 = __ldg(t + i + 2), p3 = __ldg(t + i + 3);
+  float f2 = f * f, f3 = f2 * f;
+  return 0.5f * (2.f * p1 + (-p0 + p2) * f + (2.f * p0 - 5.f * p1 + 4.f * p2 - p3) * f2 +
+                 (-p0 + 3.f * p1 - 3.f * p2 + p3) * f3);
+}
+
+__device__ __forceinline__ void kahan_add(float& s, float& c, float v) {
+  float y = __fsub_rn(v, c);
+  float t = __fadd_rn(s, y);
+  c = __fsub_rn(__fsub_rn(t, s), y);
+  s = t;
+}
+
+template <int TS>
+__global__ void __launch_bounds__(HP_THREADS)
+    k_hp_paste(const HpHalo* __restrict__ halos, const float* __restrict__ tab,
+               const uint32_t* __restrict__ hvals, const HpUnit* __restrict__ units,
+               const int64_t* __restrict__ n_units_ptr, int64_t* counter, bp_map_geom g,
+               float* ymap, float* bmap, float* ylo, float* blo, float* partials) {
+  constexpr int PR = TS / 16;
+  __shared__ float s_cx[HCH], s_cy[HCH], s_rap2[HCH], s_irf[HCH], s_ay[HCH], s_ab[HCH];
+  __shared__ int4 s_box[HCH];
+  __shared__ const float* s_tab[HCH];
+  __shared__ int64_t s_unit;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int lr = lane >> 3, lc = lane & 7;
+  const int wr0 = (w >> 1) * 4 * PR, wc0 = (w & 1) * 8 * PR;
+  const int r0 = wr0 + lr * PR, c0 = wc0 + lc * PR;
+  const int ntx = (g.nx + TS - 1) / TS, nty = (g.ny + TS - 1) / TS;
+  const int64_t n_units = *n_units_ptr;
+  for (;;) {
+    if (tid == 0) s_unit = atomicAdd((unsigned long long*)counter, 1ull);
+    __syncthreads();
+    const int64_t u = s_unit;
+    if (u >= n_units) break;
+    const HpUnit U = units[u];
+    const int mp = (int)(U.tile / ((int64_t)ntx * nty));
+    const int rem = (int)(U.tile % ((int64_t)ntx * nty));
+    const int x0 = (rem % ntx) * TS, y0 = (rem / ntx) * TS;
+    float hy[PR][PR], cy_[PR][PR], hb[PR][PR], cb_[PR][PR];
+#pragma unroll
+    for (int r = 0; r < PR; ++r)
+#pragma unroll
+      for (int c = 0; c < PR; ++c) hy[r][c] = cy_[r][c] = hb[r][c] = cb_[r][c] = 0.f;
+    for (int64_t cb = U.begin; cb < U.end; cb += HCH) {
+      const int nch = (int)min((int64_t)HCH, U.end - cb);
+      __syncthreads();
+      if (tid < nch) {
+        uint32_t hk = hvals[cb + tid];
+        const HpHalo H = halos[hk];
+        // centre relative to the tile origin, exact enough in FP32 after the FP64 shift
+        s_cx[tid] = (float)(H.cx - x0);
+        s_cy[tid] = (float)(H.cy - y0);
+        s_rap2[tid] = (float)(H.rad_px * H.rad_px);
+        s_irf[tid] = H.inv_rf_px;
+        s_ay[tid] = H.Ay;
+        s_ab[tid] = H.Ab;
+        s_tab[tid] = tab + (int64_t)hk * 2 * HP_ROW;
+        int i0, i1, j0, j1;
+        int4 bx = make_int4(1, 0, 1, 0);
+        if (hp_box(H, g, i0, i1, j0, j1)) {
+          bx.x = max(i0 - x0, 0);
+          bx.y = min(i1 - x0, TS - 1);
+          bx.z = max(j0 - y0, 0);
+          bx.w = min(j1 - y0, TS - 1);
+        }
+        s_box[tid] = bx;
+      }
+      __syncthreads();
+      for (int k = 0; k < nch; ++k) {
+        int4 bx = s_box[k];
+        if (bx.y < wc0 || bx.x > wc0 + 8 * PR - 1 || bx.w < wr0 || bx.z > wr0 + 4 * PR - 1)
+          continue;
+        const float hcx = s_cx[k], hcy = s_cy[k], rap2 = s_rap2[k], irf = s_irf[k];
+        const float* ty = s_tab[k];
+#pragma unroll
+        for (int r = 0; r < PR; ++r) {
+          float dy = (float)(r0 + r) + 0.5f - hcy;
+#pragma unroll
+          for (int c = 0; c < PR; ++c) {
+            float dx = (float)(c0 + c) + 0.5f - hcx;
+            float d2 = dx * dx + dy * dy;
+            if (d2 < rap2) {
+              float uu = sqrtf(d2) * irf;
+              if (uu < 1.0f) {
+                float chord = sqrtf(fmaxf(0.f, 1.0f - uu * uu));
+                float gy = catmull(ty, uu), gb = catmull(ty + HP_ROW, uu);
+                kahan_add(hy[r][c], cy_[r][c], s_ay[k] * chord * gy);
+                kahan_add(hb[r][c], cb_[r][c], s_ab[k] * chord * gb);
+              }
+            }
+          }
+        }
+      }
+    }
+    const int64_t mbase = (int64_t)mp * g.nx * g.ny;
+    if (U.slot < 0) {
+#pragma unroll
+      for (int r = 0; r < PR; ++r)
+#pragma unroll
+        for (int c = 0; c < PR; ++c) {
+          int gx = x0 + c0 + c, gy = y0 + r0 + r;
+          if (gx >= g.nx || gy >= g.ny) continue;
+          int64_t p = mbase + (int64_t)gy * g.nx + gx;
+          float s, e;
+          bp_two_sum(ymap[p], hy[r][c], s, e);
+          ymap[p] = s;
+          ylo[p] = ylo[p] + (e - cy_[r][c]);
+          bp_two_sum(bmap[p], hb[r][c], s, e);
+          bmap[p] = s;
+          blo[p] = blo[p] + (e - cb_[r][c]);
+        }
+    } else {
+      float* P = partials + U.slot * 4 * TS * TS;
+#pragma unroll
+      for (int r = 0; r < PR; ++r)
+#pragma unroll
+        for (int c = 0; c < PR; ++c) {
+          int q = (r0 + r) * TS + c0 + c;
+          P[q] = hy[r][c];
+          P[TS * TS + q] = -cy_[r][c];
+          P[2 * TS * TS + q] = hb[r][c];
+          P[3 * TS * TS + q] = -cb_[r][c];
+        }
+    }
+    __syncthreads();
+  }
+}
+
+template <int TS>
+__global__ void __launch_bounds__(256) k_hp_reduce(const int64_t* __restrict__ tstart,
+                                                   const int64_t* __restrict__ uoff,
+                                                   int64_t n_tiles, int unit, bp_map_geom g,
+                                                   const float* __restrict__ partials,
+                                                   float* ymap, float* bmap, float* ylo,
+                                                   float* blo) {
+  int64_t t = blockIdx.x;
+  if (t >= n_tiles) return;
+  int64_t nu = (tstart[t + 1] - tstart[t] + unit - 1) / unit;
+  if (nu <= 1) return;
+  int ntx = (g.nx + TS - 1) / TS, nty = (g.ny + TS - 1) / TS;
+  int mp = (int)(t / ((int64_t)ntx * nty)), rem = (int)(t % ((int64_t)ntx * nty));
+  int x0 = (rem % ntx) * TS, y0 = (rem / ntx) * TS;
+  int64_t u0 = uoff[t];
+  for (int q = threadIdx.x; q < TS * TS; q += blockDim.x) {
+    int gx = x0 + q % TS, gy = y0 + q / TS;
+    if (gx >= g.nx || gy >= g.ny) continue;
+    float hy = 0.f, ly = 0.f, hb = 0.f, lb = 0.f;
+    for (int64_t k = 0; k < nu; ++k) {
+      const float* P = partials + (u0 + k) * 4 * TS * TS;
+      float s, e;
+      bp_two_sum(hy, P[q], s, e);
+      hy = s;
+      ly += P[TS * TS + q] + e;
+      bp_two_sum(hb, P[2 * TS * TS + q], s, e);
+      hb = s;
+      lb += P[3 * TS * TS + q] + e;
+    }
+    int64_t p = (int64_t)mp * g.nx * g.ny + (int64_t)gy * g.nx + gx;
+    float s, e;
+    bp_two_sum(ymap[p], hy, s, e);
+    ymap[p] = s;
+    ylo[p] = ylo[p] + (ly + e);
+    bp_two_sum(bmap[p], hb, s, e);
+    bmap[p] = s;
+    blo[p] = blo[p] + (lb + e);
+  }
+}
+
+__global__ void k_finalize(int64_t npix, float* map, float* lo, float scale) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npix) return;
+  float v = map[i];
+  if (lo) {
+    v = v + lo[i];
+    lo[i] = 0.f;
+  }
+  map[i] = v * scale;
+}
+
+template <int TS>
+int hp_run(bp_ctx* ctx, int64_t n, const HpHalo* halos, const float* tab, const bp_map_geom* g,
+           float* ymap, float* bmap, float* ylo, float* blo) {
+  int r;
+  const int ntx = (g->nx + TS - 1) / TS, nty = (g->ny + TS - 1) / TS;
+  const int64_t n_tiles = (int64_t)ntx * nty * g->n_maps;
+  uint32_t* counts;
+  int64_t* offs;
+  if ((r = bp_ws(ctx, WS_COUNTS, (size_t)(n + 1) * 4, (void**)&counts))) return r;
+  if ((r = bp_ws(ctx, WS_OFFS, (size_t)(n + 1) * 8, (void**)&offs))) return r;
+  unsigned nb = (unsigned)((n + 255) / 256);
+  bp_phase_begin(ctx, BP_PH_HP_PAIRS);
+  k_hp_count<<<nb, 256, 0, ctx->stream>>>(halos, n, *g, TS, counts);
+  BP_LAUNCH_CHECK(ctx, "hp count");
+  if ((r = bp_scan_u32_to_i64(ctx, counts, offs, n))) return r;
+  BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, offs + n, 8, cudaMemcpyDeviceToHost, ctx->stream));
+  BP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const int64_t np = ctx->h_pinned[0];
+  if (np == 0) return BP_OK;
+  if (np > (int64_t)UINT32_MAX) return bp_fail(ctx, BP_ERANGE, "paste_halos: too many pairs");
+  uint32_t *k0, *v0, *k1, *v1, *ks, *vs;
+  if ((r = bp_ws(ctx, WS_KEYS0, (size_t)np * 4, (void**)&k0))) return r;
+  if ((r = bp_ws(ctx, WS_VALS0, (size_t)np * 4, (void**)&v0))) return r;
+  if ((r = bp_ws(ctx, WS_KEYS1, (size_t)np * 4, (void**)&k1))) return r;
+  if ((r = bp_ws(ctx, WS_VALS1, (size_t)np * 4, (void**)&v1))) return r;
+  k_hp_emit<<<nb, 256, 0, ctx->stream>>>(halos, n, *g, TS, offs, k0, v0);
+  BP_LAUNCH_CHECK(ctx, "hp emit");
+  int key_bits = 0;
+  while (((int64_t)1 << key_bits) < n_tiles) ++key_bits;
+  if ((r = bp_radix_sort_pairs(ctx, k0, v0, k1, v1, np, key_bits, &ks, &vs))) return r;
+  int64_t* tstart;
+  if ((r = bp_ws(ctx, WS_TILES, (size_t)(n_tiles + 1) * 20 + 64, (void**)&tstart))) return r;
+  int64_t* uoff = tstart + (n_tiles + 1);
+  uint32_t* uc = (uint32_t*)(uoff + (n_tiles + 1));
+  if ((r = bp_tile_ranges(ctx, ks, np, n_tiles, tstart))) return r;
+  const int unit = 512;
+  unsigned tb = (unsigned)((n_tiles + 255) / 256);
+  k_hp_ucount<<<tb, 256, 0, ctx->stream>>>(tstart, n_tiles, unit, uc);
+  BP_LAUNCH_CHECK(ctx, "hp unit count");
+  if ((r = bp_scan_u32_to_i64(ctx, uc, uoff, n_tiles))) return r;
+  const int64_t max_units = n_tiles + np / unit + 1;
+  HpUnit* units;
+  if ((r = bp_ws(ctx, WS_UNITS, (size_t)max_units * sizeof(HpUnit), (void**)&units))) return r;
+  k_hp_uemit<<<tb, 256, 0, ctx->stream>>>(tstart, n_tiles, unit, uoff, units);
+  BP_LAUNCH_CHECK(ctx, "hp units");
+  float* partials;
+  if ((r = bp_ws(ctx, WS_PART, (size_t)max_units * 4 * TS * TS * 4, (void**)&partials))) return r;
+  BP_CUDA(ctx, cudaMemsetAsync(ctx->d_counter + 2, 0, 8, ctx->stream));
+  bp_phase_end(ctx, BP_PH_HP_PAIRS);
+  int per_sm = 0;
+  BP_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hp_paste<TS>, HP_THREADS, 0));
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)ctx->num_sms * per_sm;
+  if (grid > max_units) grid = max_units;
+  bp_phase_begin(ctx, BP_PH_HP_PASTE);
+  k_hp_paste<TS><<<(unsigned)grid, HP_THREADS, 0, ctx->stream>>>(
+      halos, tab, vs, units, uoff + n_tiles, ctx->d_counter + 2, *g, ymap, bmap, ylo, blo,
+      partials);
+  BP_LAUNCH_CHECK(ctx, "hp paste");
+  k_hp_reduce<TS><<<(unsigned)n_tiles, 256, 0, ctx->stream>>>(tstart, uoff, n_tiles, unit, *g,
+                                                             partials, ymap, bmap, ylo, blo);
+  BP_LAUNCH_CHECK(ctx, "hp reduce");
+  bp_phase_end(ctx, BP_PH_HP_PASTE);
+  return BP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bp_paste_halos(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_y,
+                   const float* v_los, const int32_t* map_id, const double* model,
+                   const int32_t* status, const bp_map_geom* geom, double ap_r500, float* ymap,
+                   float* bmap, float* ylo, float* blo) {
+  if (!ctx) return BP_EINVAL;
+  if (!geom || geom->nx <= 0 || geom->ny <= 0 || geom->n_maps <= 0 || !(geom->dtheta > 0))
+    return bp_fail(ctx, BP_EINVAL, "bp_paste_halos: bad geometry");
+  if (n < 0) return bp_fail(ctx, BP_EINVAL, "bp_paste_halos: n < 0");
+  if (n > (int64_t)UINT32_MAX) return bp_fail(ctx, BP_ERANGE, "bp_paste_halos: n >= 2^32");
+  if (n == 0) return BP_OK;
+  if (!th_x || !th_y || !v_los || !model || !status || !ymap || !bmap || !ylo || !blo)
+    return bp_fail(ctx, BP_EINVAL, "bp_paste_halos: null pointer");
+  if (ap_r500 < 0) return bp_fail(ctx, BP_EINVAL, "bp_paste_halos: ap_r500 < 0");
+  int r = hp_constants(ctx);
+  if (r) return r;
+  HpHalo* halos;
+  if ((r = bp_ws(ctx, WS_HPAR, (size_t)n * sizeof(HpHalo), (void**)&halos))) return r;
+  float* tab;
+  if ((r = bp_ws(ctx, WS_TABLE, (size_t)n * 2 * HP_ROW * sizeof(float), (void**)&tab))) return r;
+  unsigned nb = (unsigned)((n + 255) / 256);
+  bp_phase_begin(ctx, BP_PH_HP_TABLE);
+  k_hp_prep<<<nb, 256, 0, ctx->stream>>>(ctx->p, n, th_x, th_y, v_los, map_id, model, status,
+                                         *geom, ap_r500, halos);
+  BP_LAUNCH_CHECK(ctx, "hp prep");
+  const BpParams& P = ctx->p;
+  double rn = rint(P.n_poly);
+  int n_int = (fabs(P.n_poly - rn) < 1e-12 && rn >= 1 && rn <= 16) ? (int)rn : -1;
+  int64_t nt = n * (HP_NT + 1);
+  k_hp_table<<<(unsigned)((nt + 255) / 256), 256, 0, ctx->stream>>>(halos, n, (float)P.n_poly,
+                                                                   n_int, (float)P.n_nt, tab);
+  BP_LAUNCH_CHECK(ctx, "hp table");
+  k_hp_ghosts<<<nb, 256, 0, ctx->stream>>>(halos, n, tab);
+  BP_LAUNCH_CHECK(ctx, "hp ghosts");
+  bp_phase_end(ctx, BP_PH_HP_TABLE);
+  if (ctx->hp_tile == 64) return hp_run<64>(ctx, n, halos, tab, geom, ymap, bmap, ylo, blo);
+  return hp_run<32>(ctx, n, halos, tab, geom, ymap, bmap, ylo, blo);
+}
+
+int bp_finalize_map(bp_ctx* ctx, const bp_map_geom* geom, float* ymap, float* bmap, float* ylo,
+                    float* blo, int out_kind, double nu_ghz) {
+  if (!ctx) return BP_EINVAL;
+  if (!geom || geom->nx <= 0 || geom->ny <= 0 || geom->n_maps <= 0)
+    return bp_fail(ctx, BP_EINVAL, "bp_finalize_map: bad geometry");
+  if (out_kind != BP_OUT_YB && out_kind != BP_OUT_DT)
+    return bp_fail(ctx, BP_EINVAL, "bp_finalize_map: out_kind");
+  float sy = 1.f, sb = 1.f;
+  if (out_kind == BP_OUT_DT) {
+    if (!(nu_ghz > 0)) return bp_fail(ctx, BP_EINVAL, "bp_finalize_map: nu_ghz <= 0");
+    // g_nu(x) = x (e^x + 1)/(e^x - 1) - 4 (Section 3.2), x = h nu / (k T_CMB)
+    double x = bpc::H_PLANCK * nu_ghz * 1e9 / (bpc::K_BOLTZ * ctx->p.Tcmb);
+    sy = (float)(x * (exp(x) + 1.0) / (exp(x) - 1.0) - 4.0);
+    sb = -1.f;
+  }
+  int64_t npix = (int64_t)geom->nx * geom->ny * geom->n_maps;
+  unsigned nb = (unsigned)((npix + 255) / 256);
+  bp_phase_begin(ctx, BP_PH_FINALIZE);
+  if (ymap) {
+    k_finalize<<<nb, 256, 0, ctx->stream>>>(npix, ymap, ylo, sy);
+    BP_LAUNCH_CHECK(ctx, "finalize y");
+  }
+  if (bmap) {
+    k_finalize<<<nb, 256, 0, ctx->stream>>>(npix, bmap, blo, sb);
+    BP_LAUNCH_CHECK(ctx, "finalize b");
+  }
+  bp_phase_end(ctx, BP_PH_FINALIZE);
+  return BP_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,184 @@
+// bp_internal.cuh -- shared declarations of the CUDA implementation of bp.h.
+// Device helpers, the context, the background tables and the error plumbing.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "../../include/bp.h"
+
+// ---------------------------------------------------------------- constants
+// Physical constants (CODATA 2018 / IAU 2015 nominal values).
+namespace bpc {
+constexpr double PI = 3.14159265358979323846;
+constexpr double C_KMS = 299792.458;
+constexpr double G_SI = 6.67430e-11;
+constexpr double MSUN_KG = 1.98840987e30;
+constexpr double MPC_M = 3.0856775814913673e22;
+constexpr double SIGMA_T = 6.6524587321e-29;
+constexpr double ME_C2_J = 8.1871057769e-14;
+constexpr double MP_KG = 1.67262192369e-27;
+constexpr double H_PLANCK = 6.62607015e-34;
+constexpr double K_BOLTZ = 1.380649e-23;
+// G in Mpc (km/s)^2 / Msun
+constexpr double G = G_SI * MSUN_KG / (MPC_M * 1.0e6);
+}  // namespace bpc
+
+// ---------------------------------------------------------------- tables
+// Background quantities tabulated on the host in FP64 and interpolated on the
+// device with cubic Hermite splines (values + exact derivatives at the nodes).
+struct BpTables {
+  // uniform in z: chi(z) [Mpc comoving] and tau(z)
+  const double* chi_z;   // [nz] values
+  const double* dchi_z;  // [nz] dchi/dz = c/H
+  const double* tau_z;   // [nz]
+  const double* dtau_z;  // [nz]
+  int nz;
+  double dz;
+  // uniform in chi (FP32, for particles): z(chi) and tau(chi)
+  const float* z_c;    // [nc]
+  const float* dz_c;   // [nc] dz/dchi
+  const float* tau_c;  // [nc]
+  const float* dtau_c; // [nc] dtau/dchi
+  int nc;
+  float dchi;
+  float inv_dchi;
+};
+
+struct BpParams {
+  // cosmology
+  double Om, Ob, h, Tcmb, XH;
+  double fb, mu_e, pe_frac;  // f_b, mu_e = 2/(1+X), P_e/P_th = (2X+2)/(5X+3)
+  double rho_cr0;            // Msun/Mpc^3
+  // ICM
+  double Gamma, n_poly, eps_dm, eps_star, f_star, S_star, alpha_nt, beta_nt, n_nt;
+  int energy_sign, field_fb;
+  // observables: y per (P x length) and sigma_T n_e per (rho_g x length)
+  double CP, CN;
+};
+
+// ---------------------------------------------------------------- context
+enum { WS_COUNTS = 0, WS_OFFS, WS_KEYS0, WS_VALS0, WS_KEYS1, WS_VALS1, WS_HIST, WS_TILES,
+       WS_UNITS, WS_PART, WS_MISC, WS_TABLE, WS_HPAR, WS_NSLOTS };
+
+struct bp_ctx {
+  BpParams p;
+  BpTables t;
+  cudaStream_t stream;
+  void* table_mem;
+  void* ws[WS_NSLOTS];
+  size_t ws_bytes[WS_NSLOTS];
+  int64_t* d_counter;  // small device scalars
+  int* d_flags;
+  int64_t* h_pinned;   // pinned host scalars
+  int num_sms;
+  int pp_tile, hp_tile, pp_unit;
+  int timing;
+  cudaEvent_t ev[BP_NPHASES][2];
+  double ph_ms[BP_NPHASES];
+  int ph_open[BP_NPHASES];
+  int64_t launches;
+  char msg[512];
+};
+
+// phase timing (no-ops unless bp_set_timing(ctx, 1))
+void bp_phase_begin(bp_ctx* ctx, int ph);
+void bp_phase_end(bp_ctx* ctx, int ph);
+
+int bp_fail(bp_ctx* ctx, int code, const char* fmt, ...);
+int bp_cuda_check(bp_ctx* ctx, cudaError_t e, const char* what);
+int bp_ws(bp_ctx* ctx, int slot, size_t bytes, void** out);
+
+#define BP_CUDA(ctx, call)                                        \
+  do {                                                            \
+    cudaError_t e_ = (call);                                      \
+    if (e_ != cudaSuccess) return bp_cuda_check(ctx, e_, #call);  \
+  } while (0)
+
+// checks the preceding kernel launch and counts it
+#define BP_LAUNCH_CHECK(ctx, what)                                        \
+  do {                                                                    \
+    (ctx)->launches++;                                                    \
+    cudaError_t e_ = cudaGetLastError();                                  \
+    if (e_ != cudaSuccess) return bp_cuda_check(ctx, e_, what);           \
+  } while (0)
+
+// ---------------------------------------------------------------- device helpers
+__device__ __forceinline__ double bp_hermite(const double* v, const double* d, int n, double h,
+                                             double x) {
+  double u = x / h;
+  int i = (int)u;
+  if (i < 0) i = 0;
+  if (i > n - 2) i = n - 2;
+  double t = u - i;
+  double t2 = t * t, t3 = t2 * t;
+  double h00 = 2 * t3 - 3 * t2 + 1, h10 = t3 - 2 * t2 + t, h01 = -2 * t3 + 3 * t2,
+         h11 = t3 - t2;
+  return h00 * v[i] + h10 * h * d[i] + h01 * v[i + 1] + h11 * h * d[i + 1];
+}
+
+__device__ __forceinline__ float bp_hermitef(const float* v, const float* d, int n, float h,
+                                             float inv_h, float x) {
+  float u = x * inv_h;
+  int i = (int)u;
+  if (i < 0) i = 0;
+  if (i > n - 2) i = n - 2;
+  float t = u - (float)i;
+  float t2 = t * t, t3 = t2 * t;
+  float h00 = 2.f * t3 - 3.f * t2 + 1.f, h10 = t3 - 2.f * t2 + t, h01 = -2.f * t3 + 3.f * t2,
+        h11 = t3 - t2;
+  return h00 * __ldg(v + i) + h10 * h * __ldg(d + i) + h01 * __ldg(v + i + 1) +
+         h11 * h * __ldg(d + i + 1);
+}
+
+// Integrated normalised kernel in the "split" representation used by the deposit:
+// with e = dx / h, returns w(e) for dx < 0 and w(e) - 1 = -w(-e) for dx >= 0.
+// Differences of these values give pixel weights without cancellation near w = 1.
+// Only the left half of the printed piecewise quartic (x <= 0) is evaluated.
+__device__ __forceinline__ float bp_wsplit(float dx, float h) {
+  float u = -fabsf(dx / h);  // u <= 0
+  float wl;
+  if (u <= -1.0f) {
+    wl = 0.0f;
+  } else if (u <= -0.5f) {
+    float t = 1.0f + u;
+    float t2 = t * t;
+    wl = (2.0f / 3.0f) * t2 * t2;
+  } else {
+    float u2 = u * u;
+    // (4/3)(3/8 + u - 2u^3 - 3/2 u^4) = 1/2 + 4/3 u - 8/3 u^3 - 2 u^4
+    wl = 0.5f + u * ((4.0f / 3.0f) + u2 * (-(8.0f / 3.0f) - 2.0f * u));
+  }
+  return dx < 0.0f ? wl : -wl;
+}
+
+// Pixel span of a particle, decided in FP32 with round-to-nearest and no
+// contraction: columns floor(c - h) .. floor(c + h), clipped to [0, n-1].
+// A negative or NaN radius covers nothing.
+__device__ __forceinline__ bool bp_span(float c, float h, int n, int& lo, int& hi) {
+  if (!(h >= 0.0f)) return false;
+  float a = __fsub_rn(c, h), b = __fadd_rn(c, h);
+  if (!(a == a) || !(b == b)) return false;
+  float fa = floorf(a), fb = floorf(b);
+  if (fb < 0.0f || fa > (float)(n - 1)) return false;
+  lo = fa < 0.0f ? 0 : (int)fa;
+  hi = fb > (float)(n - 1) ? n - 1 : (int)fb;
+  return true;
+}
+
+// Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
+__device__ __forceinline__ void bp_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// host helpers implemented in the .cu files
+int bp_scan_u32_to_i64(bp_ctx* ctx, const uint32_t* in, int64_t* out, int64_t n);
+int bp_radix_sort_pairs(bp_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
+                        uint32_t* vals_tmp, int64_t n, int key_bits, uint32_t** keys_out,
+                        uint32_t** vals_out);
+int bp_tile_ranges(bp_ctx* ctx, const uint32_t* keys, int64_t n, int64_t n_tiles,
+                   int64_t* tile_start);

@@ -1,0 +1,661 @@
+// bp_pp.cu -- particle-based pasting (Section 3.4).
+//
+//  k_halo_block    per-halo FP32 constants of the solved profiles
+//  k_assign        per particle: sky angles (FP64), pixel coordinates, kernel radius,
+//                  y_i and b_i (Eqs. y_i^PP,h, b_i^PP,h, field_y, field_b)
+//  k_pair_count /  (tile, particle) pairs of every tile a particle's 2h square
+//  k_pair_emit     touches, in particle order
+//  radix sort      stable by tile key (bp_sort.cu)
+//  k_units         split each tile's particle list into work units
+//  k_deposit       persistent: one CTA accumulates one work unit's particles into a
+//                  register/shared-memory tile with the separable pixel-integrated
+//                  kernel f_ij (Eqs. f_ij, integrated kernel); compensated FP32 sums;
+//                  single-unit tiles are added to the map directly, others are
+//                  written as partial tiles
+//  k_reduce_tiles  adds the partial tiles of multi-unit tiles in unit order
+// No global atomics touch the maps; every pixel sum is in a fixed order.
+#include "bp_internal.cuh"
+
+namespace {
+
+// ---------------------------------------------------------------- halo constants
+// FP32 per-halo block used by the assignment (16 floats):
+//  [0] sx   comoving h^-1 Mpc -> x = r/r_s
+//  [1] xf   r_f / r_s
+//  [2] c    r_vir / r_s
+//  [3] q500 r_s / r500
+//  [4] psi  G M / (m(c) r_s (n+1) T)   (theta = 1 - psi g(x) inside r_vir)
+//  [5] A0   |Phi0| / ((n+1) T)          (theta = 1 - A0 + A1 / x outside r_vir)
+//  [6] A1   G M / (r_s (n+1) T)
+//  [7] ant  alpha_nt f(z)
+//  [8] KY   sigma_T/(m_e c^2) (P_e/P_th) P0 M_p / rho_s  [y units x Mpc^2]
+//  [9] KB   sigma_T rho0/(mu_e m_p) M_p / rho_s        [b units x Mpc^2]
+//  [10] ok  1 if the halo solved
+constexpr int HB = 16;
+
+__global__ void k_halo_block(BpParams P, int64_t nh, const double* __restrict__ model,
+                             const int32_t* __restrict__ status, double Mp, float* blk) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nh) return;
+  auto F = [&](int f) { return model[(int64_t)f * nh + k]; };
+  double rs = F(BP_M_RS), c = F(BP_M_C), z = F(BP_M_Z), M = F(BP_M_MVIR), mc = F(BP_M_MC);
+  double T = F(BP_M_T), n1T = (P.n_poly + 1.0) * T;
+  double GM = bpc::G * M;
+  float* b = blk + k * HB;
+  bool ok = status[k] == BP_HALO_OK && rs > 0 && T > 0;
+  b[0] = ok ? (float)(1.0 / (P.h * (1.0 + z) * rs)) : 0.f;
+  b[1] = ok ? (float)(F(BP_M_RF) / rs) : 0.f;
+  b[2] = (float)c;
+  b[3] = ok ? (float)(rs / F(BP_M_R500)) : 0.f;
+  b[4] = ok ? (float)(GM / (mc * rs * n1T)) : 0.f;
+  b[5] = ok ? (float)(-F(BP_M_PHI0) / n1T) : 0.f;
+  b[6] = ok ? (float)(GM / (rs * n1T)) : 0.f;
+  b[7] = (float)F(BP_M_ANT);
+  double rhos = F(BP_M_RHOS);
+  b[8] = ok ? (float)(P.CP * P.pe_frac * F(BP_M_P0) * Mp / rhos) : 0.f;
+  b[9] = ok ? (float)(P.CN * F(BP_M_RHO0) * Mp / rhos) : 0.f;
+  b[10] = ok ? 1.f : 0.f;
+  for (int q = 11; q < HB; ++q) b[q] = 0.f;
+}
+
+// 1 - ln(1+x)/x without cancellation
+__device__ __forceinline__ float g_inner(float x) {
+  if (x < 2e-2f) return x * (0.5f - x * (1.0f / 3.0f - x * (0.25f - x * 0.2f)));
+  return 1.0f - log1pf(x) / x;
+}
+
+__device__ __forceinline__ float powi_or_pow(float t, float n, int n_int) {
+  if (n_int > 0) {
+    float r = 1.f, b = t;
+    int e = n_int;
+    while (e) {
+      if (e & 1) r *= b;
+      b *= b;
+      e >>= 1;
+    }
+    return r;
+  }
+  return powf(t, n);
+}
+
+struct AssignArgs {
+  const float *x, *y, *z, *vx, *vy, *vz, *hs;
+  const int32_t* hid;
+  const float* hpos;
+  const float* blk;
+  int64_t n, nh;
+  double th0x, th0y, inv_dth;
+  float inv_h;        // 1/h (h^-1 Mpc -> Mpc)
+  float inv_h_dth;    // 1/(h dtheta)
+  float inv_om_pix;   // 1/dtheta^2
+  float field_B;      // C_N M_p(/f_b) / c  [b units x Mpc^2 / (km/s)]
+  float n_poly;
+  int n_int;
+  float n_nt;
+  float* out;
+};
+
+__global__ void __launch_bounds__(256) k_assign(AssignArgs a, BpTables T) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  float xf = a.x[i], yf = a.y[i], zf = a.z[i];
+  // sky angles and pixel coordinates in FP64
+  double thx = atan2((double)xf, (double)zf), thy = atan2((double)yf, (double)zf);
+  float px = (float)((thx - a.th0x) * a.inv_dth);
+  float py = (float)((thy - a.th0y) * a.inv_dth);
+  float r2 = xf * xf + yf * yf + zf * zf;
+  float rh = sqrtf(r2);       // comoving h^-1 Mpc
+  float chi = rh * a.inv_h;   // comoving Mpc
+  float Y = 0.f, B = 0.f, kind = (float)BP_KIND_NONE;
+  float hp = 0.f;
+  if (rh > 0.f) {
+    hp = a.hs[i] * a.inv_h_dth / chi;
+    float zz = bp_hermitef(T.z_c, T.dz_c, T.nc, T.dchi, T.inv_dchi, chi);
+    float tau = bp_hermitef(T.tau_c, T.dtau_c, T.nc, T.dchi, T.inv_dchi, chi);
+    float DA = chi / (1.0f + zz);
+    float vr = (a.vx[i] * xf + a.vy[i] * yf + a.vz[i] * zf) / rh;
+    float geo = a.inv_om_pix / (DA * DA);
+    float ekin = expf(-tau) * vr;
+    int32_t k = a.hid[i];
+    if (k < 0) {
+      B = a.field_B * ekin * geo;
+      kind = (float)BP_KIND_FIELD;
+    } else if (k < a.nh) {
+      const float* b = a.blk + (int64_t)k * HB;
+      if (b[10] != 0.f) {
+        float dx = xf - a.hpos[k], dy = yf - a.hpos[a.nh + k], dz = zf - a.hpos[2 * a.nh + k];
+        float x = sqrtf(dx * dx + dy * dy + dz * dz) * b[0];
+        if (x < b[1]) {
+          float th = (x <= b[2]) ? 1.0f - b[4] * g_inner(x) : 1.0f - b[5] + b[6] / x;
+          th = fmaxf(th, 0.f);
+          float thn = powi_or_pow(th, a.n_poly, a.n_int);
+          float Rnt = b[7] * __powf(x * b[3], a.n_nt);
+          float vol = x * (1.0f + x) * (1.0f + x);  // rho_s / rho_NFW(r)
+          Y = b[8] * thn * th * fmaxf(0.f, 1.0f - Rnt) * vol * geo;
+          B = b[9] * thn * vol * ekin * geo * (1.0f / (float)bpc::C_KMS);
+          kind = (float)BP_KIND_HALO;
+        }
+      }
+    }
+  }
+  float4* o = reinterpret_cast<float4*>(a.out + i * BP_ASSIGNED_STRIDE);
+  o[0] = make_float4(px, py, hp, Y);
+  o[1] = make_float4(B, kind, 0.f, 0.f);
+}
+
+// ---------------------------------------------------------------- pairs
+__device__ __forceinline__ bool particle_tiles(const float4 r0, const float4 r1, int nx, int ny,
+                                               int ts, int select, int& tx0, int& tx1, int& ty0,
+                                               int& ty1) {
+  int kind = (int)r1.y;
+  if (kind == BP_KIND_NONE) return false;
+  if (select == BP_SELECT_HALO && kind != BP_KIND_HALO) return false;
+  if (select == BP_SELECT_FIELD && kind != BP_KIND_FIELD) return false;
+  int i0, i1, j0, j1;
+  if (!bp_span(r0.x, r0.z, nx, i0, i1)) return false;
+  if (!bp_span(r0.y, r0.z, ny, j0, j1)) return false;
+  tx0 = i0 / ts;
+  tx1 = i1 / ts;
+  ty0 = j0 / ts;
+  ty1 = j1 / ts;
+  return true;
+}
+
+__global__ void k_pair_count(const float4* __restrict__ rec, int64_t n, int nx, int ny, int ts,
+                             int select, uint32_t* counts) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int tx0, tx1, ty0, ty1;
+  uint32_t c = 0;
+  if (particle_tiles(rec[2 * i], rec[2 * i + 1], nx, ny, ts, select, tx0, tx1, ty0, ty1))
+    c = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+  counts[i] = c;
+}
+
+__global__ void k_pair_emit(const float4* __restrict__ rec, int64_t n, int nx, int ny, int ts,
+                            int select, int ntx, const int64_t* __restrict__ offs,
+                            uint32_t* keys, uint32_t* vals) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int tx0, tx1, ty0, ty1;
+  if (!particle_tiles(rec[2 * i], rec[2 * i + 1], nx, ny, ts, select, tx0, tx1, ty0, ty1))
+    return;
+  int64_t o = offs[i];
+  for (int ty = ty0; ty <= ty1; ++ty)
+    for (int tx = tx0; tx <= tx1; ++tx) {
+      keys[o] = (uint32_t)(ty * ntx + tx);
+      vals[o] = (uint32_t)i;
+      ++o;
+    }
+}
+
+// ---------------------------------------------------------------- work units
+struct Unit {
+  int tile;
+  int slot;      // partial slot, -1 = the tile's only unit (adds to the map directly)
+  int64_t begin;
+  int64_t end;
+};
+
+__global__ void k_unit_count(const int64_t* __restrict__ tstart, int64_t n_tiles, int unit,
+                             uint32_t* ucount) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tiles) return;
+  int64_t len = tstart[t + 1] - tstart[t];
+  ucount[t] = (uint32_t)((len + unit - 1) / unit);
+}
+
+__global__ void k_unit_emit(const int64_t* __restrict__ tstart, int64_t n_tiles, int unit,
+                            const int64_t* __restrict__ uoff, Unit* units) {
+  int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n_tiles) return;
+  int64_t b = tstart[t], e = tstart[t + 1];
+  int64_t nu = (e - b + unit - 1) / unit;
+  int64_t u0 = uoff[t];
+  for (int64_t q = 0; q < nu; ++q) {
+    Unit U;
+    U.tile = (int)t;
+    U.slot = nu > 1 ? (int)(u0 + q) : -1;
+    U.begin = b + q * unit;
+    U.end = min(e, b + (q + 1) * unit);
+    units[u0 + q] = U;
+  }
+}
+
+// ---------------------------------------------------------------- deposit
+constexpr int DEP_THREADS = 256;
+constexpr int CH = 32;  // particles per chunk
+
+template <int TS>
+struct DepSmem {
+  float a[CH][TS];    // column weights
+  float by[CH][TS];   // Y * row weights
+  float bb[CH][TS];   // B * row weights
+  float ex[CH][TS + 1];
+  float ey[CH][TS + 1];
+  float lo_y[TS * TS];
+  float lo_b[TS * TS];
+  float4 p0[CH];      // px, py, hp, Y
+  float p1[CH];       // B
+  int4 box[CH];       // footprint in tile coordinates i0, i1, j0, j1 (i0 > i1: none)
+  int hasy[CH];
+  int64_t unit;
+};
+
+template <int TS>
+__device__ __forceinline__ void fold_chunk(float (&acc)[TS / 16][TS / 16],
+                                           float (&hi)[TS / 16][TS / 16], float* lo, int r0,
+                                           int c0) {
+  constexpr int PR = TS / 16;
+#pragma unroll
+  for (int r = 0; r < PR; ++r)
+#pragma unroll
+    for (int c = 0; c < PR; ++c) {
+      float s, e;
+      bp_two_sum(hi[r][c], acc[r][c], s, e);
+      hi[r][c] = s;
+      lo[(r0 + r) * TS + c0 + c] += e;
+      acc[r][c] = 0.f;
+    }
+}
+
+template <int TS>
+__global__ void __launch_bounds__(DEP_THREADS, 2)
+    k_deposit(const float4* __restrict__ rec, const uint32_t* __restrict__ pvals,
+              const Unit* __restrict__ units, const int64_t* __restrict__ n_units_ptr,
+              int64_t* counter, int nx, int ny, int ntx, float* ymap, float* bmap, float* ylo,
+              float* blo, float* partials) {
+  constexpr int PR = TS / 16;  // pixels per thread along each axis
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  DepSmem<TS>& S = *reinterpret_cast<DepSmem<TS>*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int lr = lane >> 3, lc = lane & 7;
+  const int wr0 = (w >> 1) * 4 * PR, wc0 = (w & 1) * 8 * PR;  // warp band origin
+  const int r0 = wr0 + lr * PR, c0 = wc0 + lc * PR;              // thread block origin
+  const int64_t n_units = *n_units_ptr;
+  for (;;) {
+    if (tid == 0) S.unit = atomicAdd((unsigned long long*)counter, 1ull);
+    __syncthreads();
+    const int64_t u = S.unit;
+    if (u >= n_units) break;
+    const Unit U = units[u];
+    const int tyi = U.tile / ntx, txi = U.tile % ntx;
+    const int x0 = txi * TS, y0 = tyi * TS;
+    for (int q = tid; q < TS * TS; q += DEP_THREADS) {
+      S.lo_y[q] = 0.f;
+      S.lo_b[q] = 0.f;
+    }
+    float acc_y[PR][PR], acc_b[PR][PR], hi_y[PR][PR], hi_b[PR][PR];
+#pragma unroll
+    for (int r = 0; r < PR; ++r)
+#pragma unroll
+      for (int c = 0; c < PR; ++c) acc_y[r][c] = acc_b[r][c] = hi_y[r][c] = hi_b[r][c] = 0.f;
+    for (int64_t cb = U.begin; cb < U.end; cb += CH) {
+      const int nch = (int)min((int64_t)CH, U.end - cb);
+      __syncthreads();  // previous chunk fully consumed
+      // 1. gather particle records and footprints
+      if (tid < nch) {
+        uint32_t pi = pvals[cb + tid];
+        float4 q0 = rec[2 * (int64_t)pi];
+        float4 q1 = rec[2 * (int64_t)pi + 1];
+        S.p0[tid] = q0;
+        S.p1[tid] = q1.x;
+        int i0, i1, j0, j1;
+        int4 bx = make_int4(1, 0, 1, 0);
+        if (bp_span(q0.x, q0.z, nx, i0, i1) && bp_span(q0.y, q0.z, ny, j0, j1)) {
+          bx.x = max(i0 - x0, 0);
+          bx.y = min(i1 - x0, TS - 1);
+          bx.z = max(j0 - y0, 0);
+          bx.w = min(j1 - y0, TS - 1);
+        }
+        S.box[tid] = bx;
+        S.hasy[tid] = q0.w != 0.f;
+      }
+      __syncthreads();
+      // 2. split-kernel values at the TS+1 pixel edges of both axes
+      for (int q = tid; q < nch * (TS + 1); q += DEP_THREADS) {
+        int k = q / (TS + 1), e = q % (TS + 1);
+        float4 p = S.p0[k];
+        float dx = (float)(x0 + e) - p.x, dy = (float)(y0 + e) - p.y;
+        if (p.z > 0.f) {
+          S.ex[k][e] = bp_wsplit(dx, p.z);
+          S.ey[k][e] = bp_wsplit(dy, p.z);
+        } else {  // unused by the nearest-grid-point weights
+          S.ex[k][e] = 0.f;
+          S.ey[k][e] = 0.f;
+        }
+      }
+      __syncthreads();
+      // 3. pixel weights (difference of edge values, +1 in the cell holding the centre)
+      for (int q = tid; q < nch * TS; q += DEP_THREADS) {
+        int k = q / TS, e = q % TS;
+        float4 p = S.p0[k];
+        float ex0 = (float)(x0 + e), ex1 = ex0 + 1.f;
+        float ey0 = (float)(y0 + e), ey1 = ey0 + 1.f;
+        float ax, ay;
+        if (p.z > 0.f) {
+          ax = S.ex[k][e + 1] - S.ex[k][e] + ((ex0 < p.x && ex1 >= p.x) ? 1.f : 0.f);
+          ay = S.ey[k][e + 1] - S.ey[k][e] + ((ey0 < p.y && ey1 >= p.y) ? 1.f : 0.f);
+        } else {  // h = 0: nearest grid point
+          ax = (ex0 <= p.x && p.x < ex1) ? 1.f : 0.f;
+          ay = (ey0 <= p.y && p.y < ey1) ? 1.f : 0.f;
+        }
+        S.a[k][e] = ax;
+        S.by[k][e] = p.w * ay;
+        S.bb[k][e] = S.p1[k] * ay;
+      }
+      __syncthreads();
+      // 4. rank-1 updates of this thread's PR x PR pixels
+      for (int k = 0; k < nch; ++k) {
+        int4 bx = S.box[k];
+        bool touch = !(bx.y < wc0 || bx.x > wc0 + 8 * PR - 1 || bx.w < wr0 ||
+                       bx.z > wr0 + 4 * PR - 1);
+        if (!touch) continue;  // warp-uniform skip
+        float av[PR], bvb[PR];
+#pragma unroll
+        for (int c = 0; c < PR; ++c) av[c] = S.a[k][c0 + c];
+#pragma unroll
+        for (int r = 0; r < PR; ++r) bvb[r] = S.bb[k][r0 + r];
+#pragma unroll
+        for (int r = 0; r < PR; ++r)
+#pragma unroll
+          for (int c = 0; c < PR; ++c) acc_b[r][c] = fmaf(bvb[r], av[c], acc_b[r][c]);
+        if (S.hasy[k]) {
+          float bvy[PR];
+#pragma unroll
+          for (int r = 0; r < PR; ++r) bvy[r] = S.by[k][r0 + r];
+#pragma unroll
+          for (int r = 0; r < PR; ++r)
+#pragma unroll
+            for (int c = 0; c < PR; ++c) acc_y[r][c] = fmaf(bvy[r], av[c], acc_y[r][c]);
+        }
+      }
+      fold_chunk<TS>(acc_y, hi_y, S.lo_y, r0, c0);
+      fold_chunk<TS>(acc_b, hi_b, S.lo_b, r0, c0);
+    }
+    // 5. write the tile: straight into the map, or as a partial tile
+    if (U.slot < 0) {
+#pragma unroll
+      for (int r = 0; r < PR; ++r)
+#pragma unroll
+        for (int c = 0; c < PR; ++c) {
+          int gx = x0 + c0 + c, gy = y0 + r0 + r;
+          if (gx >= nx || gy >= ny) continue;
+          int64_t p = (int64_t)gy * nx + gx;
+          int q = (r0 + r) * TS + c0 + c;
+          float s, e;
+          bp_two_sum(ymap[p], hi_y[r][c], s, e);
+          ymap[p] = s;
+          ylo[p] = ylo[p] + (S.lo_y[q] + e);
+          bp_two_sum(bmap[p], hi_b[r][c], s, e);
+          bmap[p] = s;
+          blo[p] = blo[p] + (S.lo_b[q] + e);
+        }
+    } else {
+      float* P = partials + (int64_t)U.slot * 4 * TS * TS;
+#pragma unroll
+      for (int r = 0; r < PR; ++r)
+#pragma unroll
+        for (int c = 0; c < PR; ++c) {
+          int q = (r0 + r) * TS + c0 + c;
+          P[q] = hi_y[r][c];
+          P[TS * TS + q] = S.lo_y[q];
+          P[2 * TS * TS + q] = hi_b[r][c];
+          P[3 * TS * TS + q] = S.lo_b[q];
+        }
+    }
+    __syncthreads();
+  }
+}
+
+// one CTA per multi-unit tile: add its partial tiles in unit order, then the map
+template <int TS>
+__global__ void __launch_bounds__(256) k_reduce_tiles(const int64_t* __restrict__ tstart,
+                                                      const int64_t* __restrict__ uoff,
+                                                      int64_t n_tiles, int unit, int nx, int ny,
+                                                      int ntx, const float* __restrict__ partials,
+                                                      float* ymap, float* bmap, float* ylo,
+                                                      float* blo) {
+  int64_t t = blockIdx.x;
+  if (t >= n_tiles) return;
+  int64_t len = tstart[t + 1] - tstart[t];
+  int64_t nu = (len + unit - 1) / unit;
+  if (nu <= 1) return;
+  int64_t u0 = uoff[t];
+  int x0 = (int)(t % ntx) * TS, y0 = (int)(t / ntx) * TS;
+  for (int q = threadIdx.x; q < TS * TS; q += blockDim.x) {
+    int gx = x0 + q % TS, gy = y0 + q / TS;
+    if (gx >= nx || gy >= ny) continue;
+    float hy = 0.f, ly = 0.f, hb = 0.f, lb = 0.f;
+    for (int64_t k = 0; k < nu; ++k) {
+      const float* P = partials + (u0 + k) * 4 * TS * TS;
+      float s, e;
+      bp_two_sum(hy, P[q], s, e);
+      hy = s;
+      ly += P[TS * TS + q] + e;
+      bp_two_sum(hb, P[2 * TS * TS + q], s, e);
+      hb = s;
+      lb += P[3 * TS * TS + q] + e;
+    }
+    int64_t p = (int64_t)gy * nx + gx;
+    float s, e;
+    bp_two_sum(ymap[p], hy, s, e);
+    ymap[p] = s;
+    ylo[p] = ylo[p] + (ly + e);
+    bp_two_sum(bmap[p], hb, s, e);
+    bmap[p] = s;
+    blo[p] = blo[p] + (lb + e);
+  }
+}
+
+int check_geom(bp_ctx* ctx, const bp_map_geom* g, const char* who) {
+  if (!g) return bp_fail(ctx, BP_EINVAL, "%s: null geometry", who);
+  if (g->nx <= 0 || g->ny <= 0 || g->n_maps <= 0 || !(g->dtheta > 0))
+    return bp_fail(ctx, BP_EINVAL, "%s: bad geometry", who);
+  if (g->nx > 65536 || g->ny > 65536)
+    return bp_fail(ctx, BP_ERANGE, "%s: map side above 65536 pixels", who);
+  return BP_OK;
+}
+
+// Builds the sorted (tile, particle) list; returns keys/vals pointers and count.
+int build_pairs(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_geom* g, int select,
+                int ts, uint32_t** keys_out, uint32_t** vals_out, int64_t* npairs_out,
+                int64_t* n_tiles_out) {
+  const int ntx = (g->nx + ts - 1) / ts, nty = (g->ny + ts - 1) / ts;
+  const int64_t n_tiles = (int64_t)ntx * nty;
+  uint32_t* counts;
+  int64_t* offs;
+  int r;
+  if ((r = bp_ws(ctx, WS_COUNTS, (size_t)(n + 1) * 4, (void**)&counts))) return r;
+  if ((r = bp_ws(ctx, WS_OFFS, (size_t)(n + 1) * 8, (void**)&offs))) return r;
+  const float4* rec = reinterpret_cast<const float4*>(assigned);
+  unsigned nb = (unsigned)((n + 255) / 256);
+  bp_phase_begin(ctx, BP_PH_PAIRS);
+  k_pair_count<<<nb, 256, 0, ctx->stream>>>(rec, n, g->nx, g->ny, ts, select, counts);
+  BP_LAUNCH_CHECK(ctx, "pair count");
+  if ((r = bp_scan_u32_to_i64(ctx, counts, offs, n))) return r;
+  BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, offs + n, 8, cudaMemcpyDeviceToHost, ctx->stream));
+  BP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const int64_t np = ctx->h_pinned[0];
+  if (np > (int64_t)UINT32_MAX)
+    return bp_fail(ctx, BP_ERANGE, "paste: %lld tile pairs exceed 2^32", (long long)np);
+  uint32_t *k0, *v0, *k1, *v1;
+  if ((r = bp_ws(ctx, WS_KEYS0, (size_t)np * 4, (void**)&k0))) return r;
+  if ((r = bp_ws(ctx, WS_VALS0, (size_t)np * 4, (void**)&v0))) return r;
+  if ((r = bp_ws(ctx, WS_KEYS1, (size_t)np * 4, (void**)&k1))) return r;
+  if ((r = bp_ws(ctx, WS_VALS1, (size_t)np * 4, (void**)&v1))) return r;
+  k_pair_emit<<<nb, 256, 0, ctx->stream>>>(rec, n, g->nx, g->ny, ts, select, ntx, offs, k0, v0);
+  BP_LAUNCH_CHECK(ctx, "pair emit");
+  bp_phase_end(ctx, BP_PH_PAIRS);
+  int key_bits = 0;
+  while (((int64_t)1 << key_bits) < n_tiles) ++key_bits;
+  bp_phase_begin(ctx, BP_PH_SORT);
+  if ((r = bp_radix_sort_pairs(ctx, k0, v0, k1, v1, np, key_bits, keys_out, vals_out))) return r;
+  *npairs_out = np;
+  *n_tiles_out = n_tiles;
+  return BP_OK;
+}
+
+template <int TS>
+int deposit(bp_ctx* ctx, const float* assigned, const bp_map_geom* g, const uint32_t* keys,
+            const uint32_t* vals, int64_t np, int64_t n_tiles, float* ymap, float* bmap,
+            float* ylo, float* blo) {
+  const int ntx = (g->nx + TS - 1) / TS;
+  const int unit = ctx->pp_unit;
+  int r;
+  int64_t* tstart;
+  if ((r = bp_ws(ctx, WS_TILES, (size_t)(n_tiles + 1) * 8 * 2 + (size_t)(n_tiles + 1) * 4 + 64,
+                 (void**)&tstart)))
+    return r;
+  int64_t* uoff = tstart + (n_tiles + 1);
+  uint32_t* ucount = (uint32_t*)(uoff + (n_tiles + 1));
+  if ((r = bp_tile_ranges(ctx, keys, np, n_tiles, tstart))) return r;
+  unsigned tb = (unsigned)((n_tiles + 255) / 256);
+  k_unit_count<<<tb, 256, 0, ctx->stream>>>(tstart, n_tiles, unit, ucount);
+  BP_LAUNCH_CHECK(ctx, "unit count");
+  if ((r = bp_scan_u32_to_i64(ctx, ucount, uoff, n_tiles))) return r;
+  const int64_t max_units = n_tiles + np / unit + 1;
+  Unit* units;
+  if ((r = bp_ws(ctx, WS_UNITS, (size_t)max_units * sizeof(Unit), (void**)&units))) return r;
+  k_unit_emit<<<tb, 256, 0, ctx->stream>>>(tstart, n_tiles, unit, uoff, units);
+  BP_LAUNCH_CHECK(ctx, "unit emit");
+  float* partials;
+  if ((r = bp_ws(ctx, WS_PART, (size_t)max_units * 4 * TS * TS * sizeof(float),
+                 (void**)&partials)))
+    return r;
+  BP_CUDA(ctx, cudaMemsetAsync(ctx->d_counter + 1, 0, sizeof(int64_t), ctx->stream));
+  bp_phase_end(ctx, BP_PH_SORT);
+  const size_t smem = sizeof(DepSmem<TS>);
+  BP_CUDA(ctx, cudaFuncSetAttribute(k_deposit<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  int per_sm = 0;
+  BP_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deposit<TS>, DEP_THREADS,
+                                                             smem));
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)ctx->num_sms * per_sm;
+  if (grid > max_units) grid = max_units;
+  bp_phase_begin(ctx, BP_PH_DEPOSIT);
+  k_deposit<TS><<<(unsigned)grid, DEP_THREADS, smem, ctx->stream>>>(
+      reinterpret_cast<const float4*>(assigned), vals, units, uoff + n_tiles, ctx->d_counter + 1,
+      g->nx, g->ny, ntx, ymap, bmap, ylo, blo, partials);
+  BP_LAUNCH_CHECK(ctx, "deposit");
+  bp_phase_end(ctx, BP_PH_DEPOSIT);
+  bp_phase_begin(ctx, BP_PH_REDUCE);
+  k_reduce_tiles<TS><<<(unsigned)n_tiles, 256, 0, ctx->stream>>>(
+      tstart, uoff, n_tiles, unit, g->nx, g->ny, ntx, partials, ymap, bmap, ylo, blo);
+  BP_LAUNCH_CHECK(ctx, "reduce tiles");
+  bp_phase_end(ctx, BP_PH_REDUCE);
+  return BP_OK;
+}
+
+int halo_blocks(bp_ctx* ctx, int64_t nh, const double* model, const int32_t* status, double Mp,
+                float** blk) {
+  int r = bp_ws(ctx, WS_HPAR, (size_t)(nh > 0 ? nh : 1) * HB * sizeof(float), (void**)blk);
+  if (r) return r;
+  if (nh > 0) {
+    k_halo_block<<<(unsigned)((nh + 255) / 256), 256, 0, ctx->stream>>>(ctx->p, nh, model,
+                                                                        status, Mp, *blk);
+    BP_LAUNCH_CHECK(ctx, "halo block");
+  }
+  return BP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bp_assign_particles(bp_ctx* ctx, int64_t n, const float* x, const float* y, const float* z,
+                        const float* vx, const float* vy, const float* vz, const float* hsml,
+                        const int32_t* halo_id, double Mp, int64_t n_halos,
+                        const float* halo_pos, const double* model, const int32_t* status,
+                        const bp_map_geom* geom, float* out) {
+  if (!ctx) return BP_EINVAL;
+  if (n < 0 || n_halos < 0) return bp_fail(ctx, BP_EINVAL, "bp_assign_particles: negative size");
+  int r = check_geom(ctx, geom, "bp_assign_particles");
+  if (r) return r;
+  if (n == 0) return BP_OK;
+  if (!x || !y || !z || !vx || !vy || !vz || !hsml || !halo_id || !out)
+    return bp_fail(ctx, BP_EINVAL, "bp_assign_particles: null pointer");
+  if (n_halos > 0 && (!halo_pos || !model || !status))
+    return bp_fail(ctx, BP_EINVAL, "bp_assign_particles: null halo arrays");
+  if (!(Mp > 0)) return bp_fail(ctx, BP_EINVAL, "bp_assign_particles: Mp <= 0");
+  if (((uintptr_t)out & 15) != 0)
+    return bp_fail(ctx, BP_EINVAL, "bp_assign_particles: out must be 16-byte aligned");
+  const BpParams& P = ctx->p;
+  float* blk;
+  bp_phase_begin(ctx, BP_PH_ASSIGN);
+  if ((r = halo_blocks(ctx, n_halos, model, status, Mp / P.h, &blk))) return r;
+  AssignArgs a;
+  a.x = x; a.y = y; a.z = z; a.vx = vx; a.vy = vy; a.vz = vz; a.hs = hsml;
+  a.hid = halo_id;
+  a.hpos = halo_pos;
+  a.blk = blk;
+  a.n = n;
+  a.nh = n_halos;
+  a.th0x = geom->theta0_x;
+  a.th0y = geom->theta0_y;
+  a.inv_dth = 1.0 / geom->dtheta;
+  a.inv_h = (float)(1.0 / P.h);
+  a.inv_h_dth = (float)(1.0 / (P.h * geom->dtheta));
+  a.inv_om_pix = (float)(1.0 / (geom->dtheta * geom->dtheta));
+  a.field_B = (float)(P.CN * (Mp / P.h) * (P.field_fb ? P.fb : 1.0) / bpc::C_KMS);
+  a.n_poly = (float)P.n_poly;
+  double rn = rint(P.n_poly);
+  a.n_int = (fabs(P.n_poly - rn) < 1e-12 && rn >= 1 && rn <= 16) ? (int)rn : -1;
+  a.n_nt = (float)P.n_nt;
+  a.out = out;
+  k_assign<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(a, ctx->t);
+  BP_LAUNCH_CHECK(ctx, "assign");
+  bp_phase_end(ctx, BP_PH_ASSIGN);
+  return BP_OK;
+}
+
+int bp_paste_particles(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_geom* geom,
+                       int select, float* ymap, float* bmap, float* ylo, float* blo) {
+  if (!ctx) return BP_EINVAL;
+  int r = check_geom(ctx, geom, "bp_paste_particles");
+  if (r) return r;
+  if (geom->n_maps != 1) return bp_fail(ctx, BP_EINVAL, "bp_paste_particles: n_maps must be 1");
+  if (n < 0) return bp_fail(ctx, BP_EINVAL, "bp_paste_particles: n < 0");
+  if (n > (int64_t)UINT32_MAX) return bp_fail(ctx, BP_ERANGE, "bp_paste_particles: n >= 2^32");
+  if (select < 0 || select > 2) return bp_fail(ctx, BP_EINVAL, "bp_paste_particles: select");
+  if (n == 0) return BP_OK;
+  if (!assigned || !ymap || !bmap || !ylo || !blo)
+    return bp_fail(ctx, BP_EINVAL, "bp_paste_particles: null pointer");
+  if (((uintptr_t)assigned & 15) != 0)
+    return bp_fail(ctx, BP_EINVAL, "bp_paste_particles: records must be 16-byte aligned");
+  const int ts = ctx->pp_tile;
+  uint32_t *keys, *vals;
+  int64_t np, n_tiles;
+  if ((r = build_pairs(ctx, n, assigned, geom, select, ts, &keys, &vals, &np, &n_tiles))) return r;
+  if (np == 0) return BP_OK;
+  if (ts == 64) return deposit<64>(ctx, assigned, geom, keys, vals, np, n_tiles, ymap, bmap, ylo, blo);
+  return deposit<32>(ctx, assigned, geom, keys, vals, np, n_tiles, ymap, bmap, ylo, blo);
+}
+
+int bp_pp_pairs(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_geom* geom,
+                int select, int tile, uint32_t* keys, uint32_t* vals, int64_t capacity,
+                int64_t* n_pairs) {
+  if (!ctx) return BP_EINVAL;
+  int r = check_geom(ctx, geom, "bp_pp_pairs");
+  if (r) return r;
+  if (!n_pairs || tile <= 0 || n < 0) return bp_fail(ctx, BP_EINVAL, "bp_pp_pairs: arguments");
+  *n_pairs = 0;
+  if (n == 0) return BP_OK;
+  if (!assigned) return bp_fail(ctx, BP_EINVAL, "bp_pp_pairs: null records");
+  uint32_t *k, *v;
+  int64_t np, nt;
+  if ((r = build_pairs(ctx, n, assigned, geom, select, tile, &k, &v, &np, &nt))) return r;
+  *n_pairs = np;
+  if (np > capacity) return bp_fail(ctx, BP_ERANGE, "bp_pp_pairs: capacity %lld < %lld",
+                                    (long long)capacity, (long long)np);
+  if (np > 0) {
+    if (!keys || !vals) return bp_fail(ctx, BP_EINVAL, "bp_pp_pairs: null output");
+    BP_CUDA(ctx, cudaMemcpyAsync(keys, k, np * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    BP_CUDA(ctx, cudaMemcpyAsync(vals, v, np * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  BP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return BP_OK;
+}
+
+}  // extern "C"

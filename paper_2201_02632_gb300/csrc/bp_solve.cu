@@ -1,0 +1,518 @@
+// bp_solve.cu -- per-halo solve of the analytic ICM model (Section 2), FP64.
+//
+// One warp per halo.  The scalar halo quantities (NFW, r500, M_*, r_*) come from
+// closed forms and 1-D Newton iterations that every lane runs redundantly.  The
+// initial gas energy, the dark-matter energy and the surface pressure use the
+// isotropic Lokas & Mamon (2001) dispersion in closed form (dilogarithm) and an
+// integration by parts of the kinetic term, so no nested quadrature is needed.
+// The three conditions of Section 2.2 are reduced to one unknown: for each r_f,
+// T = P0/rho0 follows from the gas-mass condition (safeguarded Newton in
+// ln(T - T_min)), rho0 from the surface-pressure condition, and the energy
+// condition is driven to zero by safeguarded Newton in ln r_f with the exact
+// derivative of the reduced problem.  The gas integrals over [0, r_f] are
+// composite 16-point Gauss-Legendre rules whose nodes are spread over the lanes.
+#include <vector>
+
+#include "bp_internal.cuh"
+
+#define NGL 16
+#define MAX_PANEL_A 8
+#define MAX_PANEL_B 5
+
+__constant__ double c_glx[NGL];
+__constant__ double c_glw[NGL];
+__constant__ double c_li2[16];  // B_2m / (2m+1)!, m = 1..15
+
+namespace {
+
+// Gauss-Legendre nodes/weights on [-1, 1] by Newton iteration on P_n.
+void gauss_legendre(int n, double* x, double* w) {
+  for (int i = 0; i < n; ++i) {
+    double z = cos(bpc::PI * (i + 0.75) / (n + 0.5));
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      double dp = n * (z * p1 - p0) / (z * z - 1.0);
+      double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    double p0 = 1.0, p1 = z;
+    for (int k = 2; k <= n; ++k) {
+      double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k;
+      p0 = p1;
+      p1 = p2;
+    }
+    double dp = n * (z * p1 - p0) / (z * z - 1.0);
+    x[i] = -z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+bool g_const_ready = false;
+
+int upload_constants(bp_ctx* ctx) {
+  if (g_const_ready) return BP_OK;
+  double x[NGL], w[NGL];
+  gauss_legendre(NGL, x, w);
+  // Bernoulli numbers B_2m (exact rationals), divided by (2m+1)!
+  const double num[15] = {1, -1, 1, -1, 5, -691, 7, -3617, 43867, -174611, 854513,
+                          -236364091, 8553103, -23749461029.0, 8615841276005.0};
+  const double den[15] = {6, 30, 42, 30, 66, 2730, 6, 510, 798, 330, 138, 2730, 6, 870, 14322};
+  double li2[16] = {0};
+  double fact = 1.0;  // (2m+1)!
+  for (int m = 1; m <= 15; ++m) {
+    fact *= (2.0 * m) * (2.0 * m + 1.0);
+    li2[m] = num[m - 1] / den[m - 1] / fact;
+  }
+  BP_CUDA(ctx, cudaMemcpyToSymbol(c_glx, x, sizeof(x)));
+  BP_CUDA(ctx, cudaMemcpyToSymbol(c_glw, w, sizeof(w)));
+  BP_CUDA(ctx, cudaMemcpyToSymbol(c_li2, li2, sizeof(li2)));
+  g_const_ready = true;
+  return BP_OK;
+}
+
+// ---------------------------------------------------------------- device math
+__device__ double m_of(double x) {  // ln(1+x) - x/(1+x)
+  if (x < 1e-3) {
+    double x2 = x * x;
+    return x2 * (0.5 - x * (2.0 / 3.0 - x * (0.75 - x * 0.8)));
+  }
+  return log1p(x) - x / (1.0 + x);
+}
+
+// Li2 series in u = -ln(1 - z) with Bernoulli coefficients ('t Hooft & Veltman 1979)
+__device__ double li2_series(double u) {
+  double u2 = u * u, s = 0.0;
+  for (int m = 15; m >= 1; --m) s = s * u2 + c_li2[m];
+  return u * (1.0 + s * u2) - 0.25 * u2;
+}
+// Li2(-y) for y >= 0; inversion Li2(-y) = -pi^2/6 - ln^2(y)/2 - Li2(-1/y) for y > 1.
+__device__ double li2_neg(double y) {
+  if (y <= 0.0) return 0.0;
+  if (y <= 1.0) return li2_series(-log1p(y));
+  double l = log(y);
+  return -bpc::PI * bpc::PI / 6.0 - 0.5 * l * l - li2_series(-log1p(1.0 / y));
+}
+
+struct Halo {
+  double M, c, z, rvir, rs, rhos, mc, phi0, GM;
+  double r500, M500, Mstar, rstar, Egi, Edm, Ps, ant, DA, tau;
+};
+
+// rho sigma^2 of the untruncated isotropic NFW halo (Lokas & Mamon 2001, eq. 14).
+__device__ double rho_sigma2(const Halo& h, double r) {
+  double s = r / h.rvir, c = h.c, cs = c * s;
+  double l1 = log1p(cs);
+  double br = bpc::PI * bpc::PI - log(cs) - 1.0 / cs - 1.0 / ((1 + cs) * (1 + cs)) - 6.0 / (1 + cs) +
+              (1.0 + 1.0 / (cs * cs) - 4.0 / cs - 2.0 / (1 + cs)) * l1 + 3.0 * l1 * l1 +
+              6.0 * li2_neg(cs);
+  double Vv2 = h.GM / h.rvir;
+  double sig2 = 0.5 * c * c / h.mc * s * (1 + cs) * (1 + cs) * br * Vv2;
+  double x = r / h.rs;
+  double rho = h.rhos / (x * (1 + x) * (1 + x));
+  return rho * sig2;
+}
+
+// Kinetic integral int_a^b 4 pi r^2 rho sigma^2 dr, by parts:
+// (4pi/3)[r^3 K]_a^b + (4pi/3) 4 pi G rho_s^2 r_s^5 [Hq]_xa^xb, Hq' = m(x)/(1+x)^2.
+__device__ double kin_integral(const Halo& h, double a, double b) {
+  auto Hq = [](double x) { return -log1p(x) / (1 + x) - 0.5 / ((1 + x) * (1 + x)); };
+  double ka = (a > 0) ? a * a * a * rho_sigma2(h, a) : 0.0;
+  double kb = b * b * b * rho_sigma2(h, b);
+  double pre = 4.0 * bpc::PI * bpc::G * h.rhos * h.rhos * pow(h.rs, 5);
+  return 4.0 * bpc::PI / 3.0 * ((kb - ka) + pre * (Hq(b / h.rs) - Hq(a / h.rs)));
+}
+// Potential integral int_a^b Phi 4 pi r^2 rho dr inside r_vir (closed form).
+__device__ double pot_integral(const Halo& h, double a, double b) {
+  auto Q = [](double x) { return -(log1p(x) + 1.0) / (1 + x); };
+  double xa = a / h.rs, xb = b / h.rs;
+  double K = h.c / ((1 + h.c) * h.rvir);
+  return -(h.GM * h.M / (h.mc * h.mc)) * ((Q(xb) - Q(xa)) / h.rs - K * (m_of(xb) - m_of(xa)));
+}
+
+__device__ __forceinline__ double phi_of(const Halo& h, double r) {
+  if (r > h.rvir) return -h.GM / r;
+  double x = r / h.rs;
+  double l = (x < 1e-6) ? (1.0 - 0.5 * x) / h.rs : log1p(x) / r;
+  return -(h.GM / h.mc) * (l - h.c / ((1 + h.c) * h.rvir));
+}
+__device__ __forceinline__ double menc_of(const Halo& h, double r) {
+  return r >= h.rvir ? h.M : h.M * m_of(r / h.rs) / h.mc;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+struct Sums {
+  double Im, In, Ip, Jm, Jn;  // int theta^{n-1,n,n+1} r^2, int theta^{n-1,n} Phi r^2
+};
+
+struct Solver {
+  const Halo& h;
+  double n;     // polytropic index
+  int n_int;    // n if integral, else -1
+  // cached region-A nodes ([0, r_vir]) of this lane
+  double a_r2w[4], a_phi[4];
+  int na;
+
+  __device__ Solver(const Halo& hh, double nn) : h(hh), n(nn) {
+    double rn = rint(nn);
+    n_int = (fabs(nn - rn) < 1e-12 && rn >= 1 && rn <= 16) ? (int)rn : -1;
+  }
+  __device__ double pw(double th, int k_off) const {  // theta^{n - 1 + k_off}
+    if (n_int > 0) {
+      int e = n_int - 1 + k_off;
+      double r = 1.0, b = th;
+      while (e) {
+        if (e & 1) r *= b;
+        b *= b;
+        e >>= 1;
+      }
+      return r;
+    }
+    return pow(th, n - 1.0 + k_off);
+  }
+  // panel p of region A (x = r/r_s from 0 to xa) -> [a, b] in r
+  __device__ static bool panel_a(int p, double xa, double rs, double& a, double& b) {
+    double lo = 0.0, hi = fmin(0.5, xa);
+    for (int k = 0; k < p; ++k) {
+      if (hi >= xa) return false;
+      lo = hi;
+      hi = fmin(2.5 * hi, xa);
+    }
+    if (!(hi > lo)) return false;
+    a = lo * rs;
+    b = hi * rs;
+    return true;
+  }
+  __device__ static bool panel_b(int p, double rv, double rf, double& a, double& b) {
+    double lo = rv, hi = fmin(2.0 * rv, rf);
+    for (int k = 0; k < p; ++k) {
+      if (hi >= rf) return false;
+      lo = hi;
+      hi = fmin(2.0 * hi, rf);
+    }
+    if (!(hi > lo)) return false;
+    a = lo;
+    b = hi;
+    return true;
+  }
+  __device__ void cache_region_a(int lane) {
+    na = 0;
+    double xa = h.c;
+    for (int q = lane; q < MAX_PANEL_A * NGL; q += 32) {
+      int p = q / NGL, j = q % NGL;
+      double a, b;
+      if (!panel_a(p, xa, h.rs, a, b)) continue;
+      double mid = 0.5 * (a + b), hw = 0.5 * (b - a);
+      double r = mid + hw * c_glx[j];
+      a_r2w[na] = hw * c_glw[j] * r * r;
+      a_phi[na] = phi_of(h, r);
+      ++na;
+    }
+  }
+  __device__ void acc(Sums& s, double r2w, double phi, double inv_n1T) const {
+    double th = 1.0 + (h.phi0 - phi) * inv_n1T;
+    if (th <= 0.0) return;
+    double tm = pw(th, 0);
+    double tn = tm * th, tp = tn * th;
+    s.Im += r2w * tm;
+    s.In += r2w * tn;
+    s.Ip += r2w * tp;
+    s.Jm += r2w * tm * phi;
+    s.Jn += r2w * tn * phi;
+  }
+  __device__ Sums integrals(double T, double rf, int lane) const {
+    Sums s = {0, 0, 0, 0, 0};
+    double inv_n1T = 1.0 / ((n + 1.0) * T);
+    if (rf >= h.rvir) {
+      for (int k = 0; k < na; ++k) acc(s, a_r2w[k], a_phi[k], inv_n1T);
+      for (int q = lane; q < MAX_PANEL_B * NGL; q += 32) {
+        int p = q / NGL, j = q % NGL;
+        double a, b;
+        if (!panel_b(p, h.rvir, rf, a, b)) continue;
+        double mid = 0.5 * (a + b), hw = 0.5 * (b - a);
+        double r = mid + hw * c_glx[j];
+        acc(s, hw * c_glw[j] * r * r, -h.GM / r, inv_n1T);
+      }
+    } else {
+      double xa = rf / h.rs;
+      for (int q = lane; q < MAX_PANEL_A * NGL; q += 32) {
+        int p = q / NGL, j = q % NGL;
+        double a, b;
+        if (!panel_a(p, xa, h.rs, a, b)) continue;
+        double mid = 0.5 * (a + b), hw = 0.5 * (b - a);
+        double r = mid + hw * c_glx[j];
+        acc(s, hw * c_glw[j] * r * r, phi_of(h, r), inv_n1T);
+      }
+    }
+    s.Im = warp_sum(s.Im);
+    s.In = warp_sum(s.In);
+    s.Ip = warp_sum(s.Ip);
+    s.Jm = warp_sum(s.Jm);
+    s.Jn = warp_sum(s.Jn);
+    return s;
+  }
+};
+
+// Reduced problem at a given r_f: T from the gas-mass condition.
+struct Eval {
+  double T, thf, rho0, Rm, Re, dRe_dv;
+  Sums s;
+  int ok;
+};
+
+__global__ void __launch_bounds__(128) k_solve(BpParams P, BpTables TB, int64_t n,
+                                               const double* __restrict__ Mh,
+                                               const double* __restrict__ cc,
+                                               const double* __restrict__ zz, double* model,
+                                               int32_t* status, double tol, int64_t* nbad) {
+  int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  int lane = threadIdx.x & 31;
+  if (gw >= n) return;
+  const int64_t i = gw;
+  double Min = Mh[i], c = cc[i], z = zz[i];
+  auto put = [&](int f, double v) {
+    if (lane == 0) model[(int64_t)f * n + i] = v;
+  };
+  auto finish = [&](int st) {
+    if (lane == 0) {
+      status[i] = st;
+      if (st != BP_HALO_OK) atomicAdd((unsigned long long*)nbad, 1ull);
+    }
+  };
+  if (!(Min > 0 && isfinite(Min) && c > 0 && isfinite(c) && z >= 0 && z <= 10.0)) {
+    for (int f = 0; f < BP_M_NFIELDS; ++f) put(f, 0.0);
+    finish(BP_HALO_BADINPUT);
+    return;
+  }
+  Halo h;
+  h.M = Min / P.h;
+  h.c = c;
+  h.z = z;
+  h.GM = bpc::G * h.M;
+  double a3 = (1 + z) * (1 + z) * (1 + z);
+  double E2 = P.Om * a3 + (1.0 - P.Om);
+  double rho_cr = P.rho_cr0 * E2;
+  double xo = P.Om * a3 / E2 - 1.0;
+  double Dv = 18.0 * bpc::PI * bpc::PI + 82.0 * xo - 39.0 * xo * xo;
+  h.rvir = cbrt(3.0 * h.M / (4.0 * bpc::PI * Dv * rho_cr));
+  h.rs = h.rvir / c;
+  h.mc = m_of(c);
+  h.rhos = h.M / (4.0 * bpc::PI * h.rs * h.rs * h.rs * h.mc);
+  h.phi0 = -(h.GM / (h.mc * h.rvir)) * c * c / (1 + c);
+  h.DA = bp_hermite(TB.chi_z, TB.dchi_z, TB.nz, TB.dz, z) / (1 + z);
+  h.tau = bp_hermite(TB.tau_z, TB.dtau_z, TB.nz, TB.dz, z);
+  // r500: m(x)/x^3 = 500 rho_cr (4pi/3) r_s^3 m(c) / M, Newton in ln x with a bracket
+  {
+    double lnK = log(500.0 * rho_cr * 4.0 * bpc::PI / 3.0 * h.rs * h.rs * h.rs * h.mc / h.M);
+    double lo = 1e-8, hi = c, x = 0.5 * c;
+    for (int it = 0; it < 100; ++it) {
+      double mx = m_of(x);
+      double f = log(mx) - 3.0 * log(x) - lnK;
+      if (f > 0) lo = x; else hi = x;
+      double df = x * x / ((1 + x) * (1 + x)) / mx - 3.0 / x;  // d f / d x
+      double xn = x - f / df;
+      if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+      if (fabs(xn - x) < 1e-15 * x) { x = xn; break; }
+      x = xn;
+    }
+    h.r500 = x * h.rs;
+    h.M500 = 4.0 * bpc::PI / 3.0 * 500.0 * rho_cr * h.r500 * h.r500 * h.r500;
+  }
+  h.Mstar = P.f_star * pow(h.M500 / 3e14, -P.S_star) * h.M;
+  double f_max = pow(4.0, -P.n_nt) / P.alpha_nt;
+  double fz = fmin(pow(1.0 + z, P.beta_nt), (f_max - 1.0) * tanh(P.beta_nt * z) + 1.0);
+  h.ant = P.alpha_nt * fz;
+  put(BP_M_MVIR, h.M);
+  put(BP_M_C, c);
+  put(BP_M_Z, z);
+  put(BP_M_RVIR, h.rvir);
+  put(BP_M_RS, h.rs);
+  put(BP_M_RHOS, h.rhos);
+  put(BP_M_MC, h.mc);
+  put(BP_M_PHI0, h.phi0);
+  put(BP_M_R500, h.r500);
+  put(BP_M_M500, h.M500);
+  put(BP_M_MSTAR, h.Mstar);
+  put(BP_M_ANT, h.ant);
+  put(BP_M_DA, h.DA);
+  put(BP_M_TAU, h.tau);
+  if (h.Mstar >= P.fb * h.M) {
+    const int zero_fields[10] = {BP_M_RSTAR, BP_M_EGI, BP_M_EDM, BP_M_PS, BP_M_T,
+                                 BP_M_RHO0,  BP_M_P0,  BP_M_RF,  BP_M_RESM, BP_M_RESE};
+    for (int k = 0; k < 10; ++k) put(zero_fields[k], 0.0);
+    finish(BP_HALO_BADSTAR);
+    return;
+  }
+  // r_*: f_b M(<r_*) = M_*  ->  m(x) = M_* m(c) / (f_b M)
+  {
+    double tgt = h.Mstar * h.mc / (P.fb * h.M);
+    double lo = 0.0, hi = c, x = 0.5 * c;
+    for (int it = 0; it < 100; ++it) {
+      double f = m_of(x) - tgt;
+      if (f < 0) lo = x; else hi = x;
+      double df = x / ((1 + x) * (1 + x));
+      double xn = x - f / df;
+      if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
+      if (fabs(xn - x) < 1e-15 * x) { x = xn; break; }
+      x = xn;
+    }
+    h.rstar = x * h.rs;
+  }
+  h.Egi = P.fb * (1.5 * kin_integral(h, h.rstar, h.rvir) + pot_integral(h, h.rstar, h.rvir));
+  h.Edm = 1.5 * kin_integral(h, 0.0, h.rvir) + pot_integral(h, 0.0, h.rvir);
+  h.Ps = P.fb * rho_sigma2(h, h.rvir);
+  put(BP_M_RSTAR, h.rstar);
+  put(BP_M_EGI, h.Egi);
+  put(BP_M_EDM, h.Edm);
+  put(BP_M_PS, h.Ps);
+
+  const double nn = P.n_poly;
+  Solver S(h, nn);
+  S.cache_region_a(lane);
+  const double fbM = P.fb * h.M;
+  const double inj = P.eps_dm * fabs(h.Edm) + P.eps_star * h.Mstar * bpc::C_KMS * bpc::C_KMS;
+  const double absE = fabs(h.Egi);
+  const double r3v = h.rvir * h.rvir * h.rvir;
+  const double four_pi = 4.0 * bpc::PI;
+
+  // Evaluate the reduced problem at r_f, solving the gas-mass condition for T
+  // (warm start T0).  Returns residuals and d R_e / d ln r_f.
+  auto reduced = [&](double rf, double T0) -> Eval {
+    Eval e;
+    e.ok = 0;
+    double phif = phi_of(h, rf);
+    double psi = phif - h.phi0;  // > 0
+    double Tmin = psi / (nn + 1.0);
+    double lnTarget = log(fbM - h.Mstar);
+    double s = (T0 > Tmin * (1 + 1e-9)) ? log(T0 - Tmin) : log(Tmin + 0.5 * h.GM / h.rvir);
+    double slo = -INFINITY, shi = INFINITY;
+    double T = 0, thf = 0, rho0 = 0, F = 1;
+    Sums sm;
+    int it;
+    for (it = 0; it < 80; ++it) {
+      T = Tmin + exp(s);
+      thf = 1.0 + (h.phi0 - phif) / ((nn + 1.0) * T);
+      sm = S.integrals(T, rf, lane);
+      rho0 = h.Ps / (T * S.pw(thf, 2));
+      F = log(four_pi * rho0 * sm.In) - lnTarget;
+      if (!isfinite(F)) break;
+      if (fabs(F) < 1e-14) break;
+      if (F > 0) slo = s; else shi = s;
+      double dlr = (-1.0 - (nn + 1.0) * (1.0 - thf) / thf) / T;  // d ln rho0 / dT
+      double dli = nn * (sm.Im - sm.In) / (T * sm.In);           // d ln I_n / dT
+      double dFds = (T - Tmin) * (dlr + dli);
+      double step = -F / dFds;
+      if (!isfinite(step)) step = (F > 0) ? 1.0 : -1.0;
+      step = fmax(-4.0, fmin(4.0, step));
+      double sn = s + step;
+      if (isfinite(slo) && isfinite(shi) && !(sn > slo && sn < shi)) sn = 0.5 * (slo + shi);
+      s = sn;
+    }
+    if (!(fabs(F) < 1e-12)) return e;
+    // residuals and the derivative of the reduced energy residual
+    double In = sm.In, Ip = sm.Ip, Im = sm.Im, Jm = sm.Jm, Jn = sm.Jn;
+    double Egf = four_pi * rho0 * (1.5 * T * Ip + Jn);
+    double dEp = four_pi / 3.0 * (r3v - rf * rf * rf) * h.Ps;
+    double num = (P.energy_sign == 0) ? (Egf - h.Egi - inj - dEp) : (h.Egi - Egf - inj - dEp);
+    e.Re = num / absE;
+    e.Rm = (four_pi * rho0 * In + h.Mstar) / fbM - 1.0;
+    // partial derivatives
+    double dphif = bpc::G * menc_of(h, rf) / (rf * rf);
+    double dthf_drf = -dphif / ((nn + 1.0) * T);
+    double dlr_drf = -(nn + 1.0) * dthf_drf / thf;
+    double dlr_dT = (-1.0 - (nn + 1.0) * (1.0 - thf) / thf) / T;
+    double tfn = S.pw(thf, 1), tfp = tfn * thf;
+    double dG_drf = four_pi * rho0 * (In * dlr_drf + tfn * rf * rf);
+    double dG_dT = four_pi * rho0 * (In * dlr_dT + nn * (Im - In) / T);
+    double dT_drf = -dG_drf / dG_dT;
+    double dIp_dT = (nn + 1.0) * (In - Ip) / T;
+    double dJn_dT = nn * (Jm - Jn) / T;
+    double dEgf_drf = Egf * dlr_drf + four_pi * rho0 * (1.5 * T * tfp + tfn * phif) * rf * rf;
+    double dEgf_dT = Egf * dlr_dT + four_pi * rho0 * (1.5 * Ip + 1.5 * T * dIp_dT + dJn_dT);
+    double ddEp_drf = -four_pi * rf * rf * h.Ps;
+    double dtot = dEgf_drf + dEgf_dT * dT_drf;
+    double dnum = (P.energy_sign == 0) ? (dtot - ddEp_drf) : (-dtot - ddEp_drf);
+    e.dRe_dv = rf * dnum / absE;
+    e.T = T;
+    e.thf = thf;
+    e.rho0 = rho0;
+    e.s = sm;
+    e.ok = 1;
+    return e;
+  };
+
+  const double vlo0 = log(0.5 * h.rvir), vhi0 = log(10.0 * h.rvir);
+  double vlo = vlo0, vhi = vhi0;
+  double v = log(1.1 * h.rvir);
+  double Tw = 0.0;
+  int st = BP_HALO_MAXIT;
+  Eval e;
+  double rf = exp(v);
+  for (int it = 0; it < 80; ++it) {
+    rf = exp(v);
+    e = reduced(rf, Tw);
+    if (!e.ok) { st = BP_HALO_MAXIT; break; }
+    Tw = e.T;
+    if (fabs(e.Re) < tol && fabs(e.Rm) < tol) { st = BP_HALO_OK; break; }
+    if (e.Re < 0) vlo = v; else vhi = v;  // R_e increases with r_f
+    if (vhi - vlo < 1e-15 * fabs(v)) { st = BP_HALO_OK; break; }
+    double step = -e.Re / e.dRe_dv;
+    if (!isfinite(step)) step = (e.Re < 0) ? 0.5 : -0.5;
+    step = fmax(-0.5, fmin(0.5, step));
+    double vn = v + step;
+    if (!(vn > vlo && vn < vhi)) {
+      if (v <= vlo0 + 1e-12 && e.Re > 0) { st = BP_HALO_NOBRACKET; break; }
+      if (v >= vhi0 - 1e-12 && e.Re < 0) { st = BP_HALO_NOBRACKET; break; }
+      vn = 0.5 * (vlo + vhi);
+    }
+    v = vn;
+  }
+  if (e.ok && e.thf <= 0.0) st = BP_HALO_THETA;
+  put(BP_M_T, e.ok ? e.T : 0.0);
+  put(BP_M_RHO0, e.ok ? e.rho0 : 0.0);
+  put(BP_M_P0, e.ok ? e.rho0 * e.T : 0.0);
+  put(BP_M_RF, e.ok ? rf : 0.0);
+  put(BP_M_RESM, e.ok ? e.Rm : NAN);
+  put(BP_M_RESE, e.ok ? e.Re : NAN);
+  finish(st);
+}
+
+}  // namespace
+
+extern "C" int bp_solve_halos(bp_ctx* ctx, int64_t n, const double* Mvir, const double* c,
+                              const double* z, double* model, int32_t* status, int mode,
+                              double resid_tol) {
+  if (!ctx) return BP_EINVAL;
+  if (n < 0) return bp_fail(ctx, BP_EINVAL, "bp_solve_halos: n < 0");
+  if (n == 0) return BP_OK;
+  if (!Mvir || !c || !z || !model || !status)
+    return bp_fail(ctx, BP_EINVAL, "bp_solve_halos: null pointer");
+  if (mode != BP_SOLVE_FP64) return bp_fail(ctx, BP_EINVAL, "bp_solve_halos: unknown mode");
+  int r = upload_constants(ctx);
+  if (r) return r;
+  double tol = resid_tol > 0 ? resid_tol : 1e-10;
+  BP_CUDA(ctx, cudaMemsetAsync(ctx->d_counter, 0, sizeof(int64_t), ctx->stream));
+  const int threads = 128;  // 4 halos per block
+  int64_t blocks = (n * 32 + threads - 1) / threads;
+  bp_phase_begin(ctx, BP_PH_SOLVE);
+  k_solve<<<(unsigned)blocks, threads, 0, ctx->stream>>>(ctx->p, ctx->t, n, Mvir, c, z, model,
+                                                        status, tol, ctx->d_counter);
+  BP_LAUNCH_CHECK(ctx, "k_solve launch");
+  bp_phase_end(ctx, BP_PH_SOLVE);
+  BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, ctx->d_counter, sizeof(int64_t),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+  BP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  int64_t bad = ctx->h_pinned[0];
+  if (bad) return bp_fail(ctx, BP_ENOCONV, "bp_solve_halos: %lld of %lld halos not converged",
+                          (long long)bad, (long long)n);
+  return BP_OK;
+}

@@ -1,0 +1,239 @@
+// bp_sort.cu -- device-wide exclusive scan, stable LSD radix sort of (key, value)
+// pairs and per-key range boundaries.  Used to build the (tile, particle) and
+// (tile, halo) work lists; everything is deterministic (no order-dependent atomics
+// on data: the only atomics are shared-memory histogram counts).
+#include "bp_internal.cuh"
+
+namespace {
+
+constexpr int SCAN_THREADS = 1024;
+constexpr int SCAN_PER_THREAD = 8;
+constexpr int SCAN_CHUNK = SCAN_THREADS * SCAN_PER_THREAD;
+
+template <class T>
+__device__ __forceinline__ T warp_incl_scan(T v) {
+  int lane = threadIdx.x & 31;
+  for (int o = 1; o < 32; o <<= 1) {
+    T u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+// Block-wide exclusive scan of one value per thread; returns the exclusive prefix
+// and writes the block total to *total.
+template <class T>
+__device__ T block_excl_scan(T v, T* total) {
+  __shared__ T s_w[33];
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T inc = warp_incl_scan(v);
+  if (lane == 31) s_w[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    T x = lane < nw ? s_w[lane] : T(0);
+    T xi = warp_incl_scan(x);
+    if (lane < nw) s_w[lane] = xi - x;
+    if (lane == nw - 1) s_w[32] = xi;
+  }
+  __syncthreads();
+  T res = inc - v + s_w[w];
+  if (total) *total = s_w[32];
+  __syncthreads();
+  return res;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const uint32_t* in, int64_t n,
+                                                              int64_t* bsum) {
+  int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_PER_THREAD;
+  int64_t s = 0;
+  for (int k = 0; k < SCAN_PER_THREAD; ++k)
+    if (base + k < n) s += in[base + k];
+  int64_t tot;
+  block_excl_scan<int64_t>(s, &tot);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = tot;
+}
+
+// single block: in-place exclusive scan of nb block sums; writes the grand total
+// to bsum[nb]
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_bsums(int64_t* bsum, int64_t nb) {
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nb; base += SCAN_THREADS) {
+    int64_t i = base + threadIdx.x;
+    int64_t v = i < nb ? bsum[i] : 0;
+    int64_t tot;
+    int64_t ex = block_excl_scan<int64_t>(v, &tot);
+    if (i < nb) bsum[i] = ex + carry;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bsum[nb] = carry;
+}
+
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t* in, int64_t n,
+                                                            const int64_t* bsum, int64_t* out) {
+  int64_t base = (int64_t)blockIdx.x * SCAN_CHUNK + (int64_t)threadIdx.x * SCAN_PER_THREAD;
+  uint32_t v[SCAN_PER_THREAD];
+  int64_t s = 0;
+  for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0u;
+    s += v[k];
+  }
+  int64_t ex = block_excl_scan<int64_t>(s, nullptr) + bsum[blockIdx.x];
+  for (int k = 0; k < SCAN_PER_THREAD; ++k) {
+    if (base + k < n) out[base + k] = ex;
+    ex += v[k];
+  }
+}
+
+// ---------------------------------------------------------------- radix sort
+constexpr int RS_THREADS = 256;
+constexpr int RS_ROUNDS = 16;
+constexpr int RS_ITEMS = RS_THREADS * RS_ROUNDS;
+constexpr int RS_MAXDIG = 256;
+
+__global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t* keys, int64_t n,
+                                                        int shift, int nbits, uint32_t* hist,
+                                                        int64_t nblocks) {
+  __shared__ uint32_t s_h[RS_MAXDIG];
+  int ndig = 1 << nbits;
+  for (int d = threadIdx.x; d < ndig; d += RS_THREADS) s_h[d] = 0;
+  __syncthreads();
+  int64_t base = (int64_t)blockIdx.x * RS_ITEMS;
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    int64_t i = base + (int64_t)r * RS_THREADS + threadIdx.x;
+    if (i < n) atomicAdd(&s_h[(keys[i] >> shift) & (ndig - 1)], 1u);
+  }
+  __syncthreads();
+  for (int d = threadIdx.x; d < ndig; d += RS_THREADS)
+    hist[(int64_t)d * nblocks + blockIdx.x] = s_h[d];
+}
+
+// Stable scatter: items are ranked in global index order (round, warp, lane).
+__global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* kin,
+                                                           const uint32_t* vin, uint32_t* kout,
+                                                           uint32_t* vout, int64_t n, int shift,
+                                                           int nbits, const int64_t* offs,
+                                                           int64_t nblocks) {
+  __shared__ int64_t s_off[RS_MAXDIG];
+  __shared__ uint32_t s_run[RS_MAXDIG];
+  __shared__ uint32_t s_warp[RS_THREADS / 32][RS_MAXDIG];
+  const int ndig = 1 << nbits;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  for (int d = tid; d < ndig; d += RS_THREADS) {
+    s_off[d] = offs[(int64_t)d * nblocks + blockIdx.x];
+    s_run[d] = 0;
+    for (int q = 0; q < RS_THREADS / 32; ++q) s_warp[q][d] = 0;
+  }
+  __syncthreads();
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  int64_t base = (int64_t)blockIdx.x * RS_ITEMS;
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    int64_t i = base + (int64_t)r * RS_THREADS + tid;
+    bool valid = i < n;
+    uint32_t key = valid ? kin[i] : 0u, val = valid ? vin[i] : 0u;
+    uint32_t d = (key >> shift) & (uint32_t)(ndig - 1);
+    uint32_t tag = valid ? d : (0x80000000u | (uint32_t)lane);
+    uint32_t peers = __match_any_sync(0xffffffffu, tag);
+    uint32_t rank = __popc(peers & lt_mask);
+    if (valid && rank == 0) s_warp[w][d] = __popc(peers);
+    __syncthreads();
+    if (valid) {
+      uint32_t pos = s_run[d] + rank;
+      for (int q = 0; q < w; ++q) pos += s_warp[q][d];
+      int64_t dst = s_off[d] + pos;
+      kout[dst] = key;
+      vout[dst] = val;
+    }
+    __syncthreads();
+    for (int dd = tid; dd < ndig; dd += RS_THREADS) {
+      uint32_t t = 0;
+      for (int q = 0; q < RS_THREADS / 32; ++q) {
+        t += s_warp[q][dd];
+        s_warp[q][dd] = 0;
+      }
+      s_run[dd] += t;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_tile_ranges(const uint32_t* keys, int64_t n, int64_t n_tiles,
+                              int64_t* start) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i > n) return;
+  int64_t lo = (i == 0) ? 0 : (int64_t)keys[i - 1] + 1;
+  int64_t hi = (i == n) ? n_tiles : (int64_t)keys[i];
+  for (int64_t t = lo; t <= hi && t <= n_tiles; ++t) start[t] = i;
+}
+
+}  // namespace
+
+// exclusive scan of n u32 counts into out[0..n-1]; out[n] receives the total.
+int bp_scan_u32_to_i64(bp_ctx* ctx, const uint32_t* in, int64_t* out, int64_t n) {
+  int64_t nb = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
+  if (nb == 0) nb = 1;
+  int64_t* bsum;
+  int r = bp_ws(ctx, WS_MISC, (size_t)(nb + 1) * sizeof(int64_t), (void**)&bsum);
+  if (r) return r;
+  k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, ctx->stream>>>(in, n, bsum);
+  BP_LAUNCH_CHECK(ctx, "scan reduce");
+  k_scan_bsums<<<1, SCAN_THREADS, 0, ctx->stream>>>(bsum, nb);
+  BP_LAUNCH_CHECK(ctx, "scan block sums");
+  k_scan_down<<<(unsigned)nb, SCAN_THREADS, 0, ctx->stream>>>(in, n, bsum, out);
+  BP_LAUNCH_CHECK(ctx, "scan down");
+  // total
+  BP_CUDA(ctx, cudaMemcpyAsync(out + n, bsum + nb, sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                               ctx->stream));
+  return BP_OK;
+}
+
+int bp_radix_sort_pairs(bp_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
+                        uint32_t* vals_tmp, int64_t n, int key_bits, uint32_t** keys_out,
+                        uint32_t** vals_out) {
+  *keys_out = keys;
+  *vals_out = vals;
+  if (n <= 1 || key_bits <= 0) return BP_OK;
+  int64_t nblocks = (n + RS_ITEMS - 1) / RS_ITEMS;
+  int npass = (key_bits + 7) / 8;
+  int bits_per = (key_bits + npass - 1) / npass;  // balanced digit widths (<= 8)
+  uint32_t* hist;
+  int64_t* offs;
+  int r = bp_ws(ctx, WS_HIST, (size_t)RS_MAXDIG * nblocks * sizeof(uint32_t) +
+                                  ((size_t)RS_MAXDIG * nblocks + 1) * sizeof(int64_t) + 64,
+                (void**)&hist);
+  if (r) return r;
+  offs = (int64_t*)(((uintptr_t)(hist + (size_t)RS_MAXDIG * nblocks) + 15) & ~(uintptr_t)15);
+  uint32_t *ki = keys, *vi = vals, *ko = keys_tmp, *vo = vals_tmp;
+  int shift = 0;
+  for (int p = 0; p < npass; ++p) {
+    int nb = (shift + bits_per <= key_bits) ? bits_per : key_bits - shift;
+    int64_t hn = ((int64_t)1 << nb) * nblocks;
+    k_rs_hist<<<(unsigned)nblocks, RS_THREADS, 0, ctx->stream>>>(ki, n, shift, nb, hist,
+                                                                 nblocks);
+    BP_LAUNCH_CHECK(ctx, "radix hist");
+    r = bp_scan_u32_to_i64(ctx, hist, offs, hn);
+    if (r) return r;
+    k_rs_scatter<<<(unsigned)nblocks, RS_THREADS, 0, ctx->stream>>>(ki, vi, ko, vo, n, shift, nb,
+                                                                    offs, nblocks);
+    BP_LAUNCH_CHECK(ctx, "radix scatter");
+    uint32_t* t;
+    t = ki; ki = ko; ko = t;
+    t = vi; vi = vo; vo = t;
+    shift += nb;
+  }
+  *keys_out = ki;
+  *vals_out = vi;
+  return BP_OK;
+}
+
+int bp_tile_ranges(bp_ctx* ctx, const uint32_t* keys, int64_t n, int64_t n_tiles,
+                   int64_t* tile_start) {
+  int64_t threads = n + 1;
+  k_tile_ranges<<<(unsigned)((threads + 255) / 256), 256, 0, ctx->stream>>>(keys, n, n_tiles,
+                                                                            tile_start);
+  BP_LAUNCH_CHECK(ctx, "tile ranges");
+  return BP_OK;
+}

@@ -1,0 +1,128 @@
+"""Parity of the CUDA tile pair list, radix sort and PP deposit (Section 3.4, Eqs. f_ij
+and integrated kernel) with the oracle, on generator-drawn particle records."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2201_02632_gb300 import inputs as I
+from tests.gpu_common import api, assigned_tensor, ctx, folded  # noqa: F401
+from tests.helpers import assert_map_parity
+
+pytestmark = pytest.mark.gpu
+
+
+def _u32(t):
+    return t.cpu().numpy().view(np.uint32)
+
+
+@pytest.mark.parametrize("tile", [32, 64])
+@pytest.mark.parametrize("select", [0, 1, 2])
+def test_pairs_bit_exact(orc, api, ctx, tile, select):
+    nx, ny = 200, 130  # ragged tiles on both axes
+    a = I.assigned_particles(n=20000, npix=200, hmax=40, margin=30)
+    rec = assigned_tensor(a)
+    g = api.geom(nx, ny, 0.0, 0.0, 1.0)
+    k, v = ctx.pp_pairs(rec, g, tile, select)
+    ko, vo = orc.pp_pairs(a["px"], a["py"], a["hp"], a["kind"], nx, ny, tile, tile, select)
+    assert k.numel() == ko.size > 0
+    assert np.array_equal(_u32(k), ko)
+    assert np.array_equal(_u32(v), vo)
+
+
+def test_pairs_multi_pass_sort_bit_exact(orc, api, ctx):
+    # 4000 x 3000 map with 32-pixel tiles: 11750 tiles -> a two-pass radix sort
+    nx, ny = 4000, 3000
+    rng = np.random.default_rng(4)
+    n = 300000
+    a = {"px": rng.uniform(-50, nx + 50, n).astype(np.float32),
+         "py": rng.uniform(-50, ny + 50, n).astype(np.float32),
+         "hp": rng.exponential(8.0, n).astype(np.float32),
+         "Y": np.ones(n, np.float32), "B": np.ones(n, np.float32),
+         "kind": rng.integers(0, 3, n).astype(np.int32)}
+    rec = assigned_tensor(a)
+    g = api.geom(nx, ny, 0.0, 0.0, 1.0)
+    k, v = ctx.pp_pairs(rec, g, 32)
+    ko, vo = orc.pp_pairs(a["px"], a["py"], a["hp"], a["kind"], nx, ny, 32, 32)
+    assert np.array_equal(_u32(k), ko) and np.array_equal(_u32(v), vo)
+
+
+def test_pairs_edge_cases(orc, api, ctx):
+    g = api.geom(50, 40, 0.0, 0.0, 1.0)
+    # empty input
+    k, v = ctx.pp_pairs(torch.zeros((0, 8), dtype=torch.float32, device="cuda"), g, 32)
+    assert k.numel() == 0
+    # all particles off the map, NaN coordinates, kind NONE
+    a = {"px": np.array([-100, 500, np.nan, 10], np.float32),
+         "py": np.array([10, 10, 5, 10], np.float32),
+         "hp": np.array([5, 5, 1, 1], np.float32), "Y": np.ones(4, np.float32),
+         "B": np.ones(4, np.float32), "kind": np.array([0, 1, 0, 2], np.int32)}
+    k, v = ctx.pp_pairs(assigned_tensor(a), g, 32)
+    assert k.numel() == 0
+    # one particle covering the whole map
+    a1 = {kk: vv[:1].copy() for kk, vv in a.items()}
+    a1["px"][:] = 25.0
+    a1["hp"][:] = 1000.0
+    k, v = ctx.pp_pairs(assigned_tensor(a1), g, 32)
+    assert _u32(k).tolist() == [0, 1, 2, 3]
+
+
+def _deposit(api, ctx, a, nx, ny, select=0):
+    g = api.geom(nx, ny, 0.0, 0.0, 1.0)
+    maps = api.Maps.zeros(g)
+    ctx.paste_particles(assigned_tensor(a), g, maps, select)
+    return folded(maps)
+
+
+@pytest.mark.parametrize("tile,unit", [(64, 8192), (64, 256), (32, 4096), (32, 256)])
+def test_deposit_matches_oracle(orc, api, ctx, tile, unit):
+    nx, ny = 200, 130
+    a = I.assigned_particles(n=20000, npix=200, hmax=40, margin=30)
+    ctx.set_tiling(pp_tile=tile, pp_unit=unit)
+    y, b = _deposit(api, ctx, a, nx, ny)
+    ao = {k: (v.astype(np.float64) if v.dtype == np.float32 else v) for k, v in a.items()}
+    yo, bo = orc.pp_deposit(ao, orc.geom(nx, ny, 0.0, 0.0, 1.0))
+    assert_map_parity(y[0], yo, what="y")
+    assert_map_parity(b[0], bo, what="b")
+
+
+@pytest.mark.parametrize("select", [1, 2])
+def test_deposit_select(orc, api, ctx, select):
+    a = I.assigned_particles(n=5000, npix=96, hmax=20)
+    y, b = _deposit(api, ctx, a, 96, 96, select)
+    ao = {k: (v.astype(np.float64) if v.dtype == np.float32 else v) for k, v in a.items()}
+    yo, bo = orc.pp_deposit(ao, orc.geom(96, 96, 0.0, 0.0, 1.0), select=select)
+    if select == 2:
+        assert np.all(y == 0)
+    else:
+        assert_map_parity(y[0], yo, what="y")
+    assert_map_parity(b[0], bo, what="b")
+
+
+def test_deposit_conserves_interior_signal(api, ctx):
+    rng = np.random.default_rng(8)
+    n = 30000
+    hp = rng.uniform(0, 30, n).astype(np.float32)
+    a = {"px": rng.uniform(35, 265, n).astype(np.float32),
+         "py": rng.uniform(35, 165, n).astype(np.float32), "hp": hp,
+         "Y": rng.uniform(0, 1e-6, n).astype(np.float32),
+         "B": rng.normal(0, 1e-6, n).astype(np.float32), "kind": np.zeros(n, np.int32)}
+    y, b = _deposit(api, ctx, a, 300, 200)
+    assert y.sum() == pytest.approx(a["Y"].astype(np.float64).sum(), rel=1e-6)
+    assert b.sum() == pytest.approx(a["B"].astype(np.float64).sum(), rel=1e-5,
+                                    abs=1e-6 * np.abs(a["B"]).sum())
+
+
+def test_deposit_ngp_and_accumulation(api, ctx):
+    a = {"px": np.array([2.3, 7.0], np.float32), "py": np.array([6.9, 3.0], np.float32),
+         "hp": np.zeros(2, np.float32), "Y": np.array([3.0, 5.0], np.float32),
+         "B": np.array([-1.0, 2.0], np.float32), "kind": np.zeros(2, np.int32)}
+    g = api.geom(8, 8, 0.0, 0.0, 1.0)
+    maps = api.Maps.zeros(g)
+    rec = assigned_tensor(a)
+    ctx.paste_particles(rec, g, maps)
+    ctx.paste_particles(rec, g, maps)
+    ctx.finalize(g, maps)
+    y = maps.y[0].cpu().numpy()
+    assert y[6, 2] == 6.0 and y[3, 7] == 10.0 and y.sum() == 16.0
+    assert maps.b[0].cpu().numpy()[6, 2] == -2.0
+    assert float(maps.ylo.abs().sum()) == 0.0

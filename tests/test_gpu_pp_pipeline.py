@@ -1,0 +1,96 @@
+"""End-to-end PP parity on a seeded light-cone: CUDA solve -> assign -> paste -> finalize
+against the oracle's solve -> assign -> deposit (Sections 2 and 3.4)."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2201_02632_gb300 import inputs as I
+from tests.gpu_common import api, ctx, cuda, folded, gpu_geom, orc_geom  # noqa: F401
+from tests.helpers import assert_map_parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def cone():
+    return I.lightcone(n_part=300000, n_halo=200, npix=256, side_deg=2.0, seed=77)
+
+
+@pytest.fixture(scope="module")
+def oracle_side(orc, cone):
+    lc = cone
+    mo = orc.solve_halos(lc.halos.M, lc.halos.c, lc.halos.z)
+    a = orc.pp_assign(lc.parts, lc.Mp, lc.halos.pos, mo, orc_geom(orc, lc.geom))
+    return mo, a
+
+
+def _gpu_assign(api, ctx, lc, parts=None):
+    parts = parts or lc.parts
+    model, status = ctx.solve_halos(cuda(lc.halos.M), cuda(lc.halos.c), cuda(lc.halos.z))
+    tp = {k: cuda(v) for k, v in parts.items()}
+    g = gpu_geom(api, lc.geom)
+    rec = ctx.assign_particles(tp, lc.Mp, cuda(lc.halos.pos), model, status, g)
+    return rec, g
+
+
+def test_assign_matches_oracle(api, ctx, cone, oracle_side):
+    mo, a = oracle_side
+    rec, _ = _gpu_assign(api, ctx, cone)
+    r = rec.cpu().numpy().astype(np.float64)
+    kind = r[:, 5].astype(np.int32)
+    mism = np.count_nonzero(kind != a["kind"])
+    assert mism <= 2  # only particles within rounding of r_f may differ
+    ok = kind == a["kind"]
+    np.testing.assert_allclose(r[:, 0], a["px"], rtol=0, atol=2e-4)
+    np.testing.assert_allclose(r[:, 1], a["py"], rtol=0, atol=2e-4)
+    np.testing.assert_allclose(r[:, 2], a["hp"], rtol=2e-6)
+    sel = ok & (a["kind"] == 0)
+    np.testing.assert_allclose(r[sel, 3], a["Y"][sel], rtol=2e-5, atol=0)
+    np.testing.assert_allclose(r[ok, 4], a["B"][ok], rtol=2e-5, atol=1e-6 * np.abs(a["B"]).max())
+    assert np.all(r[kind == 1, 3] == 0)
+
+
+def test_pp_maps_match_oracle(orc, api, ctx, cone, oracle_side):
+    mo, a = oracle_side
+    rec, g = _gpu_assign(api, ctx, cone)
+    maps = api.Maps.zeros(g)
+    ctx.paste_particles(rec, g, maps)
+    y, b = folded(maps)
+    yo, bo = orc.pp_deposit(a, orc_geom(orc, cone.geom))
+    assert_map_parity(y[0], yo, what="y")
+    assert_map_parity(b[0], bo, what="b")
+    ctx.finalize(g, maps)
+    assert_map_parity(maps.y[0].cpu().numpy(), yo, what="y finalized")
+
+
+def test_ksz_sign_and_zero_velocity_exact(api, ctx, cone):
+    lc = cone
+    base = _gpu_assign(api, ctx, lc)
+    neg = dict(lc.parts, vx=-lc.parts["vx"], vy=-lc.parts["vy"], vz=-lc.parts["vz"])
+    zero = dict(lc.parts, vx=np.zeros_like(lc.parts["vx"]), vy=np.zeros_like(lc.parts["vy"]),
+                vz=np.zeros_like(lc.parts["vz"]))
+    out = []
+    for parts in (lc.parts, neg, zero):
+        rec, g = _gpu_assign(api, ctx, lc, parts)
+        maps = api.Maps.zeros(g)
+        ctx.paste_particles(rec, g, maps)
+        ctx.finalize(g, maps)
+        out.append((maps.y[0].cpu().numpy(), maps.b[0].cpu().numpy()))
+    (y0, b0), (y1, b1), (y2, b2) = out
+    assert np.array_equal(b1, -b0) and np.array_equal(y1, y0)
+    assert np.all(b2 == 0) and np.array_equal(y2, y0)
+    del base
+
+
+def test_halo_field_split_adds_up(api, ctx, cone):
+    rec, g = _gpu_assign(api, ctx, cone)
+    res = []
+    for sel in (0, 1, 2):
+        maps = api.Maps.zeros(g)
+        ctx.paste_particles(rec, g, maps, sel)
+        res.append(folded(maps))
+    np.testing.assert_allclose(res[0][0], res[1][0] + res[2][0], rtol=1e-5,
+                               atol=1e-6 * np.abs(res[0][0]).max())
+    np.testing.assert_allclose(res[0][1], res[1][1] + res[2][1], rtol=1e-4,
+                               atol=1e-6 * np.abs(res[0][1]).max())
+    assert np.all(res[2][0] == 0)
