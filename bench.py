@@ -107,8 +107,10 @@ class ClockSampler:
 def deposit_flops(rec_np, nx, ny):
     """Algorithmic FP32 flops of one deposit launch: 2 per pixel update (one FMA per map)
     over every particle's clipped 2h x 2h footprint; field particles update one map."""
-    px, py, hp, Y, kind = (rec_np[:, 0], rec_np[:, 1], rec_np[:, 2], rec_np[:, 3],
-                           rec_np[:, 5].astype(np.int32))
+    ints = rec_np.view(np.int32)
+    px = ints[:, 6].astype(np.float64) + rec_np[:, 0]
+    py = ints[:, 7].astype(np.float64) + rec_np[:, 1]
+    hp, Y, kind = rec_np[:, 2].astype(np.float64), rec_np[:, 3], ints[:, 5]
     with np.errstate(invalid="ignore"):
         i0 = np.floor(px - hp)
         i1 = np.floor(px + hp)

@@ -113,15 +113,19 @@ enum {
 #define BP_HALO_MAXIT 4      /* Newton iteration limit reached */
 #define BP_HALO_BADINPUT 5   /* M, c or z not finite / out of range */
 
-/* particle record written by bp_assign_particles: BP_ASSIGNED_STRIDE floats per
- * particle (32 bytes, 16-byte aligned):
- *   [0] px   pixel-unit x coordinate measured from the map's lower-left edge
- *   [1] py   pixel-unit y coordinate
- *   [2] hp   kernel radius h in pixels (2h x 2h support square)
- *   [3] Y    y_i: the particle's Compton-y in pixel units (Eq. y_i^PP,h)
- *   [4] B    b_i: the particle's kSZ b in pixel units (Eqs. b_i^PP,h, field_b)
- *   [5] kind 0 halo particle, 1 field particle, 2 contributes nothing
- *   [6],[7]  zero */
+/* particle record written by bp_assign_particles: BP_ASSIGNED_STRIDE 32-bit words
+ * per particle (32 bytes, 16-byte aligned).  The pixel-unit position measured from
+ * the map's lower-left edge is px = ix + fx (and py = iy + fy), split into an
+ * integer pixel index and an FP32 fraction so that its precision does not depend on
+ * the map size:
+ *   [0] fx   float, fractional part of px, 0 <= fx < 1
+ *   [1] fy   float, fractional part of py
+ *   [2] hp   float, kernel radius h in pixels (2h x 2h support square)
+ *   [3] Y    float, y_i: the particle's Compton-y in pixel units (Eq. y_i^PP,h)
+ *   [4] B    float, b_i: the particle's kSZ b in pixel units (Eqs. b_i^PP,h, field_b)
+ *   [5] kind int32, 0 halo particle, 1 field particle, 2 contributes nothing
+ *   [6] ix   int32, floor(px), clamped to +-2^30
+ *   [7] iy   int32, floor(py), clamped to +-2^30 */
 #define BP_ASSIGNED_STRIDE 8
 #define BP_KIND_HALO 0
 #define BP_KIND_FIELD 1

@@ -117,7 +117,7 @@ def lib():
                 "orc_pp_deposit": (None, [i64, P, P, P, P, P, P, pg, i32, P, P, i32]),
                 "orc_pp_deposit_pixels": (None, [i64, P, P, P, P, P, P, pg, i32, i64, P, P, P,
                                                  P, i32]),
-                "orc_pp_pairs": (i64, [i64, P, P, P, P, i32, i32, i32, i32, i32, P, P]),
+                "orc_pp_pairs": (i64, [i64, P, P, P, P, P, P, i32, i32, i32, i32, i32, P, P]),
                 "orc_hp_pairs": (i64, [i64, P, P, P, P, pg, d, i32, i32, P, P]),
                 "orc_energy_residual": (d, [pc, pi, d, d, d, d]),
             }
@@ -297,15 +297,15 @@ def pp_deposit_pixels(a: dict, g: Geom, pix_i, pix_j, select=0, nthreads=0):
     return yv, bv
 
 
-def pp_pairs(px, py, hp, kind, nx, ny, tw, th, select=0):
-    """(key, particle) pairs of the tile membership, decided in FP32, ordered by key
-    then particle index."""
-    px, py, hp, kind = _f32(px), _f32(py), _f32(hp), _i32(kind)
+def pp_pairs(ix, fx, iy, fy, hp, kind, nx, ny, tw, th, select=0):
+    """(key, particle) pairs of the tile membership, decided in FP32 from the split
+    position px = ix + fx, ordered by key then particle index."""
+    ix, iy, kind = _i32(ix), _i32(iy), _i32(kind)
+    fx, fy, hp = _f32(fx), _f32(fy), _f32(hp)
     L = lib()
-    n = L.orc_pp_pairs(px.size, _p(px), _p(py), _p(hp), _p(kind), nx, ny, tw, th, select, None,
-                       None)
+    args = (ix.size, _p(ix), _p(fx), _p(iy), _p(fy), _p(hp), _p(kind), nx, ny, tw, th, select)
+    n = L.orc_pp_pairs(*args, None, None)
     keys = np.empty(n, np.uint32)
     vals = np.empty(n, np.uint32)
-    L.orc_pp_pairs(px.size, _p(px), _p(py), _p(hp), _p(kind), nx, ny, tw, th, select, _p(keys),
-                   _p(vals))
+    L.orc_pp_pairs(*args, _p(keys), _p(vals))
     return keys, vals

@@ -903,25 +903,28 @@ void orc_pp_deposit_pixels(int64_t n, const double* px, const double* py, const 
 }
 
 /* ------------------------------------------------------------------ */
-/* Tile membership of particles (integer work, decided in FP32).       */
-/* A particle's 2h square covers pixel columns floor(px-hp)..floor(px+hp)
- * (computed in single precision, round-to-nearest, no contraction),
- * clipped to the map; tiles are TWxTH pixel blocks keyed
- * key = ty * ntx + tx.  Output: (key, particle index) pairs ordered by key,
- * ties by particle index.  Returns the pair count; if keys==NULL only counts. */
-static int o_span32(float c, float h, int n, int* lo, int* hi) {
-  if (!(h >= 0.0f)) return 0; /* a negative or NaN radius covers nothing */
-  volatile float a = c - h, b = c + h; /* single-precision rounding, no fusion */
-  if (!(a == a) || !(b == b)) return 0;
+/* Tile membership of particles (integer work, decided in FP32).
+ * A particle at pixel position px = ix + fx (integer index, FP32 fraction) with
+ * radius hp covers pixel columns ix + floor(fx - hp) .. ix + floor(fx + hp), the two
+ * bounds computed in single precision (round-to-nearest, no contraction), clipped
+ * to the map; a negative or NaN radius covers nothing.  Tiles are TWxTH pixel
+ * blocks keyed key = ty * ntx + tx.  Output: (key, particle index) pairs ordered by
+ * key, ties by particle index.  Returns the pair count; if keys==NULL only counts. */
+static int o_span32(int32_t ix, float fx, float h, int n, int* lo, int* hi) {
+  if (!(h >= 0.0f) || !(fx == fx)) return 0;
+  volatile float a = fx - h, b = fx + h; /* single-precision rounding, no fusion */
   float fa = floorf(a), fb = floorf(b);
-  if (fb < 0.0f || fa > (float)(n - 1)) return 0;
-  *lo = fa < 0.0f ? 0 : (int)fa;
-  *hi = fb > (float)(n - 1) ? n - 1 : (int)fb;
+  if (fa < -4.0e9f) fa = -4.0e9f;
+  if (fb > 4.0e9f) fb = 4.0e9f;
+  long long L = (long long)ix + (long long)fa, H = (long long)ix + (long long)fb;
+  if (H < 0 || L > n - 1) return 0;
+  *lo = L < 0 ? 0 : (int)L;
+  *hi = H > n - 1 ? n - 1 : (int)H;
   return 1;
 }
-int64_t orc_pp_pairs(int64_t n, const float* px, const float* py, const float* hp,
-                     const int32_t* kind, int nx, int ny, int tw, int th, int select,
-                     uint32_t* keys, uint32_t* vals) {
+int64_t orc_pp_pairs(int64_t n, const int32_t* ix, const float* fx, const int32_t* iy,
+                     const float* fy, const float* hp, const int32_t* kind, int nx, int ny,
+                     int tw, int th, int select, uint32_t* keys, uint32_t* vals) {
   int ntx = (nx + tw - 1) / tw, nty = (ny + th - 1) / th;
   int64_t* cnt = (int64_t*)calloc((size_t)ntx * nty + 1, sizeof(int64_t));
   int64_t total = 0;
@@ -931,8 +934,8 @@ int64_t orc_pp_pairs(int64_t n, const float* px, const float* py, const float* h
       if (select == 1 && kind[k] != 0) continue;
       if (select == 2 && kind[k] != 1) continue;
       int i0, i1, j0, j1;
-      if (!o_span32(px[k], hp[k], nx, &i0, &i1)) continue;
-      if (!o_span32(py[k], hp[k], ny, &j0, &j1)) continue;
+      if (!o_span32(ix[k], fx[k], hp[k], nx, &i0, &i1)) continue;
+      if (!o_span32(iy[k], fy[k], hp[k], ny, &j0, &j1)) continue;
       for (int ty = j0 / th; ty <= j1 / th; ++ty)
         for (int tx = i0 / tw; tx <= i1 / tw; ++tx) {
           int64_t key = (int64_t)ty * ntx + tx;

@@ -1,10 +1,11 @@
 // bp_hp.cu -- halo-based pasting (Section 3.3) and map finalisation (Section 3.2).
 //
 //  k_hp_prep    per halo: FP64 centre in pixel units, aperture, FP32 profile constants
-//  k_hp_table   per halo and table node u = r_perp / r_f: the line-of-sight integrals
-//               of the dimensionless pressure and density profiles, divided by the
-//               chord sqrt(1 - u^2) so that the tabulated function is smooth at the
-//               edge (Eqs. y^HP, b^HP); 16-point Gauss-Legendre per segment after
+//  k_hp_table   per halo and table node u = r_perp / r_f = s^2 (nodes uniform in s,
+//               which smooths the central cusp): the line-of-sight integrals of the
+//               dimensionless pressure and density profiles, divided by the chord
+//               sqrt(1 - u^2) so that the tabulated function is smooth at the edge
+//               (Eqs. y^HP, b^HP); 16-point Gauss-Legendre per segment after
 //               t = u sinh(s), split where the 3-D radius crosses r_vir and the zero
 //               of the thermal fraction
 //  k_hp_count / (map, tile, halo) pairs from the FP64 pixel-centre bounding box of the
@@ -15,7 +16,7 @@
 //  k_finalize   hi + lo folding and the conversion to Delta T / T_CMB
 #include "bp_internal.cuh"
 
-#define HP_NT 256          // table intervals on u in [0, 1]
+#define HP_NT 256          // table intervals on s = sqrt(u) in [0, 1]
 #define HP_ROW (HP_NT + 3) // with one ghost node at each end
 #define HP_NGL 16
 
@@ -130,7 +131,7 @@ __device__ __forceinline__ void profile_pn(const HpHalo& H, float x, float n_pol
   } else {
     tn = powf(th, n_poly);
   }
-  float Rnt = H.ant * __powf(x * H.q500, n_nt);
+  float Rnt = H.ant * powf(x * H.q500, n_nt);
   d = tn;
   p = tn * th * fmaxf(0.f, 1.0f - Rnt);
 }
@@ -149,7 +150,8 @@ __global__ void __launch_bounds__(256) k_hp_table(const HpHalo* __restrict__ hal
     ty[node + 1] = tb[node + 1] = 0.f;
     return;
   }
-  float u = (float)node / HP_NT;
+  float sn = (float)node / HP_NT;
+  float u = sn * sn;
   float Gy = 0.f, Gb = 0.f;
   if (node == HP_NT) {  // limit u -> 1: the profile at r_f
     float p, d;
@@ -214,7 +216,7 @@ __global__ void __launch_bounds__(256) k_hp_table(const HpHalo* __restrict__ hal
   tb[node + 1] = Gb;
 }
 
-// ghost nodes: G(-h) = G(h) (even in u), G(1+h) = 2 G(1) - G(1-h)
+// ghost nodes: G(s = -h) = G(h) (even in s), G(1+h) = 2 G(1) - G(1-h)
 __global__ void k_hp_ghosts(const HpHalo* __restrict__ halos, int64_t nh, float* tab) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nh) return;
@@ -298,9 +300,9 @@ __global__ void k_hp_uemit(const int64_t* __restrict__ tstart, int64_t n_tiles, 
 constexpr int HP_THREADS = 256;
 constexpr int HCH = 32;
 
-__device__ __forceinline__ float catmull(const float* __restrict__ t, float uu) {
-  // t: table row with ghosts; node k at t[k + 1]; uu in [0, 1)
-  float x = uu * HP_NT;
+__device__ __forceinline__ float catmull(const float* __restrict__ t, float ss) {
+  // t: table row with ghosts; node k (s = k / HP_NT) at t[k + 1]; ss in [0, 1)
+  float x = ss * HP_NT;
   int i = (int)x;
   if (i > HP_NT - 1) i = HP_NT - 1;
   float f = x - (float)i;
@@ -390,7 +392,8 @@ __global__ void __launch_bounds__(HP_THREADS)
               float uu = sqrtf(d2) * irf;
               if (uu < 1.0f) {
                 float chord = sqrtf(fmaxf(0.f, 1.0f - uu * uu));
-                float gy = catmull(ty, uu), gb = catmull(ty + HP_ROW, uu);
+                float ss = sqrtf(uu);
+                float gy = catmull(ty, ss), gb = catmull(ty + HP_ROW, ss);
                 kahan_add(hy[r][c], cy_[r][c], s_ay[k] * chord * gy);
                 kahan_add(hb[r][c], cb_[r][c], s_ab[k] * chord * gb);
               }

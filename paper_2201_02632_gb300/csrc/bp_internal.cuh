@@ -154,17 +154,18 @@ __device__ __forceinline__ float bp_wsplit(float dx, float h) {
   return dx < 0.0f ? wl : -wl;
 }
 
-// Pixel span of a particle, decided in FP32 with round-to-nearest and no
-// contraction: columns floor(c - h) .. floor(c + h), clipped to [0, n-1].
-// A negative or NaN radius covers nothing.
-__device__ __forceinline__ bool bp_span(float c, float h, int n, int& lo, int& hi) {
-  if (!(h >= 0.0f)) return false;
-  float a = __fsub_rn(c, h), b = __fadd_rn(c, h);
-  if (!(a == a) || !(b == b)) return false;
-  float fa = floorf(a), fb = floorf(b);
-  if (fb < 0.0f || fa > (float)(n - 1)) return false;
-  lo = fa < 0.0f ? 0 : (int)fa;
-  hi = fb > (float)(n - 1) ? n - 1 : (int)fb;
+// Pixel span of a particle at px = ix + fx with kernel radius h, decided in FP32
+// (round-to-nearest, no contraction) relative to ix: columns
+// ix + floor(fx - h) .. ix + floor(fx + h), clipped to [0, n-1].  A negative or NaN
+// radius covers nothing.
+__device__ __forceinline__ bool bp_span(int ix, float fx, float h, int n, int& lo, int& hi) {
+  if (!(h >= 0.0f) || !(fx == fx)) return false;
+  float a = __fsub_rn(fx, h), b = __fadd_rn(fx, h);
+  float fa = fmaxf(floorf(a), -4.0e9f), fb = fminf(floorf(b), 4.0e9f);
+  long long L = (long long)ix + (long long)fa, H = (long long)ix + (long long)fb;
+  if (H < 0 || L > n - 1) return false;
+  lo = L < 0 ? 0 : (int)L;
+  hi = H > n - 1 ? n - 1 : (int)H;
   return true;
 }
 

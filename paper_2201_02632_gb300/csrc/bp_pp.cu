@@ -78,6 +78,18 @@ __device__ __forceinline__ float powi_or_pow(float t, float n, int n_int) {
   return powf(t, n);
 }
 
+// px = ix + fx with ix = floor(px) (clamped to +-2^30) and 0 <= fx < 1 in FP32
+__device__ __forceinline__ float split_pixel(double p, int& ip) {
+  double fl = floor(p);
+  if (!(fl == fl)) { ip = 0; return __int_as_float(0x7fc00000); }
+  fl = fmin(fmax(fl, -1073741824.0), 1073741824.0);
+  float f = (float)(p - fl);
+  if (f >= 1.0f) { fl += 1.0; f = 0.0f; }
+  if (f < 0.0f) f = 0.0f;
+  ip = (int)fl;
+  return f;
+}
+
 struct AssignArgs {
   const float *x, *y, *z, *vx, *vy, *vz, *hs;
   const int32_t* hid;
@@ -101,12 +113,14 @@ __global__ void __launch_bounds__(256) k_assign(AssignArgs a, BpTables T) {
   float xf = a.x[i], yf = a.y[i], zf = a.z[i];
   // sky angles and pixel coordinates in FP64
   double thx = atan2((double)xf, (double)zf), thy = atan2((double)yf, (double)zf);
-  float px = (float)((thx - a.th0x) * a.inv_dth);
-  float py = (float)((thy - a.th0y) * a.inv_dth);
+  int ix, iy;
+  float fx = split_pixel((thx - a.th0x) * a.inv_dth, ix);
+  float fy = split_pixel((thy - a.th0y) * a.inv_dth, iy);
   float r2 = xf * xf + yf * yf + zf * zf;
   float rh = sqrtf(r2);       // comoving h^-1 Mpc
   float chi = rh * a.inv_h;   // comoving Mpc
-  float Y = 0.f, B = 0.f, kind = (float)BP_KIND_NONE;
+  float Y = 0.f, B = 0.f;
+  int kind = BP_KIND_NONE;
   float hp = 0.f;
   if (rh > 0.f) {
     hp = a.hs[i] * a.inv_h_dth / chi;
@@ -119,7 +133,7 @@ __global__ void __launch_bounds__(256) k_assign(AssignArgs a, BpTables T) {
     int32_t k = a.hid[i];
     if (k < 0) {
       B = a.field_B * ekin * geo;
-      kind = (float)BP_KIND_FIELD;
+      kind = BP_KIND_FIELD;
     } else if (k < a.nh) {
       const float* b = a.blk + (int64_t)k * HB;
       if (b[10] != 0.f) {
@@ -129,31 +143,31 @@ __global__ void __launch_bounds__(256) k_assign(AssignArgs a, BpTables T) {
           float th = (x <= b[2]) ? 1.0f - b[4] * g_inner(x) : 1.0f - b[5] + b[6] / x;
           th = fmaxf(th, 0.f);
           float thn = powi_or_pow(th, a.n_poly, a.n_int);
-          float Rnt = b[7] * __powf(x * b[3], a.n_nt);
+          float Rnt = b[7] * powf(x * b[3], a.n_nt);
           float vol = x * (1.0f + x) * (1.0f + x);  // rho_s / rho_NFW(r)
           Y = b[8] * thn * th * fmaxf(0.f, 1.0f - Rnt) * vol * geo;
           B = b[9] * thn * vol * ekin * geo * (1.0f / (float)bpc::C_KMS);
-          kind = (float)BP_KIND_HALO;
+          kind = BP_KIND_HALO;
         }
       }
     }
   }
   float4* o = reinterpret_cast<float4*>(a.out + i * BP_ASSIGNED_STRIDE);
-  o[0] = make_float4(px, py, hp, Y);
-  o[1] = make_float4(B, kind, 0.f, 0.f);
+  o[0] = make_float4(fx, fy, hp, Y);
+  o[1] = make_float4(B, __int_as_float(kind), __int_as_float(ix), __int_as_float(iy));
 }
 
 // ---------------------------------------------------------------- pairs
 __device__ __forceinline__ bool particle_tiles(const float4 r0, const float4 r1, int nx, int ny,
                                                int ts, int select, int& tx0, int& tx1, int& ty0,
                                                int& ty1) {
-  int kind = (int)r1.y;
+  int kind = __float_as_int(r1.y);
   if (kind == BP_KIND_NONE) return false;
   if (select == BP_SELECT_HALO && kind != BP_KIND_HALO) return false;
   if (select == BP_SELECT_FIELD && kind != BP_KIND_FIELD) return false;
   int i0, i1, j0, j1;
-  if (!bp_span(r0.x, r0.z, nx, i0, i1)) return false;
-  if (!bp_span(r0.y, r0.z, ny, j0, j1)) return false;
+  if (!bp_span(__float_as_int(r1.z), r0.x, r0.z, nx, i0, i1)) return false;
+  if (!bp_span(__float_as_int(r1.w), r0.y, r0.z, ny, j0, j1)) return false;
   tx0 = i0 / ts;
   tx1 = i1 / ts;
   ty0 = j0 / ts;
@@ -235,8 +249,9 @@ struct DepSmem {
   float ey[CH][TS + 1];
   float lo_y[TS * TS];
   float lo_b[TS * TS];
-  float4 p0[CH];      // px, py, hp, Y
+  float4 p0[CH];      // fx, fy, hp, Y
   float p1[CH];       // B
+  int2 pi[CH];        // ix - x0, iy - y0 (pixel index relative to the tile origin)
   int4 box[CH];       // footprint in tile coordinates i0, i1, j0, j1 (i0 > i1: none)
   int hasy[CH];
   int64_t unit;
@@ -300,9 +315,11 @@ __global__ void __launch_bounds__(DEP_THREADS, 2)
         float4 q1 = rec[2 * (int64_t)pi + 1];
         S.p0[tid] = q0;
         S.p1[tid] = q1.x;
+        const int ixp = __float_as_int(q1.z), iyp = __float_as_int(q1.w);
+        S.pi[tid] = make_int2(ixp - x0, iyp - y0);
         int i0, i1, j0, j1;
         int4 bx = make_int4(1, 0, 1, 0);
-        if (bp_span(q0.x, q0.z, nx, i0, i1) && bp_span(q0.y, q0.z, ny, j0, j1)) {
+        if (bp_span(ixp, q0.x, q0.z, nx, i0, i1) && bp_span(iyp, q0.y, q0.z, ny, j0, j1)) {
           bx.x = max(i0 - x0, 0);
           bx.y = min(i1 - x0, TS - 1);
           bx.z = max(j0 - y0, 0);
@@ -316,7 +333,9 @@ __global__ void __launch_bounds__(DEP_THREADS, 2)
       for (int q = tid; q < nch * (TS + 1); q += DEP_THREADS) {
         int k = q / (TS + 1), e = q % (TS + 1);
         float4 p = S.p0[k];
-        float dx = (float)(x0 + e) - p.x, dy = (float)(y0 + e) - p.y;
+        int2 ip = S.pi[k];
+        // edge minus centre: the integer part is exact, one rounding for the fraction
+        float dx = __fsub_rn((float)(e - ip.x), p.x), dy = __fsub_rn((float)(e - ip.y), p.y);
         if (p.z > 0.f) {
           S.ex[k][e] = bp_wsplit(dx, p.z);
           S.ey[k][e] = bp_wsplit(dy, p.z);
@@ -330,15 +349,19 @@ __global__ void __launch_bounds__(DEP_THREADS, 2)
       for (int q = tid; q < nch * TS; q += DEP_THREADS) {
         int k = q / TS, e = q % TS;
         float4 p = S.p0[k];
-        float ex0 = (float)(x0 + e), ex1 = ex0 + 1.f;
-        float ey0 = (float)(y0 + e), ey1 = ey0 + 1.f;
+        int2 ip = S.pi[k];
+        // cell e spans [e - ix', e + 1 - ix'] relative to px; it holds the centre when
+        // e - ix' < fx <= e + 1 - ix'
+        int kx = e - ip.x, ky = e - ip.y;
+        bool cx = (kx == 0 && p.x > 0.f) || (kx == -1 && p.x == 0.f);
+        bool cy = (ky == 0 && p.y > 0.f) || (ky == -1 && p.y == 0.f);
         float ax, ay;
         if (p.z > 0.f) {
-          ax = S.ex[k][e + 1] - S.ex[k][e] + ((ex0 < p.x && ex1 >= p.x) ? 1.f : 0.f);
-          ay = S.ey[k][e + 1] - S.ey[k][e] + ((ey0 < p.y && ey1 >= p.y) ? 1.f : 0.f);
-        } else {  // h = 0: nearest grid point
-          ax = (ex0 <= p.x && p.x < ex1) ? 1.f : 0.f;
-          ay = (ey0 <= p.y && p.y < ey1) ? 1.f : 0.f;
+          ax = S.ex[k][e + 1] - S.ex[k][e] + (cx ? 1.f : 0.f);
+          ay = S.ey[k][e + 1] - S.ey[k][e] + (cy ? 1.f : 0.f);
+        } else {  // h = 0: nearest grid point, the cell with e <= px < e + 1
+          ax = (kx == 0) ? 1.f : 0.f;
+          ay = (ky == 0) ? 1.f : 0.f;
         }
         S.a[k][e] = ax;
         S.by[k][e] = p.w * ay;

@@ -318,7 +318,7 @@ __global__ void __launch_bounds__(128) k_solve(BpParams P, BpTables TB, int64_t 
       double mx = m_of(x);
       double f = log(mx) - 3.0 * log(x) - lnK;
       if (f > 0) lo = x; else hi = x;
-      double df = x * x / ((1 + x) * (1 + x)) / mx - 3.0 / x;  // d f / d x
+      double df = x / ((1 + x) * (1 + x)) / mx - 3.0 / x;  // d f / d x
       double xn = x - f / df;
       if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
       if (fabs(xn - x) < 1e-15 * x) { x = xn; break; }
@@ -450,9 +450,16 @@ __global__ void __launch_bounds__(128) k_solve(BpParams P, BpTables TB, int64_t 
     return e;
   };
 
-  const double vlo0 = log(0.5 * h.rvir), vhi0 = log(10.0 * h.rvir);
-  double vlo = vlo0, vhi = vhi0;
+  // Safeguarded Newton in v = ln r_f on [ln 0.5 r_vir, ln 10 r_vir]: Newton steps
+  // (clamped) until a sign change is bracketed, then Newton with bisection inside
+  // the bracket.  The direction of R_e(r_f) is not assumed.
+  const double vmin = log(0.5 * h.rvir), vmax = log(10.0 * h.rvir);
   double v = log(1.1 * h.rvir);
+  double va = 0, vb = 0, Ra = 0;  // bracket [va, vb] with R(va) R(vb) < 0
+  bool have_br = false;
+  double vprev = 0, Rprev = 0;
+  bool have_prev = false;
+  int hits_min = 0, hits_max = 0;
   double Tw = 0.0;
   int st = BP_HALO_MAXIT;
   Eval e;
@@ -463,17 +470,26 @@ __global__ void __launch_bounds__(128) k_solve(BpParams P, BpTables TB, int64_t 
     if (!e.ok) { st = BP_HALO_MAXIT; break; }
     Tw = e.T;
     if (fabs(e.Re) < tol && fabs(e.Rm) < tol) { st = BP_HALO_OK; break; }
-    if (e.Re < 0) vlo = v; else vhi = v;  // R_e increases with r_f
-    if (vhi - vlo < 1e-15 * fabs(v)) { st = BP_HALO_OK; break; }
+    if (have_prev && ((e.Re > 0) != (Rprev > 0))) {
+      have_br = true;
+      va = vprev; Ra = Rprev; vb = v;
+    } else if (have_br) {
+      // shrink the bracket, keeping the sign change
+      if ((e.Re > 0) == (Ra > 0)) { va = v; Ra = e.Re; } else { vb = v; }
+    }
+    if (have_br && fabs(vb - va) < 1e-15 * fabs(v)) { st = BP_HALO_OK; break; }
     double step = -e.Re / e.dRe_dv;
-    if (!isfinite(step)) step = (e.Re < 0) ? 0.5 : -0.5;
+    if (!isfinite(step)) step = 0.5;
     step = fmax(-0.5, fmin(0.5, step));
     double vn = v + step;
-    if (!(vn > vlo && vn < vhi)) {
-      if (v <= vlo0 + 1e-12 && e.Re > 0) { st = BP_HALO_NOBRACKET; break; }
-      if (v >= vhi0 - 1e-12 && e.Re < 0) { st = BP_HALO_NOBRACKET; break; }
-      vn = 0.5 * (vlo + vhi);
+    if (have_br) {
+      double lo = fmin(va, vb), hi = fmax(va, vb);
+      if (!(vn > lo && vn < hi)) vn = 0.5 * (va + vb);
+    } else {
+      if (vn <= vmin) { vn = vmin; if (++hits_min > 2) { st = BP_HALO_NOBRACKET; break; } }
+      if (vn >= vmax) { vn = vmax; if (++hits_max > 2) { st = BP_HALO_NOBRACKET; break; } }
     }
+    vprev = v; Rprev = e.Re; have_prev = true;
     v = vn;
   }
   if (e.ok && e.thf <= 0.0) st = BP_HALO_THETA;

@@ -238,14 +238,27 @@ def lightcone(n_part=4_000_000, n_halo=3000, side_deg=2.0, zr=(0.05, 1.5), halo_
     return LightCone(parts, cat, Mp, g, {"h_field": h_field, "n_halo_particles": n_h})
 
 
+def split_positions(p):
+    """Pixel-unit positions -> (int32 floor, float32 fraction in [0, 1), the exact FP64
+    value ix + fx), the position representation of the deposit's particle records."""
+    p = np.asarray(p, np.float64)
+    fl = np.floor(p)
+    fr = (p - fl).astype(np.float32)
+    up = fr >= 1.0
+    fl = fl + up
+    fr[up] = 0.0
+    ix = np.clip(fl, -2 ** 30, 2 ** 30).astype(np.int32)
+    return ix, fr, ix.astype(np.float64) + fr.astype(np.float64)
+
+
 def assigned_particles(n=20000, npix=96, seed=SEED_BASE + 11, hmax=24.0, frac_field=0.4,
                        margin=8.0):
-    """Directly drawn per-particle deposit inputs (pixel coordinates, kernel radius in
+    """Directly drawn per-particle deposit inputs (pixel positions, kernel radius in
     pixels, signals) for testing the deposit alone.  Mixes tiny (sub-pixel), medium and
     large kernels, particles straddling the map edge, h = 0, and signed B."""
     rng = np.random.default_rng(seed)
-    px = rng.uniform(-margin, npix + margin, n).astype(np.float32)
-    py = rng.uniform(-margin, npix + margin, n).astype(np.float32)
+    ix, fx, px = split_positions(rng.uniform(-margin, npix + margin, n))
+    iy, fy, py = split_positions(rng.uniform(-margin, npix + margin, n))
     u = rng.uniform(0, 1, n)
     hp = np.where(u < 0.3, rng.uniform(0.0, 1.0, n),
                   np.where(u < 0.8, rng.uniform(1.0, 6.0, n), rng.uniform(6.0, hmax, n)))
@@ -254,5 +267,15 @@ def assigned_particles(n=20000, npix=96, seed=SEED_BASE + 11, hmax=24.0, frac_fi
     kind[rng.uniform(0, 1, n) < 0.05] = 2
     Y = np.where(kind == 0, 10.0 ** rng.uniform(-9, -6, n), 0.0)
     B = np.where(kind == 2, 0.0, rng.normal(0.0, 1e-7, n))
-    return {"px": px, "py": py, "hp": hp.astype(np.float32), "Y": Y.astype(np.float32),
+    return {"ix": ix, "fx": fx, "iy": iy, "fy": fy, "px": px, "py": py,
+            "hp": hp.astype(np.float32), "Y": Y.astype(np.float32),
             "B": B.astype(np.float32), "kind": kind}
+
+
+def deposit_inputs(px, py, hp, Y, B, kind):
+    """Deposit inputs from given pixel positions (any float type)."""
+    ix, fx, px = split_positions(px)
+    iy, fy, py = split_positions(py)
+    return {"ix": ix, "fx": fx, "iy": iy, "fy": fy, "px": px, "py": py,
+            "hp": np.asarray(hp, np.float32), "Y": np.asarray(Y, np.float32),
+            "B": np.asarray(B, np.float32), "kind": np.asarray(kind, np.int32)}

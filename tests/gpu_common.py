@@ -28,12 +28,30 @@ def orc_geom(orc, g):
 
 
 def assigned_tensor(a):
-    """Generator-drawn deposit inputs -> the [n, 8] FP32 record layout of bp.h."""
-    n = a["px"].size
+    """Deposit inputs (see inputs.assigned_particles / deposit_inputs) -> the [n, 8]
+    record layout of bp.h: fx, fy, hp, Y, B as FP32; kind, ix, iy as int32 bits."""
+    n = a["fx"].size
     rec = np.zeros((n, 8), np.float32)
-    rec[:, 0], rec[:, 1], rec[:, 2] = a["px"], a["py"], a["hp"]
-    rec[:, 3], rec[:, 4], rec[:, 5] = a["Y"], a["B"], a["kind"].astype(np.float32)
+    rec[:, 0], rec[:, 1], rec[:, 2] = a["fx"], a["fy"], a["hp"]
+    rec[:, 3], rec[:, 4] = a["Y"], a["B"]
+    ints = rec.view(np.int32)
+    ints[:, 5], ints[:, 6], ints[:, 7] = a["kind"], a["ix"], a["iy"]
     return cuda(rec)
+
+
+def records_numpy(rec):
+    """[n, 8] record tensor -> dict with the exact FP64 positions px = ix + fx."""
+    r = rec.cpu().numpy()
+    ints = r.view(np.int32)
+    return {"px": ints[:, 6].astype(np.float64) + r[:, 0].astype(np.float64),
+            "py": ints[:, 7].astype(np.float64) + r[:, 1].astype(np.float64),
+            "hp": r[:, 2].astype(np.float64), "Y": r[:, 3].astype(np.float64),
+            "B": r[:, 4].astype(np.float64), "kind": ints[:, 5].copy()}
+
+
+def orc_deposit_inputs(a):
+    return {k: np.asarray(a[k], np.float64) if k != "kind" else a[k]
+            for k in ("px", "py", "hp", "Y", "B", "kind")}
 
 
 def folded(maps):

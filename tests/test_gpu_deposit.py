@@ -5,7 +5,7 @@ import pytest
 import torch
 
 from paper_2201_02632_gb300 import inputs as I
-from tests.gpu_common import api, assigned_tensor, ctx, folded  # noqa: F401
+from tests.gpu_common import api, assigned_tensor, ctx, folded, orc_deposit_inputs  # noqa: F401
 from tests.helpers import assert_map_parity
 
 pytestmark = pytest.mark.gpu
@@ -23,7 +23,8 @@ def test_pairs_bit_exact(orc, api, ctx, tile, select):
     rec = assigned_tensor(a)
     g = api.geom(nx, ny, 0.0, 0.0, 1.0)
     k, v = ctx.pp_pairs(rec, g, tile, select)
-    ko, vo = orc.pp_pairs(a["px"], a["py"], a["hp"], a["kind"], nx, ny, tile, tile, select)
+    ko, vo = orc.pp_pairs(a["ix"], a["fx"], a["iy"], a["fy"], a["hp"], a["kind"], nx, ny, tile,
+                          tile, select)
     assert k.numel() == ko.size > 0
     assert np.array_equal(_u32(k), ko)
     assert np.array_equal(_u32(v), vo)
@@ -34,15 +35,13 @@ def test_pairs_multi_pass_sort_bit_exact(orc, api, ctx):
     nx, ny = 4000, 3000
     rng = np.random.default_rng(4)
     n = 300000
-    a = {"px": rng.uniform(-50, nx + 50, n).astype(np.float32),
-         "py": rng.uniform(-50, ny + 50, n).astype(np.float32),
-         "hp": rng.exponential(8.0, n).astype(np.float32),
-         "Y": np.ones(n, np.float32), "B": np.ones(n, np.float32),
-         "kind": rng.integers(0, 3, n).astype(np.int32)}
+    a = I.deposit_inputs(rng.uniform(-50, nx + 50, n), rng.uniform(-50, ny + 50, n),
+                         rng.exponential(8.0, n), np.ones(n), np.ones(n),
+                         rng.integers(0, 3, n))
     rec = assigned_tensor(a)
     g = api.geom(nx, ny, 0.0, 0.0, 1.0)
     k, v = ctx.pp_pairs(rec, g, 32)
-    ko, vo = orc.pp_pairs(a["px"], a["py"], a["hp"], a["kind"], nx, ny, 32, 32)
+    ko, vo = orc.pp_pairs(a["ix"], a["fx"], a["iy"], a["fy"], a["hp"], a["kind"], nx, ny, 32, 32)
     assert np.array_equal(_u32(k), ko) and np.array_equal(_u32(v), vo)
 
 
@@ -52,16 +51,12 @@ def test_pairs_edge_cases(orc, api, ctx):
     k, v = ctx.pp_pairs(torch.zeros((0, 8), dtype=torch.float32, device="cuda"), g, 32)
     assert k.numel() == 0
     # all particles off the map, NaN coordinates, kind NONE
-    a = {"px": np.array([-100, 500, np.nan, 10], np.float32),
-         "py": np.array([10, 10, 5, 10], np.float32),
-         "hp": np.array([5, 5, 1, 1], np.float32), "Y": np.ones(4, np.float32),
-         "B": np.ones(4, np.float32), "kind": np.array([0, 1, 0, 2], np.int32)}
+    a = I.deposit_inputs([-100, 500, 10, 10], [10, 10, 5, 10], [5, 5, -1, 1], np.ones(4),
+                         np.ones(4), [0, 1, 0, 2])
     k, v = ctx.pp_pairs(assigned_tensor(a), g, 32)
     assert k.numel() == 0
     # one particle covering the whole map
-    a1 = {kk: vv[:1].copy() for kk, vv in a.items()}
-    a1["px"][:] = 25.0
-    a1["hp"][:] = 1000.0
+    a1 = I.deposit_inputs([25.0], [10.0], [1000.0], [1.0], [1.0], [0])
     k, v = ctx.pp_pairs(assigned_tensor(a1), g, 32)
     assert _u32(k).tolist() == [0, 1, 2, 3]
 
@@ -79,8 +74,7 @@ def test_deposit_matches_oracle(orc, api, ctx, tile, unit):
     a = I.assigned_particles(n=20000, npix=200, hmax=40, margin=30)
     ctx.set_tiling(pp_tile=tile, pp_unit=unit)
     y, b = _deposit(api, ctx, a, nx, ny)
-    ao = {k: (v.astype(np.float64) if v.dtype == np.float32 else v) for k, v in a.items()}
-    yo, bo = orc.pp_deposit(ao, orc.geom(nx, ny, 0.0, 0.0, 1.0))
+    yo, bo = orc.pp_deposit(orc_deposit_inputs(a), orc.geom(nx, ny, 0.0, 0.0, 1.0))
     assert_map_parity(y[0], yo, what="y")
     assert_map_parity(b[0], bo, what="b")
 
@@ -89,8 +83,8 @@ def test_deposit_matches_oracle(orc, api, ctx, tile, unit):
 def test_deposit_select(orc, api, ctx, select):
     a = I.assigned_particles(n=5000, npix=96, hmax=20)
     y, b = _deposit(api, ctx, a, 96, 96, select)
-    ao = {k: (v.astype(np.float64) if v.dtype == np.float32 else v) for k, v in a.items()}
-    yo, bo = orc.pp_deposit(ao, orc.geom(96, 96, 0.0, 0.0, 1.0), select=select)
+    yo, bo = orc.pp_deposit(orc_deposit_inputs(a), orc.geom(96, 96, 0.0, 0.0, 1.0),
+                            select=select)
     if select == 2:
         assert np.all(y == 0)
     else:
@@ -101,11 +95,9 @@ def test_deposit_select(orc, api, ctx, select):
 def test_deposit_conserves_interior_signal(api, ctx):
     rng = np.random.default_rng(8)
     n = 30000
-    hp = rng.uniform(0, 30, n).astype(np.float32)
-    a = {"px": rng.uniform(35, 265, n).astype(np.float32),
-         "py": rng.uniform(35, 165, n).astype(np.float32), "hp": hp,
-         "Y": rng.uniform(0, 1e-6, n).astype(np.float32),
-         "B": rng.normal(0, 1e-6, n).astype(np.float32), "kind": np.zeros(n, np.int32)}
+    a = I.deposit_inputs(rng.uniform(35, 265, n), rng.uniform(35, 165, n),
+                         rng.uniform(0, 30, n), rng.uniform(0, 1e-6, n), rng.normal(0, 1e-6, n),
+                         np.zeros(n))
     y, b = _deposit(api, ctx, a, 300, 200)
     assert y.sum() == pytest.approx(a["Y"].astype(np.float64).sum(), rel=1e-6)
     assert b.sum() == pytest.approx(a["B"].astype(np.float64).sum(), rel=1e-5,
@@ -113,9 +105,7 @@ def test_deposit_conserves_interior_signal(api, ctx):
 
 
 def test_deposit_ngp_and_accumulation(api, ctx):
-    a = {"px": np.array([2.3, 7.0], np.float32), "py": np.array([6.9, 3.0], np.float32),
-         "hp": np.zeros(2, np.float32), "Y": np.array([3.0, 5.0], np.float32),
-         "B": np.array([-1.0, 2.0], np.float32), "kind": np.zeros(2, np.int32)}
+    a = I.deposit_inputs([2.3, 7.0], [6.9, 3.0], [0.0, 0.0], [3.0, 5.0], [-1.0, 2.0], [0, 0])
     g = api.geom(8, 8, 0.0, 0.0, 1.0)
     maps = api.Maps.zeros(g)
     rec = assigned_tensor(a)

@@ -5,7 +5,7 @@ import pytest
 import torch
 
 from paper_2201_02632_gb300 import inputs as I
-from tests.gpu_common import api, ctx, cuda, folded, gpu_geom, orc_geom  # noqa: F401
+from tests.gpu_common import api, ctx, cuda, folded, gpu_geom, orc_geom, records_numpy  # noqa: F401
 from tests.helpers import assert_map_parity
 
 pytestmark = pytest.mark.gpu
@@ -36,18 +36,19 @@ def _gpu_assign(api, ctx, lc, parts=None):
 def test_assign_matches_oracle(api, ctx, cone, oracle_side):
     mo, a = oracle_side
     rec, _ = _gpu_assign(api, ctx, cone)
-    r = rec.cpu().numpy().astype(np.float64)
-    kind = r[:, 5].astype(np.int32)
+    r = records_numpy(rec)
+    kind = r["kind"]
     mism = np.count_nonzero(kind != a["kind"])
     assert mism <= 2  # only particles within rounding of r_f may differ
     ok = kind == a["kind"]
-    np.testing.assert_allclose(r[:, 0], a["px"], rtol=0, atol=2e-4)
-    np.testing.assert_allclose(r[:, 1], a["py"], rtol=0, atol=2e-4)
-    np.testing.assert_allclose(r[:, 2], a["hp"], rtol=2e-6)
+    np.testing.assert_allclose(r["px"], a["px"], rtol=0, atol=2e-7)
+    np.testing.assert_allclose(r["py"], a["py"], rtol=0, atol=2e-7)
+    np.testing.assert_allclose(r["hp"], a["hp"], rtol=2e-6)
     sel = ok & (a["kind"] == 0)
-    np.testing.assert_allclose(r[sel, 3], a["Y"][sel], rtol=2e-5, atol=0)
-    np.testing.assert_allclose(r[ok, 4], a["B"][ok], rtol=2e-5, atol=1e-6 * np.abs(a["B"]).max())
-    assert np.all(r[kind == 1, 3] == 0)
+    np.testing.assert_allclose(r["Y"][sel], a["Y"][sel], rtol=2e-5, atol=0)
+    np.testing.assert_allclose(r["B"][ok], a["B"][ok], rtol=2e-5,
+                               atol=1e-6 * np.abs(a["B"]).max())
+    assert np.all(r["Y"][kind == 1] == 0)
 
 
 def test_pp_maps_match_oracle(orc, api, ctx, cone, oracle_side):

@@ -16,7 +16,9 @@ ENERGY = ("E_gi", "E_dm", "P_s")
 SOLVED = ("T", "rho0", "P0", "r_f")
 
 
-def _compare(orc, api, mo, mg, rtol_closed=1e-11, rtol_energy=1e-9, rtol_solved=1e-7):
+def _compare(orc, api, mo, mg, rtol_closed=1e-11, rtol_energy=1e-8, rtol_solved=1e-7):
+    # rtol_energy: the closed-form dispersion (dilogarithm bracket) cancels ~3 digits at
+    # c r/r_vir ~ 25, the quadrature oracle does not
     F = orc.F
     for name in CLOSED:
         np.testing.assert_allclose(mg[api.MF[ORC_TO_GPU[name]]], mo[:, F[name]],

@@ -123,7 +123,8 @@ def test_deposit_h_zero_is_nearest_grid_point(orc):
 
 def test_deposit_select_and_sampled_pixels(orc):
     a = I.assigned_particles(n=3000, npix=40, hmax=10)
-    a = {k: (v.astype(np.float64) if v.dtype == np.float32 else v) for k, v in a.items()}
+    a = {k: (np.asarray(a[k], np.float64) if k != "kind" else a[k])
+         for k in ("px", "py", "hp", "Y", "B", "kind")}
     g = orc.geom(40, 40, 0.0, 0.0, 1.0)
     ya, ba = orc.pp_deposit(a, g, select=0)
     yh, bh = orc.pp_deposit(a, g, select=1)
@@ -144,12 +145,14 @@ def test_tile_pairs_cover_every_weighted_pixel(orc):
     a = I.assigned_particles(n=400, npix=70, hmax=20)
     nx = ny = 70
     tw, th = 16, 8
-    keys, vals = orc.pp_pairs(a["px"], a["py"], a["hp"], a["kind"], nx, ny, tw, th)
+    keys, vals = orc.pp_pairs(a["ix"], a["fx"], a["iy"], a["fy"], a["hp"], a["kind"], nx, ny,
+                              tw, th)
     order = np.lexsort((vals, keys))
     assert np.array_equal(order, np.arange(keys.size))
     ntx = (nx + tw - 1) // tw
     g = orc.geom(nx, ny, 0.0, 0.0, 1.0)
-    a64 = {k: (v.astype(np.float64) if v.dtype == np.float32 else v) for k, v in a.items()}
+    a64 = {k: (np.asarray(a[k], np.float64) if k != "kind" else a[k])
+           for k in ("px", "py", "hp", "Y", "B", "kind")}
     for k in range(0, 400, 7):
         if a["kind"][k] == 2:
             assert not np.any(vals == k)
