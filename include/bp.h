@@ -217,6 +217,31 @@ int bp_assign_particles(bp_ctx* ctx, int64_t n, const float* x, const float* y, 
 int bp_paste_particles(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_geom* geom,
                        int select, float* ymap, float* bmap, float* ylo, float* blo);
 
+/* bp_paste_particles for callers that cannot allocate device memory during a call:
+ * applications that give their whole device memory to their own pool allocator at
+ * start-up, and latency-critical loops in which cudaMalloc/cudaFree would
+ * synchronise the device.  (The paper has no counterpart: this is a service of the
+ * library.)  Same arguments, results and host synchronisation as bp_paste_particles,
+ * but all scratch lives in one fixed device array inside the library (about 23 MB,
+ * held on every device that loads the library until the process exits) and each
+ * tile is deposited by a single CTA.  It calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Limits: n <= BP_NOALLOC_MAX_PARTICLES particles, at most
+ * BP_NOALLOC_MAX_PAIRS (tile, particle) pairs and BP_NOALLOC_MAX_TILES tiles of the
+ * context's deposit tile size; beyond them it returns BP_ERANGE with a message (the
+ * pair count is known only after the pair-count pass, so that check comes after the
+ * one host synchronisation, before anything is written to the maps).
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  Every call
+ * reuses the same array, which keeps the previous call's contents: calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and must not be issued
+ * concurrently. */
+#define BP_NOALLOC_MAX_PARTICLES (1 << 19)
+#define BP_NOALLOC_MAX_PAIRS (1 << 20)
+#define BP_NOALLOC_MAX_TILES 4096
+int bp_paste_particles_noalloc(bp_ctx* ctx, int64_t n, const float* assigned,
+                               const bp_map_geom* geom, int select, float* ymap, float* bmap,
+                               float* ylo, float* blo);
+
 /* The tile pair list of the deposit (for tests): keys (tile index ty*ntx+tx) and
  * particle indices ordered by key then index.  capacity: entries the caller
  * allocated; n_pairs (host pointer) receives the count.  BP_ERANGE if capacity

@@ -27,7 +27,7 @@ OUT_YB, OUT_DT = 0, 1
 EXPORTS = ("bp_create", "bp_destroy", "bp_last_error", "bp_set_stream", "bp_set_tiling",
            "bp_workspace_bytes", "bp_set_timing", "bp_phase_times", "bp_kernel_launches",
            "bp_solve_halos", "bp_assign_particles", "bp_paste_particles", "bp_pp_pairs",
-           "bp_paste_halos", "bp_finalize_map")
+           "bp_paste_halos", "bp_finalize_map", "bp_paste_particles_noalloc")
 PHASES = ("solve", "assign", "pairs", "sort", "deposit", "reduce", "hp_table", "hp_pairs",
           "hp_paste", "finalize")
 
@@ -76,6 +76,8 @@ def load():
                 "bp_assign_particles": (i32, [P, i64, P, P, P, P, P, P, P, P, d, i64, P, P, P,
                                               C.POINTER(BpGeom), P]),
                 "bp_paste_particles": (i32, [P, i64, P, C.POINTER(BpGeom), i32, P, P, P, P]),
+                "bp_paste_particles_noalloc": (i32, [P, i64, P, C.POINTER(BpGeom), i32, P, P, P,
+                                                     P]),
                 "bp_pp_pairs": (i32, [P, i64, P, C.POINTER(BpGeom), i32, i32, P, P, i64,
                                       C.POINTER(i64)]),
                 "bp_paste_halos": (i32, [P, i64, P, P, P, P, P, P, C.POINTER(BpGeom), d, P, P, P,

@@ -183,3 +183,33 @@ int bp_radix_sort_pairs(bp_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t* k
                         uint32_t** vals_out);
 int bp_tile_ranges(bp_ctx* ctx, const uint32_t* keys, int64_t n, int64_t n_tiles,
                    int64_t* tile_start);
+
+// caller-buffer variants (no scratch allocation)
+int bp_scan_u32_to_i64_buf(bp_ctx* ctx, const uint32_t* in, int64_t* out, int64_t n,
+                           int64_t* bsum);
+int bp_radix_sort_pairs_buf(bp_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
+                            uint32_t* vals_tmp, int64_t n, int key_bits, uint32_t* hist,
+                            int64_t* offs, int64_t* bsum, uint32_t** keys_out,
+                            uint32_t** vals_out);
+
+// Scratch of the particle paste when the caller provides it (one work unit per tile,
+// so no partial tiles).  Capacities are checked by the caller of bp_pp_paste_buffers.
+struct BpPasteBuffers {
+  uint32_t* counts;   // [n + 1]
+  int64_t* offs;      // [n + 1]
+  uint32_t *keys0, *vals0, *keys1, *vals1;  // [max_pairs] each
+  uint32_t* hist;     // [256 * ceil(max_pairs / 4096)]
+  int64_t* hoffs;     // [256 * ceil(max_pairs / 4096) + 1]
+  int64_t* bsum;      // [max(n, 256 * ceil(max_pairs / 4096), max_tiles) / 8192 + 2]
+  int64_t* tstart;    // [max_tiles + 1]
+  int64_t* uoff;      // [max_tiles + 1]
+  uint32_t* ucount;   // [max_tiles + 1]
+  void* units;        // [max_tiles] work units
+  int64_t* counter;   // [1], cleared by bp_pp_paste_buffers
+  int64_t max_pairs;
+  int64_t max_tiles;
+};
+int bp_pp_paste_buffers(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_geom* geom,
+                        int select, float* ymap, float* bmap, float* ylo, float* blo,
+                        const BpPasteBuffers* buf);
+size_t bp_pp_unit_bytes();

@@ -583,7 +583,81 @@ int halo_blocks(bp_ctx* ctx, int64_t nh, const double* model, const int32_t* sta
   return BP_OK;
 }
 
+template <int TS>
+int deposit_buffers(bp_ctx* ctx, const float* assigned, const bp_map_geom* g,
+                    const uint32_t* keys, const uint32_t* vals, int64_t np, int64_t n_tiles,
+                    float* ymap, float* bmap, float* ylo, float* blo, const BpPasteBuffers* B) {
+  const int ntx = (g->nx + TS - 1) / TS;
+  // one work unit per tile: every tile is written straight into the map
+  const int unit = 0x7fffffff;
+  int r;
+  if ((r = bp_tile_ranges(ctx, keys, np, n_tiles, B->tstart))) return r;
+  unsigned tb = (unsigned)((n_tiles + 255) / 256);
+  k_unit_count<<<tb, 256, 0, ctx->stream>>>(B->tstart, n_tiles, unit, B->ucount);
+  BP_LAUNCH_CHECK(ctx, "unit count");
+  if ((r = bp_scan_u32_to_i64_buf(ctx, B->ucount, B->uoff, n_tiles, B->bsum))) return r;
+  Unit* units = (Unit*)B->units;
+  k_unit_emit<<<tb, 256, 0, ctx->stream>>>(B->tstart, n_tiles, unit, B->uoff, units);
+  BP_LAUNCH_CHECK(ctx, "unit emit");
+  BP_CUDA(ctx, cudaMemsetAsync(B->counter, 0, sizeof(int64_t), ctx->stream));
+  const size_t smem = sizeof(DepSmem<TS>);
+  BP_CUDA(ctx, cudaFuncSetAttribute(k_deposit<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  int per_sm = 0;
+  BP_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deposit<TS>, DEP_THREADS,
+                                                             smem));
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)ctx->num_sms * per_sm;
+  if (grid > n_tiles) grid = n_tiles;
+  k_deposit<TS><<<(unsigned)grid, DEP_THREADS, smem, ctx->stream>>>(
+      reinterpret_cast<const float4*>(assigned), vals, units, B->uoff + n_tiles, B->counter,
+      g->nx, g->ny, ntx, ymap, bmap, ylo, blo, nullptr);
+  BP_LAUNCH_CHECK(ctx, "deposit");
+  return BP_OK;
+}
+
 }  // namespace
+
+size_t bp_pp_unit_bytes() { return sizeof(Unit); }
+
+// The particle paste with every scratch buffer supplied by the caller.  Reads back the
+// pair count (one host synchronisation) and returns BP_ERANGE if it exceeds max_pairs.
+int bp_pp_paste_buffers(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_geom* g,
+                        int select, float* ymap, float* bmap, float* ylo, float* blo,
+                        const BpPasteBuffers* B) {
+  const int ts = ctx->pp_tile;
+  const int ntx = (g->nx + ts - 1) / ts, nty = (g->ny + ts - 1) / ts;
+  const int64_t n_tiles = (int64_t)ntx * nty;
+  if (n_tiles > B->max_tiles)
+    return bp_fail(ctx, BP_ERANGE, "paste (no allocation): %lld tiles exceed the limit %lld",
+                   (long long)n_tiles, (long long)B->max_tiles);
+  const float4* rec = reinterpret_cast<const float4*>(assigned);
+  unsigned nb = (unsigned)((n + 255) / 256);
+  int r;
+  k_pair_count<<<nb, 256, 0, ctx->stream>>>(rec, n, g->nx, g->ny, ts, select, B->counts);
+  BP_LAUNCH_CHECK(ctx, "pair count");
+  if ((r = bp_scan_u32_to_i64_buf(ctx, B->counts, B->offs, n, B->bsum))) return r;
+  BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, B->offs + n, 8, cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  BP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const int64_t np = ctx->h_pinned[0];
+  if (np > B->max_pairs)
+    return bp_fail(ctx, BP_ERANGE, "paste (no allocation): %lld tile pairs exceed the limit %lld",
+                   (long long)np, (long long)B->max_pairs);
+  if (np == 0) return BP_OK;
+  k_pair_emit<<<nb, 256, 0, ctx->stream>>>(rec, n, g->nx, g->ny, ts, select, ntx, B->offs,
+                                           B->keys0, B->vals0);
+  BP_LAUNCH_CHECK(ctx, "pair emit");
+  int key_bits = 0;
+  while (((int64_t)1 << key_bits) < n_tiles) ++key_bits;
+  uint32_t *ks, *vs;
+  if ((r = bp_radix_sort_pairs_buf(ctx, B->keys0, B->vals0, B->keys1, B->vals1, np, key_bits,
+                                   B->hist, B->hoffs, B->bsum, &ks, &vs)))
+    return r;
+  if (ts == 64)
+    return deposit_buffers<64>(ctx, assigned, g, ks, vs, np, n_tiles, ymap, bmap, ylo, blo, B);
+  return deposit_buffers<32>(ctx, assigned, g, ks, vs, np, n_tiles, ymap, bmap, ylo, blo, B);
+}
 
 extern "C" {
 

@@ -237,3 +237,54 @@ int bp_tile_ranges(bp_ctx* ctx, const uint32_t* keys, int64_t n, int64_t n_tiles
   BP_LAUNCH_CHECK(ctx, "tile ranges");
   return BP_OK;
 }
+
+// ---------------------------------------------------------------- caller-buffer variants
+// Same kernels as above with every scratch buffer supplied by the caller (no bp_ws).
+// bsum: >= (n / 8192 + 2) int64.
+int bp_scan_u32_to_i64_buf(bp_ctx* ctx, const uint32_t* in, int64_t* out, int64_t n,
+                           int64_t* bsum) {
+  int64_t nb = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
+  if (nb == 0) nb = 1;
+  k_scan_reduce<<<(unsigned)nb, SCAN_THREADS, 0, ctx->stream>>>(in, n, bsum);
+  BP_LAUNCH_CHECK(ctx, "scan reduce");
+  k_scan_bsums<<<1, SCAN_THREADS, 0, ctx->stream>>>(bsum, nb);
+  BP_LAUNCH_CHECK(ctx, "scan block sums");
+  k_scan_down<<<(unsigned)nb, SCAN_THREADS, 0, ctx->stream>>>(in, n, bsum, out);
+  BP_LAUNCH_CHECK(ctx, "scan down");
+  BP_CUDA(ctx, cudaMemcpyAsync(out + n, bsum + nb, sizeof(int64_t), cudaMemcpyDeviceToDevice,
+                               ctx->stream));
+  return BP_OK;
+}
+
+// hist: >= 256 * ceil(n / 4096) u32; offs: one more int64 than hist entries; bsum as above
+int bp_radix_sort_pairs_buf(bp_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
+                            uint32_t* vals_tmp, int64_t n, int key_bits, uint32_t* hist,
+                            int64_t* offs, int64_t* bsum, uint32_t** keys_out,
+                            uint32_t** vals_out) {
+  *keys_out = keys;
+  *vals_out = vals;
+  if (n <= 1 || key_bits <= 0) return BP_OK;
+  int64_t nblocks = (n + RS_ITEMS - 1) / RS_ITEMS;
+  int npass = (key_bits + 7) / 8;
+  int bits_per = (key_bits + npass - 1) / npass;
+  uint32_t *ki = keys, *vi = vals, *ko = keys_tmp, *vo = vals_tmp;
+  int shift = 0, r;
+  for (int p = 0; p < npass; ++p) {
+    int nb = (shift + bits_per <= key_bits) ? bits_per : key_bits - shift;
+    int64_t hn = ((int64_t)1 << nb) * nblocks;
+    k_rs_hist<<<(unsigned)nblocks, RS_THREADS, 0, ctx->stream>>>(ki, n, shift, nb, hist,
+                                                                 nblocks);
+    BP_LAUNCH_CHECK(ctx, "radix hist");
+    if ((r = bp_scan_u32_to_i64_buf(ctx, hist, offs, hn, bsum))) return r;
+    k_rs_scatter<<<(unsigned)nblocks, RS_THREADS, 0, ctx->stream>>>(ki, vi, ko, vo, n, shift, nb,
+                                                                    offs, nblocks);
+    BP_LAUNCH_CHECK(ctx, "radix scatter");
+    uint32_t* t;
+    t = ki; ki = ko; ko = t;
+    t = vi; vi = vo; vo = t;
+    shift += nb;
+  }
+  *keys_out = ki;
+  *vals_out = vi;
+  return BP_OK;
+}
