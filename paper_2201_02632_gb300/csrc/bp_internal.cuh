@@ -154,6 +154,24 @@ __device__ __forceinline__ float bp_wsplit(float dx, float h) {
   return dx < 0.0f ? wl : -wl;
 }
 
+// The same with the reciprocal of h supplied (one multiplication instead of a
+// division per edge).
+__device__ __forceinline__ float bp_wsplit_inv(float dx, float inv_h) {
+  float u = -fabsf(dx * inv_h);  // u <= 0
+  float wl;
+  if (u <= -1.0f) {
+    wl = 0.0f;
+  } else if (u <= -0.5f) {
+    float t = 1.0f + u;
+    float t2 = t * t;
+    wl = (2.0f / 3.0f) * t2 * t2;
+  } else {
+    float u2 = u * u;
+    wl = 0.5f + u * ((4.0f / 3.0f) + u2 * (-(8.0f / 3.0f) - 2.0f * u));
+  }
+  return dx < 0.0f ? wl : -wl;
+}
+
 // Pixel span of a particle at px = ix + fx with kernel radius h, decided in FP32
 // (round-to-nearest, no contraction) relative to ix: columns
 // ix + floor(fx - h) .. ix + floor(fx + h), clipped to [0, n-1].  A negative or NaN

@@ -238,29 +238,31 @@ __global__ void k_unit_emit(const int64_t* __restrict__ tstart, int64_t n_tiles,
 
 // ---------------------------------------------------------------- deposit
 constexpr int DEP_THREADS = 256;
-constexpr int CH = 32;  // particles per chunk
+constexpr int CH = 32;          // particles per chunk
+constexpr int SEG = 16;         // cells per weight segment
+constexpr int FOLD_CHUNKS = 4;  // chunks accumulated in plain FP32 between compensated folds
 
 template <int TS>
 struct DepSmem {
   float a[CH][TS];    // column weights
   float by[CH][TS];   // Y * row weights
   float bb[CH][TS];   // B * row weights
-  float ex[CH][TS + 1];
-  float ey[CH][TS + 1];
   float lo_y[TS * TS];
   float lo_b[TS * TS];
   float4 p0[CH];      // fx, fy, hp, Y
   float p1[CH];       // B
+  float ih[CH];       // 1 / hp (0 when hp == 0)
   int2 pi[CH];        // ix - x0, iy - y0 (pixel index relative to the tile origin)
   int4 box[CH];       // footprint in tile coordinates i0, i1, j0, j1 (i0 > i1: none)
+  uint32_t wmask[CH]; // warps whose pixel band meets the footprint
   int hasy[CH];
   int64_t unit;
 };
 
 template <int TS>
-__device__ __forceinline__ void fold_chunk(float (&acc)[TS / 16][TS / 16],
-                                           float (&hi)[TS / 16][TS / 16], float* lo, int r0,
-                                           int c0) {
+__device__ __forceinline__ void fold_acc(float (&acc)[TS / 16][TS / 16],
+                                         float (&hi)[TS / 16][TS / 16], float* lo, int r0,
+                                         int c0) {
   constexpr int PR = TS / 16;
 #pragma unroll
   for (int r = 0; r < PR; ++r)
@@ -274,6 +276,29 @@ __device__ __forceinline__ void fold_chunk(float (&acc)[TS / 16][TS / 16],
     }
 }
 
+// Weights of SEG consecutive cells of one axis: cell k (relative to the particle's
+// pixel index) spans [k - f, k + 1 - f] in pixel units around the centre.  The edge
+// values use the split form of w (bp_wsplit), the cell holding the centre adds 1.
+__device__ __forceinline__ void segment_weights(int kbase, float f, float h, float ih,
+                                                float (&w)[SEG]) {
+  if (h > 0.f) {
+    float d = __fsub_rn((float)kbase, f);
+    float prev = bp_wsplit_inv(d, ih);
+#pragma unroll
+    for (int j = 0; j < SEG; ++j) {
+      int k = kbase + j;
+      float dn = __fsub_rn((float)(k + 1), f);
+      float cur = bp_wsplit_inv(dn, ih);
+      bool centre = (k == 0 && f > 0.f) || (k == -1 && f == 0.f);
+      w[j] = cur - prev + (centre ? 1.f : 0.f);
+      prev = cur;
+    }
+  } else {  // h = 0: nearest grid point
+#pragma unroll
+    for (int j = 0; j < SEG; ++j) w[j] = (kbase + j == 0) ? 1.f : 0.f;
+  }
+}
+
 template <int TS>
 __global__ void __launch_bounds__(DEP_THREADS, 2)
     k_deposit(const float4* __restrict__ rec, const uint32_t* __restrict__ pvals,
@@ -281,6 +306,7 @@ __global__ void __launch_bounds__(DEP_THREADS, 2)
               int64_t* counter, int nx, int ny, int ntx, float* ymap, float* bmap, float* ylo,
               float* blo, float* partials) {
   constexpr int PR = TS / 16;  // pixels per thread along each axis
+  constexpr int NSEG = TS / SEG;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DepSmem<TS>& S = *reinterpret_cast<DepSmem<TS>*>(smem_raw);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -305,75 +331,78 @@ __global__ void __launch_bounds__(DEP_THREADS, 2)
     for (int r = 0; r < PR; ++r)
 #pragma unroll
       for (int c = 0; c < PR; ++c) acc_y[r][c] = acc_b[r][c] = hi_y[r][c] = hi_b[r][c] = 0.f;
+    int chunks = 0;
     for (int64_t cb = U.begin; cb < U.end; cb += CH) {
       const int nch = (int)min((int64_t)CH, U.end - cb);
       __syncthreads();  // previous chunk fully consumed
-      // 1. gather particle records and footprints
+      // 1. gather particle records, footprints and warp masks
       if (tid < nch) {
         uint32_t pi = pvals[cb + tid];
         float4 q0 = rec[2 * (int64_t)pi];
         float4 q1 = rec[2 * (int64_t)pi + 1];
         S.p0[tid] = q0;
         S.p1[tid] = q1.x;
+        S.ih[tid] = q0.z > 0.f ? 1.0f / q0.z : 0.f;
         const int ixp = __float_as_int(q1.z), iyp = __float_as_int(q1.w);
         S.pi[tid] = make_int2(ixp - x0, iyp - y0);
         int i0, i1, j0, j1;
         int4 bx = make_int4(1, 0, 1, 0);
+        uint32_t m = 0;
         if (bp_span(ixp, q0.x, q0.z, nx, i0, i1) && bp_span(iyp, q0.y, q0.z, ny, j0, j1)) {
           bx.x = max(i0 - x0, 0);
           bx.y = min(i1 - x0, TS - 1);
           bx.z = max(j0 - y0, 0);
           bx.w = min(j1 - y0, TS - 1);
+#pragma unroll
+          for (int ww = 0; ww < DEP_THREADS / 32; ++ww) {
+            int a0 = (ww & 1) * 8 * PR, b0 = (ww >> 1) * 4 * PR;
+            bool hit = !(bx.y < a0 || bx.x > a0 + 8 * PR - 1 || bx.w < b0 ||
+                         bx.z > b0 + 4 * PR - 1);
+            m |= hit ? (1u << ww) : 0u;
+          }
         }
         S.box[tid] = bx;
+        S.wmask[tid] = m;
         S.hasy[tid] = q0.w != 0.f;
       }
       __syncthreads();
-      // 2. split-kernel values at the TS+1 pixel edges of both axes
-      for (int q = tid; q < nch * (TS + 1); q += DEP_THREADS) {
-        int k = q / (TS + 1), e = q % (TS + 1);
-        float4 p = S.p0[k];
-        int2 ip = S.pi[k];
-        // edge minus centre: the integer part is exact, one rounding for the fraction
-        float dx = __fsub_rn((float)(e - ip.x), p.x), dy = __fsub_rn((float)(e - ip.y), p.y);
-        if (p.z > 0.f) {
-          S.ex[k][e] = bp_wsplit(dx, p.z);
-          S.ey[k][e] = bp_wsplit(dy, p.z);
-        } else {  // unused by the nearest-grid-point weights
-          S.ex[k][e] = 0.f;
-          S.ey[k][e] = 0.f;
+      // 2. weights: one thread per (particle, axis, 16-cell segment)
+      for (int q = tid; q < nch * 2 * NSEG; q += DEP_THREADS) {
+        const int k = q / (2 * NSEG), axis = (q / NSEG) & 1, sg = q % NSEG;
+        const int cb0 = sg * SEG;
+        const float4 p = S.p0[k];
+        const int4 bx = S.box[k];
+        const int lo = axis ? bx.z : bx.x, hi = axis ? bx.w : bx.y;
+        float wv[SEG];
+        if (hi < cb0 || lo > cb0 + SEG - 1) {
+#pragma unroll
+          for (int j = 0; j < SEG; ++j) wv[j] = 0.f;
+        } else {
+          const int2 ip = S.pi[k];
+          segment_weights(cb0 - (axis ? ip.y : ip.x), axis ? p.y : p.x, p.z, S.ih[k], wv);
+        }
+        if (axis == 0) {
+          float4* dst = reinterpret_cast<float4*>(&S.a[k][cb0]);
+#pragma unroll
+          for (int j = 0; j < SEG / 4; ++j)
+            dst[j] = make_float4(wv[4 * j], wv[4 * j + 1], wv[4 * j + 2], wv[4 * j + 3]);
+        } else {
+          const float Yk = p.w, Bk = S.p1[k];
+          float4* dy = reinterpret_cast<float4*>(&S.by[k][cb0]);
+          float4* db = reinterpret_cast<float4*>(&S.bb[k][cb0]);
+#pragma unroll
+          for (int j = 0; j < SEG / 4; ++j) {
+            dy[j] = make_float4(Yk * wv[4 * j], Yk * wv[4 * j + 1], Yk * wv[4 * j + 2],
+                                Yk * wv[4 * j + 3]);
+            db[j] = make_float4(Bk * wv[4 * j], Bk * wv[4 * j + 1], Bk * wv[4 * j + 2],
+                                Bk * wv[4 * j + 3]);
+          }
         }
       }
       __syncthreads();
-      // 3. pixel weights (difference of edge values, +1 in the cell holding the centre)
-      for (int q = tid; q < nch * TS; q += DEP_THREADS) {
-        int k = q / TS, e = q % TS;
-        float4 p = S.p0[k];
-        int2 ip = S.pi[k];
-        // cell e spans [e - ix', e + 1 - ix'] relative to px; it holds the centre when
-        // e - ix' < fx <= e + 1 - ix'
-        int kx = e - ip.x, ky = e - ip.y;
-        bool cx = (kx == 0 && p.x > 0.f) || (kx == -1 && p.x == 0.f);
-        bool cy = (ky == 0 && p.y > 0.f) || (ky == -1 && p.y == 0.f);
-        float ax, ay;
-        if (p.z > 0.f) {
-          ax = S.ex[k][e + 1] - S.ex[k][e] + (cx ? 1.f : 0.f);
-          ay = S.ey[k][e + 1] - S.ey[k][e] + (cy ? 1.f : 0.f);
-        } else {  // h = 0: nearest grid point, the cell with e <= px < e + 1
-          ax = (kx == 0) ? 1.f : 0.f;
-          ay = (ky == 0) ? 1.f : 0.f;
-        }
-        S.a[k][e] = ax;
-        S.by[k][e] = p.w * ay;
-        S.bb[k][e] = S.p1[k] * ay;
-      }
-      __syncthreads();
-      // 4. rank-1 updates of this thread's PR x PR pixels
+      // 3. rank-1 updates of this thread's PR x PR pixels
       for (int k = 0; k < nch; ++k) {
-        int4 bx = S.box[k];
-        bool touch = !(bx.y < wc0 || bx.x > wc0 + 8 * PR - 1 || bx.w < wr0 ||
-                       bx.z > wr0 + 4 * PR - 1);
-        if (!touch) continue;  // warp-uniform skip
+        if (!((S.wmask[k] >> w) & 1u)) continue;  // warp-uniform skip
         float av[PR], bvb[PR];
 #pragma unroll
         for (int c = 0; c < PR; ++c) av[c] = S.a[k][c0 + c];
@@ -393,10 +422,15 @@ __global__ void __launch_bounds__(DEP_THREADS, 2)
             for (int c = 0; c < PR; ++c) acc_y[r][c] = fmaf(bvy[r], av[c], acc_y[r][c]);
         }
       }
-      fold_chunk<TS>(acc_y, hi_y, S.lo_y, r0, c0);
-      fold_chunk<TS>(acc_b, hi_b, S.lo_b, r0, c0);
+      if (++chunks == FOLD_CHUNKS) {
+        fold_acc<TS>(acc_y, hi_y, S.lo_y, r0, c0);
+        fold_acc<TS>(acc_b, hi_b, S.lo_b, r0, c0);
+        chunks = 0;
+      }
     }
-    // 5. write the tile: straight into the map, or as a partial tile
+    fold_acc<TS>(acc_y, hi_y, S.lo_y, r0, c0);
+    fold_acc<TS>(acc_b, hi_b, S.lo_b, r0, c0);
+    // 4. write the tile: straight into the map, or as a partial tile
     if (U.slot < 0) {
 #pragma unroll
       for (int r = 0; r < PR; ++r)
