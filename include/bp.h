@@ -112,6 +112,7 @@ enum {
 #define BP_HALO_THETA 3      /* theta(r_f) <= 0 */
 #define BP_HALO_MAXIT 4      /* Newton iteration limit reached */
 #define BP_HALO_BADINPUT 5   /* M, c or z not finite / out of range */
+#define BP_HALO_FALLBACK 6   /* (internal) rejected by the residual gate, awaiting the full solve */
 
 /* particle record written by bp_assign_particles: BP_ASSIGNED_STRIDE 32-bit words
  * per particle (32 bytes, 16-byte aligned).  The pixel-unit position measured from
@@ -173,7 +174,8 @@ int64_t bp_workspace_bytes(const bp_ctx* ctx);
 #define BP_PH_HP_PAIRS 7  /* HP (halo, tile) list and sort */
 #define BP_PH_HP_PASTE 8  /* HP paste and reduction */
 #define BP_PH_FINALIZE 9
-#define BP_NPHASES 10
+#define BP_PH_SURROGATE 10 /* surrogate features + BF16 inference */
+#define BP_NPHASES 11
 int bp_set_timing(bp_ctx* ctx, int on);
 int bp_phase_times(bp_ctx* ctx, double* ms, int n);
 /* Number of kernels this context has launched since it was created. */
@@ -188,6 +190,75 @@ int64_t bp_kernel_launches(const bp_ctx* ctx);
  * counter: the call synchronises the stream).  Halos are independent. */
 int bp_solve_halos(bp_ctx* ctx, int64_t n, const double* Mvir, const double* c, const double* z,
                    double* model, int32_t* status, int mode, double resid_tol);
+
+/* bp_solve_halos with options (used to generate surrogate training data and by the
+ * surrogate path):
+ *   params [3 * n] FP64 or NULL: per-halo eps_*, f_*, eps_DM (layout [3][n]); NULL uses
+ *     the context's Table-1 values;
+ *   guess  [2 * n] FP64 or NULL: starting point ln(r_f / r_vir), ln(T r_vir / (G M_vir))
+ *     per halo (layout [2][n]); non-finite entries use the default start;
+ *   max_iter: outer Newton iterations (<= 0: 80);
+ *   gate > 0 (with guess): a halo not converged to resid_tol within max_iter iterations
+ *     is accepted if both normalised residuals are <= gate; otherwise it is solved again
+ *     from the default start with the full iteration budget (the fallback).
+ * The number of halos sent to the fallback is returned by bp_last_fallback_count.
+ * Synchronises (one or two counter reads). */
+int bp_solve_halos_ex(bp_ctx* ctx, int64_t n, const double* Mvir, const double* c,
+                      const double* z, const double* params, const double* guess, int max_iter,
+                      double gate, double* model, int32_t* status, int mode, double resid_tol);
+int64_t bp_last_fallback_count(const bp_ctx* ctx);
+
+/* ---- MLP surrogate of the solve (not in the paper).
+ * Network 6 -> 128 -> 128 -> 128 -> 3, GELU (exact erf form) on the hidden layers.
+ * Features (normalised as (f - mean) / scale with `norm`): log10 M [h^-1 Msun],
+ * log10 c, z, eps_*, f_*, eps_DM.  Targets: ln(r_f / r_vir), ln(T r_vir / (G M_vir)),
+ * ln(rho0 / rho_s), normalised the same way.  norm: FP32 [18] on the device, means of the
+ * 6 features and 3 targets followed by their scales.
+ * FP32 parameters (BP_MLP_NPARAMS floats, this order): W1 [128][6], b1 [128],
+ * W2 [128][128], b2, W3 [128][128], b3, W4 [3][128], b4 [3]; W[o][i] multiplies input i
+ * into output o.  BF16 weights (BP_MLP_NWEIGHTS): W1, W2, W3, W4 in the same order.
+ * cache: FP32 [n][BP_MLP_CACHE_PER_ROW] = Z1, A1, Z2, A2, Z3, A3 per row (pre-activations
+ * and activations of the hidden layers), written by forward, read by backward. */
+#define BP_MLP_IN 6
+#define BP_MLP_HID 128
+#define BP_MLP_OUT 3
+#define BP_MLP_NPARAMS (128 * 6 + 128 + 2 * (128 * 128 + 128) + 3 * 128 + 3)
+#define BP_MLP_NWEIGHTS (128 * 6 + 2 * 128 * 128 + 3 * 128)
+#define BP_MLP_CACHE_PER_ROW (6 * 128)
+/* FP32 forward of n rows: x [n][6] -> y [n][3]. */
+int bp_mlp_forward(bp_ctx* ctx, int64_t n, const float* params, const float* x, float* y,
+                   float* cache);
+/* Gradient of sum(dy * y) with respect to the parameters (grad overwritten, FP32,
+ * parameter layout); deterministic (fixed-order reductions). */
+int bp_mlp_backward(bp_ctx* ctx, int64_t n, const float* params, const float* x,
+                    const float* cache, const float* dy, float* grad);
+/* One Adam step (bias-corrected with `step` >= 1) on params with moment buffers m, v. */
+int bp_mlp_adam(bp_ctx* ctx, float* params, const float* grad, float* m, float* v, int64_t step,
+                double lr, double beta1, double beta2, double eps);
+/* BF16 copy of the weights (round to nearest even). */
+int bp_mlp_to_bf16(bp_ctx* ctx, const float* params, uint16_t* weights_bf16);
+/* BF16 inference (BF16 weights and activations, FP32 accumulation, FP32 biases from
+ * params): x [n][6] -> y [n][3]. */
+int bp_mlp_infer_bf16(bp_ctx* ctx, int64_t n, const uint16_t* weights_bf16, const float* params,
+                      const float* x, float* y);
+/* Normalised features of n halos (params [3][n] per-halo eps_*, f_*, eps_DM or NULL for the
+ * Table-1 values).  Synchronises. */
+int bp_mlp_features(bp_ctx* ctx, int64_t n, const double* Mvir, const double* c, const double* z,
+                    const double* params, const float* norm, float* x);
+/* Normalised targets of n solved halos (model from bp_solve_halos*). */
+int bp_mlp_targets(bp_ctx* ctx, int64_t n, const double* model, const float* norm, float* t);
+/* Mean squared error of y [n][3] against t; dy = 2 (y - t) / (3 n).  loss (host pointer,
+ * may be NULL) receives the mean squared error (synchronises when given). */
+int bp_mlp_mse(bp_ctx* ctx, int64_t n, const float* y, const float* t, float* dy, double* loss);
+/* Surrogate solve: BF16 MLP prediction of (r_f, T) as the starting point of polish_iter
+ * FP64 Newton iterations (bp_solve_halos_ex with that guess and gate); halos whose
+ * normalised features fall outside hull (FP32 [12]: 6 minima then 6 maxima) or whose
+ * residual after the polish exceeds gate get the full solve.  Output as bp_solve_halos. */
+int bp_solve_halos_surrogate(bp_ctx* ctx, int64_t n, const double* Mvir, const double* c,
+                             const double* z, const double* params, const uint16_t* weights_bf16,
+                             const float* mlp_params, const float* norm, const float* hull,
+                             int polish_iter, double gate, double* model, int32_t* status,
+                             double resid_tol);
 
 /* Section 3.4: per-particle signals.
  *   x,y,z [n] FP32 comoving h^-1 Mpc; vx,vy,vz [n] FP32 km/s (peculiar);

@@ -27,9 +27,16 @@ OUT_YB, OUT_DT = 0, 1
 EXPORTS = ("bp_create", "bp_destroy", "bp_last_error", "bp_set_stream", "bp_set_tiling",
            "bp_workspace_bytes", "bp_set_timing", "bp_phase_times", "bp_kernel_launches",
            "bp_solve_halos", "bp_assign_particles", "bp_paste_particles", "bp_pp_pairs",
-           "bp_paste_halos", "bp_finalize_map", "bp_paste_particles_noalloc")
+           "bp_paste_halos", "bp_finalize_map", "bp_paste_particles_noalloc",
+           "bp_solve_halos_ex", "bp_last_fallback_count", "bp_mlp_forward", "bp_mlp_backward",
+           "bp_mlp_adam", "bp_mlp_to_bf16", "bp_mlp_infer_bf16", "bp_mlp_features",
+           "bp_mlp_targets", "bp_mlp_mse", "bp_solve_halos_surrogate")
+MLP_IN, MLP_HID, MLP_OUT = 6, 128, 3
+MLP_NPARAMS = 128 * 6 + 128 + 2 * (128 * 128 + 128) + 3 * 128 + 3
+MLP_NWEIGHTS = 128 * 6 + 2 * 128 * 128 + 3 * 128
+MLP_CACHE_PER_ROW = 6 * 128
 PHASES = ("solve", "assign", "pairs", "sort", "deposit", "reduce", "hp_table", "hp_pairs",
-          "hp_paste", "finalize")
+          "hp_paste", "finalize", "surrogate")
 
 
 class BpCosmology(C.Structure):
@@ -73,6 +80,18 @@ def load():
                 "bp_phase_times": (i32, [P, C.POINTER(C.c_double), i32]),
                 "bp_kernel_launches": (i64, [P]),
                 "bp_solve_halos": (i32, [P, i64, P, P, P, P, P, i32, d]),
+                "bp_solve_halos_ex": (i32, [P, i64, P, P, P, P, P, i32, d, P, P, i32, d]),
+                "bp_last_fallback_count": (i64, [P]),
+                "bp_mlp_forward": (i32, [P, i64, P, P, P, P]),
+                "bp_mlp_backward": (i32, [P, i64, P, P, P, P, P]),
+                "bp_mlp_adam": (i32, [P, P, P, P, P, i64, d, d, d, d]),
+                "bp_mlp_to_bf16": (i32, [P, P, P]),
+                "bp_mlp_infer_bf16": (i32, [P, i64, P, P, P, P]),
+                "bp_mlp_features": (i32, [P, i64, P, P, P, P, P, P]),
+                "bp_mlp_targets": (i32, [P, i64, P, P, P]),
+                "bp_mlp_mse": (i32, [P, i64, P, P, P, C.POINTER(d)]),
+                "bp_solve_halos_surrogate": (i32, [P, i64, P, P, P, P, P, P, P, P, i32, d, P, P,
+                                                   d]),
                 "bp_assign_particles": (i32, [P, i64, P, P, P, P, P, P, P, P, d, i64, P, P, P,
                                               C.POINTER(BpGeom), P]),
                 "bp_paste_particles": (i32, [P, i64, P, C.POINTER(BpGeom), i32, P, P, P, P]),

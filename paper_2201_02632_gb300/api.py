@@ -123,6 +123,111 @@ class Context:
         self._check(rc, allow=() if raise_on_noconv else (L.BP_ENOCONV,))
         return model, status
 
+    def solve_halos_ex(self, M, c, z, params=None, guess=None, max_iter=0, gate=0.0, tol=1e-10,
+                       raise_on_noconv=True):
+        """bp_solve_halos_ex: per-halo (eps_*, f_*, eps_DM) as params [3, n] FP64, starting
+        point guess [2, n] FP64 (ln r_f/r_vir, ln T r_vir/GM), iteration cap and gate."""
+        n = M.numel()
+        f64 = torch.float64
+        model = torch.empty((len(MODEL_FIELDS), n), dtype=f64, device=M.device)
+        status = torch.empty(n, dtype=torch.int32, device=M.device)
+        rc = self._L.bp_solve_halos_ex(self._h, n, _ptr(M, f64, "M"), _ptr(c, f64, "c"),
+                                       _ptr(z, f64, "z"), _ptr(params, f64, "params"),
+                                       _ptr(guess, f64, "guess"), int(max_iter), float(gate),
+                                       _ptr(model, f64, "model"),
+                                       _ptr(status, torch.int32, "status"), 0, float(tol))
+        self._check(rc, allow=() if raise_on_noconv else (L.BP_ENOCONV,))
+        return model, status
+
+    def last_fallback_count(self) -> int:
+        return int(self._L.bp_last_fallback_count(self._h))
+
+    # ------------------------------------------------------------ MLP surrogate
+    def mlp_forward(self, params, x, cache=None):
+        n = x.shape[0]
+        f32 = torch.float32
+        y = torch.empty((n, L.MLP_OUT), dtype=f32, device=x.device)
+        if cache is None:
+            cache = torch.empty((n, L.MLP_CACHE_PER_ROW), dtype=f32, device=x.device)
+        self._check(self._L.bp_mlp_forward(self._h, n, _ptr(params, f32, "params"),
+                                           _ptr(x, f32, "x"), _ptr(y, f32, "y"),
+                                           _ptr(cache, f32, "cache")))
+        return y, cache
+
+    def mlp_backward(self, params, x, cache, dy, grad=None):
+        f32 = torch.float32
+        if grad is None:
+            grad = torch.empty(L.MLP_NPARAMS, dtype=f32, device=x.device)
+        self._check(self._L.bp_mlp_backward(self._h, x.shape[0], _ptr(params, f32, "params"),
+                                            _ptr(x, f32, "x"), _ptr(cache, f32, "cache"),
+                                            _ptr(dy, f32, "dy"), _ptr(grad, f32, "grad")))
+        return grad
+
+    def mlp_adam(self, params, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        f32 = torch.float32
+        self._check(self._L.bp_mlp_adam(self._h, _ptr(params, f32, "params"),
+                                        _ptr(grad, f32, "grad"), _ptr(m, f32, "m"),
+                                        _ptr(v, f32, "v"), int(step), float(lr), float(beta1),
+                                        float(beta2), float(eps)))
+
+    def mlp_to_bf16(self, params):
+        wb = torch.empty(L.MLP_NWEIGHTS, dtype=torch.int16, device=params.device)
+        self._check(self._L.bp_mlp_to_bf16(self._h, _ptr(params, torch.float32, "params"),
+                                           _ptr(wb, torch.int16, "wb")))
+        return wb
+
+    def mlp_infer_bf16(self, wb, params, x):
+        n = x.shape[0]
+        y = torch.empty((n, L.MLP_OUT), dtype=torch.float32, device=x.device)
+        self._check(self._L.bp_mlp_infer_bf16(self._h, n, _ptr(wb, torch.int16, "wb"),
+                                              _ptr(params, torch.float32, "params"),
+                                              _ptr(x, torch.float32, "x"),
+                                              _ptr(y, torch.float32, "y")))
+        return y
+
+    def mlp_features(self, M, c, z, params, norm):
+        n = M.numel()
+        f64 = torch.float64
+        x = torch.empty((n, L.MLP_IN), dtype=torch.float32, device=M.device)
+        self._check(self._L.bp_mlp_features(self._h, n, _ptr(M, f64, "M"), _ptr(c, f64, "c"),
+                                            _ptr(z, f64, "z"), _ptr(params, f64, "params"),
+                                            _ptr(norm, torch.float32, "norm"),
+                                            _ptr(x, torch.float32, "x")))
+        return x
+
+    def mlp_targets(self, model, norm):
+        n = model.shape[1]
+        t = torch.empty((n, L.MLP_OUT), dtype=torch.float32, device=model.device)
+        self._check(self._L.bp_mlp_targets(self._h, n, _ptr(model, torch.float64, "model"),
+                                           _ptr(norm, torch.float32, "norm"),
+                                           _ptr(t, torch.float32, "t")))
+        return t
+
+    def mlp_mse(self, y, t, dy=None, want_loss=True):
+        f32 = torch.float32
+        if dy is None:
+            dy = torch.empty_like(y)
+        loss = C.c_double(0.0)
+        self._check(self._L.bp_mlp_mse(self._h, y.shape[0], _ptr(y, f32, "y"), _ptr(t, f32, "t"),
+                                       _ptr(dy, f32, "dy"),
+                                       C.byref(loss) if want_loss else None))
+        return dy, (loss.value if want_loss else None)
+
+    def solve_halos_surrogate(self, M, c, z, params, wb, mlp_params, norm, hull, polish_iter=2,
+                              gate=1e-4, tol=1e-10, raise_on_noconv=True):
+        n = M.numel()
+        f64, f32 = torch.float64, torch.float32
+        model = torch.empty((len(MODEL_FIELDS), n), dtype=f64, device=M.device)
+        status = torch.empty(n, dtype=torch.int32, device=M.device)
+        rc = self._L.bp_solve_halos_surrogate(
+            self._h, n, _ptr(M, f64, "M"), _ptr(c, f64, "c"), _ptr(z, f64, "z"),
+            _ptr(params, f64, "params"), _ptr(wb, torch.int16, "wb"),
+            _ptr(mlp_params, f32, "mlp_params"), _ptr(norm, f32, "norm"), _ptr(hull, f32, "hull"),
+            int(polish_iter), float(gate), _ptr(model, f64, "model"),
+            _ptr(status, torch.int32, "status"), float(tol))
+        self._check(rc, allow=() if raise_on_noconv else (L.BP_ENOCONV,))
+        return model, status
+
     # ------------------------------------------------------------ Section 3.4
     def assign_particles(self, parts: dict, Mp: float, halo_pos, model, status, g: L.BpGeom,
                          out=None):

@@ -301,6 +301,8 @@ int bp_phase_times(bp_ctx* ctx, double* ms, int n) {
 
 int64_t bp_kernel_launches(const bp_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
+int64_t bp_last_fallback_count(const bp_ctx* ctx) { return ctx ? ctx->last_fallback : 0; }
+
 int64_t bp_workspace_bytes(const bp_ctx* ctx) {
   if (!ctx) return 0;
   int64_t s = 0;

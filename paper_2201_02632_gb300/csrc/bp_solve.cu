@@ -269,15 +269,31 @@ struct Eval {
   int ok;
 };
 
+// Optional inputs of the solve: per-halo model parameters, a starting point and a
+// residual gate (used by the surrogate path).
+struct SolveExtra {
+  const double* prm;    // [3][n]: eps_*, f_*, eps_DM per halo, or null (context values)
+  const double* guess;  // [2][n]: ln(r_f / r_vir), ln(T r_vir / (G M)), or null
+  int max_outer;        // outer Newton iterations
+  double gate;          // > 0: halos not converged after max_outer iterations are
+                        //   accepted if both residuals <= gate, else flagged FALLBACK
+  int only_fallback;    // 1: solve only halos whose status is BP_HALO_FALLBACK
+};
+
 __global__ void __launch_bounds__(128) k_solve(BpParams P, BpTables TB, int64_t n,
                                                const double* __restrict__ Mh,
                                                const double* __restrict__ cc,
                                                const double* __restrict__ zz, double* model,
-                                               int32_t* status, double tol, int64_t* nbad) {
+                                               int32_t* status, double tol, int64_t* nbad,
+                                               SolveExtra X) {
   int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   int lane = threadIdx.x & 31;
   if (gw >= n) return;
   const int64_t i = gw;
+  if (X.only_fallback && status[i] != BP_HALO_FALLBACK) return;
+  const double eps_star = X.prm ? X.prm[i] : P.eps_star;
+  const double f_star = X.prm ? X.prm[n + i] : P.f_star;
+  const double eps_dm = X.prm ? X.prm[2 * n + i] : P.eps_dm;
   double Min = Mh[i], c = cc[i], z = zz[i];
   auto put = [&](int f, double v) {
     if (lane == 0) model[(int64_t)f * n + i] = v;
@@ -327,7 +343,7 @@ __global__ void __launch_bounds__(128) k_solve(BpParams P, BpTables TB, int64_t 
     h.r500 = x * h.rs;
     h.M500 = 4.0 * bpc::PI / 3.0 * 500.0 * rho_cr * h.r500 * h.r500 * h.r500;
   }
-  h.Mstar = P.f_star * pow(h.M500 / 3e14, -P.S_star) * h.M;
+  h.Mstar = f_star * pow(h.M500 / 3e14, -P.S_star) * h.M;
   double f_max = pow(4.0, -P.n_nt) / P.alpha_nt;
   double fz = fmin(pow(1.0 + z, P.beta_nt), (f_max - 1.0) * tanh(P.beta_nt * z) + 1.0);
   h.ant = P.alpha_nt * fz;
@@ -379,7 +395,7 @@ __global__ void __launch_bounds__(128) k_solve(BpParams P, BpTables TB, int64_t 
   Solver S(h, nn);
   S.cache_region_a(lane);
   const double fbM = P.fb * h.M;
-  const double inj = P.eps_dm * fabs(h.Edm) + P.eps_star * h.Mstar * bpc::C_KMS * bpc::C_KMS;
+  const double inj = eps_dm * fabs(h.Edm) + eps_star * h.Mstar * bpc::C_KMS * bpc::C_KMS;
   const double absE = fabs(h.Egi);
   const double r3v = h.rvir * h.rvir * h.rvir;
   const double four_pi = 4.0 * bpc::PI;
@@ -393,7 +409,8 @@ __global__ void __launch_bounds__(128) k_solve(BpParams P, BpTables TB, int64_t 
     double psi = phif - h.phi0;  // > 0
     double Tmin = psi / (nn + 1.0);
     double lnTarget = log(fbM - h.Mstar);
-    double s = (T0 > Tmin * (1 + 1e-9)) ? log(T0 - Tmin) : log(Tmin + 0.5 * h.GM / h.rvir);
+    double s = (T0 > Tmin * (1 + 1e-9) && isfinite(T0)) ? log(T0 - Tmin)
+                                                        : log(Tmin + 0.5 * h.GM / h.rvir);
     double slo = -INFINITY, shi = INFINITY;
     double T = 0, thf = 0, rho0 = 0, F = 1;
     Sums sm;
@@ -455,16 +472,23 @@ __global__ void __launch_bounds__(128) k_solve(BpParams P, BpTables TB, int64_t 
   // the bracket.  The direction of R_e(r_f) is not assumed.
   const double vmin = log(0.5 * h.rvir), vmax = log(10.0 * h.rvir);
   double v = log(1.1 * h.rvir);
+  double Tw = 0.0;
+  if (X.guess) {
+    double g0 = X.guess[i], g1 = X.guess[n + i];
+    if (isfinite(g0) && isfinite(g1)) {
+      v = fmin(fmax(log(h.rvir) + g0, vmin + 1e-9), vmax - 1e-9);
+      Tw = exp(g1) * h.GM / h.rvir;
+    }
+  }
   double va = 0, vb = 0, Ra = 0;  // bracket [va, vb] with R(va) R(vb) < 0
   bool have_br = false;
   double vprev = 0, Rprev = 0;
   bool have_prev = false;
   int hits_min = 0, hits_max = 0;
-  double Tw = 0.0;
   int st = BP_HALO_MAXIT;
   Eval e;
   double rf = exp(v);
-  for (int it = 0; it < 80; ++it) {
+  for (int it = 0; it < X.max_outer; ++it) {
     rf = exp(v);
     e = reduced(rf, Tw);
     if (!e.ok) { st = BP_HALO_MAXIT; break; }
@@ -492,6 +516,10 @@ __global__ void __launch_bounds__(128) k_solve(BpParams P, BpTables TB, int64_t 
     vprev = v; Rprev = e.Re; have_prev = true;
     v = vn;
   }
+  if (X.gate > 0 && st != BP_HALO_OK) {
+    bool pass = e.ok && fabs(e.Re) <= X.gate && fabs(e.Rm) <= X.gate;
+    st = pass ? BP_HALO_OK : BP_HALO_FALLBACK;
+  }
   if (e.ok && e.thf <= 0.0) st = BP_HALO_THETA;
   put(BP_M_T, e.ok ? e.T : 0.0);
   put(BP_M_RHO0, e.ok ? e.rho0 : 0.0);
@@ -504,30 +532,71 @@ __global__ void __launch_bounds__(128) k_solve(BpParams P, BpTables TB, int64_t 
 
 }  // namespace
 
-extern "C" int bp_solve_halos(bp_ctx* ctx, int64_t n, const double* Mvir, const double* c,
-                              const double* z, double* model, int32_t* status, int mode,
-                              double resid_tol) {
-  if (!ctx) return BP_EINVAL;
-  if (n < 0) return bp_fail(ctx, BP_EINVAL, "bp_solve_halos: n < 0");
-  if (n == 0) return BP_OK;
-  if (!Mvir || !c || !z || !model || !status)
-    return bp_fail(ctx, BP_EINVAL, "bp_solve_halos: null pointer");
-  if (mode != BP_SOLVE_FP64) return bp_fail(ctx, BP_EINVAL, "bp_solve_halos: unknown mode");
+static int solve_launch(bp_ctx* ctx, int64_t n, const double* Mvir, const double* c,
+                        const double* z, double* model, int32_t* status, double tol,
+                        SolveExtra X, int64_t* n_bad) {
   int r = upload_constants(ctx);
   if (r) return r;
-  double tol = resid_tol > 0 ? resid_tol : 1e-10;
   BP_CUDA(ctx, cudaMemsetAsync(ctx->d_counter, 0, sizeof(int64_t), ctx->stream));
   const int threads = 128;  // 4 halos per block
   int64_t blocks = (n * 32 + threads - 1) / threads;
   bp_phase_begin(ctx, BP_PH_SOLVE);
   k_solve<<<(unsigned)blocks, threads, 0, ctx->stream>>>(ctx->p, ctx->t, n, Mvir, c, z, model,
-                                                        status, tol, ctx->d_counter);
+                                                        status, tol, ctx->d_counter, X);
   BP_LAUNCH_CHECK(ctx, "k_solve launch");
   bp_phase_end(ctx, BP_PH_SOLVE);
   BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, ctx->d_counter, sizeof(int64_t),
                                cudaMemcpyDeviceToHost, ctx->stream));
   BP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  int64_t bad = ctx->h_pinned[0];
+  *n_bad = ctx->h_pinned[0];
+  return BP_OK;
+}
+
+static int solve_args(bp_ctx* ctx, int64_t n, const double* Mvir, const double* c,
+                      const double* z, double* model, int32_t* status, int mode) {
+  if (n < 0) return bp_fail(ctx, BP_EINVAL, "bp_solve_halos: n < 0");
+  if (n > 0 && (!Mvir || !c || !z || !model || !status))
+    return bp_fail(ctx, BP_EINVAL, "bp_solve_halos: null pointer");
+  if (mode != BP_SOLVE_FP64) return bp_fail(ctx, BP_EINVAL, "bp_solve_halos: unknown mode");
+  return BP_OK;
+}
+
+extern "C" int bp_solve_halos(bp_ctx* ctx, int64_t n, const double* Mvir, const double* c,
+                              const double* z, double* model, int32_t* status, int mode,
+                              double resid_tol) {
+  return bp_solve_halos_ex(ctx, n, Mvir, c, z, nullptr, nullptr, 0, 0.0, model, status, mode,
+                           resid_tol);
+}
+
+extern "C" int bp_solve_halos_ex(bp_ctx* ctx, int64_t n, const double* Mvir, const double* c,
+                                 const double* z, const double* params, const double* guess,
+                                 int max_iter, double gate, double* model, int32_t* status,
+                                 int mode, double resid_tol) {
+  if (!ctx) return BP_EINVAL;
+  int r = solve_args(ctx, n, Mvir, c, z, model, status, mode);
+  if (r) return r;
+  if (n == 0) return BP_OK;
+  if (gate < 0) return bp_fail(ctx, BP_EINVAL, "bp_solve_halos_ex: gate < 0");
+  SolveExtra X;
+  X.prm = params;
+  X.guess = guess;
+  X.max_outer = max_iter > 0 ? max_iter : 80;
+  X.gate = gate;
+  X.only_fallback = 0;
+  int64_t bad = 0;
+  double tol = resid_tol > 0 ? resid_tol : 1e-10;
+  if ((r = solve_launch(ctx, n, Mvir, c, z, model, status, tol, X, &bad))) return r;
+  if (bad && gate > 0 && guess) {
+    // the fallback: a full solve of the halos the gate rejected
+    X.guess = nullptr;
+    X.max_outer = 80;
+    X.gate = 0.0;
+    X.only_fallback = 1;
+    ctx->last_fallback = bad;
+    if ((r = solve_launch(ctx, n, Mvir, c, z, model, status, tol, X, &bad))) return r;
+  } else {
+    ctx->last_fallback = 0;
+  }
   if (bad) return bp_fail(ctx, BP_ENOCONV, "bp_solve_halos: %lld of %lld halos not converged",
                           (long long)bad, (long long)n);
   return BP_OK;

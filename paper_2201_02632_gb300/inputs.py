@@ -279,3 +279,28 @@ def deposit_inputs(px, py, hp, Y, B, kind):
     return {"ix": ix, "fx": fx, "iy": iy, "fy": fy, "px": px, "py": py,
             "hp": np.asarray(hp, np.float32), "Y": np.asarray(Y, np.float32),
             "B": np.asarray(B, np.float32), "kind": np.asarray(kind, np.int32)}
+
+
+# Ranges of the surrogate's inputs.  The paper quotes point values (Table 1) only; the
+# three parameters that enter the solve are varied over these ranges.
+SURROGATE_RANGES = {
+    "log10_M": (12.0, 15.3),
+    "dlog10_c": (-0.3, 0.3),      # around c = 5 (M/1e14)^-0.1
+    "z": (0.01, 3.0),
+    "eps_star": (0.0, 1.0e-5),
+    "f_star": (0.01, 0.04),
+    "eps_dm": (0.0, 0.1),
+}
+
+
+def surrogate_halos(n, seed=SEED_BASE + 4):
+    """Halo features for the surrogate: (M [h^-1 Msun], c, z, params [3, n] = eps_*, f_*,
+    eps_DM), uniform over SURROGATE_RANGES."""
+    rng = np.random.default_rng(seed)
+    R = SURROGATE_RANGES
+    M = 10.0 ** rng.uniform(*R["log10_M"], n)
+    c = 5.0 * (M / 1e14) ** -0.1 * 10.0 ** rng.uniform(*R["dlog10_c"], n)
+    z = rng.uniform(*R["z"], n)
+    prm = np.stack([rng.uniform(*R["eps_star"], n), rng.uniform(*R["f_star"], n),
+                    rng.uniform(*R["eps_dm"], n)])
+    return M, c, z, prm
