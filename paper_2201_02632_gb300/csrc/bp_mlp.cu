@@ -585,7 +585,7 @@ int bp_solve_halos_surrogate(bp_ctx* ctx, int64_t n, const double* Mvir, const d
   k_decode_guess<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, y, norm, outside, guess);
   BP_LAUNCH_CHECK(ctx, "decode guess");
   bp_phase_end(ctx, BP_PH_SURROGATE);
-  return bp_solve_halos_ex(ctx, n, Mvir, c, z, params, guess, polish_iter > 0 ? polish_iter : 2,
+  return bp_solve_halos_ex(ctx, n, Mvir, c, z, params, guess, polish_iter > 0 ? polish_iter : 4,
                            gate, model, status, BP_SOLVE_FP64, resid_tol);
 }
 

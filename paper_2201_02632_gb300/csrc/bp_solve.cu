@@ -11,6 +11,7 @@
 // condition is driven to zero by safeguarded Newton in ln r_f with the exact
 // derivative of the reduced problem.  The gas integrals over [0, r_f] are
 // composite 16-point Gauss-Legendre rules whose nodes are spread over the lanes.
+#include <algorithm>
 #include <vector>
 
 #include "bp_internal.cuh"
@@ -280,36 +281,25 @@ struct SolveExtra {
   int only_fallback;    // 1: solve only halos whose status is BP_HALO_FALLBACK
 };
 
-__global__ void __launch_bounds__(128) k_solve(BpParams P, BpTables TB, int64_t n,
-                                               const double* __restrict__ Mh,
-                                               const double* __restrict__ cc,
-                                               const double* __restrict__ zz, double* model,
-                                               int32_t* status, double tol, int64_t* nbad,
-                                               SolveExtra X) {
-  int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  int lane = threadIdx.x & 31;
-  if (gw >= n) return;
-  const int64_t i = gw;
-  if (X.only_fallback && status[i] != BP_HALO_FALLBACK) return;
-  const double eps_star = X.prm ? X.prm[i] : P.eps_star;
+// Closed-form and one-dimensional set-up of halo i, run by ONE thread.  Writes the
+// set-up fields of the model; returns false (status written) if the halo cannot be
+// solved.
+__device__ bool halo_setup(const BpParams& P, const BpTables& TB, int64_t n, int64_t i,
+                           const double* __restrict__ Mh, const double* __restrict__ cc,
+                           const double* __restrict__ zz, double* model, int32_t* status,
+                           int64_t* nbad, const SolveExtra& X, Halo& h) {
   const double f_star = X.prm ? X.prm[n + i] : P.f_star;
-  const double eps_dm = X.prm ? X.prm[2 * n + i] : P.eps_dm;
   double Min = Mh[i], c = cc[i], z = zz[i];
-  auto put = [&](int f, double v) {
-    if (lane == 0) model[(int64_t)f * n + i] = v;
-  };
+  auto put = [&](int f, double v) { model[(int64_t)f * n + i] = v; };
   auto finish = [&](int st) {
-    if (lane == 0) {
-      status[i] = st;
-      if (st != BP_HALO_OK) atomicAdd((unsigned long long*)nbad, 1ull);
-    }
+    status[i] = st;
+    if (st != BP_HALO_OK) atomicAdd((unsigned long long*)nbad, 1ull);
   };
   if (!(Min > 0 && isfinite(Min) && c > 0 && isfinite(c) && z >= 0 && z <= 10.0)) {
     for (int f = 0; f < BP_M_NFIELDS; ++f) put(f, 0.0);
     finish(BP_HALO_BADINPUT);
-    return;
+    return false;
   }
-  Halo h;
   h.M = Min / P.h;
   h.c = c;
   h.z = z;
@@ -366,7 +356,7 @@ __global__ void __launch_bounds__(128) k_solve(BpParams P, BpTables TB, int64_t 
                                  BP_M_RHO0,  BP_M_P0,  BP_M_RF,  BP_M_RESM, BP_M_RESE};
     for (int k = 0; k < 10; ++k) put(zero_fields[k], 0.0);
     finish(BP_HALO_BADSTAR);
-    return;
+    return false;
   }
   // r_*: f_b M(<r_*) = M_*  ->  m(x) = M_* m(c) / (f_b M)
   {
@@ -391,6 +381,48 @@ __global__ void __launch_bounds__(128) k_solve(BpParams P, BpTables TB, int64_t 
   put(BP_M_EDM, h.Edm);
   put(BP_M_PS, h.Ps);
 
+  return true;
+}
+
+constexpr int SOLVE_WARPS = 4;  // warps per block
+
+__global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve(
+    BpParams P, BpTables TB, int64_t n, const double* __restrict__ Mh,
+    const double* __restrict__ cc, const double* __restrict__ zz, double* model,
+    int32_t* status, double tol, int64_t* nbad, SolveExtra X, int hpw) {
+  __shared__ Halo sh_h[SOLVE_WARPS][32];
+  __shared__ int sh_ok[SOLVE_WARPS][32];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t base = ((int64_t)blockIdx.x * SOLVE_WARPS + w) * hpw;
+  if (base >= n) return;
+  // 1. set-up: lane j prepares halo base + j
+  {
+    const int64_t i = base + lane;
+    int ok = 0;
+    if (lane < hpw && i < n && (!X.only_fallback || status[i] == BP_HALO_FALLBACK)) {
+      Halo hs;
+      ok = halo_setup(P, TB, n, i, Mh, cc, zz, model, status, nbad, X, hs) ? 1 : 0;
+      if (ok) sh_h[w][lane] = hs;
+    }
+    sh_ok[w][lane] = ok;
+  }
+  __syncwarp();
+  // 2. the warp solves the prepared halos one after another, lanes over quadrature nodes
+  for (int jj = 0; jj < hpw; ++jj) {
+    if (!sh_ok[w][jj]) continue;
+    const int64_t i = base + jj;
+    const Halo h = sh_h[w][jj];
+    const double eps_star = X.prm ? X.prm[i] : P.eps_star;
+    const double eps_dm = X.prm ? X.prm[2 * n + i] : P.eps_dm;
+    auto put = [&](int f, double v) {
+      if (lane == 0) model[(int64_t)f * n + i] = v;
+    };
+    auto finish = [&](int st) {
+      if (lane == 0) {
+        status[i] = st;
+        if (st != BP_HALO_OK) atomicAdd((unsigned long long*)nbad, 1ull);
+      }
+    };
   const double nn = P.n_poly;
   Solver S(h, nn);
   S.cache_region_a(lane);
@@ -467,6 +499,50 @@ __global__ void __launch_bounds__(128) k_solve(BpParams P, BpTables TB, int64_t 
     return e;
   };
 
+  // Both conditions and their 2x2 Jacobian in (ln T, ln r_f) at a given (T, r_f),
+  // without the inner solve for T (one quadrature evaluation).
+  struct Direct {
+    double Rm, Re, J[2][2], thf, rho0;
+    int ok;
+  };
+  auto direct = [&](double T, double rf) -> Direct {
+    Direct d;
+    d.ok = 0;
+    double phif = phi_of(h, rf);
+    double thf = 1.0 + (h.phi0 - phif) / ((nn + 1.0) * T);
+    if (!(thf > 0.0)) return d;
+    Sums sm = S.integrals(T, rf, lane);
+    double rho0 = h.Ps / (T * S.pw(thf, 2));
+    double In = sm.In, Ip = sm.Ip, Im = sm.Im, Jm = sm.Jm, Jn = sm.Jn;
+    double Egf = four_pi * rho0 * (1.5 * T * Ip + Jn);
+    double dEp = four_pi / 3.0 * (r3v - rf * rf * rf) * h.Ps;
+    double num = (P.energy_sign == 0) ? (Egf - h.Egi - inj - dEp) : (h.Egi - Egf - inj - dEp);
+    d.Re = num / absE;
+    d.Rm = (four_pi * rho0 * In + h.Mstar) / fbM - 1.0;
+    double dphif = bpc::G * menc_of(h, rf) / (rf * rf);
+    double dthf_drf = -dphif / ((nn + 1.0) * T);
+    double dlr_drf = -(nn + 1.0) * dthf_drf / thf;
+    double dlr_dT = (-1.0 - (nn + 1.0) * (1.0 - thf) / thf) / T;
+    double tfn = S.pw(thf, 1), tfp = tfn * thf;
+    double dG_drf = four_pi * rho0 * (In * dlr_drf + tfn * rf * rf);
+    double dG_dT = four_pi * rho0 * (In * dlr_dT + nn * (Im - In) / T);
+    double dIp_dT = (nn + 1.0) * (In - Ip) / T;
+    double dJn_dT = nn * (Jm - Jn) / T;
+    double dEgf_drf = Egf * dlr_drf + four_pi * rho0 * (1.5 * T * tfp + tfn * phif) * rf * rf;
+    double dEgf_dT = Egf * dlr_dT + four_pi * rho0 * (1.5 * Ip + 1.5 * T * dIp_dT + dJn_dT);
+    double ddEp_drf = -four_pi * rf * rf * h.Ps;
+    double dn_dT = (P.energy_sign == 0) ? dEgf_dT : -dEgf_dT;
+    double dn_drf = (P.energy_sign == 0) ? (dEgf_drf - ddEp_drf) : (-dEgf_drf - ddEp_drf);
+    d.J[0][0] = dG_dT * T / fbM;
+    d.J[0][1] = dG_drf * rf / fbM;
+    d.J[1][0] = dn_dT * T / absE;
+    d.J[1][1] = dn_drf * rf / absE;
+    d.thf = thf;
+    d.rho0 = rho0;
+    d.ok = 1;
+    return d;
+  };
+
   // Safeguarded Newton in v = ln r_f on [ln 0.5 r_vir, ln 10 r_vir]: Newton steps
   // (clamped) until a sign change is bracketed, then Newton with bisection inside
   // the bracket.  The direction of R_e(r_f) is not assumed.
@@ -480,14 +556,43 @@ __global__ void __launch_bounds__(128) k_solve(BpParams P, BpTables TB, int64_t 
       Tw = exp(g1) * h.GM / h.rvir;
     }
   }
+  int st = BP_HALO_MAXIT;
+  Eval e;
+  double rf = exp(v);
+  if (X.guess && Tw > 0.0) {
+    // polish: two-dimensional Newton from the given starting point, one quadrature
+    // evaluation per iteration, steps halved to keep theta(r_f) > 0
+    double u = log(Tw);
+    e.ok = 0;
+    for (int it = 0; it < X.max_outer; ++it) {
+      double T = exp(u);
+      rf = exp(v);
+      Direct d = direct(T, rf);
+      if (!d.ok) { e.ok = 0; break; }
+      e.T = T; e.thf = d.thf; e.rho0 = d.rho0; e.Rm = d.Rm; e.Re = d.Re; e.ok = 1;
+      if (fabs(d.Re) < tol && fabs(d.Rm) < tol) { st = BP_HALO_OK; break; }
+      double det = d.J[0][0] * d.J[1][1] - d.J[0][1] * d.J[1][0];
+      if (!(fabs(det) > 0.0) || !isfinite(det)) break;
+      double du = (-d.Rm * d.J[1][1] + d.Re * d.J[0][1]) / det;
+      double dv = (-d.Re * d.J[0][0] + d.Rm * d.J[1][0]) / det;
+      double big = fmax(fabs(du), fabs(dv));
+      if (big > 0.5) { du *= 0.5 / big; dv *= 0.5 / big; }
+      for (int half = 0; half < 20; ++half) {
+        double vn = fmin(fmax(v + dv, vmin), vmax);
+        double Tmin_n = (phi_of(h, exp(vn)) - h.phi0) / (nn + 1.0);
+        if (exp(u + du) > Tmin_n * (1.0 + 1e-12)) break;
+        du *= 0.5;
+        dv *= 0.5;
+      }
+      u += du;
+      v = fmin(fmax(v + dv, vmin), vmax);
+    }
+  } else {
   double va = 0, vb = 0, Ra = 0;  // bracket [va, vb] with R(va) R(vb) < 0
   bool have_br = false;
   double vprev = 0, Rprev = 0;
   bool have_prev = false;
   int hits_min = 0, hits_max = 0;
-  int st = BP_HALO_MAXIT;
-  Eval e;
-  double rf = exp(v);
   for (int it = 0; it < X.max_outer; ++it) {
     rf = exp(v);
     e = reduced(rf, Tw);
@@ -516,6 +621,7 @@ __global__ void __launch_bounds__(128) k_solve(BpParams P, BpTables TB, int64_t 
     vprev = v; Rprev = e.Re; have_prev = true;
     v = vn;
   }
+  }
   if (X.gate > 0 && st != BP_HALO_OK) {
     bool pass = e.ok && fabs(e.Re) <= X.gate && fabs(e.Rm) <= X.gate;
     st = pass ? BP_HALO_OK : BP_HALO_FALLBACK;
@@ -528,6 +634,7 @@ __global__ void __launch_bounds__(128) k_solve(BpParams P, BpTables TB, int64_t 
   put(BP_M_RESM, e.ok ? e.Rm : NAN);
   put(BP_M_RESE, e.ok ? e.Re : NAN);
   finish(st);
+  }
 }
 
 }  // namespace
@@ -538,11 +645,14 @@ static int solve_launch(bp_ctx* ctx, int64_t n, const double* Mvir, const double
   int r = upload_constants(ctx);
   if (r) return r;
   BP_CUDA(ctx, cudaMemsetAsync(ctx->d_counter, 0, sizeof(int64_t), ctx->stream));
-  const int threads = 128;  // 4 halos per block
-  int64_t blocks = (n * 32 + threads - 1) / threads;
+  // halos per warp: enough warps to fill the GPU, the rest shared out 1..32 per warp
+  int64_t target_warps = (int64_t)ctx->num_sms * 16;
+  int hpw = (int)std::min<int64_t>(32, std::max<int64_t>(1, n / target_warps));
+  int64_t warps = (n + hpw - 1) / hpw;
+  int64_t blocks = (warps + SOLVE_WARPS - 1) / SOLVE_WARPS;
   bp_phase_begin(ctx, BP_PH_SOLVE);
-  k_solve<<<(unsigned)blocks, threads, 0, ctx->stream>>>(ctx->p, ctx->t, n, Mvir, c, z, model,
-                                                        status, tol, ctx->d_counter, X);
+  k_solve<<<(unsigned)blocks, 32 * SOLVE_WARPS, 0, ctx->stream>>>(
+      ctx->p, ctx->t, n, Mvir, c, z, model, status, tol, ctx->d_counter, X, hpw);
   BP_LAUNCH_CHECK(ctx, "k_solve launch");
   bp_phase_end(ctx, BP_PH_SOLVE);
   BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, ctx->d_counter, sizeof(int64_t),

@@ -107,7 +107,7 @@ class Surrogate:
             self.wb = ctx.mlp_to_bf16(self.params)
         return self.wb
 
-    def solve(self, ctx, M, c, z, prm=None, polish_iter=2, gate=1e-4, raise_on_noconv=True):
+    def solve(self, ctx, M, c, z, prm=None, polish_iter=4, gate=1e-4, raise_on_noconv=True):
         return ctx.solve_halos_surrogate(M, c, z, prm, self.bf16(ctx), self.params, self.norm,
                                          self.hull, polish_iter, gate,
                                          raise_on_noconv=raise_on_noconv)

@@ -127,6 +127,8 @@ def test_surrogate_beats_plain_solve(api, trained):
     torch.cuda.synchronize()
     t_sur = time.perf_counter() - t0
     assert (st.cpu().numpy() == 0).all()
+    print(f"surrogate {t_sur * 1e3:.1f} ms, plain {t_plain * 1e3:.1f} ms, "
+          f"fallbacks {c.last_fallback_count()} of {M.size}")
     assert t_sur < t_plain, (t_sur, t_plain)
     rf_p = m_plain[api.MF["r_f"]].cpu().numpy()
     rf_s = m_sur[api.MF["r_f"]].cpu().numpy()
