@@ -199,6 +199,72 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU leg
+def surrogate_section(api, ctx, dev, lc, args):
+    """Surrogate vs plain FP64 solve: train on solver outputs, then time both solves on
+    the same inference halos, and compare the pasted y of the light-cone halos."""
+    import torch
+
+    from paper_2201_02632_gb300 import inputs as I
+    from paper_2201_02632_gb300.surrogate import Surrogate
+
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    M, c, z, prm = I.surrogate_halos(args.sur_train, seed=I.SEED_BASE + 4)
+    sur = Surrogate.init(dev, seed=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    loss = sur.fit(ctx, t(M), t(c), t(z), t(prm), epochs=args.sur_epochs, batch=4096)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    Mi, ci, zi, pi = I.surrogate_halos(args.sur_infer, seed=I.SEED_BASE + 5)
+    a = [t(Mi), t(ci), t(zi), t(pi)]
+    w = [x[:50000] for x in a[:3]] + [a[3][:, :50000].contiguous()]
+    ctx.solve_halos_ex(*w, raise_on_noconv=False)
+    sur.solve(ctx, *w, raise_on_noconv=False)
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return out, e0.elapsed_time(e1)
+
+    (mp, sp), t_plain = timed(lambda: ctx.solve_halos_ex(*a, raise_on_noconv=False))
+    (ms, ss), t_sur = timed(lambda: sur.solve(ctx, *a, raise_on_noconv=False))
+    fallbacks = ctx.last_fallback_count()
+    ok = (sp == 0) & (ss == 0)
+    rel = {}
+    for name in ("r_f", "T", "rho0"):
+        k = api.MF[name]
+        r = (ms[k][ok] / mp[k][ok] - 1).abs()
+        rel[name] = {"max": float(r.max()), "median": float(r.median())}
+    # pasted y of the light-cone halos (Table-1 parameters) with each solve
+    cat = lc.halos
+    nh = cat.M.size
+    tab1 = np.stack([np.full(nh, 3.97e-6), np.full(nh, 0.026), np.zeros(nh)])
+    hc = [t(cat.M), t(cat.c), t(cat.z)]
+    m1, s1 = ctx.solve_halos_ex(*hc, params=t(tab1))
+    m2, s2 = sur.solve(ctx, *hc, t(tab1))
+    g = api.geom(lc.geom.nx, lc.geom.ny, lc.geom.theta0_x, lc.geom.theta0_y, lc.geom.dtheta)
+    maps = []
+    for m_, s_ in ((m1, s1), (m2, s2)):
+        mm = api.Maps.zeros(g, dev)
+        ctx.paste_halos(t(cat.thx), t(cat.thy), t(cat.vlos), m_, s_, g, mm)
+        ctx.finalize(g, mm)
+        maps.append(mm.y[0].double())
+    y_err = float(torch.linalg.norm(maps[1] - maps[0]) / torch.linalg.norm(maps[0]))
+    return {"workload": f"train on {args.sur_train} solver outputs, solve {args.sur_infer} halos "
+                        "(log M 12-15.3, z 0.01-3, eps_* 0-1e-5, f_* 0.01-0.04, eps_DM 0-0.1)",
+            "train_s": round(train_s, 2), "train_loss": loss,
+            "plain_fp64_solve_ms": t_plain, "surrogate_solve_ms": t_sur,
+            "speedup": t_plain / t_sur, "halos_per_s_plain": args.sur_infer / (t_plain * 1e-3),
+            "halos_per_s_surrogate": args.sur_infer / (t_sur * 1e-3),
+            "fallbacks": int(fallbacks), "rel_diff_vs_plain": rel,
+            "pasted_y_rel_l2_vs_plain": y_err,
+            "gate": 1e-4, "polish_newton_iters": 4}
+
+
 def run_ours(args):
     import torch
 
@@ -345,6 +411,8 @@ def run_ours(args):
         "gpu_launches": launches,
         "clocks": clocks,
     }
+    if not args.no_surrogate:
+        res["surrogate"] = surrogate_section(api, ctx, dev, lc, args)
     if not args.no_cpu_baseline and world == 1:
         threads = os.cpu_count() or 1
         t_full, det = oracle_sample(lc, args.ref_particles, args.ref_halos, threads)
@@ -369,6 +437,10 @@ def main():
     ap.add_argument("--ref-particles", type=int, default=1_000_000)
     ap.add_argument("--ref-halos", type=int, default=600)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--sur-train", type=int, default=2_000_000)
+    ap.add_argument("--sur-infer", type=int, default=10_000_000)
+    ap.add_argument("--sur-epochs", type=int, default=6)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
