@@ -265,6 +265,73 @@ def surrogate_section(api, ctx, dev, lc, args):
             "gate": 1e-4, "polish_newton_iters": 4}
 
 
+def batched_section(api, ctx, dev, args):
+    """Batched HP: many independent maps of uneven halo extents pasted by one prepared
+    plan (one persistent launch), autotuned, captured in a CUDA graph and replayed."""
+    import torch
+
+    from paper_2201_02632_gb300 import autotune
+    from paper_2201_02632_gb300 import inputs as I
+
+    cat, gi = I.batched_catalog(n_maps=args.batch_maps, mean_halos=args.batch_halos,
+                                npix=args.batch_npix)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    M, c, z = t(cat.M), t(cat.c), t(cat.z)
+    thx, thy, vl, mid = t(cat.thx), t(cat.thy), t(cat.vlos), t(cat.map_id)
+    n = cat.M.size
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    model, status = ctx.solve_halos(M, c, z, raise_on_noconv=False)
+    torch.cuda.synchronize()
+    solve_s = time.perf_counter() - t0
+    g = api.geom(gi.nx, gi.ny, gi.theta0_x, gi.theta0_y, gi.dtheta, gi.n_maps)
+    maps = api.Maps.zeros(g, dev)
+    t0 = time.perf_counter()
+    best = autotune.tune_hp(ctx, thx, thy, vl, model, status, g, maps, map_id=mid,
+                            cache_path=os.path.join(ROOT, "gpurun_out", "autotune_hp.json"),
+                            use_cache=False)
+    tune_s = time.perf_counter() - t0
+    plan = ctx.hp_plan(thx, thy, model, status, g, 0.0, mid, best["tile"], best["unit"],
+                       best["ctas_per_sm"])
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        ctx.set_stream(torch.cuda.current_stream())
+        maps.zero_()
+        plan.execute(thx, thy, vl, model, status, maps, mid)
+    torch.cuda.current_stream().wait_stream(side)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(graph):
+        ctx.set_stream(torch.cuda.current_stream())
+        maps.zero_()
+        plan.execute(thx, thy, vl, model, status, maps, mid)
+    ctx.set_stream(torch.cuda.current_stream())
+    for _ in range(3):
+        graph.replay()
+    ms = []
+    for _ in range(args.batch_steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    step = sum(ms) / len(ms)
+    pairs = plan.pairs
+    plan.close()
+    del maps
+    torch.cuda.empty_cache()
+    return {"workload": f"{gi.n_maps} maps of {gi.nx}^2 (5x5 deg^2), {n} halos "
+                        f"(Poisson({args.batch_halos:g}) per map), M 1e12-1e15 dN/dlnM ~ M^-0.9, "
+                        "z 0.01-3, r_ap = r_f",
+            "halos": int(n), "tile_pairs": int(pairs), "ms_per_step": step,
+            "halos_per_s": n / (step * 1e-3), "maps_per_s": gi.n_maps / (step * 1e-3),
+            "autotuned": {k: best[k] for k in ("tile", "unit", "ctas_per_sm", "ms")},
+            "tune_s": round(tune_s, 2), "solve_s_plain_fp64": round(solve_s, 3),
+            "graph_replay": True}
+
+
 def run_ours(args):
     import torch
 
@@ -413,6 +480,8 @@ def run_ours(args):
     }
     if not args.no_surrogate:
         res["surrogate"] = surrogate_section(api, ctx, dev, lc, args)
+    if not args.no_batched:
+        res["batched_hp"] = batched_section(api, ctx, dev, args)
     if not args.no_cpu_baseline and world == 1:
         threads = os.cpu_count() or 1
         t_full, det = oracle_sample(lc, args.ref_particles, args.ref_halos, threads)
@@ -438,6 +507,11 @@ def main():
     ap.add_argument("--ref-halos", type=int, default=600)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batch-maps", type=int, default=108)
+    ap.add_argument("--batch-halos", type=float, default=5e4)
+    ap.add_argument("--batch-npix", type=int, default=2048)
+    ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--sur-train", type=int, default=2_000_000)
     ap.add_argument("--sur-infer", type=int, default=10_000_000)
     ap.add_argument("--sur-epochs", type=int, default=6)

@@ -155,7 +155,8 @@ const char* bp_last_error(const bp_ctx* ctx);
 /* Change the stream later calls are queued on. */
 int bp_set_stream(bp_ctx* ctx, void* stream);
 /* Tile sizes: PP deposit tile (pixels per side: 32 or 64) and HP tile (32 or 64);
- * pp_unit: maximum particles per deposit work unit (>= 256).  0 keeps a value. */
+ * pp_unit: maximum particles per deposit work unit (>= 256; -1 = automatic, about 16
+ * units per resident CTA).  0 keeps a value. */
 int bp_set_tiling(bp_ctx* ctx, int pp_tile, int hp_tile, int pp_unit);
 /* Bytes of scratch the context currently holds. */
 int64_t bp_workspace_bytes(const bp_ctx* ctx);
@@ -332,6 +333,28 @@ int bp_paste_halos(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_
                    const float* v_los, const int32_t* map_id, const double* model,
                    const int32_t* status, const bp_map_geom* geom, double ap_r500, float* ymap,
                    float* bmap, float* ylo, float* blo);
+
+/* A prepared halo paste for repeated pastes of one catalogue (many maps of uneven halo
+ * extents in one persistent launch).  bp_hp_plan_create builds the (map, tile, halo)
+ * work list from the catalogue's apertures (as bp_paste_halos does; synchronises) and
+ * allocates the plan's own device buffers.  tile: 32 or 64 pixels; unit: halos per work
+ * unit (0 = automatic); ctas_per_sm: persistent CTAs per SM (0 = as many as fit).
+ * bp_hp_plan_execute then recomputes the halo tables from model and v_los and pastes
+ * into the maps with launch shapes fixed at creation: it neither synchronises nor
+ * allocates, so a caller can capture it in a CUDA graph.  The work list stays valid
+ * while the apertures (r_f, r500, D_A of model and the sky positions) are those the
+ * plan was built with.  Paste semantics are those of bp_paste_halos. */
+typedef struct bp_hp_plan bp_hp_plan;
+int bp_hp_plan_create(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_y,
+                      const int32_t* map_id, const double* model, const int32_t* status,
+                      const bp_map_geom* geom, double ap_r500, int tile, int unit,
+                      int ctas_per_sm, bp_hp_plan** plan);
+int bp_hp_plan_execute(bp_ctx* ctx, bp_hp_plan* plan, const double* th_x, const double* th_y,
+                       const float* v_los, const int32_t* map_id, const double* model,
+                       const int32_t* status, float* ymap, float* bmap, float* ylo, float* blo);
+/* (tile, halo) pairs of the plan's work list. */
+int64_t bp_hp_plan_pairs(const bp_hp_plan* plan);
+int bp_hp_plan_destroy(bp_hp_plan* plan);
 
 /* Section 3.2: fold lo into hi (hi <- fl(hi + lo), lo <- 0) for all n_maps maps;
  * out_kind BP_OUT_DT then converts to Delta T/T_CMB: g_nu(x) y (x = h nu/k T_CMB,

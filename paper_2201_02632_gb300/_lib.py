@@ -30,7 +30,8 @@ EXPORTS = ("bp_create", "bp_destroy", "bp_last_error", "bp_set_stream", "bp_set_
            "bp_paste_halos", "bp_finalize_map", "bp_paste_particles_noalloc",
            "bp_solve_halos_ex", "bp_last_fallback_count", "bp_mlp_forward", "bp_mlp_backward",
            "bp_mlp_adam", "bp_mlp_to_bf16", "bp_mlp_infer_bf16", "bp_mlp_features",
-           "bp_mlp_targets", "bp_mlp_mse", "bp_solve_halos_surrogate")
+           "bp_mlp_targets", "bp_mlp_mse", "bp_solve_halos_surrogate", "bp_hp_plan_create",
+           "bp_hp_plan_execute", "bp_hp_plan_pairs", "bp_hp_plan_destroy")
 MLP_IN, MLP_HID, MLP_OUT = 6, 128, 3
 MLP_NPARAMS = 128 * 6 + 128 + 2 * (128 * 128 + 128) + 3 * 128 + 3
 MLP_NWEIGHTS = 128 * 6 + 2 * 128 * 128 + 3 * 128
@@ -102,6 +103,11 @@ def load():
                 "bp_paste_halos": (i32, [P, i64, P, P, P, P, P, P, C.POINTER(BpGeom), d, P, P, P,
                                          P]),
                 "bp_finalize_map": (i32, [P, C.POINTER(BpGeom), P, P, P, P, i32, d]),
+                "bp_hp_plan_create": (i32, [P, i64, P, P, P, P, P, C.POINTER(BpGeom), d, i32, i32,
+                                            i32, C.POINTER(P)]),
+                "bp_hp_plan_execute": (i32, [P, P, P, P, P, P, P, P, P, P, P, P]),
+                "bp_hp_plan_pairs": (i64, [P]),
+                "bp_hp_plan_destroy": (i32, [P]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)

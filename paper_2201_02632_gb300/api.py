@@ -91,6 +91,11 @@ class Context:
             raise BpError(rc, self._L.bp_last_error(self._h).decode())
         return rc
 
+    def set_stream(self, stream):
+        """Queue later calls on `stream` (a torch.cuda.Stream)."""
+        self.stream = stream
+        self._check(self._L.bp_set_stream(self._h, C.c_void_p(stream.cuda_stream)))
+
     def set_tiling(self, pp_tile=0, hp_tile=0, pp_unit=0):
         self._check(self._L.bp_set_tiling(self._h, pp_tile, hp_tile, pp_unit))
 
@@ -296,6 +301,20 @@ class Context:
         self._check(rc)
         return maps
 
+    def hp_plan(self, thx, thy, model, status, g: L.BpGeom, ap_r500=0.0, map_id=None, tile=32,
+                unit=0, ctas_per_sm=0):
+        """bp_hp_plan_create: the work list of one catalogue, reusable (and capturable)."""
+        h = C.c_void_p()
+        rc = self._L.bp_hp_plan_create(self._h, thx.numel(), _ptr(thx, torch.float64, "thx"),
+                                       _ptr(thy, torch.float64, "thy"),
+                                       _ptr(map_id, torch.int32, "map_id"),
+                                       _ptr(model, torch.float64, "model"),
+                                       _ptr(status, torch.int32, "status"), C.byref(g),
+                                       float(ap_r500), int(tile), int(unit), int(ctas_per_sm),
+                                       C.byref(h))
+        self._check(rc)
+        return HpPlan(self, h, g)
+
     # ------------------------------------------------------------ Section 3.2
     def finalize(self, g: L.BpGeom, maps: Maps, out_kind=OUT_YB, nu_ghz=0.0):
         f32 = torch.float32
@@ -304,3 +323,36 @@ class Context:
                                      _ptr(maps.blo, f32, "blo"), int(out_kind), float(nu_ghz))
         self._check(rc)
         return maps
+
+
+class HpPlan:
+    """A prepared halo paste (bp_hp_plan_*)."""
+
+    def __init__(self, ctx: Context, handle, g):
+        self.ctx, self._h, self.geom = ctx, handle, g
+
+    @property
+    def pairs(self) -> int:
+        return int(self.ctx._L.bp_hp_plan_pairs(self._h))
+
+    def execute(self, thx, thy, vlos, model, status, maps: Maps, map_id=None):
+        f32 = torch.float32
+        rc = self.ctx._L.bp_hp_plan_execute(
+            self.ctx._h, self._h, _ptr(thx, torch.float64, "thx"), _ptr(thy, torch.float64, "thy"),
+            _ptr(vlos, f32, "vlos"), _ptr(map_id, torch.int32, "map_id"),
+            _ptr(model, torch.float64, "model"), _ptr(status, torch.int32, "status"),
+            _ptr(maps.y, f32, "y"), _ptr(maps.b, f32, "b"), _ptr(maps.ylo, f32, "ylo"),
+            _ptr(maps.blo, f32, "blo"))
+        self.ctx._check(rc)
+        return maps
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.ctx._L.bp_hp_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -214,7 +214,7 @@ int bp_create(bp_ctx** out, const bp_cosmology* cosmo, const bp_icm_params* icm,
   P.CN = bpc::SIGMA_T * bpc::MSUN_KG / (P.mu_e * bpc::MP_KG * bpc::MPC_M * bpc::MPC_M);
   ctx->pp_tile = 64;
   ctx->hp_tile = 32;
-  ctx->pp_unit = 4096;
+  ctx->pp_unit = 0;  // automatic
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -271,10 +271,11 @@ int bp_set_tiling(bp_ctx* ctx, int pp_tile, int hp_tile, int pp_unit) {
     return bp_fail(ctx, BP_EINVAL, "bp_set_tiling: pp_tile must be 32 or 64");
   if (hp_tile && hp_tile != 32 && hp_tile != 64)
     return bp_fail(ctx, BP_EINVAL, "bp_set_tiling: hp_tile must be 32 or 64");
-  if (pp_unit && pp_unit < 256) return bp_fail(ctx, BP_EINVAL, "bp_set_tiling: pp_unit < 256");
+  if (pp_unit > 0 && pp_unit < 256) return bp_fail(ctx, BP_EINVAL, "bp_set_tiling: pp_unit < 256");
   if (pp_tile) ctx->pp_tile = pp_tile;
   if (hp_tile) ctx->hp_tile = hp_tile;
-  if (pp_unit) ctx->pp_unit = pp_unit;
+  if (pp_unit > 0) ctx->pp_unit = pp_unit;
+  if (pp_unit < 0) ctx->pp_unit = 0;  // automatic
   return BP_OK;
 }
 

@@ -14,6 +14,8 @@
 //               the interpolated projected profile with Kahan compensation
 //  k_hp_reduce  partial tiles of multi-unit tiles, in unit order
 //  k_finalize   hi + lo folding and the conversion to Delta T / T_CMB
+#include <algorithm>
+
 #include "bp_internal.cuh"
 
 #define HP_NT 256          // table intervals on s = sqrt(u) in [0, 1]
@@ -88,8 +90,8 @@ __global__ void k_hp_prep(BpParams P, int64_t nh, const double* __restrict__ thx
   H.inv_rf_px = (float)(px / rf);
   double n1T = (P.n_poly + 1.0) * T, GM = bpc::G * F(BP_M_MVIR);
   H.Ay = (float)(P.CP * P.pe_frac * F(BP_M_P0) * 2.0 * rf);
-  H.Ab = (float)(P.CN * F(BP_M_RHO0) * 2.0 * rf * ((double)vlos[k] / bpc::C_KMS) *
-                 exp(-F(BP_M_TAU)));
+  double vk = vlos ? (double)vlos[k] : 0.0;
+  H.Ab = (float)(P.CN * F(BP_M_RHO0) * 2.0 * rf * (vk / bpc::C_KMS) * exp(-F(BP_M_TAU)));
   H.map = mp;
   H.ok = ok ? 1 : 0;
   H.xf = (float)(rf / rs);
@@ -276,21 +278,25 @@ struct HpUnit {
   int64_t slot;
 };
 
+// units per tile and partial-tile slots (only for tiles split into several units)
 __global__ void k_hp_ucount(const int64_t* __restrict__ tstart, int64_t n_tiles, int unit,
-                            uint32_t* uc) {
+                            uint32_t* uc, uint32_t* sc) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_tiles) return;
-  uc[t] = (uint32_t)((tstart[t + 1] - tstart[t] + unit - 1) / unit);
+  uint32_t nu = (uint32_t)((tstart[t + 1] - tstart[t] + unit - 1) / unit);
+  uc[t] = nu;
+  sc[t] = nu > 1 ? nu : 0u;
 }
 __global__ void k_hp_uemit(const int64_t* __restrict__ tstart, int64_t n_tiles, int unit,
-                           const int64_t* __restrict__ uoff, HpUnit* units) {
+                           const int64_t* __restrict__ uoff, const int64_t* __restrict__ soff,
+                           HpUnit* units) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_tiles) return;
   int64_t b = tstart[t], e = tstart[t + 1], nu = (e - b + unit - 1) / unit, u0 = uoff[t];
   for (int64_t q = 0; q < nu; ++q) {
     HpUnit U;
     U.tile = t;
-    U.slot = nu > 1 ? u0 + q : -1;
+    U.slot = nu > 1 ? soff[t] + q : -1;
     U.begin = b + q * unit;
     U.end = min(e, b + (q + 1) * unit);
     units[u0 + q] = U;
@@ -438,7 +444,7 @@ __global__ void __launch_bounds__(HP_THREADS)
 
 template <int TS>
 __global__ void __launch_bounds__(256) k_hp_reduce(const int64_t* __restrict__ tstart,
-                                                   const int64_t* __restrict__ uoff,
+                                                   const int64_t* __restrict__ soff,
                                                    int64_t n_tiles, int unit, bp_map_geom g,
                                                    const float* __restrict__ partials,
                                                    float* ymap, float* bmap, float* ylo,
@@ -450,7 +456,7 @@ __global__ void __launch_bounds__(256) k_hp_reduce(const int64_t* __restrict__ t
   int ntx = (g.nx + TS - 1) / TS, nty = (g.ny + TS - 1) / TS;
   int mp = (int)(t / ((int64_t)ntx * nty)), rem = (int)(t % ((int64_t)ntx * nty));
   int x0 = (rem % ntx) * TS, y0 = (rem / ntx) * TS;
-  int64_t u0 = uoff[t];
+  int64_t u0 = soff[t];
   for (int q = threadIdx.x; q < TS * TS; q += blockDim.x) {
     int gx = x0 + q % TS, gy = y0 + q / TS;
     if (gx >= g.nx || gy >= g.ny) continue;
@@ -487,26 +493,44 @@ __global__ void k_finalize(int64_t npix, float* map, float* lo, float scale) {
   map[i] = v * scale;
 }
 
-template <int TS>
-int hp_run(bp_ctx* ctx, int64_t n, const HpHalo* halos, const float* tab, const bp_map_geom* g,
-           float* ymap, float* bmap, float* ylo, float* blo) {
+// The (map, tile, halo) work list of a catalogue, in the context's scratch.
+struct HpList {
+  int64_t np = 0, n_tiles = 0, n_units = 0, n_slots = 0;
+  const uint32_t* vals = nullptr;  // halo indices sorted by (map, tile), then index
+  int64_t* tstart = nullptr;       // [n_tiles + 1]
+  int64_t* uoff = nullptr;         // [n_tiles + 1], uoff[n_tiles] = n_units
+  int64_t* soff = nullptr;         // [n_tiles + 1]
+  HpUnit* units = nullptr;
+  int unit = 0, ts = 0;
+};
+
+int hp_build_list(bp_ctx* ctx, int64_t n, const HpHalo* halos, const bp_map_geom* g, int TS,
+                  int unit, HpList* L) {
   int r;
   const int ntx = (g->nx + TS - 1) / TS, nty = (g->ny + TS - 1) / TS;
   const int64_t n_tiles = (int64_t)ntx * nty * g->n_maps;
+  if (n_tiles > (int64_t)UINT32_MAX) return bp_fail(ctx, BP_ERANGE, "paste_halos: too many tiles");
   uint32_t* counts;
   int64_t* offs;
   if ((r = bp_ws(ctx, WS_COUNTS, (size_t)(n + 1) * 4, (void**)&counts))) return r;
   if ((r = bp_ws(ctx, WS_OFFS, (size_t)(n + 1) * 8, (void**)&offs))) return r;
   unsigned nb = (unsigned)((n + 255) / 256);
-  bp_phase_begin(ctx, BP_PH_HP_PAIRS);
   k_hp_count<<<nb, 256, 0, ctx->stream>>>(halos, n, *g, TS, counts);
   BP_LAUNCH_CHECK(ctx, "hp count");
   if ((r = bp_scan_u32_to_i64(ctx, counts, offs, n))) return r;
   BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, offs + n, 8, cudaMemcpyDeviceToHost, ctx->stream));
   BP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   const int64_t np = ctx->h_pinned[0];
+  L->np = np;
+  L->n_tiles = n_tiles;
+  L->ts = TS;
   if (np == 0) return BP_OK;
   if (np > (int64_t)UINT32_MAX) return bp_fail(ctx, BP_ERANGE, "paste_halos: too many pairs");
+  if (unit <= 0) {  // automatic: about 16 units per resident CTA, at least 256 halos
+    int64_t u = np / ((int64_t)ctx->num_sms * 4 * 16);
+    unit = (int)std::min<int64_t>(std::max<int64_t>(u, 256), 1 << 30);
+  }
+  L->unit = unit;
   uint32_t *k0, *v0, *k1, *v1, *ks, *vs;
   if ((r = bp_ws(ctx, WS_KEYS0, (size_t)np * 4, (void**)&k0))) return r;
   if ((r = bp_ws(ctx, WS_VALS0, (size_t)np * 4, (void**)&v0))) return r;
@@ -517,69 +541,42 @@ int hp_run(bp_ctx* ctx, int64_t n, const HpHalo* halos, const float* tab, const 
   int key_bits = 0;
   while (((int64_t)1 << key_bits) < n_tiles) ++key_bits;
   if ((r = bp_radix_sort_pairs(ctx, k0, v0, k1, v1, np, key_bits, &ks, &vs))) return r;
+  L->vals = vs;
   int64_t* tstart;
-  if ((r = bp_ws(ctx, WS_TILES, (size_t)(n_tiles + 1) * 20 + 64, (void**)&tstart))) return r;
-  int64_t* uoff = tstart + (n_tiles + 1);
-  uint32_t* uc = (uint32_t*)(uoff + (n_tiles + 1));
+  if ((r = bp_ws(ctx, WS_TILES, (size_t)(n_tiles + 1) * 32 + 64, (void**)&tstart))) return r;
+  L->tstart = tstart;
+  L->uoff = tstart + (n_tiles + 1);
+  L->soff = L->uoff + (n_tiles + 1);
+  uint32_t* uc = (uint32_t*)(L->soff + (n_tiles + 1));
+  uint32_t* sc = uc + (n_tiles + 1);
   if ((r = bp_tile_ranges(ctx, ks, np, n_tiles, tstart))) return r;
-  const int unit = 512;
   unsigned tb = (unsigned)((n_tiles + 255) / 256);
-  k_hp_ucount<<<tb, 256, 0, ctx->stream>>>(tstart, n_tiles, unit, uc);
+  k_hp_ucount<<<tb, 256, 0, ctx->stream>>>(tstart, n_tiles, unit, uc, sc);
   BP_LAUNCH_CHECK(ctx, "hp unit count");
-  if ((r = bp_scan_u32_to_i64(ctx, uc, uoff, n_tiles))) return r;
-  const int64_t max_units = n_tiles + np / unit + 1;
-  HpUnit* units;
-  if ((r = bp_ws(ctx, WS_UNITS, (size_t)max_units * sizeof(HpUnit), (void**)&units))) return r;
-  k_hp_uemit<<<tb, 256, 0, ctx->stream>>>(tstart, n_tiles, unit, uoff, units);
+  if ((r = bp_scan_u32_to_i64(ctx, uc, L->uoff, n_tiles))) return r;
+  if ((r = bp_scan_u32_to_i64(ctx, sc, L->soff, n_tiles))) return r;
+  BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, L->uoff + n_tiles, 8, cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 1, L->soff + n_tiles, 8, cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  BP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  L->n_units = ctx->h_pinned[0];
+  L->n_slots = ctx->h_pinned[1];
+  if ((r = bp_ws(ctx, WS_UNITS, (size_t)(L->n_units + 1) * sizeof(HpUnit), (void**)&L->units)))
+    return r;
+  k_hp_uemit<<<tb, 256, 0, ctx->stream>>>(tstart, n_tiles, unit, L->uoff, L->soff, L->units);
   BP_LAUNCH_CHECK(ctx, "hp units");
-  float* partials;
-  if ((r = bp_ws(ctx, WS_PART, (size_t)max_units * 4 * TS * TS * 4, (void**)&partials))) return r;
-  BP_CUDA(ctx, cudaMemsetAsync(ctx->d_counter + 2, 0, 8, ctx->stream));
-  bp_phase_end(ctx, BP_PH_HP_PAIRS);
-  int per_sm = 0;
-  BP_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hp_paste<TS>, HP_THREADS, 0));
-  if (per_sm < 1) per_sm = 1;
-  int64_t grid = (int64_t)ctx->num_sms * per_sm;
-  if (grid > max_units) grid = max_units;
-  bp_phase_begin(ctx, BP_PH_HP_PASTE);
-  k_hp_paste<TS><<<(unsigned)grid, HP_THREADS, 0, ctx->stream>>>(
-      halos, tab, vs, units, uoff + n_tiles, ctx->d_counter + 2, *g, ymap, bmap, ylo, blo,
-      partials);
-  BP_LAUNCH_CHECK(ctx, "hp paste");
-  k_hp_reduce<TS><<<(unsigned)n_tiles, 256, 0, ctx->stream>>>(tstart, uoff, n_tiles, unit, *g,
-                                                             partials, ymap, bmap, ylo, blo);
-  BP_LAUNCH_CHECK(ctx, "hp reduce");
-  bp_phase_end(ctx, BP_PH_HP_PASTE);
   return BP_OK;
 }
 
-}  // namespace
-
-extern "C" {
-
-int bp_paste_halos(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_y,
-                   const float* v_los, const int32_t* map_id, const double* model,
-                   const int32_t* status, const bp_map_geom* geom, double ap_r500, float* ymap,
-                   float* bmap, float* ylo, float* blo) {
-  if (!ctx) return BP_EINVAL;
-  if (!geom || geom->nx <= 0 || geom->ny <= 0 || geom->n_maps <= 0 || !(geom->dtheta > 0))
-    return bp_fail(ctx, BP_EINVAL, "bp_paste_halos: bad geometry");
-  if (n < 0) return bp_fail(ctx, BP_EINVAL, "bp_paste_halos: n < 0");
-  if (n > (int64_t)UINT32_MAX) return bp_fail(ctx, BP_ERANGE, "bp_paste_halos: n >= 2^32");
-  if (n == 0) return BP_OK;
-  if (!th_x || !th_y || !v_los || !model || !status || !ymap || !bmap || !ylo || !blo)
-    return bp_fail(ctx, BP_EINVAL, "bp_paste_halos: null pointer");
-  if (ap_r500 < 0) return bp_fail(ctx, BP_EINVAL, "bp_paste_halos: ap_r500 < 0");
-  int r = hp_constants(ctx);
-  if (r) return r;
-  HpHalo* halos;
-  if ((r = bp_ws(ctx, WS_HPAR, (size_t)n * sizeof(HpHalo), (void**)&halos))) return r;
-  float* tab;
-  if ((r = bp_ws(ctx, WS_TABLE, (size_t)n * 2 * HP_ROW * sizeof(float), (void**)&tab))) return r;
+// Tables of the halos: profile constants, line-of-sight integrals, ghost nodes.
+int hp_tables(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_y,
+              const float* v_los, const int32_t* map_id, const double* model,
+              const int32_t* status, const bp_map_geom* g, double ap_r500, HpHalo* halos,
+              float* tab) {
   unsigned nb = (unsigned)((n + 255) / 256);
-  bp_phase_begin(ctx, BP_PH_HP_TABLE);
-  k_hp_prep<<<nb, 256, 0, ctx->stream>>>(ctx->p, n, th_x, th_y, v_los, map_id, model, status,
-                                         *geom, ap_r500, halos);
+  k_hp_prep<<<nb, 256, 0, ctx->stream>>>(ctx->p, n, th_x, th_y, v_los, map_id, model, status, *g,
+                                         ap_r500, halos);
   BP_LAUNCH_CHECK(ctx, "hp prep");
   const BpParams& P = ctx->p;
   double rn = rint(P.n_poly);
@@ -590,9 +587,220 @@ int bp_paste_halos(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_
   BP_LAUNCH_CHECK(ctx, "hp table");
   k_hp_ghosts<<<nb, 256, 0, ctx->stream>>>(halos, n, tab);
   BP_LAUNCH_CHECK(ctx, "hp ghosts");
+  return BP_OK;
+}
+
+template <int TS>
+int hp_grid(bp_ctx* ctx, int ctas_per_sm, int64_t n_units) {
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hp_paste<TS>,
+                                                                HP_THREADS, 0);
+  if (e != cudaSuccess) return -1;
+  if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)ctx->num_sms * per_sm;
+  if (grid > n_units) grid = n_units;
+  return (int)(grid > 0 ? grid : 1);
+}
+
+// The paste of a built list: persistent kernel over the work units, then the
+// fixed-order reduction of split tiles.  No host synchronisation, no allocation.
+template <int TS>
+int hp_launch(bp_ctx* ctx, const HpHalo* halos, const float* tab, const HpList& L, int grid,
+              float* partials, int64_t* counter, const bp_map_geom* g, float* ymap, float* bmap,
+              float* ylo, float* blo) {
+  BP_CUDA(ctx, cudaMemsetAsync(counter, 0, 8, ctx->stream));
+  k_hp_paste<TS><<<(unsigned)grid, HP_THREADS, 0, ctx->stream>>>(
+      halos, tab, L.vals, L.units, L.uoff + L.n_tiles, counter, *g, ymap, bmap, ylo, blo,
+      partials);
+  BP_LAUNCH_CHECK(ctx, "hp paste");
+  if (L.n_slots > 0) {
+    k_hp_reduce<TS><<<(unsigned)L.n_tiles, 256, 0, ctx->stream>>>(
+        L.tstart, L.soff, L.n_tiles, L.unit, *g, partials, ymap, bmap, ylo, blo);
+    BP_LAUNCH_CHECK(ctx, "hp reduce");
+  }
+  return BP_OK;
+}
+
+int check_hp_args(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_y,
+                  const double* model, const int32_t* status, const bp_map_geom* geom,
+                  double ap_r500, const char* who) {
+  if (!geom || geom->nx <= 0 || geom->ny <= 0 || geom->n_maps <= 0 || !(geom->dtheta > 0))
+    return bp_fail(ctx, BP_EINVAL, "%s: bad geometry", who);
+  if (n < 0) return bp_fail(ctx, BP_EINVAL, "%s: n < 0", who);
+  if (n > (int64_t)UINT32_MAX) return bp_fail(ctx, BP_ERANGE, "%s: n >= 2^32", who);
+  if (n > 0 && (!th_x || !th_y || !model || !status))
+    return bp_fail(ctx, BP_EINVAL, "%s: null pointer", who);
+  if (ap_r500 < 0) return bp_fail(ctx, BP_EINVAL, "%s: ap_r500 < 0", who);
+  return BP_OK;
+}
+
+}  // namespace
+
+// A prepared halo paste: the work list of one catalogue and its own buffers.
+struct bp_hp_plan {
+  int64_t n;
+  bp_map_geom geom;
+  double ap_r500;
+  int ts, grid;
+  HpList L;
+  HpHalo* halos;
+  float* tab;
+  float* partials;
+  int64_t* counter;
+  void* mem[8];
+};
+
+extern "C" {
+
+int bp_paste_halos(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_y,
+                   const float* v_los, const int32_t* map_id, const double* model,
+                   const int32_t* status, const bp_map_geom* geom, double ap_r500, float* ymap,
+                   float* bmap, float* ylo, float* blo) {
+  if (!ctx) return BP_EINVAL;
+  int r = check_hp_args(ctx, n, th_x, th_y, model, status, geom, ap_r500, "bp_paste_halos");
+  if (r || n == 0) return r;
+  if (!v_los || !ymap || !bmap || !ylo || !blo)
+    return bp_fail(ctx, BP_EINVAL, "bp_paste_halos: null pointer");
+  if ((r = hp_constants(ctx))) return r;
+  HpHalo* halos;
+  if ((r = bp_ws(ctx, WS_HPAR, (size_t)n * sizeof(HpHalo), (void**)&halos))) return r;
+  float* tab;
+  if ((r = bp_ws(ctx, WS_TABLE, (size_t)n * 2 * HP_ROW * sizeof(float), (void**)&tab))) return r;
+  bp_phase_begin(ctx, BP_PH_HP_TABLE);
+  if ((r = hp_tables(ctx, n, th_x, th_y, v_los, map_id, model, status, geom, ap_r500, halos, tab)))
+    return r;
   bp_phase_end(ctx, BP_PH_HP_TABLE);
-  if (ctx->hp_tile == 64) return hp_run<64>(ctx, n, halos, tab, geom, ymap, bmap, ylo, blo);
-  return hp_run<32>(ctx, n, halos, tab, geom, ymap, bmap, ylo, blo);
+  const int TS = ctx->hp_tile;
+  HpList L;
+  bp_phase_begin(ctx, BP_PH_HP_PAIRS);
+  if ((r = hp_build_list(ctx, n, halos, geom, TS, ctx->hp_unit, &L))) return r;
+  bp_phase_end(ctx, BP_PH_HP_PAIRS);
+  if (L.np == 0) return BP_OK;
+  float* partials;
+  if ((r = bp_ws(ctx, WS_PART, (size_t)(L.n_slots > 0 ? L.n_slots : 1) * 4 * TS * TS * 4,
+                 (void**)&partials)))
+    return r;
+  int grid = TS == 64 ? hp_grid<64>(ctx, 0, L.n_units) : hp_grid<32>(ctx, 0, L.n_units);
+  if (grid < 0) return bp_fail(ctx, BP_ECUDA, "bp_paste_halos: occupancy query");
+  bp_phase_begin(ctx, BP_PH_HP_PASTE);
+  r = TS == 64 ? hp_launch<64>(ctx, halos, tab, L, grid, partials, ctx->d_counter + 2, geom, ymap,
+                               bmap, ylo, blo)
+               : hp_launch<32>(ctx, halos, tab, L, grid, partials, ctx->d_counter + 2, geom, ymap,
+                               bmap, ylo, blo);
+  bp_phase_end(ctx, BP_PH_HP_PASTE);
+  return r;
+}
+
+int bp_hp_plan_create(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_y,
+                      const int32_t* map_id, const double* model, const int32_t* status,
+                      const bp_map_geom* geom, double ap_r500, int tile, int unit, int ctas_per_sm,
+                      bp_hp_plan** out) {
+  if (!ctx || !out) return BP_EINVAL;
+  *out = nullptr;
+  int r = check_hp_args(ctx, n, th_x, th_y, model, status, geom, ap_r500, "bp_hp_plan_create");
+  if (r) return r;
+  if (tile != 32 && tile != 64) return bp_fail(ctx, BP_EINVAL, "bp_hp_plan_create: tile");
+  if (unit < 0 || ctas_per_sm < 0) return bp_fail(ctx, BP_EINVAL, "bp_hp_plan_create: unit/ctas");
+  if ((r = hp_constants(ctx))) return r;
+  bp_hp_plan* p = (bp_hp_plan*)calloc(1, sizeof(bp_hp_plan));
+  if (!p) return bp_fail(ctx, BP_ENOMEM, "bp_hp_plan_create: host memory");
+  p->n = n;
+  p->geom = *geom;
+  p->ap_r500 = ap_r500;
+  p->ts = tile;
+  auto alloc = [&](int slot, size_t bytes) -> void* {
+    void* q = nullptr;
+    if (cudaMalloc(&q, bytes ? bytes : 16) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    p->mem[slot] = q;
+    return q;
+  };
+  auto fail = [&](int code, const char* what) {
+    bp_hp_plan_destroy(p);
+    return bp_fail(ctx, code, "bp_hp_plan_create: %s", what);
+  };
+  int64_t nn = n > 0 ? n : 1;
+  p->halos = (HpHalo*)alloc(0, (size_t)nn * sizeof(HpHalo));
+  p->tab = (float*)alloc(1, (size_t)nn * 2 * HP_ROW * sizeof(float));
+  p->counter = (int64_t*)alloc(2, 64);
+  if (!p->halos || !p->tab || !p->counter) return fail(BP_ENOMEM, "device memory");
+  if (n > 0) {
+    // the work list needs the apertures: prepare the halo records once here
+    unsigned nb = (unsigned)((n + 255) / 256);
+    k_hp_prep<<<nb, 256, 0, ctx->stream>>>(ctx->p, n, th_x, th_y, nullptr, map_id, model, status,
+                                           *geom, ap_r500, p->halos);
+    if (cudaGetLastError() != cudaSuccess) return fail(BP_ECUDA, "prep launch");
+    ctx->launches++;
+    HpList L;
+    if ((r = hp_build_list(ctx, n, p->halos, geom, tile, unit, &L))) {
+      bp_hp_plan_destroy(p);
+      return r;
+    }
+    p->L = L;
+    if (L.np > 0) {
+      // copy the list out of the context's scratch into the plan
+      uint32_t* vals = (uint32_t*)alloc(3, (size_t)L.np * 4);
+      int64_t* tiles = (int64_t*)alloc(4, (size_t)(L.n_tiles + 1) * 3 * 8);
+      HpUnit* units = (HpUnit*)alloc(5, (size_t)(L.n_units + 1) * sizeof(HpUnit));
+      p->partials = (float*)alloc(6, (size_t)(L.n_slots > 0 ? L.n_slots : 1) * 4 * tile * tile * 4);
+      if (!vals || !tiles || !units || !p->partials) return fail(BP_ENOMEM, "device memory");
+      cudaStream_t s = ctx->stream;
+      size_t tb = (size_t)(L.n_tiles + 1) * 8;
+      if (cudaMemcpyAsync(vals, L.vals, (size_t)L.np * 4, cudaMemcpyDeviceToDevice, s) ||
+          cudaMemcpyAsync(tiles, L.tstart, tb, cudaMemcpyDeviceToDevice, s) ||
+          cudaMemcpyAsync(tiles + (L.n_tiles + 1), L.uoff, tb, cudaMemcpyDeviceToDevice, s) ||
+          cudaMemcpyAsync(tiles + 2 * (L.n_tiles + 1), L.soff, tb, cudaMemcpyDeviceToDevice, s) ||
+          cudaMemcpyAsync(units, L.units, (size_t)L.n_units * sizeof(HpUnit),
+                          cudaMemcpyDeviceToDevice, s) ||
+          cudaStreamSynchronize(s))
+        return fail(BP_ECUDA, "copy of the work list");
+      p->L.vals = vals;
+      p->L.tstart = tiles;
+      p->L.uoff = tiles + (L.n_tiles + 1);
+      p->L.soff = tiles + 2 * (L.n_tiles + 1);
+      p->L.units = units;
+      p->grid = tile == 64 ? hp_grid<64>(ctx, ctas_per_sm, L.n_units)
+                           : hp_grid<32>(ctx, ctas_per_sm, L.n_units);
+      if (p->grid < 0) return fail(BP_ECUDA, "occupancy query");
+    }
+  }
+  *out = p;
+  return BP_OK;
+}
+
+int bp_hp_plan_execute(bp_ctx* ctx, bp_hp_plan* p, const double* th_x, const double* th_y,
+                       const float* v_los, const int32_t* map_id, const double* model,
+                       const int32_t* status, float* ymap, float* bmap, float* ylo, float* blo) {
+  if (!ctx || !p) return BP_EINVAL;
+  if (p->n == 0 || p->L.np == 0) return BP_OK;
+  if (!th_x || !th_y || !v_los || !model || !status || !ymap || !bmap || !ylo || !blo)
+    return bp_fail(ctx, BP_EINVAL, "bp_hp_plan_execute: null pointer");
+  int r;
+  bp_phase_begin(ctx, BP_PH_HP_TABLE);
+  if ((r = hp_tables(ctx, p->n, th_x, th_y, v_los, map_id, model, status, &p->geom, p->ap_r500,
+                     p->halos, p->tab)))
+    return r;
+  bp_phase_end(ctx, BP_PH_HP_TABLE);
+  bp_phase_begin(ctx, BP_PH_HP_PASTE);
+  r = p->ts == 64 ? hp_launch<64>(ctx, p->halos, p->tab, p->L, p->grid, p->partials, p->counter,
+                                  &p->geom, ymap, bmap, ylo, blo)
+                  : hp_launch<32>(ctx, p->halos, p->tab, p->L, p->grid, p->partials, p->counter,
+                                  &p->geom, ymap, bmap, ylo, blo);
+  bp_phase_end(ctx, BP_PH_HP_PASTE);
+  return r;
+}
+
+int64_t bp_hp_plan_pairs(const bp_hp_plan* p) { return p ? p->L.np : 0; }
+
+int bp_hp_plan_destroy(bp_hp_plan* p) {
+  if (!p) return BP_OK;
+  for (int k = 0; k < 8; ++k)
+    if (p->mem[k]) cudaFree(p->mem[k]);
+  free(p);
+  return BP_OK;
 }
 
 int bp_finalize_map(bp_ctx* ctx, const bp_map_geom* geom, float* ymap, float* bmap, float* ylo,

@@ -74,7 +74,7 @@ struct bp_ctx {
   int* d_flags;
   int64_t* h_pinned;   // pinned host scalars
   int num_sms;
-  int pp_tile, hp_tile, pp_unit;
+  int pp_tile, hp_tile, pp_unit, hp_unit;
   int timing;
   cudaEvent_t ev[BP_NPHASES][2];
   double ph_ms[BP_NPHASES];

@@ -211,16 +211,20 @@ struct Unit {
   int64_t end;
 };
 
+// units per tile, and partial-tile slots (only tiles split into several units need them)
 __global__ void k_unit_count(const int64_t* __restrict__ tstart, int64_t n_tiles, int unit,
-                             uint32_t* ucount) {
+                             uint32_t* ucount, uint32_t* scount) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_tiles) return;
   int64_t len = tstart[t + 1] - tstart[t];
-  ucount[t] = (uint32_t)((len + unit - 1) / unit);
+  uint32_t nu = (uint32_t)((len + unit - 1) / unit);
+  ucount[t] = nu;
+  if (scount) scount[t] = nu > 1 ? nu : 0u;
 }
 
 __global__ void k_unit_emit(const int64_t* __restrict__ tstart, int64_t n_tiles, int unit,
-                            const int64_t* __restrict__ uoff, Unit* units) {
+                            const int64_t* __restrict__ uoff, const int64_t* __restrict__ soff,
+                            Unit* units) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_tiles) return;
   int64_t b = tstart[t], e = tstart[t + 1];
@@ -229,7 +233,7 @@ __global__ void k_unit_emit(const int64_t* __restrict__ tstart, int64_t n_tiles,
   for (int64_t q = 0; q < nu; ++q) {
     Unit U;
     U.tile = (int)t;
-    U.slot = nu > 1 ? (int)(u0 + q) : -1;
+    U.slot = (nu > 1 && soff) ? (int)(soff[t] + q) : -1;
     U.begin = b + q * unit;
     U.end = min(e, b + (q + 1) * unit);
     units[u0 + q] = U;
@@ -468,7 +472,7 @@ __global__ void __launch_bounds__(DEP_THREADS, 2)
 // one CTA per multi-unit tile: add its partial tiles in unit order, then the map
 template <int TS>
 __global__ void __launch_bounds__(256) k_reduce_tiles(const int64_t* __restrict__ tstart,
-                                                      const int64_t* __restrict__ uoff,
+                                                      const int64_t* __restrict__ soff,
                                                       int64_t n_tiles, int unit, int nx, int ny,
                                                       int ntx, const float* __restrict__ partials,
                                                       float* ymap, float* bmap, float* ylo,
@@ -478,7 +482,7 @@ __global__ void __launch_bounds__(256) k_reduce_tiles(const int64_t* __restrict_
   int64_t len = tstart[t + 1] - tstart[t];
   int64_t nu = (len + unit - 1) / unit;
   if (nu <= 1) return;
-  int64_t u0 = uoff[t];
+  int64_t u0 = soff[t];
   int x0 = (int)(t % ntx) * TS, y0 = (int)(t / ntx) * TS;
   for (int q = threadIdx.x; q < TS * TS; q += blockDim.x) {
     int gx = x0 + q % TS, gy = y0 + q / TS;
@@ -558,26 +562,42 @@ int deposit(bp_ctx* ctx, const float* assigned, const bp_map_geom* g, const uint
             const uint32_t* vals, int64_t np, int64_t n_tiles, float* ymap, float* bmap,
             float* ylo, float* blo) {
   const int ntx = (g->nx + TS - 1) / TS;
-  const int unit = ctx->pp_unit;
   int r;
+  // particles per work unit: the context's value, or (auto) about 16 units per
+  // resident CTA, at least 2048
+  int64_t unit64 = ctx->pp_unit;
+  if (unit64 <= 0) {
+    unit64 = np / ((int64_t)ctx->num_sms * 2 * 16);
+    if (unit64 < 2048) unit64 = 2048;
+    if (unit64 > (1 << 30)) unit64 = 1 << 30;
+  }
+  const int unit = (int)unit64;
   int64_t* tstart;
-  if ((r = bp_ws(ctx, WS_TILES, (size_t)(n_tiles + 1) * 8 * 2 + (size_t)(n_tiles + 1) * 4 + 64,
+  if ((r = bp_ws(ctx, WS_TILES, (size_t)(n_tiles + 1) * 8 * 3 + (size_t)(n_tiles + 1) * 8 + 64,
                  (void**)&tstart)))
     return r;
   int64_t* uoff = tstart + (n_tiles + 1);
-  uint32_t* ucount = (uint32_t*)(uoff + (n_tiles + 1));
+  int64_t* soff = uoff + (n_tiles + 1);
+  uint32_t* ucount = (uint32_t*)(soff + (n_tiles + 1));
+  uint32_t* scount = ucount + (n_tiles + 1);
   if ((r = bp_tile_ranges(ctx, keys, np, n_tiles, tstart))) return r;
   unsigned tb = (unsigned)((n_tiles + 255) / 256);
-  k_unit_count<<<tb, 256, 0, ctx->stream>>>(tstart, n_tiles, unit, ucount);
+  k_unit_count<<<tb, 256, 0, ctx->stream>>>(tstart, n_tiles, unit, ucount, scount);
   BP_LAUNCH_CHECK(ctx, "unit count");
   if ((r = bp_scan_u32_to_i64(ctx, ucount, uoff, n_tiles))) return r;
+  if ((r = bp_scan_u32_to_i64(ctx, scount, soff, n_tiles))) return r;
   const int64_t max_units = n_tiles + np / unit + 1;
   Unit* units;
   if ((r = bp_ws(ctx, WS_UNITS, (size_t)max_units * sizeof(Unit), (void**)&units))) return r;
-  k_unit_emit<<<tb, 256, 0, ctx->stream>>>(tstart, n_tiles, unit, uoff, units);
+  k_unit_emit<<<tb, 256, 0, ctx->stream>>>(tstart, n_tiles, unit, uoff, soff, units);
   BP_LAUNCH_CHECK(ctx, "unit emit");
+  // partial tiles exist only for tiles split into several units
+  BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 1, soff + n_tiles, 8, cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  BP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  const int64_t n_slots = ctx->h_pinned[1];
   float* partials;
-  if ((r = bp_ws(ctx, WS_PART, (size_t)max_units * 4 * TS * TS * sizeof(float),
+  if ((r = bp_ws(ctx, WS_PART, (size_t)(n_slots > 0 ? n_slots : 1) * 4 * TS * TS * sizeof(float),
                  (void**)&partials)))
     return r;
   BP_CUDA(ctx, cudaMemsetAsync(ctx->d_counter + 1, 0, sizeof(int64_t), ctx->stream));
@@ -598,9 +618,11 @@ int deposit(bp_ctx* ctx, const float* assigned, const bp_map_geom* g, const uint
   BP_LAUNCH_CHECK(ctx, "deposit");
   bp_phase_end(ctx, BP_PH_DEPOSIT);
   bp_phase_begin(ctx, BP_PH_REDUCE);
-  k_reduce_tiles<TS><<<(unsigned)n_tiles, 256, 0, ctx->stream>>>(
-      tstart, uoff, n_tiles, unit, g->nx, g->ny, ntx, partials, ymap, bmap, ylo, blo);
-  BP_LAUNCH_CHECK(ctx, "reduce tiles");
+  if (n_slots > 0) {
+    k_reduce_tiles<TS><<<(unsigned)n_tiles, 256, 0, ctx->stream>>>(
+        tstart, soff, n_tiles, unit, g->nx, g->ny, ntx, partials, ymap, bmap, ylo, blo);
+    BP_LAUNCH_CHECK(ctx, "reduce tiles");
+  }
   bp_phase_end(ctx, BP_PH_REDUCE);
   return BP_OK;
 }
@@ -627,11 +649,11 @@ int deposit_buffers(bp_ctx* ctx, const float* assigned, const bp_map_geom* g,
   int r;
   if ((r = bp_tile_ranges(ctx, keys, np, n_tiles, B->tstart))) return r;
   unsigned tb = (unsigned)((n_tiles + 255) / 256);
-  k_unit_count<<<tb, 256, 0, ctx->stream>>>(B->tstart, n_tiles, unit, B->ucount);
+  k_unit_count<<<tb, 256, 0, ctx->stream>>>(B->tstart, n_tiles, unit, B->ucount, nullptr);
   BP_LAUNCH_CHECK(ctx, "unit count");
   if ((r = bp_scan_u32_to_i64_buf(ctx, B->ucount, B->uoff, n_tiles, B->bsum))) return r;
   Unit* units = (Unit*)B->units;
-  k_unit_emit<<<tb, 256, 0, ctx->stream>>>(B->tstart, n_tiles, unit, B->uoff, units);
+  k_unit_emit<<<tb, 256, 0, ctx->stream>>>(B->tstart, n_tiles, unit, B->uoff, nullptr, units);
   BP_LAUNCH_CHECK(ctx, "unit emit");
   BP_CUDA(ctx, cudaMemsetAsync(B->counter, 0, sizeof(int64_t), ctx->stream));
   const size_t smem = sizeof(DepSmem<TS>);
