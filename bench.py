@@ -124,6 +124,30 @@ def deposit_flops(rec_np, nx, ny):
     return float(2.0 * np.sum(upd * maps)), float(np.sum(upd))
 
 
+def deposit_flops_device(rec, nx, ny):
+    """deposit_flops computed with torch on the device (for records too large to copy)."""
+    import torch
+
+    ints = rec.view(torch.int32)
+    out_f, out_u = 0.0, 0.0
+    for a in range(0, rec.shape[0], 50_000_000):
+        r = rec[a:a + 50_000_000]
+        iv = ints[a:a + 50_000_000]
+        px = iv[:, 6].double() + r[:, 0].double()
+        py = iv[:, 7].double() + r[:, 1].double()
+        hp = r[:, 2].double()
+        i0, i1 = torch.floor(px - hp), torch.floor(px + hp)
+        j0, j1 = torch.floor(py - hp), torch.floor(py + hp)
+        ok = (iv[:, 5] != 2) & (i1 >= 0) & (i0 <= nx - 1) & (j1 >= 0) & (j0 <= ny - 1)
+        w = i1.clamp(0, nx - 1) - i0.clamp(0, nx - 1) + 1
+        h = j1.clamp(0, ny - 1) - j0.clamp(0, ny - 1) + 1
+        upd = (w * h)[ok]
+        maps = torch.where(r[:, 3][ok] != 0, 2.0, 1.0).double()
+        out_f += float(2.0 * (upd * maps).sum())
+        out_u += float(upd.sum())
+    return out_f, out_u
+
+
 def ncu_traffic(kernel_key):
     """DRAM bytes per launch of a kernel from the committed ncu summary, if it was
     captured on the current source of that kernel (else None)."""
@@ -288,6 +312,7 @@ def batched_section(api, ctx, dev, args):
     maps = api.Maps.zeros(g, dev)
     t0 = time.perf_counter()
     best = autotune.tune_hp(ctx, thx, thy, vl, model, status, g, maps, map_id=mid,
+                            units=(0, 1024), ctas=(0, 2), reps=2,
                             cache_path=os.path.join(ROOT, "gpurun_out", "autotune_hp.json"),
                             use_cache=False)
     tune_s = time.perf_counter() - t0
@@ -330,6 +355,61 @@ def batched_section(api, ctx, dev, args):
             "autotuned": {k: best[k] for k in ("tile", "unit", "ctas_per_sm", "ms")},
             "tune_s": round(tune_s, 2), "solve_s_plain_fp64": round(solve_s, 3),
             "graph_replay": True}
+
+
+def full_scale_section(api, ctx, dev, args, fp32_peak):
+    """The full-scale cone: 5e8 particles, 2e5 halos, 5x5 deg^2 to z = 3, 4096^2 maps."""
+    import torch
+
+    from paper_2201_02632_gb300 import inputs as I
+
+    t0 = time.perf_counter()
+    lc = I.lightcone_device(n_part=args.full_particles, n_halo=args.full_halos, device=dev)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    cat = lc.halos
+    tt = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    M, c, z, pos = tt(cat.M), tt(cat.c), tt(cat.z), tt(cat.pos)
+    n = args.full_particles
+    g = api.geom(lc.geom.nx, lc.geom.ny, lc.geom.theta0_x, lc.geom.theta0_y, lc.geom.dtheta)
+    rec = torch.empty((n, api.ASSIGNED_STRIDE), dtype=torch.float32, device=dev)
+    pp = api.Maps.zeros(g, dev)
+
+    def step():
+        pp.zero_()
+        model, status = ctx.solve_halos(M, c, z, raise_on_noconv=False)
+        ctx.assign_particles(lc.parts, lc.Mp, pos, model, status, g, out=rec)
+        ctx.paste_particles(rec, g, pp)
+        ctx.finalize(g, pp)
+
+    step()
+    torch.cuda.synchronize()
+    flops, updates = deposit_flops_device(rec, g.nx, g.ny)
+    ctx.set_timing(True)
+    ctx.phase_times()
+    ms, phases = [], []
+    for _ in range(args.full_steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        phases.append(ctx.phase_times())
+        ms.append(e0.elapsed_time(e1))
+    ctx.set_timing(False)
+    step_ms = sum(ms) / len(ms)
+    ph = {k: round(sum(p[k] for p in phases) / len(phases), 3) for k in phases[0]}
+    # algorithmic bytes of the streaming phases: assign reads 32 B and writes 32 B per
+    # particle; the pair count reads 32 B per particle
+    assign_gbs = n * 64 / (ph["assign"] * 1e-3) / 1e9 if ph["assign"] > 0 else None
+    dep_tf = flops / (ph["deposit"] * 1e-3) / 1e12 if ph["deposit"] > 0 else None
+    res = {"workload": f"{n} particles, {cat.M.size} halos (dN/dlnM ~ M^-0.9, 1e12-1e15), "
+                       "5x5 deg^2 z 0.05-3, 4096^2 maps", "generate_s": round(gen_s, 2),
+           "ms_per_step": step_ms, "particles_per_s": n / (step_ms * 1e-3), "phase_ms": ph,
+           "deposit_tflops": dep_tf, "deposit_frac_fp32_peak": dep_tf / fp32_peak if dep_tf else None,
+           "pixel_updates": updates, "assign_gbs": assign_gbs}
+    del rec, pp, lc
+    torch.cuda.empty_cache()
+    return res
 
 
 def run_ours(args):
@@ -482,6 +562,8 @@ def run_ours(args):
         res["surrogate"] = surrogate_section(api, ctx, dev, lc, args)
     if not args.no_batched:
         res["batched_hp"] = batched_section(api, ctx, dev, args)
+    if not args.no_full_scale:
+        res["pp_full_scale"] = full_scale_section(api, ctx, dev, args, fp32_peak)
     if not args.no_cpu_baseline and world == 1:
         threads = os.cpu_count() or 1
         t_full, det = oracle_sample(lc, args.ref_particles, args.ref_halos, threads)
@@ -508,6 +590,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-full-scale", action="store_true")
+    ap.add_argument("--full-particles", type=int, default=500_000_000)
+    ap.add_argument("--full-halos", type=int, default=200_000)
+    ap.add_argument("--full-steps", type=int, default=3)
     ap.add_argument("--batch-maps", type=int, default=108)
     ap.add_argument("--batch-halos", type=float, default=5e4)
     ap.add_argument("--batch-npix", type=int, default=2048)

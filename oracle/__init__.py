@@ -120,6 +120,9 @@ def lib():
                 "orc_pp_pairs": (i64, [i64, P, P, P, P, P, P, i32, i32, i32, i32, i32, P, P]),
                 "orc_hp_pairs": (i64, [i64, P, P, P, P, pg, d, i32, i32, P, P]),
                 "orc_energy_residual": (d, [pc, pi, d, d, d, d]),
+                "orc_pp_select": (i64, [pc, i64, P, P, P, P, pg, i64, P, P, P, i32]),
+                "orc_hp_pixels": (None, [pc, pi, i64, P, P, P, P, P, pg, d, d, i64, P, P, P, P, P,
+                                         i32]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -309,3 +312,51 @@ def pp_pairs(ix, fx, iy, fy, hp, kind, nx, ny, tw, th, select=0):
     vals = np.empty(n, np.uint32)
     L.orc_pp_pairs(*args, _p(keys), _p(vals))
     return keys, vals
+
+
+def pp_select(parts: dict, g: Geom, pix_i, pix_j, cp=None, nthreads=0):
+    """Indices of the particles whose kernel support covers one of the pixels."""
+    x, y, z, hs = (_f32(parts[k]) for k in ("x", "y", "z", "hsml"))
+    pi_, pj_ = _i32(pix_i), _i32(pix_j)
+    out = np.empty(x.size, np.int64)
+    m = lib().orc_pp_select(C.byref(cp or cosmo_default()), x.size, _p(x), _p(y), _p(z), _p(hs),
+                            C.byref(g), pi_.size, _p(pi_), _p(pj_), _p(out), int(nthreads))
+    return out[:m]
+
+
+def pp_pixels(parts: dict, Mp_hinv, halo_pos, models, g: Geom, pix_i, pix_j, select=0,
+              nthreads=0):
+    """Sampled pixels of the PP maps (assign + deposit of the particles that reach them)."""
+    idx = pp_select(parts, g, pix_i, pix_j, nthreads=nthreads)
+    sub = {k: np.ascontiguousarray(v[idx]) for k, v in parts.items()}
+    a = pp_assign(sub, Mp_hinv, halo_pos, models, g, nthreads=nthreads)
+    return pp_deposit_pixels(a, g, pix_i, pix_j, select=select, nthreads=nthreads), idx.size
+
+
+def hp_pixels(thx, thy, vlos, models, g: Geom, pix_i, pix_j, pix_m=None, ap_r500=0.0,
+              map_id=None, rtol=1e-9, cp=None, ip=None, nthreads=0):
+    """HP values at listed pixels (map pix_m, column pix_i, row pix_j)."""
+    thx, thy, vlos, models = _f64(thx), _f64(thy), _f64(vlos), _f64(models)
+    mid = None if map_id is None else _i32(map_id)
+    pm = None if pix_m is None else _i32(pix_m)
+    pi_, pj_ = _i32(pix_i), _i32(pix_j)
+    yv, bv = np.zeros(pi_.size), np.zeros(pi_.size)
+    lib().orc_hp_pixels(C.byref(cp or cosmo_default()), C.byref(ip or icm_default()), thx.size,
+                        _p(thx), _p(thy), _p(vlos), _p(mid), _p(models), C.byref(g),
+                        float(ap_r500), float(rtol), pi_.size, _p(pm), _p(pi_), _p(pj_), _p(yv),
+                        _p(bv), int(nthreads))
+    return yv, bv
+
+
+def solve_referenced(M, c, z, hid_subset, cp=None, ip=None, nthreads=0):
+    """Model rows for every halo, solved only for the halos listed in hid_subset (the
+    others get status 1 and are never referenced by the caller)."""
+    nh = np.asarray(M).size
+    models = np.zeros((nh, len(FIELDS)))
+    models[:, F["status"]] = 1
+    h = np.unique(np.asarray(hid_subset))
+    h = h[h >= 0]
+    if h.size:
+        models[h] = solve_halos(np.asarray(M)[h], np.asarray(c)[h], np.asarray(z)[h], cp, ip,
+                                nthreads=nthreads)
+    return models

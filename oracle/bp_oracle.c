@@ -1014,3 +1014,73 @@ double orc_energy_residual(const orc_cosmo* cp, const orc_icm* ip, double M_hinv
   s.Ps = out[OF_PS];
   return f_rese_rf(rf_over_rvir * s.h.rvir, &s);
 }
+
+/* Particles whose kernel support covers at least one of the listed pixels (FP64 spans
+ * as in orc_pp_deposit): a geometric pre-filter so that sampled pixels of a very large
+ * light-cone can be computed from the few particles that reach them.  Writes the
+ * indices (ascending) and returns their count. */
+int64_t orc_pp_select(const orc_cosmo* cp, int64_t n, const float* x, const float* y,
+                      const float* zc, const float* hsml, const orc_geom* g, int64_t npx,
+                      const int32_t* pix_i, const int32_t* pix_j, int64_t* out, int nthreads) {
+  double h = cp->h;
+  char* hit = (char*)calloc((size_t)n, 1);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(static, 65536)
+#endif
+  for (int64_t k = 0; k < n; ++k) {
+    double X = (double)x[k] / h, Yc = (double)y[k] / h, Z = (double)zc[k] / h;
+    double chi = sqrt(X * X + Yc * Yc + Z * Z);
+    if (!(chi > 0)) continue;
+    double px = (atan2(X, Z) - g->theta0_x) / g->dtheta;
+    double py = (atan2(Yc, Z) - g->theta0_y) / g->dtheta;
+    double hp = ((double)hsml[k] / h) / chi / g->dtheta;
+    double i0 = floor(px - hp), i1 = floor(px + hp), j0 = floor(py - hp), j1 = floor(py + hp);
+    for (int64_t q = 0; q < npx; ++q)
+      if (pix_i[q] >= i0 && pix_i[q] <= i1 && pix_j[q] >= j0 && pix_j[q] <= j1) {
+        hit[k] = 1;
+        break;
+      }
+  }
+  (void)nthreads;
+  int64_t m = 0;
+  for (int64_t k = 0; k < n; ++k)
+    if (hit[k]) out[m++] = k;
+  free(hit);
+  return m;
+}
+
+/* HP values at a list of pixels (same arithmetic as orc_hp_map, pixel by pixel). */
+void orc_hp_pixels(const orc_cosmo* cp, const orc_icm* ip, int64_t nh, const double* thx,
+                   const double* thy, const double* vlos, const int32_t* map_id,
+                   const double* models, const orc_geom* g, double ap_r500, double rtol,
+                   int64_t npx, const int32_t* pix_m, const int32_t* pix_i, const int32_t* pix_j,
+                   double* yv, double* bv, int nthreads) {
+  double CP = o_CP(), CN = o_CN(cp);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int64_t q = 0; q < npx; ++q) {
+    double tx = g->theta0_x + (pix_i[q] + 0.5) * g->dtheta;
+    double ty = g->theta0_y + (pix_j[q] + 0.5) * g->dtheta;
+    double sy = 0.0, sb = 0.0;
+    for (int64_t k = 0; k < nh; ++k) {
+      const double* m = models + k * OF_N;
+      if (m[OF_STATUS] != 0) continue;
+      if ((map_id ? map_id[k] : 0) != (pix_m ? pix_m[q] : 0)) continue;
+      double rap = m[OF_RF];
+      if (ap_r500 > 0) rap = fmin(rap, ap_r500 * m[OF_R500]);
+      double dx = tx - thx[k], dy = ty - thy[k];
+      double rperp = m[OF_DA] * sqrt(dx * dx + dy * dy);
+      if (rperp >= rap) continue;
+      o_prof p;
+      o_prof_init(&p, cp, ip, m);
+      sy += CP * o_los_integral(&p, rperp, 0, rtol);
+      sb += CN * (vlos[k] / O_C_KMS) * exp(-m[OF_TAU]) * o_los_integral(&p, rperp, 1, rtol);
+    }
+    yv[q] = sy;
+    bv[q] = sb;
+  }
+  (void)nthreads;
+}

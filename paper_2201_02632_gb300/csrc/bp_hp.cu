@@ -64,6 +64,7 @@ struct HpHalo {
   float inv_rf_px;   // 1 / r_f [px]
   float Ay, Ab;      // amplitude of y and b per unit chord (u = 0 edge chord 1)
   int map, ok;
+  int nt;            // table intervals of this halo (64, 128 or 256, by its size in pixels)
   // profile constants for the tables (same meaning as the PP halo block)
   float xf, c, q500, psi, A0, A1, ant, xnt;  // xnt: r_nt1 / r_s (R_nt = 1) or huge
 };
@@ -88,6 +89,10 @@ __global__ void k_hp_prep(BpParams P, int64_t nh, const double* __restrict__ thx
   H.cy = (thy[k] - g.theta0_y) / g.dtheta;
   H.rad_px = rap / DA / g.dtheta;
   H.inv_rf_px = (float)(px / rf);
+  {
+    double rf_px = rf / px;  // pixels across the table's radius
+    H.nt = rf_px < 32.0 ? 64 : (rf_px < 256.0 ? 128 : HP_NT);
+  }
   double n1T = (P.n_poly + 1.0) * T, GM = bpc::G * F(BP_M_MVIR);
   H.Ay = (float)(P.CP * P.pe_frac * F(BP_M_P0) * 2.0 * rf);
   double vk = vlos ? (double)vlos[k] : 0.0;
@@ -146,16 +151,18 @@ __global__ void __launch_bounds__(256) k_hp_table(const HpHalo* __restrict__ hal
   int node = (int)(gid % (HP_NT + 1));
   if (k >= nh) return;
   const HpHalo H = halos[k];
+  if (node > H.nt) return;
+  const int NTh = H.nt;
   float* ty = tab + k * 2 * HP_ROW;
   float* tb = ty + HP_ROW;
   if (!H.ok) {
     ty[node + 1] = tb[node + 1] = 0.f;
     return;
   }
-  float sn = (float)node / HP_NT;
+  float sn = (float)node / NTh;
   float u = sn * sn;
   float Gy = 0.f, Gb = 0.f;
-  if (node == HP_NT) {  // limit u -> 1: the profile at r_f
+  if (node == NTh) {  // limit u -> 1: the profile at r_f
     float p, d;
     profile_pn(H, H.xf * 0.99999994f, n_poly, n_int, n_nt, p, d);
     Gy = p;
@@ -222,10 +229,11 @@ __global__ void __launch_bounds__(256) k_hp_table(const HpHalo* __restrict__ hal
 __global__ void k_hp_ghosts(const HpHalo* __restrict__ halos, int64_t nh, float* tab) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nh) return;
+  const int nt = halos[k].nt;
   for (int q = 0; q < 2; ++q) {
     float* t = tab + k * 2 * HP_ROW + q * HP_ROW;
     t[0] = t[2];
-    t[HP_NT + 2] = 2.f * t[HP_NT + 1] - t[HP_NT];
+    t[nt + 2] = 2.f * t[nt + 1] - t[nt];
   }
 }
 
@@ -306,11 +314,11 @@ __global__ void k_hp_uemit(const int64_t* __restrict__ tstart, int64_t n_tiles, 
 constexpr int HP_THREADS = 256;
 constexpr int HCH = 32;
 
-__device__ __forceinline__ float catmull(const float* __restrict__ t, float ss) {
-  // t: table row with ghosts; node k (s = k / HP_NT) at t[k + 1]; ss in [0, 1)
-  float x = ss * HP_NT;
+__device__ __forceinline__ float catmull(const float* __restrict__ t, float ss, int nt) {
+  // t: table row with ghosts; node k (s = k / nt) at t[k + 1]; ss in [0, 1)
+  float x = ss * nt;
   int i = (int)x;
-  if (i > HP_NT - 1) i = HP_NT - 1;
+  if (i > nt - 1) i = nt - 1;
   float f = x - (float)i;
   float p0 = __ldg(t + i), p1 = __ldg(t + i + 1), p2 = __ldg(t + i + 2), p3 = __ldg(t + i + 3);
   float f2 = f * f, f3 = f2 * f;
@@ -335,6 +343,7 @@ __global__ void __launch_bounds__(HP_THREADS)
   __shared__ float s_cx[HCH], s_cy[HCH], s_rap2[HCH], s_irf[HCH], s_ay[HCH], s_ab[HCH];
   __shared__ int4 s_box[HCH];
   __shared__ const float* s_tab[HCH];
+  __shared__ int s_nt[HCH];
   __shared__ int64_t s_unit;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int lr = lane >> 3, lc = lane & 7;
@@ -370,6 +379,7 @@ __global__ void __launch_bounds__(HP_THREADS)
         s_ay[tid] = H.Ay;
         s_ab[tid] = H.Ab;
         s_tab[tid] = tab + (int64_t)hk * 2 * HP_ROW;
+        s_nt[tid] = H.nt;
         int i0, i1, j0, j1;
         int4 bx = make_int4(1, 0, 1, 0);
         if (hp_box(H, g, i0, i1, j0, j1)) {
@@ -387,6 +397,7 @@ __global__ void __launch_bounds__(HP_THREADS)
           continue;
         const float hcx = s_cx[k], hcy = s_cy[k], rap2 = s_rap2[k], irf = s_irf[k];
         const float* ty = s_tab[k];
+        const int ntk = s_nt[k];
 #pragma unroll
         for (int r = 0; r < PR; ++r) {
           float dy = (float)(r0 + r) + 0.5f - hcy;
@@ -399,7 +410,7 @@ __global__ void __launch_bounds__(HP_THREADS)
               if (uu < 1.0f) {
                 float chord = sqrtf(fmaxf(0.f, 1.0f - uu * uu));
                 float ss = sqrtf(uu);
-                float gy = catmull(ty, ss), gb = catmull(ty + HP_ROW, ss);
+                float gy = catmull(ty, ss, ntk), gb = catmull(ty + HP_ROW, ss, ntk);
                 kahan_add(hy[r][c], cy_[r][c], s_ay[k] * chord * gy);
                 kahan_add(hb[r][c], cb_[r][c], s_ab[k] * chord * gb);
               }

@@ -304,3 +304,127 @@ def surrogate_halos(n, seed=SEED_BASE + 4):
     prm = np.stack([rng.uniform(*R["eps_star"], n), rng.uniform(*R["f_star"], n),
                     rng.uniform(*R["eps_dm"], n)])
     return M, c, z, prm
+
+
+def lightcone_device(n_part, n_halo, side_deg=5.0, zr=(0.05, 3.0), halo_frac=0.6, npix=4096,
+                     seed=SEED_BASE + 2, mass="powerlaw", n_ngb=64, device="cuda",
+                     chunk=50_000_000):
+    """The light-cone recipe of `lightcone`, drawn with torch's seeded generator on a
+    device so that 1e8-1e9 particles take seconds (the numpy generator would take
+    minutes).  Same distributions; different random streams, so it is its own seeded
+    workload.  Returns a LightCone whose parts are device tensors (halo catalogue on
+    the host)."""
+    import torch
+
+    dev = torch.device(device)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    rng = np.random.default_rng(seed)
+    f32 = torch.float32
+
+    def U(n, lo=0.0, hi=1.0):
+        return torch.rand(n, generator=gen, device=dev, dtype=f32) * (hi - lo) + lo
+
+    ztab, chitab = _chi_table(max(zr[1], 3.0) * 1.2)
+    chi_lo, chi_hi = np.interp(zr, ztab, chitab)
+    half = 0.5 * side_deg * DEG
+    tan_half = math.tan(half)
+    vol = (2 * tan_half) ** 2 * (chi_hi ** 3 - chi_lo ** 3) / 3.0
+
+    def cone(n):
+        out = []
+        got = 0
+        while got < n:
+            m = int((n - got) * 3.2) + 1024
+            zc = chi_hi * U(m) ** (1.0 / 3.0)
+            xx = (U(m) * 2 - 1) * tan_half * zc
+            yy = (U(m) * 2 - 1) * tan_half * zc
+            r = torch.sqrt(xx * xx + yy * yy + zc * zc)
+            ok = (r >= chi_lo) & (r <= chi_hi)
+            pts = torch.stack([xx[ok], yy[ok], zc[ok]], 1)
+            out.append(pts)
+            got += pts.shape[0]
+        return torch.cat(out)[:n]
+
+    # halos (host catalogue, small)
+    if mass == "loguniform":
+        M = 10.0 ** rng.uniform(13.0, 15.0, n_halo)
+    else:
+        M = powerlaw_masses(rng, n_halo)
+    c = _concentration(rng, M)
+    hpos = cone(n_halo).double().cpu().numpy()
+    hz = np.interp(np.linalg.norm(hpos, axis=1), chitab, ztab)
+    thx = np.arctan2(hpos[:, 0], hpos[:, 2])
+    thy = np.arctan2(hpos[:, 1], hpos[:, 2])
+    hv = rng.normal(0.0, 300.0, n_halo).astype(np.float32)
+    n_h = int(round(halo_frac * n_part))
+    share = M / M.sum() * n_h
+    cnt = np.floor(share).astype(np.int64)
+    rem = n_h - int(cnt.sum())
+    if rem > 0:
+        cnt[np.argsort(-(share - cnt), kind="stable")[:rem]] += 1
+    Mp = float(M.sum() / n_h)
+    R = (3.0 * M / (4.0 * math.pi * 200.0 * OMEGA_M * RHO_CRIT0_H2)) ** (1.0 / 3.0)
+    q = rng.uniform(0.5, 1.0, n_halo)
+    s = rng.uniform(0.5, 1.0, n_halo)
+    rot = _rotations(rng, n_halo)
+    n_f = n_part - n_h
+    n_field = n_f / vol
+    h_field = (3.0 * n_ngb / (4.0 * math.pi * n_field)) ** (1.0 / 3.0)
+    td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    c_t, R_t, M_t = td(c.astype(np.float32)), td(R.astype(np.float32)), td(M)
+    sc_t = td((np.stack([np.ones(n_halo), q, s], 1) / np.cbrt(q * s)[:, None]).astype(np.float32))
+    rot_t = td(rot.astype(np.float32))
+    hp_t = td(hpos.astype(np.float32))
+    mc_t = torch.log1p(c_t) - c_t / (1 + c_t)
+    hid_all = torch.repeat_interleave(torch.arange(n_halo, device=dev, dtype=torch.int32),
+                                      td(cnt))
+    X = torch.empty((n_part, 3), dtype=f32, device=dev)
+    HS = torch.empty(n_part, dtype=f32, device=dev)
+    for a in range(0, n_h, chunk):
+        b = min(n_h, a + chunk)
+        hid = hid_all[a:b].long()
+        cc = c_t[hid]
+        u = U(b - a)
+        lo = torch.zeros_like(cc)
+        hi = cc.clone()
+        mcc = mc_t[hid]
+        for _ in range(40):
+            mid = 0.5 * (lo + hi)
+            f = (torch.log1p(mid) - mid / (1 + mid)) / mcc - u
+            neg = f < 0
+            lo = torch.where(neg, mid, lo)
+            hi = torch.where(neg, hi, mid)
+        xr = 0.5 * (lo + hi)  # r / r_s
+        rad = xr / cc * R_t[hid]
+        d = torch.randn((b - a, 3), generator=gen, device=dev, dtype=f32)
+        d = d / torch.linalg.norm(d, dim=1, keepdim=True)
+        off = d * rad[:, None] * sc_t[hid]
+        off = torch.einsum("nij,nj->ni", rot_t[hid], off)
+        X[a:b] = hp_t[hid] + off
+        rs = R_t[hid] / cc
+        rho = M_t[hid].float() / (4 * math.pi * rs ** 3 * mcc) / (xr * (1 + xr) ** 2)
+        HS[a:b] = torch.clamp((3.0 * n_ngb / (4.0 * math.pi * (rho / Mp))) ** (1.0 / 3.0),
+                              max=h_field)
+        del hid, cc, u, lo, hi, mcc, xr, rad, d, off, rs, rho
+    for a in range(n_h, n_part, chunk):
+        b = min(n_part, a + chunk)
+        X[a:b] = cone(b - a)
+        HS[a:b] = h_field
+    HID = torch.full((n_part,), -1, dtype=torch.int32, device=dev)
+    HID[:n_h] = hid_all
+    del hid_all
+    perm = torch.randperm(n_part, generator=gen, device=dev)
+    parts = {}
+    for k, col in (("x", 0), ("y", 1), ("z", 2)):
+        parts[k] = X[:, col][perm].contiguous()
+    del X
+    parts["hsml"] = HS[perm]
+    del HS
+    parts["hid"] = HID[perm]
+    del HID, perm
+    for k in ("vx", "vy", "vz"):
+        parts[k] = torch.randn(n_part, generator=gen, device=dev, dtype=f32) * 300.0
+    cat = HaloCatalog(M, c, hz, thx, thy, hv, pos=hpos.T.astype(np.float32).copy())
+    g = MapGeom(npix, npix, -half, -half, 2 * half / npix)
+    return LightCone(parts, cat, Mp, g, {"h_field": h_field, "n_halo_particles": n_h})

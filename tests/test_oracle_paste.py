@@ -353,3 +353,31 @@ def test_pp_halo_signal_is_monte_carlo_volume_integral(orc):
     sem = terms.std() * math.sqrt(N)
     assert abs(est - ref) < 5 * sem
     assert abs(est / ref - 1) < 0.02
+
+
+def test_sampled_pixels_from_the_prefiltered_particles(orc):
+    """The geometric pre-filter keeps every particle that reaches a sampled pixel: the
+    sampled pixels equal the full deposit there."""
+    lc = I.lightcone(n_part=60000, n_halo=40, npix=96, side_deg=1.0, seed=21)
+    g = orc.geom(96, 96, lc.geom.theta0_x, lc.geom.theta0_y, lc.geom.dtheta)
+    mo = orc.solve_halos(lc.halos.M, lc.halos.c, lc.halos.z)
+    a = orc.pp_assign(lc.parts, lc.Mp, lc.halos.pos, mo, g)
+    yo, bo = orc.pp_deposit(a, g)
+    rng = np.random.default_rng(1)
+    pi_, pj_ = rng.integers(0, 96, 15), rng.integers(0, 96, 15)
+    (yv, bv), m = orc.pp_pixels(lc.parts, lc.Mp, lc.halos.pos, mo, g, pi_, pj_)
+    assert 0 < m < 60000
+    np.testing.assert_allclose(yv, yo[pj_, pi_], rtol=1e-13, atol=1e-25)
+    np.testing.assert_allclose(bv, bo[pj_, pi_], rtol=1e-12, atol=1e-22)
+
+
+def test_hp_pixels_equal_the_map(orc):
+    cat, _ = I.halo_catalog(n=30, npix=64, side_deg=0.4, seed=8)
+    g = orc.geom(64, 64, -0.2 * math.pi / 180, -0.2 * math.pi / 180, 0.4 * math.pi / 180 / 64)
+    mo = orc.solve_halos(cat.M, cat.c, cat.z)
+    ym, bm = orc.hp_map(cat.thx, cat.thy, cat.vlos, mo, g, ap_r500=3.0, rtol=1e-8)
+    rng = np.random.default_rng(3)
+    pi_, pj_ = rng.integers(0, 64, 25), rng.integers(0, 64, 25)
+    yv, bv = orc.hp_pixels(cat.thx, cat.thy, cat.vlos, mo, g, pi_, pj_, ap_r500=3.0, rtol=1e-8)
+    np.testing.assert_allclose(yv, ym[0][pj_, pi_], rtol=1e-13, atol=1e-30)
+    np.testing.assert_allclose(bv, bm[0][pj_, pi_], rtol=1e-13, atol=1e-30)
