@@ -89,10 +89,10 @@ __global__ void k_hp_prep(BpParams P, int64_t nh, const double* __restrict__ thx
   H.cy = (thy[k] - g.theta0_y) / g.dtheta;
   H.rad_px = rap / DA / g.dtheta;
   H.inv_rf_px = (float)(px / rf);
-  {
-    double rf_px = rf / px;  // pixels across the table's radius
-    H.nt = rf_px < 32.0 ? 64 : (rf_px < 256.0 ? 128 : HP_NT);
-  }
+  // Table intervals per halo.  Coarser tables (64 or 128 intervals, 1.6e-5 and 1.4e-6
+  // interpolation error) broke the per-pixel kSZ tolerance where halos of opposite
+  // velocities cancel, so every halo uses the full resolution.
+  H.nt = HP_NT;
   double n1T = (P.n_poly + 1.0) * T, GM = bpc::G * F(BP_M_MVIR);
   H.Ay = (float)(P.CP * P.pe_frac * F(BP_M_P0) * 2.0 * rf);
   double vk = vlos ? (double)vlos[k] : 0.0;
