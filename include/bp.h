@@ -158,6 +158,16 @@ int bp_set_stream(bp_ctx* ctx, void* stream);
  * pp_unit: maximum particles per deposit work unit (>= 256; -1 = automatic, about 16
  * units per resident CTA).  0 keeps a value. */
 int bp_set_tiling(bp_ctx* ctx, int pp_tile, int hp_tile, int pp_unit);
+/* Which kernel performs the PP deposit (Section 3.4, Eqs. f_ij and the integrated
+ * kernel): BP_DEPOSIT_AUTO (the tensor-core kernel when the PP tile is 64, else the
+ * SIMT kernel), BP_DEPOSIT_SIMT (FP32 FMAs on the CUDA cores) or BP_DEPOSIT_TENSOR
+ * (tcgen05 MMAs in split TF32, tile 64 only; BP_EINVAL at paste time with tile 32).
+ * Both sum every pixel in a fixed order with compensated FP32 accumulators; they
+ * differ in the rounding of the products (FP32 against about 1e-6 relative). */
+#define BP_DEPOSIT_AUTO 0
+#define BP_DEPOSIT_SIMT 1
+#define BP_DEPOSIT_TENSOR 2
+int bp_set_deposit_kernel(bp_ctx* ctx, int kind);
 /* Bytes of scratch the context currently holds. */
 int64_t bp_workspace_bytes(const bp_ctx* ctx);
 

@@ -25,6 +25,7 @@ OUT_YB, OUT_DT = 0, 1
 
 # entry points declared in include/bp.h
 EXPORTS = ("bp_create", "bp_destroy", "bp_last_error", "bp_set_stream", "bp_set_tiling",
+           "bp_set_deposit_kernel",
            "bp_workspace_bytes", "bp_set_timing", "bp_phase_times", "bp_kernel_launches",
            "bp_solve_halos", "bp_assign_particles", "bp_paste_particles", "bp_pp_pairs",
            "bp_paste_halos", "bp_finalize_map", "bp_paste_particles_noalloc",
@@ -76,6 +77,7 @@ def load():
                 "bp_last_error": (C.c_char_p, [P]),
                 "bp_set_stream": (i32, [P, P]),
                 "bp_set_tiling": (i32, [P, i32, i32, i32]),
+                "bp_set_deposit_kernel": (i32, [P, i32]),
                 "bp_workspace_bytes": (i64, [P]),
                 "bp_set_timing": (i32, [P, i32]),
                 "bp_phase_times": (i32, [P, C.POINTER(C.c_double), i32]),

@@ -99,6 +99,11 @@ class Context:
     def set_tiling(self, pp_tile=0, hp_tile=0, pp_unit=0):
         self._check(self._L.bp_set_tiling(self._h, pp_tile, hp_tile, pp_unit))
 
+    def set_deposit_kernel(self, kind="auto"):
+        """PP deposit kernel: "auto" (tensor cores with tile 64), "simt" or "tensor"."""
+        code = {"auto": 0, "simt": 1, "tensor": 2}[kind]
+        self._check(self._L.bp_set_deposit_kernel(self._h, code))
+
     def workspace_bytes(self) -> int:
         return int(self._L.bp_workspace_bytes(self._h))
 

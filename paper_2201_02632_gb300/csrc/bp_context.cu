@@ -215,6 +215,7 @@ int bp_create(bp_ctx** out, const bp_cosmology* cosmo, const bp_icm_params* icm,
   ctx->pp_tile = 64;
   ctx->hp_tile = 32;
   ctx->pp_unit = 0;  // automatic
+  ctx->pp_kernel = BP_DEPOSIT_AUTO;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -276,6 +277,14 @@ int bp_set_tiling(bp_ctx* ctx, int pp_tile, int hp_tile, int pp_unit) {
   if (hp_tile) ctx->hp_tile = hp_tile;
   if (pp_unit > 0) ctx->pp_unit = pp_unit;
   if (pp_unit < 0) ctx->pp_unit = 0;  // automatic
+  return BP_OK;
+}
+
+int bp_set_deposit_kernel(bp_ctx* ctx, int kind) {
+  if (!ctx) return BP_EINVAL;
+  if (kind != BP_DEPOSIT_AUTO && kind != BP_DEPOSIT_SIMT && kind != BP_DEPOSIT_TENSOR)
+    return bp_fail(ctx, BP_EINVAL, "bp_set_deposit_kernel: unknown kind %d", kind);
+  ctx->pp_kernel = kind;
   return BP_OK;
 }
 

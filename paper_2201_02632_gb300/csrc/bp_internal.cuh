@@ -75,6 +75,7 @@ struct bp_ctx {
   int64_t* h_pinned;   // pinned host scalars
   int num_sms;
   int pp_tile, hp_tile, pp_unit, hp_unit;
+  int pp_kernel;  // BP_DEPOSIT_*
   int timing;
   cudaEvent_t ev[BP_NPHASES][2];
   double ph_ms[BP_NPHASES];
@@ -188,6 +189,40 @@ __device__ __forceinline__ bool bp_span(int ix, float fx, float h, int n, int& l
   return true;
 }
 
+// Weights of NC consecutive cells of one axis: cell k (relative to the particle's
+// pixel index) spans [k - f, k + 1 - f] in pixel units around the centre.  The edge
+// values use the split form of w (bp_wsplit), the cell holding the centre adds 1.
+// Every deposit kernel takes its weights from here, so they agree bit for bit.
+template <int NC>
+__device__ __forceinline__ void bp_cell_weights(int kbase, float f, float h, float ih,
+                                                float (&w)[NC]) {
+  if (h > 0.f) {
+    float d = __fsub_rn((float)kbase, f);
+    float prev = bp_wsplit_inv(d, ih);
+#pragma unroll
+    for (int j = 0; j < NC; ++j) {
+      int k = kbase + j;
+      float dn = __fsub_rn((float)(k + 1), f);
+      float cur = bp_wsplit_inv(dn, ih);
+      bool centre = (k == 0 && f > 0.f) || (k == -1 && f == 0.f);
+      w[j] = cur - prev + (centre ? 1.f : 0.f);
+      prev = cur;
+    }
+  } else {  // h = 0: nearest grid point
+#pragma unroll
+    for (int j = 0; j < NC; ++j) w[j] = (kbase + j == 0) ? 1.f : 0.f;
+  }
+}
+
+// A deposit work unit: particles [begin, end) of the tile-sorted pair list, all in tile
+// `tile`; slot >= 0 names its partial tile when the tile is split into several units.
+struct BpUnit {
+  int tile;
+  int slot;      // partial slot, -1 = the tile's only unit (adds to the map directly)
+  int64_t begin;
+  int64_t end;
+};
+
 // Error-free sum of two floats (Knuth's TwoSum): s + e == a + b exactly.
 __device__ __forceinline__ void bp_two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
@@ -232,3 +267,13 @@ int bp_pp_paste_buffers(bp_ctx* ctx, int64_t n, const float* assigned, const bp_
                         int select, float* ymap, float* bmap, float* ylo, float* blo,
                         const BpPasteBuffers* buf);
 size_t bp_pp_unit_bytes();
+
+// tensor-core deposit (tile 64): launch over the work units, and the check of its
+// timed-out-wait flag (synchronises the stream)
+int bp_deposit_tc_launch(bp_ctx* ctx, const float* assigned, const uint32_t* vals,
+                         const BpUnit* units, const int64_t* n_units_dev, int64_t* counter,
+                         int64_t max_units, const bp_map_geom* g, float* ymap, float* bmap,
+                         float* ylo, float* blo, float* partials);
+int bp_deposit_tc_check(bp_ctx* ctx);
+// true when the deposit of a paste with tile ts runs on the tensor cores
+bool bp_deposit_uses_tc(const bp_ctx* ctx, int ts);

@@ -204,12 +204,7 @@ __global__ void k_pair_emit(const float4* __restrict__ rec, int64_t n, int nx, i
 }
 
 // ---------------------------------------------------------------- work units
-struct Unit {
-  int tile;
-  int slot;      // partial slot, -1 = the tile's only unit (adds to the map directly)
-  int64_t begin;
-  int64_t end;
-};
+using Unit = BpUnit;
 
 // units per tile, and partial-tile slots (only tiles split into several units need them)
 __global__ void k_unit_count(const int64_t* __restrict__ tstart, int64_t n_tiles, int unit,
@@ -278,29 +273,6 @@ __device__ __forceinline__ void fold_acc(float (&acc)[TS / 16][TS / 16],
       lo[(r0 + r) * TS + c0 + c] += e;
       acc[r][c] = 0.f;
     }
-}
-
-// Weights of SEG consecutive cells of one axis: cell k (relative to the particle's
-// pixel index) spans [k - f, k + 1 - f] in pixel units around the centre.  The edge
-// values use the split form of w (bp_wsplit), the cell holding the centre adds 1.
-__device__ __forceinline__ void segment_weights(int kbase, float f, float h, float ih,
-                                                float (&w)[SEG]) {
-  if (h > 0.f) {
-    float d = __fsub_rn((float)kbase, f);
-    float prev = bp_wsplit_inv(d, ih);
-#pragma unroll
-    for (int j = 0; j < SEG; ++j) {
-      int k = kbase + j;
-      float dn = __fsub_rn((float)(k + 1), f);
-      float cur = bp_wsplit_inv(dn, ih);
-      bool centre = (k == 0 && f > 0.f) || (k == -1 && f == 0.f);
-      w[j] = cur - prev + (centre ? 1.f : 0.f);
-      prev = cur;
-    }
-  } else {  // h = 0: nearest grid point
-#pragma unroll
-    for (int j = 0; j < SEG; ++j) w[j] = (kbase + j == 0) ? 1.f : 0.f;
-  }
 }
 
 template <int TS>
@@ -383,7 +355,7 @@ __global__ void __launch_bounds__(DEP_THREADS, 2)
           for (int j = 0; j < SEG; ++j) wv[j] = 0.f;
         } else {
           const int2 ip = S.pi[k];
-          segment_weights(cb0 - (axis ? ip.y : ip.x), axis ? p.y : p.x, p.z, S.ih[k], wv);
+          bp_cell_weights<SEG>(cb0 - (axis ? ip.y : ip.x), axis ? p.y : p.x, p.z, S.ih[k], wv);
         }
         if (axis == 0) {
           float4* dst = reinterpret_cast<float4*>(&S.a[k][cb0]);
@@ -557,6 +529,31 @@ int build_pairs(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_geom
   return BP_OK;
 }
 
+// the SIMT deposit kernel over the work units (persistent, resident-capacity grid)
+template <int TS>
+int deposit_simt(bp_ctx* ctx, const float* assigned, const bp_map_geom* g, const uint32_t* vals,
+                 const Unit* units, const int64_t* n_units_dev, int64_t* counter,
+                 int64_t max_units, float* ymap, float* bmap, float* ylo, float* blo,
+                 float* partials) {
+  const int ntx = (g->nx + TS - 1) / TS;
+  const size_t smem = sizeof(DepSmem<TS>);
+  BP_CUDA(ctx, cudaFuncSetAttribute(k_deposit<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  int per_sm = 0;
+  BP_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deposit<TS>, DEP_THREADS,
+                                                             smem));
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)ctx->num_sms * per_sm;
+  if (grid > max_units) grid = max_units;
+  bp_phase_begin(ctx, BP_PH_DEPOSIT);
+  k_deposit<TS><<<(unsigned)grid, DEP_THREADS, smem, ctx->stream>>>(
+      reinterpret_cast<const float4*>(assigned), vals, units, n_units_dev, counter, g->nx, g->ny,
+      ntx, ymap, bmap, ylo, blo, partials);
+  BP_LAUNCH_CHECK(ctx, "deposit");
+  bp_phase_end(ctx, BP_PH_DEPOSIT);
+  return BP_OK;
+}
+
 template <int TS>
 int deposit(bp_ctx* ctx, const float* assigned, const bp_map_geom* g, const uint32_t* keys,
             const uint32_t* vals, int64_t np, int64_t n_tiles, float* ymap, float* bmap,
@@ -602,21 +599,18 @@ int deposit(bp_ctx* ctx, const float* assigned, const bp_map_geom* g, const uint
     return r;
   BP_CUDA(ctx, cudaMemsetAsync(ctx->d_counter + 1, 0, sizeof(int64_t), ctx->stream));
   bp_phase_end(ctx, BP_PH_SORT);
-  const size_t smem = sizeof(DepSmem<TS>);
-  BP_CUDA(ctx, cudaFuncSetAttribute(k_deposit<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-  int per_sm = 0;
-  BP_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deposit<TS>, DEP_THREADS,
-                                                             smem));
-  if (per_sm < 1) per_sm = 1;
-  int64_t grid = (int64_t)ctx->num_sms * per_sm;
-  if (grid > max_units) grid = max_units;
-  bp_phase_begin(ctx, BP_PH_DEPOSIT);
-  k_deposit<TS><<<(unsigned)grid, DEP_THREADS, smem, ctx->stream>>>(
-      reinterpret_cast<const float4*>(assigned), vals, units, uoff + n_tiles, ctx->d_counter + 1,
-      g->nx, g->ny, ntx, ymap, bmap, ylo, blo, partials);
-  BP_LAUNCH_CHECK(ctx, "deposit");
-  bp_phase_end(ctx, BP_PH_DEPOSIT);
+  const bool tc = bp_deposit_uses_tc(ctx, TS);
+  if (tc) {
+    bp_phase_begin(ctx, BP_PH_DEPOSIT);
+    if ((r = bp_deposit_tc_launch(ctx, assigned, vals, units, uoff + n_tiles, ctx->d_counter + 1,
+                                  max_units, g, ymap, bmap, ylo, blo, partials)))
+      return r;
+    bp_phase_end(ctx, BP_PH_DEPOSIT);
+  } else {
+    if ((r = deposit_simt<TS>(ctx, assigned, g, vals, units, uoff + n_tiles, ctx->d_counter + 1,
+                              max_units, ymap, bmap, ylo, blo, partials)))
+      return r;
+  }
   bp_phase_begin(ctx, BP_PH_REDUCE);
   if (n_slots > 0) {
     k_reduce_tiles<TS><<<(unsigned)n_tiles, 256, 0, ctx->stream>>>(
@@ -624,6 +618,7 @@ int deposit(bp_ctx* ctx, const float* assigned, const bp_map_geom* g, const uint
     BP_LAUNCH_CHECK(ctx, "reduce tiles");
   }
   bp_phase_end(ctx, BP_PH_REDUCE);
+  if (tc) return bp_deposit_tc_check(ctx);
   return BP_OK;
 }
 
@@ -643,7 +638,6 @@ template <int TS>
 int deposit_buffers(bp_ctx* ctx, const float* assigned, const bp_map_geom* g,
                     const uint32_t* keys, const uint32_t* vals, int64_t np, int64_t n_tiles,
                     float* ymap, float* bmap, float* ylo, float* blo, const BpPasteBuffers* B) {
-  const int ntx = (g->nx + TS - 1) / TS;
   // one work unit per tile: every tile is written straight into the map
   const int unit = 0x7fffffff;
   int r;
@@ -656,25 +650,24 @@ int deposit_buffers(bp_ctx* ctx, const float* assigned, const bp_map_geom* g,
   k_unit_emit<<<tb, 256, 0, ctx->stream>>>(B->tstart, n_tiles, unit, B->uoff, nullptr, units);
   BP_LAUNCH_CHECK(ctx, "unit emit");
   BP_CUDA(ctx, cudaMemsetAsync(B->counter, 0, sizeof(int64_t), ctx->stream));
-  const size_t smem = sizeof(DepSmem<TS>);
-  BP_CUDA(ctx, cudaFuncSetAttribute(k_deposit<TS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)smem));
-  int per_sm = 0;
-  BP_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_deposit<TS>, DEP_THREADS,
-                                                             smem));
-  if (per_sm < 1) per_sm = 1;
-  int64_t grid = (int64_t)ctx->num_sms * per_sm;
-  if (grid > n_tiles) grid = n_tiles;
-  k_deposit<TS><<<(unsigned)grid, DEP_THREADS, smem, ctx->stream>>>(
-      reinterpret_cast<const float4*>(assigned), vals, units, B->uoff + n_tiles, B->counter,
-      g->nx, g->ny, ntx, ymap, bmap, ylo, blo, nullptr);
-  BP_LAUNCH_CHECK(ctx, "deposit");
-  return BP_OK;
+  if (bp_deposit_uses_tc(ctx, TS)) {
+    if ((r = bp_deposit_tc_launch(ctx, assigned, vals, units, B->uoff + n_tiles, B->counter,
+                                  n_tiles, g, ymap, bmap, ylo, blo, nullptr)))
+      return r;
+    return bp_deposit_tc_check(ctx);
+  }
+  return deposit_simt<TS>(ctx, assigned, g, vals, units, B->uoff + n_tiles, B->counter, n_tiles,
+                          ymap, bmap, ylo, blo, nullptr);
 }
 
 }  // namespace
 
 size_t bp_pp_unit_bytes() { return sizeof(Unit); }
+
+bool bp_deposit_uses_tc(const bp_ctx* ctx, int ts) {
+  if (ctx->pp_kernel == BP_DEPOSIT_SIMT) return false;
+  return ts == 64;
+}
 
 // The particle paste with every scratch buffer supplied by the caller.  Reads back the
 // pair count (one host synchronisation) and returns BP_ERANGE if it exceeds max_pairs.
@@ -682,6 +675,8 @@ int bp_pp_paste_buffers(bp_ctx* ctx, int64_t n, const float* assigned, const bp_
                         int select, float* ymap, float* bmap, float* ylo, float* blo,
                         const BpPasteBuffers* B) {
   const int ts = ctx->pp_tile;
+  if (ctx->pp_kernel == BP_DEPOSIT_TENSOR && ts != 64)
+    return bp_fail(ctx, BP_EINVAL, "paste (no allocation): the tensor-core deposit needs tile 64");
   const int ntx = (g->nx + ts - 1) / ts, nty = (g->ny + ts - 1) / ts;
   const int64_t n_tiles = (int64_t)ntx * nty;
   if (n_tiles > B->max_tiles)
@@ -778,6 +773,8 @@ int bp_paste_particles(bp_ctx* ctx, int64_t n, const float* assigned, const bp_m
   if (((uintptr_t)assigned & 15) != 0)
     return bp_fail(ctx, BP_EINVAL, "bp_paste_particles: records must be 16-byte aligned");
   const int ts = ctx->pp_tile;
+  if (ctx->pp_kernel == BP_DEPOSIT_TENSOR && ts != 64)
+    return bp_fail(ctx, BP_EINVAL, "bp_paste_particles: the tensor-core deposit needs tile 64");
   uint32_t *keys, *vals;
   int64_t np, n_tiles;
   if ((r = build_pairs(ctx, n, assigned, geom, select, ts, &keys, &vals, &np, &n_tiles))) return r;

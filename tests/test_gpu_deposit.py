@@ -68,11 +68,14 @@ def _deposit(api, ctx, a, nx, ny, select=0):
     return folded(maps)
 
 
-@pytest.mark.parametrize("tile,unit", [(64, 8192), (64, 256), (32, 4096), (32, 256)])
-def test_deposit_matches_oracle(orc, api, ctx, tile, unit):
+@pytest.mark.parametrize("tile,unit,kernel", [(64, 8192, "tensor"), (64, 256, "tensor"),
+                                              (64, 8192, "simt"), (64, 256, "simt"),
+                                              (32, 4096, "auto"), (32, 256, "auto")])
+def test_deposit_matches_oracle(orc, api, ctx, tile, unit, kernel):
     nx, ny = 200, 130
     a = I.assigned_particles(n=20000, npix=200, hmax=40, margin=30)
     ctx.set_tiling(pp_tile=tile, pp_unit=unit)
+    ctx.set_deposit_kernel(kernel)
     y, b = _deposit(api, ctx, a, nx, ny)
     yo, bo = orc.pp_deposit(orc_deposit_inputs(a), orc.geom(nx, ny, 0.0, 0.0, 1.0))
     assert_map_parity(y[0], yo, what="y")
@@ -116,3 +119,29 @@ def test_deposit_ngp_and_accumulation(api, ctx):
     assert y[6, 2] == 6.0 and y[3, 7] == 10.0 and y.sum() == 16.0
     assert maps.b[0].cpu().numpy()[6, 2] == -2.0
     assert float(maps.ylo.abs().sum()) == 0.0
+
+
+def test_tensor_and_simt_deposits_agree(api, ctx):
+    """Both deposit kernels on one input: wide kernels (many particles per tile, several
+    FP32 accumulation groups, ragged chunk tails) and kSZ signals of both signs."""
+    rng = np.random.default_rng(21)
+    n = 40000
+    a = I.deposit_inputs(rng.uniform(-20, 276, n), rng.uniform(-20, 212, n),
+                         rng.exponential(12.0, n), rng.uniform(0, 1e-6, n),
+                         rng.normal(0, 1e-6, n), rng.integers(0, 2, n))
+    out = {}
+    for kernel in ("simt", "tensor"):
+        ctx.set_deposit_kernel(kernel)
+        out[kernel] = _deposit(api, ctx, a, 256, 192)
+    for m in range(2):
+        s, t = out["simt"][m][0], out["tensor"][m][0]
+        assert np.linalg.norm(t - s) <= 2e-6 * np.linalg.norm(s)
+
+
+def test_tensor_kernel_needs_tile_64(api, ctx):
+    ctx.set_tiling(pp_tile=32)
+    ctx.set_deposit_kernel("tensor")
+    a = I.deposit_inputs([5.0], [5.0], [2.0], [1.0], [1.0], [0])
+    g = api.geom(16, 16, 0.0, 0.0, 1.0)
+    with pytest.raises(RuntimeError, match="tile 64"):
+        ctx.paste_particles(assigned_tensor(a), g, api.Maps.zeros(g))
