@@ -5,17 +5,23 @@
 //   Y[j, i] += sum_k (Y_k wy_k(j)) wx_k(i),     B[j, i] += sum_k (B_k wy_k(j)) wx_k(i),
 // a rank-32 update, i.e. one 128 x 64 x 32 GEMM with the y rows and b rows stacked in M:
 //   A[r, k] = Y_k wy_k(r)  (r < 64),   B_k wy_k(r - 64)  (r >= 64);    Bop[i, k] = wx_k(i).
-// The weights are the FP32 values the SIMT deposit uses (bp_cell_weights).  Products
-// are formed in TF32 with each FP32 operand split into a TF32 head and a TF32 tail,
-// a b ~ ah bh + ah bt + at bh (three MMAs; about 1e-6 relative error per product).
-// Each group of TC_G chunks accumulates in FP32 in tensor memory and is then folded
-// into a compensated (head, tail) pair with TwoSum, also kept in tensor memory.
+// The weights are the FP32 values of the SIMT deposit (the same edge values and
+// differences as bp_cell_weights).  Products are formed in TF32 with each FP32 operand
+// split into a TF32 head and a tail (Veltkamp), a b ~ ah bh + ah bt + at bh (three MMAs;
+// about 1e-6 relative error per product).  Each group of TC_G chunks accumulates in FP32
+// in tensor memory and is then folded into a compensated (head, tail) pair with TwoSum,
+// also kept in tensor memory.
 //
-// CTA: 256 threads, persistent over work units.  Per chunk every thread computes 4 x 4
-// weights (4 particles x 4 cells of one axis) and stores them as 16-byte chunks of the
-// 128-byte-swizzled K-major operand tiles; one thread issues the 12 MMAs
-// (4 K-steps x 3 products) and commits them to the chunk's mbarrier.  Two operand
-// stages: the weights of chunk c + 1 are built while the MMAs of chunk c run.
+// CTA: 256 threads (8 warps), persistent over work units.  Weight pass: warp w takes
+// particles 4w .. 4w + 3 (K slots 4w .. 4w + 3) on both axes; lane l evaluates the
+// kernel at the tile edges l and l + 32 and gets edges l + 1 and l + 33 from its
+// neighbour, so every edge is evaluated once and all lanes of a warp follow one
+// particle.  The weights go to shared memory as the 16-byte chunk (4 particles) of rows
+// l, l + 32 (and 64 + l, 96 + l for A) of the 128-byte-swizzled K-major operand tiles.
+// One thread issues the chunk's 12 MMAs (4 K-steps x 3 products) and commits them to
+// the chunk's mbarrier.  Two operand stages: the weights of chunk c + 1 are built while
+// the MMAs of chunk c run; one CTA barrier per chunk.  A gather warp prepares the
+// particle fields of chunk c + 1 during chunk c from records copied with cp.async.
 //
 // TMEM (256 columns x 128 lanes): D0 = [0, 64), D1 = [64, 128) (accumulators of
 // alternate groups), HI = [128, 192), LO = [192, 256).  Lane r is tile row r of y
@@ -37,6 +43,8 @@ constexpr uint32_t COL_HI = 128, COL_LO = 192;
 constexpr uint32_t TC_WAIT_POLLS = 1u << 26;
 constexpr uint64_t TC_WAIT_NS = 2000000000ull;  // 2 s
 constexpr uint32_t TC_IDESC = bptc::idesc_tf32(128, TC_TS);
+constexpr int GATHER_WARP = 1;  // also prepares the particle fields of the next chunk
+constexpr int ISSUE_TID = 64;   // lane 0 of warp 2 issues the MMAs
 
 struct alignas(1024) TcStage {
   unsigned char a_hi[128 * 128];  // 128 rows x 32 TF32
@@ -47,12 +55,12 @@ struct alignas(1024) TcStage {
 
 struct TcSmem {
   TcStage st[2];
-  float4 raw[2][TC_CH][2];  // records of the current and the next chunk (cp.async)
-  float4 p0[TC_CH];   // fx, fy, hp, Y
-  float p1[TC_CH];    // B
-  float ih[TC_CH];    // 1 / hp (0 when hp == 0)
-  int2 pi[TC_CH];     // pixel index relative to the tile origin
-  int4 box[TC_CH];    // footprint in tile coordinates (i0 > i1: none)
+  float4 raw[2][TC_CH][2];  // raw records of chunks c + 1 and c + 2 (cp.async)
+  // per-particle fields of chunks c and c + 1
+  float4 p0[2][TC_CH];  // fx, fy, hp, Y
+  float p1[2][TC_CH];   // B
+  float ih[2][TC_CH];   // 1 / hp (0 when hp == 0)
+  int2 pi[2][TC_CH];    // pixel index relative to the tile origin
   uint64_t mbar[2];
   int64_t unit;
   uint32_t tmem;
@@ -61,6 +69,44 @@ struct TcSmem {
 
 __device__ __forceinline__ void st_quad(unsigned char* base, int off, const float (&v)[4]) {
   *reinterpret_cast<float4*>(base + off) = make_float4(v[0], v[1], v[2], v[3]);
+}
+
+// per-particle fields of one record (relative to the tile origin x0, y0) into slot b, l
+__device__ __forceinline__ void derive(TcSmem& S, int b, int l, float4 q0, float4 q1, int x0,
+                                       int y0) {
+  S.p0[b][l] = q0;
+  S.p1[b][l] = q1.x;
+  S.ih[b][l] = q0.z > 0.f ? 1.0f / q0.z : 0.f;
+  S.pi[b][l] = make_int2(__float_as_int(q1.z) - x0, __float_as_int(q1.w) - y0);
+}
+
+// Split-form kernel value at tile edge e (the left edge of cell e, ef = (float)e) of a
+// particle at pixel pr + f in tile coordinates (prf = (float)pr): the edge values of
+// bp_cell_weights (ef - prf is exact, and equals (float)(e - pr)).
+__device__ __forceinline__ float edge_value(float ef, float prf, float f, float ih) {
+  return bp_wsplit_inv(__fsub_rn(__fsub_rn(ef, prf), f), ih);
+}
+
+// Weights of cells l and l + 32 of one axis for one particle (every lane of the warp
+// calls this with the same particle).  e64: the edge value at e = 64.
+__device__ __forceinline__ void lane_weights(int l, float lf, int pr, float f, float h,
+                                             float ih, float e64, float& w0, float& w1) {
+  if (h > 0.f) {
+    const float prf = (float)pr;
+    const float a0 = edge_value(lf, prf, f, ih), a1 = edge_value(lf + 32.f, prf, f, ih);
+    const float t0 = __shfl_sync(0xffffffffu, a0, (l + 1) & 31);
+    const float t1 = __shfl_sync(0xffffffffu, a1, (l + 1) & 31);
+    const float n0 = l < 31 ? t0 : t1;   // edge l + 1 (lane 31: edge 32, from lane 0)
+    const float n1 = l < 31 ? t1 : e64;  // edge l + 33
+    const int kc = pr + (f > 0.f ? 0 : -1);  // the cell holding the centre
+    w0 = n0 - a0;
+    w1 = n1 - a1;
+    if (l == kc) w0 += 1.f;
+    if (l + 32 == kc) w1 += 1.f;
+  } else {  // h = 0: nearest grid point
+    w0 = l == pr ? 1.f : 0.f;
+    w1 = l + 32 == pr ? 1.f : 0.f;
+  }
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 2)
@@ -88,13 +134,12 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   const uint32_t tm = S.tmem;
   const uint32_t lanes = tm + ((uint32_t)(32 * (w & 3)) << 16);  // this warp's TMEM lanes
   const uint32_t colh = (uint32_t)(32 * (w >> 2));                // its 32 of the 64 columns
-  // weight-pass role: cells 4 seg .. 4 seg + 3 of one axis for the particles
-  // kq + 8 p (p = 0..3), stored in K slots 4 kq + p (A and B use the same order, and
-  // the eight lanes of a quarter warp read eight consecutive particles)
-  const int kq = tid & 7, seg = (tid >> 3) & 15, axis = tid >> 7;
-  const int cb0 = 4 * seg;
   const int64_t n_units = *n_units_ptr;
   int64_t gissued = 0, gdone = 0;  // chunks issued / waited for by this CTA
+  // this lane's operand chunks: rows l and l + 32 (and 64 + l, 96 + l of A), quad w
+  const int o_r0 = sw128_quad(lane, w), o_r1 = sw128_quad(lane + 32, w);
+  const int o_b0 = sw128_quad(TC_TS + lane, w), o_b1 = sw128_quad(TC_TS + lane + 32, w);
+  const float lane_f = (float)lane;
 
   // waits for chunk gi (global index) to finish its MMAs
   auto wait_chunk = [&](int64_t gi) -> bool {
@@ -153,127 +198,114 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
     const int nchunks = (int)((U.end - U.begin + TC_CH - 1) / TC_CH);
     const int64_t gbase = gissued;
     bool aborted = false;
-    // Record pipeline (threads 0..31, one particle each): the records of chunk c + 1
-    // are copied into raw[(c + 1) & 1] while chunk c is processed; the pair index of
-    // chunk c + 2 is loaded one chunk earlier still.
+    // Record pipeline, run by the gather warp (lane l = particle l of a chunk): during
+    // chunk c it derives the fields of chunk c + 1 from raw[(c + 1) & 1] (copied during
+    // chunk c - 1) and starts the copies of chunk c + 2; pair indices are loaded one
+    // chunk ahead of their copies.  Chunk 0 is gathered synchronously.
     uint32_t pv_next = 0;
-    if (tid < TC_CH) {
-      const int64_t q = U.begin + tid;
+    if (w == GATHER_WARP) {
+      const int64_t q = U.begin + lane;
       if (q < U.end) {
         const uint32_t pv = pvals[q];
-        cp_async16(&S.raw[0][tid][0], rec + 2 * (int64_t)pv);
-        cp_async16(&S.raw[0][tid][1], rec + 2 * (int64_t)pv + 1);
+        derive(S, 0, lane, rec[2 * (int64_t)pv], rec[2 * (int64_t)pv + 1], x0, y0);
+      }
+      if (q + TC_CH < U.end) {
+        const uint32_t pv = pvals[q + TC_CH];
+        cp_async16(&S.raw[1][lane][0], rec + 2 * (int64_t)pv);
+        cp_async16(&S.raw[1][lane][1], rec + 2 * (int64_t)pv + 1);
       }
       cp_async_commit();
-      if (q + TC_CH < U.end) pv_next = pvals[q + TC_CH];
+      if (q + 2 * TC_CH < U.end) pv_next = pvals[q + 2 * TC_CH];
     }
+    __syncthreads();
     for (int c = 0; c < nchunks; ++c) {
       const int64_t gi = gbase + c;
       const int s = (int)(gi & 1);
+      const int b = c & 1;  // field buffer of this chunk
       if (c >= 2) {  // stage s is free once chunk c - 2 is done
         const int cp = c - 2;
         if (wait_chunk(gi - 2) && (cp % TC_G == TC_G - 1)) fold(cp / TC_G);
       }
-      // 1. the chunk's records: derived fields; start the copies of the next chunk
       const int64_t cb = U.begin + (int64_t)c * TC_CH;
       const int nch = (int)min((int64_t)TC_CH, U.end - cb);
-      if (tid < TC_CH) {
+      // 1. weights of particles 4w .. 4w + 3 -> operand stage s
+      TcStage& T = S.st[s];
+      // edge 64 of the 8 (axis, particle) pairs: lane j < 8 evaluates pair j
+      float e64 = 0.f;
+      if (lane < 8) {
+        const int k = 4 * w + (lane & 3), ax = lane >> 2;
+        if (k < nch) {
+          const float4 q = S.p0[b][k];
+          const int2 ip = S.pi[b][k];
+          if (q.z > 0.f)
+            e64 = edge_value((float)TC_TS, (float)(ax ? ip.y : ip.x), ax ? q.y : q.x, S.ih[b][k]);
+        }
+      }
+      float wx0[4], wx1[4], wy0[4], wy1[4], Yk[4], Bk[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) {
+        const int k = 4 * w + p;
+        const float ex = __shfl_sync(0xffffffffu, e64, p);
+        const float ey = __shfl_sync(0xffffffffu, e64, 4 + p);
+        if (k < nch) {  // warp-uniform
+          const float4 q = S.p0[b][k];
+          const int2 ip = S.pi[b][k];
+          const float ih = S.ih[b][k];
+          lane_weights(lane, lane_f, ip.x, q.x, q.z, ih, ex, wx0[p], wx1[p]);
+          lane_weights(lane, lane_f, ip.y, q.y, q.z, ih, ey, wy0[p], wy1[p]);
+          Yk[p] = q.w;
+          Bk[p] = S.p1[b][k];
+        } else {
+          wx0[p] = wx1[p] = wy0[p] = wy1[p] = Yk[p] = Bk[p] = 0.f;
+        }
+      }
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {  // column weights: the B operand
+        float h4[4], l4[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          split_tf32(half ? wx1[p] : wx0[p], h4[p], l4[p]);
+        }
+        st_quad(T.b_hi, half ? o_r1 : o_r0, h4);
+        st_quad(T.b_lo, half ? o_r1 : o_r0, l4);
+      }
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {  // Y and B times row weights: the A operand
+        float hy[4], ly[4], hb[4], lb[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) {
+          const float wv = half ? wy1[p] : wy0[p];
+          split_tf32(__fmul_rn(Yk[p], wv), hy[p], ly[p]);
+          split_tf32(__fmul_rn(Bk[p], wv), hb[p], lb[p]);
+        }
+        st_quad(T.a_hi, half ? o_r1 : o_r0, hy);
+        st_quad(T.a_lo, half ? o_r1 : o_r0, ly);
+        st_quad(T.a_hi, half ? o_b1 : o_b0, hb);
+        st_quad(T.a_lo, half ? o_b1 : o_b0, lb);
+      }
+      // 2. the gather warp prepares chunk c + 1 and starts the copies of chunk c + 2
+      if (w == GATHER_WARP && c + 1 < nchunks) {
         cp_async_wait_all();
-        const float4 q0 = S.raw[c & 1][tid][0];
-        const float4 q1 = S.raw[c & 1][tid][1];
-        const int64_t qn = cb + TC_CH + tid;
-        if (qn < U.end) {
-          cp_async16(&S.raw[(c + 1) & 1][tid][0], rec + 2 * (int64_t)pv_next);
-          cp_async16(&S.raw[(c + 1) & 1][tid][1], rec + 2 * (int64_t)pv_next + 1);
+        const int64_t qn = cb + TC_CH + lane;  // this lane's particle of chunk c + 1
+        if (qn < U.end)
+          derive(S, b ^ 1, lane, S.raw[(c + 1) & 1][lane][0], S.raw[(c + 1) & 1][lane][1], x0,
+                 y0);
+        if (qn + TC_CH < U.end) {
+          cp_async16(&S.raw[c & 1][lane][0], rec + 2 * (int64_t)pv_next);
+          cp_async16(&S.raw[c & 1][lane][1], rec + 2 * (int64_t)pv_next + 1);
         }
         cp_async_commit();
-        if (qn + TC_CH < U.end) pv_next = pvals[qn + TC_CH];
-        S.p0[tid] = q0;
-        S.p1[tid] = q1.x;
-        S.ih[tid] = q0.z > 0.f ? 1.0f / q0.z : 0.f;
-        const int ixp = __float_as_int(q1.z), iyp = __float_as_int(q1.w);
-        S.pi[tid] = make_int2(ixp - x0, iyp - y0);
-        int i0, i1, j0, j1;
-        int4 bx = make_int4(1, 0, 1, 0);
-        if (bp_span(ixp, q0.x, q0.z, nx, i0, i1) && bp_span(iyp, q0.y, q0.z, ny, j0, j1)) {
-          bx.x = max(i0 - x0, 0);
-          bx.y = min(i1 - x0, TC_TS - 1);
-          bx.z = max(j0 - y0, 0);
-          bx.w = min(j1 - y0, TC_TS - 1);
-        }
-        S.box[tid] = bx;  // (tid >= nch: a stale record whose weights are never used)
+        if (qn + 2 * TC_CH < U.end) pv_next = pvals[qn + 2 * TC_CH];
       }
+      fence_proxy_async_smem();
+      tc_fence_before();
       __syncthreads();
       if (S.abort) {
         aborted = true;
         break;
       }
-      // 2. weights -> operand stage s
-      TcStage& T = S.st[s];
-      float wv[4][4];
-#pragma unroll
-      for (int p = 0; p < 4; ++p) {
-        const int k = kq + 8 * p;
-        int lo = 1, hi = 0;
-        if (k < nch) {
-          const int4 bx = S.box[k];
-          lo = axis ? bx.z : bx.x;
-          hi = axis ? bx.w : bx.y;
-        }
-        if (hi < cb0 || lo > cb0 + 3) {
-#pragma unroll
-          for (int j = 0; j < 4; ++j) wv[p][j] = 0.f;
-        } else {
-          const float4 q = S.p0[k];
-          const int2 ip = S.pi[k];
-          bp_cell_weights<4>(cb0 - (axis ? ip.y : ip.x), axis ? q.y : q.x, q.z, S.ih[k],
-                             wv[p]);
-        }
-      }
-      if (axis == 0) {  // column weights: the B operand
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          float h4[4], l4[4];
-#pragma unroll
-          for (int p = 0; p < 4; ++p) {
-            h4[p] = tf32_rna(wv[p][j]);
-            l4[p] = tf32_rna(wv[p][j] - h4[p]);
-          }
-          const int off = sw128_quad(cb0 + j, kq);
-          st_quad(T.b_hi, off, h4);
-          st_quad(T.b_lo, off, l4);
-        }
-      } else {  // Y and B times row weights: the A operand
-        float Yk[4], Bk[4];
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
-          const int k = kq + 8 * p;
-          Yk[p] = k < nch ? S.p0[k].w : 0.f;
-          Bk[p] = k < nch ? S.p1[k] : 0.f;
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          float hy[4], ly[4], hb[4], lb[4];
-#pragma unroll
-          for (int p = 0; p < 4; ++p) {
-            const float vy = Yk[p] * wv[p][j], vb = Bk[p] * wv[p][j];
-            hy[p] = tf32_rna(vy);
-            ly[p] = tf32_rna(vy - hy[p]);
-            hb[p] = tf32_rna(vb);
-            lb[p] = tf32_rna(vb - hb[p]);
-          }
-          const int oy = sw128_quad(cb0 + j, kq), ob = sw128_quad(TC_TS + cb0 + j, kq);
-          st_quad(T.a_hi, oy, hy);
-          st_quad(T.a_lo, oy, ly);
-          st_quad(T.a_hi, ob, hb);
-          st_quad(T.a_lo, ob, lb);
-        }
-      }
-      fence_proxy_async_smem();
-      tc_fence_before();
-      __syncthreads();
       // 3. one thread issues the chunk's MMAs into the group's accumulator
-      if (tid == 0) {
+      if (tid == ISSUE_TID) {
         tc_fence_after();
         const uint32_t ah = smem_u32(T.a_hi), al = smem_u32(T.a_lo);
         const uint32_t bh = smem_u32(T.b_hi), bl = smem_u32(T.b_lo);

@@ -138,40 +138,21 @@ __device__ __forceinline__ float bp_hermitef(const float* v, const float* d, int
 // Integrated normalised kernel in the "split" representation used by the deposit:
 // with e = dx / h, returns w(e) for dx < 0 and w(e) - 1 = -w(-e) for dx >= 0.
 // Differences of these values give pixel weights without cancellation near w = 1.
-// Only the left half of the printed piecewise quartic (x <= 0) is evaluated.
-__device__ __forceinline__ float bp_wsplit(float dx, float h) {
-  float u = -fabsf(dx / h);  // u <= 0
-  float wl;
-  if (u <= -1.0f) {
-    wl = 0.0f;
-  } else if (u <= -0.5f) {
-    float t = 1.0f + u;
-    float t2 = t * t;
-    wl = (2.0f / 3.0f) * t2 * t2;
-  } else {
-    float u2 = u * u;
-    // (4/3)(3/8 + u - 2u^3 - 3/2 u^4) = 1/2 + 4/3 u - 8/3 u^3 - 2 u^4
-    wl = 0.5f + u * ((4.0f / 3.0f) + u2 * (-(8.0f / 3.0f) - 2.0f * u));
-  }
-  return dx < 0.0f ? wl : -wl;
-}
-
-// The same with the reciprocal of h supplied (one multiplication instead of a
-// division per edge).
+// Only the left half of the printed piecewise quartic (x <= 0) is evaluated, at
+// a = min(|e|, 1): the outer piece (2/3)(1 - a)^4 for a >= 1/2 (zero at a = 1) and the
+// inner piece (4/3)(3/8 - a + 2a^3 - (3/2)a^4) = 1/2 - (4/3)a + (8/3)a^3 - 2a^4 below.
+// The sign is applied as a bit operation (dx is never -0 here: it is k - f with k an
+// integer-valued float and f >= 0).
 __device__ __forceinline__ float bp_wsplit_inv(float dx, float inv_h) {
-  float u = -fabsf(dx * inv_h);  // u <= 0
-  float wl;
-  if (u <= -1.0f) {
-    wl = 0.0f;
-  } else if (u <= -0.5f) {
-    float t = 1.0f + u;
-    float t2 = t * t;
-    wl = (2.0f / 3.0f) * t2 * t2;
-  } else {
-    float u2 = u * u;
-    wl = 0.5f + u * ((4.0f / 3.0f) + u2 * (-(8.0f / 3.0f) - 2.0f * u));
-  }
-  return dx < 0.0f ? wl : -wl;
+  const float a = fminf(fabsf(dx * inv_h), 1.0f);
+  const float t = 1.0f - a;
+  const float t2 = t * t;
+  const float wo = (2.0f / 3.0f) * t2 * t2;
+  const float a2 = a * a;
+  const float wi = 0.5f - a * ((4.0f / 3.0f) + a2 * (2.0f * a - (8.0f / 3.0f)));
+  const float wl = a < 0.5f ? wi : wo;
+  // dx >= 0: flip the sign of wl
+  return __int_as_float(__float_as_int(wl) ^ (~__float_as_int(dx) & (int)0x80000000));
 }
 
 // Pixel span of a particle at px = ix + fx with kernel radius h, decided in FP32
@@ -191,21 +172,23 @@ __device__ __forceinline__ bool bp_span(int ix, float fx, float h, int n, int& l
 
 // Weights of NC consecutive cells of one axis: cell k (relative to the particle's
 // pixel index) spans [k - f, k + 1 - f] in pixel units around the centre.  The edge
-// values use the split form of w (bp_wsplit), the cell holding the centre adds 1.
+// values use the split form of w (bp_wsplit_inv), the cell holding the centre adds 1.
 // Every deposit kernel takes its weights from here, so they agree bit for bit.
 template <int NC>
 __device__ __forceinline__ void bp_cell_weights(int kbase, float f, float h, float ih,
                                                 float (&w)[NC]) {
   if (h > 0.f) {
-    float d = __fsub_rn((float)kbase, f);
-    float prev = bp_wsplit_inv(d, ih);
+    // the cell whose left edge is left of the centre and whose right edge is not
+    // (0 <= f < 1): cell 0 when f > 0, cell -1 when f == 0
+    const int kc = f > 0.f ? 0 : -1;
+    const float kb = (float)kbase;  // kb + j is exact for |kbase| < 2^24
+    float prev = bp_wsplit_inv(__fsub_rn(kb, f), ih);
 #pragma unroll
     for (int j = 0; j < NC; ++j) {
-      int k = kbase + j;
-      float dn = __fsub_rn((float)(k + 1), f);
+      float dn = __fsub_rn(__fadd_rn(kb, (float)(j + 1)), f);
       float cur = bp_wsplit_inv(dn, ih);
-      bool centre = (k == 0 && f > 0.f) || (k == -1 && f == 0.f);
-      w[j] = cur - prev + (centre ? 1.f : 0.f);
+      w[j] = cur - prev;
+      if (kbase + j == kc) w[j] += 1.f;
       prev = cur;
     }
   } else {  // h = 0: nearest grid point

@@ -49,6 +49,15 @@ __device__ __forceinline__ float tf32_rna(float x) {
   return __uint_as_float(r);
 }
 
+// FP32 -> TF32 head + tail by Veltkamp splitting with 2^13 + 1: the head keeps 11
+// significant bits (round to nearest, exactly representable in TF32), head + tail == x
+// exactly; the tensor core then drops the tail's bits beyond TF32.  |x| < 2^114.
+__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
+  const float s = __fmul_rn(x, 8193.0f);
+  hi = __fsub_rn(s, __fsub_rn(s, x));
+  lo = __fsub_rn(x, hi);
+}
+
 // ------------------------------------------------------------------ mbarrier
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
