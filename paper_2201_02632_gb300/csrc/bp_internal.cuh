@@ -61,7 +61,8 @@ struct BpParams {
 
 // ---------------------------------------------------------------- context
 enum { WS_COUNTS = 0, WS_OFFS, WS_KEYS0, WS_VALS0, WS_KEYS1, WS_VALS1, WS_HIST, WS_TILES,
-       WS_UNITS, WS_PART, WS_MISC, WS_TABLE, WS_HPAR, WS_MISC2, WS_MISC3, WS_NSLOTS };
+       WS_UNITS, WS_PART, WS_MISC, WS_TABLE, WS_HPAR, WS_MISC2, WS_MISC3, WS_HALO,
+       WS_NSLOTS };
 
 struct bp_ctx {
   BpParams p;

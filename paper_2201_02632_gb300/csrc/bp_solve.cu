@@ -159,9 +159,14 @@ struct Solver {
   const Halo& h;
   double n;     // polytropic index
   int n_int;    // n if integral, else -1
-  // cached region-A nodes ([0, r_vir]) of this lane
+  // this lane's nodes of region A ([0, r_vir], fixed per halo) and of the r_f-dependent
+  // part (region B = [r_vir, r_f] when r_f >= r_vir, else region A cut at r_f):
+  // weight x r^2 and Phi(r) in fixed slots t (node q = lane + 32 t); unused slots have
+  // weight 0 and Phi = Phi0
   double a_r2w[4], a_phi[4];
-  int na;
+  double f_r2w[4], f_phi[4];
+  int a_cnt, f_cnt;  // slots in use (the nodes of a lane fill slots 0 .. cnt - 1)
+  bool full_a;  // r_f >= r_vir: region A is complete and region B follows
 
   __device__ Solver(const Halo& hh, double nn) : h(hh), n(nn) {
     double rn = rint(nn);
@@ -205,18 +210,46 @@ struct Solver {
     b = hi;
     return true;
   }
-  __device__ void cache_region_a(int lane) {
-    na = 0;
-    double xa = h.c;
-    for (int q = lane; q < MAX_PANEL_A * NGL; q += 32) {
-      int p = q / NGL, j = q % NGL;
+  // region A nodes up to x = xa of this lane into the slots (r2w, phi); returns the
+  // slots in use (panels are filled in order, so the used slots come first)
+  __device__ int nodes_a(int lane, double xa, double (&r2w)[4], double (&phi)[4]) const {
+    int cnt = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int q = lane + 32 * t, p = q / NGL, j = q % NGL;
       double a, b;
-      if (!panel_a(p, xa, h.rs, a, b)) continue;
+      r2w[t] = 0.0;
+      phi[t] = h.phi0;
+      if (q >= MAX_PANEL_A * NGL || !panel_a(p, xa, h.rs, a, b)) continue;
       double mid = 0.5 * (a + b), hw = 0.5 * (b - a);
       double r = mid + hw * c_glx[j];
-      a_r2w[na] = hw * c_glw[j] * r * r;
-      a_phi[na] = phi_of(h, r);
-      ++na;
+      r2w[t] = hw * c_glw[j] * r * r;
+      phi[t] = phi_of(h, r);
+      cnt = t + 1;
+    }
+    return cnt;
+  }
+  __device__ void cache_region_a(int lane) { a_cnt = nodes_a(lane, h.c, a_r2w, a_phi); }
+  // the nodes that depend on r_f; call before integrals() whenever r_f changes
+  __device__ void set_rf(double rf, int lane) {
+    full_a = rf >= h.rvir;
+    if (!full_a) {
+      f_cnt = nodes_a(lane, rf / h.rs, f_r2w, f_phi);
+      return;
+    }
+    f_cnt = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int q = lane + 32 * t, p = q / NGL, j = q % NGL;
+      double a, b;
+      f_r2w[t] = 0.0;
+      f_phi[t] = h.phi0;
+      if (q >= MAX_PANEL_B * NGL || !panel_b(p, h.rvir, rf, a, b)) continue;
+      double mid = 0.5 * (a + b), hw = 0.5 * (b - a);
+      double r = mid + hw * c_glx[j];
+      f_r2w[t] = hw * c_glw[j] * r * r;
+      f_phi[t] = -h.GM / r;
+      f_cnt = t + 1;
     }
   }
   __device__ void acc(Sums& s, double r2w, double phi, double inv_n1T) const {
@@ -230,30 +263,18 @@ struct Solver {
     s.Jm += r2w * tm * phi;
     s.Jn += r2w * tn * phi;
   }
-  __device__ Sums integrals(double T, double rf, int lane) const {
+  // gas integrals over [0, r_f] of the r_f last given to set_rf, at temperature T
+  __device__ Sums integrals(double T) const {
     Sums s = {0, 0, 0, 0, 0};
     double inv_n1T = 1.0 / ((n + 1.0) * T);
-    if (rf >= h.rvir) {
-      for (int k = 0; k < na; ++k) acc(s, a_r2w[k], a_phi[k], inv_n1T);
-      for (int q = lane; q < MAX_PANEL_B * NGL; q += 32) {
-        int p = q / NGL, j = q % NGL;
-        double a, b;
-        if (!panel_b(p, h.rvir, rf, a, b)) continue;
-        double mid = 0.5 * (a + b), hw = 0.5 * (b - a);
-        double r = mid + hw * c_glx[j];
-        acc(s, hw * c_glw[j] * r * r, -h.GM / r, inv_n1T);
-      }
-    } else {
-      double xa = rf / h.rs;
-      for (int q = lane; q < MAX_PANEL_A * NGL; q += 32) {
-        int p = q / NGL, j = q % NGL;
-        double a, b;
-        if (!panel_a(p, xa, h.rs, a, b)) continue;
-        double mid = 0.5 * (a + b), hw = 0.5 * (b - a);
-        double r = mid + hw * c_glx[j];
-        acc(s, hw * c_glw[j] * r * r, phi_of(h, r), inv_n1T);
-      }
+    if (full_a) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (t < a_cnt) acc(s, a_r2w[t], a_phi[t], inv_n1T);
     }
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (t < f_cnt) acc(s, f_r2w[t], f_phi[t], inv_n1T);
     s.Im = warp_sum(s.Im);
     s.In = warp_sum(s.In);
     s.Ip = warp_sum(s.Ip);
@@ -385,33 +406,40 @@ __device__ bool halo_setup(const BpParams& P, const BpTables& TB, int64_t n, int
 }
 
 constexpr int SOLVE_WARPS = 4;  // warps per block
+// |R_e| below which the nested iteration hands over to the two-dimensional Newton
+constexpr double NEWTON2D_SWITCH = 1e-3;
 
+// 1. set-up, one thread per halo (the closed forms and 1-D iterations are scalar, so
+// every lane of a warp does useful FP64 work); ok[i] = 1 if halo i goes to the solve
+__global__ void __launch_bounds__(128) k_setup(BpParams P, BpTables TB, int64_t n,
+                                               const double* __restrict__ Mh,
+                                               const double* __restrict__ cc,
+                                               const double* __restrict__ zz, double* model,
+                                               int32_t* status, int64_t* nbad, SolveExtra X,
+                                               Halo* halos, int32_t* ok) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int good = 0;
+  if (!X.only_fallback || status[i] == BP_HALO_FALLBACK) {
+    Halo hs;
+    good = halo_setup(P, TB, n, i, Mh, cc, zz, model, status, nbad, X, hs) ? 1 : 0;
+    if (good) halos[i] = hs;
+  }
+  ok[i] = good;
+}
+
+// 2. the solve: each warp takes hpw prepared halos one after another, lanes over the
+// quadrature nodes
 __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve(
-    BpParams P, BpTables TB, int64_t n, const double* __restrict__ Mh,
-    const double* __restrict__ cc, const double* __restrict__ zz, double* model,
-    int32_t* status, double tol, int64_t* nbad, SolveExtra X, int hpw) {
-  __shared__ Halo sh_h[SOLVE_WARPS][32];
-  __shared__ int sh_ok[SOLVE_WARPS][32];
+    BpParams P, int64_t n, double* model, int32_t* status, double tol, int64_t* nbad,
+    SolveExtra X, int hpw, const Halo* __restrict__ halos, const int32_t* __restrict__ okv) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t base = ((int64_t)blockIdx.x * SOLVE_WARPS + w) * hpw;
   if (base >= n) return;
-  // 1. set-up: lane j prepares halo base + j
-  {
-    const int64_t i = base + lane;
-    int ok = 0;
-    if (lane < hpw && i < n && (!X.only_fallback || status[i] == BP_HALO_FALLBACK)) {
-      Halo hs;
-      ok = halo_setup(P, TB, n, i, Mh, cc, zz, model, status, nbad, X, hs) ? 1 : 0;
-      if (ok) sh_h[w][lane] = hs;
-    }
-    sh_ok[w][lane] = ok;
-  }
-  __syncwarp();
-  // 2. the warp solves the prepared halos one after another, lanes over quadrature nodes
   for (int jj = 0; jj < hpw; ++jj) {
-    if (!sh_ok[w][jj]) continue;
     const int64_t i = base + jj;
-    const Halo h = sh_h[w][jj];
+    if (i >= n || !okv[i]) continue;
+    const Halo h = halos[i];
     const double eps_star = X.prm ? X.prm[i] : P.eps_star;
     const double eps_dm = X.prm ? X.prm[2 * n + i] : P.eps_dm;
     auto put = [&](int f, double v) {
@@ -447,10 +475,11 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve(
     double T = 0, thf = 0, rho0 = 0, F = 1;
     Sums sm;
     int it;
+    S.set_rf(rf, lane);
     for (it = 0; it < 80; ++it) {
       T = Tmin + exp(s);
       thf = 1.0 + (h.phi0 - phif) / ((nn + 1.0) * T);
-      sm = S.integrals(T, rf, lane);
+      sm = S.integrals(T);
       rho0 = h.Ps / (T * S.pw(thf, 2));
       F = log(four_pi * rho0 * sm.In) - lnTarget;
       if (!isfinite(F)) break;
@@ -461,6 +490,8 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve(
       double dFds = (T - Tmin) * (dlr + dli);
       double step = -F / dFds;
       if (!isfinite(step)) step = (F > 0) ? 1.0 : -1.0;
+      // at the rounding floor of the quadrature sum a further step changes nothing
+      if (fabs(F) < 1e-12 && fabs(step) < 1e-14 * fmax(1.0, fabs(s))) break;
       step = fmax(-4.0, fmin(4.0, step));
       double sn = s + step;
       if (isfinite(slo) && isfinite(shi) && !(sn > slo && sn < shi)) sn = 0.5 * (slo + shi);
@@ -511,7 +542,8 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve(
     double phif = phi_of(h, rf);
     double thf = 1.0 + (h.phi0 - phif) / ((nn + 1.0) * T);
     if (!(thf > 0.0)) return d;
-    Sums sm = S.integrals(T, rf, lane);
+    S.set_rf(rf, lane);
+    Sums sm = S.integrals(T);
     double rho0 = h.Ps / (T * S.pw(thf, 2));
     double In = sm.In, Ip = sm.Ip, Im = sm.Im, Jm = sm.Jm, Jn = sm.Jn;
     double Egf = four_pi * rho0 * (1.5 * T * Ip + Jn);
@@ -559,46 +591,65 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve(
   int st = BP_HALO_MAXIT;
   Eval e;
   double rf = exp(v);
-  if (X.guess && Tw > 0.0) {
-    // polish: two-dimensional Newton from the given starting point, one quadrature
-    // evaluation per iteration, steps halved to keep theta(r_f) > 0
-    double u = log(Tw);
-    e.ok = 0;
-    for (int it = 0; it < X.max_outer; ++it) {
+  // Two-dimensional Newton in (u, v) = (ln T, ln r_f), one quadrature evaluation per
+  // iteration, steps halved to keep theta(r_f) > 0.  Returns true when both residuals
+  // are below tol; (e, rf) hold the last evaluated point (e.ok = 0 if it failed).
+  auto newton2d = [&](double u, double& vv, int max_it, Eval& ee, double& rff) -> bool {
+    ee.ok = 0;
+    for (int it = 0; it < max_it; ++it) {
       double T = exp(u);
-      rf = exp(v);
-      Direct d = direct(T, rf);
-      if (!d.ok) { e.ok = 0; break; }
-      e.T = T; e.thf = d.thf; e.rho0 = d.rho0; e.Rm = d.Rm; e.Re = d.Re; e.ok = 1;
-      if (fabs(d.Re) < tol && fabs(d.Rm) < tol) { st = BP_HALO_OK; break; }
+      rff = exp(vv);
+      Direct d = direct(T, rff);
+      if (!d.ok) { ee.ok = 0; return false; }
+      ee.T = T; ee.thf = d.thf; ee.rho0 = d.rho0; ee.Rm = d.Rm; ee.Re = d.Re; ee.ok = 1;
+      if (fabs(d.Re) < tol && fabs(d.Rm) < tol) return true;
       double det = d.J[0][0] * d.J[1][1] - d.J[0][1] * d.J[1][0];
-      if (!(fabs(det) > 0.0) || !isfinite(det)) break;
+      if (!(fabs(det) > 0.0) || !isfinite(det)) return false;
       double du = (-d.Rm * d.J[1][1] + d.Re * d.J[0][1]) / det;
       double dv = (-d.Re * d.J[0][0] + d.Rm * d.J[1][0]) / det;
       double big = fmax(fabs(du), fabs(dv));
       if (big > 0.5) { du *= 0.5 / big; dv *= 0.5 / big; }
       for (int half = 0; half < 20; ++half) {
-        double vn = fmin(fmax(v + dv, vmin), vmax);
+        double vn = fmin(fmax(vv + dv, vmin), vmax);
         double Tmin_n = (phi_of(h, exp(vn)) - h.phi0) / (nn + 1.0);
         if (exp(u + du) > Tmin_n * (1.0 + 1e-12)) break;
         du *= 0.5;
         dv *= 0.5;
       }
       u += du;
-      v = fmin(fmax(v + dv, vmin), vmax);
+      vv = fmin(fmax(vv + dv, vmin), vmax);
     }
+    return false;
+  };
+  if (X.guess && Tw > 0.0) {
+    // polish from the given starting point
+    if (newton2d(log(Tw), v, X.max_outer, e, rf)) st = BP_HALO_OK;
   } else {
   double va = 0, vb = 0, Ra = 0;  // bracket [va, vb] with R(va) R(vb) < 0
   bool have_br = false;
   double vprev = 0, Rprev = 0;
   bool have_prev = false;
   int hits_min = 0, hits_max = 0;
+  bool tried2d = false;
   for (int it = 0; it < X.max_outer; ++it) {
     rf = exp(v);
     e = reduced(rf, Tw);
     if (!e.ok) { st = BP_HALO_MAXIT; break; }
     Tw = e.T;
     if (fabs(e.Re) < tol && fabs(e.Rm) < tol) { st = BP_HALO_OK; break; }
+    if (!tried2d && fabs(e.Re) < NEWTON2D_SWITCH) {
+      // close to the root: finish with the two-dimensional Newton (one quadrature per
+      // step instead of an inner solve per step); on failure continue the nested one
+      tried2d = true;
+      double v2 = v, rf2 = rf;
+      Eval e2;
+      if (newton2d(log(e.T), v2, 8, e2, rf2)) {
+        e = e2;
+        rf = rf2;
+        st = BP_HALO_OK;
+        break;
+      }
+    }
     if (have_prev && ((e.Re > 0) != (Rprev > 0))) {
       have_br = true;
       va = vprev; Ra = Rprev; vb = v;
@@ -644,6 +695,11 @@ static int solve_launch(bp_ctx* ctx, int64_t n, const double* Mvir, const double
                         SolveExtra X, int64_t* n_bad) {
   int r = upload_constants(ctx);
   if (r) return r;
+  Halo* halos;
+  if ((r = bp_ws(ctx, WS_HALO, (size_t)n * (sizeof(Halo) + sizeof(int32_t)) + 64,
+                 (void**)&halos)))
+    return r;
+  int32_t* okv = reinterpret_cast<int32_t*>(halos + n);
   BP_CUDA(ctx, cudaMemsetAsync(ctx->d_counter, 0, sizeof(int64_t), ctx->stream));
   // halos per warp: enough warps to fill the GPU, the rest shared out 1..32 per warp
   int64_t target_warps = (int64_t)ctx->num_sms * 16;
@@ -651,8 +707,11 @@ static int solve_launch(bp_ctx* ctx, int64_t n, const double* Mvir, const double
   int64_t warps = (n + hpw - 1) / hpw;
   int64_t blocks = (warps + SOLVE_WARPS - 1) / SOLVE_WARPS;
   bp_phase_begin(ctx, BP_PH_SOLVE);
+  k_setup<<<(unsigned)((n + 127) / 128), 128, 0, ctx->stream>>>(
+      ctx->p, ctx->t, n, Mvir, c, z, model, status, ctx->d_counter, X, halos, okv);
+  BP_LAUNCH_CHECK(ctx, "k_setup launch");
   k_solve<<<(unsigned)blocks, 32 * SOLVE_WARPS, 0, ctx->stream>>>(
-      ctx->p, ctx->t, n, Mvir, c, z, model, status, tol, ctx->d_counter, X, hpw);
+      ctx->p, n, model, status, tol, ctx->d_counter, X, hpw, halos, okv);
   BP_LAUNCH_CHECK(ctx, "k_solve launch");
   bp_phase_end(ctx, BP_PH_SOLVE);
   BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, ctx->d_counter, sizeof(int64_t),
