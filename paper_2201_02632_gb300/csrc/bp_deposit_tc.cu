@@ -36,7 +36,7 @@ namespace {
 
 constexpr int TC_TS = 64;        // tile side (pixels)
 constexpr int TC_CH = 32;        // particles per chunk: one 128-byte swizzle row of TF32
-constexpr int TC_G = 4;          // chunks per FP32 accumulation group
+constexpr int TC_G = 4;          // chunks per FP32 accumulation group (128 particles)
 constexpr int TC_THREADS = 256;
 constexpr uint32_t TC_COLS = 256;
 constexpr uint32_t COL_HI = 128, COL_LO = 192;
@@ -307,16 +307,17 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
       // 3. one thread issues the chunk's MMAs into the group's accumulator
       if (tid == ISSUE_TID) {
         tc_fence_after();
-        const uint32_t ah = smem_u32(T.a_hi), al = smem_u32(T.a_lo);
-        const uint32_t bh = smem_u32(T.b_hi), bl = smem_u32(T.b_lo);
+        // K-step ks starts 32 bytes further in: + 2 in the address field (bits 0-13; no
+        // carry for shared addresses below 256 KB)
+        const uint64_t dah = desc_sw128(smem_u32(T.a_hi)), dal = desc_sw128(smem_u32(T.a_lo));
+        const uint64_t dbh = desc_sw128(smem_u32(T.b_hi)), dbl = desc_sw128(smem_u32(T.b_lo));
         const uint32_t d = tm + (uint32_t)(((c / TC_G) & 1) * TC_TS);
 #pragma unroll
         for (int ks = 0; ks < TC_CH / 8; ++ks) {
-          const uint64_t dah = desc_sw128(ah + 32 * ks), dal = desc_sw128(al + 32 * ks);
-          const uint64_t dbh = desc_sw128(bh + 32 * ks), dbl = desc_sw128(bl + 32 * ks);
-          mma_tf32(d, dah, dbh, TC_IDESC, (c % TC_G != 0 || ks > 0) ? 1u : 0u);
-          mma_tf32(d, dah, dbl, TC_IDESC, 1u);
-          mma_tf32(d, dal, dbh, TC_IDESC, 1u);
+          const uint64_t o = (uint64_t)(2 * ks);
+          mma_tf32(d, dah + o, dbh + o, TC_IDESC, (c % TC_G != 0 || ks > 0) ? 1u : 0u);
+          mma_tf32(d, dah + o, dbl + o, TC_IDESC, 1u);
+          mma_tf32(d, dal + o, dbh + o, TC_IDESC, 1u);
         }
         mma_commit(&S.mbar[s]);
       }
