@@ -90,6 +90,53 @@ __device__ __forceinline__ float split_pixel(double p, int& ip) {
   return f;
 }
 
+// Sky angle atan2(x, z) of a particle and its pixel coordinate (theta - theta0) / dtheta
+// = ip + f (0 <= f < 1) in double-float FP32 arithmetic (pairs hi + lo), for
+// 0 < |x| <= z / 16 (flat-sky maps up to about 7 deg wide; returns false otherwise).
+// t = x / z is the FP32 quotient q plus the exact FMA remainder over z; atan(t) = t - t^3/3
+// + t^5/5 - ..., with the cubic term in double-float (its FP32 rounding alone would be
+// 4e-13 rad at t = 1/16) and the higher terms in FP32.  theta0 and 1/dtheta come as FP32
+// pairs.  Error about 1e-8 pixel.
+__device__ __forceinline__ bool pixel_fast(float x, float z, float rz, float th0_hi,
+                                           float th0_lo, float inv_hi, float inv_lo, int& ip,
+                                           float& f) {
+  if (!(z > 0.f) || !(fabsf(x) <= 0.0625f * z)) return false;
+  const float q = __fdiv_rn(x, z);
+  const float tl = fmaf(-q, z, x) * rz;  // the exact remainder over z
+  const float q2 = __fmul_rn(q, q), q2e = fmaf(q, q, -q2);
+  const float q3 = __fmul_rn(q2, q), q3e = fmaf(q2, q, -q3) + q2e * q;
+  const float c = __fdiv_rn(-q3, 3.0f);
+  const float ce = fmaf(-3.0f, c, -q3) * (1.0f / 3.0f);  // (-q3 - 3c) is exact
+  const float tail =
+      q3 * q2 *
+      (0.2f + q2 * (-1.0f / 7.0f + q2 * (1.0f / 9.0f + q2 * (-1.0f / 11.0f + q2 * (1.0f / 13.0f)))));
+  float s, e;
+  bp_two_sum(q, c, s, e);  // theta = s + lo
+  const float lo = e + ((tl + ce) - q3e * (1.0f / 3.0f) + tail);
+  float d, de;
+  bp_two_sum(s, -th0_hi, d, de);
+  const float dl = (de + lo) - th0_lo;  // theta - theta0 = d + dl
+  const float p = __fmul_rn(d, inv_hi);
+  const float pe = fmaf(d, inv_hi, -p) + (d * inv_lo + dl * inv_hi);
+  float fl = floorf(p);
+  float fr = (p - fl) + pe;  // pe is a few ulps of p: fr in (-1, 2)
+  if (fr < 0.f) {
+    fl -= 1.f;
+    fr += 1.f;  // may round up to 1 when fr was a tiny negative
+    if (fr >= 1.f) {
+      fl += 1.f;
+      fr = 0.f;
+    }
+  } else if (fr >= 1.f) {
+    fl += 1.f;
+    fr -= 1.f;  // exact
+  }
+  if (!(fabsf(fl) < 1073741824.f)) return false;
+  ip = (int)fl;
+  f = fr;
+  return true;
+}
+
 struct AssignArgs {
   const float *x, *y, *z, *vx, *vy, *vz, *hs;
   const int32_t* hid;
@@ -97,6 +144,7 @@ struct AssignArgs {
   const float* blk;
   int64_t n, nh;
   double th0x, th0y, inv_dth;
+  float th0x_hi, th0x_lo, th0y_hi, th0y_lo, inv_hi, inv_lo;  // FP32 pairs of the above
   float inv_h;        // 1/h (h^-1 Mpc -> Mpc)
   float inv_h_dth;    // 1/(h dtheta)
   float inv_om_pix;   // 1/dtheta^2
@@ -111,11 +159,14 @@ __global__ void __launch_bounds__(256) k_assign(AssignArgs a, BpTables T) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   float xf = a.x[i], yf = a.y[i], zf = a.z[i];
-  // sky angles and pixel coordinates in FP64
-  double thx = atan2((double)xf, (double)zf), thy = atan2((double)yf, (double)zf);
+  // sky angles and pixel coordinates: double-float FP32 near the axis, else FP64
   int ix, iy;
-  float fx = split_pixel((thx - a.th0x) * a.inv_dth, ix);
-  float fy = split_pixel((thy - a.th0y) * a.inv_dth, iy);
+  float fx, fy;
+  const float rz = 1.0f / zf;
+  if (!pixel_fast(xf, zf, rz, a.th0x_hi, a.th0x_lo, a.inv_hi, a.inv_lo, ix, fx))
+    fx = split_pixel((atan2((double)xf, (double)zf) - a.th0x) * a.inv_dth, ix);
+  if (!pixel_fast(yf, zf, rz, a.th0y_hi, a.th0y_lo, a.inv_hi, a.inv_lo, iy, fy))
+    fy = split_pixel((atan2((double)yf, (double)zf) - a.th0y) * a.inv_dth, iy);
   float r2 = xf * xf + yf * yf + zf * zf;
   float rh = sqrtf(r2);       // comoving h^-1 Mpc
   float chi = rh * a.inv_h;   // comoving Mpc
@@ -743,6 +794,13 @@ int bp_assign_particles(bp_ctx* ctx, int64_t n, const float* x, const float* y, 
   a.th0x = geom->theta0_x;
   a.th0y = geom->theta0_y;
   a.inv_dth = 1.0 / geom->dtheta;
+  auto split = [](double v, float& hi, float& lo) {
+    hi = (float)v;
+    lo = (float)(v - (double)hi);
+  };
+  split(a.th0x, a.th0x_hi, a.th0x_lo);
+  split(a.th0y, a.th0y_hi, a.th0y_lo);
+  split(a.inv_dth, a.inv_hi, a.inv_lo);
   a.inv_h = (float)(1.0 / P.h);
   a.inv_h_dth = (float)(1.0 / (P.h * geom->dtheta));
   a.inv_om_pix = (float)(1.0 / (geom->dtheta * geom->dtheta));
