@@ -95,3 +95,18 @@ def test_halo_field_split_adds_up(api, ctx, cone):
     np.testing.assert_allclose(res[0][1], res[1][1] + res[2][1], rtol=1e-4,
                                atol=1e-6 * np.abs(res[0][1]).max())
     assert np.all(res[2][0] == 0)
+
+
+def test_sky_pixels_wide_fine_map(orc, api, ctx):
+    """Pixel coordinates on a 10 x 10 deg^2, 4096^2 map: the double-float FP32 angles near
+    the axis and the FP64 angles beyond 3.6 deg off axis both agree with the oracle."""
+    lc = I.lightcone(n_part=200000, n_halo=100, npix=4096, side_deg=10.0, seed=78)
+    p = lc.parts
+    off = np.abs(p["x"]) > p["z"] / 16
+    assert off.mean() > 0.1 and (~off).mean() > 0.1  # both paths are exercised
+    mo = orc.solve_halos(lc.halos.M, lc.halos.c, lc.halos.z)
+    a = orc.pp_assign(p, lc.Mp, lc.halos.pos, mo, orc_geom(orc, lc.geom))
+    rec, _ = _gpu_assign(api, ctx, lc)
+    r = records_numpy(rec)
+    np.testing.assert_allclose(r["px"], a["px"], rtol=0, atol=2e-7)
+    np.testing.assert_allclose(r["py"], a["py"], rtol=0, atol=2e-7)
