@@ -11,6 +11,12 @@
 // condition is driven to zero by safeguarded Newton in ln r_f with the exact
 // derivative of the reduced problem.  The gas integrals over [0, r_f] are
 // composite 16-point Gauss-Legendre rules whose nodes are spread over the lanes.
+//
+// Kernels: k_setup (the scalar set-up, one thread per halo), k_presolve (the reduced
+// problem in FP32 to residuals of ~1e-4: starting points), k_solve (FP64: a
+// two-dimensional Newton in (ln T, ln r_f) from the starting point, one quadrature per
+// step, to the tolerance; the nested iteration for halos without one), then k_setup +
+// k_solve again, nested, for halos the Newton did not bring in (the fallback).
 #include <algorithm>
 #include <vector>
 
@@ -23,6 +29,8 @@
 __constant__ double c_glx[NGL];
 __constant__ double c_glw[NGL];
 __constant__ double c_li2[16];  // B_2m / (2m+1)!, m = 1..15
+__constant__ float c_glxf[NGL];  // the same rule in FP32 (pre-solve)
+__constant__ float c_glwf[NGL];
 
 namespace {
 
@@ -73,6 +81,13 @@ int upload_constants(bp_ctx* ctx) {
   BP_CUDA(ctx, cudaMemcpyToSymbol(c_glx, x, sizeof(x)));
   BP_CUDA(ctx, cudaMemcpyToSymbol(c_glw, w, sizeof(w)));
   BP_CUDA(ctx, cudaMemcpyToSymbol(c_li2, li2, sizeof(li2)));
+  float xf[NGL], wf[NGL];
+  for (int k = 0; k < NGL; ++k) {
+    xf[k] = (float)x[k];
+    wf[k] = (float)w[k];
+  }
+  BP_CUDA(ctx, cudaMemcpyToSymbol(c_glxf, xf, sizeof(xf)));
+  BP_CUDA(ctx, cudaMemcpyToSymbol(c_glwf, wf, sizeof(wf)));
   g_const_ready = true;
   return BP_OK;
 }
@@ -432,7 +447,8 @@ __global__ void __launch_bounds__(128) k_setup(BpParams P, BpTables TB, int64_t 
 // quadrature nodes
 __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve(
     BpParams P, int64_t n, double* model, int32_t* status, double tol, int64_t* nbad,
-    SolveExtra X, int hpw, const Halo* __restrict__ halos, const int32_t* __restrict__ okv) {
+    int64_t* nfallback, SolveExtra X, int hpw, const Halo* __restrict__ halos,
+    const int32_t* __restrict__ okv) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t base = ((int64_t)blockIdx.x * SOLVE_WARPS + w) * hpw;
   if (base >= n) return;
@@ -449,6 +465,7 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve(
       if (lane == 0) {
         status[i] = st;
         if (st != BP_HALO_OK) atomicAdd((unsigned long long*)nbad, 1ull);
+        if (st == BP_HALO_FALLBACK) atomicAdd((unsigned long long*)nfallback, 1ull);
       }
     };
   const double nn = P.n_poly;
@@ -688,19 +705,291 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve(
   }
 }
 
+// ---------------------------------------------------------------- FP32 pre-solve
+// Starting points for the FP64 solve: the same reduced problem (T from the gas-mass
+// condition at each r_f, Newton in ln r_f on the energy condition) in FP32, to
+// residuals of about 1e-4 (FP32 runs at many times the FP64 rate on this GPU).  The
+// FP64 two-dimensional Newton of k_solve then takes the starting point to the
+// tolerance; a halo the pre-solve cannot bring in gets no starting point (NaN) and the
+// full FP64 iteration.
+struct HaloF {
+  float c, rvir, rs, mc, phi0, GM, M;
+};
+
+__device__ __forceinline__ float m_of_f(float x) {  // ln(1+x) - x/(1+x)
+  if (x < 1e-2f) {
+    float x2 = x * x;
+    return x2 * (0.5f - x * (2.0f / 3.0f - x * (0.75f - x * 0.8f)));
+  }
+  return log1pf(x) - x / (1.0f + x);
+}
+__device__ __forceinline__ float phi_of_f(const HaloF& h, float r) {
+  if (r > h.rvir) return -h.GM / r;
+  float x = r / h.rs;
+  float l = (x < 1e-4f) ? (1.0f - 0.5f * x) / h.rs : log1pf(x) / r;
+  return -(h.GM / h.mc) * (l - h.c / ((1.0f + h.c) * h.rvir));
+}
+__device__ __forceinline__ float menc_of_f(const HaloF& h, float r) {
+  return r >= h.rvir ? h.M : h.M * m_of_f(r / h.rs) / h.mc;
+}
+__device__ __forceinline__ float warp_sum_f(float v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+struct SumsF {
+  float Im, In, Ip, Jm, Jn;
+};
+
+// FP32 counterpart of Solver: the same panels and node slots
+struct SolverF {
+  const HaloF& h;
+  int n_int;
+  float n;
+  float a_r2w[4], a_phi[4], f_r2w[4], f_phi[4];
+  int a_cnt, f_cnt;
+  bool full_a;
+
+  __device__ SolverF(const HaloF& hh, float nn, int ni) : h(hh), n_int(ni), n(nn) {}
+  __device__ float pw(float th, int k_off) const {  // theta^{n - 1 + k_off}
+    if (n_int > 0) {
+      int e = n_int - 1 + k_off;
+      float r = 1.0f, b = th;
+      while (e) {
+        if (e & 1) r *= b;
+        b *= b;
+        e >>= 1;
+      }
+      return r;
+    }
+    return powf(th, n - 1.0f + k_off);
+  }
+  __device__ int nodes_a(int lane, float xa, float (&r2w)[4], float (&phi)[4]) const {
+    int cnt = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int q = lane + 32 * t, p = q / NGL, j = q % NGL;
+      r2w[t] = 0.f;
+      phi[t] = h.phi0;
+      if (q >= MAX_PANEL_A * NGL) continue;
+      float lo = 0.f, hi = fminf(0.5f, xa);
+      bool ok = hi > lo;
+      for (int k = 0; k < p && ok; ++k) {
+        if (hi >= xa) ok = false;
+        lo = hi;
+        hi = fminf(2.5f * hi, xa);
+      }
+      if (!ok || !(hi > lo)) continue;
+      float a = lo * h.rs, b = hi * h.rs;
+      float mid = 0.5f * (a + b), hw = 0.5f * (b - a);
+      float r = mid + hw * c_glxf[j];
+      r2w[t] = hw * c_glwf[j] * r * r;
+      phi[t] = phi_of_f(h, r);
+      cnt = t + 1;
+    }
+    return cnt;
+  }
+  __device__ void cache_region_a(int lane) { a_cnt = nodes_a(lane, h.c, a_r2w, a_phi); }
+  __device__ void set_rf(float rf, int lane) {
+    full_a = rf >= h.rvir;
+    if (!full_a) {
+      f_cnt = nodes_a(lane, rf / h.rs, f_r2w, f_phi);
+      return;
+    }
+    f_cnt = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int q = lane + 32 * t, p = q / NGL, j = q % NGL;
+      f_r2w[t] = 0.f;
+      f_phi[t] = h.phi0;
+      if (q >= MAX_PANEL_B * NGL) continue;
+      float lo = h.rvir, hi = fminf(2.0f * h.rvir, rf);
+      bool ok = true;
+      for (int k = 0; k < p && ok; ++k) {
+        if (hi >= rf) ok = false;
+        lo = hi;
+        hi = fminf(2.0f * hi, rf);
+      }
+      if (!ok || !(hi > lo)) continue;
+      float mid = 0.5f * (lo + hi), hw = 0.5f * (hi - lo);
+      float r = mid + hw * c_glxf[j];
+      f_r2w[t] = hw * c_glwf[j] * r * r;
+      f_phi[t] = -h.GM / r;
+      f_cnt = t + 1;
+    }
+  }
+  __device__ void acc(SumsF& s, float r2w, float phi, float inv_n1T) const {
+    float th = 1.0f + (h.phi0 - phi) * inv_n1T;
+    if (th <= 0.0f) return;
+    float tm = pw(th, 0);
+    float tn = tm * th, tp = tn * th;
+    s.Im += r2w * tm;
+    s.In += r2w * tn;
+    s.Ip += r2w * tp;
+    s.Jm += r2w * tm * phi;
+    s.Jn += r2w * tn * phi;
+  }
+  __device__ SumsF integrals(float T) const {
+    SumsF s = {0, 0, 0, 0, 0};
+    float inv_n1T = 1.0f / ((n + 1.0f) * T);
+    if (full_a) {
+#pragma unroll
+      for (int t = 0; t < 4; ++t)
+        if (t < a_cnt) acc(s, a_r2w[t], a_phi[t], inv_n1T);
+    }
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+      if (t < f_cnt) acc(s, f_r2w[t], f_phi[t], inv_n1T);
+    s.Im = warp_sum_f(s.Im);
+    s.In = warp_sum_f(s.In);
+    s.Ip = warp_sum_f(s.Ip);
+    s.Jm = warp_sum_f(s.Jm);
+    s.Jn = warp_sum_f(s.Jn);
+    return s;
+  }
+};
+
+// guess[i] = ln(r_f / r_vir), guess[n + i] = ln(T r_vir / (G M)), or NaN
+__global__ void __launch_bounds__(32 * SOLVE_WARPS) k_presolve(
+    BpParams P, int64_t n, SolveExtra X, int hpw, const Halo* __restrict__ halos,
+    const int32_t* __restrict__ okv, double* guess) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t base = ((int64_t)blockIdx.x * SOLVE_WARPS + w) * hpw;
+  if (base >= n) return;
+  const float nn = (float)P.n_poly;
+  const double rn = rint(P.n_poly);
+  const int n_int = (fabs(P.n_poly - rn) < 1e-12 && rn >= 1 && rn <= 16) ? (int)rn : -1;
+  for (int jj = 0; jj < hpw; ++jj) {
+    const int64_t i = base + jj;
+    if (i >= n) break;
+    float g0 = __int_as_float(0x7fc00000), g1 = g0;
+    if (okv[i]) {
+      const Halo H = halos[i];
+      const HaloF h = {(float)H.c, (float)H.rvir, (float)H.rs, (float)H.mc, (float)H.phi0,
+                       (float)H.GM, (float)H.M};
+      const double eps_star = X.prm ? X.prm[i] : P.eps_star;
+      const double eps_dm = X.prm ? X.prm[2 * n + i] : P.eps_dm;
+      const float fbM = (float)(P.fb * H.M), Mstar = (float)H.Mstar, Ps = (float)H.Ps;
+      const float inj = (float)(eps_dm * fabs(H.Edm) + eps_star * H.Mstar * bpc::C_KMS * bpc::C_KMS);
+      const float Egi = (float)H.Egi, absE = fabsf(Egi);
+      const float r3v = h.rvir * h.rvir * h.rvir;
+      const float four_pi = (float)(4.0 * bpc::PI);
+      const float lnTarget = logf(fbM - Mstar);
+      SolverF S(h, nn, n_int);
+      S.cache_region_a(lane);
+      // reduced problem at r_f: T from the gas-mass condition, then R_e and dR_e/dln r_f
+      float T = 0.f, Re = 1.f, dRe = 0.f;
+      auto reduced = [&](float rf, float T0) -> bool {
+        const float phif = phi_of_f(h, rf);
+        const float Tmin = (phif - h.phi0) / (nn + 1.0f);
+        if (!(Tmin > 0.f)) return false;
+        float s = (T0 > Tmin * 1.0001f) ? logf(T0 - Tmin) : logf(Tmin + 0.5f * h.GM / h.rvir);
+        float slo = -INFINITY, shi = INFINITY, thf = 0.f, rho0 = 0.f, F = 1.f;
+        SumsF sm;
+        S.set_rf(rf, lane);
+        for (int it = 0; it < 40; ++it) {
+          T = Tmin + expf(s);
+          thf = 1.0f + (h.phi0 - phif) / ((nn + 1.0f) * T);
+          sm = S.integrals(T);
+          rho0 = Ps / (T * S.pw(thf, 2));
+          F = logf(four_pi * rho0 * sm.In) - lnTarget;
+          if (!isfinite(F)) return false;
+          if (fabsf(F) < 1e-5f) break;  // near the FP32 floor of F
+          if (F > 0) slo = s; else shi = s;
+          const float dlr = (-1.0f - (nn + 1.0f) * (1.0f - thf) / thf) / T;
+          const float dli = nn * (sm.Im - sm.In) / (T * sm.In);
+          float step = -F / ((T - Tmin) * (dlr + dli));
+          if (!isfinite(step)) step = (F > 0) ? 1.0f : -1.0f;
+          step = fmaxf(-4.0f, fminf(4.0f, step));
+          float sn = s + step;
+          if (isfinite(slo) && isfinite(shi) && !(sn > slo && sn < shi)) sn = 0.5f * (slo + shi);
+          s = sn;
+        }
+        if (!(fabsf(F) < 1e-4f)) return false;
+        const float In = sm.In, Ip = sm.Ip, Im = sm.Im, Jm = sm.Jm, Jn = sm.Jn;
+        const float Egf = four_pi * rho0 * (1.5f * T * Ip + Jn);
+        const float dEp = four_pi / 3.0f * (r3v - rf * rf * rf) * Ps;
+        const float num = (P.energy_sign == 0) ? (Egf - Egi - inj - dEp) : (Egi - Egf - inj - dEp);
+        Re = num / absE;
+        const float dphif = (float)bpc::G * menc_of_f(h, rf) / (rf * rf);
+        const float dthf_drf = -dphif / ((nn + 1.0f) * T);
+        const float dlr_drf = -(nn + 1.0f) * dthf_drf / thf;
+        const float dlr_dT = (-1.0f - (nn + 1.0f) * (1.0f - thf) / thf) / T;
+        const float tfn = S.pw(thf, 1), tfp = tfn * thf;
+        const float dG_drf = four_pi * rho0 * (In * dlr_drf + tfn * rf * rf);
+        const float dG_dT = four_pi * rho0 * (In * dlr_dT + nn * (Im - In) / T);
+        const float dT_drf = -dG_drf / dG_dT;
+        const float dIp_dT = (nn + 1.0f) * (In - Ip) / T;
+        const float dJn_dT = nn * (Jm - Jn) / T;
+        const float dEgf_drf = Egf * dlr_drf + four_pi * rho0 * (1.5f * T * tfp + tfn * phif) * rf * rf;
+        const float dEgf_dT = Egf * dlr_dT + four_pi * rho0 * (1.5f * Ip + 1.5f * T * dIp_dT + dJn_dT);
+        const float ddEp_drf = -four_pi * rf * rf * Ps;
+        const float dtot = dEgf_drf + dEgf_dT * dT_drf;
+        const float dnum = (P.energy_sign == 0) ? (dtot - ddEp_drf) : (-dtot - ddEp_drf);
+        dRe = rf * dnum / absE;
+        return isfinite(Re) && isfinite(dRe);
+      };
+      // safeguarded Newton in v = ln r_f (bracketed once the sign changes)
+      const float vmin = logf(0.5f * h.rvir), vmax = logf(10.0f * h.rvir);
+      float v = logf(1.1f * h.rvir), Tw = 0.f, vprev = 0.f, Rprev = 0.f, va = 0.f, vb = 0.f,
+            Ra = 0.f;
+      bool have_prev = false, have_br = false, done = false;
+      for (int it = 0; it < 40; ++it) {
+        const float rf = expf(v);
+        if (!reduced(rf, Tw)) break;
+        Tw = T;
+        if (fabsf(Re) < 1e-4f) {
+          done = true;
+          break;
+        }
+        if (have_prev && ((Re > 0) != (Rprev > 0))) {
+          have_br = true;
+          va = vprev; Ra = Rprev; vb = v;
+        } else if (have_br) {
+          if ((Re > 0) == (Ra > 0)) { va = v; Ra = Re; } else { vb = v; }
+        }
+        float step = -Re / dRe;
+        if (!isfinite(step)) step = 0.5f;
+        step = fmaxf(-0.5f, fminf(0.5f, step));
+        float vn = fminf(fmaxf(v + step, vmin), vmax);
+        if (have_br) {
+          const float lo = fminf(va, vb), hi = fmaxf(va, vb);
+          if (!(vn > lo && vn < hi)) vn = 0.5f * (va + vb);
+        }
+        vprev = v; Rprev = Re; have_prev = true;
+        v = vn;
+      }
+      if (done) {
+        g0 = v - logf(h.rvir);
+        g1 = logf(Tw * h.rvir / h.GM);
+      }
+    }
+    if (lane == 0) {
+      guess[i] = (double)g0;
+      guess[n + i] = (double)g1;
+    }
+  }
+}
+
 }  // namespace
 
+// presolve: run the FP32 pre-solve and start the FP64 solve from its result
+// n_bad: halos whose status is not OK; n_fallback: those of them marked FALLBACK
 static int solve_launch(bp_ctx* ctx, int64_t n, const double* Mvir, const double* c,
                         const double* z, double* model, int32_t* status, double tol,
-                        SolveExtra X, int64_t* n_bad) {
+                        SolveExtra X, int64_t* n_bad, int64_t* n_fallback,
+                        bool presolve = false) {
   int r = upload_constants(ctx);
   if (r) return r;
   Halo* halos;
-  if ((r = bp_ws(ctx, WS_HALO, (size_t)n * (sizeof(Halo) + sizeof(int32_t)) + 64,
+  if ((r = bp_ws(ctx, WS_HALO,
+                 (size_t)n * (sizeof(Halo) + 2 * sizeof(double) + sizeof(int32_t)) + 64,
                  (void**)&halos)))
     return r;
-  int32_t* okv = reinterpret_cast<int32_t*>(halos + n);
+  double* pguess = reinterpret_cast<double*>(halos + n);
+  int32_t* okv = reinterpret_cast<int32_t*>(pguess + 2 * n);
   BP_CUDA(ctx, cudaMemsetAsync(ctx->d_counter, 0, sizeof(int64_t), ctx->stream));
+  BP_CUDA(ctx, cudaMemsetAsync(ctx->d_counter + 3, 0, sizeof(int64_t), ctx->stream));
   // halos per warp: enough warps to fill the GPU, the rest shared out 1..32 per warp
   int64_t target_warps = (int64_t)ctx->num_sms * 16;
   int hpw = (int)std::min<int64_t>(32, std::max<int64_t>(1, n / target_warps));
@@ -710,14 +999,23 @@ static int solve_launch(bp_ctx* ctx, int64_t n, const double* Mvir, const double
   k_setup<<<(unsigned)((n + 127) / 128), 128, 0, ctx->stream>>>(
       ctx->p, ctx->t, n, Mvir, c, z, model, status, ctx->d_counter, X, halos, okv);
   BP_LAUNCH_CHECK(ctx, "k_setup launch");
+  if (presolve) {
+    k_presolve<<<(unsigned)blocks, 32 * SOLVE_WARPS, 0, ctx->stream>>>(ctx->p, n, X, hpw, halos,
+                                                                       okv, pguess);
+    BP_LAUNCH_CHECK(ctx, "k_presolve launch");
+    X.guess = pguess;
+  }
   k_solve<<<(unsigned)blocks, 32 * SOLVE_WARPS, 0, ctx->stream>>>(
-      ctx->p, n, model, status, tol, ctx->d_counter, X, hpw, halos, okv);
+      ctx->p, n, model, status, tol, ctx->d_counter, ctx->d_counter + 3, X, hpw, halos, okv);
   BP_LAUNCH_CHECK(ctx, "k_solve launch");
   bp_phase_end(ctx, BP_PH_SOLVE);
   BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, ctx->d_counter, sizeof(int64_t),
                                cudaMemcpyDeviceToHost, ctx->stream));
+  BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 4, ctx->d_counter + 3, sizeof(int64_t),
+                               cudaMemcpyDeviceToHost, ctx->stream));
   BP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   *n_bad = ctx->h_pinned[0];
+  *n_fallback = ctx->h_pinned[4];
   return BP_OK;
 }
 
@@ -754,17 +1052,30 @@ extern "C" int bp_solve_halos_ex(bp_ctx* ctx, int64_t n, const double* Mvir, con
   X.only_fallback = 0;
   int64_t bad = 0;
   double tol = resid_tol > 0 ? resid_tol : 1e-10;
-  if ((r = solve_launch(ctx, n, Mvir, c, z, model, status, tol, X, &bad))) return r;
-  if (bad && gate > 0 && guess) {
-    // the fallback: a full solve of the halos the gate rejected
+  // Stages: (1) the FP64 Newton from the caller's starting point, or from the FP32
+  // pre-solve when there is none; (2) for halos stage 1 marked FALLBACK after a caller's
+  // starting point: the FP32 pre-solve and the Newton from it; (3) for those still
+  // marked: the full nested FP64 iteration.  A Newton stage accepts a halo when both
+  // residuals are below the gate (the tolerance for the pre-solve stages).
+  const bool presolve = guess == nullptr;
+  if (presolve) {
+    X.max_outer = 8;
+    X.gate = tol;
+  }
+  int64_t fb = 0;
+  if ((r = solve_launch(ctx, n, Mvir, c, z, model, status, tol, X, &bad, &fb, presolve)))
+    return r;
+  ctx->last_fallback = fb;
+  for (int stage = presolve ? 3 : 2; fb > 0 && stage <= 3; ++stage) {
     X.guess = nullptr;
-    X.max_outer = 80;
-    X.gate = 0.0;
     X.only_fallback = 1;
-    ctx->last_fallback = bad;
-    if ((r = solve_launch(ctx, n, Mvir, c, z, model, status, tol, X, &bad))) return r;
-  } else {
-    ctx->last_fallback = 0;
+    X.max_outer = stage == 2 ? 8 : 80;
+    X.gate = stage == 2 ? tol : 0.0;
+    int64_t bad2 = 0, fb2 = 0;
+    if ((r = solve_launch(ctx, n, Mvir, c, z, model, status, tol, X, &bad2, &fb2, stage == 2)))
+      return r;
+    bad = bad - fb + bad2;
+    fb = fb2;
   }
   if (bad) return bp_fail(ctx, BP_ENOCONV, "bp_solve_halos: %lld of %lld halos not converged",
                           (long long)bad, (long long)n);
