@@ -111,52 +111,88 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t* keys, in
     hist[(int64_t)d * nblocks + blockIdx.x] = s_h[d];
 }
 
-// Stable scatter: items are ranked in global index order (round, warp, lane).
+// Stable scatter of one block of RS_ITEMS items.  Warp w ranks the contiguous slice
+// [w * 512, (w + 1) * 512) of the block in index order (32 items at a time, peers by
+// digit with __match_any_sync, per-warp digit counts in shared memory); the block then
+// places every item at its digit-sorted position in a shared-memory buffer and copies
+// the buffer out, so that the writes of each digit run are contiguous in memory.
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_SUB = RS_ITEMS / RS_WARPS / 32;  // items per lane
+
 __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* kin,
                                                            const uint32_t* vin, uint32_t* kout,
                                                            uint32_t* vout, int64_t n, int shift,
                                                            int nbits, const int64_t* offs,
                                                            int64_t nblocks) {
-  __shared__ int64_t s_off[RS_MAXDIG];
-  __shared__ uint32_t s_run[RS_MAXDIG];
-  __shared__ uint32_t s_warp[RS_THREADS / 32][RS_MAXDIG];
+  __shared__ uint32_t s_cnt[RS_WARPS][RS_MAXDIG];  // per-warp digit counts, then offsets
+  __shared__ uint32_t s_tot[RS_MAXDIG];
+  __shared__ uint32_t s_start[RS_MAXDIG];          // block-local start of each digit
+  __shared__ int64_t s_off[RS_MAXDIG];             // global start of this block's run
+  __shared__ uint32_t s_k[RS_ITEMS], s_v[RS_ITEMS];
   const int ndig = 1 << nbits;
+  const uint32_t dmask = (uint32_t)(ndig - 1);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  for (int d = tid; d < ndig; d += RS_THREADS) {
-    s_off[d] = offs[(int64_t)d * nblocks + blockIdx.x];
-    s_run[d] = 0;
-    for (int q = 0; q < RS_THREADS / 32; ++q) s_warp[q][d] = 0;
+  for (int d = tid; d < RS_MAXDIG; d += RS_THREADS) {
+    s_off[d] = d < ndig ? offs[(int64_t)d * nblocks + blockIdx.x] : 0;
+    for (int q = 0; q < RS_WARPS; ++q) s_cnt[q][d] = 0;
   }
   __syncthreads();
   const uint32_t lt_mask = (1u << lane) - 1u;
-  int64_t base = (int64_t)blockIdx.x * RS_ITEMS;
-  for (int r = 0; r < RS_ROUNDS; ++r) {
-    int64_t i = base + (int64_t)r * RS_THREADS + tid;
-    bool valid = i < n;
-    uint32_t key = valid ? kin[i] : 0u, val = valid ? vin[i] : 0u;
-    uint32_t d = (key >> shift) & (uint32_t)(ndig - 1);
-    uint32_t tag = valid ? d : (0x80000000u | (uint32_t)lane);
-    uint32_t peers = __match_any_sync(0xffffffffu, tag);
-    uint32_t rank = __popc(peers & lt_mask);
-    if (valid && rank == 0) s_warp[w][d] = __popc(peers);
-    __syncthreads();
-    if (valid) {
-      uint32_t pos = s_run[d] + rank;
-      for (int q = 0; q < w; ++q) pos += s_warp[q][d];
-      int64_t dst = s_off[d] + pos;
-      kout[dst] = key;
-      vout[dst] = val;
+  const int64_t bbase = (int64_t)blockIdx.x * RS_ITEMS;
+  const int64_t wbase = bbase + (int64_t)w * (RS_ITEMS / RS_WARPS);
+  uint32_t key[RS_SUB], val[RS_SUB], rnk[RS_SUB];
+#pragma unroll
+  for (int j = 0; j < RS_SUB; ++j) {
+    const int64_t i = wbase + 32 * j + lane;
+    const bool valid = i < n;
+    key[j] = valid ? kin[i] : 0u;
+    val[j] = valid ? vin[i] : 0u;
+    const uint32_t d = (key[j] >> shift) & dmask;
+    const uint32_t tag = valid ? d : (0x80000000u | (uint32_t)lane);
+    const uint32_t peers = __match_any_sync(0xffffffffu, tag);
+    const uint32_t r = __popc(peers & lt_mask);
+    const uint32_t before = valid ? s_cnt[w][d] : 0u;
+    __syncwarp();
+    if (valid && r == 0) s_cnt[w][d] = before + __popc(peers);
+    __syncwarp();
+    rnk[j] = before + r;
+  }
+  __syncthreads();
+  // per digit: exclusive offsets of the warps, and the digit's total in the block
+  for (int d = tid; d < RS_MAXDIG; d += RS_THREADS) {
+    uint32_t run = 0;
+    for (int q = 0; q < RS_WARPS; ++q) {
+      const uint32_t c = s_cnt[q][d];
+      s_cnt[q][d] = run;
+      run += c;
     }
-    __syncthreads();
-    for (int dd = tid; dd < ndig; dd += RS_THREADS) {
-      uint32_t t = 0;
-      for (int q = 0; q < RS_THREADS / 32; ++q) {
-        t += s_warp[q][dd];
-        s_warp[q][dd] = 0;
-      }
-      s_run[dd] += t;
+    s_tot[d] = run;
+  }
+  __syncthreads();
+  {
+    const uint32_t t = tid < RS_MAXDIG ? s_tot[tid] : 0u;
+    const uint32_t ex = block_excl_scan<uint32_t>(t, nullptr);
+    if (tid < RS_MAXDIG) s_start[tid] = ex;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < RS_SUB; ++j) {
+    const int64_t i = wbase + 32 * j + lane;
+    if (i < n) {
+      const uint32_t d = (key[j] >> shift) & dmask;
+      const uint32_t pos = s_start[d] + s_cnt[w][d] + rnk[j];
+      s_k[pos] = key[j];
+      s_v[pos] = val[j];
     }
-    __syncthreads();
+  }
+  __syncthreads();
+  const int nvalid = (int)min((int64_t)RS_ITEMS, n - bbase);
+  for (int p = tid; p < nvalid; p += RS_THREADS) {
+    const uint32_t k = s_k[p];
+    const uint32_t d = (k >> shift) & dmask;
+    const int64_t g = s_off[d] + (p - (int64_t)s_start[d]);
+    kout[g] = k;
+    vout[g] = s_v[p];
   }
 }
 
