@@ -42,6 +42,27 @@ def rank_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
+def replica_seed(rank, base):
+    """Seed of the light-cone a rank pastes: each replica draws its own sky."""
+    return base + 1 + rank
+
+
+def max_over_ranks(value, world, device):
+    """The largest of the ranks' values (the step time a weak-scaling job reports)."""
+    if world <= 1:
+        return float(value)
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / (ms * 1e-3)
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -428,7 +449,7 @@ def run_ours(args):
 
     B.build()
     # each rank pastes its own light-cone realisation (independent maps, no collective)
-    lc = I.lightcone(n_part=args.particles, seed=I.SEED_BASE + 1 + rank)
+    lc = I.lightcone(n_part=args.particles, seed=replica_seed(rank, I.SEED_BASE))
     n = lc.parts["x"].size
     cat = lc.halos
     nh = cat.M.size
@@ -502,11 +523,7 @@ def run_ours(args):
     launches = ctx.kernel_launches() - launches0
     clocks = sampler.stop() if rank == 0 else None
     ctx.set_timing(False)
-    t_step = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([t_step], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_step = float(t.item())
+    t_step = max_over_ranks(sum(step_ms) / len(step_ms), world, dev)
 
     # end to end through the public API: inputs from pinned host memory, maps back
     e2e_ms = []
@@ -522,11 +539,7 @@ def run_ours(args):
         e1.record()
         torch.cuda.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    t_e2e = sum(e2e_ms) / len(e2e_ms)
-    if world > 1:
-        t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world, dev)
 
     if rank != 0:
         if world > 1:
@@ -562,7 +575,7 @@ def run_ours(args):
                     "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"}
     hp_ms = mean_ph["solve"] + mean_ph["hp_table"] + mean_ph["hp_pairs"] + mean_ph["hp_paste"]
     res = {
-        "metric": METRIC, "value": n * world / (t_step * 1e-3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": job_rate(n, world, t_step), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
@@ -574,7 +587,7 @@ def run_ours(args):
         "hp_halos_per_s": nh / (hp_ms * 1e-3) if hp_ms > 0 else None,
         "phase_ms": mean_ph,
         "roofline": roofline,
-        "e2e": {"value": n * world / (t_e2e * 1e-3), "unit": UNIT,
+        "e2e": {"value": job_rate(n, world, t_e2e), "unit": UNIT,
                 "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes,
                 "ms_per_step": t_e2e},
         "gpu_launches": launches,
