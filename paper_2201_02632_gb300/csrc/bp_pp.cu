@@ -492,7 +492,9 @@ __global__ void __launch_bounds__(DEP_THREADS, 2)
   }
 }
 
-// one CTA per multi-unit tile: add its partial tiles in unit order, then the map
+// REDUCE_SPLIT CTAs per multi-unit tile (pixel slices): add its partial tiles in unit
+// order, then the map
+constexpr int REDUCE_SPLIT = 4;
 template <int TS>
 __global__ void __launch_bounds__(256) k_reduce_tiles(const int64_t* __restrict__ tstart,
                                                       const int64_t* __restrict__ soff,
@@ -500,6 +502,7 @@ __global__ void __launch_bounds__(256) k_reduce_tiles(const int64_t* __restrict_
                                                       int ntx, const float* __restrict__ partials,
                                                       float* ymap, float* bmap, float* ylo,
                                                       float* blo) {
+  // blockIdx.y: which of REDUCE_SPLIT pixel slices of the tile this CTA sums
   int64_t t = blockIdx.x;
   if (t >= n_tiles) return;
   int64_t len = tstart[t + 1] - tstart[t];
@@ -507,7 +510,9 @@ __global__ void __launch_bounds__(256) k_reduce_tiles(const int64_t* __restrict_
   if (nu <= 1) return;
   int64_t u0 = soff[t];
   int x0 = (int)(t % ntx) * TS, y0 = (int)(t / ntx) * TS;
-  for (int q = threadIdx.x; q < TS * TS; q += blockDim.x) {
+  constexpr int SLICE = TS * TS / REDUCE_SPLIT;
+  const int q_end = (blockIdx.y + 1) * SLICE;
+  for (int q = blockIdx.y * SLICE + threadIdx.x; q < q_end; q += blockDim.x) {
     int gx = x0 + q % TS, gy = y0 + q / TS;
     if (gx >= nx || gy >= ny) continue;
     float hy = 0.f, ly = 0.f, hb = 0.f, lb = 0.f;
@@ -664,7 +669,7 @@ int deposit(bp_ctx* ctx, const float* assigned, const bp_map_geom* g, const uint
   }
   bp_phase_begin(ctx, BP_PH_REDUCE);
   if (n_slots > 0) {
-    k_reduce_tiles<TS><<<(unsigned)n_tiles, 256, 0, ctx->stream>>>(
+    k_reduce_tiles<TS><<<dim3((unsigned)n_tiles, REDUCE_SPLIT), 256, 0, ctx->stream>>>(
         tstart, soff, n_tiles, unit, g->nx, g->ny, ntx, partials, ymap, bmap, ylo, blo);
     BP_LAUNCH_CHECK(ctx, "reduce tiles");
   }
