@@ -125,6 +125,30 @@ class ClockSampler:
                 "samples": len(rows), "samples_under_load": len(load)}
 
 
+def phase_bandwidth(ph, n, n_pairs, nx, ny, hbm_peak):
+    """Algorithmic bytes of the streaming phases over their live durations, and the
+    fraction of the measured HBM copy bandwidth (GB/s)."""
+    maps = 2 * nx * ny * 4  # one FP32 plane of y and of b
+    bytes_ = {
+        # particle SoA 8 x 4 B in, 32 B record out
+        "assign": n * 64,
+        # two reads of the 32 B records (count, emit), counts 4 B, offsets 8 B, pairs 8 B
+        "pairs": n * (32 + 32 + 4 + 8) + n_pairs * 8,
+        # one 8-bit pass: key read for the histogram, key + value read and written,
+        # key read for the tile ranges
+        "sort": n_pairs * (4 + 16 + 4),
+        # map and lo planes of y and b read and written, for the PP and the HP maps
+        "finalize": 2 * 4 * maps,
+    }
+    out = {}
+    for k, b in bytes_.items():
+        ms = ph.get(k, 0.0)
+        if ms > 0:
+            gbs = b / (ms * 1e-3) / 1e9
+            out[k] = {"bytes": b, "GB/s": round(gbs, 1), "frac_hbm": round(gbs / hbm_peak, 4)}
+    return out
+
+
 def deposit_flops(rec_np, nx, ny):
     """Algorithmic FP32 flops of one deposit launch: 2 per pixel update (one FMA per map)
     over every particle's clipped 2h x 2h footprint; field particles update one map."""
@@ -585,6 +609,8 @@ def run_ours(args):
                    "l2": "flushed: 256 MB write "
                    "between timed steps", "parallelism": f"replicas x{world} (weak)"},
         "hp_halos_per_s": nh / (hp_ms * 1e-3) if hp_ms > 0 else None,
+        "phase_hbm": phase_bandwidth(mean_ph, n, tile_pairs, g.nx, g.ny,
+                                     float(peaks.get("hbm_gbs", 6785.9))),
         "phase_ms": mean_ph,
         "roofline": roofline,
         "e2e": {"value": job_rate(n, world, t_e2e), "unit": UNIT,
