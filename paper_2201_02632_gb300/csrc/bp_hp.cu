@@ -5,7 +5,7 @@
 //               which smooths the central cusp): the line-of-sight integrals of the
 //               dimensionless pressure and density profiles, divided by the chord
 //               sqrt(1 - u^2) so that the tabulated function is smooth at the edge
-//               (Eqs. y^HP, b^HP); 16-point Gauss-Legendre per segment after
+//               (Eqs. y^HP, b^HP); 12-point Gauss-Legendre per segment after
 //               t = u sinh(s), split where the 3-D radius crosses r_vir and the zero
 //               of the thermal fraction
 //  k_hp_count / (map, tile, halo) pairs from the FP64 pixel-centre bounding box of the
@@ -20,7 +20,7 @@
 
 #define HP_NT 256          // table intervals on s = sqrt(u) in [0, 1]
 #define HP_ROW (HP_NT + 3) // with one ghost node at each end
-#define HP_NGL 16
+#define HP_NGL 12          // Gauss-Legendre points per segment (16 gave the same map errors)
 
 __constant__ float c_hgx[HP_NGL];
 __constant__ float c_hgw[HP_NGL];
