@@ -123,6 +123,8 @@ def lib():
                 "orc_pp_select": (i64, [pc, i64, P, P, P, P, pg, i64, P, P, P, i32]),
                 "orc_hp_pixels": (None, [pc, pi, i64, P, P, P, P, P, pg, d, d, i64, P, P, P, P, P,
                                          i32]),
+                "orc_w3": (d, [d]),
+                "orc_smoothing_lengths": (None, [i64, P, P, P, d, P, i32]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -256,6 +258,21 @@ def hp_pairs(thx, thy, models, g: Geom, ap_r500, tw, th, map_id=None):
 # ---------------------------------------------------------------- PP
 def w_sph(x):
     return lib().orc_w_sph(float(x))
+
+
+def w3(x):
+    """3-D cubic spline of Eq. SPH_kernel without its 8 / (pi h^3) factor."""
+    return lib().orc_w3(float(x))
+
+
+def smoothing_lengths(x, y, z, n_ngb=64.0, nthreads=0):
+    """h_i with (32/3) sum_j w(|r_i - r_j| / h_i) = n_ngb (all j, i included); FP32
+    positions, FP64 result in the same length unit.  O(n^2 log n): small inputs only."""
+    x, y, z = _f32(x), _f32(y), _f32(z)
+    n = x.size
+    h = np.empty(n, np.float64)
+    lib().orc_smoothing_lengths(n, _p(x), _p(y), _p(z), float(n_ngb), _p(h), nthreads)
+    return h
 
 
 def pp_assign(parts: dict, Mp_hinv, halo_pos, models, g: Geom, cp=None, ip=None, nthreads=0):

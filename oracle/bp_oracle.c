@@ -1084,3 +1084,68 @@ void orc_hp_pixels(const orc_cosmo* cp, const orc_icm* ip, int64_t nh, const dou
   }
   (void)nthreads;
 }
+
+/* ------------------------------------------------------------------ */
+/* Smoothing lengths (Section 3.4: the SPH kernel Eq. SPH_kernel and the  */
+/* effective neighbour number N_ngb).                                     */
+/* ------------------------------------------------------------------ */
+/* 3-D cubic spline of Eq. SPH_kernel without its 8 / (pi h^3) factor, x = r / h. */
+static double o_w3(double x) {
+  if (x < 0.5) return 1.0 - 6.0 * x * x + 6.0 * x * x * x;
+  if (x < 1.0) return 2.0 * (1.0 - x) * (1.0 - x) * (1.0 - x);
+  return 0.0;
+}
+double orc_w3(double x) { return o_w3(x); }
+
+static int o_cmp_double(const void* a, const void* b) {
+  double u = *(const double*)a, v = *(const double*)b;
+  return (u > v) - (u < v);
+}
+
+/* Effective number of neighbours within h of a particle whose distances to every particle
+ * (itself included, distance 0) are d[0..n-1] in ascending order:
+ * N_eff(h) = (4 pi / 3) h^3 sum_j W(d_j, h) = (32 / 3) sum_j w(d_j / h). */
+static double o_neff(const double* d, int64_t n, double h) {
+  double s = 0.0;
+  for (int64_t j = 0; j < n && d[j] < h; ++j) s += o_w3(d[j] / h);
+  return 32.0 / 3.0 * s;
+}
+
+/* Smoothing lengths: for every particle i, the h_i with N_eff(h_i) = n_ngb (N_eff grows
+ * monotonically with h), by bisection on the sorted distances to all particles.  Positions
+ * in any length unit (FP32 inputs, computed in FP64); h in the same unit.  A particle whose
+ * N_eff cannot reach n_ngb (too few particles) gets +inf. */
+void orc_smoothing_lengths(int64_t n, const float* x, const float* y, const float* z,
+                           double n_ngb, double* h, int nthreads) {
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+  (void)nthreads;
+#endif
+#pragma omp parallel
+  {
+    double* d = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+#pragma omp for schedule(dynamic, 16)
+    for (int64_t i = 0; i < n; ++i) {
+      for (int64_t j = 0; j < n; ++j) {
+        double dx = (double)x[j] - (double)x[i], dy = (double)y[j] - (double)y[i];
+        double dz = (double)z[j] - (double)z[i];
+        d[j] = sqrt(dx * dx + dy * dy + dz * dz);
+      }
+      qsort(d, (size_t)n, sizeof(double), o_cmp_double);
+      if (32.0 / 3.0 * (double)n <= n_ngb) {
+        h[i] = INFINITY;
+        continue;
+      }
+      /* bracket: N_eff(lo) < n_ngb <= N_eff(hi) */
+      double lo = 0.0, hi = d[n - 1] > 0.0 ? d[n - 1] : 1.0;
+      while (o_neff(d, n, hi) < n_ngb) hi *= 2.0;
+      for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
+        double mid = 0.5 * (lo + hi);
+        if (o_neff(d, n, mid) < n_ngb) lo = mid; else hi = mid;
+      }
+      h[i] = 0.5 * (lo + hi);
+    }
+    free(d);
+  }
+}
