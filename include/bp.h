@@ -324,6 +324,19 @@ int bp_paste_particles_noalloc(bp_ctx* ctx, int64_t n, const float* assigned,
                                const bp_map_geom* geom, int select, float* ymap, float* bmap,
                                float* ylo, float* blo);
 
+/* Section 3.4 (the SPH kernel Eq. SPH_kernel and N_ngb): smoothing lengths from the
+ * particle positions.  h_i solves N_eff(h) = (4 pi / 3) h^3 sum_j W(|r_i - r_j|, h) = n_ngb
+ * with the cubic kernel W = 8 / (pi h^3) w(r / h), the sum over all n particles (i
+ * included).  x, y, z: device FP32 positions [n] in any length unit (comoving h^-1 Mpc for
+ * bp_assign_particles); h_guess: optional device FP32 [n] starting radii (a previous h, or
+ * null: from the grid density); h_out: device FP32 [n], same unit as the positions.
+ * Uses the context's scratch and stream; synchronises.  Deterministic.  Errors:
+ * BP_EINVAL (null pointer, n_ngb outside (32/3, 1024], non-finite position), BP_ERANGE
+ * (n (32/3) <= n_ngb: no particle can reach n_ngb; n >= 2^32), BP_ENOCONV (a particle did
+ * not converge in 48 radius updates: its h is NaN). */
+int bp_smoothing_lengths(bp_ctx* ctx, int64_t n, const float* x, const float* y, const float* z,
+                         double n_ngb, const float* h_guess, float* h_out);
+
 /* The tile pair list of the deposit (for tests): keys (tile index ty*ntx+tx) and
  * particle indices ordered by key then index.  capacity: entries the caller
  * allocated; n_pairs (host pointer) receives the count.  BP_ERANGE if capacity

@@ -125,6 +125,7 @@ def lib():
                                          i32]),
                 "orc_w3": (d, [d]),
                 "orc_smoothing_lengths": (None, [i64, P, P, P, d, P, i32]),
+                "orc_smoothing_lengths_at": (None, [i64, P, P, P, d, i64, P, P, i32]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -272,6 +273,17 @@ def smoothing_lengths(x, y, z, n_ngb=64.0, nthreads=0):
     n = x.size
     h = np.empty(n, np.float64)
     lib().orc_smoothing_lengths(n, _p(x), _p(y), _p(z), float(n_ngb), _p(h), nthreads)
+    return h
+
+
+def smoothing_lengths_at(x, y, z, idx, n_ngb=64.0, nthreads=0):
+    """smoothing_lengths of the particles idx only (the sums still run over all of them):
+    O(len(idx) n log n), for sampling large inputs."""
+    x, y, z = _f32(x), _f32(y), _f32(z)
+    idx = np.ascontiguousarray(idx, dtype=np.int64)
+    h = np.empty(idx.size, np.float64)
+    lib().orc_smoothing_lengths_at(x.size, _p(x), _p(y), _p(z), float(n_ngb), idx.size,
+                                   _p(idx), _p(h), nthreads)
     return h
 
 

@@ -1115,8 +1115,31 @@ static double o_neff(const double* d, int64_t n, double h) {
  * monotonically with h), by bisection on the sorted distances to all particles.  Positions
  * in any length unit (FP32 inputs, computed in FP64); h in the same unit.  A particle whose
  * N_eff cannot reach n_ngb (too few particles) gets +inf. */
-void orc_smoothing_lengths(int64_t n, const float* x, const float* y, const float* z,
-                           double n_ngb, double* h, int nthreads) {
+/* h of particle i from its distances d[0..n-1] (scratch) to all n particles. */
+static double o_hsml_one(int64_t n, const float* x, const float* y, const float* z, int64_t i,
+                         double n_ngb, double* d) {
+  if (32.0 / 3.0 * (double)n <= n_ngb) return INFINITY;
+  for (int64_t j = 0; j < n; ++j) {
+    double dx = (double)x[j] - (double)x[i], dy = (double)y[j] - (double)y[i];
+    double dz = (double)z[j] - (double)z[i];
+    d[j] = sqrt(dx * dx + dy * dy + dz * dz);
+  }
+  qsort(d, (size_t)n, sizeof(double), o_cmp_double);
+  /* bracket: N_eff(lo) < n_ngb <= N_eff(hi) */
+  double lo = 0.0, hi = d[n - 1] > 0.0 ? d[n - 1] : 1.0;
+  while (o_neff(d, n, hi) < n_ngb) hi *= 2.0;
+  for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (o_neff(d, n, mid) < n_ngb) lo = mid; else hi = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+/* h of the m particles idx[0..m-1] (h[k] for particle idx[k]); the sums still run over all
+ * n particles.  m = n with idx = null: every particle. */
+void orc_smoothing_lengths_at(int64_t n, const float* x, const float* y, const float* z,
+                              double n_ngb, int64_t m, const int64_t* idx, double* h,
+                              int nthreads) {
 #ifdef _OPENMP
   if (nthreads > 0) omp_set_num_threads(nthreads);
 #else
@@ -1125,27 +1148,13 @@ void orc_smoothing_lengths(int64_t n, const float* x, const float* y, const floa
 #pragma omp parallel
   {
     double* d = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
-#pragma omp for schedule(dynamic, 16)
-    for (int64_t i = 0; i < n; ++i) {
-      for (int64_t j = 0; j < n; ++j) {
-        double dx = (double)x[j] - (double)x[i], dy = (double)y[j] - (double)y[i];
-        double dz = (double)z[j] - (double)z[i];
-        d[j] = sqrt(dx * dx + dy * dy + dz * dz);
-      }
-      qsort(d, (size_t)n, sizeof(double), o_cmp_double);
-      if (32.0 / 3.0 * (double)n <= n_ngb) {
-        h[i] = INFINITY;
-        continue;
-      }
-      /* bracket: N_eff(lo) < n_ngb <= N_eff(hi) */
-      double lo = 0.0, hi = d[n - 1] > 0.0 ? d[n - 1] : 1.0;
-      while (o_neff(d, n, hi) < n_ngb) hi *= 2.0;
-      for (int it = 0; it < 200 && hi - lo > 1e-15 * hi; ++it) {
-        double mid = 0.5 * (lo + hi);
-        if (o_neff(d, n, mid) < n_ngb) lo = mid; else hi = mid;
-      }
-      h[i] = 0.5 * (lo + hi);
-    }
+#pragma omp for schedule(dynamic, 1)
+    for (int64_t k = 0; k < m; ++k) h[k] = o_hsml_one(n, x, y, z, idx ? idx[k] : k, n_ngb, d);
     free(d);
   }
+}
+
+void orc_smoothing_lengths(int64_t n, const float* x, const float* y, const float* z,
+                           double n_ngb, double* h, int nthreads) {
+  orc_smoothing_lengths_at(n, x, y, z, n_ngb, n, NULL, h, nthreads);
 }

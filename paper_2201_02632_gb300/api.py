@@ -267,6 +267,18 @@ class Context:
         self._check(rc)
         return maps
 
+    def smoothing_lengths(self, x, y, z, n_ngb=64.0, guess=None, out=None):
+        """SPH smoothing lengths of FP32 positions (Section 3.4): N_eff(h_i) = n_ngb."""
+        n = x.numel()
+        f32 = torch.float32
+        if out is None:
+            out = torch.empty(n, dtype=f32, device=x.device)
+        rc = self._L.bp_smoothing_lengths(
+            self._h, n, _ptr(x, f32, "x"), _ptr(y, f32, "y"), _ptr(z, f32, "z"), float(n_ngb),
+            None if guess is None else _ptr(guess, f32, "guess"), _ptr(out, f32, "out"))
+        self._check(rc)
+        return out
+
     def pp_pairs(self, assigned, g: L.BpGeom, tile: int, select=SELECT_ALL):
         """Sorted (tile key, particle index) pairs of the deposit (uint32 as int32)."""
         n = assigned.shape[0]

@@ -62,3 +62,11 @@ def test_neighbours_shrink_h_and_too_few_particles_give_inf():
     # 5 particles: N_eff <= (32/3) 5 < 64
     q = rng.uniform(0, 1, (3, 5)).astype(np.float32)
     assert np.all(np.isinf(orc.smoothing_lengths(*q, 64.0)))
+
+
+def test_sampled_particles_match_the_full_solve():
+    rng = np.random.default_rng(5)
+    p = rng.normal(0, 1, (3, 400)).astype(np.float32)
+    idx = np.array([0, 17, 399, 17])
+    assert np.array_equal(orc.smoothing_lengths_at(*p, idx, 40.0),
+                          orc.smoothing_lengths(*p, 40.0)[idx])
