@@ -335,6 +335,32 @@ def surrogate_section(api, ctx, dev, lc, args):
             "gate": 1e-4, "polish_newton_iters": 4}
 
 
+def hsml_section(api, ctx, dev, lc, args):
+    """SPH smoothing lengths (N_ngb = 64) of the step's light-cone particles: from the grid
+    density alone and from the rule-of-thumb h of the generator as starting guesses."""
+    import torch
+
+    x, y, z = (torch.from_numpy(lc.parts[k]).to(dev) for k in "xyz")
+    guess = torch.from_numpy(lc.parts["hsml"]).to(dev)
+    n = x.numel()
+    out = {"workload": f"{n} light-cone particles (positions of the pasting step), N_ngb 64"}
+    for name, g in (("no_guess", None), ("rule_of_thumb_guess", guess)):
+        for _ in range(2):
+            h = ctx.smoothing_lengths(x, y, z, 64.0, guess=g)
+        ts = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            ctx.smoothing_lengths(x, y, z, 64.0, guess=g, out=h)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        t = float(np.median(ts))
+        out[name] = {"ms": t, "particles_per_s": n / (t * 1e-3)}
+    return out
+
+
 def batched_section(api, ctx, dev, args):
     """Batched HP: many independent maps of uneven halo extents pasted by one prepared
     plan (one persistent launch), autotuned, captured in a CUDA graph and replayed."""
@@ -621,6 +647,8 @@ def run_ours(args):
     }
     if not args.no_surrogate:
         res["surrogate"] = surrogate_section(api, ctx, dev, lc, args)
+    if not args.no_hsml:
+        res["smoothing_lengths"] = hsml_section(api, ctx, dev, lc, args)
     if not args.no_batched:
         res["batched_hp"] = batched_section(api, ctx, dev, args)
     if not args.no_full_scale:
@@ -633,6 +661,17 @@ def run_ours(args):
             "sample": (f"FP64 oracle: solve of all {nh} halos, assign+deposit of "
                        f"{det['n_part_sample']} particles, HP of {det['n_halo_sample']} "
                        f"halos, extrapolated linearly to the full step"), "detail": det}
+        if "smoothing_lengths" in res:  # the oracle's smoothing lengths at 8 particles
+            import oracle as O
+
+            idx = np.arange(0, n, n // 8)[:8]
+            t0 = time.perf_counter()
+            O.smoothing_lengths_at(lc.parts["x"], lc.parts["y"], lc.parts["z"], idx, 64.0,
+                                   nthreads=threads)
+            dt = time.perf_counter() - t0
+            res["smoothing_lengths"]["cpu_oracle"] = {
+                "particles_per_s": idx.size / dt, "sample": f"{idx.size} particles of the {n}",
+                "cores": threads, "kind": "oracle"}
     print(json.dumps(res))
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -652,6 +691,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-hsml", action="store_true")
     ap.add_argument("--no-full-scale", action="store_true")
     ap.add_argument("--full-particles", type=int, default=500_000_000)
     ap.add_argument("--full-halos", type=int, default=200_000)
