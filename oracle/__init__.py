@@ -124,6 +124,9 @@ def lib():
                 "orc_hp_pixels": (None, [pc, pi, i64, P, P, P, P, P, pg, d, d, i64, P, P, P, P, P,
                                          i32]),
                 "orc_w3": (d, [d]),
+                "orc_hpx_centres": (None, [i64, i64, P, P, P]),
+                "orc_sky_angle": (d, [d, d, d, d]),
+                "orc_hp_sky": (None, [pc, pi, i64, P, P, P, P, d, d, i64, P, P, P, P, i32]),
                 "orc_smoothing_lengths": (None, [i64, P, P, P, d, P, i32]),
                 "orc_smoothing_lengths_at": (None, [i64, P, P, P, d, i64, P, P, i32]),
             }
@@ -241,6 +244,32 @@ def hp_map(thx, thy, vlos, models, g: Geom, ap_r500=0.0, map_id=None, rtol=1e-10
                      _p(thx), _p(thy), _p(vlos), _p(mid), _p(models), C.byref(g),
                      float(ap_r500), float(rtol), _p(ym), _p(bm), int(nthreads))
     return ym, bm
+
+
+def hpx_centres(nside, pix=None):
+    """HEALPix RING pixel centres (colatitude, longitude) of pixels `pix` (default all)."""
+    if pix is None:
+        pix = np.arange(12 * nside * nside, dtype=np.int64)
+    pix = np.ascontiguousarray(pix, dtype=np.int64)
+    th, ph = np.empty(pix.size), np.empty(pix.size)
+    lib().orc_hpx_centres(int(nside), pix.size, _p(pix), _p(th), _p(ph))
+    return th, ph
+
+
+def sky_angle(t1, p1, t2, p2):
+    return lib().orc_sky_angle(float(t1), float(p1), float(t2), float(p2))
+
+
+def hp_sky(h_theta, h_phi, vlos, models, p_theta, p_phi, ap_r500=0.0, rtol=1e-9, cp=None,
+           ip=None, nthreads=0):
+    """All-sky HP values at pixel directions (p_theta, p_phi): halos at (h_theta, h_phi)."""
+    h_theta, h_phi, vlos, models = _f64(h_theta), _f64(h_phi), _f64(vlos), _f64(models)
+    p_theta, p_phi = _f64(p_theta), _f64(p_phi)
+    yv, bv = np.zeros(p_theta.size), np.zeros(p_theta.size)
+    lib().orc_hp_sky(C.byref(cp or cosmo_default()), C.byref(ip or icm_default()), h_theta.size,
+                     _p(h_theta), _p(h_phi), _p(vlos), _p(models), float(ap_r500), float(rtol),
+                     p_theta.size, _p(p_theta), _p(p_phi), _p(yv), _p(bv), int(nthreads))
+    return yv, bv
 
 
 def hp_pairs(thx, thy, models, g: Geom, ap_r500, tw, th, map_id=None):

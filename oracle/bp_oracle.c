@@ -1086,6 +1086,95 @@ void orc_hp_pixels(const orc_cosmo* cp, const orc_icm* ip, int64_t nh, const dou
 }
 
 /* ------------------------------------------------------------------ */
+/* All-sky HP (Section 5.2, all-sky maps) on the HEALPix sphere of Gorski et al. (2005), */
+/* RING ordering: 12 nside^2 equal-area pixels on 4 nside - 1 rings of constant z.       */
+/* ------------------------------------------------------------------ */
+/* Ring i (1 .. 4N - 1 from the north pole, N = nside): z = cos(theta) of its centres, pixel
+ * count, RING index of its first pixel, and the longitude of that first centre in units of
+ * the ring's pixel spacing 2 pi / count.  Polar caps (i < N and i > 3N): 4i pixels (4(4N - i)
+ * in the south), half-spacing offset; equatorial belt: 4N pixels, offset alternating with i. */
+static void o_hpx_ring(int64_t N, int64_t i, double* z, int64_t* cnt, int64_t* first,
+                       double* phase) {
+  if (i < N) {
+    *z = 1.0 - (double)(i * i) / (3.0 * (double)N * (double)N);
+    *cnt = 4 * i;
+    *first = 2 * i * (i - 1);
+    *phase = 0.5;
+  } else if (i <= 3 * N) {
+    *z = 4.0 / 3.0 - 2.0 * (double)i / (3.0 * (double)N);
+    *cnt = 4 * N;
+    *first = 2 * N * (N - 1) + 4 * N * (i - N);
+    *phase = ((i + N) & 1) ? 0.0 : 0.5;
+  } else {
+    int64_t k = 4 * N - i;
+    *z = -(1.0 - (double)(k * k) / (3.0 * (double)N * (double)N));
+    *cnt = 4 * k;
+    *first = 12 * N * N - 2 * k * (k + 1);
+    *phase = 0.5;
+  }
+}
+
+/* Centre (colatitude theta, longitude phi in [0, 2 pi)) of RING pixel p. */
+void orc_hpx_pix2ang(int64_t N, int64_t p, double* theta, double* phi) {
+  int64_t lo = 1, hi = 4 * N - 1; /* the last ring whose first pixel is <= p */
+  while (lo < hi) {
+    int64_t mid = (lo + hi + 1) / 2, cnt, first;
+    double z, ph;
+    o_hpx_ring(N, mid, &z, &cnt, &first, &ph);
+    if (first <= p) lo = mid; else hi = mid - 1;
+  }
+  int64_t cnt, first;
+  double z, ph;
+  o_hpx_ring(N, lo, &z, &cnt, &first, &ph);
+  *theta = acos(z);
+  *phi = ((double)(p - first) + ph) * (2.0 * O_PI / (double)cnt);
+}
+
+void orc_hpx_centres(int64_t N, int64_t n, const int64_t* pix, double* theta, double* phi) {
+  for (int64_t q = 0; q < n; ++q) orc_hpx_pix2ang(N, pix[q], theta + q, phi + q);
+}
+
+/* Great-circle angle between directions (t1, p1) and (t2, p2), robust at all separations. */
+double orc_sky_angle(double t1, double p1, double t2, double p2) {
+  double a[3] = {sin(t1) * cos(p1), sin(t1) * sin(p1), cos(t1)};
+  double b[3] = {sin(t2) * cos(p2), sin(t2) * sin(p2), cos(t2)};
+  double cx = a[1] * b[2] - a[2] * b[1], cy = a[2] * b[0] - a[0] * b[2], cz = a[0] * b[1] - a[1] * b[0];
+  return atan2(sqrt(cx * cx + cy * cy + cz * cz), a[0] * b[0] + a[1] * b[1] + a[2] * b[2]);
+}
+
+/* All-sky HP at listed pixel directions: every halo whose aperture contains the direction
+ * adds its LOS integrals at r_perp = D_A psi, psi the great-circle angle to the halo
+ * (the flat-sky r_perp = D_A |theta - theta_h| with the angle measured on the sphere). */
+void orc_hp_sky(const orc_cosmo* cp, const orc_icm* ip, int64_t nh, const double* h_theta,
+                const double* h_phi, const double* vlos, const double* models, double ap_r500,
+                double rtol, int64_t npx, const double* p_theta, const double* p_phi, double* yv,
+                double* bv, int nthreads) {
+  double CP = o_CP(), CN = o_CN(cp);
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+  for (int64_t q = 0; q < npx; ++q) {
+    double sy = 0.0, sb = 0.0;
+    for (int64_t k = 0; k < nh; ++k) {
+      const double* m = models + k * OF_N;
+      if (m[OF_STATUS] != 0) continue;
+      double rap = m[OF_RF];
+      if (ap_r500 > 0) rap = fmin(rap, ap_r500 * m[OF_R500]);
+      double rperp = m[OF_DA] * orc_sky_angle(p_theta[q], p_phi[q], h_theta[k], h_phi[k]);
+      if (rperp >= rap) continue;
+      o_prof p;
+      o_prof_init(&p, cp, ip, m);
+      sy += CP * o_los_integral(&p, rperp, 0, rtol);
+      sb += CN * (vlos[k] / O_C_KMS) * exp(-m[OF_TAU]) * o_los_integral(&p, rperp, 1, rtol);
+    }
+    yv[q] = sy;
+    bv[q] = sb;
+  }
+  (void)nthreads;
+}
+
+/* ------------------------------------------------------------------ */
 /* Smoothing lengths (Section 3.4: the SPH kernel Eq. SPH_kernel and the  */
 /* effective neighbour number N_ngb).                                     */
 /* ------------------------------------------------------------------ */
