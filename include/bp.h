@@ -357,6 +357,26 @@ int bp_paste_halos(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_
                    const int32_t* status, const bp_map_geom* geom, double ap_r500, float* ymap,
                    float* bmap, float* ylo, float* blo);
 
+/* All-sky maps (Section 5.2) by the HP of Section 3.3 (Eqs. y^HP, b^HP) on the HEALPix
+ * sphere of Gorski et al. (2005), RING ordering: npix = 12 nside^2 equal-area pixels, pixel p
+ * of ring i (1 .. 4 nside - 1, north to south) at colatitude acos(z_i).  Each halo adds its
+ * projected profiles at r_perp = D_A psi to every pixel centre within its aperture, psi the
+ * great-circle angle to the halo (r_ap = r_f, or min(r_f, ap_r500 r500) when ap_r500 > 0).
+ * theta, phi: device FP64 [n] colatitude in [0, pi] and longitude [rad] (any value, taken
+ * modulo 2 pi) of the halo centres; v_los: FP32 [n] km/s (positive receding); model and
+ * status: bp_solve_halos output for the same n halos (halos whose status is not OK, or
+ * whose theta is outside [0, pi], add nothing).  ymap, bmap, ylo, blo: device FP32 [npix]
+ * in RING order, accumulated (hi + lo, as bp_paste_halos); finalise with bp_finalize_map
+ * and a geometry of nx = 12 nside, ny = nside.  nside: 1 .. 16384.  Halos are processed in
+ * chunks of 2^22 (bounded table memory); each pixel adds its halos in catalogue order
+ * within a chunk: deterministic.  Synchronises once per chunk (pair-list size).  Errors:
+ * BP_EINVAL (null pointer, nside, ap_r500 < 0), BP_ERANGE (n >= 2^32, more than 2^32 pairs
+ * in a chunk). */
+int bp_paste_halos_healpix(bp_ctx* ctx, int64_t n, const double* theta, const double* phi,
+                           const float* v_los, const double* model, const int32_t* status,
+                           int nside, double ap_r500, float* ymap, float* bmap, float* ylo,
+                           float* blo);
+
 /* A prepared halo paste for repeated pastes of one catalogue (many maps of uneven halo
  * extents in one persistent launch).  bp_hp_plan_create builds the (map, tile, halo)
  * work list from the catalogue's apertures (as bp_paste_halos does; synchronises) and

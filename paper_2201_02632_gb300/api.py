@@ -14,7 +14,7 @@ from . import _lib as L
 from ._lib import (ASSIGNED_STRIDE, KIND_FIELD, KIND_HALO, KIND_NONE, MF, MODEL_FIELDS,
                    OUT_DT, OUT_YB, SELECT_ALL, SELECT_FIELD, SELECT_HALO, BpError)
 
-__all__ = ["Context", "Maps", "geom", "MF", "MODEL_FIELDS", "ASSIGNED_STRIDE", "KIND_HALO",
+__all__ = ["Context", "Maps", "geom", "healpix_geom", "healpix_maps", "MF", "MODEL_FIELDS", "ASSIGNED_STRIDE", "KIND_HALO",
            "KIND_FIELD", "KIND_NONE", "SELECT_ALL", "SELECT_HALO", "SELECT_FIELD", "OUT_YB",
            "OUT_DT", "BpError"]
 
@@ -54,6 +54,16 @@ class Maps:
         for t in (self.y, self.b, self.ylo, self.blo):
             t.zero_()
         return self
+
+
+def healpix_geom(nside) -> L.BpGeom:
+    """The geometry that bp_finalize_map uses for a HEALPix map of 12 nside^2 pixels."""
+    return geom(12 * nside, nside, 0.0, 0.0, 1.0)
+
+
+def healpix_maps(nside, device="cuda") -> Maps:
+    """Zeroed HEALPix maps in RING order, shape [1, nside, 12 nside] (flat index = pixel)."""
+    return Maps.zeros(healpix_geom(nside), device)
 
 
 class Context:
@@ -315,6 +325,19 @@ class Context:
                                     float(ap_r500), _ptr(maps.y, f32, "y"),
                                     _ptr(maps.b, f32, "b"), _ptr(maps.ylo, f32, "ylo"),
                                     _ptr(maps.blo, f32, "blo"))
+        self._check(rc)
+        return maps
+
+    def paste_halos_healpix(self, theta, phi, vlos, model, status, nside, maps: Maps,
+                            ap_r500=0.0):
+        """All-sky HP on HEALPix (RING order); maps from healpix_maps(nside)."""
+        f32 = torch.float32
+        rc = self._L.bp_paste_halos_healpix(
+            self._h, theta.numel(), _ptr(theta, torch.float64, "theta"),
+            _ptr(phi, torch.float64, "phi"), _ptr(vlos, f32, "vlos"),
+            _ptr(model, torch.float64, "model"), _ptr(status, torch.int32, "status"), int(nside),
+            float(ap_r500), _ptr(maps.y, f32, "y"), _ptr(maps.b, f32, "b"),
+            _ptr(maps.ylo, f32, "ylo"), _ptr(maps.blo, f32, "blo"))
         self._check(rc)
         return maps
 

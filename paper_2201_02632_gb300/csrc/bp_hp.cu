@@ -15,6 +15,7 @@
 //  k_hp_reduce  partial tiles of multi-unit tiles, in unit order
 //  k_finalize   hi + lo folding and the conversion to Delta T / T_CMB
 #include <algorithm>
+#include <vector>
 
 #include "bp_internal.cuh"
 
@@ -69,6 +70,35 @@ struct HpHalo {
   float xf, c, q500, psi, A0, A1, ant, xnt;  // xnt: r_nt1 / r_s (R_nt = 1) or huge
 };
 
+// Profile constants and amplitudes of halo k (shared by the flat-sky and the all-sky
+// preparations); false when the halo has no valid model.
+__device__ __forceinline__ bool hp_fill_profile(const BpParams& P, int64_t nh, int64_t k,
+                                                const float* __restrict__ vlos,
+                                                const double* __restrict__ model,
+                                                const int32_t* __restrict__ status, HpHalo& H) {
+  auto F = [&](int f) { return model[(int64_t)f * nh + k]; };
+  double rs = F(BP_M_RS), rf = F(BP_M_RF), T = F(BP_M_T), DA = F(BP_M_DA);
+  bool ok = status[k] == BP_HALO_OK && rs > 0 && rf > 0 && T > 0 && DA > 0;
+  // Table intervals per halo.  Coarser tables (64 or 128 intervals, 1.6e-5 and 1.4e-6
+  // interpolation error) broke the per-pixel kSZ tolerance where halos of opposite
+  // velocities cancel, so every halo uses the full resolution.
+  H.nt = HP_NT;
+  double n1T = (P.n_poly + 1.0) * T, GM = bpc::G * F(BP_M_MVIR);
+  H.Ay = (float)(P.CP * P.pe_frac * F(BP_M_P0) * 2.0 * rf);
+  double vk = vlos ? (double)vlos[k] : 0.0;
+  H.Ab = (float)(P.CN * F(BP_M_RHO0) * 2.0 * rf * (vk / bpc::C_KMS) * exp(-F(BP_M_TAU)));
+  H.xf = (float)(rf / rs);
+  H.c = (float)F(BP_M_C);
+  H.q500 = (float)(rs / F(BP_M_R500));
+  H.psi = (float)(GM / (F(BP_M_MC) * rs * n1T));
+  H.A0 = (float)(-F(BP_M_PHI0) / n1T);
+  H.A1 = (float)(GM / (rs * n1T));
+  H.ant = (float)F(BP_M_ANT);
+  double xnt = (F(BP_M_ANT) > 0) ? F(BP_M_R500) * pow(1.0 / F(BP_M_ANT), 1.0 / P.n_nt) / rs : 1e30;
+  H.xnt = (float)fmin(xnt, 1e30);
+  return ok;
+}
+
 __global__ void k_hp_prep(BpParams P, int64_t nh, const double* __restrict__ thx,
                           const double* __restrict__ thy, const float* __restrict__ vlos,
                           const int32_t* __restrict__ map_id, const double* __restrict__ model,
@@ -79,9 +109,8 @@ __global__ void k_hp_prep(BpParams P, int64_t nh, const double* __restrict__ thx
   auto F = [&](int f) { return model[(int64_t)f * nh + k]; };
   HpHalo H;
   int mp = map_id ? map_id[k] : 0;
-  double rs = F(BP_M_RS), rf = F(BP_M_RF), T = F(BP_M_T), DA = F(BP_M_DA);
-  bool ok = status[k] == BP_HALO_OK && rs > 0 && rf > 0 && T > 0 && DA > 0 && mp >= 0 &&
-            mp < g.n_maps;
+  bool ok = hp_fill_profile(P, nh, k, vlos, model, status, H) && mp >= 0 && mp < g.n_maps;
+  double rf = F(BP_M_RF), DA = F(BP_M_DA);
   double rap = rf;
   if (ap_r500 > 0) rap = fmin(rap, ap_r500 * F(BP_M_R500));
   double px = DA * g.dtheta;  // Mpc per pixel at the halo
@@ -89,25 +118,8 @@ __global__ void k_hp_prep(BpParams P, int64_t nh, const double* __restrict__ thx
   H.cy = (thy[k] - g.theta0_y) / g.dtheta;
   H.rad_px = rap / DA / g.dtheta;
   H.inv_rf_px = (float)(px / rf);
-  // Table intervals per halo.  Coarser tables (64 or 128 intervals, 1.6e-5 and 1.4e-6
-  // interpolation error) broke the per-pixel kSZ tolerance where halos of opposite
-  // velocities cancel, so every halo uses the full resolution.
-  H.nt = HP_NT;
-  double n1T = (P.n_poly + 1.0) * T, GM = bpc::G * F(BP_M_MVIR);
-  H.Ay = (float)(P.CP * P.pe_frac * F(BP_M_P0) * 2.0 * rf);
-  double vk = vlos ? (double)vlos[k] : 0.0;
-  H.Ab = (float)(P.CN * F(BP_M_RHO0) * 2.0 * rf * (vk / bpc::C_KMS) * exp(-F(BP_M_TAU)));
   H.map = mp;
   H.ok = ok ? 1 : 0;
-  H.xf = (float)(rf / rs);
-  H.c = (float)F(BP_M_C);
-  H.q500 = (float)(rs / F(BP_M_R500));
-  H.psi = (float)(GM / (F(BP_M_MC) * rs * n1T));
-  H.A0 = (float)(-F(BP_M_PHI0) / n1T);
-  H.A1 = (float)(GM / (rs * n1T));
-  H.ant = (float)F(BP_M_ANT);
-  double xnt = (F(BP_M_ANT) > 0) ? F(BP_M_R500) * pow(1.0 / F(BP_M_ANT), 1.0 / P.n_nt) / rs : 1e30;
-  H.xnt = (float)fmin(xnt, 1e30);
   out[k] = H;
 }
 
@@ -647,6 +659,311 @@ int check_hp_args(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_y
   return BP_OK;
 }
 
+// ---------------------------------------------------------------- all-sky HP on HEALPix
+// All-sky maps (Section 5.2) with the HP of Section 3.3 on the HEALPix sphere (Gorski et
+// al. 2005), RING ordering: 12 nside^2 equal-area pixels on 4 nside - 1 rings of constant
+// colatitude.  A ring is cut into segments of HS_SEG consecutive pixels; (segment, halo)
+// pairs come from each halo's aperture cap ring by ring, are sorted by segment, and one CTA
+// per segment owns its pixels: it adds its halos in sorted order (fixed-order sums, no
+// atomics).  The pixel-halo angle uses the half-angle (haversine) form with the colatitude
+// difference taken in FP64 and the longitude offset in double-float pixel units, so that it
+// keeps FP32 relative accuracy down to sub-pixel separations at nside 8192.
+constexpr int HS_SEG = 256;  // pixels per segment = threads per paste CTA
+constexpr int HS_CH = 256;   // pairs staged in shared memory at a time
+
+struct HsRing {
+  double theta;      // colatitude of the ring's centres
+  int64_t first;     // RING index of its first pixel
+  float sin_t;       // sin(theta)
+  float phase;       // longitude of the first centre in units of dphi (0 or 1/2)
+  float dphi;        // 2 pi / cnt (for offsets of a few pixels only)
+  int32_t cnt;       // pixels on the ring
+  uint32_t seg0;     // id of its first segment
+  int32_t pad;
+};
+
+// Per-halo all-sky record: HpHalo with cx = colatitude, cy = longitude in [0, 2 pi),
+// rad_px = aperture angle [rad], inv_rf_px = D_A / r_f [1/rad].
+// Halos h0 .. h0 + m - 1 of a catalogue of n (the model is field-major over all n); out[k]
+// describes halo h0 + k.
+__global__ void k_hs_prep(BpParams P, int64_t n, int64_t h0, int64_t m,
+                          const double* __restrict__ theta, const double* __restrict__ phi,
+                          const float* __restrict__ vlos, const double* __restrict__ model,
+                          const int32_t* __restrict__ status, double ap_r500, HpHalo* out) {
+  const int64_t kl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (kl >= m) return;
+  const int64_t k = h0 + kl;
+  auto F = [&](int f) { return model[(int64_t)f * n + k]; };
+  HpHalo H;
+  const double th = theta[k], ph = phi[k];
+  bool ok = hp_fill_profile(P, n, k, vlos, model, status, H) && th >= 0.0 && th <= bpc::PI &&
+            isfinite(ph);
+  double rf = F(BP_M_RF), DA = F(BP_M_DA);
+  double rap = rf;
+  if (ap_r500 > 0) rap = fmin(rap, ap_r500 * F(BP_M_R500));
+  double pm = ok ? fmod(ph, 2.0 * bpc::PI) : 0.0;
+  if (pm < 0.0) pm += 2.0 * bpc::PI;
+  H.cx = ok ? th : 0.0;
+  H.cy = pm;
+  H.rad_px = ok ? fmin(rap / DA, bpc::PI) : 0.0;
+  H.inv_rf_px = (float)(DA / rf);
+  H.map = 0;
+  H.ok = ok ? 1 : 0;
+  out[kl] = H;
+}
+
+// first ring (0-based) whose colatitude is >= t
+__device__ __forceinline__ int hs_ring_at(const HsRing* __restrict__ R, int nr, double t) {
+  int lo = 0, hi = nr;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (R[mid].theta < t) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+// Pixels of ring G that the aperture of H may touch: [j0, j1] (centre indices, possibly
+// outside [0, cnt) and then wrapping; one pixel of margin each side), or the whole ring.
+// Returns false when the ring misses the cap.  The exact test is the paste's.
+__device__ __forceinline__ bool hs_ring_span(const HpHalo& H, const HsRing& G, bool& full,
+                                             int& j0, int& j1) {
+  const float dth = (float)(G.theta - H.cx);
+  const float alpha = (float)H.rad_px;
+  const float sa = sinf(0.5f * alpha), sd = sinf(0.5f * dth);
+  const float den = sinf((float)H.cx) * G.sin_t;
+  full = false;
+  if (!(den > 1e-30f)) {  // halo on a pole: the ring is entirely in or out
+    if (fabsf(dth) >= alpha) return false;
+    full = true;
+    return true;
+  }
+  const float q = (sa * sa - sd * sd) / den;  // sin^2(half longitude width)
+  if (q <= 0.f) return false;
+  if (q >= 1.f) {
+    full = true;
+    return true;
+  }
+  const float w = 2.0f * asinf(sqrtf(q)) / G.dphi + 1.0f;
+  const float e = (float)(H.cy * (double)G.cnt * (0.5 / bpc::PI)) - G.phase;
+  j0 = (int)floorf(e - w);
+  j1 = (int)ceilf(e + w);
+  if (j1 - j0 + 1 >= G.cnt) full = true;
+  return true;
+}
+
+// Segments of a ring span, in ascending order: calls f(segment id)
+template <typename Fn>
+__device__ __forceinline__ void hs_span_segments(const HsRing& G, bool full, int j0, int j1,
+                                                 Fn f) {
+  const int last = (G.cnt - 1) / HS_SEG;
+  if (!full) {
+    const int a = ((j0 % G.cnt) + G.cnt) % G.cnt, b = a + (j1 - j0);
+    if (b < G.cnt) {
+      for (int c = a / HS_SEG; c <= b / HS_SEG; ++c) f(G.seg0 + c);
+      return;
+    }
+    const int cb = (b - G.cnt) / HS_SEG, ca = a / HS_SEG;  // [0, cb] and [ca, last]
+    if (cb < ca) {
+      for (int c = 0; c <= cb; ++c) f(G.seg0 + c);
+      for (int c = ca; c <= last; ++c) f(G.seg0 + c);
+      return;
+    }
+  }
+  for (int c = 0; c <= last; ++c) f(G.seg0 + c);
+}
+
+__device__ __forceinline__ void hs_ring_range(const HpHalo& H, const HsRing* R, int nr, int& r0,
+                                              int& r1) {
+  r0 = hs_ring_at(R, nr, H.cx - H.rad_px);
+  r1 = hs_ring_at(R, nr, H.cx + H.rad_px) - 1;  // last ring with theta < cx + rad (+ margin)
+  if (r0 > 0) --r0;
+  if (r1 < nr - 1) ++r1;
+}
+
+__global__ void k_hs_count(const HpHalo* __restrict__ halos, int64_t nh,
+                           const HsRing* __restrict__ R, int nr, uint32_t* counts) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nh) return;
+  const HpHalo H = halos[k];
+  uint32_t c = 0;
+  if (H.ok) {
+    int r0, r1;
+    hs_ring_range(H, R, nr, r0, r1);
+    for (int r = r0; r <= r1; ++r) {
+      const HsRing G = R[r];
+      bool full;
+      int j0 = 0, j1 = 0;
+      if (hs_ring_span(H, G, full, j0, j1)) hs_span_segments(G, full, j0, j1, [&](uint32_t) { ++c; });
+    }
+  }
+  counts[k] = c;
+}
+
+__global__ void k_hs_emit(const HpHalo* __restrict__ halos, int64_t nh,
+                          const HsRing* __restrict__ R, int nr,
+                          const int64_t* __restrict__ offs, uint32_t* keys, uint32_t* vals) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nh) return;
+  const HpHalo H = halos[k];
+  if (!H.ok) return;
+  int64_t o = offs[k];
+  const int64_t end = offs[k + 1];
+  int r0, r1;
+  hs_ring_range(H, R, nr, r0, r1);
+  for (int r = r0; r <= r1; ++r) {
+    const HsRing G = R[r];
+    bool full;
+    int j0 = 0, j1 = 0;
+    if (hs_ring_span(H, G, full, j0, j1))
+      hs_span_segments(G, full, j0, j1, [&](uint32_t sg) {
+        if (o < end) {  // the count pass gave exactly this many
+          keys[o] = sg;
+          vals[o] = (uint32_t)k;
+          ++o;
+        }
+      });
+  }
+}
+
+// One CTA per segment: thread t owns pixel seg_start + t of the segment's ring.
+__global__ void __launch_bounds__(HS_SEG)
+    k_hs_paste(const HpHalo* __restrict__ halos, const float* __restrict__ tab,
+               const uint32_t* __restrict__ hvals, const int64_t* __restrict__ sstart,
+               const HsRing* __restrict__ R, int nr, float* ymap, float* bmap, float* ylo,
+               float* blo) {
+  __shared__ float s_dth2[HS_CH], s_sp[HS_CH], s_rh[HS_CH], s_rl[HS_CH], s_sa2[HS_CH];
+  __shared__ float s_irf[HS_CH], s_ay[HS_CH], s_ab[HS_CH];
+  __shared__ int2 s_rng[HS_CH];
+  __shared__ const float* s_tab[HS_CH];
+  __shared__ int s_nt[HS_CH];
+  const uint32_t sg = blockIdx.x;
+  const int64_t b0 = sstart[sg], b1 = sstart[sg + 1];
+  if (b0 == b1) return;
+  const int tid = threadIdx.x;
+  // the segment's ring: the last ring whose first segment is <= sg
+  int lo = 0, hi = nr - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (R[mid].seg0 <= sg) lo = mid; else hi = mid - 1;
+  }
+  const HsRing G = R[lo];
+  const int c0 = (int)(sg - G.seg0) * HS_SEG;  // ring-local index of the segment's first pixel
+  const int npx = min(HS_SEG, G.cnt - c0);
+  const bool whole = G.cnt <= HS_SEG;
+  float hy = 0.f, cy = 0.f, hb = 0.f, cb = 0.f;
+  for (int64_t base = b0; base < b1; base += HS_CH) {
+    const int nch = (int)min((int64_t)HS_CH, b1 - base);
+    __syncthreads();
+    if (tid < nch) {
+      const uint32_t hk = hvals[base + tid];  // index within the chunk
+      const HpHalo H = halos[hk];
+      const float dth = (float)(G.theta - H.cx);
+      const float sd = sinf(0.5f * dth);
+      s_dth2[tid] = sd * sd;
+      s_sp[tid] = sinf((float)H.cx) * G.sin_t;
+      // the halo's longitude in pixel units from the segment's first centre (FP64 from the
+      // exact pixel count: an FP32 spacing would misplace centres far along the ring by
+      // up to 2e-7 rad), the representative nearest the segment's middle, as a double-float
+      double rel = H.cy * (double)G.cnt * (0.5 / bpc::PI) - (double)G.phase - (double)c0;
+      rel -= (double)G.cnt * rint((rel - 0.5 * HS_SEG) / (double)G.cnt);
+      const float rh = (float)rel;
+      s_rh[tid] = rh;
+      s_rl[tid] = (float)(rel - (double)rh);
+      const float sa = sinf(0.5f * (float)H.rad_px);
+      s_sa2[tid] = sa * sa;
+      s_irf[tid] = H.inv_rf_px;
+      s_ay[tid] = H.Ay;
+      s_ab[tid] = H.Ab;
+      s_tab[tid] = tab + (int64_t)hk * 2 * HP_ROW;
+      s_nt[tid] = H.nt;
+      // the segment's pixels to test: all of them when the span can wrap into the segment
+      // from both sides, else the span around the representative
+      bool full;
+      int j0 = 0, j1 = 0;
+      int2 rg = make_int2(0, npx - 1);
+      if (!hs_ring_span(H, G, full, j0, j1)) {
+        rg = make_int2(1, 0);
+      } else if (!full && !whole && (j1 - j0) + HS_SEG < G.cnt) {
+        const float w = 0.5f * (float)(j1 - j0);
+        rg.x = max(0, (int)floorf(rh - w) - 1);
+        rg.y = min(npx - 1, (int)ceilf(rh + w) + 1);
+      }
+      s_rng[tid] = rg;
+    }
+    __syncthreads();
+    if (tid < npx) {
+      for (int q = 0; q < nch; ++q) {
+        const int2 rg = s_rng[q];
+        if (tid < rg.x || tid > rg.y) continue;
+        float dp = ((float)tid - s_rh[q]) - s_rl[q];  // longitude offset [pixels]
+        dp -= (float)G.cnt * rintf(dp / (float)G.cnt);
+        const float sp = sinf(0.5f * dp * G.dphi);
+        const float hav = s_dth2[q] + s_sp[q] * sp * sp;  // sin^2(psi / 2)
+        if (!(hav < s_sa2[q])) continue;
+        const float psi = 2.0f * asinf(sqrtf(hav));
+        const float uu = psi * s_irf[q];
+        if (uu < 1.0f) {
+          const float chord = sqrtf(fmaxf(0.f, 1.0f - uu * uu));
+          const float ss = sqrtf(uu);
+          const float* ty = s_tab[q];
+          const float gy = catmull(ty, ss, s_nt[q]), gb = catmull(ty + HP_ROW, ss, s_nt[q]);
+          kahan_add(hy, cy, s_ay[q] * chord * gy);
+          kahan_add(hb, cb, s_ab[q] * chord * gb);
+        }
+      }
+    }
+  }
+  if (tid < npx) {
+    const int64_t p = G.first + c0 + tid;
+    float sv, e;
+    bp_two_sum(ymap[p], hy, sv, e);
+    ymap[p] = sv;
+    ylo[p] = ylo[p] + (e - cy);
+    bp_two_sum(bmap[p], hb, sv, e);
+    bmap[p] = sv;
+    blo[p] = blo[p] + (e - cb);
+  }
+}
+
+// The ring table of nside N (host, FP64): 4N - 1 rings, segments counted along them.
+void hs_ring_table(int64_t N, HsRing* R, int64_t* n_seg) {
+  uint32_t seg = 0;
+  for (int64_t i = 1; i <= 4 * N - 1; ++i) {
+    HsRing G;
+    double z;
+    int64_t cnt, first;
+    double phase;
+    if (i < N) {
+      z = 1.0 - (double)(i * i) / (3.0 * (double)N * (double)N);
+      cnt = 4 * i;
+      first = 2 * i * (i - 1);
+      phase = 0.5;
+    } else if (i <= 3 * N) {
+      z = 4.0 / 3.0 - 2.0 * (double)i / (3.0 * (double)N);
+      cnt = 4 * N;
+      first = 2 * N * (N - 1) + 4 * N * (i - N);
+      phase = ((i + N) & 1) ? 0.0 : 0.5;
+    } else {
+      const int64_t k = 4 * N - i;
+      z = -(1.0 - (double)(k * k) / (3.0 * (double)N * (double)N));
+      cnt = 4 * k;
+      first = 12 * N * N - 2 * k * (k + 1);
+      phase = 0.5;
+    }
+    G.theta = acos(z);
+    G.first = first;
+    G.sin_t = (float)sqrt((1.0 - z) * (1.0 + z));
+    G.phase = (float)phase;
+    G.dphi = (float)(2.0 * bpc::PI / (double)cnt);
+    G.cnt = (int32_t)cnt;
+    G.seg0 = seg;
+    G.pad = 0;
+    R[i - 1] = G;
+    seg += (uint32_t)((cnt + HS_SEG - 1) / HS_SEG);
+  }
+  *n_seg = seg;
+}
+
 }  // namespace
 
 // A prepared halo paste: the work list of one catalogue and its own buffers.
@@ -842,6 +1159,94 @@ int bp_finalize_map(bp_ctx* ctx, const bp_map_geom* geom, float* ymap, float* bm
     BP_LAUNCH_CHECK(ctx, "finalize b");
   }
   bp_phase_end(ctx, BP_PH_FINALIZE);
+  return BP_OK;
+}
+
+int bp_paste_halos_healpix(bp_ctx* ctx, int64_t n, const double* theta, const double* phi,
+                           const float* v_los, const double* model, const int32_t* status,
+                           int nside, double ap_r500, float* ymap, float* bmap, float* ylo,
+                           float* blo) {
+  if (!ctx) return BP_EINVAL;
+  if (n < 0) return bp_fail(ctx, BP_EINVAL, "bp_paste_halos_healpix: n < 0");
+  if (nside < 1 || nside > 16384)
+    return bp_fail(ctx, BP_EINVAL, "bp_paste_halos_healpix: nside outside [1, 16384]");
+  if (ap_r500 < 0) return bp_fail(ctx, BP_EINVAL, "bp_paste_halos_healpix: ap_r500 < 0");
+  if (n == 0) return BP_OK;
+  if (n > (int64_t)UINT32_MAX) return bp_fail(ctx, BP_ERANGE, "bp_paste_halos_healpix: n >= 2^32");
+  if (!theta || !phi || !v_los || !model || !status || !ymap || !bmap || !ylo || !blo)
+    return bp_fail(ctx, BP_EINVAL, "bp_paste_halos_healpix: null pointer");
+  int r;
+  if ((r = hp_constants(ctx))) return r;
+  // ring table (cached per nside in the context's scratch)
+  const int nr = 4 * nside - 1;
+  std::vector<HsRing> hr(nr);
+  int64_t n_seg = 0;
+  hs_ring_table(nside, hr.data(), &n_seg);
+  HsRing* R;
+  if ((r = bp_ws(ctx, WS_MISC3, (size_t)nr * sizeof(HsRing), (void**)&R))) return r;
+  BP_CUDA(ctx, cudaMemcpyAsync(R, hr.data(), (size_t)nr * sizeof(HsRing), cudaMemcpyHostToDevice,
+                               ctx->stream));
+  // halos in chunks (bounded table memory); each chunk adds into the maps
+  const int64_t CHUNK = (int64_t)1 << 22;
+  for (int64_t h0 = 0; h0 < n; h0 += CHUNK) {
+    const int64_t m = std::min(CHUNK, n - h0);
+    HpHalo* halos;
+    float* tab;
+    if ((r = bp_ws(ctx, WS_HPAR, (size_t)m * sizeof(HpHalo), (void**)&halos))) return r;
+    if ((r = bp_ws(ctx, WS_TABLE, (size_t)m * 2 * HP_ROW * sizeof(float), (void**)&tab))) return r;
+    const unsigned nb = (unsigned)((m + 255) / 256);
+    bp_phase_begin(ctx, BP_PH_HP_TABLE);
+    k_hs_prep<<<nb, 256, 0, ctx->stream>>>(ctx->p, n, h0, m, theta, phi, v_los, model, status,
+                                           ap_r500, halos);
+    BP_LAUNCH_CHECK(ctx, "healpix prep");
+    const BpParams& P = ctx->p;
+    double rn = rint(P.n_poly);
+    int n_int = (fabs(P.n_poly - rn) < 1e-12 && rn >= 1 && rn <= 16) ? (int)rn : -1;
+    int64_t nt = m * (HP_NT + 1);
+    k_hp_table<<<(unsigned)((nt + 255) / 256), 256, 0, ctx->stream>>>(
+        halos, m, (float)P.n_poly, n_int, (float)P.n_nt, tab);
+    BP_LAUNCH_CHECK(ctx, "healpix table");
+    k_hp_ghosts<<<nb, 256, 0, ctx->stream>>>(halos, m, tab);
+    BP_LAUNCH_CHECK(ctx, "healpix ghosts");
+    bp_phase_end(ctx, BP_PH_HP_TABLE);
+    // (segment, halo) pairs sorted by segment
+    bp_phase_begin(ctx, BP_PH_HP_PAIRS);
+    uint32_t* counts;
+    int64_t* offs;
+    if ((r = bp_ws(ctx, WS_COUNTS, (size_t)(m + 1) * 4, (void**)&counts))) return r;
+    if ((r = bp_ws(ctx, WS_OFFS, (size_t)(m + 1) * 8, (void**)&offs))) return r;
+    k_hs_count<<<nb, 256, 0, ctx->stream>>>(halos, m, R, nr, counts);
+    BP_LAUNCH_CHECK(ctx, "healpix count");
+    if ((r = bp_scan_u32_to_i64(ctx, counts, offs, m))) return r;
+    BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, offs + m, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    BP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const int64_t np = ctx->h_pinned[0];
+    if (np > (int64_t)UINT32_MAX)
+      return bp_fail(ctx, BP_ERANGE, "bp_paste_halos_healpix: too many pairs");
+    if (np == 0) {
+      bp_phase_end(ctx, BP_PH_HP_PAIRS);
+      continue;
+    }
+    uint32_t *k0, *v0, *k1, *v1, *ks, *vs;
+    if ((r = bp_ws(ctx, WS_KEYS0, (size_t)np * 4, (void**)&k0))) return r;
+    if ((r = bp_ws(ctx, WS_VALS0, (size_t)np * 4, (void**)&v0))) return r;
+    if ((r = bp_ws(ctx, WS_KEYS1, (size_t)np * 4, (void**)&k1))) return r;
+    if ((r = bp_ws(ctx, WS_VALS1, (size_t)np * 4, (void**)&v1))) return r;
+    k_hs_emit<<<nb, 256, 0, ctx->stream>>>(halos, m, R, nr, offs, k0, v0);
+    BP_LAUNCH_CHECK(ctx, "healpix emit");
+    int key_bits = 0;
+    while (((int64_t)1 << key_bits) < n_seg) ++key_bits;
+    if ((r = bp_radix_sort_pairs(ctx, k0, v0, k1, v1, np, key_bits, &ks, &vs))) return r;
+    int64_t* sstart;
+    if ((r = bp_ws(ctx, WS_TILES, (size_t)(n_seg + 1) * 8, (void**)&sstart))) return r;
+    if ((r = bp_tile_ranges(ctx, ks, np, n_seg, sstart))) return r;
+    bp_phase_end(ctx, BP_PH_HP_PAIRS);
+    bp_phase_begin(ctx, BP_PH_HP_PASTE);
+    k_hs_paste<<<(unsigned)n_seg, HS_SEG, 0, ctx->stream>>>(halos, tab, vs, sstart, R, nr, ymap,
+                                                            bmap, ylo, blo);
+    BP_LAUNCH_CHECK(ctx, "healpix paste");
+    bp_phase_end(ctx, BP_PH_HP_PASTE);
+  }
   return BP_OK;
 }
 

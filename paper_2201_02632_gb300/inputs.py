@@ -123,6 +123,32 @@ def batched_catalog(n_maps=108, mean_halos=5e4, seed=SEED_BASE + 3, side_deg=5.0
     return HaloCatalog(M, c, z, thx, thy, vlos, map_id=map_id), g
 
 
+def allsky_catalog(n, seed=SEED_BASE + 5, logm=None, zr=(0.01, 3.0), volume=True,
+                   n_polar=0):
+    """All-sky halo catalogue: directions uniform on the sphere (colatitude theta, longitude
+    phi), masses dN/dlnM ~ M^-0.9 on [1e12, 1e15] (or log-uniform on logm), redshifts
+    uniform in comoving volume on zr (or uniform in z), v_los ~ N(0, 300 km/s).  n_polar
+    of the halos are put within 0.02 rad of a pole (half north, half south)."""
+    rng = np.random.default_rng(seed)
+    M = powerlaw_masses(rng, n) if logm is None else 10.0 ** rng.uniform(logm[0], logm[1], n)
+    c = _concentration(rng, M)
+    if volume:
+        ztab, chitab = _chi_table(zr[1] * 1.05)
+        c0, c1 = np.interp(zr, ztab, chitab)
+        chi = (c0 ** 3 + rng.uniform(0.0, 1.0, n) * (c1 ** 3 - c0 ** 3)) ** (1.0 / 3.0)
+        z = np.interp(chi, chitab, ztab)
+    else:
+        z = rng.uniform(zr[0], zr[1], n)
+    theta = np.arccos(rng.uniform(-1.0, 1.0, n))
+    phi = rng.uniform(0.0, 2 * math.pi, n)
+    if n_polar:
+        k = rng.choice(n, n_polar, replace=False)
+        t = rng.uniform(0.0, 0.02, n_polar)
+        theta[k] = np.where(np.arange(n_polar) % 2 == 0, t, math.pi - t)
+    vlos = rng.normal(0.0, 300.0, n).astype(np.float32)
+    return {"M": M, "c": c, "z": z, "theta": theta, "phi": phi, "vlos": vlos}
+
+
 def _cone_points(rng, n, tan_half, chi_lo, chi_hi):
     """Points uniform in comoving volume with |x/z|,|y/z| <= tan_half and chi in range."""
     out = np.empty((0, 3))
