@@ -418,3 +418,34 @@ def solve_referenced(M, c, z, hid_subset, cp=None, ip=None, nthreads=0):
         models[h] = solve_halos(np.asarray(M)[h], np.asarray(c)[h], np.asarray(z)[h], cp, ip,
                                 nthreads=nthreads)
     return models
+
+
+# ---------------------------------------------------------------- Section 5.3
+def power_spectrum(m, dtheta, edges):
+    """Flat-sky angular power spectrum of a map [ny, nx] (FP64, numpy FFT): with
+    a(l) = dtheta^2 sum f e^{-i l.theta}, l = 2 pi (kx / (nx dtheta), ky / (ny dtheta)),
+    returns the mean of |a|^2 / (nx ny dtheta^2) over the modes with edges[b] <= |l| <
+    edges[b + 1] and the mode counts.  Each mode's |l|^2 is formed as
+    (4 pi pi) ((kx / Lx)^2 + (ky / Ly)^2) with 1 / L precomputed, compared with edges^2."""
+    f = np.asarray(m, np.float64)
+    ny, nx = f.shape
+    F = np.fft.fft2(f)
+    power = (dtheta * dtheta / (nx * ny)) * (F.real * F.real + F.imag * F.imag)
+    fx = np.fft.fftfreq(nx, 1.0 / nx)  # integer frequencies, [-n/2, n/2)
+    fy = np.fft.fftfreq(ny, 1.0 / ny)
+    ux = fx * (1.0 / (nx * dtheta))
+    uy = fy * (1.0 / (ny * dtheta))
+    l2 = (4.0 * np.pi * np.pi) * (ux[None, :] * ux[None, :] + uy[:, None] * uy[:, None])
+    e = np.asarray(edges, np.float64)
+    e2 = e * e
+    nb = e.size - 1
+    b = np.searchsorted(e2, l2, side="right") - 1
+    ok = (l2 >= e2[0]) & (l2 < e2[-1])
+    cl = np.zeros(nb)
+    cnt = np.zeros(nb, np.int64)
+    for k in range(nb):
+        sel = ok & (b == k)
+        cnt[k] = sel.sum()
+        if cnt[k]:
+            cl[k] = power[sel].sum() / cnt[k]
+    return cl, cnt
