@@ -406,6 +406,32 @@ def allsky_section(api, ctx, dev, args):
     return out
 
 
+def spectrum_section(api, ctx, dev, maps_y, dtheta):
+    """Flat-sky C_l (30 logarithmic bins, 1e2-1e5) of the step's y map and of a 4096^2 map;
+    FP64 FFT (5 n log2 n flops per map)."""
+    import torch
+
+    out = {}
+    for name, m, d in (("step_y_map", maps_y, dtheta),
+                       ("map_4096", torch.randn((4096, 4096), device=dev), dtheta / 4)):
+        for _ in range(3):
+            ctx.power_spectrum(m, d)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            ctx.power_spectrum(m, d)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        t = float(np.median(ts))
+        npx = m.numel()
+        flops = 5.0 * npx * math.log2(npx)
+        out[name] = {"shape": list(m.shape), "ms": t, "fp64_tflops": flops / (t * 1e-3) / 1e12}
+    return out
+
+
 def batched_section(api, ctx, dev, args):
     """Batched HP: many independent maps of uneven halo extents pasted by one prepared
     plan (one persistent launch), autotuned, captured in a CUDA graph and replayed."""
@@ -694,6 +720,7 @@ def run_ours(args):
         res["surrogate"] = surrogate_section(api, ctx, dev, lc, args)
     if not args.no_hsml:
         res["smoothing_lengths"] = hsml_section(api, ctx, dev, lc, args)
+    res["power_spectrum"] = spectrum_section(api, ctx, dev, pp.y[0], g.dtheta)
     if not args.no_batched:
         res["batched_hp"] = batched_section(api, ctx, dev, args)
     if not args.no_allsky:

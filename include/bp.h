@@ -377,6 +377,19 @@ int bp_paste_halos_healpix(bp_ctx* ctx, int64_t n, const double* theta, const do
                            int nside, double ap_r500, float* ymap, float* bmap, float* ylo,
                            float* blo);
 
+/* Section 5.3: the angular power spectrum of a flat-sky map (the FFT of the map, binned in
+ * multipole).  map (+ lo when not NULL): device FP32 [ny][nx] of square pixels of side dtheta
+ * [rad]; nx, ny powers of two in [2, 8192].  With a(l) = dtheta^2 sum_pixels f e^{-i l.theta}
+ * and l = 2 pi (kx / (nx dtheta), ky / (ny dtheta)) for the integer frequencies (kx in
+ * [-nx/2, nx/2)), cl[b] is the mean of |a(l)|^2 / (nx ny dtheta^2) over the modes with
+ * edges[b] <= |l| < edges[b + 1] (0 for an empty bin), nmodes[b] their count.  edges: HOST
+ * FP64 [nb + 1], increasing from >= 0, nb in [1, 256] (the paper uses 30 logarithmic bins
+ * over 1e2 < l < 1e5); cl: device FP64 [nb]; nmodes: device int64 [nb] or NULL.  FP64
+ * throughout; deterministic.  Synchronises once (uploads twiddles and edges).  Errors:
+ * BP_EINVAL (sizes, dtheta, edges, null pointer). */
+int bp_power_spectrum(bp_ctx* ctx, const float* map, const float* lo, int nx, int ny,
+                      double dtheta, int nb, const double* edges, double* cl, int64_t* nmodes);
+
 /* A prepared halo paste for repeated pastes of one catalogue (many maps of uneven halo
  * extents in one persistent launch).  bp_hp_plan_create builds the (map, tile, halo)
  * work list from the catalogue's apertures (as bp_paste_halos does; synchronises) and

@@ -28,7 +28,7 @@ EXPORTS = ("bp_create", "bp_destroy", "bp_last_error", "bp_set_stream", "bp_set_
            "bp_set_deposit_kernel",
            "bp_workspace_bytes", "bp_set_timing", "bp_phase_times", "bp_kernel_launches",
            "bp_solve_halos", "bp_assign_particles", "bp_paste_particles", "bp_pp_pairs",
-           "bp_smoothing_lengths", "bp_paste_halos_healpix",
+           "bp_smoothing_lengths", "bp_paste_halos_healpix", "bp_power_spectrum",
            "bp_paste_halos", "bp_finalize_map", "bp_paste_particles_noalloc",
            "bp_solve_halos_ex", "bp_last_fallback_count", "bp_mlp_forward", "bp_mlp_backward",
            "bp_mlp_adam", "bp_mlp_to_bf16", "bp_mlp_infer_bf16", "bp_mlp_features",
@@ -103,6 +103,7 @@ def load():
                                                      P]),
                 "bp_smoothing_lengths": (i32, [P, i64, P, P, P, d, P, P]),
                 "bp_paste_halos_healpix": (i32, [P, i64, P, P, P, P, P, i32, d, P, P, P, P]),
+                "bp_power_spectrum": (i32, [P, P, P, i32, i32, d, i32, P, P, P]),
                 "bp_pp_pairs": (i32, [P, i64, P, C.POINTER(BpGeom), i32, i32, P, P, i64,
                                       C.POINTER(i64)]),
                 "bp_paste_halos": (i32, [P, i64, P, P, P, P, P, P, C.POINTER(BpGeom), d, P, P, P,

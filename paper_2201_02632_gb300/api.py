@@ -8,13 +8,14 @@ from __future__ import annotations
 import ctypes as C
 from dataclasses import dataclass
 
+import numpy as np
 import torch
 
 from . import _lib as L
 from ._lib import (ASSIGNED_STRIDE, KIND_FIELD, KIND_HALO, KIND_NONE, MF, MODEL_FIELDS,
                    OUT_DT, OUT_YB, SELECT_ALL, SELECT_FIELD, SELECT_HALO, BpError)
 
-__all__ = ["Context", "Maps", "geom", "healpix_geom", "healpix_maps", "MF", "MODEL_FIELDS", "ASSIGNED_STRIDE", "KIND_HALO",
+__all__ = ["Context", "Maps", "geom", "healpix_geom", "healpix_maps", "default_ell_edges", "MF", "MODEL_FIELDS", "ASSIGNED_STRIDE", "KIND_HALO",
            "KIND_FIELD", "KIND_NONE", "SELECT_ALL", "SELECT_HALO", "SELECT_FIELD", "OUT_YB",
            "OUT_DT", "BpError"]
 
@@ -54,6 +55,11 @@ class Maps:
         for t in (self.y, self.b, self.ylo, self.blo):
             t.zero_()
         return self
+
+
+def default_ell_edges(lmin=1e2, lmax=1e5, nbins=30):
+    """Logarithmic multipole bin edges (the paper's flat-sky binning: 30 bins, 1e2-1e5)."""
+    return 10.0 ** np.linspace(np.log10(lmin), np.log10(lmax), nbins + 1)
 
 
 def healpix_geom(nside) -> L.BpGeom:
@@ -340,6 +346,24 @@ class Context:
             _ptr(maps.ylo, f32, "ylo"), _ptr(maps.blo, f32, "blo"))
         self._check(rc)
         return maps
+
+    def power_spectrum(self, m, dtheta, edges=None, lo=None):
+        """Binned flat-sky C_l of an FP32 map [ny, nx] (Section 5.3).  edges: multipole bin
+        edges (default 30 logarithmic bins on [1e2, 1e5]).  Returns (l_centres, C_l,
+        n_modes) with C_l and n_modes on the device."""
+        if edges is None:
+            edges = default_ell_edges()
+        e = np.ascontiguousarray(edges, dtype=np.float64)
+        ny, nx = m.shape[-2], m.shape[-1]
+        nb = e.size - 1
+        cl = torch.empty(nb, dtype=torch.float64, device=m.device)
+        nm = torch.empty(nb, dtype=torch.int64, device=m.device)
+        rc = self._L.bp_power_spectrum(
+            self._h, _ptr(m, torch.float32, "map"), _ptr(lo, torch.float32, "lo"), int(nx),
+            int(ny), float(dtheta), nb, e.ctypes.data_as(C.c_void_p), _ptr(cl, torch.float64, "cl"),
+            _ptr(nm, torch.int64, "nmodes"))
+        self._check(rc)
+        return np.sqrt(e[:-1] * e[1:]), cl, nm
 
     def hp_plan(self, thx, thy, model, status, g: L.BpGeom, ap_r500=0.0, map_id=None, tile=32,
                 unit=0, ctas_per_sm=0):
