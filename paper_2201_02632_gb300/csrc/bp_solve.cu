@@ -213,18 +213,6 @@ struct Solver {
     b = hi * rs;
     return true;
   }
-  __device__ static bool panel_b(int p, double rv, double rf, double& a, double& b) {
-    double lo = rv, hi = fmin(2.0 * rv, rf);
-    for (int k = 0; k < p; ++k) {
-      if (hi >= rf) return false;
-      lo = hi;
-      hi = fmin(2.0 * hi, rf);
-    }
-    if (!(hi > lo)) return false;
-    a = lo;
-    b = hi;
-    return true;
-  }
   // region A nodes up to x = xa of this lane into the slots (r2w, phi); returns the
   // slots in use (panels are filled in order, so the used slots come first)
   __device__ int nodes_a(int lane, double xa, double (&r2w)[4], double (&phi)[4]) const {
@@ -256,10 +244,14 @@ struct Solver {
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
       const int q = lane + 32 * t, p = q / NGL, j = q % NGL;
-      double a, b;
       f_r2w[t] = 0.0;
       f_phi[t] = h.phi0;
-      if (q >= MAX_PANEL_B * NGL || !panel_b(p, h.rvir, rf, a, b)) continue;
+      // panel p of region B: [2^p r_vir, min(2^(p+1) r_vir, r_f)], present while
+      // 2^p r_vir < r_f (doubling panels from r_vir to r_f)
+      if (q >= MAX_PANEL_B * NGL) continue;
+      const double a = h.rvir * (double)(1 << p);
+      if (!(a < rf)) continue;
+      const double b = fmin(2.0 * a, rf);
       double mid = 0.5 * (a + b), hw = 0.5 * (b - a);
       double r = mid + hw * c_glx[j];
       f_r2w[t] = hw * c_glw[j] * r * r;
@@ -279,9 +271,10 @@ struct Solver {
     s.Jn += r2w * tn * phi;
   }
   // gas integrals over [0, r_f] of the r_f last given to set_rf, at temperature T
-  __device__ Sums integrals(double T) const {
+  __device__ Sums integrals(double T) const { return integrals_inv(1.0 / ((n + 1.0) * T)); }
+  // the same with inv_n1T = 1 / ((n + 1) T) given
+  __device__ Sums integrals_inv(double inv_n1T) const {
     Sums s = {0, 0, 0, 0, 0};
-    double inv_n1T = 1.0 / ((n + 1.0) * T);
     if (full_a) {
 #pragma unroll
       for (int t = 0; t < 4; ++t)
@@ -553,39 +546,44 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve(
     double Rm, Re, J[2][2], thf, rho0;
     int ok;
   };
-  auto direct = [&](double T, double rf) -> Direct {
+  // (phif = Phi(r_f) given: the caller has it from its step control.)  Divisions, each a
+  // dozen instructions on the slow FP64 pipe, are reduced to four reciprocals.
+  const double inv_np1 = 1.0 / (nn + 1.0), inv_fbM = 1.0 / fbM, inv_absE = 1.0 / absE;
+  auto direct = [&](double T, double rf, double phif) -> Direct {
     Direct d;
     d.ok = 0;
-    double phif = phi_of(h, rf);
-    double thf = 1.0 + (h.phi0 - phif) / ((nn + 1.0) * T);
+    const double inv_T = 1.0 / T;
+    const double inv_n1T = inv_T * inv_np1;
+    double thf = 1.0 + (h.phi0 - phif) * inv_n1T;
     if (!(thf > 0.0)) return d;
     S.set_rf(rf, lane);
-    Sums sm = S.integrals(T);
-    double rho0 = h.Ps / (T * S.pw(thf, 2));
+    Sums sm = S.integrals_inv(inv_n1T);
+    double rho0 = h.Ps * inv_T / S.pw(thf, 2);
     double In = sm.In, Ip = sm.Ip, Im = sm.Im, Jm = sm.Jm, Jn = sm.Jn;
     double Egf = four_pi * rho0 * (1.5 * T * Ip + Jn);
     double dEp = four_pi / 3.0 * (r3v - rf * rf * rf) * h.Ps;
     double num = (P.energy_sign == 0) ? (Egf - h.Egi - inj - dEp) : (h.Egi - Egf - inj - dEp);
-    d.Re = num / absE;
-    d.Rm = (four_pi * rho0 * In + h.Mstar) / fbM - 1.0;
-    double dphif = bpc::G * menc_of(h, rf) / (rf * rf);
-    double dthf_drf = -dphif / ((nn + 1.0) * T);
-    double dlr_drf = -(nn + 1.0) * dthf_drf / thf;
-    double dlr_dT = (-1.0 - (nn + 1.0) * (1.0 - thf) / thf) / T;
+    d.Re = num * inv_absE;
+    d.Rm = (four_pi * rho0 * In + h.Mstar) * inv_fbM - 1.0;
+    const double inv_rf = 1.0 / rf, inv_thf = 1.0 / thf;
+    double dphif = bpc::G * menc_of(h, rf) * inv_rf * inv_rf;
+    double dthf_drf = -dphif * inv_n1T;
+    double dlr_drf = -(nn + 1.0) * dthf_drf * inv_thf;
+    double dlr_dT = (-1.0 - (nn + 1.0) * (1.0 - thf) * inv_thf) * inv_T;
     double tfn = S.pw(thf, 1), tfp = tfn * thf;
     double dG_drf = four_pi * rho0 * (In * dlr_drf + tfn * rf * rf);
-    double dG_dT = four_pi * rho0 * (In * dlr_dT + nn * (Im - In) / T);
-    double dIp_dT = (nn + 1.0) * (In - Ip) / T;
-    double dJn_dT = nn * (Jm - Jn) / T;
+    double dG_dT = four_pi * rho0 * (In * dlr_dT + nn * (Im - In) * inv_T);
+    double dIp_dT = (nn + 1.0) * (In - Ip) * inv_T;
+    double dJn_dT = nn * (Jm - Jn) * inv_T;
     double dEgf_drf = Egf * dlr_drf + four_pi * rho0 * (1.5 * T * tfp + tfn * phif) * rf * rf;
     double dEgf_dT = Egf * dlr_dT + four_pi * rho0 * (1.5 * Ip + 1.5 * T * dIp_dT + dJn_dT);
     double ddEp_drf = -four_pi * rf * rf * h.Ps;
     double dn_dT = (P.energy_sign == 0) ? dEgf_dT : -dEgf_dT;
     double dn_drf = (P.energy_sign == 0) ? (dEgf_drf - ddEp_drf) : (-dEgf_drf - ddEp_drf);
-    d.J[0][0] = dG_dT * T / fbM;
-    d.J[0][1] = dG_drf * rf / fbM;
-    d.J[1][0] = dn_dT * T / absE;
-    d.J[1][1] = dn_drf * rf / absE;
+    d.J[0][0] = dG_dT * T * inv_fbM;
+    d.J[0][1] = dG_drf * rf * inv_fbM;
+    d.J[1][0] = dn_dT * T * inv_absE;
+    d.J[1][1] = dn_drf * rf * inv_absE;
     d.thf = thf;
     d.rho0 = rho0;
     d.ok = 1;
@@ -610,37 +608,46 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve(
   double rf = exp(v);
   // Two-dimensional Newton in (u, v) = (ln T, ln r_f), one quadrature evaluation per
   // iteration, steps halved to keep theta(r_f) > 0.  Returns true when both residuals
-  // are below tol; (e, rf) hold the last evaluated point (e.ok = 0 if it failed).
-  auto newton2d = [&](double u, double& vv, int max_it, Eval& ee, double& rff) -> bool {
+  // are below tol; (ee, rff) hold the last evaluated point (ee.ok = 0 if it failed).
+  // The step is applied multiplicatively, T e^du and r_f e^dv, with e^d from its series
+  // to fourth order (|d| <= 0.5; the residuals are evaluated at the point actually
+  // reached, so the update only has to be a good Newton step, and near the root it is
+  // exact to rounding); Phi(r_f) of the accepted point carries into the next evaluation.
+  auto expq = [](double d) { return 1.0 + d * (1.0 + d * (0.5 + d * (1.0 / 6.0 + d * (1.0 / 24.0)))); };
+  auto newton2d = [&](double T, double& rff, int max_it, Eval& ee) -> bool {
     ee.ok = 0;
+    const double rmin = 0.5 * h.rvir, rmax = 10.0 * h.rvir;
+    double phif = phi_of(h, rff);
     for (int it = 0; it < max_it; ++it) {
-      double T = exp(u);
-      rff = exp(vv);
-      Direct d = direct(T, rff);
+      Direct d = direct(T, rff, phif);
       if (!d.ok) { ee.ok = 0; return false; }
       ee.T = T; ee.thf = d.thf; ee.rho0 = d.rho0; ee.Rm = d.Rm; ee.Re = d.Re; ee.ok = 1;
       if (fabs(d.Re) < tol && fabs(d.Rm) < tol) return true;
       double det = d.J[0][0] * d.J[1][1] - d.J[0][1] * d.J[1][0];
       if (!(fabs(det) > 0.0) || !isfinite(det)) return false;
-      double du = (-d.Rm * d.J[1][1] + d.Re * d.J[0][1]) / det;
-      double dv = (-d.Re * d.J[0][0] + d.Rm * d.J[1][0]) / det;
+      const double idet = 1.0 / det;
+      double du = (-d.Rm * d.J[1][1] + d.Re * d.J[0][1]) * idet;
+      double dv = (-d.Re * d.J[0][0] + d.Rm * d.J[1][0]) * idet;
       double big = fmax(fabs(du), fabs(dv));
       if (big > 0.5) { du *= 0.5 / big; dv *= 0.5 / big; }
+      double Tn = T, rn = rff, phin = phif;
       for (int half = 0; half < 20; ++half) {
-        double vn = fmin(fmax(vv + dv, vmin), vmax);
-        double Tmin_n = (phi_of(h, exp(vn)) - h.phi0) / (nn + 1.0);
-        if (exp(u + du) > Tmin_n * (1.0 + 1e-12)) break;
+        rn = fmin(fmax(rff * expq(dv), rmin), rmax);
+        phin = phi_of(h, rn);
+        Tn = T * expq(du);
+        if (Tn > (phin - h.phi0) * inv_np1 * (1.0 + 1e-12)) break;
         du *= 0.5;
         dv *= 0.5;
       }
-      u += du;
-      vv = fmin(fmax(vv + dv, vmin), vmax);
+      T = Tn;
+      rff = rn;
+      phif = phin;
     }
     return false;
   };
   if (X.guess && Tw > 0.0) {
     // polish from the given starting point
-    if (newton2d(log(Tw), v, X.max_outer, e, rf)) st = BP_HALO_OK;
+    if (newton2d(Tw, rf, X.max_outer, e)) st = BP_HALO_OK;
   } else {
   double va = 0, vb = 0, Ra = 0;  // bracket [va, vb] with R(va) R(vb) < 0
   bool have_br = false;
@@ -658,9 +665,9 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve(
       // close to the root: finish with the two-dimensional Newton (one quadrature per
       // step instead of an inner solve per step); on failure continue the nested one
       tried2d = true;
-      double v2 = v, rf2 = rf;
+      double rf2 = rf;
       Eval e2;
-      if (newton2d(log(e.T), v2, 8, e2, rf2)) {
+      if (newton2d(e.T, rf2, 8, e2)) {
         e = e2;
         rf = rf2;
         st = BP_HALO_OK;
@@ -874,7 +881,7 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_presolve(
       const float Egi = (float)H.Egi, absE = fabsf(Egi);
       const float r3v = h.rvir * h.rvir * h.rvir;
       const float four_pi = (float)(4.0 * bpc::PI);
-      const float lnTarget = logf(fbM - Mstar);
+      const float inv_target = 1.0f / (fbM - Mstar);
       SolverF S(h, nn, n_int);
       S.cache_region_a(lane);
       // reduced problem at r_f: T from the gas-mass condition, then R_e and dR_e/dln r_f
@@ -892,9 +899,10 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_presolve(
           thf = 1.0f + (h.phi0 - phif) / ((nn + 1.0f) * T);
           sm = S.integrals(T);
           rho0 = Ps / (T * S.pw(thf, 2));
-          F = logf(four_pi * rho0 * sm.In) - lnTarget;
+          // the log of the ratio: a difference of two logs near 35 would floor F at 4e-6
+          F = logf(four_pi * rho0 * sm.In * inv_target);
           if (!isfinite(F)) return false;
-          if (fabsf(F) < 1e-5f) break;  // near the FP32 floor of F
+          if (fabsf(F) < 1e-6f) break;  // near the FP32 floor of F
           if (F > 0) slo = s; else shi = s;
           const float dlr = (-1.0f - (nn + 1.0f) * (1.0f - thf) / thf) / T;
           const float dli = nn * (sm.Im - sm.In) / (T * sm.In);
@@ -934,13 +942,21 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_presolve(
       float v = logf(1.1f * h.rvir), Tw = 0.f, vprev = 0.f, Rprev = 0.f, va = 0.f, vb = 0.f,
             Ra = 0.f;
       bool have_prev = false, have_br = false, done = false;
+      float v_ok = 0.f, T_ok = 0.f;
       for (int it = 0; it < 40; ++it) {
         const float rf = expf(v);
         if (!reduced(rf, Tw)) break;
         Tw = T;
         if (fabsf(Re) < 1e-4f) {
+          // one Newton step more (quadratic from here) takes R_e to the FP32 floor of a
+          // few 1e-6, so that the FP64 polish needs one step instead of two
+          const bool again = !done && fabsf(Re) > 2e-6f;
           done = true;
-          break;
+          v_ok = v;
+          T_ok = T;
+          if (!again) break;
+        } else if (done) {
+          break;  // the extra step went astray: keep the point below 1e-4
         }
         if (have_prev && ((Re > 0) != (Rprev > 0))) {
           have_br = true;
@@ -960,8 +976,8 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_presolve(
         v = vn;
       }
       if (done) {
-        g0 = v - logf(h.rvir);
-        g1 = logf(Tw * h.rvir / h.GM);
+        g0 = v_ok - logf(h.rvir);
+        g1 = logf(T_ok * h.rvir / h.GM);
       }
     }
     if (lane == 0) {
