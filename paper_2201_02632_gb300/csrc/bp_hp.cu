@@ -156,6 +156,61 @@ __device__ __forceinline__ void profile_pn(const HpHalo& H, float x, float n_pol
   p = tn * th * fmaxf(0.f, 1.0f - Rnt);
 }
 
+// The line-of-sight integrals of the dimensionless pressure and density at projected radius
+// u = r_perp / r_f in [0, 1), in units of r_f, NOT divided by the chord (Eqs. y^HP, b^HP):
+// 12-point Gauss-Legendre per segment, split where the 3-D radius crosses r_vir and the zero
+// of the thermal fraction; u = 0 in t directly, u > 0 after t = u sinh(s).
+__device__ __forceinline__ void hp_los(const HpHalo& H, float u, float n_poly, int n_int,
+                                       float n_nt, float& Sy, float& Sb) {
+  const float kinks[2] = {H.c / H.xf, H.xnt / H.xf};
+  float segs[4];
+  int ns = 0;
+  float sy = 0.f, sb = 0.f;
+  if (u == 0.f) {
+    segs[ns++] = 0.f;
+    for (int q = 0; q < 2; ++q)
+      if (kinks[q] > 0.f && kinks[q] < 1.0f) segs[ns++] = kinks[q];
+    segs[ns++] = 1.0f;
+    if (ns == 4 && segs[1] > segs[2]) { float t = segs[1]; segs[1] = segs[2]; segs[2] = t; }
+    for (int s = 0; s + 1 < ns; ++s) {
+      float a = segs[s], b = segs[s + 1], mid = 0.5f * (a + b), hw = 0.5f * (b - a);
+      for (int j = 0; j < HP_NGL; ++j) {
+        float t = mid + hw * c_hgx[j];
+        float p, d;
+        profile_pn(H, t * H.xf, n_poly, n_int, n_nt, p, d);
+        sy += hw * c_hgw[j] * p;
+        sb += hw * c_hgw[j] * d;
+      }
+    }
+  } else {
+    // t = u sinh(s): r/r_f = u cosh(s); s in [0, asinh(L/u)]
+    const float L = sqrtf(fmaxf(0.f, 1.0f - u * u));
+    float smax = asinhf(L / u);
+    segs[ns++] = 0.f;
+    for (int q = 0; q < 2; ++q)
+      if (kinks[q] > u && kinks[q] < 1.0f) {
+        float sk = acoshf(kinks[q] / u);
+        if (sk > 0.f && sk < smax) segs[ns++] = sk;
+      }
+    segs[ns++] = smax;
+    if (ns == 4 && segs[1] > segs[2]) { float t = segs[1]; segs[1] = segs[2]; segs[2] = t; }
+    for (int s = 0; s + 1 < ns; ++s) {
+      float a = segs[s], b = segs[s + 1], mid = 0.5f * (a + b), hw = 0.5f * (b - a);
+      for (int j = 0; j < HP_NGL; ++j) {
+        float sv = mid + hw * c_hgx[j];
+        float ch = coshf(sv);
+        float p, d;
+        profile_pn(H, u * ch * H.xf, n_poly, n_int, n_nt, p, d);
+        float wj = hw * c_hgw[j] * u * ch;
+        sy += wj * p;
+        sb += wj * d;
+      }
+    }
+  }
+  Sy = sy;
+  Sb = sb;
+}
+
 __global__ void __launch_bounds__(256) k_hp_table(const HpHalo* __restrict__ halos, int64_t nh,
                                                   float n_poly, int n_int, float n_nt,
                                                   float* tab) {
@@ -164,7 +219,7 @@ __global__ void __launch_bounds__(256) k_hp_table(const HpHalo* __restrict__ hal
   int node = (int)(gid % (HP_NT + 1));
   if (k >= nh) return;
   const HpHalo H = halos[k];
-  if (node > H.nt) return;
+  if (node > H.nt || H.nt == 0) return;  // nt = 0: evaluated at its pixels, no table
   const int NTh = H.nt;
   float* ty = tab + k * 2 * HP_ROW;
   float* tb = ty + HP_ROW;
@@ -181,58 +236,12 @@ __global__ void __launch_bounds__(256) k_hp_table(const HpHalo* __restrict__ hal
     Gy = p;
     Gb = d;
   } else {
-    float L = sqrtf(fmaxf(0.f, 1.0f - u * u));  // chord half-length in units of r_f
-    // radii (in units of r_f) where the integrand has a kink
-    float kinks[2] = {H.c / H.xf, H.xnt / H.xf};
-    float segs[4];
-    int ns = 0;
-    if (node == 0) {
-      // u = 0: integrate in t directly
-      segs[ns++] = 0.f;
-      for (int q = 0; q < 2; ++q)
-        if (kinks[q] > 0.f && kinks[q] < 1.0f) segs[ns++] = kinks[q];
-      segs[ns++] = 1.0f;
-      if (ns == 4 && segs[1] > segs[2]) { float t = segs[1]; segs[1] = segs[2]; segs[2] = t; }
-      float sy = 0.f, sb = 0.f;
-      for (int s = 0; s + 1 < ns; ++s) {
-        float a = segs[s], b = segs[s + 1], mid = 0.5f * (a + b), hw = 0.5f * (b - a);
-        for (int j = 0; j < HP_NGL; ++j) {
-          float t = mid + hw * c_hgx[j];
-          float p, d;
-          profile_pn(H, t * H.xf, n_poly, n_int, n_nt, p, d);
-          sy += hw * c_hgw[j] * p;
-          sb += hw * c_hgw[j] * d;
-        }
-      }
-      Gy = sy;
-      Gb = sb;
-    } else {
-      // t = u sinh(s): r/r_f = u cosh(s); s in [0, asinh(L/u)]
-      float smax = asinhf(L / u);
-      segs[ns++] = 0.f;
-      for (int q = 0; q < 2; ++q)
-        if (kinks[q] > u && kinks[q] < 1.0f) {
-          float sk = acoshf(kinks[q] / u);
-          if (sk > 0.f && sk < smax) segs[ns++] = sk;
-        }
-      segs[ns++] = smax;
-      if (ns == 4 && segs[1] > segs[2]) { float t = segs[1]; segs[1] = segs[2]; segs[2] = t; }
-      float sy = 0.f, sb = 0.f;
-      for (int s = 0; s + 1 < ns; ++s) {
-        float a = segs[s], b = segs[s + 1], mid = 0.5f * (a + b), hw = 0.5f * (b - a);
-        for (int j = 0; j < HP_NGL; ++j) {
-          float sv = mid + hw * c_hgx[j];
-          float ch = coshf(sv);
-          float p, d;
-          profile_pn(H, u * ch * H.xf, n_poly, n_int, n_nt, p, d);
-          float wj = hw * c_hgw[j] * u * ch;
-          sy += wj * p;
-          sb += wj * d;
-        }
-      }
-      Gy = sy / L;
-      Gb = sb / L;
-    }
+    float sy, sb;
+    hp_los(H, u, n_poly, n_int, n_nt, sy, sb);
+    // divided by the chord sqrt(1 - u^2) (1 at u = 0): smooth up to the edge
+    const float L = node == 0 ? 1.0f : sqrtf(fmaxf(0.f, 1.0f - u * u));
+    Gy = sy / L;
+    Gb = sb / L;
   }
   ty[node + 1] = Gy;
   tb[node + 1] = Gb;
@@ -243,6 +252,7 @@ __global__ void k_hp_ghosts(const HpHalo* __restrict__ halos, int64_t nh, float*
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nh) return;
   const int nt = halos[k].nt;
+  if (nt == 0) return;
   for (int q = 0; q < 2; ++q) {
     float* t = tab + k * 2 * HP_ROW + q * HP_ROW;
     t[0] = t[2];
@@ -670,6 +680,10 @@ int check_hp_args(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_y
 // keeps FP32 relative accuracy down to sub-pixel separations at nside 8192.
 constexpr int HS_SEG = 256;  // pixels per segment = threads per paste CTA
 constexpr int HS_CH = 256;   // pairs staged in shared memory at a time
+// Halos whose aperture covers fewer pixels than this get their LOS integrals evaluated at
+// each covered pixel instead of a 257-node table (most all-sky halos cover a few dozen
+// pixels at nside 8192; a table would cost more than the pixels it serves).
+constexpr float HS_DIRECT_PIX = 32.f;
 
 struct HsRing {
   double theta;      // colatitude of the ring's centres
@@ -689,7 +703,8 @@ struct HsRing {
 __global__ void k_hs_prep(BpParams P, int64_t n, int64_t h0, int64_t m,
                           const double* __restrict__ theta, const double* __restrict__ phi,
                           const float* __restrict__ vlos, const double* __restrict__ model,
-                          const int32_t* __restrict__ status, double ap_r500, HpHalo* out) {
+                          const int32_t* __restrict__ status, double ap_r500, int nside,
+                          HpHalo* out) {
   const int64_t kl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (kl >= m) return;
   const int64_t k = h0 + kl;
@@ -709,6 +724,9 @@ __global__ void k_hs_prep(BpParams P, int64_t n, int64_t h0, int64_t m,
   H.inv_rf_px = (float)(DA / rf);
   H.map = 0;
   H.ok = ok ? 1 : 0;
+  // aperture area in pixels: pi alpha^2 / (4 pi / (12 nside^2))
+  const double npx = 3.0 * H.rad_px * H.rad_px * (double)nside * (double)nside;
+  if (npx < HS_DIRECT_PIX) H.nt = 0;
   out[kl] = H;
 }
 
@@ -829,13 +847,14 @@ __global__ void k_hs_emit(const HpHalo* __restrict__ halos, int64_t nh,
 __global__ void __launch_bounds__(HS_SEG)
     k_hs_paste(const HpHalo* __restrict__ halos, const float* __restrict__ tab,
                const uint32_t* __restrict__ hvals, const int64_t* __restrict__ sstart,
-               const HsRing* __restrict__ R, int nr, float* ymap, float* bmap, float* ylo,
-               float* blo) {
+               const HsRing* __restrict__ R, int nr, float n_poly, int n_int, float n_nt,
+               float* ymap, float* bmap, float* ylo, float* blo) {
   __shared__ float s_dth2[HS_CH], s_sp[HS_CH], s_rh[HS_CH], s_rl[HS_CH], s_sa2[HS_CH];
   __shared__ float s_irf[HS_CH], s_ay[HS_CH], s_ab[HS_CH];
   __shared__ int2 s_rng[HS_CH];
   __shared__ const float* s_tab[HS_CH];
   __shared__ int s_nt[HS_CH];
+  __shared__ uint32_t s_hk[HS_CH];
   const uint32_t sg = blockIdx.x;
   const int64_t b0 = sstart[sg], b1 = sstart[sg + 1];
   if (b0 == b1) return;
@@ -876,6 +895,7 @@ __global__ void __launch_bounds__(HS_SEG)
       s_ab[tid] = H.Ab;
       s_tab[tid] = tab + (int64_t)hk * 2 * HP_ROW;
       s_nt[tid] = H.nt;
+      s_hk[tid] = hk;
       // the segment's pixels to test: all of them when the span can wrap into the segment
       // from both sides, else the span around the representative
       bool full;
@@ -903,12 +923,21 @@ __global__ void __launch_bounds__(HS_SEG)
         const float psi = 2.0f * asinf(sqrtf(hav));
         const float uu = psi * s_irf[q];
         if (uu < 1.0f) {
-          const float chord = sqrtf(fmaxf(0.f, 1.0f - uu * uu));
-          const float ss = sqrtf(uu);
-          const float* ty = s_tab[q];
-          const float gy = catmull(ty, ss, s_nt[q]), gb = catmull(ty + HP_ROW, ss, s_nt[q]);
-          kahan_add(hy, cy, s_ay[q] * chord * gy);
-          kahan_add(hb, cb, s_ab[q] * chord * gb);
+          const int ntq = s_nt[q];
+          if (ntq > 0) {
+            const float chord = sqrtf(fmaxf(0.f, 1.0f - uu * uu));
+            const float ss = sqrtf(uu);
+            const float* ty = s_tab[q];
+            const float gy = catmull(ty, ss, ntq), gb = catmull(ty + HP_ROW, ss, ntq);
+            kahan_add(hy, cy, s_ay[q] * chord * gy);
+            kahan_add(hb, cb, s_ab[q] * chord * gb);
+          } else {  // small halo: the integrals at this pixel (chord times table value)
+            const HpHalo Hq = halos[s_hk[q]];
+            float sy, sb;
+            hp_los(Hq, uu, n_poly, n_int, n_nt, sy, sb);
+            kahan_add(hy, cy, s_ay[q] * sy);
+            kahan_add(hb, cb, s_ab[q] * sb);
+          }
         }
       }
     }
@@ -1197,7 +1226,7 @@ int bp_paste_halos_healpix(bp_ctx* ctx, int64_t n, const double* theta, const do
     const unsigned nb = (unsigned)((m + 255) / 256);
     bp_phase_begin(ctx, BP_PH_HP_TABLE);
     k_hs_prep<<<nb, 256, 0, ctx->stream>>>(ctx->p, n, h0, m, theta, phi, v_los, model, status,
-                                           ap_r500, halos);
+                                           ap_r500, nside, halos);
     BP_LAUNCH_CHECK(ctx, "healpix prep");
     const BpParams& P = ctx->p;
     double rn = rint(P.n_poly);
@@ -1242,8 +1271,9 @@ int bp_paste_halos_healpix(bp_ctx* ctx, int64_t n, const double* theta, const do
     if ((r = bp_tile_ranges(ctx, ks, np, n_seg, sstart))) return r;
     bp_phase_end(ctx, BP_PH_HP_PAIRS);
     bp_phase_begin(ctx, BP_PH_HP_PASTE);
-    k_hs_paste<<<(unsigned)n_seg, HS_SEG, 0, ctx->stream>>>(halos, tab, vs, sstart, R, nr, ymap,
-                                                            bmap, ylo, blo);
+    k_hs_paste<<<(unsigned)n_seg, HS_SEG, 0, ctx->stream>>>(
+        halos, tab, vs, sstart, R, nr, (float)P.n_poly, n_int, (float)P.n_nt, ymap, bmap, ylo,
+        blo);
     BP_LAUNCH_CHECK(ctx, "healpix paste");
     bp_phase_end(ctx, BP_PH_HP_PASTE);
   }
