@@ -114,6 +114,8 @@ def lib():
                 "orc_w_sph": (d, [d]),
                 "orc_pp_assign": (None, [pc, pi, i64, P, P, P, P, P, P, P, P, d, i64, P, P, pg,
                                          P, P, P, P, P, P, i32]),
+                "orc_pp_assign_phi": (None, [pc, pi, i64, P, P, P, P, P, P, P, P, P, d, i64, P, P,
+                                             pg, P, P, P, P, P, P, i32]),
                 "orc_pp_deposit": (None, [i64, P, P, P, P, P, P, pg, i32, P, P, i32]),
                 "orc_pp_deposit_pixels": (None, [i64, P, P, P, P, P, P, pg, i32, i64, P, P, P,
                                                  P, i32]),
@@ -316,9 +318,11 @@ def smoothing_lengths_at(x, y, z, idx, n_ngb=64.0, nthreads=0):
     return h
 
 
-def pp_assign(parts: dict, Mp_hinv, halo_pos, models, g: Geom, cp=None, ip=None, nthreads=0):
+def pp_assign(parts: dict, Mp_hinv, halo_pos, models, g: Geom, cp=None, ip=None, nthreads=0,
+              phi=None):
     """Per-particle signals.  parts: x,y,z,vx,vy,vz,hsml (float32), hid (int32).
-    halo_pos: float32 [3, nh].  Returns dict px,py,hp,Y,B (FP64) and kind (int32)."""
+    halo_pos: float32 [3, nh].  phi: optional float32 per-particle potential [(km/s)^2] (the
+    potential-based variant).  Returns dict px,py,hp,Y,B (FP64) and kind (int32)."""
     x, y, z = _f32(parts["x"]), _f32(parts["y"]), _f32(parts["z"])
     vx, vy, vz = _f32(parts["vx"]), _f32(parts["vy"]), _f32(parts["vz"])
     hs, hid = _f32(parts["hsml"]), _i32(parts["hid"])
@@ -328,10 +332,12 @@ def pp_assign(parts: dict, Mp_hinv, halo_pos, models, g: Geom, cp=None, ip=None,
     out = {k: np.empty(n, np.float64) for k in ("px", "py", "hp", "Y", "B")}
     kind = np.empty(n, np.int32)
     nh = hpos.shape[1] if hpos.ndim == 2 else 0
-    lib().orc_pp_assign(C.byref(cp or cosmo_default()), C.byref(ip or icm_default()), n, _p(x),
-                        _p(y), _p(z), _p(vx), _p(vy), _p(vz), _p(hs), _p(hid), float(Mp_hinv),
-                        nh, _p(hpos), _p(models), C.byref(g), _p(out["px"]), _p(out["py"]),
-                        _p(out["hp"]), _p(out["Y"]), _p(out["B"]), _p(kind), int(nthreads))
+    ph = None if phi is None else _f32(phi)
+    lib().orc_pp_assign_phi(C.byref(cp or cosmo_default()), C.byref(ip or icm_default()), n,
+                            _p(x), _p(y), _p(z), _p(vx), _p(vy), _p(vz), _p(ph), _p(hs), _p(hid),
+                            float(Mp_hinv), nh, _p(hpos), _p(models), C.byref(g), _p(out["px"]),
+                            _p(out["py"]), _p(out["hp"]), _p(out["Y"]), _p(out["B"]), _p(kind),
+                            int(nthreads))
     out["kind"] = kind
     return out
 

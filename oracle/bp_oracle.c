@@ -754,12 +754,33 @@ double orc_w_sph(double x) {
  * Output per particle (FP64): pixel coordinates px,py (pixel units from the map's
  * lower-left edge), kernel radius hp in pixels, Y = y_i (pixel-y units) and B = b_i,
  * and kind (0 halo, 1 field, 2 no contribution). */
+/* Potential-based variant: with phi (per-particle potential, (km/s)^2, zero at infinity) a
+ * halo particle's polytropic variable is theta_i = 1 + (Phi0 - phi_i) / ((n + 1) T) -- the
+ * relation theta(Phi) of Section 2.1 at the particle's own potential -- instead of
+ * theta(r_i); P_e and rho_g follow from theta_i, V_i, R_nt and the r_f cut stay at r_i.
+ * phi = NULL: the paper's spherical assignment. */
+void orc_pp_assign_phi(const orc_cosmo* cp, const orc_icm* ip, int64_t n, const float* x,
+                       const float* y, const float* zc, const float* vx, const float* vy,
+                       const float* vz, const float* phi, const float* hsml, const int32_t* hid,
+                       double Mp_hinv, int64_t nh, const float* hpos /*[3][nh]*/,
+                       const double* models, const orc_geom* g, double* px, double* py,
+                       double* hp, double* Y, double* B, int32_t* kind, int nthreads);
 void orc_pp_assign(const orc_cosmo* cp, const orc_icm* ip, int64_t n, const float* x,
                    const float* y, const float* zc, const float* vx, const float* vy,
                    const float* vz, const float* hsml, const int32_t* hid, double Mp_hinv,
                    int64_t nh, const float* hpos /*[3][nh]*/, const double* models,
                    const orc_geom* g, double* px, double* py, double* hp, double* Y,
                    double* B, int32_t* kind, int nthreads) {
+  orc_pp_assign_phi(cp, ip, n, x, y, zc, vx, vy, vz, NULL, hsml, hid, Mp_hinv, nh, hpos, models,
+                    g, px, py, hp, Y, B, kind, nthreads);
+}
+
+void orc_pp_assign_phi(const orc_cosmo* cp, const orc_icm* ip, int64_t n, const float* x,
+                       const float* y, const float* zc, const float* vx, const float* vy,
+                       const float* vz, const float* phi, const float* hsml, const int32_t* hid,
+                       double Mp_hinv, int64_t nh, const float* hpos /*[3][nh]*/,
+                       const double* models, const orc_geom* g, double* px, double* py,
+                       double* hp, double* Y, double* B, int32_t* kind, int nthreads) {
   double CP = o_CP(), CN = o_CN(cp);
   double h = cp->h, fb = cp->Ob / cp->Om;
   double Mp = Mp_hinv / h;
@@ -801,8 +822,20 @@ void orc_pp_assign(const orc_cosmo* cp, const orc_icm* ip, int64_t n, const floa
     o_prof_init(&p, cp, ip, m);
     if (r >= p.rf) continue;
     double V = Mp / o_rho_nfw(&p.h, r); /* volume from the NFW density at r_i */
-    Y[i] = CP * o_Pe(&p, r) * V * geo;
-    B[i] = CN * (vr / O_C_KMS) * exp(-tau) * o_rhog(&p, r) * V * geo;
+    if (phi) {
+      double th = 1.0 + (p.phi0 - (double)phi[i]) / ((p.n + 1.0) * p.T);
+      double Pe = 0.0, rg = 0.0;
+      if (th > 0) {
+        double Rnt = p.ant * pow(r / p.r500, p.n_nt);
+        Pe = p.pe_frac * p.P0 * pow(th, p.n + 1.0) * fmax(0.0, 1.0 - Rnt);
+        rg = p.rho0 * pow(th, p.n);
+      }
+      Y[i] = CP * Pe * V * geo;
+      B[i] = CN * (vr / O_C_KMS) * exp(-tau) * rg * V * geo;
+    } else {
+      Y[i] = CP * o_Pe(&p, r) * V * geo;
+      B[i] = CN * (vr / O_C_KMS) * exp(-tau) * o_rhog(&p, r) * V * geo;
+    }
     kind[i] = 0;
   }
   (void)nthreads;

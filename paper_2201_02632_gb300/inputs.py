@@ -261,7 +261,12 @@ def lightcone(n_part=4_000_000, n_halo=3000, side_deg=2.0, zr=(0.05, 1.5), halo_
     }
     cat = HaloCatalog(M, c, hz, thx, thy, hv, pos=hp.T.astype(np.float32).copy())
     g = MapGeom(npix, npix, -half, -half, 2 * half / npix)
-    return LightCone(parts, cat, Mp, g, {"h_field": h_field, "n_halo_particles": n_h})
+    # each halo particle's radius on its cloud's ellipsoidal shell (before the axis ratios
+    # and the rotation; comoving h^-1 Mpc), NaN for the field: the geometry a potential on
+    # ellipsoidal shells needs
+    r_ell = np.concatenate([rad, np.full(n_f, np.nan)])[perm]
+    return LightCone(parts, cat, Mp, g, {"h_field": h_field, "n_halo_particles": n_h,
+                                         "r_ell": r_ell})
 
 
 def split_positions(p):

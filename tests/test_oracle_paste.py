@@ -381,3 +381,65 @@ def test_hp_pixels_equal_the_map(orc):
     yv, bv = orc.hp_pixels(cat.thx, cat.thy, cat.vlos, mo, g, pi_, pj_, ap_r500=3.0, rtol=1e-8)
     np.testing.assert_allclose(yv, ym[0][pj_, pi_], rtol=1e-13, atol=1e-30)
     np.testing.assert_allclose(bv, bm[0][pj_, pi_], rtol=1e-13, atol=1e-30)
+
+
+# ---------------------------------------------------------------- potential-based variant
+def _halo_particle_phi(orc, lc, mo, r_of):
+    """phi_i of every halo particle from the oracle's NFW potential at radius r_of(i) [Mpc]."""
+    F = orc.F
+    hid = lc.parts["hid"]
+    phi = np.zeros(hid.size, np.float32)
+    for k in np.unique(hid[hid >= 0]):
+        sel = np.nonzero(hid == k)[0]
+        _, _, p = orc.nfw_eval(lc.halos.M[k], lc.halos.c[k], lc.halos.z[k], r_of(sel, k))
+        phi[sel] = p
+    return phi
+
+
+def test_potential_variant_reduces_to_the_spherical_model(orc):
+    """phi_i = Phi_NFW(r_i) gives the spherical assignment (up to phi's FP32 rounding)."""
+    lc = I.lightcone(n_part=20000, n_halo=40, npix=128, side_deg=1.0, seed=12)
+    mo = orc.solve_halos(lc.halos.M, lc.halos.c, lc.halos.z)
+    F = orc.F
+    h = orc.cosmo_default().h
+    pos = np.stack([lc.parts["x"], lc.parts["y"], lc.parts["z"]]).astype(np.float64)
+    hp = lc.halos.pos.astype(np.float64)
+    r_i = lambda sel, k: (np.linalg.norm(pos[:, sel] - hp[:, k:k + 1], axis=0) / h
+                          / (1 + lc.halos.z[k]))
+    phi = _halo_particle_phi(orc, lc, mo, r_i)
+    g = orc.geom(lc.geom.nx, lc.geom.ny, lc.geom.theta0_x, lc.geom.theta0_y, lc.geom.dtheta)
+    a = orc.pp_assign(lc.parts, lc.Mp, lc.halos.pos, mo, g)
+    b = orc.pp_assign(lc.parts, lc.Mp, lc.halos.pos, mo, g, phi=phi)
+    assert np.array_equal(a["kind"], b["kind"]) and np.count_nonzero(a["kind"] == 0) > 5000
+    np.testing.assert_allclose(b["Y"], a["Y"], rtol=2e-6, atol=1e-6 * a["Y"].max())
+    np.testing.assert_allclose(b["B"], a["B"], rtol=2e-6, atol=1e-6 * np.abs(a["B"]).max())
+    assert np.array_equal(b["px"], a["px"]) and np.array_equal(b["hp"], a["hp"])
+
+
+def test_potential_variant_is_polytropic_in_phi(orc):
+    """For one particle, (Y / Y(Phi0))^(1/(n+1)) is affine in phi and 1 at Phi0, the density
+    follows the same theta (B ratio = Y ratio^(n/(n+1))), and theta <= 0 gives nothing."""
+    lc = I.lightcone(n_part=4000, n_halo=10, npix=64, side_deg=1.0, seed=13)
+    mo = orc.solve_halos(lc.halos.M, lc.halos.c, lc.halos.z)
+    F = orc.F
+    g = orc.geom(lc.geom.nx, lc.geom.ny, lc.geom.theta0_x, lc.geom.theta0_y, lc.geom.dtheta)
+    base = orc.pp_assign(lc.parts, lc.Mp, lc.halos.pos, mo, g)
+    i = int(np.nonzero((base["kind"] == 0) & (base["Y"] > 0) & (base["B"] != 0))[0][0])
+    k = lc.parts["hid"][i]
+    one = {kk: v[i:i + 1] for kk, v in lc.parts.items()}
+    phi0, T = mo[k, F["Phi0"]], mo[k, F["T"]]
+    n = 1 / (1.2 - 1)
+    vals = [phi0 + t * (n + 1) * T for t in (0.0, 0.2, 0.4, 0.6)]
+    ys, bs = [], []
+    for v in vals:
+        r = orc.pp_assign(one, lc.Mp, lc.halos.pos, mo, g, phi=np.array([v], np.float32))
+        ys.append(r["Y"][0])
+        bs.append(r["B"][0])
+    th = (np.array(ys) / ys[0]) ** (1 / (n + 1))
+    assert th[0] == 1.0
+    assert np.allclose(np.diff(th, 2), 0.0, atol=1e-6)  # affine in phi
+    assert th[1] < 1.0  # a shallower potential makes the gas cooler
+    assert np.allclose(np.array(bs) / bs[0], th ** n, rtol=1e-6)
+    r = orc.pp_assign(one, lc.Mp, lc.halos.pos, mo, g,
+                      phi=np.array([phi0 + 1.01 * (n + 1) * T], np.float32))
+    assert r["Y"][0] == 0.0 and r["B"][0] == 0.0 and r["kind"][0] == 0
