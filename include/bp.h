@@ -288,6 +288,22 @@ int bp_assign_particles(bp_ctx* ctx, int64_t n, const float* x, const float* y, 
                         const float* halo_pos, const double* model, const int32_t* status,
                         const bp_map_geom* geom, float* out);
 
+/* bp_assign_particles with a per-particle gravitational potential phi (device FP32 [n],
+ * physical (km/s)^2, zero at infinity, the halo's own potential at the particle as an
+ * N-body code provides it), or NULL (then identical to bp_assign_particles).  A halo
+ * particle then gets theta_i = 1 + (Phi0 - phi_i) / ((n + 1) T) in place of theta(r_i) of the
+ * spherical model (Section 2.1's polytropic relation between theta and the potential,
+ * evaluated with the particle's own potential: the gas follows the halo's equipotentials,
+ * carrying its asphericity); P_e and n_e follow from theta_i as before, while V_i, R_nt and
+ * the r_f cut stay at r_i.  The paper's PP uses the spherical model; this variant is an
+ * extension. */
+int bp_assign_particles_phi(bp_ctx* ctx, int64_t n, const float* x, const float* y,
+                            const float* z, const float* vx, const float* vy, const float* vz,
+                            const float* phi, const float* hsml, const int32_t* halo_id,
+                            double Mp, int64_t n_halos, const float* halo_pos,
+                            const double* model, const int32_t* status,
+                            const bp_map_geom* geom, float* out);
+
 /* Section 3.4: deposit assigned particles through the separable pixel-integrated
  * SPH kernel, f_ij = [w((x_i+ - x_p)/h) - w((x_i- - x_p)/h)] [same in y].
  *   assigned [BP_ASSIGNED_STRIDE * n] FP32 (from bp_assign_particles or the caller)

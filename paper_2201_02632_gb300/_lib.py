@@ -29,6 +29,7 @@ EXPORTS = ("bp_create", "bp_destroy", "bp_last_error", "bp_set_stream", "bp_set_
            "bp_workspace_bytes", "bp_set_timing", "bp_phase_times", "bp_kernel_launches",
            "bp_solve_halos", "bp_assign_particles", "bp_paste_particles", "bp_pp_pairs",
            "bp_smoothing_lengths", "bp_paste_halos_healpix", "bp_power_spectrum",
+           "bp_assign_particles_phi",
            "bp_paste_halos", "bp_finalize_map", "bp_paste_particles_noalloc",
            "bp_solve_halos_ex", "bp_last_fallback_count", "bp_mlp_forward", "bp_mlp_backward",
            "bp_mlp_adam", "bp_mlp_to_bf16", "bp_mlp_infer_bf16", "bp_mlp_features",
@@ -98,6 +99,8 @@ def load():
                                                    d]),
                 "bp_assign_particles": (i32, [P, i64, P, P, P, P, P, P, P, P, d, i64, P, P, P,
                                               C.POINTER(BpGeom), P]),
+                "bp_assign_particles_phi": (i32, [P, i64, P, P, P, P, P, P, P, P, P, d, i64, P,
+                                                  P, P, C.POINTER(BpGeom), P]),
                 "bp_paste_particles": (i32, [P, i64, P, C.POINTER(BpGeom), i32, P, P, P, P]),
                 "bp_paste_particles_noalloc": (i32, [P, i64, P, C.POINTER(BpGeom), i32, P, P, P,
                                                      P]),

@@ -256,20 +256,24 @@ class Context:
 
     # ------------------------------------------------------------ Section 3.4
     def assign_particles(self, parts: dict, Mp: float, halo_pos, model, status, g: L.BpGeom,
-                         out=None):
-        """Per-particle signals.  parts: x,y,z,vx,vy,vz,hsml (FP32), hid (int32).
+                         out=None, phi=None):
+        """Per-particle signals.  parts: x,y,z,vx,vy,vz,hsml (FP32), hid (int32).  phi: optional
+        FP32 per-particle potential [(km/s)^2] (bp_assign_particles_phi).
         Returns the [n, 8] FP32 record tensor."""
         n = parts["x"].numel()
         f32 = torch.float32
         if out is None:
             out = torch.empty((n, ASSIGNED_STRIDE), dtype=f32, device=parts["x"].device)
         nh = 0 if halo_pos is None else halo_pos.shape[-1]
-        rc = self._L.bp_assign_particles(
-            self._h, n, *(_ptr(parts[k], f32, k) for k in ("x", "y", "z", "vx", "vy", "vz",
-                                                           "hsml")),
-            _ptr(parts["hid"], torch.int32, "hid"), float(Mp), nh,
-            _ptr(halo_pos, f32, "halo_pos"), _ptr(model, torch.float64, "model"),
-            _ptr(status, torch.int32, "status"), C.byref(g), _ptr(out, f32, "out"))
+        xyzv = [_ptr(parts[k], f32, k) for k in ("x", "y", "z", "vx", "vy", "vz")]
+        tail = [_ptr(parts["hsml"], f32, "hsml"), _ptr(parts["hid"], torch.int32, "hid"),
+                float(Mp), nh, _ptr(halo_pos, f32, "halo_pos"),
+                _ptr(model, torch.float64, "model"), _ptr(status, torch.int32, "status"),
+                C.byref(g), _ptr(out, f32, "out")]
+        if phi is None:
+            rc = self._L.bp_assign_particles(self._h, n, *xyzv, *tail)
+        else:
+            rc = self._L.bp_assign_particles_phi(self._h, n, *xyzv, _ptr(phi, f32, "phi"), *tail)
         self._check(rc)
         return out
 

@@ -55,7 +55,9 @@ __global__ void k_halo_block(BpParams P, int64_t nh, const double* __restrict__ 
   b[8] = ok ? (float)(P.CP * P.pe_frac * F(BP_M_P0) * Mp / rhos) : 0.f;
   b[9] = ok ? (float)(P.CN * F(BP_M_RHO0) * Mp / rhos) : 0.f;
   b[10] = ok ? 1.f : 0.f;
-  for (int q = 11; q < HB; ++q) b[q] = 0.f;
+  b[11] = ok ? (float)F(BP_M_PHI0) : 0.f;  // the potential-based variant: theta = 1 +
+  b[12] = ok ? (float)(1.0 / n1T) : 0.f;   //   (Phi0 - phi_i) / ((n + 1) T)
+  for (int q = 13; q < HB; ++q) b[q] = 0.f;
 }
 
 // 1 - ln(1+x)/x without cancellation
@@ -139,6 +141,7 @@ __device__ __forceinline__ bool pixel_fast(float x, float z, float rz, float th0
 
 struct AssignArgs {
   const float *x, *y, *z, *vx, *vy, *vz, *hs;
+  const float* phi;  // per-particle potential [(km/s)^2] or null (spherical model at r_i)
   const int32_t* hid;
   const float* hpos;
   const float* blk;
@@ -191,7 +194,8 @@ __global__ void __launch_bounds__(256) k_assign(AssignArgs a, BpTables T) {
         float dx = xf - a.hpos[k], dy = yf - a.hpos[a.nh + k], dz = zf - a.hpos[2 * a.nh + k];
         float x = sqrtf(dx * dx + dy * dy + dz * dz) * b[0];
         if (x < b[1]) {
-          float th = (x <= b[2]) ? 1.0f - b[4] * g_inner(x) : 1.0f - b[5] + b[6] / x;
+          float th = a.phi ? 1.0f + (b[11] - a.phi[i]) * b[12]
+                           : ((x <= b[2]) ? 1.0f - b[4] * g_inner(x) : 1.0f - b[5] + b[6] / x);
           th = fmaxf(th, 0.f);
           float thn = powi_or_pow(th, a.n_poly, a.n_int);
           float Rnt = b[7] * powf(x * b[3], a.n_nt);
@@ -773,6 +777,16 @@ int bp_assign_particles(bp_ctx* ctx, int64_t n, const float* x, const float* y, 
                         const int32_t* halo_id, double Mp, int64_t n_halos,
                         const float* halo_pos, const double* model, const int32_t* status,
                         const bp_map_geom* geom, float* out) {
+  return bp_assign_particles_phi(ctx, n, x, y, z, vx, vy, vz, nullptr, hsml, halo_id, Mp, n_halos,
+                                 halo_pos, model, status, geom, out);
+}
+
+int bp_assign_particles_phi(bp_ctx* ctx, int64_t n, const float* x, const float* y,
+                            const float* z, const float* vx, const float* vy, const float* vz,
+                            const float* phi, const float* hsml, const int32_t* halo_id,
+                            double Mp, int64_t n_halos, const float* halo_pos,
+                            const double* model, const int32_t* status,
+                            const bp_map_geom* geom, float* out) {
   if (!ctx) return BP_EINVAL;
   if (n < 0 || n_halos < 0) return bp_fail(ctx, BP_EINVAL, "bp_assign_particles: negative size");
   int r = check_geom(ctx, geom, "bp_assign_particles");
@@ -791,6 +805,7 @@ int bp_assign_particles(bp_ctx* ctx, int64_t n, const float* x, const float* y, 
   if ((r = halo_blocks(ctx, n_halos, model, status, Mp / P.h, &blk))) return r;
   AssignArgs a;
   a.x = x; a.y = y; a.z = z; a.vx = vx; a.vy = vy; a.vz = vz; a.hs = hsml;
+  a.phi = phi;
   a.hid = halo_id;
   a.hpos = halo_pos;
   a.blk = blk;
