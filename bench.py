@@ -720,7 +720,8 @@ def run_ours(args):
         res["surrogate"] = surrogate_section(api, ctx, dev, lc, args)
     if not args.no_hsml:
         res["smoothing_lengths"] = hsml_section(api, ctx, dev, lc, args)
-    res["power_spectrum"] = spectrum_section(api, ctx, dev, pp.y[0], g.dtheta)
+    if not args.no_spectrum:
+        res["power_spectrum"] = spectrum_section(api, ctx, dev, pp.y[0], g.dtheta)
     if not args.no_batched:
         res["batched_hp"] = batched_section(api, ctx, dev, args)
     if not args.no_allsky:
@@ -767,6 +768,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-hsml", action="store_true")
     ap.add_argument("--no-allsky", action="store_true")
+    ap.add_argument("--no-spectrum", action="store_true")
     ap.add_argument("--allsky-halos", type=int, default=41_000_000)
     ap.add_argument("--allsky-nside", type=int, default=8192)
     ap.add_argument("--no-full-scale", action="store_true")

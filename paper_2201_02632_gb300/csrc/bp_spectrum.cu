@@ -12,7 +12,7 @@
 //  k_fft_bin      one CTA per former column (frequency kx): the same FFT along y, then every
 //                 mode's power and bin (FP64, explicitly rounded |l|^2 against the squared
 //                 edges), and per-bin sums of the row in a fixed lane / shuffle order
-//  k_bin_reduce   per bin: the row partials summed in row order, divided by the mode count
+//  k_bin_reduce   per bin: the row partials summed in a fixed tree, divided by the mode count
 //
 // Everything is FP64 (the FFT costs ~5 n log2 n flops per map, small next to the pastes), so
 // the bins agree with an FP64 reference to rounding and each mode's bin is decided exactly
@@ -134,18 +134,35 @@ __global__ void __launch_bounds__(FT_THREADS)
   }
 }
 
-__global__ void k_bin_reduce(const double* __restrict__ psum, const int* __restrict__ pcnt,
-                             int nrows, int nb, double* cl, int64_t* nmodes) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= nb) return;
+// One block per bin: rows summed lane-strided, then a fixed shared-memory tree (the same
+// order on every run).
+constexpr int BR_THREADS = 256;
+__global__ void __launch_bounds__(BR_THREADS)
+    k_bin_reduce(const double* __restrict__ psum, const int* __restrict__ pcnt, int nrows, int nb,
+                 double* cl, int64_t* nmodes) {
+  __shared__ double s_s[BR_THREADS];
+  __shared__ long long s_c[BR_THREADS];
+  const int b = blockIdx.x, t = threadIdx.x;
   double s = 0.0;
-  int64_t c = 0;
-  for (int r = 0; r < nrows; ++r) {
+  long long c = 0;
+  for (int r = t; r < nrows; r += BR_THREADS) {
     s += psum[(int64_t)r * nb + b];
     c += pcnt[(int64_t)r * nb + b];
   }
-  cl[b] = c > 0 ? s / (double)c : 0.0;
-  if (nmodes) nmodes[b] = c;
+  s_s[t] = s;
+  s_c[t] = c;
+  __syncthreads();
+  for (int o = BR_THREADS / 2; o > 0; o >>= 1) {
+    if (t < o) {
+      s_s[t] += s_s[t + o];
+      s_c[t] += s_c[t + o];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    cl[b] = s_c[0] > 0 ? s_s[0] / (double)s_c[0] : 0.0;
+    if (nmodes) nmodes[b] = s_c[0];
+  }
 }
 
 int log2_exact(int n) {
@@ -212,7 +229,7 @@ extern "C" int bp_power_spectrum(bp_ctx* ctx, const float* map, const float* lo,
   k_fft_bin<<<nx, ty, smy, ctx->stream>>>(B, nx, ny, lgy, wy, inv_lx, inv_ly, c2, norm, e2, nb,
                                           psum, pcnt);
   BP_LAUNCH_CHECK(ctx, "fft bins");
-  k_bin_reduce<<<(nb + 127) / 128, 128, 0, ctx->stream>>>(psum, pcnt, nx, nb, cl, nmodes);
+  k_bin_reduce<<<nb, BR_THREADS, 0, ctx->stream>>>(psum, pcnt, nx, nb, cl, nmodes);
   BP_LAUNCH_CHECK(ctx, "bin reduce");
   return BP_OK;
 }
