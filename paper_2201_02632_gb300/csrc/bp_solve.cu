@@ -310,6 +310,41 @@ struct SolveExtra {
   int only_fallback;    // 1: solve only halos whose status is BP_HALO_FALLBACK
 };
 
+// FP32 versions of the two set-up roots (same equations, bracket and Newton as the FP64
+// loops, stopped at the FP32 resolution): starting points for them.  Any start inside the
+// bracket leads the FP64 iteration to the same root; a good one saves its FP64 steps.
+__device__ __forceinline__ float m_of_f32(float x) {
+  if (x < 1e-2f) return x * x * (0.5f - x * (2.0f / 3.0f - x * (0.75f - x * 0.8f)));
+  return log1pf(x) - x / (1.0f + x);
+}
+__device__ double fp32_root_r500(float lnK, float c) {
+  float lo = 1e-8f, hi = c, x = 0.5f * c;
+  for (int it = 0; it < 40; ++it) {
+    const float mx = m_of_f32(x);
+    const float f = logf(mx) - 3.0f * logf(x) - lnK;
+    if (f > 0) lo = x; else hi = x;
+    const float df = x / ((1 + x) * (1 + x)) / mx - 3.0f / x;
+    float xn = x - f / df;
+    if (!(xn > lo && xn < hi)) xn = 0.5f * (lo + hi);
+    if (fabsf(xn - x) < 1e-6f * x) { x = xn; break; }
+    x = xn;
+  }
+  return (x > 1e-8f && x < c && isfinite(x)) ? (double)x : 0.5 * (double)c;
+}
+__device__ double fp32_root_mstar(float tgt, float c) {
+  float lo = 0.f, hi = c, x = 0.5f * c;
+  for (int it = 0; it < 40; ++it) {
+    const float f = m_of_f32(x) - tgt;
+    if (f < 0) lo = x; else hi = x;
+    const float df = x / ((1 + x) * (1 + x));
+    float xn = x - f / df;
+    if (!(xn > lo && xn < hi)) xn = 0.5f * (lo + hi);
+    if (fabsf(xn - x) < 1e-6f * x) { x = xn; break; }
+    x = xn;
+  }
+  return (x > 0.f && x < c && isfinite(x)) ? (double)x : 0.5 * (double)c;
+}
+
 // Closed-form and one-dimensional set-up of halo i, run by ONE thread.  Writes the
 // set-up fields of the model; returns false (status written) if the halo cannot be
 // solved.
@@ -345,10 +380,11 @@ __device__ bool halo_setup(const BpParams& P, const BpTables& TB, int64_t n, int
   h.phi0 = -(h.GM / (h.mc * h.rvir)) * c * c / (1 + c);
   h.DA = bp_hermite(TB.chi_z, TB.dchi_z, TB.nz, TB.dz, z) / (1 + z);
   h.tau = bp_hermite(TB.tau_z, TB.dtau_z, TB.nz, TB.dz, z);
-  // r500: m(x)/x^3 = 500 rho_cr (4pi/3) r_s^3 m(c) / M, Newton in ln x with a bracket
+  // r500: m(x)/x^3 = 500 rho_cr (4pi/3) r_s^3 m(c) / M, Newton in ln x with a bracket,
+  // started from the same iteration in FP32 (a few FP64 steps remain on the slow pipe)
   {
     double lnK = log(500.0 * rho_cr * 4.0 * bpc::PI / 3.0 * h.rs * h.rs * h.rs * h.mc / h.M);
-    double lo = 1e-8, hi = c, x = 0.5 * c;
+    double lo = 1e-8, hi = c, x = fp32_root_r500((float)lnK, (float)c);
     for (int it = 0; it < 100; ++it) {
       double mx = m_of(x);
       double f = log(mx) - 3.0 * log(x) - lnK;
@@ -387,10 +423,10 @@ __device__ bool halo_setup(const BpParams& P, const BpTables& TB, int64_t n, int
     finish(BP_HALO_BADSTAR);
     return false;
   }
-  // r_*: f_b M(<r_*) = M_*  ->  m(x) = M_* m(c) / (f_b M)
+  // r_*: f_b M(<r_*) = M_*  ->  m(x) = M_* m(c) / (f_b M), from an FP32 start as r500
   {
     double tgt = h.Mstar * h.mc / (P.fb * h.M);
-    double lo = 0.0, hi = c, x = 0.5 * c;
+    double lo = 0.0, hi = c, x = fp32_root_mstar((float)tgt, (float)c);
     for (int it = 0; it < 100; ++it) {
       double f = m_of(x) - tgt;
       if (f < 0) lo = x; else hi = x;

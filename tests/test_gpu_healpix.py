@@ -96,3 +96,25 @@ def test_nside_8192_sampled(orc, api, ctx):
     np.testing.assert_allclose(bg, bo, rtol=1e-4, atol=1e-4 * np.abs(bo).max())
     del maps
     torch.cuda.empty_cache()
+
+
+def test_errors_and_empty_catalogue(api, ctx):
+    maps = api.healpix_maps(4)
+    e = torch.empty(0, dtype=torch.float64, device="cuda")
+    model = torch.empty((24, 0), dtype=torch.float64, device="cuda")
+    status = torch.empty(0, dtype=torch.int32, device="cuda")
+    v = torch.empty(0, dtype=torch.float32, device="cuda")
+    ctx.paste_halos_healpix(e, e, v, model, status, 4, maps)  # nothing to paste
+    assert float(maps.y.abs().sum()) == 0.0
+    cat = I.allsky_catalog(5, seed=I.SEED_BASE + 84)
+    model, status = ctx.solve_halos(cuda(cat["M"]), cuda(cat["c"]), cuda(cat["z"]))
+    args = (cuda(cat["theta"]), cuda(cat["phi"]), cuda(cat["vlos"]), model, status)
+    for nside, ap in ((0, 0.0), (16385, 0.0), (4, -1.0)):
+        with pytest.raises(api.BpError) as err:
+            ctx.paste_halos_healpix(*args, nside, maps, ap_r500=ap)
+        assert "BP_EINVAL" in str(err.value)
+    # halos outside [0, pi] in colatitude add nothing
+    bad = cuda(np.full(5, 4.0))
+    maps.zero_()
+    ctx.paste_halos_healpix(bad, args[1], args[2], model, status, 4, maps)
+    assert float(maps.y.abs().sum()) == 0.0
