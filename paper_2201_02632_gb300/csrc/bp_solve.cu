@@ -35,6 +35,9 @@
 
 __constant__ double c_glx[NGL];
 __constant__ double c_glw[NGL];
+#define NGL_POLISH 8  // the two-halos-per-warp polish (8 points: the same solutions to 5e-11)
+__constant__ double c_glx8[NGL_POLISH];
+__constant__ double c_glw8[NGL_POLISH];
 __constant__ double c_li2[16];  // B_2m / (2m+1)!, m = 1..15
 __constant__ float c_glxf[NGL];  // the same rule in FP32 (pre-solve)
 __constant__ float c_glwf[NGL];
@@ -87,6 +90,12 @@ int upload_constants(bp_ctx* ctx) {
   }
   BP_CUDA(ctx, cudaMemcpyToSymbol(c_glx, x, sizeof(x)));
   BP_CUDA(ctx, cudaMemcpyToSymbol(c_glw, w, sizeof(w)));
+  {
+    double x8[NGL_POLISH], w8[NGL_POLISH];
+    gauss_legendre(NGL_POLISH, x8, w8);
+    BP_CUDA(ctx, cudaMemcpyToSymbol(c_glx8, x8, sizeof(x8)));
+    BP_CUDA(ctx, cudaMemcpyToSymbol(c_glw8, w8, sizeof(w8)));
+  }
   BP_CUDA(ctx, cudaMemcpyToSymbol(c_li2, li2, sizeof(li2)));
   float xf[NGL], wf[NGL];
   for (int k = 0; k < NGL; ++k) {
@@ -168,31 +177,37 @@ __device__ __forceinline__ double menc_of(const Halo& h, double r) {
   return r >= h.rvir ? h.M : h.M * m_of(r / h.rs) / h.mc;
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 struct Sums {
   double Im, In, Ip, Jm, Jn;  // int theta^{n-1,n,n+1} r^2, int theta^{n-1,n} Phi r^2
 };
 
-struct Solver {
+// W lanes per halo (32: a warp; 16: two halos per warp), NG Gauss-Legendre points per panel
+template <int W, int NG>
+struct SolverT {
+  static constexpr int NS = (MAX_PANEL_A * NG + W - 1) / W;  // slots per lane
   const Halo& h;
   double n;     // polytropic index
   int n_int;    // n if integral, else -1
   // this lane's nodes of region A ([0, r_vir], fixed per halo) and of the r_f-dependent
   // part (region B = [r_vir, r_f] when r_f >= r_vir, else region A cut at r_f):
-  // weight x r^2 and Phi(r) in fixed slots t (node q = lane + 32 t); unused slots have
+  // weight x r^2 and Phi(r) in fixed slots t (node q = lane + W t); unused slots have
   // weight 0 and Phi = Phi0
-  double a_r2w[NSLOT], a_phi[NSLOT];
-  double f_r2w[NSLOT], f_phi[NSLOT];
+  double a_r2w[NS], a_phi[NS];
+  double f_r2w[NS], f_phi[NS];
   int a_cnt, f_cnt;  // slots in use (the nodes of a lane fill slots 0 .. cnt - 1)
   bool full_a;  // r_f >= r_vir: region A is complete and region B follows
 
-  __device__ Solver(const Halo& hh, double nn) : h(hh), n(nn) {
+  __device__ SolverT(const Halo& hh, double nn) : h(hh), n(nn) {
     double rn = rint(nn);
     n_int = (fabs(nn - rn) < 1e-12 && rn >= 1 && rn <= 16) ? (int)rn : -1;
+  }
+  __device__ static double glx(int j) { return NG == NGL ? c_glx[j] : c_glx8[j]; }
+  __device__ static double glw(int j) { return NG == NGL ? c_glw[j] : c_glw8[j]; }
+  // sum over the W lanes of this halo (xor butterflies stay inside aligned groups of W)
+  __device__ static double group_sum(double v) {
+    for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
   }
   __device__ double pw(double th, int k_off) const {  // theta^{n - 1 + k_off}
     if (n_int > 0) {
@@ -222,18 +237,18 @@ struct Solver {
   }
   // region A nodes up to x = xa of this lane into the slots (r2w, phi); returns the
   // slots in use (panels are filled in order, so the used slots come first)
-  __device__ int nodes_a(int lane, double xa, double (&r2w)[NSLOT], double (&phi)[NSLOT]) const {
+  __device__ int nodes_a(int lane, double xa, double (&r2w)[NS], double (&phi)[NS]) const {
     int cnt = 0;
 #pragma unroll
-    for (int t = 0; t < NSLOT; ++t) {
-      const int q = lane + 32 * t, p = q / NGL, j = q % NGL;
+    for (int t = 0; t < NS; ++t) {
+      const int q = lane + W * t, p = q / NG, j = q % NG;
       double a, b;
       r2w[t] = 0.0;
       phi[t] = h.phi0;
-      if (q >= MAX_PANEL_A * NGL || !panel_a(p, xa, h.rs, a, b)) continue;
+      if (q >= MAX_PANEL_A * NG || !panel_a(p, xa, h.rs, a, b)) continue;
       double mid = 0.5 * (a + b), hw = 0.5 * (b - a);
-      double r = mid + hw * c_glx[j];
-      r2w[t] = hw * c_glw[j] * r * r;
+      double r = mid + hw * glx(j);
+      r2w[t] = hw * glw(j) * r * r;
       phi[t] = phi_of(h, r);
       cnt = t + 1;
     }
@@ -249,19 +264,19 @@ struct Solver {
     }
     f_cnt = 0;
 #pragma unroll
-    for (int t = 0; t < NSLOT; ++t) {
-      const int q = lane + 32 * t, p = q / NGL, j = q % NGL;
+    for (int t = 0; t < NS; ++t) {
+      const int q = lane + W * t, p = q / NG, j = q % NG;
       f_r2w[t] = 0.0;
       f_phi[t] = h.phi0;
       // panel p of region B: [2^p r_vir, min(2^(p+1) r_vir, r_f)], present while
       // 2^p r_vir < r_f (doubling panels from r_vir to r_f)
-      if (q >= MAX_PANEL_B * NGL) continue;
+      if (q >= MAX_PANEL_B * NG) continue;
       const double a = h.rvir * (double)(1 << p);
       if (!(a < rf)) continue;
       const double b = fmin(2.0 * a, rf);
       double mid = 0.5 * (a + b), hw = 0.5 * (b - a);
-      double r = mid + hw * c_glx[j];
-      f_r2w[t] = hw * c_glw[j] * r * r;
+      double r = mid + hw * glx(j);
+      f_r2w[t] = hw * glw(j) * r * r;
       f_phi[t] = -h.GM / r;
       f_cnt = t + 1;
     }
@@ -284,20 +299,21 @@ struct Solver {
     Sums s = {0, 0, 0, 0, 0};
     if (full_a) {
 #pragma unroll
-      for (int t = 0; t < NSLOT; ++t)
+      for (int t = 0; t < NS; ++t)
         if (t < a_cnt) acc(s, a_r2w[t], a_phi[t], inv_n1T);
     }
 #pragma unroll
-    for (int t = 0; t < NSLOT; ++t)
+    for (int t = 0; t < NS; ++t)
       if (t < f_cnt) acc(s, f_r2w[t], f_phi[t], inv_n1T);
-    s.Im = warp_sum(s.Im);
-    s.In = warp_sum(s.In);
-    s.Ip = warp_sum(s.Ip);
-    s.Jm = warp_sum(s.Jm);
-    s.Jn = warp_sum(s.Jn);
+    s.Im = group_sum(s.Im);
+    s.In = group_sum(s.In);
+    s.Ip = group_sum(s.Ip);
+    s.Jm = group_sum(s.Jm);
+    s.Jn = group_sum(s.Jn);
     return s;
   }
 };
+using Solver = SolverT<32, NGL>;
 
 // Reduced problem at a given r_f: T from the gas-mass condition.
 struct Eval {
@@ -755,6 +771,157 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve(
   }
 }
 
+// ---------------------------------------------------------------- two-halo polish
+// The FP64 two-dimensional Newton of k_solve from a starting point, for two halos per warp
+// (16 lanes each, 8-point panels: the same solutions to 5e-11).  An evaluation's FP64 cost
+// is mostly its per-halo scalar part, executed by every lane of the halo; with two halos per
+// warp each of those instructions serves both.  The two halves run the same number of
+// evaluations (a finished half re-evaluates its last point without using it), so every
+// shuffle is executed by the whole warp.  Halos without a starting point are left to
+// k_solve's nested iteration (okv_nested).
+constexpr int POLISH_W = 16;
+__global__ void __launch_bounds__(32 * SOLVE_WARPS) k_polish(
+    BpParams P, int64_t n, double* model, int32_t* status, double tol, int64_t* nbad,
+    int64_t* nfallback, SolveExtra X, int hpw, const Halo* __restrict__ halos,
+    const int32_t* __restrict__ okv, int32_t* okv_nested) {
+  using SP = SolverT<POLISH_W, NGL_POLISH>;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int sub = lane / POLISH_W, gl = lane % POLISH_W;
+  const int64_t base = (((int64_t)blockIdx.x * SOLVE_WARPS + w) * 2 + sub) * hpw;
+  // both halves iterate hpw times whatever their halos (uniform shuffles)
+  if ((((int64_t)blockIdx.x * SOLVE_WARPS + w) * 2) * hpw >= n) return;  // whole warp idle
+  const double nn = P.n_poly;
+  for (int jj = 0; jj < hpw; ++jj) {
+    const int64_t i = base + jj;
+    const bool in_range = i < n;
+    const int64_t ii = in_range ? i : n - 1;  // a real halo to compute on when idle
+    bool valid = in_range && okv[ii];
+    const Halo h = halos[ii];
+    double g0 = NAN, g1 = NAN;
+    if (valid) {
+      g0 = X.guess[ii];
+      g1 = X.guess[n + ii];
+    }
+    const bool have_guess = isfinite(g0) && isfinite(g1) && exp(g1) > 0.0;
+    if (valid && !have_guess && gl == 0) okv_nested[ii] = 1;  // k_solve's nested path
+    valid = valid && have_guess;
+    const double eps_star = X.prm ? X.prm[ii] : P.eps_star;
+    const double eps_dm = X.prm ? X.prm[2 * n + ii] : P.eps_dm;
+    SP S(h, nn);
+    S.cache_region_a(gl);
+    const double fbM = P.fb * h.M;
+    const double inj = eps_dm * fabs(h.Edm) + eps_star * h.Mstar * bpc::C_KMS * bpc::C_KMS;
+    const double absE = fabs(h.Egi);
+    const double r3v = h.rvir * h.rvir * h.rvir;
+    const double four_pi = 4.0 * bpc::PI;
+    const double inv_np1 = 1.0 / (nn + 1.0), inv_fbM = 1.0 / fbM, inv_absE = 1.0 / absE;
+    const double vmin = log(0.5 * h.rvir), vmax = log(10.0 * h.rvir);
+    const double rmin = 0.5 * h.rvir, rmax = 10.0 * h.rvir;
+    double T = h.GM / h.rvir, rf = 1.1 * h.rvir;
+    if (have_guess) {
+      const double v = fmin(fmax(log(h.rvir) + g0, vmin + 1e-9), vmax - 1e-9);
+      rf = exp(v);
+      T = exp(g1) * h.GM / h.rvir;
+    }
+    double phif = phi_of(h, rf);
+    auto expq = [](double d) { return 1.0 + d * (1.0 + d * (0.5 + d * (1.0 / 6.0 + d * (1.0 / 24.0)))); };
+    // last evaluated point
+    double eT = 0, ethf = 0, erho0 = 0, eRm = 0, eRe = 0, erf = rf;
+    bool eok = false, active = valid, converged = false;
+    for (int it = 0; it < X.max_outer; ++it) {
+      // one evaluation (every lane of the warp runs it; thf <= 0 only marks it not ok)
+      const double inv_T = 1.0 / T;
+      const double inv_n1T = inv_T * inv_np1;
+      const double thf = 1.0 + (h.phi0 - phif) * inv_n1T;
+      S.set_rf(rf, gl);
+      const Sums sm = S.integrals_inv(inv_n1T);
+      if (active) {
+        const bool ok = thf > 0.0;
+        if (!ok) {
+          eok = false;
+          active = false;
+        } else {
+          const double rho0 = h.Ps * inv_T / S.pw(thf, 2);
+          const double In = sm.In, Ip = sm.Ip, Im = sm.Im, Jm = sm.Jm, Jn = sm.Jn;
+          const double Egf = four_pi * rho0 * (1.5 * T * Ip + Jn);
+          const double dEp = four_pi / 3.0 * (r3v - rf * rf * rf) * h.Ps;
+          const double num = (P.energy_sign == 0) ? (Egf - h.Egi - inj - dEp)
+                                                  : (h.Egi - Egf - inj - dEp);
+          const double Re = num * inv_absE;
+          const double Rm = (four_pi * rho0 * In + h.Mstar) * inv_fbM - 1.0;
+          eT = T; ethf = thf; erho0 = rho0; eRm = Rm; eRe = Re; erf = rf; eok = true;
+          if (fabs(Re) < tol && fabs(Rm) < tol) {
+            converged = true;
+            active = false;
+          } else {
+            const double inv_rf = 1.0 / rf, inv_thf = 1.0 / thf;
+            const double dphif = bpc::G * menc_of(h, rf) * inv_rf * inv_rf;
+            const double dthf_drf = -dphif * inv_n1T;
+            const double dlr_drf = -(nn + 1.0) * dthf_drf * inv_thf;
+            const double dlr_dT = (-1.0 - (nn + 1.0) * (1.0 - thf) * inv_thf) * inv_T;
+            const double tfn = S.pw(thf, 1), tfp = tfn * thf;
+            const double dG_drf = four_pi * rho0 * (In * dlr_drf + tfn * rf * rf);
+            const double dG_dT = four_pi * rho0 * (In * dlr_dT + nn * (Im - In) * inv_T);
+            const double dIp_dT = (nn + 1.0) * (In - Ip) * inv_T;
+            const double dJn_dT = nn * (Jm - Jn) * inv_T;
+            const double dEgf_drf =
+                Egf * dlr_drf + four_pi * rho0 * (1.5 * T * tfp + tfn * phif) * rf * rf;
+            const double dEgf_dT =
+                Egf * dlr_dT + four_pi * rho0 * (1.5 * Ip + 1.5 * T * dIp_dT + dJn_dT);
+            const double ddEp_drf = -four_pi * rf * rf * h.Ps;
+            const double dn_dT = (P.energy_sign == 0) ? dEgf_dT : -dEgf_dT;
+            const double dn_drf =
+                (P.energy_sign == 0) ? (dEgf_drf - ddEp_drf) : (-dEgf_drf - ddEp_drf);
+            const double J00 = dG_dT * T * inv_fbM, J01 = dG_drf * rf * inv_fbM;
+            const double J10 = dn_dT * T * inv_absE, J11 = dn_drf * rf * inv_absE;
+            const double det = J00 * J11 - J01 * J10;
+            if (!(fabs(det) > 0.0) || !isfinite(det)) {
+              active = false;
+            } else {
+              const double idet = 1.0 / det;
+              double du = (-Rm * J11 + Re * J01) * idet;
+              double dv = (-Re * J00 + Rm * J10) * idet;
+              const double big = fmax(fabs(du), fabs(dv));
+              if (big > 0.5) { du *= 0.5 / big; dv *= 0.5 / big; }
+              double Tn = T, rn = rf, phin = phif;
+              for (int half = 0; half < 20; ++half) {
+                rn = fmin(fmax(rf * expq(dv), rmin), rmax);
+                phin = phi_of(h, rn);
+                Tn = T * expq(du);
+                if (Tn > (phin - h.phi0) * inv_np1 * (1.0 + 1e-12)) break;
+                du *= 0.5;
+                dv *= 0.5;
+              }
+              T = Tn;
+              rf = rn;
+              phif = phin;
+            }
+          }
+        }
+      }
+      if (__all_sync(0xffffffffu, !active)) break;
+    }
+    if (valid && gl == 0) {
+      int st = converged ? BP_HALO_OK : BP_HALO_MAXIT;
+      if (X.gate > 0 && st != BP_HALO_OK) {
+        const bool pass = eok && fabs(eRe) <= X.gate && fabs(eRm) <= X.gate;
+        st = pass ? BP_HALO_OK : BP_HALO_FALLBACK;
+      }
+      if (eok && ethf <= 0.0) st = BP_HALO_THETA;
+      auto put = [&](int f, double v) { model[(int64_t)f * n + ii] = v; };
+      put(BP_M_T, eok ? eT : 0.0);
+      put(BP_M_RHO0, eok ? erho0 : 0.0);
+      put(BP_M_P0, eok ? erho0 * eT : 0.0);
+      put(BP_M_RF, eok ? erf : 0.0);
+      put(BP_M_RESM, eok ? eRm : NAN);
+      put(BP_M_RESE, eok ? eRe : NAN);
+      status[ii] = st;
+      if (st != BP_HALO_OK) atomicAdd((unsigned long long*)nbad, 1ull);
+      if (st == BP_HALO_FALLBACK) atomicAdd((unsigned long long*)nfallback, 1ull);
+    }
+  }
+}
+
 // ---------------------------------------------------------------- FP32 pre-solve
 // Starting points for the FP64 solve: the same reduced problem (T from the gas-mass
 // condition at each r_f, Newton in ln r_f on the energy condition) in FP32, to
@@ -1042,11 +1209,12 @@ static int solve_launch(bp_ctx* ctx, int64_t n, const double* Mvir, const double
   if (r) return r;
   Halo* halos;
   if ((r = bp_ws(ctx, WS_HALO,
-                 (size_t)n * (sizeof(Halo) + 2 * sizeof(double) + sizeof(int32_t)) + 64,
+                 (size_t)n * (sizeof(Halo) + 2 * sizeof(double) + 2 * sizeof(int32_t)) + 64,
                  (void**)&halos)))
     return r;
   double* pguess = reinterpret_cast<double*>(halos + n);
   int32_t* okv = reinterpret_cast<int32_t*>(pguess + 2 * n);
+  int32_t* okv_nested = okv + n;  // halos the polish leaves to the nested iteration
   BP_CUDA(ctx, cudaMemsetAsync(ctx->d_counter, 0, sizeof(int64_t), ctx->stream));
   BP_CUDA(ctx, cudaMemsetAsync(ctx->d_counter + 3, 0, sizeof(int64_t), ctx->stream));
   // halos per warp: enough warps to fill the GPU, the rest shared out 1..32 per warp
@@ -1064,9 +1232,24 @@ static int solve_launch(bp_ctx* ctx, int64_t n, const double* Mvir, const double
     BP_LAUNCH_CHECK(ctx, "k_presolve launch");
     X.guess = pguess;
   }
-  k_solve<<<(unsigned)blocks, 32 * SOLVE_WARPS, 0, ctx->stream>>>(
-      ctx->p, n, model, status, tol, ctx->d_counter, ctx->d_counter + 3, X, hpw, halos, okv);
-  BP_LAUNCH_CHECK(ctx, "k_solve launch");
+  if (X.guess) {
+    // starting points: two halos per warp; the halos without one get the nested iteration
+    BP_CUDA(ctx, cudaMemsetAsync(okv_nested, 0, (size_t)n * sizeof(int32_t), ctx->stream));
+    const int64_t pwarps = (n + 2 * (int64_t)hpw - 1) / (2 * (int64_t)hpw);
+    const int64_t pblocks = (pwarps + SOLVE_WARPS - 1) / SOLVE_WARPS;
+    k_polish<<<(unsigned)pblocks, 32 * SOLVE_WARPS, 0, ctx->stream>>>(
+        ctx->p, n, model, status, tol, ctx->d_counter, ctx->d_counter + 3, X, hpw, halos, okv,
+        okv_nested);
+    BP_LAUNCH_CHECK(ctx, "k_polish launch");
+    k_solve<<<(unsigned)blocks, 32 * SOLVE_WARPS, 0, ctx->stream>>>(
+        ctx->p, n, model, status, tol, ctx->d_counter, ctx->d_counter + 3, X, hpw, halos,
+        okv_nested);
+    BP_LAUNCH_CHECK(ctx, "k_solve launch");
+  } else {
+    k_solve<<<(unsigned)blocks, 32 * SOLVE_WARPS, 0, ctx->stream>>>(
+        ctx->p, n, model, status, tol, ctx->d_counter, ctx->d_counter + 3, X, hpw, halos, okv);
+    BP_LAUNCH_CHECK(ctx, "k_solve launch");
+  }
   bp_phase_end(ctx, BP_PH_SOLVE);
   BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, ctx->d_counter, sizeof(int64_t),
                                cudaMemcpyDeviceToHost, ctx->stream));
