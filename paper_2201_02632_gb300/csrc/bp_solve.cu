@@ -771,15 +771,16 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve(
   }
 }
 
-// ---------------------------------------------------------------- two-halo polish
-// The FP64 two-dimensional Newton of k_solve from a starting point, for two halos per warp
-// (16 lanes each, 8-point panels: the same solutions to 5e-11).  An evaluation's FP64 cost
-// is mostly its per-halo scalar part, executed by every lane of the halo; with two halos per
-// warp each of those instructions serves both.  The two halves run the same number of
-// evaluations (a finished half re-evaluates its last point without using it), so every
-// shuffle is executed by the whole warp.  Halos without a starting point are left to
+// ---------------------------------------------------------------- multi-halo polish
+// The FP64 two-dimensional Newton of k_solve from a starting point, for several halos per
+// warp (POLISH_W lanes each, 8-point panels: the same solutions to 5e-11).  An evaluation's
+// FP64 cost is mostly its per-halo scalar part, executed by every lane of the halo; with
+// POLISH_H halos per warp each of those instructions serves all of them.  The groups run the
+// same number of evaluations (a finished group re-evaluates its last point without using
+// it), so every shuffle is executed by the whole warp.  Halos without a starting point are left to
 // k_solve's nested iteration (okv_nested).
-constexpr int POLISH_W = 16;
+constexpr int POLISH_W = 8;                  // lanes per halo (16: 15% slower)
+constexpr int POLISH_H = 32 / POLISH_W;       // halos per warp
 __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_polish(
     BpParams P, int64_t n, double* model, int32_t* status, double tol, int64_t* nbad,
     int64_t* nfallback, SolveExtra X, int hpw, const Halo* __restrict__ halos,
@@ -787,9 +788,9 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_polish(
   using SP = SolverT<POLISH_W, NGL_POLISH>;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sub = lane / POLISH_W, gl = lane % POLISH_W;
-  const int64_t base = (((int64_t)blockIdx.x * SOLVE_WARPS + w) * 2 + sub) * hpw;
-  // both halves iterate hpw times whatever their halos (uniform shuffles)
-  if ((((int64_t)blockIdx.x * SOLVE_WARPS + w) * 2) * hpw >= n) return;  // whole warp idle
+  const int64_t base = (((int64_t)blockIdx.x * SOLVE_WARPS + w) * POLISH_H + sub) * hpw;
+  // every group iterates hpw times whatever its halos (uniform shuffles)
+  if ((((int64_t)blockIdx.x * SOLVE_WARPS + w) * POLISH_H) * hpw >= n) return;  // idle warp
   const double nn = P.n_poly;
   for (int jj = 0; jj < hpw; ++jj) {
     const int64_t i = base + jj;
@@ -1235,7 +1236,7 @@ static int solve_launch(bp_ctx* ctx, int64_t n, const double* Mvir, const double
   if (X.guess) {
     // starting points: two halos per warp; the halos without one get the nested iteration
     BP_CUDA(ctx, cudaMemsetAsync(okv_nested, 0, (size_t)n * sizeof(int32_t), ctx->stream));
-    const int64_t pwarps = (n + 2 * (int64_t)hpw - 1) / (2 * (int64_t)hpw);
+    const int64_t pwarps = (n + POLISH_H * (int64_t)hpw - 1) / (POLISH_H * (int64_t)hpw);
     const int64_t pblocks = (pwarps + SOLVE_WARPS - 1) / SOLVE_WARPS;
     k_polish<<<(unsigned)pblocks, 32 * SOLVE_WARPS, 0, ctx->stream>>>(
         ctx->p, n, model, status, tol, ctx->d_counter, ctx->d_counter + 3, X, hpw, halos, okv,
