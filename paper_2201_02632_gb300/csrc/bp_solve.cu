@@ -950,25 +950,30 @@ __device__ __forceinline__ float phi_of_f(const HaloF& h, float r) {
 __device__ __forceinline__ float menc_of_f(const HaloF& h, float r) {
   return r >= h.rvir ? h.M : h.M * m_of_f(r / h.rs) / h.mc;
 }
-__device__ __forceinline__ float warp_sum_f(float v) {
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
 
 struct SumsF {
   float Im, In, Ip, Jm, Jn;
 };
 
-// FP32 counterpart of Solver: the same panels and node slots
-struct SolverF {
+// FP32 counterpart of SolverT: the same panels and node slots (W lanes, NG points)
+template <int W, int NG>
+struct SolverFT {
+  static constexpr int NS = (MAX_PANEL_A * NG + W - 1) / W;
   const HaloF& h;
   int n_int;
   float n;
-  float a_r2w[NSLOT], a_phi[NSLOT], f_r2w[NSLOT], f_phi[NSLOT];
+  float a_r2w[NS], a_phi[NS], f_r2w[NS], f_phi[NS];
   int a_cnt, f_cnt;
   bool full_a;
 
-  __device__ SolverF(const HaloF& hh, float nn, int ni) : h(hh), n_int(ni), n(nn) {}
+  __device__ SolverFT(const HaloF& hh, float nn, int ni) : h(hh), n_int(ni), n(nn) {}
+  static_assert(NG == NGL, "FP32 rule tabulated for NGL points only");
+  __device__ static float glx(int j) { return c_glxf[j]; }
+  __device__ static float glw(int j) { return c_glwf[j]; }
+  __device__ static float group_sum(float v) {
+    for (int o = W / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+  }
   __device__ float pw(float th, int k_off) const {  // theta^{n - 1 + k_off}
     if (n_int > 0) {
       int e = n_int - 1 + k_off;
@@ -982,14 +987,14 @@ struct SolverF {
     }
     return powf(th, n - 1.0f + k_off);
   }
-  __device__ int nodes_a(int lane, float xa, float (&r2w)[NSLOT], float (&phi)[NSLOT]) const {
+  __device__ int nodes_a(int lane, float xa, float (&r2w)[NS], float (&phi)[NS]) const {
     int cnt = 0;
 #pragma unroll
-    for (int t = 0; t < NSLOT; ++t) {
-      const int q = lane + 32 * t, p = q / NGL, j = q % NGL;
+    for (int t = 0; t < NS; ++t) {
+      const int q = lane + W * t, p = q / NG, j = q % NG;
       r2w[t] = 0.f;
       phi[t] = h.phi0;
-      if (q >= MAX_PANEL_A * NGL) continue;
+      if (q >= MAX_PANEL_A * NG) continue;
       float lo = 0.f, hi = fminf(0.5f, xa);
       bool ok = hi > lo;
       for (int k = 0; k < p && ok; ++k) {
@@ -1000,8 +1005,8 @@ struct SolverF {
       if (!ok || !(hi > lo)) continue;
       float a = lo * h.rs, b = hi * h.rs;
       float mid = 0.5f * (a + b), hw = 0.5f * (b - a);
-      float r = mid + hw * c_glxf[j];
-      r2w[t] = hw * c_glwf[j] * r * r;
+      float r = mid + hw * glx(j);
+      r2w[t] = hw * glw(j) * r * r;
       phi[t] = phi_of_f(h, r);
       cnt = t + 1;
     }
@@ -1016,11 +1021,11 @@ struct SolverF {
     }
     f_cnt = 0;
 #pragma unroll
-    for (int t = 0; t < NSLOT; ++t) {
-      const int q = lane + 32 * t, p = q / NGL, j = q % NGL;
+    for (int t = 0; t < NS; ++t) {
+      const int q = lane + W * t, p = q / NG, j = q % NG;
       f_r2w[t] = 0.f;
       f_phi[t] = h.phi0;
-      if (q >= MAX_PANEL_B * NGL) continue;
+      if (q >= MAX_PANEL_B * NG) continue;
       float lo = h.rvir, hi = fminf(2.0f * h.rvir, rf);
       bool ok = true;
       for (int k = 0; k < p && ok; ++k) {
@@ -1030,8 +1035,8 @@ struct SolverF {
       }
       if (!ok || !(hi > lo)) continue;
       float mid = 0.5f * (lo + hi), hw = 0.5f * (hi - lo);
-      float r = mid + hw * c_glxf[j];
-      f_r2w[t] = hw * c_glwf[j] * r * r;
+      float r = mid + hw * glx(j);
+      f_r2w[t] = hw * glw(j) * r * r;
       f_phi[t] = -h.GM / r;
       f_cnt = t + 1;
     }
@@ -1052,20 +1057,22 @@ struct SolverF {
     float inv_n1T = 1.0f / ((n + 1.0f) * T);
     if (full_a) {
 #pragma unroll
-      for (int t = 0; t < NSLOT; ++t)
+      for (int t = 0; t < NS; ++t)
         if (t < a_cnt) acc(s, a_r2w[t], a_phi[t], inv_n1T);
     }
 #pragma unroll
-    for (int t = 0; t < NSLOT; ++t)
+    for (int t = 0; t < NS; ++t)
       if (t < f_cnt) acc(s, f_r2w[t], f_phi[t], inv_n1T);
-    s.Im = warp_sum_f(s.Im);
-    s.In = warp_sum_f(s.In);
-    s.Ip = warp_sum_f(s.Ip);
-    s.Jm = warp_sum_f(s.Jm);
-    s.Jn = warp_sum_f(s.Jn);
+    s.Im = group_sum(s.Im);
+    s.In = group_sum(s.In);
+    s.Ip = group_sum(s.Ip);
+    s.Jm = group_sum(s.Jm);
+    s.Jn = group_sum(s.Jn);
     return s;
   }
 };
+
+using SolverF = SolverFT<32, NGL>;
 
 // guess[i] = ln(r_f / r_vir), guess[n + i] = ln(T r_vir / (G M)), or NaN
 __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_presolve(
@@ -1118,6 +1125,9 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_presolve(
           const float dlr = (-1.0f - (nn + 1.0f) * (1.0f - thf) / thf) / T;
           const float dli = nn * (sm.Im - sm.In) / (T * sm.In);
           float step = -F / ((T - Tmin) * (dlr + dli));
+          // at the FP32 rounding floor (a step below the resolution of s) T has converged
+          if (fabsf(F) < 1e-4f && isfinite(step) && fabsf(step) < 4e-7f * fmaxf(1.0f, fabsf(s)))
+            break;
           if (!isfinite(step)) step = (F > 0) ? 1.0f : -1.0f;
           step = fmaxf(-4.0f, fminf(4.0f, step));
           float sn = s + step;
