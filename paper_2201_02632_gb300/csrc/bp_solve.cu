@@ -150,23 +150,6 @@ __device__ double rho_sigma2(const Halo& h, double r) {
   return rho * sig2;
 }
 
-// Kinetic integral int_a^b 4 pi r^2 rho sigma^2 dr, by parts:
-// (4pi/3)[r^3 K]_a^b + (4pi/3) 4 pi G rho_s^2 r_s^5 [Hq]_xa^xb, Hq' = m(x)/(1+x)^2.
-__device__ double kin_integral(const Halo& h, double a, double b) {
-  auto Hq = [](double x) { return -log1p(x) / (1 + x) - 0.5 / ((1 + x) * (1 + x)); };
-  double ka = (a > 0) ? a * a * a * rho_sigma2(h, a) : 0.0;
-  double kb = b * b * b * rho_sigma2(h, b);
-  double pre = 4.0 * bpc::PI * bpc::G * h.rhos * h.rhos * pow(h.rs, 5);
-  return 4.0 * bpc::PI / 3.0 * ((kb - ka) + pre * (Hq(b / h.rs) - Hq(a / h.rs)));
-}
-// Potential integral int_a^b Phi 4 pi r^2 rho dr inside r_vir (closed form).
-__device__ double pot_integral(const Halo& h, double a, double b) {
-  auto Q = [](double x) { return -(log1p(x) + 1.0) / (1 + x); };
-  double xa = a / h.rs, xb = b / h.rs;
-  double K = h.c / ((1 + h.c) * h.rvir);
-  return -(h.GM * h.M / (h.mc * h.mc)) * ((Q(xb) - Q(xa)) / h.rs - K * (m_of(xb) - m_of(xa)));
-}
-
 __device__ __forceinline__ double phi_of(const Halo& h, double r) {
   if (r > h.rvir) return -h.GM / r;
   double x = r / h.rs;
@@ -461,9 +444,30 @@ __device__ bool halo_setup(const BpParams& P, const BpTables& TB, int64_t n, int
     }
     h.rstar = x * h.rs;
   }
-  h.Egi = P.fb * (1.5 * kin_integral(h, h.rstar, h.rvir) + pot_integral(h, h.rstar, h.rvir));
-  h.Edm = 1.5 * kin_integral(h, 0.0, h.rvir) + pot_integral(h, 0.0, h.rvir);
-  h.Ps = P.fb * rho_sigma2(h, h.rvir);
+  // E_g,i over [r_*, r_vir] and E_DM over [0, r_vir] share their r_vir end: rho sigma^2 at
+  // r_vir (also the surface pressure) and the closed forms there are evaluated once
+  {
+    const double rs2v = rho_sigma2(h, h.rvir);
+    const double kin_pre = 4.0 * bpc::PI * bpc::G * h.rhos * h.rhos * pow(h.rs, 5);
+    auto Hq = [](double x) { return -log1p(x) / (1 + x) - 0.5 / ((1 + x) * (1 + x)); };
+    auto Q = [](double x) { return -(log1p(x) + 1.0) / (1 + x); };
+    const double xs = h.rstar / h.rs, xv = h.rvir / h.rs;
+    const double r3v = h.rvir * h.rvir * h.rvir, r3s = h.rstar * h.rstar * h.rstar;
+    const double Hv = Hq(xv), Qv = Q(xv), mv = m_of(xv);
+    const double K = h.c / ((1 + h.c) * h.rvir);
+    const double pot_pre = -(h.GM * h.M / (h.mc * h.mc));
+    // kinetic integral int_a^{r_vir} 4 pi r^2 rho sigma^2 dr by parts:
+    //   (4pi/3)[r^3 rho sigma^2]_a^{r_vir} + (4pi/3) 4 pi G rho_s^2 r_s^5 [Hq]_{a/r_s}^{c},
+    //   Hq' = m(x)/(1+x)^2; potential integral int_a^{r_vir} Phi 4 pi r^2 rho dr in closed form
+    const double kin_s = 4.0 * bpc::PI / 3.0 *
+                         ((r3v * rs2v - r3s * rho_sigma2(h, h.rstar)) + kin_pre * (Hv - Hq(xs)));
+    const double kin_0 = 4.0 * bpc::PI / 3.0 * (r3v * rs2v + kin_pre * (Hv - Hq(0.0)));
+    const double pot_s = pot_pre * ((Qv - Q(xs)) / h.rs - K * (mv - m_of(xs)));
+    const double pot_0 = pot_pre * ((Qv - Q(0.0)) / h.rs - K * (mv - m_of(0.0)));
+    h.Egi = P.fb * (1.5 * kin_s + pot_s);
+    h.Edm = 1.5 * kin_0 + pot_0;
+    h.Ps = P.fb * rs2v;
+  }
   put(BP_M_RSTAR, h.rstar);
   put(BP_M_EGI, h.Egi);
   put(BP_M_EDM, h.Edm);
