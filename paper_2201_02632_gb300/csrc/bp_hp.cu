@@ -817,9 +817,68 @@ __global__ void k_hs_count(const HpHalo* __restrict__ halos, int64_t nh,
   counts[k] = c;
 }
 
+// The geometry of one (segment, halo) pair: the halo's colatitude offset and longitude in
+// pixel units from the segment's first centre, and the segment's pixels to test.
+struct HsPair {
+  float dth2, sp, rh, rl, sa2;
+  int2 rg;  // pixels rg.x .. rg.y of the segment (empty when rg.x > rg.y)
+};
+__device__ __forceinline__ HsPair hs_pair(const HpHalo& H, const HsRing& G, int c0, int npx) {
+  HsPair q;
+  const float dth = (float)(G.theta - H.cx);
+  const float sd = sinf(0.5f * dth);
+  q.dth2 = sd * sd;
+  q.sp = sinf((float)H.cx) * G.sin_t;
+  // the halo's longitude in pixel units from the segment's first centre (FP64 from the exact
+  // pixel count: an FP32 spacing would misplace centres far along the ring by up to 2e-7 rad),
+  // the representative nearest the segment's middle, as a double-float
+  double rel = H.cy * (double)G.cnt * (0.5 / bpc::PI) - (double)G.phase - (double)c0;
+  rel -= (double)G.cnt * rint((rel - 0.5 * HS_SEG) / (double)G.cnt);
+  q.rh = (float)rel;
+  q.rl = (float)(rel - (double)q.rh);
+  const float sa = sinf(0.5f * (float)H.rad_px);
+  q.sa2 = sa * sa;
+  // all of the segment's pixels when the span can wrap into it from both sides, else the
+  // span around the representative
+  bool full;
+  int j0 = 0, j1 = 0;
+  q.rg = make_int2(0, npx - 1);
+  if (!hs_ring_span(H, G, full, j0, j1)) {
+    q.rg = make_int2(1, 0);
+  } else if (!full && G.cnt > HS_SEG && (j1 - j0) + HS_SEG < G.cnt) {
+    const float w = 0.5f * (float)(j1 - j0);
+    q.rg.x = max(0, (int)floorf(q.rh - w) - 1);
+    q.rg.y = min(npx - 1, (int)ceilf(q.rh + w) + 1);
+  }
+  return q;
+}
+// u = r_perp / r_f of pixel t of the segment, or false outside the aperture
+__device__ __forceinline__ bool hs_pixel_u(const HsPair& q, const HsRing& G, float irf, int t,
+                                           float& uu) {
+  float dp = ((float)t - q.rh) - q.rl;  // longitude offset [pixels]
+  dp -= (float)G.cnt * rintf(dp / (float)G.cnt);
+  const float sp = sinf(0.5f * dp * G.dphi);
+  const float hav = q.dth2 + q.sp * sp * sp;  // sin^2(psi / 2)
+  if (!(hav < q.sa2)) return false;
+  uu = 2.0f * asinf(sqrtf(hav)) * irf;
+  return uu < 1.0f;
+}
+__device__ __forceinline__ int hs_ring_of_segment(const HsRing* __restrict__ R, int nr,
+                                                  uint32_t sg) {
+  int lo = 0, hi = nr - 1;  // the last ring whose first segment is <= sg
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (R[mid].seg0 <= sg) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Pairs in emission order o: key = segment, value = o; per pair its halo and, for a halo
+// evaluated at its pixels (nt = 0), the segment's pixel range and the number of values.
 __global__ void k_hs_emit(const HpHalo* __restrict__ halos, int64_t nh,
                           const HsRing* __restrict__ R, int nr,
-                          const int64_t* __restrict__ offs, uint32_t* keys, uint32_t* vals) {
+                          const int64_t* __restrict__ offs, uint32_t* keys, uint32_t* vals,
+                          uint32_t* p_halo, int2* p_rg, uint32_t* p_len) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nh) return;
   const HpHalo H = halos[k];
@@ -836,108 +895,137 @@ __global__ void k_hs_emit(const HpHalo* __restrict__ halos, int64_t nh,
       hs_span_segments(G, full, j0, j1, [&](uint32_t sg) {
         if (o < end) {  // the count pass gave exactly this many
           keys[o] = sg;
-          vals[o] = (uint32_t)k;
+          vals[o] = (uint32_t)o;
+          p_halo[o] = (uint32_t)k;
+          uint32_t len = 0;
+          if (H.nt == 0) {
+            const int c0 = (int)(sg - G.seg0) * HS_SEG;
+            const HsPair q = hs_pair(H, G, c0, min(HS_SEG, G.cnt - c0));
+            p_rg[o] = q.rg;
+            len = q.rg.y >= q.rg.x ? (uint32_t)(q.rg.y - q.rg.x + 1) : 0u;
+          }
+          p_len[o] = len;
           ++o;
         }
       });
   }
 }
 
-// One CTA per segment: thread t owns pixel seg_start + t of the segment's ring.
+// The values of the halos evaluated at their pixels, before the pairs are sorted: one warp
+// per HS_DIRECT_HPW consecutive halos, lanes over the (pair, pixel) values of all their pairs
+// (emission order; pairs of halos with tables hold none), each value finding its pair by
+// binary search and its halo through the pair.
+constexpr int HS_DIRECT_HPW = 8;
+__global__ void __launch_bounds__(256)
+    k_hs_direct(const HpHalo* __restrict__ halos, int64_t nh, const HsRing* __restrict__ R,
+                int nr, const int64_t* __restrict__ offs, const uint32_t* __restrict__ keys,
+                const uint32_t* __restrict__ p_halo, const int2* __restrict__ p_rg,
+                const int64_t* __restrict__ voff, float n_poly, int n_int, float n_nt,
+                float2* vals) {
+  const int64_t k0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * HS_DIRECT_HPW;
+  const int lane = threadIdx.x & 31;
+  if (k0 >= nh) return;
+  const int64_t k1 = min(nh, k0 + (int64_t)HS_DIRECT_HPW);
+  const int64_t o0 = offs[k0], o1 = offs[k1];
+  const int64_t e0 = voff[o0], e1 = voff[o1];
+  for (int64_t e = e0 + lane; e < e1; e += 32) {
+    int64_t lo = o0, hi = o1 - 1;  // the pair holding value e: the last with voff <= e
+    while (lo < hi) {
+      const int64_t mid = (lo + hi + 1) >> 1;
+      if (voff[mid] <= e) lo = mid; else hi = mid - 1;
+    }
+    const HpHalo H = halos[p_halo[lo]];
+    const uint32_t sg = keys[lo];
+    const HsRing G = R[hs_ring_of_segment(R, nr, sg)];
+    const int c0 = (int)(sg - G.seg0) * HS_SEG;
+    const HsPair q = hs_pair(H, G, c0, min(HS_SEG, G.cnt - c0));
+    const int t = p_rg[lo].x + (int)(e - voff[lo]);
+    float uu, sy = 0.f, sb = 0.f;
+    if (hs_pixel_u(q, G, H.inv_rf_px, t, uu)) {
+      hp_los(H, uu, n_poly, n_int, n_nt, sy, sb);  // chord times the table value
+      sy *= H.Ay;
+      sb *= H.Ab;
+    }
+    vals[e] = make_float2(sy, sb);
+  }
+}
+
+// One CTA per segment: thread t owns pixel seg_start + t of the segment's ring.  Pairs in
+// sorted order (value = emission index); a halo with a table is interpolated at each pixel,
+// a halo evaluated at its pixels adds the values k_hs_direct stored.
 __global__ void __launch_bounds__(HS_SEG)
     k_hs_paste(const HpHalo* __restrict__ halos, const float* __restrict__ tab,
-               const uint32_t* __restrict__ hvals, const int64_t* __restrict__ sstart,
-               const HsRing* __restrict__ R, int nr, float n_poly, int n_int, float n_nt,
-               float* ymap, float* bmap, float* ylo, float* blo) {
+               const uint32_t* __restrict__ pvals, const int64_t* __restrict__ sstart,
+               const HsRing* __restrict__ R, int nr, const uint32_t* __restrict__ p_halo,
+               const int2* __restrict__ p_rg, const int64_t* __restrict__ voff,
+               const float2* __restrict__ dvals, float* ymap, float* bmap, float* ylo,
+               float* blo) {
   __shared__ float s_dth2[HS_CH], s_sp[HS_CH], s_rh[HS_CH], s_rl[HS_CH], s_sa2[HS_CH];
   __shared__ float s_irf[HS_CH], s_ay[HS_CH], s_ab[HS_CH];
   __shared__ int2 s_rng[HS_CH];
   __shared__ const float* s_tab[HS_CH];
   __shared__ int s_nt[HS_CH];
-  __shared__ uint32_t s_hk[HS_CH];
+  __shared__ int64_t s_vo[HS_CH];
   const uint32_t sg = blockIdx.x;
   const int64_t b0 = sstart[sg], b1 = sstart[sg + 1];
   if (b0 == b1) return;
   const int tid = threadIdx.x;
-  // the segment's ring: the last ring whose first segment is <= sg
-  int lo = 0, hi = nr - 1;
-  while (lo < hi) {
-    int mid = (lo + hi + 1) >> 1;
-    if (R[mid].seg0 <= sg) lo = mid; else hi = mid - 1;
-  }
-  const HsRing G = R[lo];
+  const HsRing G = R[hs_ring_of_segment(R, nr, sg)];
   const int c0 = (int)(sg - G.seg0) * HS_SEG;  // ring-local index of the segment's first pixel
   const int npx = min(HS_SEG, G.cnt - c0);
-  const bool whole = G.cnt <= HS_SEG;
   float hy = 0.f, cy = 0.f, hb = 0.f, cb = 0.f;
   for (int64_t base = b0; base < b1; base += HS_CH) {
     const int nch = (int)min((int64_t)HS_CH, b1 - base);
     __syncthreads();
     if (tid < nch) {
-      const uint32_t hk = hvals[base + tid];  // index within the chunk
+      const uint32_t o = pvals[base + tid];
+      const uint32_t hk = p_halo[o];  // index within the chunk
       const HpHalo H = halos[hk];
-      const float dth = (float)(G.theta - H.cx);
-      const float sd = sinf(0.5f * dth);
-      s_dth2[tid] = sd * sd;
-      s_sp[tid] = sinf((float)H.cx) * G.sin_t;
-      // the halo's longitude in pixel units from the segment's first centre (FP64 from the
-      // exact pixel count: an FP32 spacing would misplace centres far along the ring by
-      // up to 2e-7 rad), the representative nearest the segment's middle, as a double-float
-      double rel = H.cy * (double)G.cnt * (0.5 / bpc::PI) - (double)G.phase - (double)c0;
-      rel -= (double)G.cnt * rint((rel - 0.5 * HS_SEG) / (double)G.cnt);
-      const float rh = (float)rel;
-      s_rh[tid] = rh;
-      s_rl[tid] = (float)(rel - (double)rh);
-      const float sa = sinf(0.5f * (float)H.rad_px);
-      s_sa2[tid] = sa * sa;
-      s_irf[tid] = H.inv_rf_px;
-      s_ay[tid] = H.Ay;
-      s_ab[tid] = H.Ab;
-      s_tab[tid] = tab + (int64_t)hk * 2 * HP_ROW;
       s_nt[tid] = H.nt;
-      s_hk[tid] = hk;
-      // the segment's pixels to test: all of them when the span can wrap into the segment
-      // from both sides, else the span around the representative
-      bool full;
-      int j0 = 0, j1 = 0;
-      int2 rg = make_int2(0, npx - 1);
-      if (!hs_ring_span(H, G, full, j0, j1)) {
-        rg = make_int2(1, 0);
-      } else if (!full && !whole && (j1 - j0) + HS_SEG < G.cnt) {
-        const float w = 0.5f * (float)(j1 - j0);
-        rg.x = max(0, (int)floorf(rh - w) - 1);
-        rg.y = min(npx - 1, (int)ceilf(rh + w) + 1);
+      if (H.nt == 0) {  // values stored by k_hs_direct for pixels rg.x .. rg.y
+        const int2 rg = p_rg[o];
+        s_rng[tid] = rg;
+        s_vo[tid] = voff[o] - rg.x;
+      } else {
+        const HsPair q = hs_pair(H, G, c0, npx);
+        s_dth2[tid] = q.dth2;
+        s_sp[tid] = q.sp;
+        s_rh[tid] = q.rh;
+        s_rl[tid] = q.rl;
+        s_sa2[tid] = q.sa2;
+        s_rng[tid] = q.rg;
+        s_irf[tid] = H.inv_rf_px;
+        s_ay[tid] = H.Ay;
+        s_ab[tid] = H.Ab;
+        s_tab[tid] = tab + (int64_t)hk * 2 * HP_ROW;
       }
-      s_rng[tid] = rg;
     }
     __syncthreads();
     if (tid < npx) {
       for (int q = 0; q < nch; ++q) {
         const int2 rg = s_rng[q];
         if (tid < rg.x || tid > rg.y) continue;
-        float dp = ((float)tid - s_rh[q]) - s_rl[q];  // longitude offset [pixels]
-        dp -= (float)G.cnt * rintf(dp / (float)G.cnt);
-        const float sp = sinf(0.5f * dp * G.dphi);
-        const float hav = s_dth2[q] + s_sp[q] * sp * sp;  // sin^2(psi / 2)
-        if (!(hav < s_sa2[q])) continue;
-        const float psi = 2.0f * asinf(sqrtf(hav));
-        const float uu = psi * s_irf[q];
-        if (uu < 1.0f) {
-          const int ntq = s_nt[q];
-          if (ntq > 0) {
-            const float chord = sqrtf(fmaxf(0.f, 1.0f - uu * uu));
-            const float ss = sqrtf(uu);
-            const float* ty = s_tab[q];
-            const float gy = catmull(ty, ss, ntq), gb = catmull(ty + HP_ROW, ss, ntq);
-            kahan_add(hy, cy, s_ay[q] * chord * gy);
-            kahan_add(hb, cb, s_ab[q] * chord * gb);
-          } else {  // small halo: the integrals at this pixel (chord times table value)
-            const HpHalo Hq = halos[s_hk[q]];
-            float sy, sb;
-            hp_los(Hq, uu, n_poly, n_int, n_nt, sy, sb);
-            kahan_add(hy, cy, s_ay[q] * sy);
-            kahan_add(hb, cb, s_ab[q] * sb);
-          }
+        const int ntq = s_nt[q];
+        if (ntq == 0) {
+          const float2 v = dvals[s_vo[q] + tid];
+          kahan_add(hy, cy, v.x);
+          kahan_add(hb, cb, v.y);
+          continue;
+        }
+        HsPair pq;
+        pq.dth2 = s_dth2[q];
+        pq.sp = s_sp[q];
+        pq.rh = s_rh[q];
+        pq.rl = s_rl[q];
+        pq.sa2 = s_sa2[q];
+        float uu;
+        if (hs_pixel_u(pq, G, s_irf[q], tid, uu)) {
+          const float chord = sqrtf(fmaxf(0.f, 1.0f - uu * uu));
+          const float ss = sqrtf(uu);
+          const float* ty = s_tab[q];
+          const float gy = catmull(ty, ss, ntq), gb = catmull(ty + HP_ROW, ss, ntq);
+          kahan_add(hy, cy, s_ay[q] * chord * gy);
+          kahan_add(hb, cb, s_ab[q] * chord * gb);
         }
       }
     }
@@ -1261,8 +1349,31 @@ int bp_paste_halos_healpix(bp_ctx* ctx, int64_t n, const double* theta, const do
     if ((r = bp_ws(ctx, WS_VALS0, (size_t)np * 4, (void**)&v0))) return r;
     if ((r = bp_ws(ctx, WS_KEYS1, (size_t)np * 4, (void**)&k1))) return r;
     if ((r = bp_ws(ctx, WS_VALS1, (size_t)np * 4, (void**)&v1))) return r;
-    k_hs_emit<<<nb, 256, 0, ctx->stream>>>(halos, m, R, nr, offs, k0, v0);
+    // per pair: its halo, and for halos evaluated at their pixels the pixel range and the
+    // offset of its values
+    char* pbuf;
+    if ((r = bp_ws(ctx, WS_UNITS, (size_t)np * 16 + 64, (void**)&pbuf))) return r;
+    int2* p_rg = reinterpret_cast<int2*>(pbuf);
+    uint32_t* p_halo = reinterpret_cast<uint32_t*>(p_rg + np);
+    uint32_t* p_len = p_halo + np;
+    int64_t* voff;
+    if ((r = bp_ws(ctx, WS_PART, (size_t)(np + 1) * 8, (void**)&voff))) return r;
+    k_hs_emit<<<nb, 256, 0, ctx->stream>>>(halos, m, R, nr, offs, k0, v0, p_halo, p_rg, p_len);
     BP_LAUNCH_CHECK(ctx, "healpix emit");
+    if ((r = bp_scan_u32_to_i64(ctx, p_len, voff, np))) return r;
+    BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, voff + np, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    BP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    const int64_t nval = ctx->h_pinned[0];
+    float2* dvals;
+    if ((r = bp_ws(ctx, WS_HALO, (size_t)(nval > 0 ? nval : 1) * sizeof(float2), (void**)&dvals)))
+      return r;
+    if (nval > 0) {  // before the sort: it reads the keys in emission order
+      const int64_t dwarps = (m + HS_DIRECT_HPW - 1) / HS_DIRECT_HPW;
+      k_hs_direct<<<(unsigned)((dwarps * 32 + 255) / 256), 256, 0, ctx->stream>>>(
+          halos, m, R, nr, offs, k0, p_halo, p_rg, voff, (float)P.n_poly, n_int, (float)P.n_nt,
+          dvals);
+      BP_LAUNCH_CHECK(ctx, "healpix direct values");
+    }
     int key_bits = 0;
     while (((int64_t)1 << key_bits) < n_seg) ++key_bits;
     if ((r = bp_radix_sort_pairs(ctx, k0, v0, k1, v1, np, key_bits, &ks, &vs))) return r;
@@ -1272,8 +1383,7 @@ int bp_paste_halos_healpix(bp_ctx* ctx, int64_t n, const double* theta, const do
     bp_phase_end(ctx, BP_PH_HP_PAIRS);
     bp_phase_begin(ctx, BP_PH_HP_PASTE);
     k_hs_paste<<<(unsigned)n_seg, HS_SEG, 0, ctx->stream>>>(
-        halos, tab, vs, sstart, R, nr, (float)P.n_poly, n_int, (float)P.n_nt, ymap, bmap, ylo,
-        blo);
+        halos, tab, vs, sstart, R, nr, p_halo, p_rg, voff, dvals, ymap, bmap, ylo, blo);
     BP_LAUNCH_CHECK(ctx, "healpix paste");
     bp_phase_end(ctx, BP_PH_HP_PASTE);
   }
