@@ -22,6 +22,11 @@
 #define HP_NT 256          // table intervals on s = sqrt(u) in [0, 1]
 #define HP_ROW (HP_NT + 3) // with one ghost node at each end
 #define HP_NGL 12          // Gauss-Legendre points per segment (16 gave the same map errors)
+// Halos whose aperture covers fewer pixels than this get their LOS integrals evaluated at each
+// covered pixel instead of a 257-node table (a table would cost more than the pixels it
+// serves; most halos of the batched and all-sky catalogues cover a few dozen pixels).  Both
+// pastes ran fastest between 128 and 1024 pixels.
+#define HP_DIRECT_PIX 256.0
 
 __constant__ float c_hgx[HP_NGL];
 __constant__ float c_hgw[HP_NGL];
@@ -120,6 +125,7 @@ __global__ void k_hp_prep(BpParams P, int64_t nh, const double* __restrict__ thx
   H.inv_rf_px = (float)(px / rf);
   H.map = mp;
   H.ok = ok ? 1 : 0;
+  if (bpc::PI * H.rad_px * H.rad_px < HP_DIRECT_PIX) H.nt = 0;  // evaluated at its pixels
   out[k] = H;
 }
 
@@ -275,15 +281,21 @@ __device__ __forceinline__ bool hp_box(const HpHalo& H, const bp_map_geom& g, in
   return true;
 }
 
+// Per halo: the tiles its pixel box touches, and the values it needs if it is evaluated at
+// its pixels (its whole box, row-major).
 __global__ void k_hp_count(const HpHalo* __restrict__ halos, int64_t nh, bp_map_geom g, int ts,
-                           uint32_t* counts) {
+                           uint32_t* counts, uint32_t* dlen) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nh) return;
   int i0, i1, j0, j1;
-  uint32_t c = 0;
-  if (hp_box(halos[k], g, i0, i1, j0, j1))
+  uint32_t c = 0, d = 0;
+  const HpHalo H = halos[k];
+  if (hp_box(H, g, i0, i1, j0, j1)) {
     c = (uint32_t)((i1 / ts - i0 / ts + 1) * (j1 / ts - j0 / ts + 1));
+    if (H.nt == 0) d = (uint32_t)((i1 - i0 + 1) * (j1 - j0 + 1));
+  }
   counts[k] = c;
+  dlen[k] = d;
 }
 
 __global__ void k_hp_emit(const HpHalo* __restrict__ halos, int64_t nh, bp_map_geom g, int ts,
@@ -361,12 +373,15 @@ __global__ void __launch_bounds__(HP_THREADS)
     k_hp_paste(const HpHalo* __restrict__ halos, const float* __restrict__ tab,
                const uint32_t* __restrict__ hvals, const HpUnit* __restrict__ units,
                const int64_t* __restrict__ n_units_ptr, int64_t* counter, bp_map_geom g,
-               float* ymap, float* bmap, float* ylo, float* blo, float* partials) {
+               const int64_t* __restrict__ hvoff, const float2* __restrict__ dvals, float* ymap,
+               float* bmap, float* ylo, float* blo, float* partials) {
   constexpr int PR = TS / 16;
   __shared__ float s_cx[HCH], s_cy[HCH], s_rap2[HCH], s_irf[HCH], s_ay[HCH], s_ab[HCH];
   __shared__ int4 s_box[HCH];
   __shared__ const float* s_tab[HCH];
   __shared__ int s_nt[HCH];
+  __shared__ int64_t s_dv[HCH];  // nt = 0: index of the value of tile pixel (0, 0) ...
+  __shared__ int s_bw[HCH];      // ... and of the halo's box row length
   __shared__ int64_t s_unit;
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int lr = lane >> 3, lc = lane & 7;
@@ -404,23 +419,46 @@ __global__ void __launch_bounds__(HP_THREADS)
         s_tab[tid] = tab + (int64_t)hk * 2 * HP_ROW;
         s_nt[tid] = H.nt;
         int i0, i1, j0, j1;
-        int4 bx = make_int4(1, 0, 1, 0);
+        int4 bx = make_int4(1, 0, 1, 0);  // empty
+        int64_t dv = 0;
+        int bw = 0;
         if (hp_box(H, g, i0, i1, j0, j1)) {
-          bx.x = max(i0 - x0, 0);
-          bx.y = min(i1 - x0, TS - 1);
-          bx.z = max(j0 - y0, 0);
-          bx.w = min(j1 - y0, TS - 1);
+          const int4 t = make_int4(max(i0 - x0, 0), min(i1 - x0, TS - 1), max(j0 - y0, 0),
+                                   min(j1 - y0, TS - 1));
+          if (t.y >= t.x && t.w >= t.z) bx = t;
+          bw = i1 - i0 + 1;
+          // the halo's values are row-major over its box (i0..i1, j0..j1)
+          if (H.nt == 0) dv = hvoff[hk] + (int64_t)(y0 - j0) * bw + (x0 - i0);
         }
         s_box[tid] = bx;
+        s_dv[tid] = dv;
+        s_bw[tid] = bw;
       }
       __syncthreads();
       for (int k = 0; k < nch; ++k) {
         int4 bx = s_box[k];
         if (bx.y < wc0 || bx.x > wc0 + 8 * PR - 1 || bx.w < wr0 || bx.z > wr0 + 4 * PR - 1)
           continue;
+        const int ntk = s_nt[k];
+        if (ntk == 0) {  // values stored by k_hp_direct
+          const int bw = s_bw[k];
+          const int64_t dv0 = s_dv[k];
+#pragma unroll
+          for (int r = 0; r < PR; ++r) {
+            const int rr = r0 + r;
+#pragma unroll
+            for (int c = 0; c < PR; ++c) {
+              const int cc = c0 + c;
+              if (cc < bx.x || cc > bx.y || rr < bx.z || rr > bx.w) continue;
+              const float2 v = dvals[dv0 + (int64_t)rr * bw + cc];
+              kahan_add(hy[r][c], cy_[r][c], v.x);
+              kahan_add(hb[r][c], cb_[r][c], v.y);
+            }
+          }
+          continue;
+        }
         const float hcx = s_cx[k], hcy = s_cy[k], rap2 = s_rap2[k], irf = s_irf[k];
         const float* ty = s_tab[k];
-        const int ntk = s_nt[k];
 #pragma unroll
         for (int r = 0; r < PR; ++r) {
           float dy = (float)(r0 + r) + 0.5f - hcy;
@@ -530,13 +568,62 @@ __global__ void k_finalize(int64_t npix, float* map, float* lo, float scale) {
 // The (map, tile, halo) work list of a catalogue, in the context's scratch.
 struct HpList {
   int64_t np = 0, n_tiles = 0, n_units = 0, n_slots = 0;
+  int64_t nh = 0, nval = 0;        // halos; values of the halos evaluated at their pixels
   const uint32_t* vals = nullptr;  // halo indices sorted by (map, tile), then index
+  int64_t* hvoff = nullptr;        // [nh + 1]: first value of each halo (nt = 0 halos)
   int64_t* tstart = nullptr;       // [n_tiles + 1]
   int64_t* uoff = nullptr;         // [n_tiles + 1], uoff[n_tiles] = n_units
   int64_t* soff = nullptr;         // [n_tiles + 1]
   HpUnit* units = nullptr;
   int unit = 0, ts = 0;
 };
+
+// The last index in [lo, hi] whose first value is <= e: the halo holding value e.
+__device__ __forceinline__ int64_t hp_owner(const int64_t* __restrict__ voff, int64_t lo,
+                                            int64_t hi, int64_t e) {
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) >> 1;
+    if (voff[mid] <= e) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// The values (chord-weighted LOS integrals times the amplitudes) of the halos evaluated at
+// their pixels, row-major over each halo's pixel box: one warp per vpw consecutive values (the
+// same work for every warp however the values are spread over the halos), lanes taking them
+// in turn, each finding its halo by binary search inside the warp's range of halos; pixels
+// outside the aperture get zeros.
+__global__ void __launch_bounds__(256)
+    k_hp_direct(const HpHalo* __restrict__ halos, const int64_t* __restrict__ hvoff, int64_t nh,
+                int64_t nval, int vpw, bp_map_geom g, float n_poly, int n_int, float n_nt,
+                float2* dv) {
+  const int64_t e0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * vpw;
+  const int lane = threadIdx.x & 31;
+  if (e0 >= nval) return;
+  const int64_t e1 = min(nval, e0 + vpw);
+  const int64_t ka = hp_owner(hvoff, 0, nh - 1, e0);
+  const int64_t kb = hp_owner(hvoff, ka, nh - 1, e1 - 1);
+  for (int64_t e = e0 + lane; e < e1; e += 32) {
+    const int64_t k = hp_owner(hvoff, ka, kb, e);
+    const HpHalo H = halos[k];
+    int i0, i1, j0, j1;
+    hp_box(H, g, i0, i1, j0, j1);  // non-empty: the halo has values
+    const int local = (int)(e - hvoff[k]), bw = i1 - i0 + 1;
+    const int col = i0 + local % bw, row = j0 + local / bw;
+    const float dx = (float)((double)col + 0.5 - H.cx), dy = (float)((double)row + 0.5 - H.cy);
+    const float d2 = dx * dx + dy * dy;
+    float sy = 0.f, sb = 0.f;
+    if (d2 < (float)(H.rad_px * H.rad_px)) {
+      const float uu = sqrtf(d2) * H.inv_rf_px;
+      if (uu < 1.0f) {
+        hp_los(H, uu, n_poly, n_int, n_nt, sy, sb);  // chord times the table value
+        sy *= H.Ay;
+        sb *= H.Ab;
+      }
+    }
+    dv[e] = make_float2(sy, sb);
+  }
+}
 
 int hp_build_list(bp_ctx* ctx, int64_t n, const HpHalo* halos, const bp_map_geom* g, int TS,
                   int unit, HpList* L) {
@@ -545,17 +632,25 @@ int hp_build_list(bp_ctx* ctx, int64_t n, const HpHalo* halos, const bp_map_geom
   const int64_t n_tiles = (int64_t)ntx * nty * g->n_maps;
   if (n_tiles > (int64_t)UINT32_MAX) return bp_fail(ctx, BP_ERANGE, "paste_halos: too many tiles");
   uint32_t* counts;
-  int64_t* offs;
-  if ((r = bp_ws(ctx, WS_COUNTS, (size_t)(n + 1) * 4, (void**)&counts))) return r;
+  int64_t *offs, *hvoff;
+  if ((r = bp_ws(ctx, WS_COUNTS, (size_t)(n + 1) * 8, (void**)&counts))) return r;
   if ((r = bp_ws(ctx, WS_OFFS, (size_t)(n + 1) * 8, (void**)&offs))) return r;
+  if ((r = bp_ws(ctx, WS_HALO, (size_t)(n + 1) * 8, (void**)&hvoff))) return r;
+  uint32_t* dlen = counts + (n + 1);
   unsigned nb = (unsigned)((n + 255) / 256);
-  k_hp_count<<<nb, 256, 0, ctx->stream>>>(halos, n, *g, TS, counts);
+  k_hp_count<<<nb, 256, 0, ctx->stream>>>(halos, n, *g, TS, counts, dlen);
   BP_LAUNCH_CHECK(ctx, "hp count");
   if ((r = bp_scan_u32_to_i64(ctx, counts, offs, n))) return r;
+  if ((r = bp_scan_u32_to_i64(ctx, dlen, hvoff, n))) return r;
   BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, offs + n, 8, cudaMemcpyDeviceToHost, ctx->stream));
+  BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 1, hvoff + n, 8, cudaMemcpyDeviceToHost,
+                               ctx->stream));
   BP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   const int64_t np = ctx->h_pinned[0];
   L->np = np;
+  L->nh = n;
+  L->nval = ctx->h_pinned[1];
+  L->hvoff = hvoff;
   L->n_tiles = n_tiles;
   L->ts = TS;
   if (np == 0) return BP_OK;
@@ -641,12 +736,24 @@ int hp_grid(bp_ctx* ctx, int ctas_per_sm, int64_t n_units) {
 // fixed-order reduction of split tiles.  No host synchronisation, no allocation.
 template <int TS>
 int hp_launch(bp_ctx* ctx, const HpHalo* halos, const float* tab, const HpList& L, int grid,
-              float* partials, int64_t* counter, const bp_map_geom* g, float* ymap, float* bmap,
-              float* ylo, float* blo) {
+              float* partials, int64_t* counter, const bp_map_geom* g, float2* dvals,
+              float* ymap, float* bmap, float* ylo, float* blo) {
+  if (L.nval > 0) {  // the values of the halos evaluated at their pixels
+    const BpParams& P = ctx->p;
+    const double rn = rint(P.n_poly);
+    const int n_int = (fabs(P.n_poly - rn) < 1e-12 && rn >= 1 && rn <= 16) ? (int)rn : -1;
+    // values per warp: a multiple of 32, up to 256, small enough for 32 warps per SM
+    const int64_t full = (int64_t)ctx->num_sms * 32;
+    const int vpw = (int)std::min<int64_t>(256, ((L.nval + full - 1) / full + 31) / 32 * 32);
+    const int64_t warps = (L.nval + vpw - 1) / vpw;
+    k_hp_direct<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, ctx->stream>>>(
+        halos, L.hvoff, L.nh, L.nval, vpw, *g, (float)P.n_poly, n_int, (float)P.n_nt, dvals);
+    BP_LAUNCH_CHECK(ctx, "hp direct values");
+  }
   BP_CUDA(ctx, cudaMemsetAsync(counter, 0, 8, ctx->stream));
   k_hp_paste<TS><<<(unsigned)grid, HP_THREADS, 0, ctx->stream>>>(
-      halos, tab, L.vals, L.units, L.uoff + L.n_tiles, counter, *g, ymap, bmap, ylo, blo,
-      partials);
+      halos, tab, L.vals, L.units, L.uoff + L.n_tiles, counter, *g, L.hvoff, dvals, ymap, bmap,
+      ylo, blo, partials);
   BP_LAUNCH_CHECK(ctx, "hp paste");
   if (L.n_slots > 0) {
     k_hp_reduce<TS><<<(unsigned)L.n_tiles, 256, 0, ctx->stream>>>(
@@ -680,10 +787,6 @@ int check_hp_args(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_y
 // keeps FP32 relative accuracy down to sub-pixel separations at nside 8192.
 constexpr int HS_SEG = 256;  // pixels per segment = threads per paste CTA
 constexpr int HS_CH = 256;   // pairs staged in shared memory at a time
-// Halos whose aperture covers fewer pixels than this get their LOS integrals evaluated at
-// each covered pixel instead of a 257-node table (most all-sky halos cover a few dozen
-// pixels at nside 8192; a table would cost more than the pixels it serves).
-constexpr float HS_DIRECT_PIX = 32.f;
 
 struct HsRing {
   double theta;      // colatitude of the ring's centres
@@ -726,7 +829,7 @@ __global__ void k_hs_prep(BpParams P, int64_t n, int64_t h0, int64_t m,
   H.ok = ok ? 1 : 0;
   // aperture area in pixels: pi alpha^2 / (4 pi / (12 nside^2))
   const double npx = 3.0 * H.rad_px * H.rad_px * (double)nside * (double)nside;
-  if (npx < HS_DIRECT_PIX) H.nt = 0;
+  if (npx < HP_DIRECT_PIX) H.nt = 0;
   out[kl] = H;
 }
 
@@ -1094,7 +1197,8 @@ struct bp_hp_plan {
   float* tab;
   float* partials;
   int64_t* counter;
-  void* mem[8];
+  float2* dvals;  // values of the halos evaluated at their pixels
+  void* mem[9];
 };
 
 extern "C" {
@@ -1129,11 +1233,15 @@ int bp_paste_halos(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_
     return r;
   int grid = TS == 64 ? hp_grid<64>(ctx, 0, L.n_units) : hp_grid<32>(ctx, 0, L.n_units);
   if (grid < 0) return bp_fail(ctx, BP_ECUDA, "bp_paste_halos: occupancy query");
+  float2* dvals;
+  if ((r = bp_ws(ctx, WS_MISC3, (size_t)(L.nval > 0 ? L.nval : 1) * sizeof(float2),
+                 (void**)&dvals)))
+    return r;
   bp_phase_begin(ctx, BP_PH_HP_PASTE);
-  r = TS == 64 ? hp_launch<64>(ctx, halos, tab, L, grid, partials, ctx->d_counter + 2, geom, ymap,
-                               bmap, ylo, blo)
-               : hp_launch<32>(ctx, halos, tab, L, grid, partials, ctx->d_counter + 2, geom, ymap,
-                               bmap, ylo, blo);
+  r = TS == 64 ? hp_launch<64>(ctx, halos, tab, L, grid, partials, ctx->d_counter + 2, geom, dvals,
+                               ymap, bmap, ylo, blo)
+               : hp_launch<32>(ctx, halos, tab, L, grid, partials, ctx->d_counter + 2, geom, dvals,
+                               ymap, bmap, ylo, blo);
   bp_phase_end(ctx, BP_PH_HP_PASTE);
   return r;
 }
@@ -1192,7 +1300,10 @@ int bp_hp_plan_create(bp_ctx* ctx, int64_t n, const double* th_x, const double* 
       int64_t* tiles = (int64_t*)alloc(4, (size_t)(L.n_tiles + 1) * 3 * 8);
       HpUnit* units = (HpUnit*)alloc(5, (size_t)(L.n_units + 1) * sizeof(HpUnit));
       p->partials = (float*)alloc(6, (size_t)(L.n_slots > 0 ? L.n_slots : 1) * 4 * tile * tile * 4);
-      if (!vals || !tiles || !units || !p->partials) return fail(BP_ENOMEM, "device memory");
+      int64_t* hvoff = (int64_t*)alloc(7, (size_t)(n + 1) * 8);
+      p->dvals = (float2*)alloc(8, (size_t)(L.nval > 0 ? L.nval : 1) * sizeof(float2));
+      if (!vals || !tiles || !units || !p->partials || !hvoff || !p->dvals)
+        return fail(BP_ENOMEM, "device memory");
       cudaStream_t s = ctx->stream;
       size_t tb = (size_t)(L.n_tiles + 1) * 8;
       if (cudaMemcpyAsync(vals, L.vals, (size_t)L.np * 4, cudaMemcpyDeviceToDevice, s) ||
@@ -1201,6 +1312,7 @@ int bp_hp_plan_create(bp_ctx* ctx, int64_t n, const double* th_x, const double* 
           cudaMemcpyAsync(tiles + 2 * (L.n_tiles + 1), L.soff, tb, cudaMemcpyDeviceToDevice, s) ||
           cudaMemcpyAsync(units, L.units, (size_t)L.n_units * sizeof(HpUnit),
                           cudaMemcpyDeviceToDevice, s) ||
+          cudaMemcpyAsync(hvoff, L.hvoff, (size_t)(n + 1) * 8, cudaMemcpyDeviceToDevice, s) ||
           cudaStreamSynchronize(s))
         return fail(BP_ECUDA, "copy of the work list");
       p->L.vals = vals;
@@ -1208,6 +1320,7 @@ int bp_hp_plan_create(bp_ctx* ctx, int64_t n, const double* th_x, const double* 
       p->L.uoff = tiles + (L.n_tiles + 1);
       p->L.soff = tiles + 2 * (L.n_tiles + 1);
       p->L.units = units;
+      p->L.hvoff = hvoff;
       p->grid = tile == 64 ? hp_grid<64>(ctx, ctas_per_sm, L.n_units)
                            : hp_grid<32>(ctx, ctas_per_sm, L.n_units);
       if (p->grid < 0) return fail(BP_ECUDA, "occupancy query");
@@ -1232,9 +1345,9 @@ int bp_hp_plan_execute(bp_ctx* ctx, bp_hp_plan* p, const double* th_x, const dou
   bp_phase_end(ctx, BP_PH_HP_TABLE);
   bp_phase_begin(ctx, BP_PH_HP_PASTE);
   r = p->ts == 64 ? hp_launch<64>(ctx, p->halos, p->tab, p->L, p->grid, p->partials, p->counter,
-                                  &p->geom, ymap, bmap, ylo, blo)
+                                  &p->geom, p->dvals, ymap, bmap, ylo, blo)
                   : hp_launch<32>(ctx, p->halos, p->tab, p->L, p->grid, p->partials, p->counter,
-                                  &p->geom, ymap, bmap, ylo, blo);
+                                  &p->geom, p->dvals, ymap, bmap, ylo, blo);
   bp_phase_end(ctx, BP_PH_HP_PASTE);
   return r;
 }
@@ -1243,7 +1356,7 @@ int64_t bp_hp_plan_pairs(const bp_hp_plan* p) { return p ? p->L.np : 0; }
 
 int bp_hp_plan_destroy(bp_hp_plan* p) {
   if (!p) return BP_OK;
-  for (int k = 0; k < 8; ++k)
+  for (int k = 0; k < 9; ++k)
     if (p->mem[k]) cudaFree(p->mem[k]);
   free(p);
   return BP_OK;
