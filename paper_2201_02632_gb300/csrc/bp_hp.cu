@@ -704,8 +704,9 @@ int hp_tables(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_y,
               const int32_t* status, const bp_map_geom* g, double ap_r500, HpHalo* halos,
               float* tab) {
   unsigned nb = (unsigned)((n + 255) / 256);
-  k_hp_prep<<<nb, 256, 0, ctx->stream>>>(ctx->p, n, th_x, th_y, v_los, map_id, model, status, *g,
-                                         ap_r500, halos);
+  const int pb = bp_item_block(ctx, n, 256);
+  k_hp_prep<<<(unsigned)((n + pb - 1) / pb), pb, 0, ctx->stream>>>(
+      ctx->p, n, th_x, th_y, v_los, map_id, model, status, *g, ap_r500, halos);
   BP_LAUNCH_CHECK(ctx, "hp prep");
   const BpParams& P = ctx->p;
   double rn = rint(P.n_poly);
@@ -1283,9 +1284,9 @@ int bp_hp_plan_create(bp_ctx* ctx, int64_t n, const double* th_x, const double* 
   if (!p->halos || !p->tab || !p->counter) return fail(BP_ENOMEM, "device memory");
   if (n > 0) {
     // the work list needs the apertures: prepare the halo records once here
-    unsigned nb = (unsigned)((n + 255) / 256);
-    k_hp_prep<<<nb, 256, 0, ctx->stream>>>(ctx->p, n, th_x, th_y, nullptr, map_id, model, status,
-                                           *geom, ap_r500, p->halos);
+    const int pb = bp_item_block(ctx, n, 256);
+    k_hp_prep<<<(unsigned)((n + pb - 1) / pb), pb, 0, ctx->stream>>>(
+        ctx->p, n, th_x, th_y, nullptr, map_id, model, status, *geom, ap_r500, p->halos);
     if (cudaGetLastError() != cudaSuccess) return fail(BP_ECUDA, "prep launch");
     ctx->launches++;
     HpList L;

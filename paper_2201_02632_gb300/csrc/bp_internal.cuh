@@ -94,6 +94,13 @@ int bp_fail(bp_ctx* ctx, int code, const char* fmt, ...);
 int bp_cuda_check(bp_ctx* ctx, cudaError_t e, const char* what);
 int bp_ws(bp_ctx* ctx, int slot, size_t bytes, void** out);
 
+// Threads per block of a one-thread-per-item launch: `big`, or one warp per block when
+// blocks of `big` would cover fewer SMs than the GPU has.  Scalar FP64 work is bound by each
+// SM's FP64 rate, so a small catalogue runs fastest as one warp on each of many SMs.
+inline int bp_item_block(const bp_ctx* ctx, int64_t n, int big) {
+  return n < (int64_t)big * ctx->num_sms ? 32 : big;
+}
+
 #define BP_CUDA(ctx, call)                                        \
   do {                                                            \
     cudaError_t e_ = (call);                                      \

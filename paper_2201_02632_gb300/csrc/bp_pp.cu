@@ -687,7 +687,8 @@ int halo_blocks(bp_ctx* ctx, int64_t nh, const double* model, const int32_t* sta
   int r = bp_ws(ctx, WS_HPAR, (size_t)(nh > 0 ? nh : 1) * HB * sizeof(float), (void**)blk);
   if (r) return r;
   if (nh > 0) {
-    k_halo_block<<<(unsigned)((nh + 255) / 256), 256, 0, ctx->stream>>>(ctx->p, nh, model,
+    const int hb = bp_item_block(ctx, nh, 256);
+    k_halo_block<<<(unsigned)((nh + hb - 1) / hb), hb, 0, ctx->stream>>>(ctx->p, nh, model,
                                                                         status, Mp, *blk);
     BP_LAUNCH_CHECK(ctx, "halo block");
   }

@@ -331,8 +331,8 @@ __device__ double fp32_root_r500(float lnK, float c) {
     if (f > 0) lo = x; else hi = x;
     const float df = x / ((1 + x) * (1 + x)) / mx - 3.0f / x;
     float xn = x - f / df;
-    if (!(xn > lo && xn < hi)) xn = 0.5f * (lo + hi);
-    if (fabsf(xn - x) < 1e-6f * x) { x = xn; break; }
+    if (fabsf(xn - x) < 1e-6f * x) { x = xn; break; }  // before the bracket test: at the
+    if (!(xn > lo && xn < hi)) xn = 0.5f * (lo + hi);  // root the step can land on its end
     x = xn;
   }
   return (x > 1e-8f && x < c && isfinite(x)) ? (double)x : 0.5 * (double)c;
@@ -344,8 +344,8 @@ __device__ double fp32_root_mstar(float tgt, float c) {
     if (f < 0) lo = x; else hi = x;
     const float df = x / ((1 + x) * (1 + x));
     float xn = x - f / df;
-    if (!(xn > lo && xn < hi)) xn = 0.5f * (lo + hi);
-    if (fabsf(xn - x) < 1e-6f * x) { x = xn; break; }
+    if (fabsf(xn - x) < 1e-6f * x) { x = xn; break; }  // before the bracket test: at the
+    if (!(xn > lo && xn < hi)) xn = 0.5f * (lo + hi);  // root the step can land on its end
     x = xn;
   }
   return (x > 0.f && x < c && isfinite(x)) ? (double)x : 0.5 * (double)c;
@@ -397,8 +397,8 @@ __device__ bool halo_setup(const BpParams& P, const BpTables& TB, int64_t n, int
       if (f > 0) lo = x; else hi = x;
       double df = x / ((1 + x) * (1 + x)) / mx - 3.0 / x;  // d f / d x
       double xn = x - f / df;
+      if (fabs(xn - x) < 1e-15 * x) { x = xn; break; }  // converged (f may be exactly 0)
       if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
-      if (fabs(xn - x) < 1e-15 * x) { x = xn; break; }
       x = xn;
     }
     h.r500 = x * h.rs;
@@ -438,8 +438,8 @@ __device__ bool halo_setup(const BpParams& P, const BpTables& TB, int64_t n, int
       if (f < 0) lo = x; else hi = x;
       double df = x / ((1 + x) * (1 + x));
       double xn = x - f / df;
+      if (fabs(xn - x) < 1e-15 * x) { x = xn; break; }  // converged (f may be exactly 0)
       if (!(xn > lo && xn < hi)) xn = 0.5 * (lo + hi);
-      if (fabs(xn - x) < 1e-15 * x) { x = xn; break; }
       x = xn;
     }
     h.rstar = x * h.rs;
@@ -506,7 +506,7 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_solve(
     int64_t* nfallback, SolveExtra X, int hpw, const Halo* __restrict__ halos,
     const int32_t* __restrict__ okv) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t base = ((int64_t)blockIdx.x * SOLVE_WARPS + w) * hpw;
+  const int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + w) * hpw;
   if (base >= n) return;
   for (int jj = 0; jj < hpw; ++jj) {
     const int64_t i = base + jj;
@@ -792,9 +792,9 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_polish(
   using SP = SolverT<POLISH_W, NGL_POLISH>;
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int sub = lane / POLISH_W, gl = lane % POLISH_W;
-  const int64_t base = (((int64_t)blockIdx.x * SOLVE_WARPS + w) * POLISH_H + sub) * hpw;
+  const int64_t base = (((int64_t)blockIdx.x * (blockDim.x >> 5) + w) * POLISH_H + sub) * hpw;
   // every group iterates hpw times whatever its halos (uniform shuffles)
-  if ((((int64_t)blockIdx.x * SOLVE_WARPS + w) * POLISH_H) * hpw >= n) return;  // idle warp
+  if ((((int64_t)blockIdx.x * (blockDim.x >> 5) + w) * POLISH_H) * hpw >= n) return;  // idle warp
   const double nn = P.n_poly;
   for (int jj = 0; jj < hpw; ++jj) {
     const int64_t i = base + jj;
@@ -1083,7 +1083,7 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_presolve(
     BpParams P, int64_t n, SolveExtra X, int hpw, const Halo* __restrict__ halos,
     const int32_t* __restrict__ okv, double* guess) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t base = ((int64_t)blockIdx.x * SOLVE_WARPS + w) * hpw;
+  const int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + w) * hpw;
   if (base >= n) return;
   const float nn = (float)P.n_poly;
   const double rn = rint(P.n_poly);
@@ -1238,7 +1238,8 @@ static int solve_launch(bp_ctx* ctx, int64_t n, const double* Mvir, const double
   int64_t warps = (n + hpw - 1) / hpw;
   int64_t blocks = (warps + SOLVE_WARPS - 1) / SOLVE_WARPS;
   bp_phase_begin(ctx, BP_PH_SOLVE);
-  k_setup<<<(unsigned)((n + 127) / 128), 128, 0, ctx->stream>>>(
+  const int sb = bp_item_block(ctx, n, 128);
+  k_setup<<<(unsigned)((n + sb - 1) / sb), sb, 0, ctx->stream>>>(
       ctx->p, ctx->t, n, Mvir, c, z, model, status, ctx->d_counter, X, halos, okv);
   BP_LAUNCH_CHECK(ctx, "k_setup launch");
   if (presolve) {
@@ -1251,8 +1252,10 @@ static int solve_launch(bp_ctx* ctx, int64_t n, const double* Mvir, const double
     // starting points: two halos per warp; the halos without one get the nested iteration
     BP_CUDA(ctx, cudaMemsetAsync(okv_nested, 0, (size_t)n * sizeof(int32_t), ctx->stream));
     const int64_t pwarps = (n + POLISH_H * (int64_t)hpw - 1) / (POLISH_H * (int64_t)hpw);
-    const int64_t pblocks = (pwarps + SOLVE_WARPS - 1) / SOLVE_WARPS;
-    k_polish<<<(unsigned)pblocks, 32 * SOLVE_WARPS, 0, ctx->stream>>>(
+    // one-warp blocks when there are few warps, so that they spread evenly over the SMs
+    const int pw = pwarps < (int64_t)SOLVE_WARPS * ctx->num_sms * 4 ? 1 : SOLVE_WARPS;
+    const int64_t pblocks = (pwarps + pw - 1) / pw;
+    k_polish<<<(unsigned)pblocks, 32 * pw, 0, ctx->stream>>>(
         ctx->p, n, model, status, tol, ctx->d_counter, ctx->d_counter + 3, X, hpw, halos, okv,
         okv_nested);
     BP_LAUNCH_CHECK(ctx, "k_polish launch");
