@@ -115,7 +115,10 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t* keys, in
 // [w * 512, (w + 1) * 512) of the block in index order (32 items at a time, peers by
 // digit with __match_any_sync, per-warp digit counts in shared memory); the block then
 // places every item at its digit-sorted position in a shared-memory buffer and copies
-// the buffer out, so that the writes of each digit run are contiguous in memory.
+// the buffer out, so that the writes of each digit run are contiguous in memory.  Only
+// the ranks stay in registers between the two passes (keys and values are read again for
+// the placement, from L2): this keeps the kernel at about half the registers, twice the
+// resident blocks.
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_SUB = RS_ITEMS / RS_WARPS / 32;  // items per lane
 
@@ -140,14 +143,13 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* kin,
   const uint32_t lt_mask = (1u << lane) - 1u;
   const int64_t bbase = (int64_t)blockIdx.x * RS_ITEMS;
   const int64_t wbase = bbase + (int64_t)w * (RS_ITEMS / RS_WARPS);
-  uint32_t key[RS_SUB], val[RS_SUB], rnk[RS_SUB];
+  uint32_t rnk[RS_SUB];
 #pragma unroll
   for (int j = 0; j < RS_SUB; ++j) {
     const int64_t i = wbase + 32 * j + lane;
     const bool valid = i < n;
-    key[j] = valid ? kin[i] : 0u;
-    val[j] = valid ? vin[i] : 0u;
-    const uint32_t d = (key[j] >> shift) & dmask;
+    const uint32_t key = valid ? kin[i] : 0u;
+    const uint32_t d = (key >> shift) & dmask;
     const uint32_t tag = valid ? d : (0x80000000u | (uint32_t)lane);
     const uint32_t peers = __match_any_sync(0xffffffffu, tag);
     const uint32_t r = __popc(peers & lt_mask);
@@ -179,10 +181,11 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* kin,
   for (int j = 0; j < RS_SUB; ++j) {
     const int64_t i = wbase + 32 * j + lane;
     if (i < n) {
-      const uint32_t d = (key[j] >> shift) & dmask;
+      const uint32_t key = kin[i];
+      const uint32_t d = (key >> shift) & dmask;
       const uint32_t pos = s_start[d] + s_cnt[w][d] + rnk[j];
-      s_k[pos] = key[j];
-      s_v[pos] = val[j];
+      s_k[pos] = key;
+      s_v[pos] = vin[i];
     }
   }
   __syncthreads();
@@ -203,6 +206,18 @@ __global__ void k_tile_ranges(const uint32_t* keys, int64_t n, int64_t n_tiles,
   int64_t lo = (i == 0) ? 0 : (int64_t)keys[i - 1] + 1;
   int64_t hi = (i == n) ? n_tiles : (int64_t)keys[i];
   for (int64_t t = lo; t <= hi && t <= n_tiles; ++t) start[t] = i;
+}
+
+// The scatter's 45 KB of shared memory per block: ask for the largest carveout, so that
+// the four blocks its registers allow are resident together.
+void rs_prefer_shared() {
+  static bool done = false;
+  if (!done) {
+    cudaFuncSetAttribute(k_rs_scatter, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         (int)cudaSharedmemCarveoutMaxShared);
+    cudaGetLastError();  // a preference only
+    done = true;
+  }
 }
 
 }  // namespace
@@ -243,6 +258,7 @@ int bp_radix_sort_pairs(bp_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t* k
   if (r) return r;
   offs = (int64_t*)(((uintptr_t)(hist + (size_t)RS_MAXDIG * nblocks) + 15) & ~(uintptr_t)15);
   uint32_t *ki = keys, *vi = vals, *ko = keys_tmp, *vo = vals_tmp;
+  rs_prefer_shared();
   int shift = 0;
   for (int p = 0; p < npass; ++p) {
     int nb = (shift + bits_per <= key_bits) ? bits_per : key_bits - shift;
@@ -304,6 +320,7 @@ int bp_radix_sort_pairs_buf(bp_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_
   int npass = (key_bits + 7) / 8;
   int bits_per = (key_bits + npass - 1) / npass;
   uint32_t *ki = keys, *vi = vals, *ko = keys_tmp, *vo = vals_tmp;
+  rs_prefer_shared();
   int shift = 0, r;
   for (int p = 0; p < npass; ++p) {
     int nb = (shift + bits_per <= key_bits) ? bits_per : key_bits - shift;
