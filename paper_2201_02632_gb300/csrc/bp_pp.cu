@@ -241,21 +241,41 @@ __global__ void k_pair_count(const float4* __restrict__ rec, int64_t n, int nx, 
   counts[i] = c;
 }
 
+// The warp's particles own one contiguous range of pairs (offs is their exclusive scan):
+// lanes write it 32 consecutive pairs at a time, each finding its particle by a binary
+// search over the warp's 32 offsets (shuffles), so that every store is coalesced.
 __global__ void k_pair_emit(const float4* __restrict__ rec, int64_t n, int nx, int ny, int ts,
                             int select, int ntx, const int64_t* __restrict__ offs,
                             uint32_t* keys, uint32_t* vals) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  int tx0, tx1, ty0, ty1;
-  if (!particle_tiles(rec[2 * i], rec[2 * i + 1], nx, ny, ts, select, tx0, tx1, ty0, ty1))
-    return;
-  int64_t o = offs[i];
-  for (int ty = ty0; ty <= ty1; ++ty)
-    for (int tx = tx0; tx <= tx1; ++tx) {
-      keys[o] = (uint32_t)(ty * ntx + tx);
-      vals[o] = (uint32_t)i;
-      ++o;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int64_t i0 = i - lane;
+  if (i0 >= n) return;  // the whole warp
+  int tx0 = 0, ty0 = 0, w = 1, cnt = 0;
+  if (i < n) {
+    int tx1, ty1;
+    if (particle_tiles(rec[2 * i], rec[2 * i + 1], nx, ny, ts, select, tx0, tx1, ty0, ty1)) {
+      w = tx1 - tx0 + 1;
+      cnt = w * (ty1 - ty0 + 1);
     }
+  }
+  const int64_t base = offs[i0];
+  const int rel = (int)(offs[i < n ? i : n] - base);  // past the end: the total
+  const int end = __shfl_sync(0xffffffffu, rel + cnt, 31);
+  for (int e0 = 0; e0 < end; e0 += 32) {  // warp-uniform trip count
+    const int e = e0 + lane;
+    int p = 0;  // the last particle of the warp whose first pair is <= e
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1)
+      if (__shfl_sync(0xffffffffu, rel, p + step) <= e) p += step;
+    const int px0 = __shfl_sync(0xffffffffu, tx0, p), py0 = __shfl_sync(0xffffffffu, ty0, p);
+    const int pw = __shfl_sync(0xffffffffu, w, p), prel = __shfl_sync(0xffffffffu, rel, p);
+    if (e < end) {
+      const int local = e - prel;
+      keys[base + e] = (uint32_t)((py0 + local / pw) * ntx + px0 + local % pw);
+      vals[base + e] = (uint32_t)(i0 + p);
+    }
+  }
 }
 
 // ---------------------------------------------------------------- work units
