@@ -49,12 +49,12 @@ __device__ __forceinline__ float tf32_rna(float x) {
   return __uint_as_float(r);
 }
 
-// FP32 -> TF32 head + tail by Veltkamp splitting with 2^13 + 1: the head keeps 11
-// significant bits (round to nearest, exactly representable in TF32), head + tail == x
-// exactly; the tensor core then drops the tail's bits beyond TF32.  |x| < 2^114.
+// FP32 -> TF32 head + tail: the head keeps 11 significant bits (the mantissa rounded to
+// nearest, ties away, by an integer add on the bit pattern and a mask: exactly
+// representable in TF32), head + tail == x exactly; the tensor core then drops the tail's
+// bits beyond TF32.  |x| < 2^127.  Two integer instructions and one FP32 subtraction.
 __device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
-  const float s = __fmul_rn(x, 8193.0f);
-  hi = __fsub_rn(s, __fsub_rn(s, x));
+  hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
   lo = __fsub_rn(x, hi);
 }
 
