@@ -203,7 +203,9 @@ def ncu_traffic(kernel_key):
         d = json.load(open(path))[kernel_key]
     except Exception:
         return None
-    src = open(os.path.join(ROOT, "paper_2201_02632_gb300", "csrc", d["source"]), "rb").read()
+    files = d["sources"] if "sources" in d else [d["source"]]
+    src = b"".join(open(os.path.join(ROOT, "paper_2201_02632_gb300", "csrc", f), "rb").read()
+                   for f in files)
     if hashlib.sha256(src).hexdigest()[:16] != d.get("source_sha256_16"):
         return None
     return d.get("dram_bytes_per_launch_scaled")

@@ -7,8 +7,8 @@
 //   A[r, k] = Y_k wy_k(r)  (r < 64),   B_k wy_k(r - 64)  (r >= 64);    Bop[i, k] = wx_k(i).
 // The weights are the FP32 values of the SIMT deposit (the same edge values and
 // differences as bp_cell_weights).  Products are formed in TF32 with each FP32 operand
-// split into a TF32 head and a tail (Veltkamp), a b ~ ah bh + ah bt + at bh (three MMAs;
-// about 1e-6 relative error per product).  Each group of TC_G chunks accumulates in FP32
+// split into a TF32 head (rounded) and an exact tail, a b ~ ah bh + ah bt + at bh (three
+// MMAs; about 1e-6 relative error per product).  Each group of TC_G chunks accumulates in FP32
 // in tensor memory and is then folded into a compensated (head, tail) pair with TwoSum,
 // also kept in tensor memory.
 //
