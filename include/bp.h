@@ -136,7 +136,8 @@ enum {
 #define BP_SELECT_HALO 1
 #define BP_SELECT_FIELD 2
 
-#define BP_SOLVE_FP64 0
+#define BP_SOLVE_FP64 0        /* FP64 solve (FP32 pre-solve, then FP64 Newton to resid_tol) */
+#define BP_SOLVE_FP64_SEEDED 1 /* bp_solve_halos_ex only: the guess starts the FP32 pre-solve */
 
 #define BP_OUT_YB 0     /* maps hold y and b */
 #define BP_OUT_DT 1     /* maps hold Delta T / T_CMB: g_nu(x) y and -b */
@@ -212,6 +213,10 @@ int bp_solve_halos(bp_ctx* ctx, int64_t n, const double* Mvir, const double* c, 
  *   gate > 0 (with guess): a halo not converged to resid_tol within max_iter iterations
  *     is accepted if both normalised residuals are <= gate; otherwise it is solved again
  *     from the default start with the full iteration budget (the fallback).
+ *   mode: BP_SOLVE_FP64: the guess starts the FP64 Newton directly;
+ *     BP_SOLVE_FP64_SEEDED: the guess starts the FP32 pre-solve, whose result starts the
+ *     FP64 Newton (max_iter and gate apply to that Newton; halos without a finite guess
+ *     get the pre-solve's default start); without a guess both are bp_solve_halos.
  * The number of halos sent to the fallback is returned by bp_last_fallback_count.
  * Synchronises (one or two counter reads). */
 int bp_solve_halos_ex(bp_ctx* ctx, int64_t n, const double* Mvir, const double* c,
@@ -249,7 +254,9 @@ int bp_mlp_adam(bp_ctx* ctx, float* params, const float* grad, float* m, float* 
 /* BF16 copy of the weights (round to nearest even). */
 int bp_mlp_to_bf16(bp_ctx* ctx, const float* params, uint16_t* weights_bf16);
 /* BF16 inference (BF16 weights and activations, FP32 accumulation, FP32 biases from
- * params): x [n][6] -> y [n][3]. */
+ * params): x [n][6] -> y [n][3].  The two 128 x 128 layers run on the tensor cores;
+ * weights_bf16 must be 16-byte aligned (BP_EINVAL otherwise).  Synchronises: a timed-out
+ * tensor-core wait returns BP_ETIMEOUT. */
 int bp_mlp_infer_bf16(bp_ctx* ctx, int64_t n, const uint16_t* weights_bf16, const float* params,
                       const float* x, float* y);
 /* Normalised features of n halos (params [3][n] per-halo eps_*, f_*, eps_DM or NULL for the
@@ -261,10 +268,12 @@ int bp_mlp_targets(bp_ctx* ctx, int64_t n, const double* model, const float* nor
 /* Mean squared error of y [n][3] against t; dy = 2 (y - t) / (3 n).  loss (host pointer,
  * may be NULL) receives the mean squared error (synchronises when given). */
 int bp_mlp_mse(bp_ctx* ctx, int64_t n, const float* y, const float* t, float* dy, double* loss);
-/* Surrogate solve: BF16 MLP prediction of (r_f, T) as the starting point of polish_iter
- * FP64 Newton iterations (bp_solve_halos_ex with that guess and gate); halos whose
- * normalised features fall outside hull (FP32 [12]: 6 minima then 6 maxima) or whose
- * residual after the polish exceeds gate get the full solve.  Output as bp_solve_halos. */
+/* Surrogate solve: BF16 MLP prediction of (r_f, T) as the seed of the FP32 pre-solve, then
+ * at most polish_iter FP64 Newton iterations (bp_solve_halos_ex, BP_SOLVE_FP64_SEEDED, with
+ * that guess and gate).  Halos whose normalised features fall outside hull (FP32 [12]: 6
+ * minima then 6 maxima) get the plain solve's default start, and halos whose residual after
+ * the polish exceeds gate get the full solve; bp_last_fallback_count returns both.  Output
+ * as bp_solve_halos. */
 int bp_solve_halos_surrogate(bp_ctx* ctx, int64_t n, const double* Mvir, const double* c,
                              const double* z, const double* params, const uint16_t* weights_bf16,
                              const float* mlp_params, const float* norm, const float* hull,

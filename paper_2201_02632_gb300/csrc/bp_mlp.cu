@@ -8,17 +8,19 @@
 //                    transposed weight (data gradient, GELU' epilogue), k_wgrad (per
 //                    row-chunk weight/bias gradient partials) + k_sum_partials (fixed
 //                    order), k_adam
-//  inference:        k_infer_bf16, all four layers fused per 64-row tile, BF16 weights
-//                    and BF16 activations, FP32 accumulation
+//  inference:        k_infer_tc, all four layers fused per 128-row tile, BF16 weights and
+//                    activations, FP32 accumulation; the two 128 x 128 layers on the
+//                    tensor cores (tcgen05, accumulator in tensor memory)
 //  helpers:          k_features, k_targets, k_mse
-// The surrogate solve (bp_solve_halos_surrogate) decodes the prediction into the
-// starting point of a few FP64 Newton iterations of bp_solve_halos_ex, whose residual
-// gate sends the rejected halos to the full solve.
+// The surrogate solve (bp_solve_halos_surrogate) decodes the prediction into the seed of
+// the FP32 pre-solve of bp_solve_halos_ex, whose FP64 Newton and residual gate follow (the
+// rejected halos get the full solve).
 #include <cuda_bf16.h>
 
 #include <vector>
 
 #include "bp_internal.cuh"
+#include "bp_tc.cuh"
 
 namespace {
 
@@ -228,80 +230,219 @@ __global__ void k_to_bf16(const float* __restrict__ p, __nv_bfloat16* __restrict
   wb[j] = __float2bfloat16_rn(p[src]);
 }
 
-// Fused BF16 inference: 64 rows per CTA; weights staged KC inputs at a time; BF16
-// activations in shared memory; FP32 accumulation.
-__global__ void __launch_bounds__(DT) k_infer_bf16(int64_t n, const float* __restrict__ X,
-                                                   const __nv_bfloat16* __restrict__ wb,
-                                                   const float* __restrict__ par,
-                                                   float* __restrict__ Y) {
-  __shared__ __align__(16) __nv_bfloat16 Ws[KC][HID];          // [i][o] chunk
-  __shared__ __align__(16) __nv_bfloat16 Act[2][HID][ROWS + 8];  // ping-pong [i][r]
-  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
-  const int64_t row0 = (int64_t)blockIdx.x * ROWS;
-  for (int idx = tid; idx < ROWS * IN; idx += DT) {
-    int r = idx / IN, i = idx % IN;
-    int64_t row = row0 + r;
-    Act[0][i][r] = __float2bfloat16_rn(row < n ? X[row * IN + i] : 0.f);
+// ---------------------------------------------------------------- tensor-core inference
+// BF16 inference: a persistent CTA of 256 threads takes 128 rows at a time.  Layer 1 (6
+// inputs) runs on the CUDA cores and writes its BF16 activations straight into the A operand
+// of layer 2 (K-major, 128-byte swizzle, two K blocks of 64 inputs, 16 KB each).  Layers 2
+// and 3 are one 128 x 128 x 128 tcgen05 GEMM each (kind::f16, BF16 operands) against W2 and
+// W3, staged once per CTA in the same layout as the B operand, with the FP32 accumulator in
+// tensor memory.  Their epilogues (bias, GELU, rounding to BF16) read it back, warp w taking
+// rows 32 (w % 4) .. + 31 and columns 64 (w / 4) .. + 63; layer 4 (3 outputs, FP32 sums of
+// BF16 activations times BF16 weights) is folded into layer 3's epilogue.  Every mbarrier
+// wait is bounded; a timeout sets *err and stops the CTA.
+constexpr int TI_M = 128, TI_THREADS = 256;
+constexpr int TI_KB = TI_M * 128;  // bytes of one K block (128 rows x 64 BF16)
+constexpr uint32_t TI_COLS = 128;
+constexpr uint32_t TI_IDESC = bptc::idesc_bf16(TI_M, HID);
+constexpr uint32_t TI_WAIT_POLLS = 1u << 26;
+constexpr uint64_t TI_WAIT_NS = 2000000000ull;  // 2 s
+
+struct alignas(1024) TiSmem {
+  unsigned char w2[2 * TI_KB];
+  unsigned char w3[2 * TI_KB];
+  unsigned char act[2 * TI_KB];
+  float w1[HID * IN];
+  float b1[HID], b2[HID], b3[HID];
+  float w4[OUT * HID];
+  float b4[4];
+  float ypart[2][TI_M][OUT];  // layer-4 sums of the two column halves
+  uint64_t mbar;
+  uint32_t tmem;
+};
+
+// byte offset of the 16-byte chunk holding inputs 8 q .. 8 q + 7 (q < 16) of row r
+__device__ __forceinline__ int ti_chunk(int r, int q) {
+  return (q >> 3) * TI_KB + (r >> 3) * 1024 + (r & 7) * 128 + (((q & 7) ^ (r & 7)) << 4);
+}
+
+__device__ __forceinline__ uint4 pack8_bf16(const float* v) {
+  uint4 u;
+  uint32_t* wd = reinterpret_cast<uint32_t*>(&u);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const __nv_bfloat162 t = __floats2bfloat162_rn(v[2 * j], v[2 * j + 1]);
+    wd[j] = *reinterpret_cast<const uint32_t*>(&t);
   }
-  int cur = 0;
-  auto layer = [&](int k_in, int n_out, int wofs, int bofs, bool act, bool last) {
-    const int o0 = lane * 4;
-    float acc[8][4];
+  return u;
+}
+
+__device__ __forceinline__ float bf16_round(float v) {
+  return __bfloat162float(__float2bfloat16_rn(v));
+}
+
+__global__ void __launch_bounds__(TI_THREADS) k_infer_tc(int64_t n, const float* __restrict__ X,
+                                                         const __nv_bfloat16* __restrict__ wb,
+                                                         const float* __restrict__ par,
+                                                         float* __restrict__ Y, int* err) {
+  using namespace bptc;
+  extern __shared__ unsigned char ti_raw[];
+  TiSmem& S = *reinterpret_cast<TiSmem*>(((uintptr_t)ti_raw + 1023) & ~(uintptr_t)1023);
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int64_t ntiles = (n + TI_M - 1) / TI_M;
+  if (w == 0) {
+    tmem_alloc(&S.tmem, TI_COLS);
+    tmem_relinquish();
+  }
+  if (tid == 0) {
+    mbar_init(&S.mbar, 1);
+    fence_mbar_init();
+  }
+  // W2, W3 ([out][in], 16-byte chunks of 8 inputs) into the B-operand layout; the rest FP32
+  const uint4* w2g = reinterpret_cast<const uint4*>(wb + WB_W2);
+  const uint4* w3g = reinterpret_cast<const uint4*>(wb + WB_W3);
+  for (int c = tid; c < HID * 16; c += TI_THREADS) {
+    const int o = c >> 4, q = c & 15;
+    *reinterpret_cast<uint4*>(S.w2 + ti_chunk(o, q)) = w2g[c];
+    *reinterpret_cast<uint4*>(S.w3 + ti_chunk(o, q)) = w3g[c];
+  }
+  for (int i = tid; i < HID * IN; i += TI_THREADS) S.w1[i] = __bfloat162float(wb[WB_W1 + i]);
+  for (int i = tid; i < OUT * HID; i += TI_THREADS) S.w4[i] = __bfloat162float(wb[WB_W4 + i]);
+  for (int i = tid; i < HID; i += TI_THREADS) {
+    S.b1[i] = par[OFF_B1 + i];
+    S.b2[i] = par[OFF_B2 + i];
+    S.b3[i] = par[OFF_B3 + i];
+  }
+  if (tid < OUT) S.b4[tid] = par[OFF_B4 + tid];
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tm = S.tmem;
+  const int qw = w & 3, hw = w >> 2;  // this warp's TMEM lane quarter and column half
+  const uint32_t t_rows = tm + ((uint32_t)(32 * qw) << 16);
+  const int er = 32 * qw + lane;                      // epilogue row
+  const int r1 = tid & (TI_M - 1), h1 = tid >> 7;     // layer-1 row and output half
+  uint32_t phase = 0;
+  bool ok = true;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t row0 = tile * TI_M;
+    {  // layer 1: row r1, outputs 64 h1 .. 64 h1 + 63
+      const int64_t row = row0 + r1;
+      float x[IN];
 #pragma unroll
-    for (int r = 0; r < 8; ++r)
+      for (int i = 0; i < IN; ++i) x[i] = bf16_round(row < n ? X[row * IN + i] : 0.f);
+      for (int g = 0; g < 8; ++g) {
+        float a[8];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) acc[r][c] = 0.f;
-    for (int k0 = 0; k0 < k_in; k0 += KC) {
-      const int kn = min(KC, k_in - k0);
-      __syncthreads();
-      for (int idx = tid; idx < kn * HID; idx += DT) {
-        int o = idx % HID, i = idx / HID;
-        Ws[i][o] = o < n_out ? wb[wofs + (int64_t)o * k_in + k0 + i] : __float2bfloat16_rn(0.f);
-      }
-      __syncthreads();
-      if (o0 < n_out) {
-        for (int i = 0; i < kn; ++i) {
-          uint4 raw = *reinterpret_cast<const uint4*>(&Act[cur][k0 + i][w * 8]);
-          const __nv_bfloat16* xv = reinterpret_cast<const __nv_bfloat16*>(&raw);
-          float xr[8];
+        for (int j = 0; j < 8; ++j) {
+          const int o = 64 * h1 + 8 * g + j;
+          float acc = 0.f;
 #pragma unroll
-          for (int r = 0; r < 8; ++r) xr[r] = __bfloat162float(xv[r]);
-          uint2 wraw = *reinterpret_cast<const uint2*>(&Ws[i][o0]);
-          const __nv_bfloat16* wv = reinterpret_cast<const __nv_bfloat16*>(&wraw);
-          float wc[4];
-#pragma unroll
-          for (int c = 0; c < 4; ++c) wc[c] = __bfloat162float(wv[c]);
-#pragma unroll
-          for (int r = 0; r < 8; ++r)
-#pragma unroll
-            for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(xr[r], wc[c], acc[r][c]);
+          for (int i = 0; i < IN; ++i) acc = fmaf(x[i], S.w1[o * IN + i], acc);
+          a[j] = gelu(acc + S.b1[o]);
         }
+        *reinterpret_cast<uint4*>(S.act + ti_chunk(r1, 8 * h1 + g)) = pack8_bf16(a);
       }
     }
-    if (o0 < n_out) {
+    for (int layer = 0; layer < 2; ++layer) {  // layers 2 and 3
+      fence_proxy_async_smem();  // the activations, written by the threads, to the MMA
+      tc_fence_before();
+      __syncthreads();
+      tc_fence_after();
+      if (tid == 0) {
+        const unsigned char* Bw = layer == 0 ? S.w2 : S.w3;
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        int o = o0 + c;
-        if (o >= n_out) continue;
-        float bo = par[bofs + o];
+        for (int kb = 0; kb < 2; ++kb) {
+          const uint64_t da = desc_sw128(smem_u32(S.act + kb * TI_KB));
+          const uint64_t db = desc_sw128(smem_u32(Bw + kb * TI_KB));
 #pragma unroll
-        for (int r = 0; r < 8; ++r) {
-          float z = acc[r][c] + bo;
-          if (last) {
-            int64_t row = row0 + w * 8 + r;
-            if (row < n) Y[row * OUT + o] = z;
-          } else {
-            Act[cur ^ 1][o][w * 8 + r] = __float2bfloat16_rn(act ? gelu(z) : z);
+          for (int ks = 0; ks < 4; ++ks)  // K step of 16 BF16 = 32 bytes: + 2 in the address
+            mma_bf16(tm, da + 2 * ks, db + 2 * ks, TI_IDESC, (kb | ks) ? 1u : 0u);
+        }
+        mma_commit(&S.mbar);
+      }
+      bool got = mbar_wait_bounded(&S.mbar, phase, TI_WAIT_POLLS, TI_WAIT_NS);
+      got = __syncthreads_and(got) != 0;
+      if (!got) {
+        if (tid == 0) atomicExch(err, 1);
+        ok = false;
+        break;
+      }
+      phase ^= 1u;
+      tc_fence_after();
+      const float* bias = layer == 0 ? S.b2 : S.b3;
+      float y0 = 0.f, y1 = 0.f, y2 = 0.f;
+#pragma unroll
+      for (int c16 = 0; c16 < 4; ++c16) {
+        const int col0 = 64 * hw + 16 * c16;
+        float v[16];
+        tmem_ld16(t_rows + (uint32_t)col0, v);
+        tmem_wait_ld();
+        float a[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) a[j] = bf16_round(gelu(v[j] + bias[col0 + j]));
+        if (layer == 0) {
+          *reinterpret_cast<uint4*>(S.act + ti_chunk(er, col0 / 8)) = pack8_bf16(a);
+          *reinterpret_cast<uint4*>(S.act + ti_chunk(er, col0 / 8 + 1)) = pack8_bf16(a + 8);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            y0 = fmaf(a[j], S.w4[col0 + j], y0);
+            y1 = fmaf(a[j], S.w4[HID + col0 + j], y1);
+            y2 = fmaf(a[j], S.w4[2 * HID + col0 + j], y2);
           }
         }
       }
+      if (layer == 1) {
+        S.ypart[hw][er][0] = y0;
+        S.ypart[hw][er][1] = y1;
+        S.ypart[hw][er][2] = y2;
+      }
     }
-    cur ^= 1;
-  };
-  layer(IN, HID, WB_W1, OFF_B1, true, false);
-  layer(HID, HID, WB_W2, OFF_B2, true, false);
-  layer(HID, HID, WB_W3, OFF_B3, true, false);
-  layer(HID, OUT, WB_W4, OFF_B4, false, true);
+    if (!ok) break;
+    tc_fence_before();
+    __syncthreads();
+    if (tid < TI_M && row0 + tid < n) {
+      const int64_t row = row0 + tid;
+#pragma unroll
+      for (int o = 0; o < OUT; ++o)
+        Y[row * OUT + o] = (S.ypart[0][tid][o] + S.ypart[1][tid][o]) + S.b4[o];
+    }
+  }
+  // a timed-out batch may still be running: wait for it (bounded) before releasing TMEM
+  if (!ok) mbar_wait_bounded(&S.mbar, phase, TI_WAIT_POLLS, TI_WAIT_NS);
+  tc_fence_before();
+  __syncthreads();
+  if (w == 0) tmem_dealloc(tm, TI_COLS);
+}
+
+// Launches the tensor-core inference (at most two CTAs per SM: 128 TMEM columns each and
+// ~100 KB of shared memory) and queues the read-back of its timeout flag into
+// h_pinned[7]; infer_check reads it after a synchronisation.
+int infer_tc(bp_ctx* ctx, int64_t n, const float* x, const uint16_t* wb, const float* par,
+             float* y) {
+  if (n <= 0) return BP_OK;
+  if (((uintptr_t)wb & 15) != 0)
+    return bp_fail(ctx, BP_EINVAL, "mlp inference: BF16 weights not 16-byte aligned");
+  const size_t smem = sizeof(TiSmem) + 1024;
+  BP_CUDA(ctx, cudaFuncSetAttribute(k_infer_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)smem));
+  BP_CUDA(ctx, cudaFuncSetAttribute(k_infer_tc, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                    100));
+  const int64_t ntiles = (n + TI_M - 1) / TI_M;
+  const int64_t grid = std::min<int64_t>(ntiles, (int64_t)ctx->num_sms * 2);
+  BP_CUDA(ctx, cudaMemsetAsync(ctx->d_flags + 1, 0, sizeof(int), ctx->stream));
+  k_infer_tc<<<(unsigned)grid, TI_THREADS, smem, ctx->stream>>>(
+      n, x, reinterpret_cast<const __nv_bfloat16*>(wb), par, y, ctx->d_flags + 1);
+  BP_LAUNCH_CHECK(ctx, "mlp infer (tensor cores)");
+  BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 7, ctx->d_flags + 1, sizeof(int),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+  return BP_OK;
+}
+// after a synchronisation of the stream: did an inference wait time out?
+int infer_check(bp_ctx* ctx) {
+  if (*reinterpret_cast<const int*>(ctx->h_pinned + 7))
+    return bp_fail(ctx, BP_ETIMEOUT, "mlp inference: a tensor-core wait timed out");
+  return BP_OK;
 }
 
 // norm layout: [0..8] means of the 6 features and 3 targets, [9..17] their scales
@@ -360,12 +501,15 @@ __global__ void k_mse(int64_t n, const float* __restrict__ Y, const float* __res
 // decoded prediction -> starting point of the FP64 solve; outside the hull -> NaN
 __global__ void k_decode_guess(int64_t n, const float* __restrict__ Y,
                                const float* __restrict__ norm, const int* __restrict__ outside,
-                               double* __restrict__ guess) {
+                               double* __restrict__ guess, unsigned long long* n_outside) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double g0 = (double)Y[i * OUT + 0] * norm[9 + IN + 0] + norm[IN + 0];
   double g1 = (double)Y[i * OUT + 1] * norm[9 + IN + 1] + norm[IN + 1];
-  if (outside[i]) g0 = g1 = NAN;
+  if (outside[i]) {
+    g0 = g1 = NAN;
+    atomicAdd(n_outside, 1ull);  // an integer count: the same whatever the order
+  }
   guess[i] = g0;
   guess[n + i] = g1;
 }
@@ -495,10 +639,9 @@ int bp_mlp_infer_bf16(bp_ctx* ctx, int64_t n, const uint16_t* weights_bf16, cons
   if (r || n == 0) return r;
   if (!weights_bf16 || !params || !x || !y)
     return bp_fail(ctx, BP_EINVAL, "bp_mlp_infer_bf16: null pointer");
-  k_infer_bf16<<<(unsigned)((n + ROWS - 1) / ROWS), DT, 0, ctx->stream>>>(
-      n, x, (const __nv_bfloat16*)weights_bf16, params, y);
-  BP_LAUNCH_CHECK(ctx, "mlp infer");
-  return BP_OK;
+  if ((r = infer_tc(ctx, n, x, weights_bf16, params, y))) return r;
+  BP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return infer_check(ctx);
 }
 
 int bp_mlp_features(bp_ctx* ctx, int64_t n, const double* Mvir, const double* c, const double* z,
@@ -579,14 +722,25 @@ int bp_solve_halos_surrogate(bp_ctx* ctx, int64_t n, const double* Mvir, const d
   k_features<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, Mvir, c, z, params, norm, x,
                                                                    hull, outside);
   BP_LAUNCH_CHECK(ctx, "features");
-  k_infer_bf16<<<(unsigned)((n + ROWS - 1) / ROWS), DT, 0, ctx->stream>>>(
-      n, x, (const __nv_bfloat16*)weights_bf16, mlp_params, y);
-  BP_LAUNCH_CHECK(ctx, "mlp infer");
-  k_decode_guess<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, y, norm, outside, guess);
+  if ((r = infer_tc(ctx, n, x, weights_bf16, mlp_params, y))) return r;
+  unsigned long long* n_out = (unsigned long long*)(ctx->d_counter + 6);
+  BP_CUDA(ctx, cudaMemsetAsync(n_out, 0, sizeof(int64_t), ctx->stream));
+  k_decode_guess<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(n, y, norm, outside, guess,
+                                                                      n_out);
   BP_LAUNCH_CHECK(ctx, "decode guess");
+  BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 6, n_out, sizeof(int64_t), cudaMemcpyDeviceToHost,
+                               ctx->stream));
   bp_phase_end(ctx, BP_PH_SURROGATE);
-  return bp_solve_halos_ex(ctx, n, Mvir, c, z, params, guess, polish_iter > 0 ? polish_iter : 4,
-                           gate, model, status, BP_SOLVE_FP64, resid_tol);
+  // the prediction seeds the FP32 pre-solve; the halos outside the hull take its default
+  // start (the plain solve), and count as fallbacks with those the gate rejects
+  r = bp_solve_halos_ex(ctx, n, Mvir, c, z, params, guess, polish_iter > 0 ? polish_iter : 4,
+                        gate, model, status, BP_SOLVE_FP64_SEEDED, resid_tol);
+  if (r == BP_OK || r == BP_ENOCONV) {  // the solve synchronised: the counts have arrived
+    ctx->last_fallback += ctx->h_pinned[6];
+    const int t = infer_check(ctx);
+    if (t) return t;
+  }
+  return r;
 }
 
 }  // extern "C"

@@ -1162,10 +1162,18 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_presolve(
         dRe = rf * dnum / absE;
         return isfinite(Re) && isfinite(dRe);
       };
-      // safeguarded Newton in v = ln r_f (bracketed once the sign changes)
+      // safeguarded Newton in v = ln r_f (bracketed once the sign changes), from the
+      // caller's starting point when it has one (a seeded pre-solve), else from 1.1 r_vir
       const float vmin = logf(0.5f * h.rvir), vmax = logf(10.0f * h.rvir);
       float v = logf(1.1f * h.rvir), Tw = 0.f, vprev = 0.f, Rprev = 0.f, va = 0.f, vb = 0.f,
             Ra = 0.f;
+      if (X.guess) {
+        const double s0 = X.guess[i], s1 = X.guess[n + i];
+        if (isfinite(s0) && isfinite(s1)) {
+          v = fminf(fmaxf(logf(h.rvir) + (float)s0, vmin), vmax);
+          Tw = (float)(exp(s1) * H.GM / H.rvir);  // T = e^s1 G M / r_vir
+        }
+      }
       bool have_prev = false, have_br = false, done = false;
       float v_ok = 0.f, T_ok = 0.f;
       for (int it = 0; it < 40; ++it) {
@@ -1284,7 +1292,8 @@ static int solve_args(bp_ctx* ctx, int64_t n, const double* Mvir, const double* 
   if (n < 0) return bp_fail(ctx, BP_EINVAL, "bp_solve_halos: n < 0");
   if (n > 0 && (!Mvir || !c || !z || !model || !status))
     return bp_fail(ctx, BP_EINVAL, "bp_solve_halos: null pointer");
-  if (mode != BP_SOLVE_FP64) return bp_fail(ctx, BP_EINVAL, "bp_solve_halos: unknown mode");
+  if (mode != BP_SOLVE_FP64 && mode != BP_SOLVE_FP64_SEEDED)
+    return bp_fail(ctx, BP_EINVAL, "bp_solve_halos: unknown mode");
   return BP_OK;
 }
 
@@ -1313,14 +1322,16 @@ extern "C" int bp_solve_halos_ex(bp_ctx* ctx, int64_t n, const double* Mvir, con
   int64_t bad = 0;
   double tol = resid_tol > 0 ? resid_tol : 1e-10;
   // Stages: (1) the FP64 Newton from the caller's starting point, or from the FP32
-  // pre-solve when there is none; (2) for halos stage 1 marked FALLBACK after a caller's
-  // starting point: the FP32 pre-solve and the Newton from it; (3) for those still
-  // marked: the full nested FP64 iteration.  A Newton stage accepts a halo when both
-  // residuals are below the gate (the tolerance for the pre-solve stages).
-  const bool presolve = guess == nullptr;
+  // pre-solve when there is none or when it seeds the pre-solve (BP_SOLVE_FP64_SEEDED);
+  // (2) for halos stage 1 marked FALLBACK after a caller's starting point: the FP32
+  // pre-solve and the Newton from it; (3) for those still marked: the full nested FP64
+  // iteration.  A Newton stage accepts a halo when both residuals are below the gate (the
+  // tolerance for the unseeded pre-solve stages, the caller's gate for a seeded one).
+  const bool seeded = mode == BP_SOLVE_FP64_SEEDED && guess != nullptr;
+  const bool presolve = guess == nullptr || seeded;
   if (presolve) {
-    X.max_outer = 8;
-    X.gate = tol;
+    X.max_outer = seeded && max_iter > 0 ? max_iter : 8;
+    X.gate = seeded && gate > 0 ? gate : tol;
   }
   int64_t fb = 0;
   if ((r = solve_launch(ctx, n, Mvir, c, z, model, status, tol, X, &bad, &fb, presolve)))

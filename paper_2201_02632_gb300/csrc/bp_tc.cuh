@@ -1,5 +1,6 @@
 // bp_tc.cuh -- inline-PTX wrappers for the fifth-generation tensor cores (tcgen05),
-// tensor memory (TMEM) and shared-memory mbarriers, as used by the tensor-core deposit.
+// tensor memory (TMEM) and shared-memory mbarriers, as used by the tensor-core deposit and
+// the surrogate's inference.
 //
 // Operand layout: K-major with the 128-byte swizzle.  A row holds 32 TF32 values
 // (128 bytes); 8 rows form a 1024-byte atom; the 16-byte chunk q of row r sits at chunk
@@ -39,6 +40,13 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
 // dense, no negation; N in bits 17-22 (N / 8), M in bits 24-28 (M / 16).
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+// Instruction descriptor of kind::f16 with BF16 A and B (both K-major), FP32 accumulator,
+// dense, no negation; N in bits 17-22 (N / 8), M in bits 24-28 (M / 16).
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
          ((uint32_t)(M >> 4) << 24);
 }
 
@@ -144,6 +152,16 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint6
       "{\n.reg .pred p;\n"
       "setp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (here BF16 operands), issued by one thread
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
       "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
       : "memory");
 }

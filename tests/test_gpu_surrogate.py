@@ -68,6 +68,24 @@ def test_bf16_inference_close_to_fp32(api, ctx):
     assert np.linalg.norm(a - b) <= 1e-2 * np.linalg.norm(b)
 
 
+def test_bf16_inference_many_tiles(api, ctx):
+    """The tensor-core inference over many 128-row tiles per CTA and a ragged last tile:
+    the same agreement with the FP32 forward, row by row in norm."""
+    p = _rand_params(7)
+    n = 300_001
+    x = np.random.default_rng(8).uniform(-1, 1, (n, 6)).astype(np.float32)
+    P, X = cuda(p), cuda(x)
+    y32, _ = ctx.mlp_forward(P, X)
+    y16 = ctx.mlp_infer_bf16(ctx.mlp_to_bf16(P), P, X)
+    a, b = y16.cpu().numpy(), y32.cpu().numpy()
+    assert np.isfinite(a).all()
+    assert np.linalg.norm(a - b) <= 1e-2 * np.linalg.norm(b)
+    # no tile or row left out or shifted (that would differ by the size of the outputs):
+    # every element within the BF16 bound of the 777-row test
+    assert np.abs(a - b).max() <= 3e-2 * max(1.0, np.abs(b).max())
+    assert np.abs(b - np.roll(b, 1, axis=0)).max() > 10 * np.abs(a - b).max()
+
+
 @pytest.fixture(scope="module")
 def trained(api):
     from paper_2201_02632_gb300.surrogate import Surrogate
