@@ -77,3 +77,32 @@ def test_solve_empty_is_noop(api, ctx):
     e = torch.empty(0, dtype=torch.float64, device="cuda")
     model, status = ctx.solve_halos(e, e, e)
     assert model.shape == (len(api.MODEL_FIELDS), 0)
+
+
+def test_seeded_presolve_reaches_the_same_solutions(orc, api, ctx):
+    """BP_SOLVE_FP64_SEEDED: a starting point seeds the FP32 pre-solve.  From the exact
+    solution, from a perturbed one and from no (non-finite) guess the solve reaches the
+    oracle's solutions to the same tolerance as the plain solve."""
+    cat, _ = I.halo_catalog(n=200)
+    M, c, z = cat.M, cat.c, cat.z
+    mo = orc.solve_halos(M, c, z)
+    plain, st = ctx.solve_halos(cuda(M), cuda(c), cuda(z))
+    p = plain.cpu().numpy()
+    assert (st.cpu().numpy() == 0).all()
+    F = api.MF
+    exact = np.stack([np.log(p[F["r_f"]] / p[F["r_vir"]]),
+                      np.log(p[F["T"]] * p[F["r_vir"]] / (4.30091e-9 * p[F["Mvir"]]))])
+    rng = np.random.default_rng(4)
+    perturbed = exact + rng.normal(0, 0.2, exact.shape)
+    nonfinite = exact.copy()
+    nonfinite[:, ::3] = np.nan
+    for guess in (exact, perturbed, nonfinite):
+        model, status = ctx.solve_halos_ex(cuda(M), cuda(c), cuda(z),
+                                           guess=cuda(np.ascontiguousarray(guess)), max_iter=8,
+                                           gate=1e-10, seeded=True)
+        mg = model.cpu().numpy()
+        assert (status.cpu().numpy() == 0).all()
+        _compare(orc, api, mo, mg)
+        assert np.abs(mg[F["res_m"]]).max() < 1e-10 and np.abs(mg[F["res_e"]]).max() < 1e-10
+        for name in SOLVED:
+            np.testing.assert_allclose(mg[F[name]], p[F[name]], rtol=1e-8, err_msg=name)
