@@ -281,10 +281,17 @@ __device__ __forceinline__ bool hp_box(const HpHalo& H, const bp_map_geom& g, in
   return true;
 }
 
+// The pixel box of a halo evaluated at its pixels, with its centre relative to the centre of
+// the box's first pixel (one FP64 subtraction per halo, then FP32 per pixel as in the paste).
+struct HpDBox {
+  int i0, j0, bw;
+  float cxr, cyr, rad2;
+};
+
 // Per halo: the tiles its pixel box touches, and the values it needs if it is evaluated at
-// its pixels (its whole box, row-major).
+// its pixels (its whole box, row-major), with that box.
 __global__ void k_hp_count(const HpHalo* __restrict__ halos, int64_t nh, bp_map_geom g, int ts,
-                           uint32_t* counts, uint32_t* dlen) {
+                           uint32_t* counts, uint32_t* dlen, HpDBox* dbox) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nh) return;
   int i0, i1, j0, j1;
@@ -292,7 +299,17 @@ __global__ void k_hp_count(const HpHalo* __restrict__ halos, int64_t nh, bp_map_
   const HpHalo H = halos[k];
   if (hp_box(H, g, i0, i1, j0, j1)) {
     c = (uint32_t)((i1 / ts - i0 / ts + 1) * (j1 / ts - j0 / ts + 1));
-    if (H.nt == 0) d = (uint32_t)((i1 - i0 + 1) * (j1 - j0 + 1));
+    if (H.nt == 0) {
+      d = (uint32_t)((i1 - i0 + 1) * (j1 - j0 + 1));
+      HpDBox D;
+      D.i0 = i0;
+      D.j0 = j0;
+      D.bw = i1 - i0 + 1;
+      D.cxr = (float)(H.cx - 0.5 - (double)i0);
+      D.cyr = (float)(H.cy - 0.5 - (double)j0);
+      D.rad2 = (float)(H.rad_px * H.rad_px);
+      dbox[k] = D;
+    }
   }
   counts[k] = c;
   dlen[k] = d;
@@ -571,6 +588,7 @@ struct HpList {
   int64_t nh = 0, nval = 0;        // halos; values of the halos evaluated at their pixels
   const uint32_t* vals = nullptr;  // halo indices sorted by (map, tile), then index
   int64_t* hvoff = nullptr;        // [nh + 1]: first value of each halo (nt = 0 halos)
+  HpDBox* dbox = nullptr;          // [nh]: the box of each of those halos
   int64_t* tstart = nullptr;       // [n_tiles + 1]
   int64_t* uoff = nullptr;         // [n_tiles + 1], uoff[n_tiles] = n_units
   int64_t* soff = nullptr;         // [n_tiles + 1]
@@ -594,9 +612,9 @@ __device__ __forceinline__ int64_t hp_owner(const int64_t* __restrict__ voff, in
 // in turn, each finding its halo by binary search inside the warp's range of halos; pixels
 // outside the aperture get zeros.
 __global__ void __launch_bounds__(256)
-    k_hp_direct(const HpHalo* __restrict__ halos, const int64_t* __restrict__ hvoff, int64_t nh,
-                int64_t nval, int vpw, bp_map_geom g, float n_poly, int n_int, float n_nt,
-                float2* dv) {
+    k_hp_direct(const HpHalo* __restrict__ halos, const int64_t* __restrict__ hvoff,
+                const HpDBox* __restrict__ dbox, int64_t nh, int64_t nval, int vpw,
+                float n_poly, int n_int, float n_nt, float2* dv) {
   const int64_t e0 = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * vpw;
   const int lane = threadIdx.x & 31;
   if (e0 >= nval) return;
@@ -605,15 +623,13 @@ __global__ void __launch_bounds__(256)
   const int64_t kb = hp_owner(hvoff, ka, nh - 1, e1 - 1);
   for (int64_t e = e0 + lane; e < e1; e += 32) {
     const int64_t k = hp_owner(hvoff, ka, kb, e);
-    const HpHalo H = halos[k];
-    int i0, i1, j0, j1;
-    hp_box(H, g, i0, i1, j0, j1);  // non-empty: the halo has values
-    const int local = (int)(e - hvoff[k]), bw = i1 - i0 + 1;
-    const int col = i0 + local % bw, row = j0 + local / bw;
-    const float dx = (float)((double)col + 0.5 - H.cx), dy = (float)((double)row + 0.5 - H.cy);
+    const HpDBox D = dbox[k];
+    const int local = (int)(e - hvoff[k]);
+    const float dx = (float)(local % D.bw) - D.cxr, dy = (float)(local / D.bw) - D.cyr;
     const float d2 = dx * dx + dy * dy;
     float sy = 0.f, sb = 0.f;
-    if (d2 < (float)(H.rad_px * H.rad_px)) {
+    if (d2 < D.rad2) {
+      const HpHalo H = halos[k];
       const float uu = sqrtf(d2) * H.inv_rf_px;
       if (uu < 1.0f) {
         hp_los(H, uu, n_poly, n_int, n_nt, sy, sb);  // chord times the table value
@@ -636,9 +652,11 @@ int hp_build_list(bp_ctx* ctx, int64_t n, const HpHalo* halos, const bp_map_geom
   if ((r = bp_ws(ctx, WS_COUNTS, (size_t)(n + 1) * 8, (void**)&counts))) return r;
   if ((r = bp_ws(ctx, WS_OFFS, (size_t)(n + 1) * 8, (void**)&offs))) return r;
   if ((r = bp_ws(ctx, WS_HALO, (size_t)(n + 1) * 8, (void**)&hvoff))) return r;
+  HpDBox* dbox;
+  if ((r = bp_ws(ctx, WS_MISC2, (size_t)n * sizeof(HpDBox), (void**)&dbox))) return r;
   uint32_t* dlen = counts + (n + 1);
   unsigned nb = (unsigned)((n + 255) / 256);
-  k_hp_count<<<nb, 256, 0, ctx->stream>>>(halos, n, *g, TS, counts, dlen);
+  k_hp_count<<<nb, 256, 0, ctx->stream>>>(halos, n, *g, TS, counts, dlen, dbox);
   BP_LAUNCH_CHECK(ctx, "hp count");
   if ((r = bp_scan_u32_to_i64(ctx, counts, offs, n))) return r;
   if ((r = bp_scan_u32_to_i64(ctx, dlen, hvoff, n))) return r;
@@ -651,6 +669,7 @@ int hp_build_list(bp_ctx* ctx, int64_t n, const HpHalo* halos, const bp_map_geom
   L->nh = n;
   L->nval = ctx->h_pinned[1];
   L->hvoff = hvoff;
+  L->dbox = dbox;
   L->n_tiles = n_tiles;
   L->ts = TS;
   if (np == 0) return BP_OK;
@@ -748,7 +767,8 @@ int hp_launch(bp_ctx* ctx, const HpHalo* halos, const float* tab, const HpList& 
     const int vpw = (int)std::min<int64_t>(256, ((L.nval + full - 1) / full + 31) / 32 * 32);
     const int64_t warps = (L.nval + vpw - 1) / vpw;
     k_hp_direct<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, ctx->stream>>>(
-        halos, L.hvoff, L.nh, L.nval, vpw, *g, (float)P.n_poly, n_int, (float)P.n_nt, dvals);
+        halos, L.hvoff, L.dbox, L.nh, L.nval, vpw, (float)P.n_poly, n_int, (float)P.n_nt,
+        dvals);
     BP_LAUNCH_CHECK(ctx, "hp direct values");
   }
   BP_CUDA(ctx, cudaMemsetAsync(counter, 0, 8, ctx->stream));
@@ -1199,7 +1219,7 @@ struct bp_hp_plan {
   float* partials;
   int64_t* counter;
   float2* dvals;  // values of the halos evaluated at their pixels
-  void* mem[9];
+  void* mem[10];
 };
 
 extern "C" {
@@ -1302,8 +1322,9 @@ int bp_hp_plan_create(bp_ctx* ctx, int64_t n, const double* th_x, const double* 
       HpUnit* units = (HpUnit*)alloc(5, (size_t)(L.n_units + 1) * sizeof(HpUnit));
       p->partials = (float*)alloc(6, (size_t)(L.n_slots > 0 ? L.n_slots : 1) * 4 * tile * tile * 4);
       int64_t* hvoff = (int64_t*)alloc(7, (size_t)(n + 1) * 8);
+      HpDBox* dbox = (HpDBox*)alloc(9, (size_t)n * sizeof(HpDBox));
       p->dvals = (float2*)alloc(8, (size_t)(L.nval > 0 ? L.nval : 1) * sizeof(float2));
-      if (!vals || !tiles || !units || !p->partials || !hvoff || !p->dvals)
+      if (!vals || !tiles || !units || !p->partials || !hvoff || !dbox || !p->dvals)
         return fail(BP_ENOMEM, "device memory");
       cudaStream_t s = ctx->stream;
       size_t tb = (size_t)(L.n_tiles + 1) * 8;
@@ -1314,6 +1335,8 @@ int bp_hp_plan_create(bp_ctx* ctx, int64_t n, const double* th_x, const double* 
           cudaMemcpyAsync(units, L.units, (size_t)L.n_units * sizeof(HpUnit),
                           cudaMemcpyDeviceToDevice, s) ||
           cudaMemcpyAsync(hvoff, L.hvoff, (size_t)(n + 1) * 8, cudaMemcpyDeviceToDevice, s) ||
+          cudaMemcpyAsync(dbox, L.dbox, (size_t)n * sizeof(HpDBox), cudaMemcpyDeviceToDevice,
+                          s) ||
           cudaStreamSynchronize(s))
         return fail(BP_ECUDA, "copy of the work list");
       p->L.vals = vals;
@@ -1322,6 +1345,7 @@ int bp_hp_plan_create(bp_ctx* ctx, int64_t n, const double* th_x, const double* 
       p->L.soff = tiles + 2 * (L.n_tiles + 1);
       p->L.units = units;
       p->L.hvoff = hvoff;
+      p->L.dbox = dbox;
       p->grid = tile == 64 ? hp_grid<64>(ctx, ctas_per_sm, L.n_units)
                            : hp_grid<32>(ctx, ctas_per_sm, L.n_units);
       if (p->grid < 0) return fail(BP_ECUDA, "occupancy query");
@@ -1357,7 +1381,7 @@ int64_t bp_hp_plan_pairs(const bp_hp_plan* p) { return p ? p->L.np : 0; }
 
 int bp_hp_plan_destroy(bp_hp_plan* p) {
   if (!p) return BP_OK;
-  for (int k = 0; k < 9; ++k)
+  for (int k = 0; k < 10; ++k)
     if (p->mem[k]) cudaFree(p->mem[k]);
   free(p);
   return BP_OK;
