@@ -442,10 +442,20 @@ __global__ void __launch_bounds__(HP_THREADS)
         if (hp_box(H, g, i0, i1, j0, j1)) {
           const int4 t = make_int4(max(i0 - x0, 0), min(i1 - x0, TS - 1), max(j0 - y0, 0),
                                    min(j1 - y0, TS - 1));
-          if (t.y >= t.x && t.w >= t.z) bx = t;
+          const bool any = t.y >= t.x && t.w >= t.z;
+          if (any) bx = t;
           bw = i1 - i0 + 1;
           // the halo's values are row-major over its box (i0..i1, j0..j1)
-          if (H.nt == 0) dv = hvoff[hk] + (int64_t)(y0 - j0) * bw + (x0 - i0);
+          if (H.nt == 0) {
+            dv = hvoff[hk] + (int64_t)(y0 - j0) * bw + (x0 - i0);
+            if (any) {  // its rows in this tile into L2 before the warps read them
+              const int64_t ea = hvoff[hk] + (int64_t)(y0 + t.z - j0) * bw;
+              const int64_t eb = hvoff[hk] + (int64_t)(y0 + t.w - j0) * bw + bw - 1;
+              const uintptr_t pa = (uintptr_t)(dvals + ea) & ~(uintptr_t)127;
+              for (uintptr_t a = pa; a <= (uintptr_t)(dvals + eb); a += 128)
+                asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+            }
+          }
         }
         s_box[tid] = bx;
         s_dv[tid] = dv;
