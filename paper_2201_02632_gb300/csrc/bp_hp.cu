@@ -217,17 +217,20 @@ __device__ __forceinline__ void hp_los(const HpHalo& H, float u, float n_poly, i
   Sb = sb;
 }
 
-__global__ void __launch_bounds__(256) k_hp_table(const HpHalo* __restrict__ halos, int64_t nh,
+// Table slot j of nh: halo tlist[j] (a list of the halos that need a table), or halo j
+// when tlist is null.
+__global__ void __launch_bounds__(256) k_hp_table(const HpHalo* __restrict__ halos,
+                                                  const uint32_t* __restrict__ tlist, int64_t nh,
                                                   float n_poly, int n_int, float n_nt,
                                                   float* tab) {
   int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  int64_t k = gid / (HP_NT + 1);
+  int64_t j = gid / (HP_NT + 1);
   int node = (int)(gid % (HP_NT + 1));
-  if (k >= nh) return;
-  const HpHalo H = halos[k];
+  if (j >= nh) return;
+  const HpHalo H = halos[tlist ? (int64_t)tlist[j] : j];
   if (node > H.nt || H.nt == 0) return;  // nt = 0: evaluated at its pixels, no table
   const int NTh = H.nt;
-  float* ty = tab + k * 2 * HP_ROW;
+  float* ty = tab + j * 2 * HP_ROW;
   float* tb = ty + HP_ROW;
   if (!H.ok) {
     ty[node + 1] = tb[node + 1] = 0.f;
@@ -254,13 +257,14 @@ __global__ void __launch_bounds__(256) k_hp_table(const HpHalo* __restrict__ hal
 }
 
 // ghost nodes: G(s = -h) = G(h) (even in s), G(1+h) = 2 G(1) - G(1-h)
-__global__ void k_hp_ghosts(const HpHalo* __restrict__ halos, int64_t nh, float* tab) {
-  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= nh) return;
-  const int nt = halos[k].nt;
+__global__ void k_hp_ghosts(const HpHalo* __restrict__ halos, const uint32_t* __restrict__ tlist,
+                            int64_t nh, float* tab) {
+  int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nh) return;
+  const int nt = halos[tlist ? (int64_t)tlist[j] : j].nt;
   if (nt == 0) return;
   for (int q = 0; q < 2; ++q) {
-    float* t = tab + k * 2 * HP_ROW + q * HP_ROW;
+    float* t = tab + j * 2 * HP_ROW + q * HP_ROW;
     t[0] = t[2];
     t[nt + 2] = 2.f * t[nt + 1] - t[nt];
   }
@@ -288,14 +292,15 @@ struct HpDBox {
   float cxr, cyr, rad2;
 };
 
-// Per halo: the tiles its pixel box touches, and the values it needs if it is evaluated at
-// its pixels (its whole box, row-major), with that box.
+// Per halo: the tiles its pixel box touches, the values it needs if it is evaluated at its
+// pixels (its whole box, row-major) with that box, and whether it needs a table (a halo on
+// some map that is not evaluated at its pixels).
 __global__ void k_hp_count(const HpHalo* __restrict__ halos, int64_t nh, bp_map_geom g, int ts,
-                           uint32_t* counts, uint32_t* dlen, HpDBox* dbox) {
+                           uint32_t* counts, uint32_t* dlen, HpDBox* dbox, uint32_t* tflag) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nh) return;
   int i0, i1, j0, j1;
-  uint32_t c = 0, d = 0;
+  uint32_t c = 0, d = 0, tf = 0;
   const HpHalo H = halos[k];
   if (hp_box(H, g, i0, i1, j0, j1)) {
     c = (uint32_t)((i1 / ts - i0 / ts + 1) * (j1 / ts - j0 / ts + 1));
@@ -309,10 +314,20 @@ __global__ void k_hp_count(const HpHalo* __restrict__ halos, int64_t nh, bp_map_
       D.cyr = (float)(H.cy - 0.5 - (double)j0);
       D.rad2 = (float)(H.rad_px * H.rad_px);
       dbox[k] = D;
+    } else {
+      tf = 1;
     }
   }
   counts[k] = c;
   dlen[k] = d;
+  tflag[k] = tf;
+}
+
+// The halos that need a table, in index order: slot toff[k] of the compact table store.
+__global__ void k_hp_tab_emit(const uint32_t* __restrict__ tflag, const int64_t* __restrict__ toff,
+                              int64_t nh, uint32_t* tlist) {
+  int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nh && tflag[k]) tlist[toff[k]] = (uint32_t)k;
 }
 
 __global__ void k_hp_emit(const HpHalo* __restrict__ halos, int64_t nh, bp_map_geom g, int ts,
@@ -390,7 +405,8 @@ __global__ void __launch_bounds__(HP_THREADS)
     k_hp_paste(const HpHalo* __restrict__ halos, const float* __restrict__ tab,
                const uint32_t* __restrict__ hvals, const HpUnit* __restrict__ units,
                const int64_t* __restrict__ n_units_ptr, int64_t* counter, bp_map_geom g,
-               const int64_t* __restrict__ hvoff, const float2* __restrict__ dvals, float* ymap,
+               const int64_t* __restrict__ hvoff, const float2* __restrict__ dvals,
+               const int64_t* __restrict__ toff, float* ymap,
                float* bmap, float* ylo, float* blo, float* partials) {
   constexpr int PR = TS / 16;
   __shared__ float s_cx[HCH], s_cy[HCH], s_rap2[HCH], s_irf[HCH], s_ay[HCH], s_ab[HCH];
@@ -433,7 +449,7 @@ __global__ void __launch_bounds__(HP_THREADS)
         s_irf[tid] = H.inv_rf_px;
         s_ay[tid] = H.Ay;
         s_ab[tid] = H.Ab;
-        s_tab[tid] = tab + (int64_t)hk * 2 * HP_ROW;
+        s_tab[tid] = H.nt > 0 ? tab + toff[hk] * 2 * HP_ROW : tab;  // its table slot
         s_nt[tid] = H.nt;
         int i0, i1, j0, j1;
         int4 bx = make_int4(1, 0, 1, 0);  // empty
@@ -599,6 +615,9 @@ struct HpList {
   const uint32_t* vals = nullptr;  // halo indices sorted by (map, tile), then index
   int64_t* hvoff = nullptr;        // [nh + 1]: first value of each halo (nt = 0 halos)
   HpDBox* dbox = nullptr;          // [nh]: the box of each of those halos
+  int64_t n_table = 0;             // halos with a table
+  int64_t* toff = nullptr;         // [nh + 1]: table slot of each halo (exclusive scan)
+  uint32_t* tlist = nullptr;       // [n_table]: the halo of each table slot
   int64_t* tstart = nullptr;       // [n_tiles + 1]
   int64_t* uoff = nullptr;         // [n_tiles + 1], uoff[n_tiles] = n_units
   int64_t* soff = nullptr;         // [n_tiles + 1]
@@ -659,27 +678,38 @@ int hp_build_list(bp_ctx* ctx, int64_t n, const HpHalo* halos, const bp_map_geom
   if (n_tiles > (int64_t)UINT32_MAX) return bp_fail(ctx, BP_ERANGE, "paste_halos: too many tiles");
   uint32_t* counts;
   int64_t *offs, *hvoff;
-  if ((r = bp_ws(ctx, WS_COUNTS, (size_t)(n + 1) * 8, (void**)&counts))) return r;
-  if ((r = bp_ws(ctx, WS_OFFS, (size_t)(n + 1) * 8, (void**)&offs))) return r;
-  if ((r = bp_ws(ctx, WS_HALO, (size_t)(n + 1) * 8, (void**)&hvoff))) return r;
+  if ((r = bp_ws(ctx, WS_COUNTS, (size_t)(n + 1) * 12, (void**)&counts))) return r;
+  if ((r = bp_ws(ctx, WS_OFFS, (size_t)(n + 1) * 12, (void**)&offs))) return r;
+  if ((r = bp_ws(ctx, WS_HALO, (size_t)(n + 1) * 16, (void**)&hvoff))) return r;
   HpDBox* dbox;
   if ((r = bp_ws(ctx, WS_MISC2, (size_t)n * sizeof(HpDBox), (void**)&dbox))) return r;
   uint32_t* dlen = counts + (n + 1);
+  uint32_t* tflag = dlen + (n + 1);
+  int64_t* toff = hvoff + (n + 1);
+  uint32_t* tlist = reinterpret_cast<uint32_t*>(offs + (n + 1));
   unsigned nb = (unsigned)((n + 255) / 256);
-  k_hp_count<<<nb, 256, 0, ctx->stream>>>(halos, n, *g, TS, counts, dlen, dbox);
+  k_hp_count<<<nb, 256, 0, ctx->stream>>>(halos, n, *g, TS, counts, dlen, dbox, tflag);
   BP_LAUNCH_CHECK(ctx, "hp count");
   if ((r = bp_scan_u32_to_i64(ctx, counts, offs, n))) return r;
   if ((r = bp_scan_u32_to_i64(ctx, dlen, hvoff, n))) return r;
+  if ((r = bp_scan_u32_to_i64(ctx, tflag, toff, n))) return r;
   BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, offs + n, 8, cudaMemcpyDeviceToHost, ctx->stream));
   BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 1, hvoff + n, 8, cudaMemcpyDeviceToHost,
                                ctx->stream));
+  BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 2, toff + n, 8, cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  k_hp_tab_emit<<<nb, 256, 0, ctx->stream>>>(tflag, toff, n, tlist);
+  BP_LAUNCH_CHECK(ctx, "hp table list");
   BP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   const int64_t np = ctx->h_pinned[0];
   L->np = np;
   L->nh = n;
   L->nval = ctx->h_pinned[1];
+  L->n_table = ctx->h_pinned[2];
   L->hvoff = hvoff;
   L->dbox = dbox;
+  L->toff = toff;
+  L->tlist = tlist;
   L->n_tiles = n_tiles;
   L->ts = TS;
   if (np == 0) return BP_OK;
@@ -727,24 +757,31 @@ int hp_build_list(bp_ctx* ctx, int64_t n, const HpHalo* halos, const bp_map_geom
   return BP_OK;
 }
 
-// Tables of the halos: profile constants, line-of-sight integrals, ghost nodes.
-int hp_tables(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_y,
-              const float* v_los, const int32_t* map_id, const double* model,
-              const int32_t* status, const bp_map_geom* g, double ap_r500, HpHalo* halos,
-              float* tab) {
-  unsigned nb = (unsigned)((n + 255) / 256);
+// Halo records: profile constants, amplitudes, apertures in pixels.
+int hp_prep(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_y, const float* v_los,
+            const int32_t* map_id, const double* model, const int32_t* status,
+            const bp_map_geom* g, double ap_r500, HpHalo* halos) {
   const int pb = bp_item_block(ctx, n, 256);
   k_hp_prep<<<(unsigned)((n + pb - 1) / pb), pb, 0, ctx->stream>>>(
       ctx->p, n, th_x, th_y, v_los, map_id, model, status, *g, ap_r500, halos);
   BP_LAUNCH_CHECK(ctx, "hp prep");
+  return BP_OK;
+}
+
+// Tables (line-of-sight integrals and ghost nodes) of the n_table halos of tlist, slot j for
+// halo tlist[j].
+int hp_tables(bp_ctx* ctx, const HpHalo* halos, const uint32_t* tlist, int64_t n_table,
+              float* tab) {
+  if (n_table <= 0) return BP_OK;
   const BpParams& P = ctx->p;
   double rn = rint(P.n_poly);
   int n_int = (fabs(P.n_poly - rn) < 1e-12 && rn >= 1 && rn <= 16) ? (int)rn : -1;
-  int64_t nt = n * (HP_NT + 1);
-  k_hp_table<<<(unsigned)((nt + 255) / 256), 256, 0, ctx->stream>>>(halos, n, (float)P.n_poly,
-                                                                   n_int, (float)P.n_nt, tab);
+  int64_t nt = n_table * (HP_NT + 1);
+  k_hp_table<<<(unsigned)((nt + 255) / 256), 256, 0, ctx->stream>>>(
+      halos, tlist, n_table, (float)P.n_poly, n_int, (float)P.n_nt, tab);
   BP_LAUNCH_CHECK(ctx, "hp table");
-  k_hp_ghosts<<<nb, 256, 0, ctx->stream>>>(halos, n, tab);
+  k_hp_ghosts<<<(unsigned)((n_table + 255) / 256), 256, 0, ctx->stream>>>(halos, tlist, n_table,
+                                                                         tab);
   BP_LAUNCH_CHECK(ctx, "hp ghosts");
   return BP_OK;
 }
@@ -783,8 +820,8 @@ int hp_launch(bp_ctx* ctx, const HpHalo* halos, const float* tab, const HpList& 
   }
   BP_CUDA(ctx, cudaMemsetAsync(counter, 0, 8, ctx->stream));
   k_hp_paste<TS><<<(unsigned)grid, HP_THREADS, 0, ctx->stream>>>(
-      halos, tab, L.vals, L.units, L.uoff + L.n_tiles, counter, *g, L.hvoff, dvals, ymap, bmap,
-      ylo, blo, partials);
+      halos, tab, L.vals, L.units, L.uoff + L.n_tiles, counter, *g, L.hvoff, dvals, L.toff, ymap,
+      bmap, ylo, blo, partials);
   BP_LAUNCH_CHECK(ctx, "hp paste");
   if (L.n_slots > 0) {
     k_hp_reduce<TS><<<(unsigned)L.n_tiles, 256, 0, ctx->stream>>>(
@@ -1229,7 +1266,7 @@ struct bp_hp_plan {
   float* partials;
   int64_t* counter;
   float2* dvals;  // values of the halos evaluated at their pixels
-  void* mem[10];
+  void* mem[12];
 };
 
 extern "C" {
@@ -1246,18 +1283,22 @@ int bp_paste_halos(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_
   if ((r = hp_constants(ctx))) return r;
   HpHalo* halos;
   if ((r = bp_ws(ctx, WS_HPAR, (size_t)n * sizeof(HpHalo), (void**)&halos))) return r;
-  float* tab;
-  if ((r = bp_ws(ctx, WS_TABLE, (size_t)n * 2 * HP_ROW * sizeof(float), (void**)&tab))) return r;
-  bp_phase_begin(ctx, BP_PH_HP_TABLE);
-  if ((r = hp_tables(ctx, n, th_x, th_y, v_los, map_id, model, status, geom, ap_r500, halos, tab)))
-    return r;
-  bp_phase_end(ctx, BP_PH_HP_TABLE);
   const int TS = ctx->hp_tile;
   HpList L;
+  // halo records and the work list (which also lists the halos that need a table)
   bp_phase_begin(ctx, BP_PH_HP_PAIRS);
+  if ((r = hp_prep(ctx, n, th_x, th_y, v_los, map_id, model, status, geom, ap_r500, halos)))
+    return r;
   if ((r = hp_build_list(ctx, n, halos, geom, TS, ctx->hp_unit, &L))) return r;
   bp_phase_end(ctx, BP_PH_HP_PAIRS);
   if (L.np == 0) return BP_OK;
+  float* tab;
+  if ((r = bp_ws(ctx, WS_TABLE, (size_t)(L.n_table > 0 ? L.n_table : 1) * 2 * HP_ROW *
+                                    sizeof(float), (void**)&tab)))
+    return r;
+  bp_phase_begin(ctx, BP_PH_HP_TABLE);
+  if ((r = hp_tables(ctx, halos, L.tlist, L.n_table, tab))) return r;
+  bp_phase_end(ctx, BP_PH_HP_TABLE);
   float* partials;
   if ((r = bp_ws(ctx, WS_PART, (size_t)(L.n_slots > 0 ? L.n_slots : 1) * 4 * TS * TS * 4,
                  (void**)&partials)))
@@ -1309,9 +1350,8 @@ int bp_hp_plan_create(bp_ctx* ctx, int64_t n, const double* th_x, const double* 
   };
   int64_t nn = n > 0 ? n : 1;
   p->halos = (HpHalo*)alloc(0, (size_t)nn * sizeof(HpHalo));
-  p->tab = (float*)alloc(1, (size_t)nn * 2 * HP_ROW * sizeof(float));
   p->counter = (int64_t*)alloc(2, 64);
-  if (!p->halos || !p->tab || !p->counter) return fail(BP_ENOMEM, "device memory");
+  if (!p->halos || !p->counter) return fail(BP_ENOMEM, "device memory");
   if (n > 0) {
     // the work list needs the apertures: prepare the halo records once here
     const int pb = bp_item_block(ctx, n, 256);
@@ -1334,7 +1374,12 @@ int bp_hp_plan_create(bp_ctx* ctx, int64_t n, const double* th_x, const double* 
       int64_t* hvoff = (int64_t*)alloc(7, (size_t)(n + 1) * 8);
       HpDBox* dbox = (HpDBox*)alloc(9, (size_t)n * sizeof(HpDBox));
       p->dvals = (float2*)alloc(8, (size_t)(L.nval > 0 ? L.nval : 1) * sizeof(float2));
-      if (!vals || !tiles || !units || !p->partials || !hvoff || !dbox || !p->dvals)
+      int64_t* toff = (int64_t*)alloc(10, (size_t)(n + 1) * 8);
+      uint32_t* tlist = (uint32_t*)alloc(11, (size_t)(L.n_table > 0 ? L.n_table : 1) * 4);
+      p->tab = (float*)alloc(1, (size_t)(L.n_table > 0 ? L.n_table : 1) * 2 * HP_ROW *
+                                    sizeof(float));
+      if (!vals || !tiles || !units || !p->partials || !hvoff || !dbox || !p->dvals || !toff ||
+          !tlist || !p->tab)
         return fail(BP_ENOMEM, "device memory");
       cudaStream_t s = ctx->stream;
       size_t tb = (size_t)(L.n_tiles + 1) * 8;
@@ -1347,6 +1392,9 @@ int bp_hp_plan_create(bp_ctx* ctx, int64_t n, const double* th_x, const double* 
           cudaMemcpyAsync(hvoff, L.hvoff, (size_t)(n + 1) * 8, cudaMemcpyDeviceToDevice, s) ||
           cudaMemcpyAsync(dbox, L.dbox, (size_t)n * sizeof(HpDBox), cudaMemcpyDeviceToDevice,
                           s) ||
+          cudaMemcpyAsync(toff, L.toff, (size_t)(n + 1) * 8, cudaMemcpyDeviceToDevice, s) ||
+          (L.n_table > 0 && cudaMemcpyAsync(tlist, L.tlist, (size_t)L.n_table * 4,
+                                            cudaMemcpyDeviceToDevice, s)) ||
           cudaStreamSynchronize(s))
         return fail(BP_ECUDA, "copy of the work list");
       p->L.vals = vals;
@@ -1356,6 +1404,8 @@ int bp_hp_plan_create(bp_ctx* ctx, int64_t n, const double* th_x, const double* 
       p->L.units = units;
       p->L.hvoff = hvoff;
       p->L.dbox = dbox;
+      p->L.toff = toff;
+      p->L.tlist = tlist;
       p->grid = tile == 64 ? hp_grid<64>(ctx, ctas_per_sm, L.n_units)
                            : hp_grid<32>(ctx, ctas_per_sm, L.n_units);
       if (p->grid < 0) return fail(BP_ECUDA, "occupancy query");
@@ -1374,9 +1424,10 @@ int bp_hp_plan_execute(bp_ctx* ctx, bp_hp_plan* p, const double* th_x, const dou
     return bp_fail(ctx, BP_EINVAL, "bp_hp_plan_execute: null pointer");
   int r;
   bp_phase_begin(ctx, BP_PH_HP_TABLE);
-  if ((r = hp_tables(ctx, p->n, th_x, th_y, v_los, map_id, model, status, &p->geom, p->ap_r500,
-                     p->halos, p->tab)))
+  if ((r = hp_prep(ctx, p->n, th_x, th_y, v_los, map_id, model, status, &p->geom, p->ap_r500,
+                   p->halos)))
     return r;
+  if ((r = hp_tables(ctx, p->halos, p->L.tlist, p->L.n_table, p->tab))) return r;
   bp_phase_end(ctx, BP_PH_HP_TABLE);
   bp_phase_begin(ctx, BP_PH_HP_PASTE);
   r = p->ts == 64 ? hp_launch<64>(ctx, p->halos, p->tab, p->L, p->grid, p->partials, p->counter,
@@ -1391,7 +1442,7 @@ int64_t bp_hp_plan_pairs(const bp_hp_plan* p) { return p ? p->L.np : 0; }
 
 int bp_hp_plan_destroy(bp_hp_plan* p) {
   if (!p) return BP_OK;
-  for (int k = 0; k < 10; ++k)
+  for (int k = 0; k < 12; ++k)
     if (p->mem[k]) cudaFree(p->mem[k]);
   free(p);
   return BP_OK;
@@ -1469,9 +1520,9 @@ int bp_paste_halos_healpix(bp_ctx* ctx, int64_t n, const double* theta, const do
     int n_int = (fabs(P.n_poly - rn) < 1e-12 && rn >= 1 && rn <= 16) ? (int)rn : -1;
     int64_t nt = m * (HP_NT + 1);
     k_hp_table<<<(unsigned)((nt + 255) / 256), 256, 0, ctx->stream>>>(
-        halos, m, (float)P.n_poly, n_int, (float)P.n_nt, tab);
+        halos, nullptr, m, (float)P.n_poly, n_int, (float)P.n_nt, tab);
     BP_LAUNCH_CHECK(ctx, "healpix table");
-    k_hp_ghosts<<<nb, 256, 0, ctx->stream>>>(halos, m, tab);
+    k_hp_ghosts<<<nb, 256, 0, ctx->stream>>>(halos, nullptr, m, tab);
     BP_LAUNCH_CHECK(ctx, "healpix ghosts");
     bp_phase_end(ctx, BP_PH_HP_TABLE);
     // (segment, halo) pairs sorted by segment
