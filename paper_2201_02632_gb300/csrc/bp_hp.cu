@@ -1,7 +1,8 @@
 // bp_hp.cu -- halo-based pasting (Section 3.3) and map finalisation (Section 3.2).
 //
-//  k_hp_prep    per halo: FP64 centre in pixel units, aperture, FP32 profile constants
-//  k_hp_table   per halo and table node u = r_perp / r_f = s^2 (nodes uniform in s,
+//  k_hp_prep    per halo: FP64 centre in pixel units, aperture, FP32 profile constants;
+//               halos whose aperture covers fewer than HP_DIRECT_PIX pixels get no table
+//  k_hp_table   per tabled halo and table node u = r_perp / r_f = s^2 (nodes uniform in s,
 //               which smooths the central cusp): the line-of-sight integrals of the
 //               dimensionless pressure and density profiles, divided by the chord
 //               sqrt(1 - u^2) so that the tabulated function is smooth at the edge
@@ -9,9 +10,12 @@
 //               t = u sinh(s), split where the 3-D radius crosses r_vir and the zero
 //               of the thermal fraction
 //  k_hp_count / (map, tile, halo) pairs from the FP64 pixel-centre bounding box of the
-//  k_hp_emit    aperture disc
+//  k_hp_emit    aperture disc; the count also sizes the values of the untabled halos and
+//               flags the halos that need a table (k_hp_tab_emit lists them, in order)
+//  k_hp_direct  the line-of-sight integrals of the untabled halos at each of their pixels
 //  k_hp_paste   persistent over work units; each pixel centre inside the aperture adds
-//               the interpolated projected profile with Kahan compensation
+//               the interpolated projected profile (or the stored value of an untabled
+//               halo) with Kahan compensation
 //  k_hp_reduce  partial tiles of multi-unit tiles, in unit order
 //  k_finalize   hi + lo folding and the conversion to Delta T / T_CMB
 #include <algorithm>
