@@ -973,8 +973,11 @@ __device__ __forceinline__ void hs_ring_range(const HpHalo& H, const HsRing* R, 
   if (r1 < nr - 1) ++r1;
 }
 
+// Per halo: its (segment, halo) pairs, and whether it needs a table (a halo with pairs
+// that is not evaluated at its pixels).
 __global__ void k_hs_count(const HpHalo* __restrict__ halos, int64_t nh,
-                           const HsRing* __restrict__ R, int nr, uint32_t* counts) {
+                           const HsRing* __restrict__ R, int nr, uint32_t* counts,
+                           uint32_t* tflag) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nh) return;
   const HpHalo H = halos[k];
@@ -990,6 +993,7 @@ __global__ void k_hs_count(const HpHalo* __restrict__ halos, int64_t nh,
     }
   }
   counts[k] = c;
+  tflag[k] = (c > 0 && H.nt > 0) ? 1u : 0u;
 }
 
 // The geometry of one (segment, halo) pair: the halo's colatitude offset and longitude in
@@ -1133,8 +1137,8 @@ __global__ void __launch_bounds__(HS_SEG)
                const uint32_t* __restrict__ pvals, const int64_t* __restrict__ sstart,
                const HsRing* __restrict__ R, int nr, const uint32_t* __restrict__ p_halo,
                const int2* __restrict__ p_rg, const int64_t* __restrict__ voff,
-               const float2* __restrict__ dvals, float* ymap, float* bmap, float* ylo,
-               float* blo) {
+               const float2* __restrict__ dvals, const int64_t* __restrict__ toff, float* ymap,
+               float* bmap, float* ylo, float* blo) {
   __shared__ float s_dth2[HS_CH], s_sp[HS_CH], s_rh[HS_CH], s_rl[HS_CH], s_sa2[HS_CH];
   __shared__ float s_irf[HS_CH], s_ay[HS_CH], s_ab[HS_CH];
   __shared__ int2 s_rng[HS_CH];
@@ -1172,7 +1176,7 @@ __global__ void __launch_bounds__(HS_SEG)
         s_irf[tid] = H.inv_rf_px;
         s_ay[tid] = H.Ay;
         s_ab[tid] = H.Ab;
-        s_tab[tid] = tab + (int64_t)hk * 2 * HP_ROW;
+        s_tab[tid] = H.nt > 0 ? tab + toff[hk] * 2 * HP_ROW : tab;  // its table slot
       }
     }
     __syncthreads();
@@ -1511,42 +1515,49 @@ int bp_paste_halos_healpix(bp_ctx* ctx, int64_t n, const double* theta, const do
   for (int64_t h0 = 0; h0 < n; h0 += CHUNK) {
     const int64_t m = std::min(CHUNK, n - h0);
     HpHalo* halos;
-    float* tab;
     if ((r = bp_ws(ctx, WS_HPAR, (size_t)m * sizeof(HpHalo), (void**)&halos))) return r;
-    if ((r = bp_ws(ctx, WS_TABLE, (size_t)m * 2 * HP_ROW * sizeof(float), (void**)&tab))) return r;
     const unsigned nb = (unsigned)((m + 255) / 256);
+    const BpParams& P = ctx->p;
+    double rn = rint(P.n_poly);
+    int n_int = (fabs(P.n_poly - rn) < 1e-12 && rn >= 1 && rn <= 16) ? (int)rn : -1;
+    // halo records, pair counts, and the compact list of the halos that need a table
     bp_phase_begin(ctx, BP_PH_HP_TABLE);
     k_hs_prep<<<nb, 256, 0, ctx->stream>>>(ctx->p, n, h0, m, theta, phi, v_los, model, status,
                                            ap_r500, nside, halos);
     BP_LAUNCH_CHECK(ctx, "healpix prep");
-    const BpParams& P = ctx->p;
-    double rn = rint(P.n_poly);
-    int n_int = (fabs(P.n_poly - rn) < 1e-12 && rn >= 1 && rn <= 16) ? (int)rn : -1;
-    int64_t nt = m * (HP_NT + 1);
-    k_hp_table<<<(unsigned)((nt + 255) / 256), 256, 0, ctx->stream>>>(
-        halos, nullptr, m, (float)P.n_poly, n_int, (float)P.n_nt, tab);
-    BP_LAUNCH_CHECK(ctx, "healpix table");
-    k_hp_ghosts<<<nb, 256, 0, ctx->stream>>>(halos, nullptr, m, tab);
-    BP_LAUNCH_CHECK(ctx, "healpix ghosts");
-    bp_phase_end(ctx, BP_PH_HP_TABLE);
-    // (segment, halo) pairs sorted by segment
-    bp_phase_begin(ctx, BP_PH_HP_PAIRS);
     uint32_t* counts;
-    int64_t* offs;
-    if ((r = bp_ws(ctx, WS_COUNTS, (size_t)(m + 1) * 4, (void**)&counts))) return r;
-    if ((r = bp_ws(ctx, WS_OFFS, (size_t)(m + 1) * 8, (void**)&offs))) return r;
-    k_hs_count<<<nb, 256, 0, ctx->stream>>>(halos, m, R, nr, counts);
+    int64_t *offs, *toff;
+    if ((r = bp_ws(ctx, WS_COUNTS, (size_t)(m + 1) * 8, (void**)&counts))) return r;
+    if ((r = bp_ws(ctx, WS_OFFS, (size_t)(m + 1) * 16, (void**)&offs))) return r;
+    uint32_t* tflag = counts + (m + 1);
+    toff = offs + (m + 1);
+    uint32_t* tlist;
+    if ((r = bp_ws(ctx, WS_MISC2, (size_t)m * 4 + 16, (void**)&tlist))) return r;
+    k_hs_count<<<nb, 256, 0, ctx->stream>>>(halos, m, R, nr, counts, tflag);
     BP_LAUNCH_CHECK(ctx, "healpix count");
     if ((r = bp_scan_u32_to_i64(ctx, counts, offs, m))) return r;
+    if ((r = bp_scan_u32_to_i64(ctx, tflag, toff, m))) return r;
     BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned, offs + m, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 1, toff + m, 8, cudaMemcpyDeviceToHost,
+                                 ctx->stream));
+    k_hp_tab_emit<<<nb, 256, 0, ctx->stream>>>(tflag, toff, m, tlist);
+    BP_LAUNCH_CHECK(ctx, "healpix table list");
     BP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-    const int64_t np = ctx->h_pinned[0];
+    const int64_t np = ctx->h_pinned[0], n_table = ctx->h_pinned[1];
     if (np > (int64_t)UINT32_MAX)
       return bp_fail(ctx, BP_ERANGE, "bp_paste_halos_healpix: too many pairs");
     if (np == 0) {
-      bp_phase_end(ctx, BP_PH_HP_PAIRS);
+      bp_phase_end(ctx, BP_PH_HP_TABLE);
       continue;
     }
+    float* tab;
+    if ((r = bp_ws(ctx, WS_TABLE, (size_t)(n_table > 0 ? n_table : 1) * 2 * HP_ROW *
+                                      sizeof(float), (void**)&tab)))
+      return r;
+    if ((r = hp_tables(ctx, halos, tlist, n_table, tab))) return r;
+    bp_phase_end(ctx, BP_PH_HP_TABLE);
+    // (segment, halo) pairs sorted by segment
+    bp_phase_begin(ctx, BP_PH_HP_PAIRS);
     uint32_t *k0, *v0, *k1, *v1, *ks, *vs;
     if ((r = bp_ws(ctx, WS_KEYS0, (size_t)np * 4, (void**)&k0))) return r;
     if ((r = bp_ws(ctx, WS_VALS0, (size_t)np * 4, (void**)&v0))) return r;
@@ -1586,7 +1597,7 @@ int bp_paste_halos_healpix(bp_ctx* ctx, int64_t n, const double* theta, const do
     bp_phase_end(ctx, BP_PH_HP_PAIRS);
     bp_phase_begin(ctx, BP_PH_HP_PASTE);
     k_hs_paste<<<(unsigned)n_seg, HS_SEG, 0, ctx->stream>>>(
-        halos, tab, vs, sstart, R, nr, p_halo, p_rg, voff, dvals, ymap, bmap, ylo, blo);
+        halos, tab, vs, sstart, R, nr, p_halo, p_rg, voff, dvals, toff, ymap, bmap, ylo, blo);
     BP_LAUNCH_CHECK(ctx, "healpix paste");
     bp_phase_end(ctx, BP_PH_HP_PASTE);
   }
