@@ -312,6 +312,26 @@ int bp_assign_particles_phi(bp_ctx* ctx, int64_t n, const float* x, const float*
                             double Mp, int64_t n_halos, const float* halo_pos,
                             const double* model, const int32_t* status,
                             const bp_map_geom* geom, float* out);
+/* bp_assign_particles_phi in parts, so that the pair list can be built before the halos are
+ * solved (the record's geometry does not depend on the solve):
+ *   BP_ASSIGN_ALL: the whole record (bp_assign_particles_phi);
+ *   BP_ASSIGN_GEOMETRY: pixel coordinates, h in pixels and the kind from the halo id alone
+ *     (HALO for 0 <= halo_id < n_halos, FIELD below 0), Y = B = 0; halo_pos, model and status
+ *     are not read and may be NULL;
+ *   BP_ASSIGN_SIGNALS: Y, B and the kind only, into records the geometry part wrote; the
+ *     result is then the whole record of BP_ASSIGN_ALL, bit for bit.
+ * A pair list built from geometry records may hold halo particles that the signals part
+ * turns to BP_KIND_NONE (outside the truncation radius, or an unsolved halo): they deposit
+ * zeros.  Other arguments and errors as bp_assign_particles; unknown part: BP_EINVAL. */
+#define BP_ASSIGN_ALL 0
+#define BP_ASSIGN_GEOMETRY 1
+#define BP_ASSIGN_SIGNALS 2
+int bp_assign_particles_part(bp_ctx* ctx, int64_t n, const float* x, const float* y,
+                             const float* z, const float* vx, const float* vy, const float* vz,
+                             const float* phi, const float* hsml, const int32_t* halo_id,
+                             double Mp, int64_t n_halos, const float* halo_pos,
+                             const double* model, const int32_t* status,
+                             const bp_map_geom* geom, float* out, int part);
 
 /* Section 3.4: deposit assigned particles through the separable pixel-integrated
  * SPH kernel, f_ij = [w((x_i+ - x_p)/h) - w((x_i- - x_p)/h)] [same in y].
@@ -323,6 +343,20 @@ int bp_assign_particles_phi(bp_ctx* ctx, int64_t n, const float* x, const float*
  * compensated FP32 sums.  Synchronises once to size the pair list. */
 int bp_paste_particles(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_geom* geom,
                        int select, float* ymap, float* bmap, float* ylo, float* blo);
+
+/* bp_paste_particles in two calls.  bp_pp_prepare builds the sorted (tile, particle) list
+ * and the work units from the records' geometry (pixel coordinates, h, kind), in the
+ * context's scratch (synchronises, as bp_paste_particles); bp_pp_deposit then deposits the
+ * records' Y and B through it, which may have been written in between (by
+ * bp_assign_particles_part with BP_ASSIGN_SIGNALS).  The solve and the assign calls may run
+ * on the context in between; a call that reuses the scratch holding the list (a paste, a
+ * sort) is detected.  bp_pp_deposit needs the same records pointer, n, geometry and select
+ * as the last bp_pp_prepare, and the prepared list intact: otherwise BP_EINVAL.
+ * prepare + deposit == bp_paste_particles. */
+int bp_pp_prepare(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_geom* geom,
+                  int select);
+int bp_pp_deposit(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_geom* geom,
+                  int select, float* ymap, float* bmap, float* ylo, float* blo);
 
 /* bp_paste_particles for callers that cannot allocate device memory during a call:
  * applications that give their whole device memory to their own pool allocator at

@@ -21,6 +21,7 @@ MF = {n: i for i, n in enumerate(MODEL_FIELDS)}
 ASSIGNED_STRIDE = 8
 KIND_HALO, KIND_FIELD, KIND_NONE = 0, 1, 2
 SELECT_ALL, SELECT_HALO, SELECT_FIELD = 0, 1, 2
+ASSIGN_ALL, ASSIGN_GEOMETRY, ASSIGN_SIGNALS = 0, 1, 2
 OUT_YB, OUT_DT = 0, 1
 
 # entry points declared in include/bp.h
@@ -29,7 +30,8 @@ EXPORTS = ("bp_create", "bp_destroy", "bp_last_error", "bp_set_stream", "bp_set_
            "bp_workspace_bytes", "bp_set_timing", "bp_phase_times", "bp_kernel_launches",
            "bp_solve_halos", "bp_assign_particles", "bp_paste_particles", "bp_pp_pairs",
            "bp_smoothing_lengths", "bp_paste_halos_healpix", "bp_power_spectrum",
-           "bp_assign_particles_phi",
+           "bp_assign_particles_phi", "bp_assign_particles_part", "bp_pp_prepare",
+           "bp_pp_deposit",
            "bp_paste_halos", "bp_finalize_map", "bp_paste_particles_noalloc",
            "bp_solve_halos_ex", "bp_last_fallback_count", "bp_mlp_forward", "bp_mlp_backward",
            "bp_mlp_adam", "bp_mlp_to_bf16", "bp_mlp_infer_bf16", "bp_mlp_features",
@@ -101,7 +103,11 @@ def load():
                                               C.POINTER(BpGeom), P]),
                 "bp_assign_particles_phi": (i32, [P, i64, P, P, P, P, P, P, P, P, P, d, i64, P,
                                                   P, P, C.POINTER(BpGeom), P]),
+                "bp_assign_particles_part": (i32, [P, i64, P, P, P, P, P, P, P, P, P, d, i64,
+                                                   P, P, P, C.POINTER(BpGeom), P, i32]),
                 "bp_paste_particles": (i32, [P, i64, P, C.POINTER(BpGeom), i32, P, P, P, P]),
+                "bp_pp_prepare": (i32, [P, i64, P, C.POINTER(BpGeom), i32]),
+                "bp_pp_deposit": (i32, [P, i64, P, C.POINTER(BpGeom), i32, P, P, P, P]),
                 "bp_paste_particles_noalloc": (i32, [P, i64, P, C.POINTER(BpGeom), i32, P, P, P,
                                                      P]),
                 "bp_smoothing_lengths": (i32, [P, i64, P, P, P, d, P, P]),

@@ -12,11 +12,13 @@ import numpy as np
 import torch
 
 from . import _lib as L
-from ._lib import (ASSIGNED_STRIDE, KIND_FIELD, KIND_HALO, KIND_NONE, MF, MODEL_FIELDS,
-                   OUT_DT, OUT_YB, SELECT_ALL, SELECT_FIELD, SELECT_HALO, BpError)
+from ._lib import (ASSIGN_ALL, ASSIGN_GEOMETRY, ASSIGN_SIGNALS, ASSIGNED_STRIDE, KIND_FIELD,
+                   KIND_HALO, KIND_NONE, MF, MODEL_FIELDS, OUT_DT, OUT_YB, SELECT_ALL,
+                   SELECT_FIELD, SELECT_HALO, BpError)
 
 __all__ = ["Context", "Maps", "geom", "healpix_geom", "healpix_maps", "default_ell_edges", "MF", "MODEL_FIELDS", "ASSIGNED_STRIDE", "KIND_HALO",
-           "KIND_FIELD", "KIND_NONE", "SELECT_ALL", "SELECT_HALO", "SELECT_FIELD", "OUT_YB",
+           "KIND_FIELD", "KIND_NONE", "ASSIGN_ALL", "ASSIGN_GEOMETRY", "ASSIGN_SIGNALS",
+           "SELECT_ALL", "SELECT_HALO", "SELECT_FIELD", "OUT_YB",
            "OUT_DT", "BpError"]
 
 
@@ -259,10 +261,11 @@ class Context:
 
     # ------------------------------------------------------------ Section 3.4
     def assign_particles(self, parts: dict, Mp: float, halo_pos, model, status, g: L.BpGeom,
-                         out=None, phi=None):
+                         out=None, phi=None, part=None):
         """Per-particle signals.  parts: x,y,z,vx,vy,vz,hsml (FP32), hid (int32).  phi: optional
-        FP32 per-particle potential [(km/s)^2] (bp_assign_particles_phi).
-        Returns the [n, 8] FP32 record tensor."""
+        FP32 per-particle potential [(km/s)^2] (bp_assign_particles_phi).  part: None (the whole
+        record) or ASSIGN_GEOMETRY / ASSIGN_SIGNALS (bp_assign_particles_part; the geometry
+        part reads no halo model).  Returns the [n, 8] FP32 record tensor."""
         n = parts["x"].numel()
         f32 = torch.float32
         if out is None:
@@ -273,12 +276,31 @@ class Context:
                 float(Mp), nh, _ptr(halo_pos, f32, "halo_pos"),
                 _ptr(model, torch.float64, "model"), _ptr(status, torch.int32, "status"),
                 C.byref(g), _ptr(out, f32, "out")]
-        if phi is None:
+        if part is not None:
+            rc = self._L.bp_assign_particles_part(self._h, n, *xyzv, _ptr(phi, f32, "phi"),
+                                                  *tail, int(part))
+        elif phi is None:
             rc = self._L.bp_assign_particles(self._h, n, *xyzv, *tail)
         else:
             rc = self._L.bp_assign_particles_phi(self._h, n, *xyzv, _ptr(phi, f32, "phi"), *tail)
         self._check(rc)
         return out
+
+    def pp_prepare(self, assigned, g: L.BpGeom, select=SELECT_ALL):
+        """bp_pp_prepare: the sorted pair list and work units of the records' geometry."""
+        self._check(self._L.bp_pp_prepare(self._h, assigned.shape[0],
+                                          _ptr(assigned, torch.float32, "assigned"), C.byref(g),
+                                          int(select)))
+
+    def pp_deposit(self, assigned, g: L.BpGeom, maps: Maps, select=SELECT_ALL):
+        """bp_pp_deposit: the records' Y and B through the list of the last pp_prepare."""
+        f32 = torch.float32
+        rc = self._L.bp_pp_deposit(self._h, assigned.shape[0], _ptr(assigned, f32, "assigned"),
+                                   C.byref(g), int(select), _ptr(maps.y, f32, "y"),
+                                   _ptr(maps.b, f32, "b"), _ptr(maps.ylo, f32, "ylo"),
+                                   _ptr(maps.blo, f32, "blo"))
+        self._check(rc)
+        return maps
 
     def paste_particles(self, assigned, g: L.BpGeom, maps: Maps, select=SELECT_ALL):
         n = assigned.shape[0]

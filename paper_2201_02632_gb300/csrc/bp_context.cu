@@ -24,6 +24,7 @@ int bp_cuda_check(bp_ctx* ctx, cudaError_t e, const char* what) {
 
 // Grow-only scratch slot.  Frees the old block after synchronising the stream.
 int bp_ws(bp_ctx* ctx, int slot, size_t bytes, void** out) {
+  ++ctx->ws_gen[slot];
   if (bytes == 0) bytes = 16;
   if (ctx->ws_bytes[slot] < bytes) {
     if (ctx->ws[slot]) {

@@ -64,6 +64,22 @@ enum { WS_COUNTS = 0, WS_OFFS, WS_KEYS0, WS_VALS0, WS_KEYS1, WS_VALS1, WS_HIST, 
        WS_UNITS, WS_PART, WS_MISC, WS_TABLE, WS_HPAR, WS_MISC2, WS_MISC3, WS_HALO,
        WS_NSLOTS };
 
+// A particle work list built by bp_pp_prepare for bp_pp_deposit (in the context's scratch;
+// ws_gen records the generation of each slot it lives in, so that a deposit can tell
+// whether another call has reused them since).
+struct PpPrepared {
+  int valid;
+  const float* assigned;
+  int64_t n;
+  bp_map_geom g;
+  int select, ts, unit;
+  int64_t np, n_tiles, max_units, n_slots;
+  const uint32_t* vals;
+  int64_t *tstart, *uoff, *soff;
+  void* units;
+  uint64_t gen[WS_NSLOTS];
+};
+
 struct bp_ctx {
   BpParams p;
   BpTables t;
@@ -71,6 +87,8 @@ struct bp_ctx {
   void* table_mem;
   void* ws[WS_NSLOTS];
   size_t ws_bytes[WS_NSLOTS];
+  uint64_t ws_gen[WS_NSLOTS];  // calls of bp_ws per slot (every user of a slot asks for it)
+  PpPrepared pp_prep;
   int64_t* d_counter;  // small device scalars
   int* d_flags;
   int64_t* h_pinned;   // pinned host scalars

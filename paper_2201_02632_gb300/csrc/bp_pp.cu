@@ -14,6 +14,8 @@
 //                  written as partial tiles
 //  k_reduce_tiles  adds the partial tiles of multi-unit tiles in unit order
 // No global atomics touch the maps; every pixel sum is in a fixed order.
+#include <cstring>
+
 #include "bp_internal.cuh"
 
 namespace {
@@ -158,26 +160,39 @@ struct AssignArgs {
   float* out;
 };
 
+// MODE 0: the whole record.  MODE 1 (geometry, needs no solved halos): pixel coordinates and
+// h in pixels, Y = B = 0, and the kind from the halo id alone (a halo particle outside its
+// halo's truncation radius stays HALO, with zero signals later).  MODE 2 (signals): only Y,
+// B and the kind, the same values as MODE 0, into a record whose geometry MODE 1 wrote.
+template <int MODE>
 __global__ void __launch_bounds__(256) k_assign(AssignArgs a, BpTables T) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.n) return;
   float xf = a.x[i], yf = a.y[i], zf = a.z[i];
   // sky angles and pixel coordinates: double-float FP32 near the axis, else FP64
-  int ix, iy;
-  float fx, fy;
-  const float rz = 1.0f / zf;
-  if (!pixel_fast(xf, zf, rz, a.th0x_hi, a.th0x_lo, a.inv_hi, a.inv_lo, ix, fx))
-    fx = split_pixel((atan2((double)xf, (double)zf) - a.th0x) * a.inv_dth, ix);
-  if (!pixel_fast(yf, zf, rz, a.th0y_hi, a.th0y_lo, a.inv_hi, a.inv_lo, iy, fy))
-    fy = split_pixel((atan2((double)yf, (double)zf) - a.th0y) * a.inv_dth, iy);
+  int ix = 0, iy = 0;
+  float fx = 0.f, fy = 0.f;
+  if constexpr (MODE != 2) {
+    const float rz = 1.0f / zf;
+    if (!pixel_fast(xf, zf, rz, a.th0x_hi, a.th0x_lo, a.inv_hi, a.inv_lo, ix, fx))
+      fx = split_pixel((atan2((double)xf, (double)zf) - a.th0x) * a.inv_dth, ix);
+    if (!pixel_fast(yf, zf, rz, a.th0y_hi, a.th0y_lo, a.inv_hi, a.inv_lo, iy, fy))
+      fy = split_pixel((atan2((double)yf, (double)zf) - a.th0y) * a.inv_dth, iy);
+  }
   float r2 = xf * xf + yf * yf + zf * zf;
   float rh = sqrtf(r2);       // comoving h^-1 Mpc
   float chi = rh * a.inv_h;   // comoving Mpc
   float Y = 0.f, B = 0.f;
   int kind = BP_KIND_NONE;
   float hp = 0.f;
-  if (rh > 0.f) {
-    hp = a.hs[i] * a.inv_h_dth / chi;
+  if constexpr (MODE == 1) {
+    if (rh > 0.f) {
+      hp = a.hs[i] * a.inv_h_dth / chi;
+      const int32_t k = a.hid[i];
+      kind = k < 0 ? BP_KIND_FIELD : (k < a.nh ? BP_KIND_HALO : BP_KIND_NONE);
+    }
+  } else if (rh > 0.f) {
+    if constexpr (MODE == 0) hp = a.hs[i] * a.inv_h_dth / chi;
     float zz = bp_hermitef(T.z_c, T.dz_c, T.nc, T.dchi, T.inv_dchi, chi);
     float tau = bp_hermitef(T.tau_c, T.dtau_c, T.nc, T.dchi, T.inv_dchi, chi);
     float DA = chi / (1.0f + zz);
@@ -207,9 +222,15 @@ __global__ void __launch_bounds__(256) k_assign(AssignArgs a, BpTables T) {
       }
     }
   }
-  float4* o = reinterpret_cast<float4*>(a.out + i * BP_ASSIGNED_STRIDE);
-  o[0] = make_float4(fx, fy, hp, Y);
-  o[1] = make_float4(B, __int_as_float(kind), __int_as_float(ix), __int_as_float(iy));
+  if constexpr (MODE == 2) {
+    float* o = a.out + i * BP_ASSIGNED_STRIDE;
+    o[3] = Y;
+    *reinterpret_cast<float2*>(o + 4) = make_float2(B, __int_as_float(kind));
+  } else {
+    float4* o = reinterpret_cast<float4*>(a.out + i * BP_ASSIGNED_STRIDE);
+    o[0] = make_float4(fx, fy, hp, Y);
+    o[1] = make_float4(B, __int_as_float(kind), __int_as_float(ix), __int_as_float(iy));
+  }
 }
 
 // ---------------------------------------------------------------- pairs
@@ -634,11 +655,11 @@ int deposit_simt(bp_ctx* ctx, const float* assigned, const bp_map_geom* g, const
   return BP_OK;
 }
 
+// Work units of a sorted pair list (tile ranges, units, partial-tile slots), recorded in P
+// with the generations of the scratch slots they live in.  Synchronises once.
 template <int TS>
-int deposit(bp_ctx* ctx, const float* assigned, const bp_map_geom* g, const uint32_t* keys,
-            const uint32_t* vals, int64_t np, int64_t n_tiles, float* ymap, float* bmap,
-            float* ylo, float* blo) {
-  const int ntx = (g->nx + TS - 1) / TS;
+int prepare_units(bp_ctx* ctx, const uint32_t* keys, const uint32_t* vals, int64_t np,
+                  int64_t n_tiles, PpPrepared* P) {
   int r;
   // particles per work unit: the context's value, or (auto) about 16 units per
   // resident CTA, at least 2048
@@ -672,34 +693,67 @@ int deposit(bp_ctx* ctx, const float* assigned, const bp_map_geom* g, const uint
   BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 1, soff + n_tiles, 8, cudaMemcpyDeviceToHost,
                                ctx->stream));
   BP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
-  const int64_t n_slots = ctx->h_pinned[1];
+  P->ts = TS;
+  P->unit = unit;
+  P->np = np;
+  P->n_tiles = n_tiles;
+  P->max_units = max_units;
+  P->n_slots = ctx->h_pinned[1];
+  P->vals = vals;
+  P->tstart = tstart;
+  P->uoff = uoff;
+  P->soff = soff;
+  P->units = units;
+  for (int k = 0; k < WS_NSLOTS; ++k) P->gen[k] = ctx->ws_gen[k];
+  return BP_OK;
+}
+
+// The deposit and the fixed-order reduction of a prepared list.
+template <int TS>
+int launch_deposit(bp_ctx* ctx, const float* assigned, const bp_map_geom* g,
+                   const PpPrepared& P, float* ymap, float* bmap, float* ylo, float* blo) {
+  int r;
+  const int ntx = (g->nx + TS - 1) / TS;
   float* partials;
-  if ((r = bp_ws(ctx, WS_PART, (size_t)(n_slots > 0 ? n_slots : 1) * 4 * TS * TS * sizeof(float),
+  if ((r = bp_ws(ctx, WS_PART,
+                 (size_t)(P.n_slots > 0 ? P.n_slots : 1) * 4 * TS * TS * sizeof(float),
                  (void**)&partials)))
     return r;
+  const Unit* units = (const Unit*)P.units;
   BP_CUDA(ctx, cudaMemsetAsync(ctx->d_counter + 1, 0, sizeof(int64_t), ctx->stream));
-  bp_phase_end(ctx, BP_PH_SORT);
   const bool tc = bp_deposit_uses_tc(ctx, TS);
   if (tc) {
     bp_phase_begin(ctx, BP_PH_DEPOSIT);
-    if ((r = bp_deposit_tc_launch(ctx, assigned, vals, units, uoff + n_tiles, ctx->d_counter + 1,
-                                  max_units, g, ymap, bmap, ylo, blo, partials)))
+    if ((r = bp_deposit_tc_launch(ctx, assigned, P.vals, units, P.uoff + P.n_tiles,
+                                  ctx->d_counter + 1, P.max_units, g, ymap, bmap, ylo, blo,
+                                  partials)))
       return r;
     bp_phase_end(ctx, BP_PH_DEPOSIT);
   } else {
-    if ((r = deposit_simt<TS>(ctx, assigned, g, vals, units, uoff + n_tiles, ctx->d_counter + 1,
-                              max_units, ymap, bmap, ylo, blo, partials)))
+    if ((r = deposit_simt<TS>(ctx, assigned, g, P.vals, units, P.uoff + P.n_tiles,
+                              ctx->d_counter + 1, P.max_units, ymap, bmap, ylo, blo, partials)))
       return r;
   }
   bp_phase_begin(ctx, BP_PH_REDUCE);
-  if (n_slots > 0) {
-    k_reduce_tiles<TS><<<dim3((unsigned)n_tiles, REDUCE_SPLIT), 256, 0, ctx->stream>>>(
-        tstart, soff, n_tiles, unit, g->nx, g->ny, ntx, partials, ymap, bmap, ylo, blo);
+  if (P.n_slots > 0) {
+    k_reduce_tiles<TS><<<dim3((unsigned)P.n_tiles, REDUCE_SPLIT), 256, 0, ctx->stream>>>(
+        P.tstart, P.soff, P.n_tiles, P.unit, g->nx, g->ny, ntx, partials, ymap, bmap, ylo, blo);
     BP_LAUNCH_CHECK(ctx, "reduce tiles");
   }
   bp_phase_end(ctx, BP_PH_REDUCE);
   if (tc) return bp_deposit_tc_check(ctx);
   return BP_OK;
+}
+
+template <int TS>
+int deposit(bp_ctx* ctx, const float* assigned, const bp_map_geom* g, const uint32_t* keys,
+            const uint32_t* vals, int64_t np, int64_t n_tiles, float* ymap, float* bmap,
+            float* ylo, float* blo) {
+  PpPrepared P;
+  int r = prepare_units<TS>(ctx, keys, vals, np, n_tiles, &P);
+  if (r) return r;
+  bp_phase_end(ctx, BP_PH_SORT);
+  return launch_deposit<TS>(ctx, assigned, g, P, ymap, bmap, ylo, blo);
 }
 
 int halo_blocks(bp_ctx* ctx, int64_t nh, const double* model, const int32_t* status, double Mp,
@@ -808,22 +862,36 @@ int bp_assign_particles_phi(bp_ctx* ctx, int64_t n, const float* x, const float*
                             double Mp, int64_t n_halos, const float* halo_pos,
                             const double* model, const int32_t* status,
                             const bp_map_geom* geom, float* out) {
+  return bp_assign_particles_part(ctx, n, x, y, z, vx, vy, vz, phi, hsml, halo_id, Mp, n_halos,
+                                  halo_pos, model, status, geom, out, BP_ASSIGN_ALL);
+}
+
+int bp_assign_particles_part(bp_ctx* ctx, int64_t n, const float* x, const float* y,
+                             const float* z, const float* vx, const float* vy, const float* vz,
+                             const float* phi, const float* hsml, const int32_t* halo_id,
+                             double Mp, int64_t n_halos, const float* halo_pos,
+                             const double* model, const int32_t* status,
+                             const bp_map_geom* geom, float* out, int part) {
   if (!ctx) return BP_EINVAL;
   if (n < 0 || n_halos < 0) return bp_fail(ctx, BP_EINVAL, "bp_assign_particles: negative size");
+  if (part != BP_ASSIGN_ALL && part != BP_ASSIGN_GEOMETRY && part != BP_ASSIGN_SIGNALS)
+    return bp_fail(ctx, BP_EINVAL, "bp_assign_particles: unknown part");
   int r = check_geom(ctx, geom, "bp_assign_particles");
   if (r) return r;
   if (n == 0) return BP_OK;
   if (!x || !y || !z || !vx || !vy || !vz || !hsml || !halo_id || !out)
     return bp_fail(ctx, BP_EINVAL, "bp_assign_particles: null pointer");
-  if (n_halos > 0 && (!halo_pos || !model || !status))
+  if (part != BP_ASSIGN_GEOMETRY && n_halos > 0 && (!halo_pos || !model || !status))
     return bp_fail(ctx, BP_EINVAL, "bp_assign_particles: null halo arrays");
   if (!(Mp > 0)) return bp_fail(ctx, BP_EINVAL, "bp_assign_particles: Mp <= 0");
   if (((uintptr_t)out & 15) != 0)
     return bp_fail(ctx, BP_EINVAL, "bp_assign_particles: out must be 16-byte aligned");
   const BpParams& P = ctx->p;
-  float* blk;
+  float* blk = nullptr;
   bp_phase_begin(ctx, BP_PH_ASSIGN);
-  if ((r = halo_blocks(ctx, n_halos, model, status, Mp / P.h, &blk))) return r;
+  if (part != BP_ASSIGN_GEOMETRY &&
+      (r = halo_blocks(ctx, n_halos, model, status, Mp / P.h, &blk)))
+    return r;
   AssignArgs a;
   a.x = x; a.y = y; a.z = z; a.vx = vx; a.vy = vy; a.vz = vz; a.hs = hsml;
   a.phi = phi;
@@ -851,7 +919,13 @@ int bp_assign_particles_phi(bp_ctx* ctx, int64_t n, const float* x, const float*
   a.n_int = (fabs(P.n_poly - rn) < 1e-12 && rn >= 1 && rn <= 16) ? (int)rn : -1;
   a.n_nt = (float)P.n_nt;
   a.out = out;
-  k_assign<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(a, ctx->t);
+  const unsigned nb = (unsigned)((n + 255) / 256);
+  if (part == BP_ASSIGN_GEOMETRY)
+    k_assign<1><<<nb, 256, 0, ctx->stream>>>(a, ctx->t);
+  else if (part == BP_ASSIGN_SIGNALS)
+    k_assign<2><<<nb, 256, 0, ctx->stream>>>(a, ctx->t);
+  else
+    k_assign<0><<<nb, 256, 0, ctx->stream>>>(a, ctx->t);
   BP_LAUNCH_CHECK(ctx, "assign");
   bp_phase_end(ctx, BP_PH_ASSIGN);
   return BP_OK;
@@ -880,6 +954,63 @@ int bp_paste_particles(bp_ctx* ctx, int64_t n, const float* assigned, const bp_m
   if (np == 0) return BP_OK;
   if (ts == 64) return deposit<64>(ctx, assigned, geom, keys, vals, np, n_tiles, ymap, bmap, ylo, blo);
   return deposit<32>(ctx, assigned, geom, keys, vals, np, n_tiles, ymap, bmap, ylo, blo);
+}
+
+int bp_pp_prepare(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_geom* geom,
+                  int select) {
+  if (!ctx) return BP_EINVAL;
+  ctx->pp_prep.valid = 0;
+  int r = check_geom(ctx, geom, "bp_pp_prepare");
+  if (r) return r;
+  if (geom->n_maps != 1) return bp_fail(ctx, BP_EINVAL, "bp_pp_prepare: n_maps must be 1");
+  if (n < 0) return bp_fail(ctx, BP_EINVAL, "bp_pp_prepare: n < 0");
+  if (n > (int64_t)UINT32_MAX) return bp_fail(ctx, BP_ERANGE, "bp_pp_prepare: n >= 2^32");
+  if (select < 0 || select > 2) return bp_fail(ctx, BP_EINVAL, "bp_pp_prepare: select");
+  if (n > 0 && !assigned) return bp_fail(ctx, BP_EINVAL, "bp_pp_prepare: null records");
+  if (((uintptr_t)assigned & 15) != 0)
+    return bp_fail(ctx, BP_EINVAL, "bp_pp_prepare: records must be 16-byte aligned");
+  const int ts = ctx->pp_tile;
+  if (ctx->pp_kernel == BP_DEPOSIT_TENSOR && ts != 64)
+    return bp_fail(ctx, BP_EINVAL, "bp_pp_prepare: the tensor-core deposit needs tile 64");
+  PpPrepared& P = ctx->pp_prep;
+  P.assigned = assigned;
+  P.n = n;
+  P.g = *geom;
+  P.select = select;
+  P.ts = ts;
+  P.np = 0;
+  if (n > 0) {
+    uint32_t *keys, *vals;
+    int64_t np, n_tiles;
+    if ((r = build_pairs(ctx, n, assigned, geom, select, ts, &keys, &vals, &np, &n_tiles)))
+      return r;
+    if (np > 0) {
+      r = ts == 64 ? prepare_units<64>(ctx, keys, vals, np, n_tiles, &P)
+                   : prepare_units<32>(ctx, keys, vals, np, n_tiles, &P);
+      if (r) return r;
+    }
+    bp_phase_end(ctx, BP_PH_SORT);
+  }
+  P.valid = 1;
+  return BP_OK;
+}
+
+int bp_pp_deposit(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_geom* geom,
+                  int select, float* ymap, float* bmap, float* ylo, float* blo) {
+  if (!ctx) return BP_EINVAL;
+  const PpPrepared& P = ctx->pp_prep;
+  if (!P.valid || P.assigned != assigned || P.n != n || !geom || P.select != select ||
+      P.ts != ctx->pp_tile || memcmp(&P.g, geom, sizeof(bp_map_geom)) != 0)
+    return bp_fail(ctx, BP_EINVAL, "bp_pp_deposit: no bp_pp_prepare of these records");
+  if (P.np == 0 || n == 0) return BP_OK;
+  for (int k : {(int)WS_KEYS0, (int)WS_VALS0, (int)WS_KEYS1, (int)WS_VALS1, (int)WS_TILES,
+                (int)WS_UNITS})
+    if (ctx->ws_gen[k] != P.gen[k])
+      return bp_fail(ctx, BP_EINVAL, "bp_pp_deposit: the prepared list was overwritten");
+  if (!ymap || !bmap || !ylo || !blo)
+    return bp_fail(ctx, BP_EINVAL, "bp_pp_deposit: null pointer");
+  return P.ts == 64 ? launch_deposit<64>(ctx, assigned, geom, P, ymap, bmap, ylo, blo)
+                    : launch_deposit<32>(ctx, assigned, geom, P, ymap, bmap, ylo, blo);
 }
 
 int bp_pp_pairs(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_geom* geom,

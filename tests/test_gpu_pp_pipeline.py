@@ -147,3 +147,46 @@ def test_potential_variant_matches_oracle(orc, api, ctx, cone, oracle_side):
     yo, bo = orc.pp_deposit(a, orc_geom(orc, lc.geom))
     assert_map_parity(y[0], yo, what="y (potential-based)")
     assert_map_parity(b[0], bo, what="b (potential-based)")
+
+
+def test_assign_in_parts_and_prepared_deposit(api, ctx, cone):
+    """bp_assign_particles_part and bp_pp_prepare / bp_pp_deposit: the geometry part, the pair
+    list built from it before the solve, then the signals part and the deposit give the
+    records of the one-pass assign bit for bit and the maps of bp_paste_particles."""
+    lc = cone
+    rec_all, g = _gpu_assign(api, ctx, lc)
+    maps_all = api.Maps.zeros(g)
+    ctx.paste_particles(rec_all, g, maps_all)
+    tp = {k: cuda(v) for k, v in lc.parts.items()}
+    pos = cuda(lc.halos.pos)
+    rec = torch.full_like(rec_all, float("nan"))
+    ctx.assign_particles(tp, lc.Mp, pos, None, None, g, out=rec, part=api.ASSIGN_GEOMETRY)
+    geo = rec.clone()
+    assert float(geo[:, 3].abs().sum()) == 0.0 and float(geo[:, 4].abs().sum()) == 0.0
+    ctx.pp_prepare(rec, g)
+    model, status = ctx.solve_halos(cuda(lc.halos.M), cuda(lc.halos.c), cuda(lc.halos.z))
+    ctx.assign_particles(tp, lc.Mp, pos, model, status, g, out=rec, part=api.ASSIGN_SIGNALS)
+    a, b = rec.cpu().numpy().view(np.uint32), rec_all.cpu().numpy().view(np.uint32)
+    assert np.array_equal(a, b)
+    maps = api.Maps.zeros(g)
+    ctx.pp_deposit(rec, g, maps)
+    y, bb = folded(maps)
+    y0, b0 = folded(maps_all)
+    # the list may hold halo particles the signals part turned to NONE (zero signals), so
+    # the tensor-core groups can differ: rounding of the FP32 group sums only
+    assert np.linalg.norm(y - y0) <= 1e-6 * np.linalg.norm(y0)
+    assert np.linalg.norm(bb - b0) <= 1e-6 * np.linalg.norm(b0)
+    # misuse is refused: another select, or a list overwritten by another call
+    with pytest.raises(api.BpError) as err:
+        ctx.pp_deposit(rec, g, maps, select=api.SELECT_HALO)
+    assert "BP_EINVAL" in str(err.value)
+    ctx.pp_prepare(rec, g)
+    hp = api.Maps.zeros(g)
+    cat = lc.halos
+    ctx.paste_halos(cuda(cat.thx), cuda(cat.thy), cuda(cat.vlos), model, status, g, hp)
+    with pytest.raises(api.BpError) as err:
+        ctx.pp_deposit(rec, g, maps)
+    assert "BP_EINVAL" in str(err.value)
+    with pytest.raises(api.BpError) as err:
+        api.Context().pp_deposit(rec, g, maps)
+    assert "BP_EINVAL" in str(err.value)
