@@ -140,14 +140,16 @@ enum {
 #define BP_SOLVE_FP64_SEEDED 1 /* bp_solve_halos_ex only: the guess starts the FP32 pre-solve */
 
 #define BP_OUT_YB 0     /* maps hold y and b */
-#define BP_OUT_DT 1     /* maps hold Delta T / T_CMB: g_nu(x) y and -b */
+#define BP_OUT_DT 1     /* maps hold Delta T / T_CMB: g_nu(x) y and -b, with
+                         * g_nu(x) = x (e^x + 1)/(e^x - 1) - 4 (Section 3.2) */
 
 typedef struct bp_ctx bp_ctx;
 
 /* Create a context on the current CUDA device.  stream: a cudaStream_t (NULL = the
  * legacy default stream).  Builds the background tables (chi(z), tau(z), z(chi)) on
- * the host in FP64 and uploads them (synchronous).  Returns BP_EINVAL for
- * non-physical parameters. */
+ * the host in FP64 and uploads them (synchronous); also loads the device array and the
+ * kernels of bp_paste_particles_noalloc on this device (once per device).  Returns
+ * BP_EINVAL for non-physical parameters. */
 int bp_create(bp_ctx** ctx, const bp_cosmology* cosmo, const bp_icm_params* icm, void* stream);
 /* Free the context and its scratch (synchronises its stream). */
 int bp_destroy(bp_ctx* ctx);
@@ -362,20 +364,23 @@ int bp_pp_deposit(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_ge
  * applications that give their whole device memory to their own pool allocator at
  * start-up, and latency-critical loops in which cudaMalloc/cudaFree would
  * synchronise the device.  (The paper has no counterpart: this is a service of the
- * library.)  Same arguments, results and host synchronisation as bp_paste_particles,
- * but all scratch lives in one fixed device array inside the library (about 23 MB,
- * held on every device that loads the library until the process exits) and each
+ * library.)  Same arguments, results and host synchronisation as bp_paste_particles
+ * (the call waits once on the context's stream, to read back the pair count), but all
+ * scratch lives in one fixed device array inside the library (about 23 MB) and each
  * tile is deposited by a single CTA.  It calls no cudaMalloc, cudaFree or other
- * allocating routine.  Limits: n <= BP_NOALLOC_MAX_PARTICLES particles, at most
- * BP_NOALLOC_MAX_PAIRS (tile, particle) pairs and BP_NOALLOC_MAX_TILES tiles of the
- * context's deposit tile size; beyond them it returns BP_ERANGE with a message (the
- * pair count is known only after the pair-count pass, so that check comes after the
- * one host synchronisation, before anything is written to the maps).
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.  Every call
- * reuses the same array, which keeps the previous call's contents: calls whose work
- * overlaps on the GPU (other streams, other host threads) race and must not be issued
- * concurrently. */
+ * allocating routine.  CUDA loads a library's device code and arrays lazily, and that
+ * load takes device memory, so bp_create does it: creating a context brings the array
+ * into being on the context's device (held there until the process exits) and loads
+ * every kernel this call launches.  Create the context before reserving the device
+ * memory, and make the call on the context's device.  Limits: n <=
+ * BP_NOALLOC_MAX_PARTICLES particles, at most BP_NOALLOC_MAX_PAIRS (tile, particle)
+ * pairs and BP_NOALLOC_MAX_TILES tiles of the context's deposit tile size; beyond them
+ * it returns BP_ERANGE with a message and leaves the maps as they were (the pair count
+ * is known only after the pair-count pass, so that check comes after the host
+ * synchronisation, before anything is written to the maps).  Every call reuses the same
+ * array, which keeps the previous call's contents: calls whose work overlaps on the GPU
+ * (other streams, other host threads, other contexts of the device) race and must not be
+ * issued concurrently. */
 #define BP_NOALLOC_MAX_PARTICLES (1 << 19)
 #define BP_NOALLOC_MAX_PAIRS (1 << 20)
 #define BP_NOALLOC_MAX_TILES 4096
@@ -415,6 +420,19 @@ int bp_paste_halos(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_
                    const float* v_los, const int32_t* map_id, const double* model,
                    const int32_t* status, const bp_map_geom* geom, double ap_r500, float* ymap,
                    float* bmap, float* ylo, float* blo);
+
+/* The (map, tile, halo) work list of bp_paste_halos (Section 3.3: the pixel centres a halo
+ * can reach lie in the FP64 bounding box floor(c - r_ap) .. floor(c + r_ap) of its aperture
+ * disc, c the centre in pixel-centre index units, r_ap in pixels; a halo adds to every tile
+ * that box touches).  Arguments as bp_paste_halos (v_los is not needed); tile: 32 or 64.
+ * keys: (map_id * nty + ty) * ntx + tx, vals: halo indices, ordered by key then index, into
+ * caller device arrays of `capacity` entries; n_pairs (host pointer) receives the count.
+ * Halos whose status is not OK, or whose map_id is outside [0, n_maps), have no pairs.
+ * BP_ERANGE if capacity is too small (nothing written).  For tests; synchronises. */
+int bp_hp_pairs(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_y,
+                const int32_t* map_id, const double* model, const int32_t* status,
+                const bp_map_geom* geom, double ap_r500, int tile, uint32_t* keys, uint32_t* vals,
+                int64_t capacity, int64_t* n_pairs);
 
 /* All-sky maps (Section 5.2) by the HP of Section 3.3 (Eqs. y^HP, b^HP) on the HEALPix
  * sphere of Gorski et al. (2005), RING ordering: npix = 12 nside^2 equal-area pixels, pixel p

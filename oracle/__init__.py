@@ -120,6 +120,7 @@ def lib():
                 "orc_pp_deposit_pixels": (None, [i64, P, P, P, P, P, P, pg, i32, i64, P, P, P,
                                                  P, i32]),
                 "orc_pp_pairs": (i64, [i64, P, P, P, P, P, P, i32, i32, i32, i32, i32, P, P]),
+                "orc_g_nu": (d, [d, d]),
                 "orc_hp_pairs": (i64, [i64, P, P, P, P, pg, d, i32, i32, P, P]),
                 "orc_energy_residual": (d, [pc, pi, d, d, d, d]),
                 "orc_pp_select": (i64, [pc, i64, P, P, P, P, pg, i64, P, P, P, i32]),
@@ -272,6 +273,18 @@ def hp_sky(h_theta, h_phi, vlos, models, p_theta, p_phi, ap_r500=0.0, rtol=1e-9,
                      _p(h_theta), _p(h_phi), _p(vlos), _p(models), float(ap_r500), float(rtol),
                      p_theta.size, _p(p_theta), _p(p_phi), _p(yv), _p(bv), int(nthreads))
     return yv, bv
+
+
+def g_nu(nu_ghz, cp=None):
+    """Section 3.2: the tSZ frequency factor g(x), x = h nu / (k_B T_CMB)."""
+    return lib().orc_g_nu(float(nu_ghz), float((cp or cosmo_default()).Tcmb))
+
+
+def delta_t(y, b, nu_ghz, cp=None):
+    """Section 3.2: Delta T / T_CMB maps from y and b maps (FP64): g(x) y (tSZ) and -b
+    (kSZ)."""
+    g = g_nu(nu_ghz, cp)
+    return g * np.asarray(y, np.float64), -np.asarray(b, np.float64)
 
 
 def hp_pairs(thx, thy, models, g: Geom, ap_r500, tw, th, map_id=None):

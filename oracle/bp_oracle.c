@@ -41,6 +41,8 @@ static const double O_MPC_M = 3.0856775814913673e22;  /* m */
 static const double O_SIGMA_T = 6.6524587321e-29;     /* m^2 */
 static const double O_ME_C2_J = 8.1871057769e-14;     /* 510.99895 keV in J */
 static const double O_MP_KG = 1.67262192369e-27;      /* kg */
+static const double O_H_PLANCK = 6.62607015e-34;       /* J s (exact, SI 2019) */
+static const double O_K_B = 1.380649e-23;              /* J/K (exact, SI 2019) */
 
 static double o_G(void) { /* Mpc (km/s)^2 / Msun */
   return O_G_SI * O_MSUN_KG / (O_MPC_M * 1.0e6);
@@ -664,6 +666,17 @@ static double o_CN(const orc_cosmo* cp) {
 }
 double orc_const_CP(void) { return o_CP(); }
 double orc_const_CN(const orc_cosmo* cp) { return o_CN(cp); }
+
+/* Section 3.2: frequency factor of the tSZ temperature change, Delta T / T_CMB = g(x) y
+ * with x = h nu / (k_B T_CMB).  Reading of the printed factor: it shows the ratio
+ * (e^x - 1)/(e^x + 1), whose Rayleigh-Jeans limit would be -4; the non-relativistic
+ * Kompaneets solution that the section invokes gives the inverse ratio,
+ * g(x) = x (e^x + 1)/(e^x - 1) - 4 = x coth(x/2) - 4 (-2 as x -> 0, null near 217 GHz),
+ * which is used here. */
+double orc_g_nu(double nu_ghz, double Tcmb) {
+  double x = O_H_PLANCK * (nu_ghz * 1.0e9) / (O_K_B * Tcmb);
+  return x / tanh(0.5 * x) - 4.0;
+}
 
 /* ------------------------------------------------------------------ */
 /* Halo-based pasting (Section 3.3, Eqs. y^HP and b^HP).                */

@@ -32,7 +32,7 @@ EXPORTS = ("bp_create", "bp_destroy", "bp_last_error", "bp_set_stream", "bp_set_
            "bp_smoothing_lengths", "bp_paste_halos_healpix", "bp_power_spectrum",
            "bp_assign_particles_phi", "bp_assign_particles_part", "bp_pp_prepare",
            "bp_pp_deposit",
-           "bp_paste_halos", "bp_finalize_map", "bp_paste_particles_noalloc",
+           "bp_paste_halos", "bp_hp_pairs", "bp_finalize_map", "bp_paste_particles_noalloc",
            "bp_solve_halos_ex", "bp_last_fallback_count", "bp_mlp_forward", "bp_mlp_backward",
            "bp_mlp_adam", "bp_mlp_to_bf16", "bp_mlp_infer_bf16", "bp_mlp_features",
            "bp_mlp_targets", "bp_mlp_mse", "bp_solve_halos_surrogate", "bp_hp_plan_create",
@@ -117,6 +117,8 @@ def load():
                                       C.POINTER(i64)]),
                 "bp_paste_halos": (i32, [P, i64, P, P, P, P, P, P, C.POINTER(BpGeom), d, P, P, P,
                                          P]),
+                "bp_hp_pairs": (i32, [P, i64, P, P, P, P, P, C.POINTER(BpGeom), d, i32, P, P, i64,
+                                      C.POINTER(i64)]),
                 "bp_finalize_map": (i32, [P, C.POINTER(BpGeom), P, P, P, P, i32, d]),
                 "bp_hp_plan_create": (i32, [P, i64, P, P, P, P, P, C.POINTER(BpGeom), d, i32, i32,
                                             i32, C.POINTER(P)]),

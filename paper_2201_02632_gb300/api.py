@@ -363,6 +363,32 @@ class Context:
         self._check(rc)
         return maps
 
+    def hp_pairs(self, thx, thy, model, status, g: L.BpGeom, tile: int, ap_r500=0.0,
+                 map_id=None):
+        """Sorted ((map, tile) key, halo index) pairs of the halo paste (uint32 as int32)."""
+        n = thx.numel()
+        dev = thx.device
+        cnt = C.c_int64(0)
+
+        def call(cap):
+            keys = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+            vals = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+            rc = self._L.bp_hp_pairs(self._h, n, _ptr(thx, torch.float64, "thx"),
+                                     _ptr(thy, torch.float64, "thy"),
+                                     _ptr(map_id, torch.int32, "map_id"),
+                                     _ptr(model, torch.float64, "model"),
+                                     _ptr(status, torch.int32, "status"), C.byref(g),
+                                     float(ap_r500), int(tile), _ptr(keys, torch.int32, "k"),
+                                     _ptr(vals, torch.int32, "v"), cap, C.byref(cnt))
+            return rc, keys, vals
+
+        rc, keys, vals = call(1)
+        if rc == L.BP_ERANGE:
+            rc, keys, vals = call(int(cnt.value))
+        self._check(rc)
+        m = int(cnt.value)
+        return keys[:m], vals[:m]
+
     def paste_halos_healpix(self, theta, phi, vlos, model, status, nside, maps: Maps,
                             ap_r500=0.0):
         """All-sky HP on HEALPix (RING order); maps from healpix_maps(nside)."""

@@ -232,6 +232,9 @@ int bp_create(bp_ctx** out, const bp_cosmology* cosmo, const bp_icm_params* icm,
     cudaError_t e3 = cudaMallocHost(&ctx->h_pinned, 64 * sizeof(int64_t));
     if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
       r = bp_fail(nullptr, BP_ECUDA, "bp_create: scalar buffers");
+    // the allocation-free paste's device array and kernels, loaded now (bp_noalloc.cu)
+    if (r == BP_OK && (r = bp_noalloc_setup(ctx)) != BP_OK)
+      snprintf(g_tls_msg, sizeof(g_tls_msg), "%s", ctx->msg);
   } else {
     snprintf(g_tls_msg, sizeof(g_tls_msg), "%s", ctx->msg);
   }

@@ -430,3 +430,11 @@ int bp_deposit_tc_check(bp_ctx* ctx) {
   if (*h) return bp_fail(ctx, BP_ETIMEOUT, "deposit: a tensor-core wait timed out");
   return BP_OK;
 }
+
+// Loads the tensor-core deposit kernel (CUDA loads modules lazily: its first launch would
+// otherwise load its code into device memory).
+int bp_deposit_tc_preload(bp_ctx* ctx) {
+  cudaFuncAttributes a;
+  BP_CUDA(ctx, cudaFuncGetAttributes(&a, k_deposit_tc));
+  return BP_OK;
+}

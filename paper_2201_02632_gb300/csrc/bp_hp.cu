@@ -616,6 +616,7 @@ __global__ void k_finalize(int64_t npix, float* map, float* lo, float scale) {
 struct HpList {
   int64_t np = 0, n_tiles = 0, n_units = 0, n_slots = 0;
   int64_t nh = 0, nval = 0;        // halos; values of the halos evaluated at their pixels
+  const uint32_t* keys = nullptr;  // (map, tile) keys, sorted
   const uint32_t* vals = nullptr;  // halo indices sorted by (map, tile), then index
   int64_t* hvoff = nullptr;        // [nh + 1]: first value of each halo (nt = 0 halos)
   HpDBox* dbox = nullptr;          // [nh]: the box of each of those halos
@@ -733,6 +734,7 @@ int hp_build_list(bp_ctx* ctx, int64_t n, const HpHalo* halos, const bp_map_geom
   int key_bits = 0;
   while (((int64_t)1 << key_bits) < n_tiles) ++key_bits;
   if ((r = bp_radix_sort_pairs(ctx, k0, v0, k1, v1, np, key_bits, &ks, &vs))) return r;
+  L->keys = ks;
   L->vals = vs;
   int64_t* tstart;
   if ((r = bp_ws(ctx, WS_TILES, (size_t)(n_tiles + 1) * 32 + 64, (void**)&tstart))) return r;
@@ -1324,6 +1326,37 @@ int bp_paste_halos(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_
                                ymap, bmap, ylo, blo);
   bp_phase_end(ctx, BP_PH_HP_PASTE);
   return r;
+}
+
+int bp_hp_pairs(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_y,
+                const int32_t* map_id, const double* model, const int32_t* status,
+                const bp_map_geom* geom, double ap_r500, int tile, uint32_t* keys, uint32_t* vals,
+                int64_t capacity, int64_t* n_pairs) {
+  if (!ctx) return BP_EINVAL;
+  if (!n_pairs) return bp_fail(ctx, BP_EINVAL, "bp_hp_pairs: null count");
+  *n_pairs = 0;
+  int r = check_hp_args(ctx, n, th_x, th_y, model, status, geom, ap_r500, "bp_hp_pairs");
+  if (r) return r;
+  if (tile != 32 && tile != 64) return bp_fail(ctx, BP_EINVAL, "bp_hp_pairs: tile must be 32 or 64");
+  if (n == 0) return BP_OK;
+  HpHalo* halos;
+  if ((r = bp_ws(ctx, WS_HPAR, (size_t)n * sizeof(HpHalo), (void**)&halos))) return r;
+  // the records and the work list of bp_paste_halos (v_los only enters the amplitudes)
+  if ((r = hp_prep(ctx, n, th_x, th_y, nullptr, map_id, model, status, geom, ap_r500, halos)))
+    return r;
+  HpList L;
+  if ((r = hp_build_list(ctx, n, halos, geom, tile, ctx->hp_unit, &L))) return r;
+  *n_pairs = L.np;
+  if (L.np > capacity)
+    return bp_fail(ctx, BP_ERANGE, "bp_hp_pairs: capacity %lld < %lld", (long long)capacity,
+                   (long long)L.np);
+  if (L.np > 0) {
+    if (!keys || !vals) return bp_fail(ctx, BP_EINVAL, "bp_hp_pairs: null output");
+    BP_CUDA(ctx, cudaMemcpyAsync(keys, L.keys, L.np * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+    BP_CUDA(ctx, cudaMemcpyAsync(vals, L.vals, L.np * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+  }
+  BP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  return BP_OK;
 }
 
 int bp_hp_plan_create(bp_ctx* ctx, int64_t n, const double* th_x, const double* th_y,

@@ -284,5 +284,11 @@ int bp_deposit_tc_launch(bp_ctx* ctx, const float* assigned, const uint32_t* val
                          int64_t max_units, const bp_map_geom* g, float* ymap, float* bmap,
                          float* ylo, float* blo, float* partials);
 int bp_deposit_tc_check(bp_ctx* ctx);
+// Kernels loaded ahead of their first launch (cudaFuncGetAttributes), and the allocation-free
+// paste's device array resolved, when a context is created (bp_noalloc.cu)
+int bp_pp_preload(bp_ctx* ctx);
+int bp_sort_preload(bp_ctx* ctx);
+int bp_deposit_tc_preload(bp_ctx* ctx);
+int bp_noalloc_setup(bp_ctx* ctx);
 // true when the deposit of a paste with tile ts runs on the tensor cores
 bool bp_deposit_uses_tc(const bp_ctx* ctx, int ts);

@@ -8,8 +8,11 @@
 // runs the same pair list, radix sort and tiled deposit kernels as
 // bp_paste_particles, with all of its scratch in the fixed file-scope device array
 // below instead of the context's grow-on-demand buffers, and with one work unit per
-// tile (no partial tiles).  The array is allocated when the library is loaded on a
-// device and held until the process exits.
+// tile (no partial tiles).  CUDA loads a library's device code and arrays lazily, at their
+// first use, and that load takes device memory; so bp_create does the set-up here
+// (bp_noalloc_setup): it resolves the array's device address, which brings the array into
+// being on the context's device, and loads every kernel this paste launches.  The array is
+// then held until the process exits, and a later call allocates nothing.
 #include <mutex>
 
 #include "bp_internal.cuh"
@@ -71,6 +74,21 @@ int scratch_address(bp_ctx* ctx, unsigned char** out) {
 }
 
 }  // namespace
+
+// Called by bp_create with the context's device current: the array's address and the kernels
+// of the paste, so that bp_paste_particles_noalloc itself loads nothing.  A device id the
+// table cannot hold is left to the paste call, which reports it.
+int bp_noalloc_setup(bp_ctx* ctx) {
+  int dev = 0;
+  BP_CUDA(ctx, cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return BP_OK;
+  unsigned char* base = nullptr;
+  int r;
+  if ((r = scratch_address(ctx, &base))) return r;
+  if ((r = bp_pp_preload(ctx))) return r;
+  if ((r = bp_sort_preload(ctx))) return r;
+  return bp_deposit_tc_preload(ctx);
+}
 
 extern "C" int bp_paste_particles_noalloc(bp_ctx* ctx, int64_t n, const float* assigned,
                                           const bp_map_geom* geom, int select, float* ymap,

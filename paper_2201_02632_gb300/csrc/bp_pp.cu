@@ -799,6 +799,19 @@ int deposit_buffers(bp_ctx* ctx, const float* assigned, const bp_map_geom* g,
 
 size_t bp_pp_unit_bytes() { return sizeof(Unit); }
 
+// Loads the kernels that bp_pp_paste_buffers launches from this file (CUDA loads modules
+// lazily: a kernel's first launch would otherwise load its code into device memory).
+int bp_pp_preload(bp_ctx* ctx) {
+  cudaFuncAttributes a;
+  BP_CUDA(ctx, cudaFuncGetAttributes(&a, k_pair_count));
+  BP_CUDA(ctx, cudaFuncGetAttributes(&a, k_pair_emit));
+  BP_CUDA(ctx, cudaFuncGetAttributes(&a, k_unit_count));
+  BP_CUDA(ctx, cudaFuncGetAttributes(&a, k_unit_emit));
+  BP_CUDA(ctx, cudaFuncGetAttributes(&a, k_deposit<32>));
+  BP_CUDA(ctx, cudaFuncGetAttributes(&a, k_deposit<64>));
+  return BP_OK;
+}
+
 bool bp_deposit_uses_tc(const bp_ctx* ctx, int ts) {
   if (ctx->pp_kernel == BP_DEPOSIT_SIMT) return false;
   return ts == 64;

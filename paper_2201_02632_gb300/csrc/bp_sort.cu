@@ -341,3 +341,16 @@ int bp_radix_sort_pairs_buf(bp_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_
   *vals_out = vi;
   return BP_OK;
 }
+
+// Loads the scan, radix-sort and tile-range kernels (CUDA loads modules lazily: a kernel's
+// first launch would otherwise load its code into device memory).
+int bp_sort_preload(bp_ctx* ctx) {
+  cudaFuncAttributes a;
+  BP_CUDA(ctx, cudaFuncGetAttributes(&a, k_scan_reduce));
+  BP_CUDA(ctx, cudaFuncGetAttributes(&a, k_scan_bsums));
+  BP_CUDA(ctx, cudaFuncGetAttributes(&a, k_scan_down));
+  BP_CUDA(ctx, cudaFuncGetAttributes(&a, k_rs_hist));
+  BP_CUDA(ctx, cudaFuncGetAttributes(&a, k_rs_scatter));
+  BP_CUDA(ctx, cudaFuncGetAttributes(&a, k_tile_ranges));
+  return BP_OK;
+}

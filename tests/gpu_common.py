@@ -76,3 +76,18 @@ def ctx(api):
     yield c
     torch.cuda.synchronize()
     c.close()
+
+
+def gpu_model_from_oracle(api, mo):
+    """The oracle's solved models [n, n_fields] in the library's field-major layout, with
+    the oracle's status codes: lets a GPU call run on exactly the oracle's solution."""
+    from oracle import F
+
+    n = mo.shape[0]
+    m = np.zeros((len(api.MODEL_FIELDS), n), np.float64)
+    for o, gname in ORC_TO_GPU.items():
+        m[api.MF[gname]] = mo[:, F[o]]
+    m[api.MF["res_m"]] = mo[:, F["res_m"]]
+    m[api.MF["res_e"]] = mo[:, F["res_e"]]
+    status = mo[:, F["status"]].astype(np.int32)
+    return cuda(m), cuda(status)
