@@ -171,6 +171,13 @@ int bp_set_tiling(bp_ctx* ctx, int pp_tile, int hp_tile, int pp_unit);
 #define BP_DEPOSIT_SIMT 1
 #define BP_DEPOSIT_TENSOR 2
 int bp_set_deposit_kernel(bp_ctx* ctx, int kind);
+/* Test of the bounded waits (not in the paper): when polls > 0, every CTA of the context's
+ * later tensor-core deposits first waits, for at most `polls` reads, on a device flag that
+ * nothing sets, before it issues any MMA or writes anything; the deposit then gives up,
+ * frees its tensor memory and the paste returns BP_ETIMEOUT with the maps unchanged, and the
+ * context stays usable.  polls = 0 (the default) turns the test off.  BP_EINVAL for polls
+ * outside [0, 2^31). */
+int bp_set_wait_test(bp_ctx* ctx, int64_t polls);
 /* Bytes of scratch the context currently holds. */
 int64_t bp_workspace_bytes(const bp_ctx* ctx);
 

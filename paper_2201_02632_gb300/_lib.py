@@ -26,7 +26,7 @@ OUT_YB, OUT_DT = 0, 1
 
 # entry points declared in include/bp.h
 EXPORTS = ("bp_create", "bp_destroy", "bp_last_error", "bp_set_stream", "bp_set_tiling",
-           "bp_set_deposit_kernel",
+           "bp_set_deposit_kernel", "bp_set_wait_test",
            "bp_workspace_bytes", "bp_set_timing", "bp_phase_times", "bp_kernel_launches",
            "bp_solve_halos", "bp_assign_particles", "bp_paste_particles", "bp_pp_pairs",
            "bp_smoothing_lengths", "bp_paste_halos_healpix", "bp_power_spectrum",
@@ -82,6 +82,7 @@ def load():
                 "bp_set_stream": (i32, [P, P]),
                 "bp_set_tiling": (i32, [P, i32, i32, i32]),
                 "bp_set_deposit_kernel": (i32, [P, i32]),
+                "bp_set_wait_test": (i32, [P, i64]),
                 "bp_workspace_bytes": (i64, [P]),
                 "bp_set_timing": (i32, [P, i32]),
                 "bp_phase_times": (i32, [P, C.POINTER(C.c_double), i32]),

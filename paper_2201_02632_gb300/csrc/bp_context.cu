@@ -292,6 +292,14 @@ int bp_set_deposit_kernel(bp_ctx* ctx, int kind) {
   return BP_OK;
 }
 
+int bp_set_wait_test(bp_ctx* ctx, int64_t polls) {
+  if (!ctx) return BP_EINVAL;
+  if (polls < 0 || polls > 0x7fffffff)
+    return bp_fail(ctx, BP_EINVAL, "bp_set_wait_test: polls outside [0, 2^31)");
+  ctx->test_stall_polls = polls;
+  return BP_OK;
+}
+
 int bp_set_timing(bp_ctx* ctx, int on) {
   if (!ctx) return BP_EINVAL;
   if (on && !ctx->ev[0][0]) {

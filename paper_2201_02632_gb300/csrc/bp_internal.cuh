@@ -101,6 +101,7 @@ struct bp_ctx {
   int ph_open[BP_NPHASES];
   int64_t launches;
   int64_t last_fallback;  // halos the residual gate sent to the full solve
+  int64_t test_stall_polls;  // > 0: the tensor-core deposit first waits on a flag nothing sets
   char msg[512];
 };
 

@@ -546,10 +546,11 @@ __global__ void __launch_bounds__(256) k_reduce_tiles(const int64_t* __restrict_
                                                       int64_t n_tiles, int unit, int nx, int ny,
                                                       int ntx, const float* __restrict__ partials,
                                                       float* ymap, float* bmap, float* ylo,
-                                                      float* blo) {
+                                                      float* blo, const int* __restrict__ err) {
   // blockIdx.y: which of REDUCE_SPLIT pixel slices of the tile this CTA sums
   int64_t t = blockIdx.x;
   if (t >= n_tiles) return;
+  if (err && *err) return;  // the deposit gave up: its partial tiles are incomplete
   int64_t len = tstart[t + 1] - tstart[t];
   int64_t nu = (len + unit - 1) / unit;
   if (nu <= 1) return;
@@ -737,7 +738,8 @@ int launch_deposit(bp_ctx* ctx, const float* assigned, const bp_map_geom* g,
   bp_phase_begin(ctx, BP_PH_REDUCE);
   if (P.n_slots > 0) {
     k_reduce_tiles<TS><<<dim3((unsigned)P.n_tiles, REDUCE_SPLIT), 256, 0, ctx->stream>>>(
-        P.tstart, P.soff, P.n_tiles, P.unit, g->nx, g->ny, ntx, partials, ymap, bmap, ylo, blo);
+        P.tstart, P.soff, P.n_tiles, P.unit, g->nx, g->ny, ntx, partials, ymap, bmap, ylo, blo,
+        tc ? ctx->d_flags : nullptr);
     BP_LAUNCH_CHECK(ctx, "reduce tiles");
   }
   bp_phase_end(ctx, BP_PH_REDUCE);

@@ -145,3 +145,32 @@ def test_tensor_kernel_needs_tile_64(api, ctx):
     g = api.geom(16, 16, 0.0, 0.0, 1.0)
     with pytest.raises(RuntimeError, match="tile 64"):
         ctx.paste_particles(assigned_tensor(a), g, api.Maps.zeros(g))
+
+
+@pytest.mark.parametrize("unit", [256, 8192])
+def test_tensor_deposit_timeout_returns_error_and_keeps_context(api, ctx, unit):
+    """A bounded device wait that runs out (bp_set_wait_test: every CTA first waits on a flag
+    that nothing sets, before issuing any MMA): the paste returns BP_ETIMEOUT, the maps are
+    untouched (partial tiles included: unit 256 splits tiles), and the next paste on the same
+    context is the normal result, bit for bit."""
+    a = I.assigned_particles(n=20000, npix=200, hmax=40, margin=30)
+    rec = assigned_tensor(a)
+    g = api.geom(200, 130, 0.0, 0.0, 1.0)
+    ctx.set_tiling(pp_tile=64, pp_unit=unit)
+    ctx.set_deposit_kernel("tensor")
+    ref = api.Maps.zeros(g)
+    ctx.paste_particles(rec, g, ref)
+    ctx.set_wait_test(2000)
+    maps = api.Maps.zeros(g)
+    for t in (maps.y, maps.b, maps.ylo, maps.blo):
+        t.fill_(0.25)
+    with pytest.raises(api.BpError, match="BP_ETIMEOUT"):
+        ctx.paste_particles(rec, g, maps)
+    torch.cuda.synchronize()
+    for t in (maps.y, maps.b, maps.ylo, maps.blo):
+        assert bool((t == 0.25).all())
+    ctx.set_wait_test(0)
+    again = api.Maps.zeros(g)
+    ctx.paste_particles(rec, g, again)
+    for x, y in ((again.y, ref.y), (again.b, ref.b), (again.ylo, ref.ylo), (again.blo, ref.blo)):
+        assert torch.equal(x, y)
