@@ -29,10 +29,12 @@
 //    l + 33 from its neighbour, so every edge is evaluated once;
 //  - it writes its 16-byte chunk (4 particles) of rows l, l + 32 (and 64 + l, 96 + l of A)
 //    of the 128-byte-swizzled K-major operand tiles of the chunk's stage;
-//  - it arrives on the stage's counter; the eighth warp to arrive issues the chunk's 12 MMAs
-//    (4 K-steps x 3 products) and commits them to the stage's mbarrier.
-// There is no CTA barrier per chunk: a warp only waits for the MMAs of the chunk that last
-// used the stage it is about to fill (two stages), so warps drift by up to a chunk.
+//  - it arrives on the stage's mbarrier (release) and counter; the eighth warp to count
+//    acquires the stage through the mbarrier, issues the chunk's 12 MMAs (4 K-steps x 3
+//    products) and commits them to the stage's completion mbarrier.
+// There is no CTA barrier per chunk: a warp computes its weights in registers, then waits
+// only for the MMAs of the chunk that last used the stage it is about to fill (two stages),
+// so warps drift by up to a chunk; a group's fold comes after the warp's next arrival.
 // Each warp folds and writes out its own quarter of the tensor-memory tile (its 32 lanes,
 // 32 of the 64 columns).
 //
@@ -61,6 +63,9 @@ constexpr float KT = 0.9036020040512085f;
 constexpr float KS = 1.277886152267456f;
 constexpr float NGP_IH = 1.0e38f;  // 1/h of a particle with h = 0
 constexpr float FAR = -1.0e6f;     // tile position of an empty slot
+#ifndef TC_SLEEP_NS
+#define TC_SLEEP_NS 20000  // a waiting warp sleeps (it wakes when the phase completes)
+#endif
 
 struct alignas(1024) TcStage {
   unsigned char a_hi[128 * 128];  // 128 rows x 32 TF32
@@ -82,8 +87,9 @@ struct TcSmem {
   TcStage st[2];
   float4 raw[TC_WARPS][TC_RING][4][2];  // records (two 16-byte halves) per warp and chunk
   TcField fld[TC_WARPS][4];
-  uint64_t mbar[2];
-  uint32_t arrive[2];  // warps arrived at each stage (cumulative; the eighth issues)
+  uint64_t mbar[2];     // per stage: the chunk's MMAs completed (tcgen05.commit)
+  uint64_t full[2];     // per stage: all eight warps wrote their operands (release arrivals)
+  uint32_t arrive[2];   // warps arrived at each stage (cumulative, relaxed; the eighth issues)
   int64_t unit[2];
   int64_t issued;      // chunks whose MMAs were issued
   uint32_t tmem;
@@ -129,15 +135,6 @@ __device__ __forceinline__ void axis_weights(int l, float lf, float4 a, float e6
   if (l + 32 == kc) w1 += 1.f;
 }
 
-__device__ __forceinline__ uint32_t atom_add_acq_rel(uint32_t* p, uint32_t v) {
-  uint32_t old;
-  asm volatile("atom.acq_rel.cta.shared::cta.add.u32 %0, [%1], %2;"
-               : "=r"(old)
-               : "r"(bptc::smem_u32(p)), "r"(v)
-               : "memory");
-  return old;
-}
-
 __global__ void __launch_bounds__(TC_THREADS, 2)
     k_deposit_tc(const float4* __restrict__ rec, const uint32_t* __restrict__ pvals,
                  const BpUnit* __restrict__ units, const int64_t* __restrict__ n_units_ptr,
@@ -156,6 +153,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   if (tid == 0) {
     mbar_init(&S.mbar[0], 1);
     mbar_init(&S.mbar[1], 1);
+    mbar_init(&S.full[0], TC_WARPS);
+    mbar_init(&S.full[1], TC_WARPS);
     fence_mbar_init();
     S.arrive[0] = S.arrive[1] = 0u;
     S.issued = 0;
@@ -188,7 +187,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
   __syncthreads();
   // waits for the MMAs of chunk gi (global index) to complete
   auto wait_chunk = [&](int64_t gi) -> bool {
-    bool ok = mbar_wait_bounded(&S.mbar[gi & 1], (uint32_t)((gi >> 1) & 1), wc.polls, wc.ns);
+    bool ok = TC_SLEEP_NS > 0 ? mbar_wait_bounded_sleep(&S.mbar[gi & 1], (uint32_t)((gi >> 1) & 1),
+                                                        wc.polls, wc.ns, TC_SLEEP_NS)
+                              : mbar_wait_bounded(&S.mbar[gi & 1], (uint32_t)((gi >> 1) & 1),
+                                                  wc.polls, wc.ns);
     ok = __all_sync(0xffffffffu, ok);  // the TMEM accesses that follow are warp-collective
     if (!ok) fail();
     gdone = gi + 1;
@@ -308,15 +310,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         }
       }
       __syncwarp();
-      // 3. stage s is free once the MMAs of chunk gc - 2 are done (fold at group ends)
-      if (gc >= 2 && gdone <= gc - 2) {
-        if (!wait_chunk(gc - 2)) {
-          aborted = true;
-          break;
-        }
-        if (c >= 2 && (c - 2) % TC_G == TC_G - 1) fold((c - 2) / TC_G);
-      }
-      // 4. weights of particles 4w .. 4w + 3 -> operand stage s
+      // 3. weights of particles 4w .. 4w + 3 (in registers: the stage may still be busy)
       TcStage& T = S.st[s];
       float wx0[4], wx1[4], wy0[4], wy1[4], Yk[4], Bk[4];
 #pragma unroll
@@ -328,6 +322,16 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         axis_weights(lane, lane_f, F.ax[1], m.y, kc.y, wy0[p], wy1[p]);
         Yk[p] = m.z;
         Bk[p] = m.w;
+      }
+      // 4. stage s is free once the MMAs of chunk gc - 2 are done; a group that ended there
+      // is folded after this chunk's arrival
+      bool fold_now = false;
+      if (gc >= 2 && gdone <= gc - 2) {
+        if (!wait_chunk(gc - 2)) {
+          aborted = true;
+          break;
+        }
+        fold_now = c >= 2 && (c - 2) % TC_G == TC_G - 1;
       }
 #pragma unroll
       for (int half = 0; half < 2; ++half) {  // column weights: the B operand
@@ -354,10 +358,23 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
       fence_proxy_async_smem();
       tc_fence_before();
       __syncwarp();
-      // 5. arrive; the eighth warp issues the chunk's MMAs into the group's accumulator
+      // 5. arrive (release, on the stage's mbarrier); the warp whose count is the eighth
+      // acquires the stage through that mbarrier and issues the chunk's MMAs into the group's
+      // accumulator (the counter only elects the issuer: a relaxed atomic, no memory fence)
       if (lane == 0) {
-        const uint32_t old = atom_add_acq_rel(&S.arrive[s], 1u);
-        if ((old & (TC_WARPS - 1)) == TC_WARPS - 1) {
+        mbar_arrive(&S.full[s]);
+        const uint32_t old = atomicAdd(&S.arrive[s], 1u);
+        bool issue = (old & (TC_WARPS - 1)) == TC_WARPS - 1;
+        if (issue &&
+            !(TC_SLEEP_NS > 0 ? mbar_wait_bounded_sleep(&S.full[s], (uint32_t)((gc >> 1) & 1),
+                                                        wc.polls, wc.ns, TC_SLEEP_NS)
+                              : mbar_wait_bounded(&S.full[s], (uint32_t)((gc >> 1) & 1),
+                                                  wc.polls, wc.ns))) {
+          issue = false;  // the other warps time out on this chunk's MMAs in turn
+          S.abort = 1;
+          atomicExch(err, 1);
+        }
+        if (issue) {
           tc_fence_after();
           // K-step ks starts 32 bytes further in: + 2 in the address field (bits 0-13; no
           // carry for shared addresses below 256 KB)
@@ -376,6 +393,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
         }
       }
       __syncwarp();
+      // the group's accumulator is overwritten only by the MMAs of chunk c + 3 (the first of
+      // group (c - 2) / TC_G + 2), which wait for this warp's arrival there
+      if (fold_now) fold((c - 2) / TC_G);
     }
     if (lane < 8) cp_async_wait_all();  // no copy outlives the unit
     if (!aborted) {

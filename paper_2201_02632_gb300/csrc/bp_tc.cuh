@@ -73,6 +73,14 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
+// arrive once on the mbarrier (release at CTA scope: this thread's earlier writes, and those
+// made visible to it, happen before the phase completes for its waiters)
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile(
+      "{\n.reg .b64 st;\n"
+      "mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar))
+      : "memory");
+}
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -88,6 +96,33 @@ __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
+}
+// Like mbar_try_wait, but the thread may be suspended for up to hint_ns nanoseconds while
+// the phase is incomplete (it resumes when the phase completes), so that a waiting warp takes
+// no issue slots from the warps it waits for.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity,
+                                                    uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+// mbar_wait_bounded with suspending polls (hint_ns each).
+__device__ __forceinline__ bool mbar_wait_bounded_sleep(uint64_t* bar, uint32_t parity,
+                                                        uint32_t max_iter, uint64_t max_ns,
+                                                        uint32_t hint_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (uint32_t it = 1; it < max_iter; ++it) {
+    if (mbar_try_wait_sleep(bar, parity, hint_ns)) return true;
+    if ((it & 7) == 0 && global_ns() - t0 > max_ns) return false;
+  }
+  return false;
 }
 // Waits for the phase with the given parity to complete; gives up after max_iter polls
 // or max_ns nanoseconds, whichever comes first.
