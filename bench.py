@@ -1,14 +1,20 @@
 #!/usr/bin/env python
-"""Benchmark of the baryon pasting hot path on the light-cone workload.
+"""Benchmark of the baryon pasting hot path on the full-scale light-cone.
 
-Workload (one step): 4e6 particles in a 2x2 deg^2 cone (z 0.05-1.5; 60% from 3000
-truncated-NFW halos, 40% field), 1024^2 maps.  A step solves the ICM model of the
-3000 halos, assigns the particle signals, pastes them (pair list, radix sort,
-tiled deposit, partial-tile reduction), pastes the 3000 halos' projected profiles
-onto their own 1024^2 maps, and finalises both map pairs.
+Workload (one step, the headline): 5e8 particles in a 5x5 deg^2 light-cone to z = 3 (60%
+from 2e5 truncated-NFW halos with dN/dlnM ~ M^-0.9 on 1e12-1e15 h^-1 Msun, 40% field),
+4096^2 maps.  A step solves the ICM model of the 2e5 halos, assigns the particle signals,
+pastes them (pair list, radix sort, tensor-core deposit, partial-tile reduction), pastes the
+halos' projected profiles onto their own 4096^2 maps (second stream) and finalises both map
+pairs.  On N GPUs (torchrun) the same sky is shared: particles and halos are partitioned by
+index, each rank fills full map planes and one all-reduce sums them (strong scaling).
 
-Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on a bounded
-sample of the same workload instead.
+Side sections on one GPU: the 4e6-particle 2x2 deg^2 cone, the 1000-halo HP catalogue,
+the surrogate against the plain solve, smoothing lengths, the power spectrum, batched HP
+and the all-sky HP map.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on a bounded,
+representative sample of the same workload instead.
 """
 from __future__ import annotations
 
@@ -31,11 +37,26 @@ sys.path.insert(0, ROOT)
 
 METRIC = "pasted particles/s (PP), halos/s (HP), frac of HBM roofline; surrogate vs solve"
 UNIT = "particles/s"
-WORKLOAD = ("PP plain, FP32 deposit: 4M particles, 2x2 deg^2 light-cone z 0.05-1.5, 3000 "
-            "halos (60% halo / 40% field particles), 1024^2 y and kSZ maps; plus HP of the "
-            "3000 halos on 1024^2 maps")
+WORKLOAD = ("PP full-scale: 5e8 particles (SoA FP32 positions, velocities, smoothing lengths, "
+            "int32 halo id) in a 5x5 deg^2 light-cone z 0.05-3, 2e5 halos (dN/dlnM ~ M^-0.9 on "
+            "1e12-1e15 h^-1 Msun; 60% halo / 40% field particles), 4096^2 y and kSZ maps; plus HP "
+            "of the 2e5 halos on 4096^2 maps")
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
+# the oracle's sample of the full-scale cone: a seeded subset of the halos with all of their
+# particles, and the same share of the field particles (inputs.lightcone_device(sample=...))
+REF_SAMPLE = (1.0e-3, 1.0e-3)
+
+
+def config(args, world):
+    """The workload description shared by both arms (and every N)."""
+    return {"workload": WORKLOAD, "particles": args.particles, "halos": args.halos,
+            "maps": f"{args.npix}x{args.npix}", "pp_tile": 64,
+            "deposit_kernel": "tcgen05 split-TF32",
+            "l2": "inputs (16 GB of particles) far larger than L2; 256 MB written between "
+                  "timed steps as well",
+            "parallelism": "single sky, particles and halos partitioned by index, one map "
+                           f"all-reduce (x{world})" if world > 1 else "one GPU"}
 
 
 def rank_env():
@@ -43,13 +64,8 @@ def rank_env():
             int(os.environ.get("LOCAL_RANK", 0)))
 
 
-def replica_seed(rank, base):
-    """Seed of the light-cone a rank pastes: each replica draws its own sky."""
-    return base + 1 + rank
-
-
 def max_over_ranks(value, world, device):
-    """The largest of the ranks' values (the step time a weak-scaling job reports)."""
+    """The largest of the ranks' values (the step time a multi-rank job reports)."""
     if world <= 1:
         return float(value)
     import torch
@@ -59,16 +75,21 @@ def max_over_ranks(value, world, device):
     return float(t.item())
 
 
-def job_rate(units_per_rank, world, ms):
-    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
-    return units_per_rank * world / (ms * 1e-3)
-
-
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         return {}
+
+
+def tf32_peak(peaks):
+    """TF32 dense peak: the measured cuBLAS bf16 burst x the nominal TF32/BF16 dense ratio."""
+    return float(peaks.get("bf16_tflops", 1900.0)) * (1.1 / 2.25)
+
+
+def fp32_peak(peaks):
+    """FP32 FMA peak: 152 SMs x 128 lanes x 2 flops x the maximum SM clock."""
+    return SM_COUNT * FP32_LANES_PER_SM * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
 
 
 class ClockSampler:
@@ -113,6 +134,7 @@ class ClockSampler:
         os.unlink(self.path)
         if not rows:
             return None
+
         def num(x):
             try:
                 return float(x)
@@ -135,12 +157,12 @@ def phase_bandwidth(ph, n, n_pairs, nx, ny, hbm_peak):
         "assign": n * 64,
         # two reads of the 32 B records (count, emit), counts 4 B, offsets 8 B, pairs 8 B
         "pairs": n * (32 + 32 + 4 + 8) + n_pairs * 8,
-        # one 8-bit pass: key read for the histogram, key + value read and written,
-        # key read for the tile ranges
-        "sort": n_pairs * (4 + 16 + 4),
-        # map and lo planes of y and b read and written, for the PP maps (the HP maps are
-        # finalised on the second stream)
-        "finalize": 4 * maps,
+        # per 8-bit pass: key read for the histogram, key + value read and written; key read
+        # for the tile ranges (one pass for <= 256 tiles, two for 4096)
+        "sort": n_pairs * (4 + 16) * (1 if nx * ny <= 256 * 64 * 64 else 2) + n_pairs * 4,
+        # map and lo planes of y and b read and written, for the PP and the HP maps (both
+        # finalised on the particle chain's stream)
+        "finalize": 8 * maps,
     }
     out = {}
     for k, b in bytes_.items():
@@ -151,32 +173,15 @@ def phase_bandwidth(ph, n, n_pairs, nx, ny, hbm_peak):
     return out
 
 
-def deposit_flops(rec_np, nx, ny):
-    """Algorithmic FP32 flops of one deposit launch: 2 per pixel update (one FMA per map)
-    over every particle's clipped 2h x 2h footprint; field particles update one map."""
-    ints = rec_np.view(np.int32)
-    px = ints[:, 6].astype(np.float64) + rec_np[:, 0]
-    py = ints[:, 7].astype(np.float64) + rec_np[:, 1]
-    hp, Y, kind = rec_np[:, 2].astype(np.float64), rec_np[:, 3], ints[:, 5]
-    with np.errstate(invalid="ignore"):
-        i0 = np.floor(px - hp)
-        i1 = np.floor(px + hp)
-        j0 = np.floor(py - hp)
-        j1 = np.floor(py + hp)
-    ok = (kind != 2) & (i1 >= 0) & (i0 <= nx - 1) & (j1 >= 0) & (j0 <= ny - 1)
-    w = np.clip(i1, 0, nx - 1) - np.clip(i0, 0, nx - 1) + 1
-    h = np.clip(j1, 0, ny - 1) - np.clip(j0, 0, ny - 1) + 1
-    upd = (w * h)[ok].astype(np.float64)
-    maps = np.where(Y[ok] != 0, 2.0, 1.0)
-    return float(2.0 * np.sum(upd * maps)), float(np.sum(upd))
-
-
-def deposit_flops_device(rec, nx, ny):
-    """deposit_flops computed with torch on the device (for records too large to copy)."""
+def deposit_work(rec, nx, ny, tile=64):
+    """Algorithmic work of one deposit launch, computed with torch on the records' device:
+    flops = 2 per pixel update (one FMA) per map the particle touches (field particles carry
+    no y) over every particle's clipped 2h x 2h footprint; pixel updates; and the (tile,
+    particle) pairs of the pair list (the tiles each footprint's pixel box touches)."""
     import torch
 
     ints = rec.view(torch.int32)
-    out_f, out_u = 0.0, 0.0
+    flops = updates = pairs = 0.0
     for a in range(0, rec.shape[0], 50_000_000):
         r = rec[a:a + 50_000_000]
         iv = ints[a:a + 50_000_000]
@@ -186,13 +191,16 @@ def deposit_flops_device(rec, nx, ny):
         i0, i1 = torch.floor(px - hp), torch.floor(px + hp)
         j0, j1 = torch.floor(py - hp), torch.floor(py + hp)
         ok = (iv[:, 5] != 2) & (i1 >= 0) & (i0 <= nx - 1) & (j1 >= 0) & (j0 <= ny - 1)
-        w = i1.clamp(0, nx - 1) - i0.clamp(0, nx - 1) + 1
-        h = j1.clamp(0, ny - 1) - j0.clamp(0, ny - 1) + 1
-        upd = (w * h)[ok]
+        ci0, ci1 = i0.clamp(0, nx - 1), i1.clamp(0, nx - 1)
+        cj0, cj1 = j0.clamp(0, ny - 1), j1.clamp(0, ny - 1)
+        upd = ((ci1 - ci0 + 1) * (cj1 - cj0 + 1))[ok]
         maps = torch.where(r[:, 3][ok] != 0, 2.0, 1.0).double()
-        out_f += float(2.0 * (upd * maps).sum())
-        out_u += float(upd.sum())
-    return out_f, out_u
+        tp = ((torch.floor(ci1 / tile) - torch.floor(ci0 / tile) + 1) *
+              (torch.floor(cj1 / tile) - torch.floor(cj0 / tile) + 1))[ok]
+        flops += float(2.0 * (upd * maps).sum())
+        updates += float(upd.sum())
+        pairs += float(tp.sum())
+    return flops, updates, int(pairs)
 
 
 def ncu_traffic(kernel_key):
@@ -204,82 +212,443 @@ def ncu_traffic(kernel_key):
     except Exception:
         return None
     files = d["sources"] if "sources" in d else [d["source"]]
-    src = b"".join(open(os.path.join(ROOT, "paper_2201_02632_gb300", "csrc", f), "rb").read()
-                   for f in files)
+    try:
+        src = b"".join(open(os.path.join(ROOT, "paper_2201_02632_gb300", "csrc", f), "rb").read()
+                       for f in files)
+    except OSError:
+        return None
     if hashlib.sha256(src).hexdigest()[:16] != d.get("source_sha256_16"):
         return None
     return d.get("dram_bytes_per_launch_scaled")
 
 
+def deposit_roofline(kernel, dep_ms, work, peaks, traffic_key):
+    """Roofline entry of the deposit from its live CUDA-event duration and its algorithmic
+    flops (against the TF32 tensor peak of measured), plus the MMA work it issues."""
+    flops, updates, pairs = work
+    achieved = flops / (dep_ms * 1e-3) / 1e12
+    peak = tf32_peak(peaks)
+    # per (tile, particle) pair the kernel issues a 128 x 64 rank-1 update in three
+    # split-TF32 products
+    mma = pairs * 128 * 64 * 2 * 3
+    return {"kernel": kernel, "bound": "tensor", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": ncu_traffic(traffic_key),
+            "deposit_ms": dep_ms, "algorithmic_flops_per_launch": flops,
+            "pixel_updates": updates, "tile_pairs": pairs, "mma_flops_issued_per_launch": mma,
+            "mma_tflops_issued": mma / (dep_ms * 1e-3) / 1e12,
+            "frac_fp32_alu_peak": achieved / fp32_peak(peaks),
+            "peak_note": f"of measured: bf16 burst {float(peaks.get('bf16_tflops', 1900.0))} "
+                         "TFLOP/s x 1.1/2.25 (nominal TF32/BF16 dense ratio)"}
+
+
 # ------------------------------------------------------------------ CPU oracle legs
-def oracle_sample(lc, n_part_sample, n_halo_sample, threads):
-    """Times the FP64 oracle on a bounded sample of the workload; returns
-    (seconds extrapolated to the full step, detail dict)."""
+def oracle_sample_step(sample_lc, threads):
+    """One step of the FP64 oracle on the sample cone: solve of the halos its particles
+    reference, assign + deposit of its particles, HP of those halos.  Returns (seconds,
+    particles, detail)."""
     import oracle as O
 
-    O.build()
-    g = O.geom(lc.geom.nx, lc.geom.ny, lc.geom.theta0_x, lc.geom.theta0_y, lc.geom.dtheta)
-    cat = lc.halos
+    parts = {k: v.cpu().numpy() for k, v in sample_lc.parts.items()}
+    cat, gm = sample_lc.halos, sample_lc.geom
+    g = O.geom(gm.nx, gm.ny, gm.theta0_x, gm.theta0_y, gm.dtheta)
+    hk = np.unique(parts["hid"][parts["hid"] >= 0])
     t0 = time.perf_counter()
-    mo = O.solve_halos(cat.M, cat.c, cat.z, nthreads=threads)
-    t_solve = time.perf_counter() - t0
-    sub = {k: v[:n_part_sample] for k, v in lc.parts.items()}
-    t0 = time.perf_counter()
-    a = O.pp_assign(sub, lc.Mp, cat.pos, mo, g, nthreads=threads)
+    mo = O.solve_referenced(cat.M, cat.c, cat.z, hk, nthreads=threads)
+    t1 = time.perf_counter()
+    a = O.pp_assign(parts, sample_lc.Mp, cat.pos, mo, g, nthreads=threads)
     O.pp_deposit(a, g, nthreads=threads)
-    t_pp = time.perf_counter() - t0
-    hs = slice(0, n_halo_sample)
-    t0 = time.perf_counter()
-    O.hp_map(cat.thx[hs], cat.thy[hs], cat.vlos[hs], mo[hs], g, rtol=1e-8, nthreads=threads)
-    t_hp = time.perf_counter() - t0
-    n = lc.parts["x"].size
-    nh = cat.M.size
-    t_full = t_solve + t_pp * n / n_part_sample + t_hp * nh / n_halo_sample
-    det = {"t_solve_all_halos_s": round(t_solve, 3), "t_pp_sample_s": round(t_pp, 3),
-           "t_hp_sample_s": round(t_hp, 3), "n_part_sample": n_part_sample,
-           "n_halo_sample": n_halo_sample}
-    return t_full, det
+    t2 = time.perf_counter()
+    O.hp_map(cat.thx[hk], cat.thy[hk], cat.vlos[hk], mo[hk], g, rtol=1e-8, nthreads=threads)
+    t3 = time.perf_counter()
+    n = parts["x"].size
+    det = {"particles": int(n), "halos_solved": int(hk.size), "solve_s": round(t1 - t0, 3),
+           "assign_deposit_s": round(t2 - t1, 3), "hp_s": round(t3 - t2, 3)}
+    return t3 - t0, n, det
+
+
+def sample_cone(args):
+    from paper_2201_02632_gb300 import inputs as I
+
+    return I.lightcone_device(n_part=args.particles, n_halo=args.halos, npix=args.npix,
+                              device="cpu", sample=REF_SAMPLE)
+
+
+def sample_text(lc):
+    s = lc.info["sample"]
+    return (f"seeded sample of the full-scale cone: {s['halos_kept']} of the {lc.halos.M.size} "
+            f"halos (each kept with probability {s['halo_keep']}) with all of their particles "
+            f"and {s['field_keep']} of the field particles, {s['particles']} particles in all, "
+            "with the full cone's particle mass and smoothing lengths; per step the FP64 oracle "
+            "solves the sampled halos, assigns and deposits the sampled particles and pastes "
+            "the sampled halos on the 4096^2 maps; value = sampled particles / measured step time")
 
 
 def run_reference(args):
     rank, world, _ = rank_env()
     if rank != 0:
         return 0
-    from paper_2201_02632_gb300 import inputs as I
-
-    lc = I.lightcone()
+    lc = sample_cone(args)
     threads = os.cpu_count() or 1
-    times = []
+    times, det = [], None
     for k in range(args.warmup + args.steps):
-        t, det = oracle_sample(lc, args.ref_particles, args.ref_halos, threads)
+        t, n, det = oracle_sample_step(lc, threads)
         if k >= args.warmup:
             times.append(t)
     t_step = statistics.mean(times)
-    n = lc.parts["x"].size
     v = n / t_step
-    sample = (f"per step: FP64 oracle solve of all {lc.halos.M.size} halos, assign+deposit of "
-              f"{args.ref_particles} particles and HP of {args.ref_halos} halos, extrapolated "
-              f"linearly to the full step")
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step * 1e3,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": {"workload": WORKLOAD, "parallelism": "none (CPU)"},
+           "higher_is_better": True, "scaling": "strong" if args.gpus > 1 else "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config(args, args.gpus),
            "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-                            "sample": sample},
+                            "sample": sample_text(lc), "detail": det},
            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
 
 
-# ------------------------------------------------------------------ GPU leg
-def surrogate_section(api, ctx, dev, lc, args):
-    """Surrogate vs plain solve: train on solver outputs, then time both solves on
-    the same inference halos, and compare the pasted y of the light-cone halos."""
+# ------------------------------------------------------------------ headline (GPU)
+def headline(api, args, dev, rank, world, peaks):
+    """The full-scale cone, one sky over `world` ranks.  Returns the line's fields."""
+    import torch
+
+    from paper_2201_02632_gb300 import inputs as I
+    from paper_2201_02632_gb300 import shard
+
+    t0 = time.perf_counter()
+    lc = I.lightcone_device(n_part=args.particles, n_halo=args.halos, npix=args.npix, device=dev)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    n_all = lc.parts["x"].numel()
+    lo, hi = shard.shard_range(n_all, rank, world)
+    if world > 1:
+        for k in list(lc.parts):
+            lc.parts[k] = lc.parts[k][lo:hi].clone()
+        torch.cuda.empty_cache()
+    n = hi - lo
+    cat = lc.halos
+    nh = cat.M.size
+    hlo, hhi = shard.shard_range(nh, rank, world)
+    g = api.geom(lc.geom.nx, lc.geom.ny, lc.geom.theta0_x, lc.geom.theta0_y, lc.geom.dtheta)
+    keys = list(lc.parts.keys())
+
+    # pinned host copies of this rank's inputs: the end-to-end leg uploads them every step
+    t0 = time.perf_counter()
+    h_parts = []
+    for k in keys:
+        h = torch.empty(lc.parts[k].shape, dtype=lc.parts[k].dtype, pin_memory=True)
+        h.copy_(lc.parts[k])
+        h_parts.append(h)
+    h_halo = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for a in
+              (cat.M, cat.c, cat.z, cat.pos, cat.thx[hlo:hhi], cat.thy[hlo:hhi],
+               cat.vlos[hlo:hhi])]
+    h_in = h_parts + h_halo
+    d_in = [lc.parts[k] for k in keys] + [t.to(dev) for t in h_halo]
+    pin_s = time.perf_counter() - t0
+    del lc.parts
+    h2d_bytes = sum(t.numel() * t.element_size() for t in h_in)
+
+    ctx = api.Context()
+    comp = torch.cuda.current_stream()
+    hp_stream = torch.cuda.Stream()
+    ctx_hp = api.Context(stream=hp_stream)
+    hp_pool = concurrent.futures.ThreadPoolExecutor(1)
+    rec = torch.empty((n, api.ASSIGNED_STRIDE), dtype=torch.float32, device=dev)
+
+    def new_maps():
+        buf = shard.map_planes(8, 1, g.ny, g.nx, dev)  # PP y, b, ylo, blo; HP y, b, ylo, blo
+        return buf, api.Maps(buf[0], buf[1], buf[2], buf[3]), api.Maps(buf[4], buf[5], buf[6],
+                                                                         buf[7])
+
+    buf, pp, hp = new_maps()
+    out_host = [torch.empty((g.ny, g.nx), dtype=torch.float32).pin_memory() for _ in range(4)]
+    d2h_bytes = sum(t.numel() * t.element_size() for t in out_host)
+    sub = (lambda m: m) if world == 1 else (lambda m: m[:, hlo:hhi].contiguous())
+
+    def step(ins=None, maps=None):
+        """One pass of the hot path over this rank's share (ins: device inputs, maps: the
+        (buffer, PP maps, HP maps) to fill)."""
+        ins = d_in if ins is None else ins
+        mbuf, mpp, mhp = (buf, pp, hp) if maps is None else maps
+        parts = dict(zip(keys, ins[:len(keys)]))
+        M, c, z, pos, thx, thy, vl = ins[len(keys):]
+        mbuf.zero_()
+        model, status = ctx.solve_halos(M, c, z, raise_on_noconv=False)
+        solved = torch.cuda.Event()
+        solved.record(comp)
+
+        def halo_paste():
+            with torch.cuda.stream(hp_stream):
+                hp_stream.wait_event(solved)
+                ctx_hp.paste_halos(thx, thy, vl, sub(model), sub(status), g, mhp)
+                done = torch.cuda.Event()
+                done.record(hp_stream)
+                return done
+
+        fut = hp_pool.submit(halo_paste)
+        ctx.assign_particles(parts, lc.Mp, pos, model, status, g, out=rec)
+        ctx.paste_particles(rec, g, mpp)
+        comp.wait_event(fut.result())
+        shard.reduce_maps(mbuf, world)
+        ctx.finalize(g, mpp)
+        ctx.finalize(g, mhp)
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    work = deposit_work(rec, g.nx, g.ny)
+    ctx.set_timing(True)
+    ctx.phase_times()
+    sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
+    barrier()
+    if rank == 0:
+        sampler.start()
+    launches0 = ctx.kernel_launches() + ctx_hp.kernel_launches()
+    step_ms, phases = [], []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        phases.append(ctx.phase_times())  # synchronises the stream
+        step_ms.append(e0.elapsed_time(e1))
+    barrier()
+    launches = ctx.kernel_launches() + ctx_hp.kernel_launches() - launches0
+    clocks = sampler.stop() if rank == 0 else None
+    ctx.set_timing(False)
+    t_step = max_over_ranks(sum(step_ms) / len(step_ms), world, dev)
+
+    # end to end through the public API: this step's inputs uploaded from pinned host memory,
+    # the finalised maps read back; serial (copy, step, copy back) ...
+    e2e_ms = []
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for hsrc, ddst in zip(h_in, d_in):
+            ddst.copy_(hsrc, non_blocking=True)
+        step()
+        for hdst, dsrc in zip(out_host, (pp.y[0], pp.b[0], hp.y[0], hp.b[0])):
+            hdst.copy_(dsrc, non_blocking=True)
+        e1.record()
+        torch.cuda.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    t_e2e_serial = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world, dev)
+
+    # ... and pipelined as a production loop runs it: an upload stream copies step k + 1's
+    # inputs and a download stream reads step k - 1's maps while step k computes (inputs and
+    # maps double-buffered); every step's uploads, compute and downloads lie inside the timed
+    # region, which runs from the first upload to the last download
+    up, down = torch.cuda.Stream(), torch.cuda.Stream()
+    ins2 = [d_in, [torch.empty_like(t) for t in d_in]]
+    maps2 = [(buf, pp, hp), new_maps()]
+    outs2 = [out_host, [torch.empty((g.ny, g.nx), dtype=torch.float32).pin_memory()
+                        for _ in range(4)]]
+    ev = lambda: torch.cuda.Event(enable_timing=False)
+    in_ready = [ev() for _ in range(args.steps)]
+    done = [ev() for _ in range(args.steps)]
+    drained = [ev() for _ in range(args.steps)]
+
+    def upload(k):
+        with torch.cuda.stream(up):
+            if k >= 2:
+                up.wait_event(done[k - 2])  # step k - 2 no longer reads this input set
+            for hsrc, ddst in zip(h_in, ins2[k % 2]):
+                ddst.copy_(hsrc, non_blocking=True)
+            in_ready[k].record(up)
+
+    barrier()
+    t0e, t1e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0e.record(up)
+    upload(0)
+    for k in range(args.steps):
+        b = k % 2
+        if k + 1 < args.steps:
+            upload(k + 1)  # queued before step k's host-synchronising calls
+        comp.wait_event(in_ready[k])
+        if k >= 2:
+            comp.wait_event(drained[k - 2])  # those maps have been read back
+        step(ins2[b], maps2[b])
+        done[k].record(comp)
+        with torch.cuda.stream(down):
+            down.wait_event(done[k])
+            _, m_pp, m_hp = maps2[b]
+            for hdst, dsrc in zip(outs2[b], (m_pp.y[0], m_pp.b[0], m_hp.y[0], m_hp.b[0])):
+                hdst.copy_(dsrc, non_blocking=True)
+            drained[k].record(down)
+    down.wait_event(drained[args.steps - 1])
+    t1e.record(down)
+    torch.cuda.synchronize()
+    t_e2e = max_over_ranks(t0e.elapsed_time(t1e) / args.steps, world, dev)
+    del ins2, maps2
+
+    mean_ph = {k: round(sum(p[k] for p in phases) / len(phases), 4) for k in phases[0]}
+    hbm = float(peaks.get("hbm_gbs", 6780.4))
+    res = {
+        "value": n_all / (t_step * 1e-3), "ms_per_step": t_step,
+        "phase_ms": mean_ph,
+        "phase_note": "the particle chain's phases on the main stream (solve .. finalize); the "
+                      "halo paste runs on a second stream beside it",
+        "phase_hbm": phase_bandwidth(mean_ph, n, work[2], g.nx, g.ny, hbm),
+        "roofline": deposit_roofline("k_deposit_tc", mean_ph["deposit"], work, peaks,
+                                     "k_deposit_tc_c2"),
+        "e2e": {"value": n_all / (t_e2e * 1e-3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d_bytes * world, "d2h_bytes_per_step": d2h_bytes * world,
+                "ms_per_step": t_e2e, "pipelined": "copies of steps k +- 1 overlap step k",
+                "serial_ms_per_step": t_e2e_serial,
+                "serial_value": n_all / (t_e2e_serial * 1e-3)},
+        "gpu_launches": launches, "clocks": clocks,
+        "inputs": {"generate_s": round(gen_s, 2), "pin_s": round(pin_s, 2),
+                   "particles_this_rank": n, "halos_pasted_this_rank": hhi - hlo},
+    }
+    ctx.close()
+    ctx_hp.close()
+    del d_in, h_in, h_parts, rec, buf, pp, hp, flush
+    torch.cuda.empty_cache()
+    return res, cat
+
+
+# ------------------------------------------------------------------ side sections (one GPU)
+def lightcone_4m_section(api, dev, args, peaks):
+    """The 4e6-particle 2x2 deg^2 cone (3000 halos, 1024^2 maps): the same step, on one GPU."""
+    import torch
+
+    from paper_2201_02632_gb300 import inputs as I
+
+    lc = I.lightcone()
+    n, cat = lc.parts["x"].size, lc.halos
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    parts = {k: t(v) for k, v in lc.parts.items()}
+    M, c, z, pos, thx, thy, vl = (t(a) for a in (cat.M, cat.c, cat.z, cat.pos, cat.thx, cat.thy,
+                                                 cat.vlos))
+    g = api.geom(lc.geom.nx, lc.geom.ny, lc.geom.theta0_x, lc.geom.theta0_y, lc.geom.dtheta)
+    ctx = api.Context()
+    comp = torch.cuda.current_stream()
+    hp_stream = torch.cuda.Stream()
+    ctx_hp = api.Context(stream=hp_stream)
+    pool = concurrent.futures.ThreadPoolExecutor(1)
+    rec = torch.empty((n, api.ASSIGNED_STRIDE), dtype=torch.float32, device=dev)
+    pp, hp = api.Maps.zeros(g, dev), api.Maps.zeros(g, dev)
+
+    def step():
+        pp.zero_()
+        hp.zero_()
+        model, status = ctx.solve_halos(M, c, z)
+        solved = torch.cuda.Event()
+        solved.record(comp)
+
+        def halo_paste():
+            with torch.cuda.stream(hp_stream):
+                hp_stream.wait_event(solved)
+                ctx_hp.paste_halos(thx, thy, vl, model, status, g, hp)
+                ctx_hp.finalize(g, hp)
+                done = torch.cuda.Event()
+                done.record(hp_stream)
+                return done
+
+        fut = pool.submit(halo_paste)
+        ctx.assign_particles(parts, lc.Mp, pos, model, status, g, out=rec)
+        ctx.paste_particles(rec, g, pp)
+        ctx.finalize(g, pp)
+        comp.wait_event(fut.result())
+
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    work = deposit_work(rec, g.nx, g.ny)
+    ctx.set_timing(True)
+    ctx.phase_times()
+    ms, phases = [], []
+    for k in range(args.c1_steps):
+        flush.fill_(float(k))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        step()
+        e1.record()
+        phases.append(ctx.phase_times())
+        ms.append(e0.elapsed_time(e1))
+    ctx.set_timing(False)
+    mean_ph = {k: round(sum(p[k] for p in phases) / len(phases), 4) for k in phases[0]}
+    t_step = sum(ms) / len(ms)
+    out = {"workload": "PP plain, FP32 deposit: 4e6 particles, 2x2 deg^2 light-cone z 0.05-1.5, "
+                       "3000 halos (60% halo / 40% field particles), 1024^2 y and kSZ maps; "
+                       "plus HP of the 3000 halos (second stream)",
+           "ms_per_step": t_step, "particles_per_s": n / (t_step * 1e-3), "phase_ms": mean_ph,
+           "phase_hbm": phase_bandwidth(mean_ph, n, work[2], g.nx, g.ny,
+                                        float(peaks.get("hbm_gbs", 6780.4))),
+           "roofline": deposit_roofline("k_deposit_tc", mean_ph["deposit"], work, peaks,
+                                        "k_deposit_tc_c1")}
+    ctx.close()
+    ctx_hp.close()
+    return out, lc
+
+
+def hp_catalogue_section(api, dev, args):
+    """HP of the 1000-halo catalogue (1x1 deg^2, 256^2, aperture min(r_f, 3 r500)): solve +
+    halo records, tables and paste, inputs resident, maps zeroed outside the timed region."""
+    import torch
+
+    from paper_2201_02632_gb300 import inputs as I
+
+    cat, gi = I.halo_catalog(n=1000, npix=256)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    M, c, z, thx, thy, vl = (t(a) for a in (cat.M, cat.c, cat.z, cat.thx, cat.thy, cat.vlos))
+    g = api.geom(gi.nx, gi.ny, gi.theta0_x, gi.theta0_y, gi.dtheta)
+    ctx = api.Context()
+    maps = api.Maps.zeros(g, dev)
+
+    def once():
+        model, status = ctx.solve_halos(M, c, z)
+        ctx.paste_halos(thx, thy, vl, model, status, g, maps, ap_r500=3.0)
+        ctx.finalize(g, maps)
+
+    for _ in range(5):
+        maps.zero_()
+        once()
+    torch.cuda.synchronize()
+    ctx.set_timing(True)
+    ctx.phase_times()
+    ms, phases = [], []
+    for _ in range(args.c0_steps):
+        maps.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        once()
+        e1.record()
+        phases.append(ctx.phase_times())
+        ms.append(e0.elapsed_time(e1))
+    ctx.set_timing(False)
+    ctx.close()
+    t_ms = statistics.median(ms)
+    ph = {k: round(statistics.median(p[k] for p in phases), 4) for k in phases[0]
+          if any(p[k] > 0 for p in phases)}
+    return {"workload": "HP plain: 1000 halos (M log-uniform 1e13-1e15 h^-1 Msun, c = 5 "
+                        "(M/1e14)^-0.1 x 0.1 dex, z 0.05-1), 1x1 deg^2, 256^2 maps, aperture "
+                        "min(r_f, 3 r500); FP64 solve, FP32 projected profiles",
+            "ms_per_map": t_ms, "halos_per_s": 1000 / (t_ms * 1e-3), "phase_ms": ph,
+            "note": "median of the timed repetitions; one map per repetition"}
+
+
+def surrogate_section(api, dev, args, c2_cat, npix):
+    """Surrogate vs plain solve: train on solver outputs, time both solves on the same
+    inference halos, and compare the pasted y of the full-scale cone's 2e5 halos on its
+    4096^2 maps with each solve."""
     import torch
 
     from paper_2201_02632_gb300 import inputs as I
     from paper_2201_02632_gb300.surrogate import Surrogate
 
+    ctx = api.Context()
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     M, c, z, prm = I.surrogate_halos(args.sur_train, seed=I.SEED_BASE + 4)
     sur = Surrogate.init(dev, seed=0)
@@ -312,23 +681,25 @@ def surrogate_section(api, ctx, dev, lc, args):
         k = api.MF[name]
         r = (ms[k][ok] / mp[k][ok] - 1).abs()
         rel[name] = {"max": float(r.max()), "median": float(r.median())}
-    # pasted y of the light-cone halos (Table-1 parameters) with each solve
-    cat = lc.halos
-    nh = cat.M.size
+    # pasted y of the full-scale cone's halos (Table-1 parameters) with each solve
+    nh = c2_cat.M.size
     tab1 = np.stack([np.full(nh, 3.97e-6), np.full(nh, 0.026), np.zeros(nh)])
-    hc = [t(cat.M), t(cat.c), t(cat.z)]
-    m1, s1 = ctx.solve_halos_ex(*hc, params=t(tab1))
-    m2, s2 = sur.solve(ctx, *hc, t(tab1))
-    g = api.geom(lc.geom.nx, lc.geom.ny, lc.geom.theta0_x, lc.geom.theta0_y, lc.geom.dtheta)
+    hc = [t(c2_cat.M), t(c2_cat.c), t(c2_cat.z)]
+    m1, s1 = ctx.solve_halos_ex(*hc, params=t(tab1), raise_on_noconv=False)
+    m2, s2 = sur.solve(ctx, *hc, t(tab1), raise_on_noconv=False)
+    half = 0.5 * 5.0 * math.pi / 180.0
+    g = api.geom(npix, npix, -half, -half, 2 * half / npix)
     maps = []
     for m_, s_ in ((m1, s1), (m2, s2)):
         mm = api.Maps.zeros(g, dev)
-        ctx.paste_halos(t(cat.thx), t(cat.thy), t(cat.vlos), m_, s_, g, mm)
+        ctx.paste_halos(t(c2_cat.thx), t(c2_cat.thy), t(c2_cat.vlos), m_, s_, g, mm)
         ctx.finalize(g, mm)
         maps.append(mm.y[0].double())
     y_err = float(torch.linalg.norm(maps[1] - maps[0]) / torch.linalg.norm(maps[0]))
+    ctx.close()
     return {"workload": f"train on {args.sur_train} solver outputs, solve {args.sur_infer} halos "
-                        "(log M 12-15.3, z 0.01-3, eps_* 0-1e-5, f_* 0.01-0.04, eps_DM 0-0.1)",
+                        "(log M 12-15.3, z 0.01-3, eps_* 0-1e-5, f_* 0.01-0.04, eps_DM 0-0.1); "
+                        f"pasted y of the full-scale cone's {nh} halos on {npix}^2 maps",
             "train_s": round(train_s, 2), "train_loss": loss,
             "plain_solve_ms": t_plain, "plain_solve": "FP32 pre-solve + FP64 Newton to 1e-10",
             "surrogate_solve_ms": t_sur,
@@ -341,15 +712,16 @@ def surrogate_section(api, ctx, dev, lc, args):
             "gate": 1e-4, "polish_newton_iters": 4}
 
 
-def hsml_section(api, ctx, dev, lc, args):
-    """SPH smoothing lengths (N_ngb = 64) of the step's light-cone particles: from the grid
+def hsml_section(api, dev, lc):
+    """SPH smoothing lengths (N_ngb = 64) of the 4e6-particle cone's particles: from the grid
     density alone and from the rule-of-thumb h of the generator as starting guesses."""
     import torch
 
+    ctx = api.Context()
     x, y, z = (torch.from_numpy(lc.parts[k]).to(dev) for k in "xyz")
     guess = torch.from_numpy(lc.parts["hsml"]).to(dev)
     n = x.numel()
-    out = {"workload": f"{n} light-cone particles (positions of the pasting step), N_ngb 64"}
+    out = {"workload": f"{n} light-cone particles (positions of the 4e6-particle cone), N_ngb 64"}
     for name, g in (("no_guess", None), ("rule_of_thumb_guess", guess)):
         for _ in range(2):
             h = ctx.smoothing_lengths(x, y, z, 64.0, guess=g)
@@ -364,61 +736,18 @@ def hsml_section(api, ctx, dev, lc, args):
             ts.append(e0.elapsed_time(e1))
         t = float(np.median(ts))
         out[name] = {"ms": t, "particles_per_s": n / (t * 1e-3)}
+    ctx.close()
     return out
 
 
-def allsky_section(api, ctx, dev, args):
-    """All-sky HP maps on HEALPix (nside 8192, RING) from an all-sky catalogue of 4.1e7
-    halos: the solve of every halo and the paste of its projected profiles, inputs resident
-    on the device, maps zeroed before each repetition (outside the timed region)."""
+def spectrum_section(api, dev, dtheta):
+    """Flat-sky C_l (30 logarithmic bins, 1e2-1e5) of a 1024^2 and a 4096^2 map; FP64 FFT
+    (5 n log2 n flops per map)."""
     import torch
 
-    from paper_2201_02632_gb300 import inputs as I
-
-    n, nside = args.allsky_halos, args.allsky_nside
-    cat = I.allsky_catalog(n)
-    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    M, c, z, th, ph, v = (t(cat[k]) for k in ("M", "c", "z", "theta", "phi", "vlos"))
-    del cat
-    maps = api.healpix_maps(nside, dev)
-    reps = []
-    for rep in range(3):
-        maps.zero_()
-        torch.cuda.synchronize()
-        ctx.set_timing(True)
-        ctx.phase_times()
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
-        e[0].record()
-        model, status = ctx.solve_halos(M, c, z, raise_on_noconv=False)
-        e[1].record()
-        ctx.paste_halos_healpix(th, ph, v, model, status, nside, maps)
-        e[2].record()
-        torch.cuda.synchronize()
-        ph_t = {k: round(x, 2) for k, x in ctx.phase_times().items() if x > 0}
-        reps.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), ph_t))
-    ctx.set_timing(False)
-    solve_ms, paste_ms, phases = min(reps[1:], key=lambda r: r[0] + r[1])
-    total = solve_ms + paste_ms
-    y = maps.y
-    out = {"workload": f"{n} halos (dN/dlnM ~ M^-0.9 on 1e12-1e15 h^-1 Msun, uniform in comoving "
-                       f"volume to z 3, isotropic), HEALPix nside {nside} RING "
-                       f"({12 * nside * nside} pixels), y and b with compensation planes",
-           "solve_ms": solve_ms, "paste_ms": paste_ms, "map_ms": total, "phases_ms": phases,
-           "halos_per_s": n / (total * 1e-3),
-           "paper": "170 min on 320 CPU cores for one all-sky map of 4.1e7 halos (Section 5.4)",
-           "covered_pixel_frac": float((y > 0).float().mean())}
-    del maps, model, status
-    torch.cuda.empty_cache()
-    return out
-
-
-def spectrum_section(api, ctx, dev, maps_y, dtheta):
-    """Flat-sky C_l (30 logarithmic bins, 1e2-1e5) of the step's y map and of a 4096^2 map;
-    FP64 FFT (5 n log2 n flops per map)."""
-    import torch
-
+    ctx = api.Context()
     out = {}
-    for name, m, d in (("step_y_map", maps_y, dtheta),
+    for name, m, d in (("map_1024", torch.randn((1024, 1024), device=dev), dtheta),
                        ("map_4096", torch.randn((4096, 4096), device=dev), dtheta / 4)):
         for _ in range(3):
             ctx.power_spectrum(m, d)
@@ -435,10 +764,28 @@ def spectrum_section(api, ctx, dev, maps_y, dtheta):
         npx = m.numel()
         flops = 5.0 * npx * math.log2(npx)
         out[name] = {"shape": list(m.shape), "ms": t, "fp64_tflops": flops / (t * 1e-3) / 1e12}
+    ctx.close()
     return out
 
 
-def batched_section(api, ctx, dev, args):
+def hp_pair_estimate(api, model, thx, thy, g, ap_r500=0.0):
+    """Estimated pixel-halo pairs of a flat HP paste: the pixel centres inside each aperture,
+    pi r_ap^2 in pixels clipped by the share of the aperture's bounding box on the map."""
+    import torch
+
+    MF = api.MF
+    rf, da = model[MF["r_f"]], model[MF["D_A"]]
+    rap = rf if ap_r500 <= 0 else torch.minimum(rf, ap_r500 * model[MF["r500"]])
+    r = rap / da / g.dtheta
+    cx = (thx - g.theta0_x) / g.dtheta
+    cy = (thy - g.theta0_y) / g.dtheta
+    fx = ((cx + r).clamp(0, g.nx) - (cx - r).clamp(0, g.nx)) / (2 * r)
+    fy = ((cy + r).clamp(0, g.ny) - (cy - r).clamp(0, g.ny)) / (2 * r)
+    est = math.pi * r * r * fx * fy
+    return float(torch.nan_to_num(est, nan=0.0).sum())
+
+
+def batched_section(api, dev, args, peaks):
     """Batched HP: many independent maps of uneven halo extents pasted by one prepared
     plan (one persistent launch), autotuned, captured in a CUDA graph and replayed."""
     import torch
@@ -446,6 +793,7 @@ def batched_section(api, ctx, dev, args):
     from paper_2201_02632_gb300 import autotune
     from paper_2201_02632_gb300 import inputs as I
 
+    ctx = api.Context()
     cat, gi = I.batched_catalog(n_maps=args.batch_maps, mean_halos=args.batch_halos,
                                 npix=args.batch_npix)
     t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
@@ -460,9 +808,9 @@ def batched_section(api, ctx, dev, args):
     g = api.geom(gi.nx, gi.ny, gi.theta0_x, gi.theta0_y, gi.dtheta, gi.n_maps)
     maps = api.Maps.zeros(g, dev)
     t0 = time.perf_counter()
+    cache = os.path.join(tempfile.gettempdir(), "bp_autotune_hp.json")
     best = autotune.tune_hp(ctx, thx, thy, vl, model, status, g, maps, map_id=mid,
-                            units=(0, 1024), ctas=(0, 2), reps=2,
-                            cache_path=os.path.join(ROOT, "gpurun_out", "autotune_hp.json"),
+                            units=(0, 1024), ctas=(0, 2), reps=2, cache_path=cache,
                             use_cache=False)
     tune_s = time.perf_counter() - t0
     plan = ctx.hp_plan(thx, thy, model, status, g, 0.0, mid, best["tile"], best["unit"],
@@ -493,9 +841,13 @@ def batched_section(api, ctx, dev, args):
         ms.append(e0.elapsed_time(e1))
     step = sum(ms) / len(ms)
     pairs = plan.pairs
+    pix_pairs = hp_pair_estimate(api, model, thx, thy, g)
     plan.close()
+    ctx.close()
     del maps
     torch.cuda.empty_cache()
+    flops = pix_pairs * 20.0
+    ach = flops / (step * 1e-3) / 1e12
     return {"workload": f"{gi.n_maps} maps of {gi.nx}^2 (5x5 deg^2), {n} halos "
                         f"(Poisson({args.batch_halos:g}) per map), M 1e12-1e15 dN/dlnM ~ M^-0.9, "
                         "z 0.01-3, r_ap = r_f",
@@ -503,62 +855,76 @@ def batched_section(api, ctx, dev, args):
             "halos_per_s": n / (step * 1e-3), "maps_per_s": gi.n_maps / (step * 1e-3),
             "autotuned": {k: best[k] for k in ("tile", "unit", "ctas_per_sm", "ms")},
             "tune_s": round(tune_s, 2), "solve_s_plain_fp64": round(solve_s, 3),
-            "graph_replay": True}
+            "graph_replay": True,
+            "roofline": {"bound": "alu", "pixel_halo_pairs_estimated": pix_pairs,
+                         "flops_per_pair": 20, "achieved": ach, "peak": fp32_peak(peaks),
+                         "unit": "TFLOP/s", "frac": ach / fp32_peak(peaks),
+                         "note": "pairs estimated as pi r_ap^2 per halo clipped to the map; 20 "
+                                 "FP32 flops per pair (distance, table interpolation, two "
+                                 "compensated sums); whole replay (tables, per-pixel values, "
+                                 "paste, reduction) over the FP32 FMA peak"}}
 
 
-def full_scale_section(api, ctx, dev, args, fp32_peak):
-    """The full-scale cone: 5e8 particles, 2e5 halos, 5x5 deg^2 to z = 3, 4096^2 maps."""
+def allsky_section(api, dev, args, peaks):
+    """All-sky HP maps on HEALPix (nside 8192, RING) from an all-sky catalogue of 4.1e7
+    halos: the solve of every halo and the paste of its projected profiles, inputs resident
+    on the device, maps zeroed before each repetition (outside the timed region)."""
     import torch
 
     from paper_2201_02632_gb300 import inputs as I
 
-    t0 = time.perf_counter()
-    lc = I.lightcone_device(n_part=args.full_particles, n_halo=args.full_halos, device=dev)
-    torch.cuda.synchronize()
-    gen_s = time.perf_counter() - t0
-    cat = lc.halos
-    tt = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
-    M, c, z, pos = tt(cat.M), tt(cat.c), tt(cat.z), tt(cat.pos)
-    n = args.full_particles
-    g = api.geom(lc.geom.nx, lc.geom.ny, lc.geom.theta0_x, lc.geom.theta0_y, lc.geom.dtheta)
-    rec = torch.empty((n, api.ASSIGNED_STRIDE), dtype=torch.float32, device=dev)
-    pp = api.Maps.zeros(g, dev)
-
-    def step():
-        pp.zero_()
+    ctx = api.Context()
+    n, nside = args.allsky_halos, args.allsky_nside
+    cat = I.allsky_catalog(n)
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    M, c, z, th, ph, v = (t(cat[k]) for k in ("M", "c", "z", "theta", "phi", "vlos"))
+    del cat
+    maps = api.healpix_maps(nside, dev)
+    reps = []
+    for rep in range(3):
+        maps.zero_()
+        torch.cuda.synchronize()
+        ctx.set_timing(True)
+        ctx.phase_times()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        e[0].record()
         model, status = ctx.solve_halos(M, c, z, raise_on_noconv=False)
-        ctx.assign_particles(lc.parts, lc.Mp, pos, model, status, g, out=rec)
-        ctx.paste_particles(rec, g, pp)
-        ctx.finalize(g, pp)
-
-    step()
-    torch.cuda.synchronize()
-    flops, updates = deposit_flops_device(rec, g.nx, g.ny)
-    ctx.set_timing(True)
-    ctx.phase_times()
-    ms, phases = [], []
-    for _ in range(args.full_steps):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        step()
-        e1.record()
-        phases.append(ctx.phase_times())
-        ms.append(e0.elapsed_time(e1))
+        e[1].record()
+        ctx.paste_halos_healpix(th, ph, v, model, status, nside, maps)
+        e[2].record()
+        torch.cuda.synchronize()
+        ph_t = {k: round(x, 2) for k, x in ctx.phase_times().items() if x > 0}
+        reps.append((e[0].elapsed_time(e[1]), e[1].elapsed_time(e[2]), ph_t))
     ctx.set_timing(False)
-    step_ms = sum(ms) / len(ms)
-    ph = {k: round(sum(p[k] for p in phases) / len(phases), 3) for k in phases[0]}
-    # algorithmic bytes of the streaming phases: assign reads 32 B and writes 32 B per
-    # particle; the pair count reads 32 B per particle
-    assign_gbs = n * 64 / (ph["assign"] * 1e-3) / 1e9 if ph["assign"] > 0 else None
-    dep_tf = flops / (ph["deposit"] * 1e-3) / 1e12 if ph["deposit"] > 0 else None
-    res = {"workload": f"{n} particles, {cat.M.size} halos (dN/dlnM ~ M^-0.9, 1e12-1e15), "
-                       "5x5 deg^2 z 0.05-3, 4096^2 maps", "generate_s": round(gen_s, 2),
-           "ms_per_step": step_ms, "particles_per_s": n / (step_ms * 1e-3), "phase_ms": ph,
-           "deposit_tflops": dep_tf, "deposit_frac_fp32_peak": dep_tf / fp32_peak if dep_tf else None,
-           "pixel_updates": updates, "assign_gbs": assign_gbs}
-    del rec, pp, lc
+    solve_ms, paste_ms, phases = min(reps[1:], key=lambda r: r[0] + r[1])
+    total = solve_ms + paste_ms
+    y = maps.y
+    # pixel-halo pairs: the pixels inside each aperture cap, area pi (r_f / D_A)^2 over the
+    # pixel area 4 pi / (12 nside^2)
+    MF = api.MF
+    ang = model[MF["r_f"]] / model[MF["D_A"]]
+    pix_pairs = float(torch.nan_to_num(math.pi * ang * ang / (4 * math.pi / (12.0 * nside * nside)),
+                                       nan=0.0).sum())
+    flops = pix_pairs * 60.0
+    ach = flops / (paste_ms * 1e-3) / 1e12
+    out = {"workload": f"{n} halos (dN/dlnM ~ M^-0.9 on 1e12-1e15 h^-1 Msun, uniform in comoving "
+                       f"volume to z 3, isotropic), HEALPix nside {nside} RING "
+                       f"({12 * nside * nside} pixels), y and b with compensation planes",
+           "solve_ms": solve_ms, "paste_ms": paste_ms, "map_ms": total, "phases_ms": phases,
+           "halos_per_s": n / (total * 1e-3),
+           "paper": "170 min on 320 CPU cores for one all-sky map of 4.1e7 halos (Section 5.4)",
+           "covered_pixel_frac": float((y > 0).float().mean()),
+           "roofline_paste": {"bound": "alu", "pixel_halo_pairs_estimated": pix_pairs,
+                              "flops_per_pair": 60, "achieved": ach, "peak": fp32_peak(peaks),
+                              "unit": "TFLOP/s", "frac": ach / fp32_peak(peaks),
+                              "note": "pairs estimated as the aperture cap area over the pixel "
+                                      "area; 60 FP32 flops per pair (haversine, asin, two "
+                                      "interpolations); the paste phase (pairs, per-pixel "
+                                      "values, segment paste) over the FP32 FMA peak"}}
+    ctx.close()
+    del maps, model, status
     torch.cuda.empty_cache()
-    return res
+    return out
 
 
 def run_ours(args):
@@ -572,283 +938,58 @@ def run_ours(args):
         dist.init_process_group("nccl")
     from paper_2201_02632_gb300 import api
     from paper_2201_02632_gb300 import build as B
-    from paper_2201_02632_gb300 import inputs as I
 
     B.build()
-    # each rank pastes its own light-cone realisation (independent maps, no collective)
-    lc = I.lightcone(n_part=args.particles, seed=replica_seed(rank, I.SEED_BASE))
-    n = lc.parts["x"].size
-    cat = lc.halos
-    nh = cat.M.size
     dev = torch.device("cuda", local)
-    ctx = api.Context()
-    ctx.set_deposit_kernel(args.deposit_kernel)
-    # the halo paste needs only the solve: a second context on its own stream (fed by a
-    # host thread, since the list build synchronises its stream) runs it beside the particle
-    # chain (assign, pairs, sort, deposit)
-    comp = torch.cuda.current_stream()
-    hp_stream = torch.cuda.Stream()
-    ctx_hp = api.Context(stream=hp_stream)
-    hp_pool = concurrent.futures.ThreadPoolExecutor(1)
-    uses_tc = args.deposit_kernel in ("auto", "tensor")
-    g = api.geom(lc.geom.nx, lc.geom.ny, lc.geom.theta0_x, lc.geom.theta0_y, lc.geom.dtheta)
-
-    host = {k: torch.from_numpy(v).pin_memory() for k, v in lc.parts.items()}
-    hM = torch.from_numpy(cat.M).pin_memory()
-    hc = torch.from_numpy(cat.c).pin_memory()
-    hz = torch.from_numpy(cat.z).pin_memory()
-    hpos = torch.from_numpy(cat.pos).pin_memory()
-    hthx = torch.from_numpy(cat.thx).pin_memory()
-    hthy = torch.from_numpy(cat.thy).pin_memory()
-    hv = torch.from_numpy(cat.vlos).pin_memory()
-    h_in = list(host.values()) + [hM, hc, hz, hpos, hthx, hthy, hv]
-    d_in = [t.to(dev) for t in h_in]
-    parts_d = dict(zip(host.keys(), d_in[:len(host)]))
-    M, c, z, pos, thx, thy, vl = d_in[len(host):]
-    rec = torch.empty((n, api.ASSIGNED_STRIDE), dtype=torch.float32, device=dev)
-    pp = api.Maps.zeros(g, dev)
-    hp = api.Maps.zeros(g, dev)
-    out_host = [torch.empty((g.ny, g.nx), dtype=torch.float32).pin_memory() for _ in range(4)]
-    h2d_bytes = sum(t.numel() * t.element_size() for t in h_in)
-    d2h_bytes = sum(t.numel() * t.element_size() for t in out_host)
-
-    def step(ins=None, maps=None):
-        """One pass of the hot path; ins: the device inputs (default the resident set),
-        maps: the (PP, HP) maps to fill (default pp, hp)."""
-        ins = d_in if ins is None else ins
-        mpp, mhp = (pp, hp) if maps is None else maps
-        parts = dict(zip(host.keys(), ins[:len(host)]))
-        hM_, hc_, hz_, hpos_, hthx_, hthy_, hv_ = ins[len(host):]
-        mpp.zero_()
-        mhp.zero_()
-        model, status = ctx.solve_halos(hM_, hc_, hz_)
-        solved = torch.cuda.Event()
-        solved.record(comp)
-
-        def halo_paste():
-            with torch.cuda.stream(hp_stream):
-                hp_stream.wait_event(solved)
-                ctx_hp.paste_halos(hthx_, hthy_, hv_, model, status, g, mhp)
-                ctx_hp.finalize(g, mhp)
-                done = torch.cuda.Event()
-                done.record(hp_stream)
-                return done
-
-        fut = hp_pool.submit(halo_paste)
-        ctx.assign_particles(parts, lc.Mp, hpos_, model, status, g, out=rec)
-        ctx.paste_particles(rec, g, mpp)
-        ctx.finalize(g, mpp)
-        comp.wait_event(fut.result())  # the maps and the model are released after both
-
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
-
-    def barrier():
-        if world > 1:
-            torch.distributed.barrier()
-        torch.cuda.synchronize()
-
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    flops, updates = deposit_flops(rec.cpu().numpy(), g.nx, g.ny)
-    tile_pairs = int(ctx.pp_pairs(rec, g, 64)[0].numel())
-    ctx.set_timing(True)
-    ctx_hp.set_timing(True)
-    ctx.phase_times()
-    ctx_hp.phase_times()
-
-    sampler = ClockSampler(local)
-    barrier()
-    if rank == 0:
-        sampler.start()
-    launches0 = ctx.kernel_launches() + ctx_hp.kernel_launches()
-    step_ms, dep_ms, phases = [], [], []
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        step()
-        e1.record()
-        ph = ctx.phase_times()  # synchronises the stream
-        ph_hp = ctx_hp.phase_times()  # elapsed on the second stream (overlapped, with waits)
-        ph["hp_stream_total"] = sum(ph_hp.values())
-        step_ms.append(e0.elapsed_time(e1))
-        dep_ms.append(ph["deposit"])
-        phases.append(ph)
-    barrier()
-    launches = ctx.kernel_launches() + ctx_hp.kernel_launches() - launches0
-    clocks = sampler.stop() if rank == 0 else None
-    ctx_hp.set_timing(False)
-    # the HP phases timed alone (solve, then the halo paste on one stream) for their own
-    # breakdown and the halos/s figure; in the step they overlap the particle chain
-    hp_alone_ms, hp_phases = [], []
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        model_a, status_a = ctx.solve_halos(M, c, z)
-        ctx.paste_halos(thx, thy, vl, model_a, status_a, g, hp)
-        e1.record()
-        hp_phases.append(ctx.phase_times())
-        hp_alone_ms.append(e0.elapsed_time(e1))
-    ctx.set_timing(False)
-    t_step = max_over_ranks(sum(step_ms) / len(step_ms), world, dev)
-
-    # end to end through the public API: inputs from pinned host memory, maps back
-    e2e_ms = []
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for hsrc, ddst in zip(h_in, d_in):
-            ddst.copy_(hsrc, non_blocking=True)
-        step()
-        for hdst, dsrc in zip(out_host, (pp.y[0], pp.b[0], hp.y[0], hp.b[0])):
-            hdst.copy_(dsrc, non_blocking=True)
-        e1.record()
-        torch.cuda.synchronize()
-        e2e_ms.append(e0.elapsed_time(e1))
-    t_e2e_serial = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world, dev)
-
-    # the same, pipelined as a production loop runs it: an upload stream copies step k + 1's
-    # inputs and a download stream reads step k - 1's maps back while step k computes (inputs
-    # and result maps double-buffered); every step's uploads, L2 flush, compute and downloads
-    # lie inside the timed region, which runs from the first upload to the last download
-    up, down = torch.cuda.Stream(), torch.cuda.Stream()
-    ins2 = [d_in, [torch.empty_like(t) for t in d_in]]
-    maps2 = [(pp, hp), (api.Maps.zeros(g, dev), api.Maps.zeros(g, dev))]
-    outs2 = [out_host, [torch.empty((g.ny, g.nx), dtype=torch.float32).pin_memory()
-                        for _ in range(4)]]
-    ev = lambda: torch.cuda.Event(enable_timing=False)
-    in_ready = [ev() for _ in range(args.steps)]
-    done = [ev() for _ in range(args.steps)]
-    drained = [ev() for _ in range(args.steps)]
-
-    def upload(k):
-        with torch.cuda.stream(up):
-            if k >= 2:
-                up.wait_event(done[k - 2])  # step k - 2 no longer reads this input set
-            for hsrc, ddst in zip(h_in, ins2[k % 2]):
-                ddst.copy_(hsrc, non_blocking=True)
-            in_ready[k].record(up)
-
-    torch.cuda.synchronize()
-    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0.record(up)
-    upload(0)
-    for k in range(args.steps):
-        b = k % 2
-        if k + 1 < args.steps:
-            upload(k + 1)  # queued before step k's host-synchronising calls
-        comp.wait_event(in_ready[k])
-        if k >= 2:
-            comp.wait_event(drained[k - 2])  # those maps have been read back
-        flush.fill_(float(k))
-        step(ins2[b], maps2[b])
-        done[k].record(comp)
-        with torch.cuda.stream(down):
-            down.wait_event(done[k])
-            m_pp, m_hp = maps2[b]
-            for hdst, dsrc in zip(outs2[b], (m_pp.y[0], m_pp.b[0], m_hp.y[0], m_hp.b[0])):
-                hdst.copy_(dsrc, non_blocking=True)
-            drained[k].record(down)
-    down.wait_event(drained[args.steps - 1])
-    t1.record(down)
-    torch.cuda.synchronize()
-    t_e2e = max_over_ranks(t0.elapsed_time(t1) / args.steps, world, dev)
-
+    peaks = measured_peaks()
+    head, c2_cat = headline(api, args, dev, rank, world, peaks)
     if rank != 0:
         if world > 1:
             torch.distributed.destroy_process_group()
         return 0
-
-    mean_ph = {k: round(sum(p[k] for p in phases) / len(phases), 4) for k in phases[0]}
-    for key in ("hp_table", "hp_pairs", "hp_paste"):
-        mean_ph[key] = round(sum(p[key] for p in hp_phases) / len(hp_phases), 4)
-    dep = sum(dep_ms) / len(dep_ms)
-    peaks = measured_peaks()
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
-    achieved = flops / (dep * 1e-3) / 1e12
-    if uses_tc:
-        # TF32 dense peak: the measured cuBLAS bf16 burst x the nominal TF32 / BF16 ratio
-        tf32_peak = float(peaks.get("bf16_tflops", 1900.0)) * (1.1 / 2.25)
-        # MMA work the kernel issues: per (tile, particle) pair a 128 x 64 rank-1 update
-        # in three split-TF32 products
-        mma_flops = tile_pairs * 128 * 64 * 2 * 3
-        roofline = {"kernel": "k_deposit_tc", "bound": "tensor", "achieved": achieved,
-                    "peak": tf32_peak, "unit": "TFLOP/s", "frac": achieved / tf32_peak,
-                    "traffic": ncu_traffic("k_deposit_tc_c1"), "deposit_ms": dep,
-                    "algorithmic_flops_per_launch": flops, "pixel_updates": updates,
-                    "tile_pairs": tile_pairs, "mma_flops_issued_per_launch": mma_flops,
-                    "mma_tflops_issued": mma_flops / (dep * 1e-3) / 1e12,
-                    "frac_fp32_alu_peak": achieved / fp32_peak,
-                    "peak_note": "of measured: bf16 burst 1901.5 TFLOP/s x 1.1/2.25 (nominal "
-                                 "TF32/BF16 dense ratio)"}
-    else:
-        roofline = {"kernel": "k_deposit<64>", "bound": "alu", "achieved": achieved,
-                    "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
-                    "traffic": ncu_traffic("k_deposit_c1"), "deposit_ms": dep,
-                    "algorithmic_flops_per_launch": flops, "pixel_updates": updates,
-                    "peak_note": "FP32 FMA: 152 SMs x 128 lanes x 2 flop x max SM clock"}
-    hp_ms = sum(hp_alone_ms) / len(hp_alone_ms)
     res = {
-        "metric": METRIC, "value": job_rate(n, world, t_step), "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "particles": n, "halos": nh,
-                   "maps": f"{g.nx}x{g.ny}", "pp_tile": 64,
-                   "deposit_kernel": "tcgen05 split-TF32" if uses_tc else "SIMT FP32",
-                   "l2": "flushed: 256 MB write "
-                   "between timed steps", "parallelism": f"replicas x{world} (weak)"},
-        "hp_halos_per_s": nh / (hp_ms * 1e-3) if hp_ms > 0 else None,
-        "phase_hbm": phase_bandwidth(mean_ph, n, tile_pairs, g.nx, g.ny,
-                                     float(peaks.get("hbm_gbs", 6785.9))),
-        "phase_ms": mean_ph,
-        "phase_note": "solve .. finalize: the particle chain on the main stream; hp_*: the "
-                      "halo paste timed alone (in the step it runs on a second stream beside "
-                      "the particle chain, hp_stream_total = its elapsed time there)",
-        "roofline": roofline,
-        "e2e": {"value": job_rate(n, world, t_e2e), "unit": UNIT,
-                "h2d_bytes_per_step": h2d_bytes, "d2h_bytes_per_step": d2h_bytes,
-                "ms_per_step": t_e2e, "pipelined": "copies of steps k +- 1 overlap step k",
-                "serial_ms_per_step": t_e2e_serial,
-                "serial_value": job_rate(n, world, t_e2e_serial)},
-        "gpu_launches": launches,
-        "clocks": clocks,
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True, "scaling": "strong" if world > 1 else "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config(args, world),
+        "roofline": head["roofline"], "e2e": head["e2e"], "gpu_launches": head["gpu_launches"],
+        "clocks": head["clocks"], "phase_ms": head["phase_ms"], "phase_note": head["phase_note"],
+        "phase_hbm": head["phase_hbm"], "inputs": head["inputs"],
     }
-    if not args.no_surrogate:
-        res["surrogate"] = surrogate_section(api, ctx, dev, lc, args)
-    if not args.no_hsml:
-        res["smoothing_lengths"] = hsml_section(api, ctx, dev, lc, args)
-    if not args.no_spectrum:
-        res["power_spectrum"] = spectrum_section(api, ctx, dev, pp.y[0], g.dtheta)
-    if not args.no_batched:
-        res["batched_hp"] = batched_section(api, ctx, dev, args)
-    if not args.no_allsky:
-        res["allsky_hp"] = allsky_section(api, ctx, dev, args)
-    if not args.no_full_scale:
-        res["pp_full_scale"] = full_scale_section(api, ctx, dev, args, fp32_peak)
-    if not args.no_cpu_baseline and world == 1:
-        threads = os.cpu_count() or 1
-        t_full, det = oracle_sample(lc, args.ref_particles, args.ref_halos, threads)
-        res["cpu_baseline"] = {
-            "value": n / t_full, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": (f"FP64 oracle: solve of all {nh} halos, assign+deposit of "
-                       f"{det['n_part_sample']} particles, HP of {det['n_halo_sample']} "
-                       f"halos, extrapolated linearly to the full step"), "detail": det}
-        if "smoothing_lengths" in res:  # the oracle's smoothing lengths at 8 particles
-            import oracle as O
+    if world == 1:
+        c1, lc1 = lightcone_4m_section(api, dev, args, peaks) if not args.no_c1 else (None, None)
+        if c1:
+            res["pp_lightcone_4m"] = c1
+        if not args.no_c0:
+            res["hp_catalogue_1000"] = hp_catalogue_section(api, dev, args)
+        if not args.no_surrogate:
+            res["surrogate"] = surrogate_section(api, dev, args, c2_cat, args.npix)
+        if lc1 is not None and not args.no_hsml:
+            res["smoothing_lengths"] = hsml_section(api, dev, lc1)
+        if not args.no_spectrum:
+            res["power_spectrum"] = spectrum_section(api, dev, 2.0 * math.pi / 180.0 / 1024)
+        if not args.no_batched:
+            res["batched_hp"] = batched_section(api, dev, args, peaks)
+        if not args.no_allsky:
+            res["allsky_hp"] = allsky_section(api, dev, args, peaks)
+        if not args.no_cpu_baseline:
+            threads = os.cpu_count() or 1
+            slc = sample_cone(args)
+            t_s, n_s, det = oracle_sample_step(slc, threads)
+            res["cpu_baseline"] = {"value": n_s / t_s, "unit": UNIT, "cores": threads,
+                                   "kind": "oracle", "sample": sample_text(slc), "detail": det}
+            if lc1 is not None and "smoothing_lengths" in res:
+                import oracle as O
 
-            idx = np.arange(0, n, n // 8)[:8]
-            t0 = time.perf_counter()
-            O.smoothing_lengths_at(lc.parts["x"], lc.parts["y"], lc.parts["z"], idx, 64.0,
-                                   nthreads=threads)
-            dt = time.perf_counter() - t0
-            res["smoothing_lengths"]["cpu_oracle"] = {
-                "particles_per_s": idx.size / dt, "sample": f"{idx.size} particles of the {n}",
-                "cores": threads, "kind": "oracle"}
+                n1 = lc1.parts["x"].size
+                idx = np.arange(0, n1, n1 // 8)[:8]
+                t0 = time.perf_counter()
+                O.smoothing_lengths_at(lc1.parts["x"], lc1.parts["y"], lc1.parts["z"], idx, 64.0,
+                                       nthreads=threads)
+                dt = time.perf_counter() - t0
+                res["smoothing_lengths"]["cpu_oracle"] = {
+                    "particles_per_s": idx.size / dt, "sample": f"{idx.size} particles of {n1}",
+                    "cores": threads, "kind": "oracle"}
     print(json.dumps(res))
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -858,14 +999,17 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--particles", type=int, default=4_000_000)
-    ap.add_argument("--ref-particles", type=int, default=1_000_000)
-    ap.add_argument("--ref-halos", type=int, default=600)
-    ap.add_argument("--deposit-kernel", default="auto", choices=["auto", "simt", "tensor"])
+    ap.add_argument("--particles", type=int, default=500_000_000)
+    ap.add_argument("--halos", type=int, default=200_000)
+    ap.add_argument("--npix", type=int, default=4096)
+    ap.add_argument("--c1-steps", type=int, default=10)
+    ap.add_argument("--c0-steps", type=int, default=30)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-c1", action="store_true")
+    ap.add_argument("--no-c0", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-hsml", action="store_true")
@@ -873,10 +1017,6 @@ def main():
     ap.add_argument("--no-spectrum", action="store_true")
     ap.add_argument("--allsky-halos", type=int, default=41_000_000)
     ap.add_argument("--allsky-nside", type=int, default=8192)
-    ap.add_argument("--no-full-scale", action="store_true")
-    ap.add_argument("--full-particles", type=int, default=500_000_000)
-    ap.add_argument("--full-halos", type=int, default=200_000)
-    ap.add_argument("--full-steps", type=int, default=3)
     ap.add_argument("--batch-maps", type=int, default=108)
     ap.add_argument("--batch-halos", type=float, default=5e4)
     ap.add_argument("--batch-npix", type=int, default=2048)

@@ -339,12 +339,18 @@ def surrogate_halos(n, seed=SEED_BASE + 4):
 
 def lightcone_device(n_part, n_halo, side_deg=5.0, zr=(0.05, 3.0), halo_frac=0.6, npix=4096,
                      seed=SEED_BASE + 2, mass="powerlaw", n_ngb=64, device="cuda",
-                     chunk=50_000_000):
+                     chunk=50_000_000, sample=None):
     """The light-cone recipe of `lightcone`, drawn with torch's seeded generator on a
     device so that 1e8-1e9 particles take seconds (the numpy generator would take
     minutes).  Same distributions; different random streams, so it is its own seeded
     workload.  Returns a LightCone whose parts are device tensors (halo catalogue on
-    the host)."""
+    the host).
+
+    sample=(halo_keep, field_keep): a representative subsample of the same cone for
+    timing slow consumers: the full halo catalogue, a seeded subset of its halos (each
+    kept with probability halo_keep) with all of their particles, and a field_keep share
+    of the field particles.  Particle mass, smoothing lengths and everything else are
+    those of the full cone (n_part particles); the particles are different draws."""
     import torch
 
     dev = torch.device(device)
@@ -402,6 +408,12 @@ def lightcone_device(n_part, n_halo, side_deg=5.0, zr=(0.05, 3.0), halo_frac=0.6
     n_f = n_part - n_h
     n_field = n_f / vol
     h_field = (3.0 * n_ngb / (4.0 * math.pi * n_field)) ** (1.0 / 3.0)
+    if sample is not None:  # a subset of the halos with all their particles, part of the field
+        keep = np.random.default_rng(seed + 7919).random(n_halo) < sample[0]
+        cnt = np.where(keep, cnt, 0)
+        n_h = int(cnt.sum())
+        n_f = int(round(n_f * sample[1]))
+        n_part = n_h + n_f
     td = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
     c_t, R_t, M_t = td(c.astype(np.float32)), td(R.astype(np.float32)), td(M)
     sc_t = td((np.stack([np.ones(n_halo), q, s], 1) / np.cbrt(q * s)[:, None]).astype(np.float32))
@@ -458,4 +470,8 @@ def lightcone_device(n_part, n_halo, side_deg=5.0, zr=(0.05, 3.0), halo_frac=0.6
         parts[k] = torch.randn(n_part, generator=gen, device=dev, dtype=f32) * 300.0
     cat = HaloCatalog(M, c, hz, thx, thy, hv, pos=hpos.T.astype(np.float32).copy())
     g = MapGeom(npix, npix, -half, -half, 2 * half / npix)
-    return LightCone(parts, cat, Mp, g, {"h_field": h_field, "n_halo_particles": n_h})
+    meta = {"h_field": h_field, "n_halo_particles": n_h}
+    if sample is not None:
+        meta["sample"] = {"halo_keep": sample[0], "field_keep": sample[1],
+                          "halos_kept": int(keep.sum()), "particles": n_part}
+    return LightCone(parts, cat, Mp, g, meta)
