@@ -171,6 +171,13 @@ int bp_set_tiling(bp_ctx* ctx, int pp_tile, int hp_tile, int pp_unit);
 #define BP_DEPOSIT_SIMT 1
 #define BP_DEPOSIT_TENSOR 2
 int bp_set_deposit_kernel(bp_ctx* ctx, int kind);
+/* With the tensor-core deposit, particles whose pixel box (clipped to the map) is at most
+ * `span` pixels on both axes are deposited by a second kernel instead (one CTA per tile, one
+ * thread per particle, the same cell weights, exact 64-bit fixed-point sums in shared memory:
+ * deterministic), added after the large particles of each tile.  span: 0 (every particle on
+ * the tensor cores) .. 8, or -1 (the default): 8 when the map has at least 4 tiles of 64
+ * pixels per SM, else 0.  BP_EINVAL outside [-1, 8]. */
+int bp_set_small_span(bp_ctx* ctx, int span);
 /* Test of the bounded waits (not in the paper): when polls > 0, every CTA of the context's
  * later tensor-core deposits first waits, for at most `polls` reads, on a device flag that
  * nothing sets, before it issues any MMA or writes anything; the deposit then gives up,
@@ -196,7 +203,8 @@ int64_t bp_workspace_bytes(const bp_ctx* ctx);
 #define BP_PH_HP_PASTE 8  /* HP paste and reduction */
 #define BP_PH_FINALIZE 9
 #define BP_PH_SURROGATE 10 /* surrogate features + BF16 inference */
-#define BP_NPHASES 11
+#define BP_PH_DEPOSIT_SMALL 11 /* small-particle deposit (bp_set_small_span) */
+#define BP_NPHASES 12
 int bp_set_timing(bp_ctx* ctx, int on);
 int bp_phase_times(bp_ctx* ctx, double* ms, int n);
 /* Number of kernels this context has launched since it was created. */

@@ -26,7 +26,7 @@ OUT_YB, OUT_DT = 0, 1
 
 # entry points declared in include/bp.h
 EXPORTS = ("bp_create", "bp_destroy", "bp_last_error", "bp_set_stream", "bp_set_tiling",
-           "bp_set_deposit_kernel", "bp_set_wait_test",
+           "bp_set_deposit_kernel", "bp_set_wait_test", "bp_set_small_span",
            "bp_workspace_bytes", "bp_set_timing", "bp_phase_times", "bp_kernel_launches",
            "bp_solve_halos", "bp_assign_particles", "bp_paste_particles", "bp_pp_pairs",
            "bp_smoothing_lengths", "bp_paste_halos_healpix", "bp_power_spectrum",
@@ -42,7 +42,7 @@ MLP_NPARAMS = 128 * 6 + 128 + 2 * (128 * 128 + 128) + 3 * 128 + 3
 MLP_NWEIGHTS = 128 * 6 + 2 * 128 * 128 + 3 * 128
 MLP_CACHE_PER_ROW = 6 * 128
 PHASES = ("solve", "assign", "pairs", "sort", "deposit", "reduce", "hp_table", "hp_pairs",
-          "hp_paste", "finalize", "surrogate")
+          "hp_paste", "finalize", "surrogate", "deposit_small")
 
 
 class BpCosmology(C.Structure):
@@ -83,6 +83,7 @@ def load():
                 "bp_set_tiling": (i32, [P, i32, i32, i32]),
                 "bp_set_deposit_kernel": (i32, [P, i32]),
                 "bp_set_wait_test": (i32, [P, i64]),
+                "bp_set_small_span": (i32, [P, i32]),
                 "bp_workspace_bytes": (i64, [P]),
                 "bp_set_timing": (i32, [P, i32]),
                 "bp_phase_times": (i32, [P, C.POINTER(C.c_double), i32]),

@@ -122,6 +122,10 @@ class Context:
         code = {"auto": 0, "simt": 1, "tensor": 2}[kind]
         self._check(self._L.bp_set_deposit_kernel(self._h, code))
 
+    def set_small_span(self, span: int):
+        """bp_set_small_span: the largest pixel span of the small-particle deposit (0: off)."""
+        self._check(self._L.bp_set_small_span(self._h, int(span)))
+
     def set_wait_test(self, polls: int):
         """bp_set_wait_test: make the tensor-core deposit's first wait run out (polls > 0)."""
         self._check(self._L.bp_set_wait_test(self._h, int(polls)))

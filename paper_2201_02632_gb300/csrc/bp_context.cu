@@ -217,6 +217,7 @@ int bp_create(bp_ctx** out, const bp_cosmology* cosmo, const bp_icm_params* icm,
   ctx->hp_tile = 32;
   ctx->pp_unit = 0;  // automatic
   ctx->pp_kernel = BP_DEPOSIT_AUTO;
+  ctx->small_span = -1;  // automatic
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -289,6 +290,14 @@ int bp_set_deposit_kernel(bp_ctx* ctx, int kind) {
   if (kind != BP_DEPOSIT_AUTO && kind != BP_DEPOSIT_SIMT && kind != BP_DEPOSIT_TENSOR)
     return bp_fail(ctx, BP_EINVAL, "bp_set_deposit_kernel: unknown kind %d", kind);
   ctx->pp_kernel = kind;
+  return BP_OK;
+}
+
+int bp_set_small_span(bp_ctx* ctx, int span) {
+  if (!ctx) return BP_EINVAL;
+  if (span < -1 || span > 8)
+    return bp_fail(ctx, BP_EINVAL, "bp_set_small_span: span outside [-1, 8]");
+  ctx->small_span = span;
   return BP_OK;
 }
 

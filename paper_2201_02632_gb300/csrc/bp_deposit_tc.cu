@@ -58,9 +58,8 @@ constexpr int TC_RING = 3;       // record ring per warp (chunks)
 constexpr uint32_t TC_COLS = 256;
 constexpr uint32_t COL_HI = 128, COL_LO = 192;
 constexpr uint32_t TC_IDESC = bptc::idesc_tf32(128, TC_TS);
-// (2/3)^(1/4) and (8/3)^(1/4): t^4 and s^4 of the scaled arguments carry the quartic's weights
-constexpr float KT = 0.9036020040512085f;
-constexpr float KS = 1.277886152267456f;
+constexpr float KT = BP_KT;
+constexpr float KS = BP_KS;
 constexpr float NGP_IH = 1.0e38f;  // 1/h of a particle with h = 0
 constexpr float FAR = -1.0e6f;     // tile position of an empty slot
 #ifndef TC_SLEEP_NS
@@ -108,15 +107,9 @@ __device__ __forceinline__ void st_quad(unsigned char* base, int off, const floa
   *reinterpret_cast<float4*>(base + off) = make_float4(v[0], v[1], v[2], v[3]);
 }
 
-// Edge value in the split representation: w(u) for dx < 0, w(u) - 1 = -w(-u) for dx >= 0,
-// u = dx / h, from |dx| and the scales k1 = KT / h, k2 = KS / h.  dx is never -0 (it is an
-// integer-valued float minus a fraction f >= 0).
+// Edge value in the split representation (bp_edge_split).
 __device__ __forceinline__ float edge_split(float dx, float k1, float k2) {
-  const float t = fmaxf(fmaf(-k1, fabsf(dx), KT), 0.f);         // KT (1 - a), clipped
-  const float s = fmaxf(fmaf(-k2, fabsf(dx), 0.5f * KS), 0.f);  // KS (1/2 - a), clipped
-  const float A = t * t, B = s * s;
-  const float w = fmaf(A, A, -(B * B));
-  return __int_as_float(__float_as_int(w) ^ (~__float_as_int(dx) & (int)0x80000000));
+  return bp_edge_split(dx, k1, k2);
 }
 
 // Weights of cells l and l + 32 of one axis for one particle (all lanes of the warp call this

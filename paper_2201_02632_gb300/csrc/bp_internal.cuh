@@ -73,7 +73,8 @@ struct PpPrepared {
   int64_t n;
   bp_map_geom g;
   int select, ts, unit;
-  int64_t np, n_tiles, max_units, n_slots;
+  int ks;  // 2: keys 4 tile + size class (classes 1-3: the small-particle deposit)
+  int64_t np, n_tiles, n_keys, max_units, n_slots;
   const uint32_t* vals;
   int64_t *tstart, *uoff, *soff;
   void* units;
@@ -95,6 +96,7 @@ struct bp_ctx {
   int num_sms;
   int pp_tile, hp_tile, pp_unit, hp_unit;
   int pp_kernel;  // BP_DEPOSIT_*
+  int small_span; // particles at most this many pixels wide take the small-particle deposit
   int timing;
   cudaEvent_t ev[BP_NPHASES][2];
   double ph_ms[BP_NPHASES];
@@ -180,6 +182,23 @@ __device__ __forceinline__ float bp_wsplit_inv(float dx, float inv_h) {
   const float wl = a < 0.5f ? wi : wo;
   // dx >= 0: flip the sign of wl
   return __int_as_float(__float_as_int(wl) ^ (~__float_as_int(dx) & (int)0x80000000));
+}
+
+// The integrated kernel at a cell edge in the same split representation, from the truncated-
+// power form of the piecewise quartic: with a = |dx| / h,
+//   w_left(a) = (2/3) max(1 - a, 0)^4 - (8/3) max(1/2 - a, 0)^4,
+// (the inner piece 1/2 - (4/3) a + (8/3) a^3 - 2 a^4 below a = 1/2, the outer piece
+// (2/3)(1 - a)^4 above, zero beyond a = 1), from |dx| and the scales k1 = BP_KT / h,
+// k2 = BP_KS / h: no branch, no piece selection.  h = 0 is an infinite scale (k1, k2 = BP_KT,
+// BP_KS x 1e38): every edge off the particle is 0.  dx must not be -0 or 0 with h = 0.
+constexpr float BP_KT = 0.9036020040512085f;  // (2/3)^(1/4)
+constexpr float BP_KS = 1.277886152267456f;   // (8/3)^(1/4)
+__device__ __forceinline__ float bp_edge_split(float dx, float k1, float k2) {
+  const float t = fmaxf(fmaf(-k1, fabsf(dx), BP_KT), 0.f);            // KT (1 - a), clipped
+  const float s = fmaxf(fmaf(-k2, fabsf(dx), 0.5f * BP_KS), 0.f);     // KS (1/2 - a), clipped
+  const float A = t * t, B = s * s;
+  const float w = fmaf(A, A, -(B * B));
+  return __int_as_float(__float_as_int(w) ^ (~__float_as_int(dx) & (int)0x80000000));
 }
 
 // Pixel span of a particle at px = ix + fx with kernel radius h, decided in FP32

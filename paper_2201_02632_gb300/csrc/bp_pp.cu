@@ -234,9 +234,12 @@ __global__ void __launch_bounds__(256) k_assign(AssignArgs a, BpTables T) {
 }
 
 // ---------------------------------------------------------------- pairs
+// The tiles a particle's clipped pixel box touches, and its size class: 0 when the box is
+// wider than `sspan` pixels on an axis (or sspan is 0), else 1, 2, 3 for a box at most 2, 4,
+// 8 pixels on both axes (the small-particle deposit takes them grouped by size).
 __device__ __forceinline__ bool particle_tiles(const float4 r0, const float4 r1, int nx, int ny,
                                                int ts, int select, int& tx0, int& tx1, int& ty0,
-                                               int& ty1) {
+                                               int& ty1, int sspan, int& cls) {
   int kind = __float_as_int(r1.y);
   if (kind == BP_KIND_NONE) return false;
   if (select == BP_SELECT_HALO && kind != BP_KIND_HALO) return false;
@@ -244,6 +247,8 @@ __device__ __forceinline__ bool particle_tiles(const float4 r0, const float4 r1,
   int i0, i1, j0, j1;
   if (!bp_span(__float_as_int(r1.z), r0.x, r0.z, nx, i0, i1)) return false;
   if (!bp_span(__float_as_int(r1.w), r0.y, r0.z, ny, j0, j1)) return false;
+  const int span = max(i1 - i0, j1 - j0) + 1;
+  cls = span > sspan ? 0 : (span <= 2 ? 1 : (span <= 4 ? 2 : 3));
   tx0 = i0 / ts;
   tx1 = i1 / ts;
   ty0 = j0 / ts;
@@ -255,31 +260,37 @@ __global__ void k_pair_count(const float4* __restrict__ rec, int64_t n, int nx, 
                              int select, uint32_t* counts) {
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  int tx0, tx1, ty0, ty1;
+  int tx0, tx1, ty0, ty1, cls;
   uint32_t c = 0;
-  if (particle_tiles(rec[2 * i], rec[2 * i + 1], nx, ny, ts, select, tx0, tx1, ty0, ty1))
+  if (particle_tiles(rec[2 * i], rec[2 * i + 1], nx, ny, ts, select, tx0, tx1, ty0, ty1, 0,
+                     cls))
     c = (uint32_t)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
   counts[i] = c;
 }
 
 // The warp's particles own one contiguous range of pairs (offs is their exclusive scan):
 // lanes write it 32 consecutive pairs at a time, each finding its particle by a binary
-// search over the warp's 32 offsets (shuffles), so that every store is coalesced.
+// search over the warp's 32 offsets (shuffles), so that every store is coalesced.  With
+// sspan > 0 the key is 4 tile + the particle's size class (particle_tiles: 0 for the
+// tensor-core deposit, 1-3 for the small-particle deposit); with sspan = 0 it is the tile.
 __global__ void k_pair_emit(const float4* __restrict__ rec, int64_t n, int nx, int ny, int ts,
                             int select, int ntx, const int64_t* __restrict__ offs,
-                            uint32_t* keys, uint32_t* vals) {
+                            uint32_t* keys, uint32_t* vals, int sspan) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const int64_t i0 = i - lane;
   if (i0 >= n) return;  // the whole warp
-  int tx0 = 0, ty0 = 0, w = 1, cnt = 0;
+  int tx0 = 0, ty0 = 0, w = 1, cnt = 0, cls = 0;
   if (i < n) {
-    int tx1, ty1;
-    if (particle_tiles(rec[2 * i], rec[2 * i + 1], nx, ny, ts, select, tx0, tx1, ty0, ty1)) {
+    int tx1, ty1, c = 0;
+    if (particle_tiles(rec[2 * i], rec[2 * i + 1], nx, ny, ts, select, tx0, tx1, ty0, ty1, sspan,
+                       c)) {
       w = tx1 - tx0 + 1;
       cnt = w * (ty1 - ty0 + 1);
+      cls = c;
     }
   }
+  const int ks = sspan > 0 ? 2 : 0;
   const int64_t base = offs[i0];
   const int rel = (int)(offs[i < n ? i : n] - base);  // past the end: the total
   const int end = __shfl_sync(0xffffffffu, rel + cnt, 31);
@@ -291,9 +302,10 @@ __global__ void k_pair_emit(const float4* __restrict__ rec, int64_t n, int nx, i
       if (__shfl_sync(0xffffffffu, rel, p + step) <= e) p += step;
     const int px0 = __shfl_sync(0xffffffffu, tx0, p), py0 = __shfl_sync(0xffffffffu, ty0, p);
     const int pw = __shfl_sync(0xffffffffu, w, p), prel = __shfl_sync(0xffffffffu, rel, p);
+    const int pc = __shfl_sync(0xffffffffu, cls, p);
     if (e < end) {
       const int local = e - prel;
-      keys[base + e] = (uint32_t)((py0 + local / pw) * ntx + px0 + local % pw);
+      keys[base + e] = ((uint32_t)((py0 + local / pw) * ntx + px0 + local % pw) << ks) | pc;
       vals[base + e] = (uint32_t)(i0 + p);
     }
   }
@@ -302,12 +314,13 @@ __global__ void k_pair_emit(const float4* __restrict__ rec, int64_t n, int nx, i
 // ---------------------------------------------------------------- work units
 using Unit = BpUnit;
 
-// units per tile, and partial-tile slots (only tiles split into several units need them)
+// units per key, and partial-tile slots (only keys split into several units need them); with
+// ks = 2 only the keys 4 tile get units (the others: small particles, k_deposit_small)
 __global__ void k_unit_count(const int64_t* __restrict__ tstart, int64_t n_tiles, int unit,
-                             uint32_t* ucount, uint32_t* scount) {
+                             uint32_t* ucount, uint32_t* scount, int ks = 0) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_tiles) return;
-  int64_t len = tstart[t + 1] - tstart[t];
+  int64_t len = (t & ((1 << ks) - 1)) ? 0 : tstart[t + 1] - tstart[t];
   uint32_t nu = (uint32_t)((len + unit - 1) / unit);
   ucount[t] = nu;
   if (scount) scount[t] = nu > 1 ? nu : 0u;
@@ -315,15 +328,16 @@ __global__ void k_unit_count(const int64_t* __restrict__ tstart, int64_t n_tiles
 
 __global__ void k_unit_emit(const int64_t* __restrict__ tstart, int64_t n_tiles, int unit,
                             const int64_t* __restrict__ uoff, const int64_t* __restrict__ soff,
-                            Unit* units) {
+                            Unit* units, int ks = 0) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n_tiles) return;
+  if (t & ((1 << ks) - 1)) return;
   int64_t b = tstart[t], e = tstart[t + 1];
   int64_t nu = (e - b + unit - 1) / unit;
   int64_t u0 = uoff[t];
   for (int64_t q = 0; q < nu; ++q) {
     Unit U;
-    U.tile = (int)t;
+    U.tile = (int)(t >> ks);
     U.slot = (nu > 1 && soff) ? (int)(soff[t] + q) : -1;
     U.begin = b + q * unit;
     U.end = min(e, b + (q + 1) * unit);
@@ -546,15 +560,17 @@ __global__ void __launch_bounds__(256) k_reduce_tiles(const int64_t* __restrict_
                                                       int64_t n_tiles, int unit, int nx, int ny,
                                                       int ntx, const float* __restrict__ partials,
                                                       float* ymap, float* bmap, float* ylo,
-                                                      float* blo, const int* __restrict__ err) {
+                                                      float* blo, const int* __restrict__ err,
+                                                      int ks) {
   // blockIdx.y: which of REDUCE_SPLIT pixel slices of the tile this CTA sums
   int64_t t = blockIdx.x;
   if (t >= n_tiles) return;
   if (err && *err) return;  // the deposit gave up: its partial tiles are incomplete
-  int64_t len = tstart[t + 1] - tstart[t];
+  const int64_t key = t << ks;  // the tile's (large-particle) key
+  int64_t len = tstart[key + 1] - tstart[key];
   int64_t nu = (len + unit - 1) / unit;
   if (nu <= 1) return;
-  int64_t u0 = soff[t];
+  int64_t u0 = soff[key];
   int x0 = (int)(t % ntx) * TS, y0 = (int)(t / ntx) * TS;
   constexpr int SLICE = TS * TS / REDUCE_SPLIT;
   const int q_end = (blockIdx.y + 1) * SLICE;
@@ -583,6 +599,144 @@ __global__ void __launch_bounds__(256) k_reduce_tiles(const int64_t* __restrict_
   }
 }
 
+// ---------------------------------------------------------------- small particles
+// Particles whose clipped pixel box is at most sspan (<= SMALL_MAX = 8) pixels on both axes
+// (most halo particles of a large light-cone cover a few pixels) are deposited here instead
+// of as dense 64 x 64 tensor-core updates.  One CTA per tile, one thread per particle (sorted by size
+// class, then index, so that a warp's particles have similar boxes and its lanes similar
+// trip counts): the thread computes its particle's cell weights from the edge values of
+// bp_edge_split (those of the tensor-core deposit) and adds Y wx wy and B wx wy of every
+// covered cell to the tile's accumulators as 64-bit fixed-point integers, with shared-memory
+// atomics.  Integer sums do not depend on the order of the additions: the result is
+// deterministic.  Each map's scale 2^S is fixed per tile from its largest |Y| (|B|) and the
+// particle count n, so that no cell sum can overflow (a cell's sum is at most n max|Y|) and the
+// quantum is 2^-61 n max|Y|: far below the FP32 rounding of the products.
+constexpr int SMALL_MAX = 8;
+constexpr int SMALL_THREADS = 512;
+struct SmallSmem {
+  unsigned long long acc[2][64 * 64];      // y, b of the 64 x 64 tile
+  float wx[SMALL_THREADS][SMALL_MAX + 1];  // each thread's column weights (padded rows)
+  float amax[2][SMALL_THREADS / 32];
+};
+
+// v (|v| < 2^62) as an integer, truncated toward zero, with integer instructions (the
+// conversion instruction to 64-bit integers measured slower here)
+__device__ __forceinline__ long long small_fix(float v) {
+  const int b = __float_as_int(v);
+  const int e = ((b >> 23) & 0xff) - 150;  // v = m 2^e with the 24-bit significand m
+  const long long m = (long long)((b & 0x7fffff) | 0x800000);
+  const long long q = e >= 0 ? (m << e) : (e > -24 ? (m >> (-e)) : 0ll);
+  return b < 0 ? -q : q;
+}
+
+// exponent S with n * amax * 2^S < 2^61 (0 when amax is 0)
+__device__ __forceinline__ int small_scale(float amax, int64_t n) {
+  if (!(amax > 0.f)) return 0;
+  int ex;
+  frexp((double)amax * (double)n, &ex);
+  return 61 - ex;
+}
+
+__global__ void __launch_bounds__(SMALL_THREADS) k_deposit_small(
+    const float4* __restrict__ rec, const uint32_t* __restrict__ pvals,
+    const int64_t* __restrict__ tstart, int ntx, int nx, int ny, float* ymap, float* bmap,
+    float* ylo, float* blo, const int* __restrict__ err) {
+  extern __shared__ __align__(16) unsigned char small_raw[];
+  SmallSmem& S = *reinterpret_cast<SmallSmem*>(small_raw);
+  const int t = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
+  if (err && *err) return;  // the tensor-core deposit before it gave up
+  const int64_t b = tstart[4 * (int64_t)t + 1], e = tstart[4 * (int64_t)t + 4];  // classes 1-3
+  if (b >= e) return;
+  const int x0 = (t % ntx) * 64, y0 = (t / ntx) * 64;
+  for (int q = tid; q < 2 * 64 * 64; q += SMALL_THREADS) (&S.acc[0][0])[q] = 0ull;
+  // 1. the largest |Y| and |B| of the tile's particles
+  float my = 0.f, mb = 0.f;
+  for (int64_t k = b + tid; k < e; k += SMALL_THREADS) {
+    const int64_t pv = pvals[k];
+    my = fmaxf(my, fabsf(rec[2 * pv].w));
+    mb = fmaxf(mb, fabsf(rec[2 * pv + 1].x));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, o));
+    mb = fmaxf(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+  }
+  if (lane == 0) {
+    S.amax[0][wp] = my;
+    S.amax[1][wp] = mb;
+  }
+  __syncthreads();
+  my = mb = 0.f;
+#pragma unroll
+  for (int q = 0; q < SMALL_THREADS / 32; ++q) {
+    my = fmaxf(my, S.amax[0][q]);
+    mb = fmaxf(mb, S.amax[1][q]);
+  }
+  const int sy = small_scale(my, e - b), sb = small_scale(mb, e - b);
+  // 2. every particle's cells, as fixed-point integers
+  float* wx = S.wx[tid];
+  for (int64_t k = b + tid; k < e; k += SMALL_THREADS) {
+    const int64_t pv = pvals[k];
+    const float4 r0 = rec[2 * pv], r1 = rec[2 * pv + 1];
+    const int ix = __float_as_int(r1.z), iy = __float_as_int(r1.w);
+    int i0, i1, j0, j1;
+    if (!bp_span(ix, r0.x, r0.z, nx, i0, i1) || !bp_span(iy, r0.y, r0.z, ny, j0, j1)) continue;
+    i0 = max(i0, x0);
+    i1 = min(i1, x0 + 63);
+    j0 = max(j0, y0);
+    j1 = min(j1, y0 + 63);
+    if (i0 > i1 || j0 > j1) continue;
+    const bool ngp = !(r0.z > 0.f);
+    const float ih = ngp ? 1.0e38f : __frcp_rn(r0.z);
+    const float k1 = BP_KT * ih, k2 = BP_KS * ih;
+    const float fx = (ngp && !(r0.x > 0.f)) ? 1.0e-30f : r0.x;
+    const float fy = (ngp && !(r0.y > 0.f)) ? 1.0e-30f : r0.y;
+    const int kcx = ix + (fx > 0.f ? 0 : -1), kcy = iy + (fy > 0.f ? 0 : -1);
+    float v = bp_edge_split(__fsub_rn((float)(i0 - ix), fx), k1, k2);
+    for (int i = i0; i <= i1; ++i) {
+      const float vn = bp_edge_split(__fsub_rn((float)(i + 1 - ix), fx), k1, k2);
+      wx[i - i0] = (vn - v) + (i == kcx ? 1.f : 0.f);
+      v = vn;
+    }
+    const float Ys = ldexpf(r0.w, sy), Bs = ldexpf(r1.x, sb);
+    const bool has_y = r0.w != 0.f;
+    float u = bp_edge_split(__fsub_rn((float)(j0 - iy), fy), k1, k2);
+    for (int j = j0; j <= j1; ++j) {
+      const float un = bp_edge_split(__fsub_rn((float)(j + 1 - iy), fy), k1, k2);
+      const float wy = (un - u) + (j == kcy ? 1.f : 0.f);
+      u = un;
+      const float ay = Ys * wy, ab = Bs * wy;
+      unsigned long long* ry = &S.acc[0][(j - y0) * 64 + (i0 - x0)];
+      unsigned long long* rb = &S.acc[1][(j - y0) * 64 + (i0 - x0)];
+      for (int c = 0; c <= i1 - i0; ++c) {
+        const float w = wx[c];
+        if (has_y) atomicAdd(ry + c, (unsigned long long)small_fix(ay * w));
+        atomicAdd(rb + c, (unsigned long long)small_fix(ab * w));
+      }
+    }
+  }
+  __syncthreads();
+  // 3. the tile's sums into the map (compensated)
+  for (int q = tid; q < 64 * 64; q += SMALL_THREADS) {
+    const int gx = x0 + (q & 63), gy = y0 + (q >> 6);
+    if (gx >= nx || gy >= ny) continue;
+    const int64_t p = (int64_t)gy * nx + gx;
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const long long a = (long long)S.acc[m][q];
+      if (a == 0) continue;
+      const double vv = ldexp((double)a, -(m ? sb : sy));
+      const float hi = (float)vv, lo = (float)(vv - (double)hi);
+      float* map = m ? bmap : ymap;
+      float* mlo = m ? blo : ylo;
+      float sm, er;
+      bp_two_sum(map[p], hi, sm, er);
+      map[p] = sm;
+      mlo[p] = mlo[p] + (lo + er);
+    }
+  }
+}
+
 int check_geom(bp_ctx* ctx, const bp_map_geom* g, const char* who) {
   if (!g) return bp_fail(ctx, BP_EINVAL, "%s: null geometry", who);
   if (g->nx <= 0 || g->ny <= 0 || g->n_maps <= 0 || !(g->dtheta > 0))
@@ -592,10 +746,11 @@ int check_geom(bp_ctx* ctx, const bp_map_geom* g, const char* who) {
   return BP_OK;
 }
 
-// Builds the sorted (tile, particle) list; returns keys/vals pointers and count.
+// Builds the sorted (tile, particle) list; returns keys/vals pointers and count.  sspan > 0:
+// keys 4 tile + the particle's size class (see k_pair_emit).
 int build_pairs(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_geom* g, int select,
                 int ts, uint32_t** keys_out, uint32_t** vals_out, int64_t* npairs_out,
-                int64_t* n_tiles_out) {
+                int64_t* n_tiles_out, int sspan = 0) {
   const int ntx = (g->nx + ts - 1) / ts, nty = (g->ny + ts - 1) / ts;
   const int64_t n_tiles = (int64_t)ntx * nty;
   uint32_t* counts;
@@ -619,11 +774,12 @@ int build_pairs(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_geom
   if ((r = bp_ws(ctx, WS_VALS0, (size_t)np * 4, (void**)&v0))) return r;
   if ((r = bp_ws(ctx, WS_KEYS1, (size_t)np * 4, (void**)&k1))) return r;
   if ((r = bp_ws(ctx, WS_VALS1, (size_t)np * 4, (void**)&v1))) return r;
-  k_pair_emit<<<nb, 256, 0, ctx->stream>>>(rec, n, g->nx, g->ny, ts, select, ntx, offs, k0, v0);
+  k_pair_emit<<<nb, 256, 0, ctx->stream>>>(rec, n, g->nx, g->ny, ts, select, ntx, offs, k0, v0,
+                                           sspan);
   BP_LAUNCH_CHECK(ctx, "pair emit");
   bp_phase_end(ctx, BP_PH_PAIRS);
   int key_bits = 0;
-  while (((int64_t)1 << key_bits) < n_tiles) ++key_bits;
+  while (((int64_t)1 << key_bits) < (n_tiles << (sspan > 0 ? 2 : 0))) ++key_bits;
   bp_phase_begin(ctx, BP_PH_SORT);
   if ((r = bp_radix_sort_pairs(ctx, k0, v0, k1, v1, np, key_bits, keys_out, vals_out))) return r;
   *npairs_out = np;
@@ -660,8 +816,9 @@ int deposit_simt(bp_ctx* ctx, const float* assigned, const bp_map_geom* g, const
 // with the generations of the scratch slots they live in.  Synchronises once.
 template <int TS>
 int prepare_units(bp_ctx* ctx, const uint32_t* keys, const uint32_t* vals, int64_t np,
-                  int64_t n_tiles, PpPrepared* P) {
+                  int64_t n_tiles, PpPrepared* P, int ks = 0) {
   int r;
+  const int64_t n_keys = n_tiles << ks;  // ks = 2: four keys per tile (size classes)
   // particles per work unit: the context's value, or (auto) about 16 units per
   // resident CTA, at least 2048
   int64_t unit64 = ctx->pp_unit;
@@ -672,32 +829,34 @@ int prepare_units(bp_ctx* ctx, const uint32_t* keys, const uint32_t* vals, int64
   }
   const int unit = (int)unit64;
   int64_t* tstart;
-  if ((r = bp_ws(ctx, WS_TILES, (size_t)(n_tiles + 1) * 8 * 3 + (size_t)(n_tiles + 1) * 8 + 64,
+  if ((r = bp_ws(ctx, WS_TILES, (size_t)(n_keys + 1) * 8 * 3 + (size_t)(n_keys + 1) * 8 + 64,
                  (void**)&tstart)))
     return r;
-  int64_t* uoff = tstart + (n_tiles + 1);
-  int64_t* soff = uoff + (n_tiles + 1);
-  uint32_t* ucount = (uint32_t*)(soff + (n_tiles + 1));
-  uint32_t* scount = ucount + (n_tiles + 1);
-  if ((r = bp_tile_ranges(ctx, keys, np, n_tiles, tstart))) return r;
-  unsigned tb = (unsigned)((n_tiles + 255) / 256);
-  k_unit_count<<<tb, 256, 0, ctx->stream>>>(tstart, n_tiles, unit, ucount, scount);
+  int64_t* uoff = tstart + (n_keys + 1);
+  int64_t* soff = uoff + (n_keys + 1);
+  uint32_t* ucount = (uint32_t*)(soff + (n_keys + 1));
+  uint32_t* scount = ucount + (n_keys + 1);
+  if ((r = bp_tile_ranges(ctx, keys, np, n_keys, tstart))) return r;
+  unsigned tb = (unsigned)((n_keys + 255) / 256);
+  k_unit_count<<<tb, 256, 0, ctx->stream>>>(tstart, n_keys, unit, ucount, scount, ks);
   BP_LAUNCH_CHECK(ctx, "unit count");
-  if ((r = bp_scan_u32_to_i64(ctx, ucount, uoff, n_tiles))) return r;
-  if ((r = bp_scan_u32_to_i64(ctx, scount, soff, n_tiles))) return r;
-  const int64_t max_units = n_tiles + np / unit + 1;
+  if ((r = bp_scan_u32_to_i64(ctx, ucount, uoff, n_keys))) return r;
+  if ((r = bp_scan_u32_to_i64(ctx, scount, soff, n_keys))) return r;
+  const int64_t max_units = n_keys + np / unit + 1;
   Unit* units;
   if ((r = bp_ws(ctx, WS_UNITS, (size_t)max_units * sizeof(Unit), (void**)&units))) return r;
-  k_unit_emit<<<tb, 256, 0, ctx->stream>>>(tstart, n_tiles, unit, uoff, soff, units);
+  k_unit_emit<<<tb, 256, 0, ctx->stream>>>(tstart, n_keys, unit, uoff, soff, units, ks);
   BP_LAUNCH_CHECK(ctx, "unit emit");
   // partial tiles exist only for tiles split into several units
-  BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 1, soff + n_tiles, 8, cudaMemcpyDeviceToHost,
+  BP_CUDA(ctx, cudaMemcpyAsync(ctx->h_pinned + 1, soff + n_keys, 8, cudaMemcpyDeviceToHost,
                                ctx->stream));
   BP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
   P->ts = TS;
   P->unit = unit;
   P->np = np;
   P->n_tiles = n_tiles;
+  P->n_keys = n_keys;
+  P->ks = ks;
   P->max_units = max_units;
   P->n_slots = ctx->h_pinned[1];
   P->vals = vals;
@@ -725,13 +884,13 @@ int launch_deposit(bp_ctx* ctx, const float* assigned, const bp_map_geom* g,
   const bool tc = bp_deposit_uses_tc(ctx, TS);
   if (tc) {
     bp_phase_begin(ctx, BP_PH_DEPOSIT);
-    if ((r = bp_deposit_tc_launch(ctx, assigned, P.vals, units, P.uoff + P.n_tiles,
+    if ((r = bp_deposit_tc_launch(ctx, assigned, P.vals, units, P.uoff + P.n_keys,
                                   ctx->d_counter + 1, P.max_units, g, ymap, bmap, ylo, blo,
                                   partials)))
       return r;
     bp_phase_end(ctx, BP_PH_DEPOSIT);
   } else {
-    if ((r = deposit_simt<TS>(ctx, assigned, g, P.vals, units, P.uoff + P.n_tiles,
+    if ((r = deposit_simt<TS>(ctx, assigned, g, P.vals, units, P.uoff + P.n_keys,
                               ctx->d_counter + 1, P.max_units, ymap, bmap, ylo, blo, partials)))
       return r;
   }
@@ -739,10 +898,21 @@ int launch_deposit(bp_ctx* ctx, const float* assigned, const bp_map_geom* g,
   if (P.n_slots > 0) {
     k_reduce_tiles<TS><<<dim3((unsigned)P.n_tiles, REDUCE_SPLIT), 256, 0, ctx->stream>>>(
         P.tstart, P.soff, P.n_tiles, P.unit, g->nx, g->ny, ntx, partials, ymap, bmap, ylo, blo,
-        tc ? ctx->d_flags : nullptr);
+        tc ? ctx->d_flags : nullptr, P.ks);
     BP_LAUNCH_CHECK(ctx, "reduce tiles");
   }
   bp_phase_end(ctx, BP_PH_REDUCE);
+  if (P.ks) {  // the small particles, after the large ones of every tile
+    bp_phase_begin(ctx, BP_PH_DEPOSIT_SMALL);
+    const size_t smem = sizeof(SmallSmem);
+    BP_CUDA(ctx, cudaFuncSetAttribute(k_deposit_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+    k_deposit_small<<<(unsigned)P.n_tiles, SMALL_THREADS, smem, ctx->stream>>>(
+        reinterpret_cast<const float4*>(assigned), P.vals, P.tstart, ntx, g->nx, g->ny, ymap, bmap,
+        ylo, blo, tc ? ctx->d_flags : nullptr);
+    BP_LAUNCH_CHECK(ctx, "deposit (small particles)");
+    bp_phase_end(ctx, BP_PH_DEPOSIT_SMALL);
+  }
   if (tc) return bp_deposit_tc_check(ctx);
   return BP_OK;
 }
@@ -750,9 +920,9 @@ int launch_deposit(bp_ctx* ctx, const float* assigned, const bp_map_geom* g,
 template <int TS>
 int deposit(bp_ctx* ctx, const float* assigned, const bp_map_geom* g, const uint32_t* keys,
             const uint32_t* vals, int64_t np, int64_t n_tiles, float* ymap, float* bmap,
-            float* ylo, float* blo) {
+            float* ylo, float* blo, int ks) {
   PpPrepared P;
-  int r = prepare_units<TS>(ctx, keys, vals, np, n_tiles, &P);
+  int r = prepare_units<TS>(ctx, keys, vals, np, n_tiles, &P, ks);
   if (r) return r;
   bp_phase_end(ctx, BP_PH_SORT);
   return launch_deposit<TS>(ctx, assigned, g, P, ymap, bmap, ylo, blo);
@@ -811,12 +981,24 @@ int bp_pp_preload(bp_ctx* ctx) {
   BP_CUDA(ctx, cudaFuncGetAttributes(&a, k_unit_emit));
   BP_CUDA(ctx, cudaFuncGetAttributes(&a, k_deposit<32>));
   BP_CUDA(ctx, cudaFuncGetAttributes(&a, k_deposit<64>));
+  BP_CUDA(ctx, cudaFuncGetAttributes(&a, k_deposit_small));
   return BP_OK;
 }
 
 bool bp_deposit_uses_tc(const bp_ctx* ctx, int ts) {
   if (ctx->pp_kernel == BP_DEPOSIT_SIMT) return false;
   return ts == 64;
+}
+
+// The small-particle span of a paste: with the tensor-core deposit (tile 64), the context's
+// threshold, or automatically 8 when the map has at least 4 tiles per SM (the small-particle
+// kernel runs one CTA per tile: with fewer tiles it leaves SMs idle and measured slower than
+// the tensor cores alone); 0 (no split) otherwise.
+static int pp_small_span(const bp_ctx* ctx, int ts, const bp_map_geom* g) {
+  if (!bp_deposit_uses_tc(ctx, ts) || ts != 64) return 0;
+  if (ctx->small_span >= 0) return ctx->small_span;
+  const int64_t tiles = (int64_t)((g->nx + 63) / 64) * ((g->ny + 63) / 64);
+  return tiles >= 4 * (int64_t)ctx->num_sms ? 8 : 0;
 }
 
 // The particle paste with every scratch buffer supplied by the caller.  Reads back the
@@ -847,7 +1029,7 @@ int bp_pp_paste_buffers(bp_ctx* ctx, int64_t n, const float* assigned, const bp_
                    (long long)np, (long long)B->max_pairs);
   if (np == 0) return BP_OK;
   k_pair_emit<<<nb, 256, 0, ctx->stream>>>(rec, n, g->nx, g->ny, ts, select, ntx, B->offs,
-                                           B->keys0, B->vals0);
+                                           B->keys0, B->vals0, 0);
   BP_LAUNCH_CHECK(ctx, "pair emit");
   int key_bits = 0;
   while (((int64_t)1 << key_bits) < n_tiles) ++key_bits;
@@ -965,10 +1147,14 @@ int bp_paste_particles(bp_ctx* ctx, int64_t n, const float* assigned, const bp_m
     return bp_fail(ctx, BP_EINVAL, "bp_paste_particles: the tensor-core deposit needs tile 64");
   uint32_t *keys, *vals;
   int64_t np, n_tiles;
-  if ((r = build_pairs(ctx, n, assigned, geom, select, ts, &keys, &vals, &np, &n_tiles))) return r;
+  const int sspan = pp_small_span(ctx, ts, geom);
+  if ((r = build_pairs(ctx, n, assigned, geom, select, ts, &keys, &vals, &np, &n_tiles, sspan)))
+    return r;
   if (np == 0) return BP_OK;
-  if (ts == 64) return deposit<64>(ctx, assigned, geom, keys, vals, np, n_tiles, ymap, bmap, ylo, blo);
-  return deposit<32>(ctx, assigned, geom, keys, vals, np, n_tiles, ymap, bmap, ylo, blo);
+  const int ks = sspan > 0 ? 2 : 0;
+  if (ts == 64)
+    return deposit<64>(ctx, assigned, geom, keys, vals, np, n_tiles, ymap, bmap, ylo, blo, ks);
+  return deposit<32>(ctx, assigned, geom, keys, vals, np, n_tiles, ymap, bmap, ylo, blo, ks);
 }
 
 int bp_pp_prepare(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_geom* geom,
@@ -997,11 +1183,14 @@ int bp_pp_prepare(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_ge
   if (n > 0) {
     uint32_t *keys, *vals;
     int64_t np, n_tiles;
-    if ((r = build_pairs(ctx, n, assigned, geom, select, ts, &keys, &vals, &np, &n_tiles)))
+    const int sspan = pp_small_span(ctx, ts, geom);
+    if ((r = build_pairs(ctx, n, assigned, geom, select, ts, &keys, &vals, &np, &n_tiles,
+                         sspan)))
       return r;
     if (np > 0) {
-      r = ts == 64 ? prepare_units<64>(ctx, keys, vals, np, n_tiles, &P)
-                   : prepare_units<32>(ctx, keys, vals, np, n_tiles, &P);
+      const int ks = sspan > 0 ? 2 : 0;
+      r = ts == 64 ? prepare_units<64>(ctx, keys, vals, np, n_tiles, &P, ks)
+                   : prepare_units<32>(ctx, keys, vals, np, n_tiles, &P, ks);
       if (r) return r;
     }
     bp_phase_end(ctx, BP_PH_SORT);
@@ -1015,7 +1204,8 @@ int bp_pp_deposit(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_ge
   if (!ctx) return BP_EINVAL;
   const PpPrepared& P = ctx->pp_prep;
   if (!P.valid || P.assigned != assigned || P.n != n || !geom || P.select != select ||
-      P.ts != ctx->pp_tile || memcmp(&P.g, geom, sizeof(bp_map_geom)) != 0)
+      P.ts != ctx->pp_tile || memcmp(&P.g, geom, sizeof(bp_map_geom)) != 0 ||
+      (P.np > 0 && P.ks != (pp_small_span(ctx, P.ts, geom) > 0 ? 2 : 0)))
     return bp_fail(ctx, BP_EINVAL, "bp_pp_deposit: no bp_pp_prepare of these records");
   if (P.np == 0 || n == 0) return BP_OK;
   for (int k : {(int)WS_KEYS0, (int)WS_VALS0, (int)WS_KEYS1, (int)WS_VALS1, (int)WS_TILES,

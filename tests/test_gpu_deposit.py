@@ -174,3 +174,68 @@ def test_tensor_deposit_timeout_returns_error_and_keeps_context(api, ctx, unit):
     ctx.paste_particles(rec, g, again)
     for x, y in ((again.y, ref.y), (again.b, ref.b), (again.ylo, ref.ylo), (again.blo, ref.blo)):
         assert torch.equal(x, y)
+
+
+def _mixed_sizes(n, nx, ny, seed):
+    """Records with kernels from sub-pixel to 60 pixels (most within the small-particle span),
+    signed kSZ, a few h = 0 particles, some footprints crossing the map edges."""
+    rng = np.random.default_rng(seed)
+    hp = np.where(rng.random(n) < 0.75, rng.exponential(2.0, n), rng.uniform(8.0, 60.0, n))
+    hp[rng.random(n) < 0.02] = 0.0
+    return I.deposit_inputs(rng.uniform(-10, nx + 10, n), rng.uniform(-10, ny + 10, n), hp,
+                            rng.uniform(0, 1e-6, n), rng.normal(0, 1e-6, n),
+                            rng.integers(0, 2, n))
+
+
+@pytest.mark.parametrize("span", [8, 3, 0])
+def test_small_particle_deposit_matches_oracle(orc, api, ctx, span):
+    """The small-particle deposit (particles at most `span` pixels wide, in size classes of at
+    most 2, 4, 8 pixels; 0 = all on the tensor cores) against the oracle, with several tiles per
+    map and ragged edges."""
+    nx, ny = 300, 200
+    a = _mixed_sizes(60000, nx, ny, 33)
+    ctx.set_small_span(span)
+    y, b = _deposit(api, ctx, a, nx, ny)
+    yo, bo = orc.pp_deposit(orc_deposit_inputs(a), orc.geom(nx, ny, 0.0, 0.0, 1.0))
+    assert_map_parity(y[0], yo, what="y")
+    assert_map_parity(b[0], bo, what="b")
+
+
+def test_small_particle_deposit_agrees_with_tensor_cores_and_repeats_bitwise(api, ctx):
+    nx, ny = 256, 192
+    a = _mixed_sizes(80000, nx, ny, 44)
+    out = {}
+    for span in (8, 0):
+        ctx.set_small_span(span)
+        out[span] = _deposit(api, ctx, a, nx, ny)
+    for m in range(2):
+        s, t = out[8][m][0], out[0][m][0]
+        assert np.linalg.norm(t - s) <= 2e-6 * np.linalg.norm(t)
+    ctx.set_small_span(8)
+    again = _deposit(api, ctx, a, nx, ny)
+    assert np.array_equal(again[0], out[8][0]) and np.array_equal(again[1], out[8][1])
+
+
+def test_small_particle_deposit_wide_dynamic_range(orc, api, ctx):
+    """Small particles of amplitudes over 12 decades in one tile: the fixed-point scale of the
+    tile follows its largest amplitude, and the faint particles keep their relative accuracy
+    wherever they dominate a pixel."""
+    rng = np.random.default_rng(55)
+    n = 4000
+    px, py = rng.uniform(2, 62, n), rng.uniform(2, 62, n)
+    Y = 10.0 ** rng.uniform(-12, 0, n)
+    a = I.deposit_inputs(px, py, rng.uniform(0.3, 3.0, n), Y, -Y, np.zeros(n))
+    ctx.set_small_span(8)
+    y, b = _deposit(api, ctx, a, 64, 64)
+    yo, bo = orc.pp_deposit(orc_deposit_inputs(a), orc.geom(64, 64, 0.0, 0.0, 1.0))
+    assert_map_parity(y[0], yo, what="y")
+    assert_map_parity(b[0], bo, what="b")
+    # pixels six decades below the maximum still within the per-pixel tolerance
+    mask = yo > 1e-6 * yo.max()
+    assert np.max(np.abs(y[0][mask] - yo[mask]) / yo[mask]) < 1e-4
+
+
+def test_small_span_rejects_out_of_range(api, ctx):
+    for bad in (-2, 9):
+        with pytest.raises(api.BpError, match="BP_EINVAL"):
+            ctx.set_small_span(bad)
