@@ -120,7 +120,16 @@ static int build_tables(bp_ctx* ctx) {
     tc[j] = (float)tz;
     dtc[j] = (float)(tau_per_mpc * (1 + z) * (1 + z));
   }
-  size_t bytes = 4 * nz * sizeof(double) + 4 * nc * sizeof(float);
+  // the particle tables once more, interleaved per node (z, dz/dchi, tau, dtau/dchi): one
+  // 16-byte load per node for a particle's Hermite interpolation of z(chi) and tau(chi)
+  std::vector<float> zt4(4 * (size_t)nc);
+  for (int j = 0; j < nc; ++j) {
+    zt4[4 * j] = zc[j];
+    zt4[4 * j + 1] = dzc[j];
+    zt4[4 * j + 2] = tc[j];
+    zt4[4 * j + 3] = dtc[j];
+  }
+  size_t bytes = 4 * nz * sizeof(double) + 8 * nc * sizeof(float);
   BP_CUDA(ctx, cudaMalloc(&ctx->table_mem, bytes));
   char* base = (char*)ctx->table_mem;
   double* dd = (double*)base;
@@ -133,6 +142,7 @@ static int build_tables(bp_ctx* ctx) {
   BP_CUDA(ctx, cudaMemcpy(ff + nc, dzc.data(), nc * 4, cudaMemcpyHostToDevice));
   BP_CUDA(ctx, cudaMemcpy(ff + 2 * nc, tc.data(), nc * 4, cudaMemcpyHostToDevice));
   BP_CUDA(ctx, cudaMemcpy(ff + 3 * nc, dtc.data(), nc * 4, cudaMemcpyHostToDevice));
+  BP_CUDA(ctx, cudaMemcpy(ff + 4 * nc, zt4.data(), (size_t)nc * 16, cudaMemcpyHostToDevice));
   BpTables& T = ctx->t;
   T.chi_z = dd;
   T.dchi_z = dd + nz;
@@ -144,6 +154,7 @@ static int build_tables(bp_ctx* ctx) {
   T.dz_c = ff + nc;
   T.tau_c = ff + 2 * nc;
   T.dtau_c = ff + 3 * nc;
+  T.zt4 = reinterpret_cast<const float4*>(ff + 4 * nc);
   T.nc = nc;
   T.dchi = (float)dch;
   T.inv_dchi = (float)(1.0 / dch);

@@ -42,6 +42,7 @@ struct BpTables {
   const float* dz_c;   // [nc] dz/dchi
   const float* tau_c;  // [nc]
   const float* dtau_c; // [nc] dtau/dchi
+  const float4* zt4;   // [nc] the same four, interleaved per node (16-byte aligned)
   int nc;
   float dchi;
   float inv_dchi;
@@ -162,6 +163,24 @@ __device__ __forceinline__ float bp_hermitef(const float* v, const float* d, int
         h11 = t3 - t2;
   return h00 * __ldg(v + i) + h10 * h * __ldg(d + i) + h01 * __ldg(v + i + 1) +
          h11 * h * __ldg(d + i + 1);
+}
+
+// z(chi) and tau(chi) of a particle by cubic Hermite interpolation of the interleaved
+// per-node table (two 16-byte loads).
+__device__ __forceinline__ void bp_hermite_ztau(const BpTables& T, float x, float& z,
+                                                float& tau) {
+  float u = x * T.inv_dchi;
+  int i = (int)u;
+  if (i < 0) i = 0;
+  if (i > T.nc - 2) i = T.nc - 2;
+  const float t = u - (float)i;
+  const float t2 = t * t, t3 = t2 * t;
+  const float h00 = 2.f * t3 - 3.f * t2 + 1.f, h10 = t3 - 2.f * t2 + t, h01 = -2.f * t3 + 3.f * t2,
+              h11 = t3 - t2;
+  const float4 a = __ldg(T.zt4 + i), b = __ldg(T.zt4 + i + 1);
+  const float h = T.dchi;
+  z = h00 * a.x + h10 * h * a.y + h01 * b.x + h11 * h * b.y;
+  tau = h00 * a.z + h10 * h * a.w + h01 * b.z + h11 * h * b.w;
 }
 
 // Integrated normalised kernel in the "split" representation used by the deposit:

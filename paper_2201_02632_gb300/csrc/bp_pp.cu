@@ -33,10 +33,13 @@ namespace {
 //  [8] KY   sigma_T/(m_e c^2) (P_e/P_th) P0 M_p / rho_s  [y units x Mpc^2]
 //  [9] KB   sigma_T rho0/(mu_e m_p) M_p / rho_s        [b units x Mpc^2]
 //  [10] ok  1 if the halo solved
+//  [11] Phi0, [12] 1 / ((n+1) T)   (the potential-based variant)
+//  [13..15] the halo centre (comoving h^-1 Mpc), so that a particle reads one 64-byte block
 constexpr int HB = 16;
 
 __global__ void k_halo_block(BpParams P, int64_t nh, const double* __restrict__ model,
-                             const int32_t* __restrict__ status, double Mp, float* blk) {
+                             const int32_t* __restrict__ status, double Mp,
+                             const float* __restrict__ hpos, float* blk) {
   int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nh) return;
   auto F = [&](int f) { return model[(int64_t)f * nh + k]; };
@@ -59,7 +62,9 @@ __global__ void k_halo_block(BpParams P, int64_t nh, const double* __restrict__ 
   b[10] = ok ? 1.f : 0.f;
   b[11] = ok ? (float)F(BP_M_PHI0) : 0.f;  // the potential-based variant: theta = 1 +
   b[12] = ok ? (float)(1.0 / n1T) : 0.f;   //   (Phi0 - phi_i) / ((n + 1) T)
-  for (int q = 13; q < HB; ++q) b[q] = 0.f;
+  b[13] = hpos ? hpos[k] : 0.f;
+  b[14] = hpos ? hpos[nh + k] : 0.f;
+  b[15] = hpos ? hpos[2 * nh + k] : 0.f;
 }
 
 // 1 - ln(1+x)/x without cancellation
@@ -164,11 +169,11 @@ struct AssignArgs {
 // h in pixels, Y = B = 0, and the kind from the halo id alone (a halo particle outside its
 // halo's truncation radius stays HALO, with zero signals later).  MODE 2 (signals): only Y,
 // B and the kind, the same values as MODE 0, into a record whose geometry MODE 1 wrote.
+// The record of particle i from its SoA fields.
 template <int MODE>
-__global__ void __launch_bounds__(256) k_assign(AssignArgs a, BpTables T) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= a.n) return;
-  float xf = a.x[i], yf = a.y[i], zf = a.z[i];
+__device__ __forceinline__ void assign_one(const AssignArgs& a, const BpTables& T, int64_t i,
+                                           float xf, float yf, float zf, float vxf, float vyf,
+                                           float vzf, float hsf, int32_t k) {
   // sky angles and pixel coordinates: double-float FP32 near the axis, else FP64
   int ix = 0, iy = 0;
   float fx = 0.f, fy = 0.f;
@@ -187,36 +192,38 @@ __global__ void __launch_bounds__(256) k_assign(AssignArgs a, BpTables T) {
   float hp = 0.f;
   if constexpr (MODE == 1) {
     if (rh > 0.f) {
-      hp = a.hs[i] * a.inv_h_dth / chi;
-      const int32_t k = a.hid[i];
+      hp = hsf * a.inv_h_dth / chi;
       kind = k < 0 ? BP_KIND_FIELD : (k < a.nh ? BP_KIND_HALO : BP_KIND_NONE);
     }
   } else if (rh > 0.f) {
-    if constexpr (MODE == 0) hp = a.hs[i] * a.inv_h_dth / chi;
-    float zz = bp_hermitef(T.z_c, T.dz_c, T.nc, T.dchi, T.inv_dchi, chi);
-    float tau = bp_hermitef(T.tau_c, T.dtau_c, T.nc, T.dchi, T.inv_dchi, chi);
-    float DA = chi / (1.0f + zz);
-    float vr = (a.vx[i] * xf + a.vy[i] * yf + a.vz[i] * zf) / rh;
-    float geo = a.inv_om_pix / (DA * DA);
-    float ekin = expf(-tau) * vr;
-    int32_t k = a.hid[i];
+    if constexpr (MODE == 0) hp = hsf * a.inv_h_dth / chi;  // exact rounding: the pair list
+    float zz, tau;
+    bp_hermite_ztau(T, chi, zz, tau);
+    // FP32 factors of the signals: approximate divisions and exponentials (a few ulps)
+    const float DA = __fdividef(chi, 1.0f + zz);
+    const float vr = __fdividef(vxf * xf + vyf * yf + vzf * zf, rh);
+    const float geo = __fdividef(a.inv_om_pix, DA * DA);
+    const float ekin = __expf(-tau) * vr;
     if (k < 0) {
       B = a.field_B * ekin * geo;
       kind = BP_KIND_FIELD;
     } else if (k < a.nh) {
-      const float* b = a.blk + (int64_t)k * HB;
-      if (b[10] != 0.f) {
-        float dx = xf - a.hpos[k], dy = yf - a.hpos[a.nh + k], dz = zf - a.hpos[2 * a.nh + k];
-        float x = sqrtf(dx * dx + dy * dy + dz * dz) * b[0];
-        if (x < b[1]) {
-          float th = a.phi ? 1.0f + (b[11] - a.phi[i]) * b[12]
-                           : ((x <= b[2]) ? 1.0f - b[4] * g_inner(x) : 1.0f - b[5] + b[6] / x);
+      // the halo's block: 16 floats, read as four 16-byte loads
+      const float4* bq = reinterpret_cast<const float4*>(a.blk) + (int64_t)k * (HB / 4);
+      const float4 b0 = __ldg(bq), b1 = __ldg(bq + 1), b2 = __ldg(bq + 2), b3 = __ldg(bq + 3);
+      if (b2.z != 0.f) {
+        float dx = xf - b3.y, dy = yf - b3.z, dz = zf - b3.w;
+        float x = sqrtf(dx * dx + dy * dy + dz * dz) * b0.x;
+        if (x < b0.y) {
+          float th = a.phi ? 1.0f + (b2.w - a.phi[i]) * b3.x
+                           : ((x <= b0.z) ? 1.0f - b1.x * g_inner(x)
+                                          : 1.0f - b1.y + __fdividef(b1.z, x));
           th = fmaxf(th, 0.f);
           float thn = powi_or_pow(th, a.n_poly, a.n_int);
-          float Rnt = b[7] * powf(x * b[3], a.n_nt);
+          float Rnt = b1.w * __powf(x * b0.w, a.n_nt);
           float vol = x * (1.0f + x) * (1.0f + x);  // rho_s / rho_NFW(r)
-          Y = b[8] * thn * th * fmaxf(0.f, 1.0f - Rnt) * vol * geo;
-          B = b[9] * thn * vol * ekin * geo * (1.0f / (float)bpc::C_KMS);
+          Y = b2.x * thn * th * fmaxf(0.f, 1.0f - Rnt) * vol * geo;
+          B = b2.y * thn * vol * ekin * geo * (1.0f / (float)bpc::C_KMS);
           kind = BP_KIND_HALO;
         }
       }
@@ -231,6 +238,39 @@ __global__ void __launch_bounds__(256) k_assign(AssignArgs a, BpTables T) {
     o[0] = make_float4(fx, fy, hp, Y);
     o[1] = make_float4(B, __int_as_float(kind), __int_as_float(ix), __int_as_float(iy));
   }
+}
+
+// one particle per thread (any alignment of the SoA arrays)
+template <int MODE>
+__global__ void __launch_bounds__(256) k_assign(AssignArgs a, BpTables T) {
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.n) return;
+  assign_one<MODE>(a, T, i, a.x[i], a.y[i], a.z[i], a.vx[i], a.vy[i], a.vz[i], a.hs[i],
+                   a.hid[i]);
+}
+
+// four consecutive particles per thread, the SoA fields read with 16-byte loads (every array
+// 16-byte aligned); the last n % 4 particles are left to k_assign
+template <int MODE>
+__global__ void __launch_bounds__(256) k_assign4(AssignArgs a, BpTables T) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (4 * q + 3 >= a.n) return;
+  const float4 x = __ldg(reinterpret_cast<const float4*>(a.x) + q);
+  const float4 y = __ldg(reinterpret_cast<const float4*>(a.y) + q);
+  const float4 z = __ldg(reinterpret_cast<const float4*>(a.z) + q);
+  const float4 h = __ldg(reinterpret_cast<const float4*>(a.hs) + q);
+  const int4 k = __ldg(reinterpret_cast<const int4*>(a.hid) + q);
+  float4 vx = make_float4(0.f, 0.f, 0.f, 0.f), vy = vx, vz = vx;
+  if constexpr (MODE != 1) {
+    vx = __ldg(reinterpret_cast<const float4*>(a.vx) + q);
+    vy = __ldg(reinterpret_cast<const float4*>(a.vy) + q);
+    vz = __ldg(reinterpret_cast<const float4*>(a.vz) + q);
+  }
+  const int64_t i = 4 * q;
+  assign_one<MODE>(a, T, i, x.x, y.x, z.x, vx.x, vy.x, vz.x, h.x, k.x);
+  assign_one<MODE>(a, T, i + 1, x.y, y.y, z.y, vx.y, vy.y, vz.y, h.y, k.y);
+  assign_one<MODE>(a, T, i + 2, x.z, y.z, z.z, vx.z, vy.z, vz.z, h.z, k.z);
+  assign_one<MODE>(a, T, i + 3, x.w, y.w, z.w, vx.w, vy.w, vz.w, h.w, k.w);
 }
 
 // ---------------------------------------------------------------- pairs
@@ -929,13 +969,14 @@ int deposit(bp_ctx* ctx, const float* assigned, const bp_map_geom* g, const uint
 }
 
 int halo_blocks(bp_ctx* ctx, int64_t nh, const double* model, const int32_t* status, double Mp,
-                float** blk) {
+                const float* hpos, float** blk) {
   int r = bp_ws(ctx, WS_HPAR, (size_t)(nh > 0 ? nh : 1) * HB * sizeof(float), (void**)blk);
   if (r) return r;
   if (nh > 0) {
     const int hb = bp_item_block(ctx, nh, 256);
     k_halo_block<<<(unsigned)((nh + hb - 1) / hb), hb, 0, ctx->stream>>>(ctx->p, nh, model,
-                                                                        status, Mp, *blk);
+                                                                        status, Mp, hpos,
+                                                                        *blk);
     BP_LAUNCH_CHECK(ctx, "halo block");
   }
   return BP_OK;
@@ -1087,7 +1128,7 @@ int bp_assign_particles_part(bp_ctx* ctx, int64_t n, const float* x, const float
   float* blk = nullptr;
   bp_phase_begin(ctx, BP_PH_ASSIGN);
   if (part != BP_ASSIGN_GEOMETRY &&
-      (r = halo_blocks(ctx, n_halos, model, status, Mp / P.h, &blk)))
+      (r = halo_blocks(ctx, n_halos, model, status, Mp / P.h, halo_pos, &blk)))
     return r;
   AssignArgs a;
   a.x = x; a.y = y; a.z = z; a.vx = vx; a.vy = vy; a.vz = vz; a.hs = hsml;
@@ -1116,14 +1157,40 @@ int bp_assign_particles_part(bp_ctx* ctx, int64_t n, const float* x, const float
   a.n_int = (fabs(P.n_poly - rn) < 1e-12 && rn >= 1 && rn <= 16) ? (int)rn : -1;
   a.n_nt = (float)P.n_nt;
   a.out = out;
-  const unsigned nb = (unsigned)((n + 255) / 256);
-  if (part == BP_ASSIGN_GEOMETRY)
-    k_assign<1><<<nb, 256, 0, ctx->stream>>>(a, ctx->t);
-  else if (part == BP_ASSIGN_SIGNALS)
-    k_assign<2><<<nb, 256, 0, ctx->stream>>>(a, ctx->t);
-  else
-    k_assign<0><<<nb, 256, 0, ctx->stream>>>(a, ctx->t);
-  BP_LAUNCH_CHECK(ctx, "assign");
+  // 16-byte SoA loads, 4 particles per thread, when every array allows them; the tail (and
+  // unaligned arrays) one particle per thread
+  auto al16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
+  const bool vec = al16(x) && al16(y) && al16(z) && al16(vx) && al16(vy) && al16(vz) &&
+                   al16(hsml) && al16(halo_id);
+  const int64_t n4 = vec ? n / 4 : 0;  // particles [0, 4 n4) by the vector kernel
+  if (n4 > 0) {
+    const unsigned nb4 = (unsigned)((n4 + 255) / 256);
+    if (part == BP_ASSIGN_GEOMETRY)
+      k_assign4<1><<<nb4, 256, 0, ctx->stream>>>(a, ctx->t);
+    else if (part == BP_ASSIGN_SIGNALS)
+      k_assign4<2><<<nb4, 256, 0, ctx->stream>>>(a, ctx->t);
+    else
+      k_assign4<0><<<nb4, 256, 0, ctx->stream>>>(a, ctx->t);
+    BP_LAUNCH_CHECK(ctx, "assign (4 per thread)");
+  }
+  if (4 * n4 < n) {
+    AssignArgs t = a;  // the rest: particle 4 n4 + j is element j of shifted arrays
+    const int64_t o = 4 * n4;
+    t.x = x + o; t.y = y + o; t.z = z + o; t.vx = vx + o; t.vy = vy + o; t.vz = vz + o;
+    t.hs = hsml + o;
+    t.hid = halo_id + o;
+    t.phi = phi ? phi + o : nullptr;
+    t.out = out + o * BP_ASSIGNED_STRIDE;
+    t.n = n - o;
+    const unsigned nb = (unsigned)((t.n + 255) / 256);
+    if (part == BP_ASSIGN_GEOMETRY)
+      k_assign<1><<<nb, 256, 0, ctx->stream>>>(t, ctx->t);
+    else if (part == BP_ASSIGN_SIGNALS)
+      k_assign<2><<<nb, 256, 0, ctx->stream>>>(t, ctx->t);
+    else
+      k_assign<0><<<nb, 256, 0, ctx->stream>>>(t, ctx->t);
+    BP_LAUNCH_CHECK(ctx, "assign");
+  }
   bp_phase_end(ctx, BP_PH_ASSIGN);
   return BP_OK;
 }

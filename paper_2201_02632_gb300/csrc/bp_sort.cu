@@ -199,13 +199,18 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* kin,
   }
 }
 
-__global__ void k_tile_ranges(const uint32_t* keys, int64_t n, int64_t n_tiles,
+// start[t] = the first index whose key is >= t (t = 0 .. n_tiles; start[n_tiles] = n), by a
+// binary search per key over the sorted keys: n_tiles + 1 threads, log2(n) reads each.
+__global__ void k_tile_ranges(const uint32_t* __restrict__ keys, int64_t n, int64_t n_tiles,
                               int64_t* start) {
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i > n) return;
-  int64_t lo = (i == 0) ? 0 : (int64_t)keys[i - 1] + 1;
-  int64_t hi = (i == n) ? n_tiles : (int64_t)keys[i];
-  for (int64_t t = lo; t <= hi && t <= n_tiles; ++t) start[t] = i;
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t > n_tiles) return;
+  int64_t lo = 0, hi = n;  // answer in [lo, hi]
+  while (lo < hi) {
+    const int64_t mid = lo + ((hi - lo) >> 1);
+    if ((int64_t)keys[mid] < t) lo = mid + 1; else hi = mid;
+  }
+  start[t] = lo;
 }
 
 // The scatter's 45 KB of shared memory per block: ask for the largest carveout, so that
@@ -283,7 +288,7 @@ int bp_radix_sort_pairs(bp_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t* k
 
 int bp_tile_ranges(bp_ctx* ctx, const uint32_t* keys, int64_t n, int64_t n_tiles,
                    int64_t* tile_start) {
-  int64_t threads = n + 1;
+  int64_t threads = n_tiles + 1;
   k_tile_ranges<<<(unsigned)((threads + 255) / 256), 256, 0, ctx->stream>>>(keys, n, n_tiles,
                                                                             tile_start);
   BP_LAUNCH_CHECK(ctx, "tile ranges");
