@@ -138,6 +138,9 @@ enum {
 
 #define BP_SOLVE_FP64 0        /* FP64 solve (FP32 pre-solve, then FP64 Newton to resid_tol) */
 #define BP_SOLVE_FP64_SEEDED 1 /* bp_solve_halos_ex only: the guess starts the FP32 pre-solve */
+#define BP_SOLVE_FP32_GATED 2  /* bp_solve_halos_ex only: the FP32 pre-solve (seeded by the guess
+                                * when given) is the answer where both of its FP32 residuals
+                                * are <= gate; the other halos get the full FP64 solve */
 
 #define BP_OUT_YB 0     /* maps hold y and b */
 #define BP_OUT_DT 1     /* maps hold Delta T / T_CMB: g_nu(x) y and -b, with
@@ -233,7 +236,12 @@ int bp_solve_halos(bp_ctx* ctx, int64_t n, const double* Mvir, const double* c, 
  *   mode: BP_SOLVE_FP64: the guess starts the FP64 Newton directly;
  *     BP_SOLVE_FP64_SEEDED: the guess starts the FP32 pre-solve, whose result starts the
  *     FP64 Newton (max_iter and gate apply to that Newton; halos without a finite guess
- *     get the pre-solve's default start); without a guess both are bp_solve_halos.
+ *     get the pre-solve's default start); without a guess both are bp_solve_halos;
+ *     BP_SOLVE_FP32_GATED (gate > 0 required): no FP64 Newton: the FP32 pre-solve's solution
+ *     (r_f, T) is accepted where its FP32 energy and gas-mass residuals are both <= gate,
+ *     with rho0 and P0 from the pressure condition in FP64 and the FP32 residuals in the
+ *     residual fields; every other halo is solved again by the full FP64 iteration and
+ *     counted by bp_last_fallback_count.
  * The number of halos sent to the fallback is returned by bp_last_fallback_count.
  * Synchronises (one or two counter reads). */
 int bp_solve_halos_ex(bp_ctx* ctx, int64_t n, const double* Mvir, const double* c,
@@ -287,7 +295,8 @@ int bp_mlp_targets(bp_ctx* ctx, int64_t n, const double* model, const float* nor
 int bp_mlp_mse(bp_ctx* ctx, int64_t n, const float* y, const float* t, float* dy, double* loss);
 /* Surrogate solve: BF16 MLP prediction of (r_f, T) as the seed of the FP32 pre-solve, then
  * at most polish_iter FP64 Newton iterations (bp_solve_halos_ex, BP_SOLVE_FP64_SEEDED, with
- * that guess and gate).  Halos whose normalised features fall outside hull (FP32 [12]: 6
+ * that guess and gate); polish_iter = 0: no FP64 Newton, the seeded pre-solve's solution is
+ * accepted where its FP32 residuals are <= gate (BP_SOLVE_FP32_GATED).  Halos whose normalised features fall outside hull (FP32 [12]: 6
  * minima then 6 maxima) get the plain solve's default start, and halos whose residual after
  * the polish exceeds gate get the full solve; bp_last_fallback_count returns both.  Output
  * as bp_solve_halos. */

@@ -612,6 +612,22 @@ __global__ void k_finalize(int64_t npix, float* map, float* lo, float scale) {
   map[i] = v * scale;
 }
 
+// y and b planes with their lo planes, four pixels per thread (16-byte accesses; every plane
+// 16-byte aligned), the same arithmetic as k_finalize; pixels [0, 4 n4).
+__global__ void k_finalize4(int64_t n4, float4* y, float4* ylo, float sy, float4* b,
+                            float4* blo, float sb) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n4) return;
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  float4 v = y[i], l = ylo[i];
+  y[i] = make_float4((v.x + l.x) * sy, (v.y + l.y) * sy, (v.z + l.z) * sy, (v.w + l.w) * sy);
+  ylo[i] = z;
+  v = b[i];
+  l = blo[i];
+  b[i] = make_float4((v.x + l.x) * sb, (v.y + l.y) * sb, (v.z + l.z) * sb, (v.w + l.w) * sb);
+  blo[i] = z;
+}
+
 // The (map, tile, halo) work list of a catalogue, in the context's scratch.
 struct HpList {
   int64_t np = 0, n_tiles = 0, n_units = 0, n_slots = 0;
@@ -1507,6 +1523,26 @@ int bp_finalize_map(bp_ctx* ctx, const bp_map_geom* geom, float* ymap, float* bm
   int64_t npix = (int64_t)geom->nx * geom->ny * geom->n_maps;
   unsigned nb = (unsigned)((npix + 255) / 256);
   bp_phase_begin(ctx, BP_PH_FINALIZE);
+  auto al16 = [](const void* p) { return ((uintptr_t)p & 15) == 0; };
+  if (ymap && bmap && ylo && blo && al16(ymap) && al16(bmap) && al16(ylo) && al16(blo)) {
+    // both planes in one pass, four pixels per thread; the npix % 4 tail below
+    const int64_t n4 = npix / 4;
+    if (n4 > 0) {
+      k_finalize4<<<(unsigned)((n4 + 255) / 256), 256, 0, ctx->stream>>>(
+          n4, reinterpret_cast<float4*>(ymap), reinterpret_cast<float4*>(ylo), sy,
+          reinterpret_cast<float4*>(bmap), reinterpret_cast<float4*>(blo), sb);
+      BP_LAUNCH_CHECK(ctx, "finalize (4 per thread)");
+    }
+    const int64_t t = npix - 4 * n4;
+    if (t > 0) {
+      k_finalize<<<1, 256, 0, ctx->stream>>>(t, ymap + 4 * n4, ylo + 4 * n4, sy);
+      BP_LAUNCH_CHECK(ctx, "finalize y");
+      k_finalize<<<1, 256, 0, ctx->stream>>>(t, bmap + 4 * n4, blo + 4 * n4, sb);
+      BP_LAUNCH_CHECK(ctx, "finalize b");
+    }
+    bp_phase_end(ctx, BP_PH_FINALIZE);
+    return BP_OK;
+  }
   if (ymap) {
     k_finalize<<<nb, 256, 0, ctx->stream>>>(npix, ymap, ylo, sy);
     BP_LAUNCH_CHECK(ctx, "finalize y");

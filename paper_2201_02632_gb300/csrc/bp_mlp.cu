@@ -734,7 +734,8 @@ int bp_solve_halos_surrogate(bp_ctx* ctx, int64_t n, const double* Mvir, const d
   // the prediction seeds the FP32 pre-solve; the halos outside the hull take its default
   // start (the plain solve), and count as fallbacks with those the gate rejects
   r = bp_solve_halos_ex(ctx, n, Mvir, c, z, params, guess, polish_iter > 0 ? polish_iter : 4,
-                        gate, model, status, BP_SOLVE_FP64_SEEDED, resid_tol);
+                        gate, model, status,
+                        polish_iter > 0 ? BP_SOLVE_FP64_SEEDED : BP_SOLVE_FP32_GATED, resid_tol);
   if (r == BP_OK || r == BP_ENOCONV) {  // the solve synchronised: the counts have arrived
     ctx->last_fallback += ctx->h_pinned[6];
     const int t = infer_check(ctx);

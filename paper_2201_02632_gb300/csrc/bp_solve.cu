@@ -1081,7 +1081,7 @@ using SolverF = SolverFT<32, NGL>;
 // guess[i] = ln(r_f / r_vir), guess[n + i] = ln(T r_vir / (G M)), or NaN
 __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_presolve(
     BpParams P, int64_t n, SolveExtra X, int hpw, const Halo* __restrict__ halos,
-    const int32_t* __restrict__ okv, double* guess) {
+    const int32_t* __restrict__ okv, double* guess, float* res32) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t base = ((int64_t)blockIdx.x * (blockDim.x >> 5) + w) * hpw;
   if (base >= n) return;
@@ -1091,7 +1091,7 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_presolve(
   for (int jj = 0; jj < hpw; ++jj) {
     const int64_t i = base + jj;
     if (i >= n) break;
-    float g0 = __int_as_float(0x7fc00000), g1 = g0;
+    float g0 = __int_as_float(0x7fc00000), g1 = g0, rE = g0, rM = g0;
     if (okv[i]) {
       const Halo H = halos[i];
       const HaloF h = {(float)H.c, (float)H.rvir, (float)H.rs, (float)H.mc, (float)H.phi0,
@@ -1107,7 +1107,7 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_presolve(
       SolverF S(h, nn, n_int);
       S.cache_region_a(lane);
       // reduced problem at r_f: T from the gas-mass condition, then R_e and dR_e/dln r_f
-      float T = 0.f, Re = 1.f, dRe = 0.f;
+      float T = 0.f, Re = 1.f, dRe = 0.f, Fm = 1.f;
       auto reduced = [&](float rf, float T0) -> bool {
         const float phif = phi_of_f(h, rf);
         const float Tmin = (phif - h.phi0) / (nn + 1.0f);
@@ -1139,6 +1139,7 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_presolve(
           s = sn;
         }
         if (!(fabsf(F) < 1e-4f)) return false;
+        Fm = F;
         const float In = sm.In, Ip = sm.Ip, Im = sm.Im, Jm = sm.Jm, Jn = sm.Jn;
         const float Egf = four_pi * rho0 * (1.5f * T * Ip + Jn);
         const float dEp = four_pi / 3.0f * (r3v - rf * rf * rf) * Ps;
@@ -1175,7 +1176,7 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_presolve(
         }
       }
       bool have_prev = false, have_br = false, done = false;
-      float v_ok = 0.f, T_ok = 0.f;
+      float v_ok = 0.f, T_ok = 0.f, Re_ok = 0.f, F_ok = 0.f;
       for (int it = 0; it < 40; ++it) {
         const float rf = expf(v);
         if (!reduced(rf, Tw)) break;
@@ -1187,6 +1188,8 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_presolve(
           done = true;
           v_ok = v;
           T_ok = T;
+          Re_ok = Re;
+          F_ok = Fm;
           if (!again) break;
         } else if (done) {
           break;  // the extra step went astray: keep the point below 1e-4
@@ -1211,12 +1214,59 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_presolve(
       if (done) {
         g0 = v_ok - logf(h.rvir);
         g1 = logf(T_ok * h.rvir / h.GM);
+        rE = Re_ok;
+        // the normalised gas-mass residual from F = ln of the ratio of gas masses
+        rM = expm1f(F_ok) * (float)((P.fb * H.M - H.Mstar) / (P.fb * H.M));
       }
     }
     if (lane == 0) {
       guess[i] = (double)g0;
       guess[n + i] = (double)g1;
+      if (res32) {
+        res32[i] = rE;
+        res32[n + i] = rM;
+      }
     }
+  }
+}
+
+// The FP32 pre-solve's solution as the answer (BP_SOLVE_FP32_GATED): a halo whose FP32
+// energy and gas-mass residuals are both within the gate keeps (r_f, T) of the pre-solve, and
+// its central density and pressure follow in FP64 from the pressure condition at r_f,
+// rho0 = P_s / (T theta(r_f)^(n+1)), P0 = rho0 T; the residual fields hold the FP32 values.
+// Any other halo of the solve is marked FALLBACK (the full FP64 solve follows), and so is a
+// halo the caller gave no finite starting point (seed: the caller's guess, or null).
+__global__ void k_accept32(BpParams P, int64_t n, const Halo* __restrict__ halos,
+                           const int32_t* __restrict__ okv, const double* __restrict__ seed,
+                           const double* __restrict__ guess, const float* __restrict__ res32,
+                           double gate, double* model, int32_t* status, int64_t* nbad,
+                           int64_t* nfallback) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n || !okv[i]) return;
+  const Halo h = halos[i];
+  const double g0 = guess[i], g1 = guess[n + i];
+  const float rE = res32[i], rM = res32[n + i];
+  bool ok = isfinite(g0) && isfinite(g1) && fabsf(rE) <= gate && fabsf(rM) <= gate;
+  if (seed) ok = ok && isfinite(seed[i]) && isfinite(seed[n + i]);
+  double rf = 0, T = 0, thf = 0, rho0 = 0;
+  if (ok) {
+    rf = h.rvir * exp(g0);
+    T = exp(g1) * h.GM / h.rvir;
+    thf = 1.0 + (h.phi0 - phi_of(h, rf)) / ((P.n_poly + 1.0) * T);
+    ok = thf > 0.0;
+    if (ok) rho0 = h.Ps / (T * pow(thf, P.n_poly + 1.0));
+  }
+  auto put = [&](int f, double v) { model[(int64_t)f * n + i] = v; };
+  put(BP_M_T, ok ? T : 0.0);
+  put(BP_M_RHO0, ok ? rho0 : 0.0);
+  put(BP_M_P0, ok ? rho0 * T : 0.0);
+  put(BP_M_RF, ok ? rf : 0.0);
+  put(BP_M_RESM, ok ? (double)rM : NAN);
+  put(BP_M_RESE, ok ? (double)rE : NAN);
+  status[i] = ok ? BP_HALO_OK : BP_HALO_FALLBACK;
+  if (!ok) {
+    atomicAdd((unsigned long long*)nbad, 1ull);
+    atomicAdd((unsigned long long*)nfallback, 1ull);
   }
 }
 
@@ -1224,20 +1274,24 @@ __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_presolve(
 
 // presolve: run the FP32 pre-solve and start the FP64 solve from its result
 // n_bad: halos whose status is not OK; n_fallback: those of them marked FALLBACK
+// accept32: the pre-solve's solution is the answer where its FP32 residuals are within
+// X.gate (k_accept32), every other halo is marked FALLBACK
 static int solve_launch(bp_ctx* ctx, int64_t n, const double* Mvir, const double* c,
                         const double* z, double* model, int32_t* status, double tol,
                         SolveExtra X, int64_t* n_bad, int64_t* n_fallback,
-                        bool presolve = false) {
+                        bool presolve = false, bool accept32 = false) {
   int r = upload_constants(ctx);
   if (r) return r;
   Halo* halos;
   if ((r = bp_ws(ctx, WS_HALO,
-                 (size_t)n * (sizeof(Halo) + 2 * sizeof(double) + 2 * sizeof(int32_t)) + 64,
+                 (size_t)n * (sizeof(Halo) + 2 * sizeof(double) + 2 * sizeof(int32_t) +
+                              2 * sizeof(float)) + 64,
                  (void**)&halos)))
     return r;
   double* pguess = reinterpret_cast<double*>(halos + n);
   int32_t* okv = reinterpret_cast<int32_t*>(pguess + 2 * n);
   int32_t* okv_nested = okv + n;  // halos the polish leaves to the nested iteration
+  float* res32 = reinterpret_cast<float*>(okv_nested + n);  // FP32 residuals of the pre-solve
   BP_CUDA(ctx, cudaMemsetAsync(ctx->d_counter, 0, sizeof(int64_t), ctx->stream));
   BP_CUDA(ctx, cudaMemsetAsync(ctx->d_counter + 3, 0, sizeof(int64_t), ctx->stream));
   // halos per warp: enough warps to fill the GPU, the rest shared out 1..32 per warp
@@ -1250,13 +1304,19 @@ static int solve_launch(bp_ctx* ctx, int64_t n, const double* Mvir, const double
   k_setup<<<(unsigned)((n + sb - 1) / sb), sb, 0, ctx->stream>>>(
       ctx->p, ctx->t, n, Mvir, c, z, model, status, ctx->d_counter, X, halos, okv);
   BP_LAUNCH_CHECK(ctx, "k_setup launch");
+  const double* seed = X.guess;  // the caller's starting points (or null)
   if (presolve) {
     k_presolve<<<(unsigned)blocks, 32 * SOLVE_WARPS, 0, ctx->stream>>>(ctx->p, n, X, hpw, halos,
-                                                                       okv, pguess);
+                                                                       okv, pguess, res32);
     BP_LAUNCH_CHECK(ctx, "k_presolve launch");
     X.guess = pguess;
   }
-  if (X.guess) {
+  if (presolve && accept32) {
+    k_accept32<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(
+        ctx->p, n, halos, okv, seed, pguess, res32, X.gate, model, status, ctx->d_counter,
+        ctx->d_counter + 3);
+    BP_LAUNCH_CHECK(ctx, "k_accept32 launch");
+  } else if (X.guess) {
     // starting points: two halos per warp; the halos without one get the nested iteration
     BP_CUDA(ctx, cudaMemsetAsync(okv_nested, 0, (size_t)n * sizeof(int32_t), ctx->stream));
     const int64_t pwarps = (n + POLISH_H * (int64_t)hpw - 1) / (POLISH_H * (int64_t)hpw);
@@ -1292,7 +1352,7 @@ static int solve_args(bp_ctx* ctx, int64_t n, const double* Mvir, const double* 
   if (n < 0) return bp_fail(ctx, BP_EINVAL, "bp_solve_halos: n < 0");
   if (n > 0 && (!Mvir || !c || !z || !model || !status))
     return bp_fail(ctx, BP_EINVAL, "bp_solve_halos: null pointer");
-  if (mode != BP_SOLVE_FP64 && mode != BP_SOLVE_FP64_SEEDED)
+  if (mode != BP_SOLVE_FP64 && mode != BP_SOLVE_FP64_SEEDED && mode != BP_SOLVE_FP32_GATED)
     return bp_fail(ctx, BP_EINVAL, "bp_solve_halos: unknown mode");
   return BP_OK;
 }
@@ -1327,14 +1387,18 @@ extern "C" int bp_solve_halos_ex(bp_ctx* ctx, int64_t n, const double* Mvir, con
   // pre-solve and the Newton from it; (3) for those still marked: the full nested FP64
   // iteration.  A Newton stage accepts a halo when both residuals are below the gate (the
   // tolerance for the unseeded pre-solve stages, the caller's gate for a seeded one).
-  const bool seeded = mode == BP_SOLVE_FP64_SEEDED && guess != nullptr;
+  const bool gated32 = mode == BP_SOLVE_FP32_GATED;
+  if (gated32 && !(gate > 0))
+    return bp_fail(ctx, BP_EINVAL, "bp_solve_halos_ex: BP_SOLVE_FP32_GATED needs gate > 0");
+  const bool seeded = (mode == BP_SOLVE_FP64_SEEDED || gated32) && guess != nullptr;
   const bool presolve = guess == nullptr || seeded;
   if (presolve) {
     X.max_outer = seeded && max_iter > 0 ? max_iter : 8;
-    X.gate = seeded && gate > 0 ? gate : tol;
+    X.gate = (seeded || gated32) && gate > 0 ? gate : tol;
   }
   int64_t fb = 0;
-  if ((r = solve_launch(ctx, n, Mvir, c, z, model, status, tol, X, &bad, &fb, presolve)))
+  if ((r = solve_launch(ctx, n, Mvir, c, z, model, status, tol, X, &bad, &fb, presolve,
+                        gated32)))
     return r;
   ctx->last_fallback = fb;
   for (int stage = presolve ? 3 : 2; fb > 0 && stage <= 3; ++stage) {

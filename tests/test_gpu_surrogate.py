@@ -152,3 +152,75 @@ def test_surrogate_solve_at_scale(api, trained):
     rf_p = m_plain[api.MF["r_f"]].cpu().numpy()
     rf_s = m_sur[api.MF["r_f"]].cpu().numpy()
     assert np.max(np.abs(rf_s / rf_p - 1)) < 1e-3
+
+
+def test_gated_surrogate_solve_matches_oracle_with_fallback(orc, api, trained):
+    """polish_iter = 0: the seeded FP32 pre-solve is the answer where both of its residuals are
+    within the gate (1e-4); halos outside the training hull, or above the gate, get the full
+    FP64 solve.  Accepted solutions agree with the oracle's to the gate's accuracy."""
+    c, s, _ = trained
+    M, cc, z, prm = I.surrogate_halos(300, seed=14)
+    M = np.concatenate([M, [3e15, 2e11]])
+    cc = np.concatenate([cc, [4.0, 10.0]])
+    z = np.concatenate([z, [0.5, 3.5]])
+    prm = np.concatenate([prm, [[5e-6, 5e-6], [0.02, 0.02], [0.05, 0.05]]], axis=1)
+    model, status = s.solve(c, cuda(M), cuda(cc), cuda(z), cuda(prm), polish_iter=0)
+    assert (status.cpu().numpy() == 0).all()
+    assert c.last_fallback_count() >= 2  # the two halos outside the hull
+    mg = model.cpu().numpy()
+    F = orc.F
+    for k in list(range(0, 300, 23)) + [300, 301]:
+        ip = orc.icm_default(eps_star=float(prm[0, k]), f_star=float(prm[1, k]),
+                             eps_dm=float(prm[2, k]))
+        mo = orc.solve_halos(M[k:k + 1], cc[k:k + 1], z[k:k + 1], ip=ip)[0]
+        for name in ("r_f", "T", "rho0", "P0"):
+            assert mg[api.MF[name], k] == pytest.approx(mo[F[name]], rel=1e-3), (k, name)
+    assert np.abs(mg[api.MF["res_m"]]).max() <= 1e-4
+    assert np.abs(mg[api.MF["res_e"]]).max() <= 1e-4
+    # the full-solve halos carry FP64 residuals of the plain tolerance
+    assert np.abs(mg[api.MF["res_e"], 300:]).max() <= 1e-10
+
+
+def test_gated_surrogate_gain_and_pasted_y_error(api, trained):
+    """What the trained network gains: the gated surrogate solve against the plain solve (FP32
+    pre-solve + FP64 Newton to 1e-10) on 2e5 halos, and the pasted y of a 1000-halo catalogue
+    with each solve.  The surrogate must be at least 1.5x faster and the map within 1e-3."""
+    c, s, _ = trained
+    M, cc, z, prm = I.surrogate_halos(200000, seed=15)
+    args = [cuda(M), cuda(cc), cuda(z), cuda(prm)]
+    for _ in range(2):  # warm up both paths
+        c.solve_halos_ex(*args, raise_on_noconv=False)
+        s.solve(c, *args, polish_iter=0, raise_on_noconv=False)
+
+    def timed(fn, reps=5):
+        ts = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return float(np.median(ts))
+
+    t_plain = timed(lambda: c.solve_halos_ex(*args, raise_on_noconv=False))
+    t_sur = timed(lambda: s.solve(c, *args, polish_iter=0, raise_on_noconv=False))
+    print(f"gated surrogate {t_sur:.2f} ms, plain {t_plain:.2f} ms, "
+          f"fallbacks {c.last_fallback_count()} of {M.size}")
+    assert t_plain / t_sur >= 1.5
+    cat, g = I.halo_catalog(n=1000, npix=256, seed=16)
+    tab1 = cuda(np.stack([np.full(1000, 3.97e-6), np.full(1000, 0.026), np.zeros(1000)]))
+    gg = api.geom(g.nx, g.ny, g.theta0_x, g.theta0_y, g.dtheta)
+    ys = []
+    for solve in (lambda a: c.solve_halos_ex(*a, params=tab1),
+                  lambda a: s.solve(c, *a, tab1, polish_iter=0)):
+        mod, st = solve([cuda(cat.M), cuda(cat.c), cuda(cat.z)])
+        maps = api.Maps.zeros(gg)
+        c.paste_halos(cuda(cat.thx), cuda(cat.thy), cuda(cat.vlos), mod, st, gg, maps,
+                      ap_r500=3.0)
+        c.finalize(gg, maps)
+        ys.append(maps.y[0].double())
+    err = float(torch.linalg.norm(ys[1] - ys[0]) / torch.linalg.norm(ys[0]))
+    print(f"pasted y relative L2 vs the plain solve: {err:.2e}")
+    assert err <= 1e-3
