@@ -173,15 +173,17 @@ def phase_bandwidth(ph, n, n_pairs, nx, ny, hbm_peak):
     return out
 
 
-def deposit_work(rec, nx, ny, tile=64):
-    """Algorithmic work of one deposit launch, computed with torch on the records' device:
-    flops = 2 per pixel update (one FMA) per map the particle touches (field particles carry
-    no y) over every particle's clipped 2h x 2h footprint; pixel updates; and the (tile,
-    particle) pairs of the pair list (the tiles each footprint's pixel box touches)."""
+def deposit_work(rec, nx, ny, tile=64, sspan=0):
+    """Algorithmic work of one deposit, computed with torch on the records' device, split
+    between the tensor-core kernel and the small-particle kernel (particles whose clipped
+    pixel box is at most `sspan` pixels wide; 0: none): flops = 2 per pixel update (one FMA)
+    per map the particle touches (field particles carry no y) over every particle's clipped
+    2h x 2h footprint; pixel updates; and the (tile, particle) pairs of the pair list (the
+    tiles each footprint's pixel box touches)."""
     import torch
 
     ints = rec.view(torch.int32)
-    flops = updates = pairs = 0.0
+    w = {k: 0.0 for k in ("flops", "flops_tc", "updates", "pairs", "pairs_tc")}
     for a in range(0, rec.shape[0], 50_000_000):
         r = rec[a:a + 50_000_000]
         iv = ints[a:a + 50_000_000]
@@ -191,16 +193,26 @@ def deposit_work(rec, nx, ny, tile=64):
         i0, i1 = torch.floor(px - hp), torch.floor(px + hp)
         j0, j1 = torch.floor(py - hp), torch.floor(py + hp)
         ok = (iv[:, 5] != 2) & (i1 >= 0) & (i0 <= nx - 1) & (j1 >= 0) & (j0 <= ny - 1)
-        ci0, ci1 = i0.clamp(0, nx - 1), i1.clamp(0, nx - 1)
-        cj0, cj1 = j0.clamp(0, ny - 1), j1.clamp(0, ny - 1)
-        upd = ((ci1 - ci0 + 1) * (cj1 - cj0 + 1))[ok]
-        maps = torch.where(r[:, 3][ok] != 0, 2.0, 1.0).double()
+        ci0, ci1 = i0.clamp(0, nx - 1)[ok], i1.clamp(0, nx - 1)[ok]
+        cj0, cj1 = j0.clamp(0, ny - 1)[ok], j1.clamp(0, ny - 1)[ok]
+        upd = (ci1 - ci0 + 1) * (cj1 - cj0 + 1)
+        fl = 2.0 * upd * torch.where(r[:, 3][ok] != 0, 2.0, 1.0).double()
         tp = ((torch.floor(ci1 / tile) - torch.floor(ci0 / tile) + 1) *
-              (torch.floor(cj1 / tile) - torch.floor(cj0 / tile) + 1))[ok]
-        flops += float(2.0 * (upd * maps).sum())
-        updates += float(upd.sum())
-        pairs += float(tp.sum())
-    return flops, updates, int(pairs)
+              (torch.floor(cj1 / tile) - torch.floor(cj0 / tile) + 1))
+        big = torch.maximum(ci1 - ci0, cj1 - cj0) + 1 > sspan
+        w["flops"] += float(fl.sum())
+        w["flops_tc"] += float(fl[big].sum())
+        w["updates"] += float(upd.sum())
+        w["pairs"] += float(tp.sum())
+        w["pairs_tc"] += float(tp[big].sum())
+    w["pairs"], w["pairs_tc"] = int(w["pairs"]), int(w["pairs_tc"])
+    return w
+
+
+def small_span_auto(nx, ny, tile=64):
+    """The small-particle span the library picks by default: 8 pixels on maps with at least
+    4 tiles per SM, else 0 (every particle on the tensor cores)."""
+    return 8 if -(-nx // tile) * -(-ny // tile) >= 4 * SM_COUNT else 0
 
 
 def ncu_traffic(kernel_key):
@@ -222,23 +234,35 @@ def ncu_traffic(kernel_key):
     return d.get("dram_bytes_per_launch_scaled")
 
 
-def deposit_roofline(kernel, dep_ms, work, peaks, traffic_key):
-    """Roofline entry of the deposit from its live CUDA-event duration and its algorithmic
-    flops (against the TF32 tensor peak of measured), plus the MMA work it issues."""
-    flops, updates, pairs = work
-    achieved = flops / (dep_ms * 1e-3) / 1e12
+def deposit_roofline(kernel, ph, work, peaks, traffic_key):
+    """Roofline entry of the tensor-core deposit from its live CUDA-event duration and the
+    algorithmic flops of the particles it deposits (against the TF32 tensor peak of
+    measured), plus the MMA work it issues; the small-particle kernel (FP32 ALU and shared
+    memory) beside it."""
+    dep_ms, small_ms = ph["deposit"], ph.get("deposit_small", 0.0)
+    achieved = work["flops_tc"] / (dep_ms * 1e-3) / 1e12
     peak = tf32_peak(peaks)
     # per (tile, particle) pair the kernel issues a 128 x 64 rank-1 update in three
     # split-TF32 products
-    mma = pairs * 128 * 64 * 2 * 3
-    return {"kernel": kernel, "bound": "tensor", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": ncu_traffic(traffic_key),
-            "deposit_ms": dep_ms, "algorithmic_flops_per_launch": flops,
-            "pixel_updates": updates, "tile_pairs": pairs, "mma_flops_issued_per_launch": mma,
-            "mma_tflops_issued": mma / (dep_ms * 1e-3) / 1e12,
-            "frac_fp32_alu_peak": achieved / fp32_peak(peaks),
-            "peak_note": f"of measured: bf16 burst {float(peaks.get('bf16_tflops', 1900.0))} "
-                         "TFLOP/s x 1.1/2.25 (nominal TF32/BF16 dense ratio)"}
+    mma = work["pairs_tc"] * 128 * 64 * 2 * 3
+    out = {"kernel": kernel, "bound": "tensor", "achieved": achieved, "peak": peak,
+           "unit": "TFLOP/s", "frac": achieved / peak, "traffic": ncu_traffic(traffic_key),
+           "deposit_ms": dep_ms, "algorithmic_flops_per_launch": work["flops_tc"],
+           "pixel_updates_all": work["updates"], "tile_pairs": work["pairs_tc"],
+           "mma_flops_issued_per_launch": mma,
+           "mma_tflops_issued": mma / (dep_ms * 1e-3) / 1e12,
+           "frac_fp32_alu_peak": achieved / fp32_peak(peaks),
+           "peak_note": f"of measured: bf16 burst {float(peaks.get('bf16_tflops', 1900.0))} "
+                        "TFLOP/s x 1.1/2.25 (nominal TF32/BF16 dense ratio)"}
+    if small_ms > 0:
+        fs = work["flops"] - work["flops_tc"]
+        out["small"] = {"kernel": "k_deposit_small", "bound": "alu", "ms": small_ms,
+                        "algorithmic_flops_per_launch": fs,
+                        "tile_pairs": work["pairs"] - work["pairs_tc"],
+                        "achieved": fs / (small_ms * 1e-3) / 1e12, "peak": fp32_peak(peaks),
+                        "unit": "TFLOP/s",
+                        "frac": fs / (small_ms * 1e-3) / 1e12 / fp32_peak(peaks)}
+    return out
 
 
 # ------------------------------------------------------------------ CPU oracle legs
@@ -404,7 +428,7 @@ def headline(api, args, dev, rank, world, peaks):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    work = deposit_work(rec, g.nx, g.ny)
+    work = deposit_work(rec, g.nx, g.ny, sspan=small_span_auto(g.nx, g.ny))
     ctx.set_timing(True)
     ctx.phase_times()
     sampler = ClockSampler(int(os.environ.get("LOCAL_RANK", 0)))
@@ -498,8 +522,8 @@ def headline(api, args, dev, rank, world, peaks):
         "phase_ms": mean_ph,
         "phase_note": "the particle chain's phases on the main stream (solve .. finalize); the "
                       "halo paste runs on a second stream beside it",
-        "phase_hbm": phase_bandwidth(mean_ph, n, work[2], g.nx, g.ny, hbm),
-        "roofline": deposit_roofline("k_deposit_tc", mean_ph["deposit"], work, peaks,
+        "phase_hbm": phase_bandwidth(mean_ph, n, work["pairs"], g.nx, g.ny, hbm),
+        "roofline": deposit_roofline("k_deposit_tc", mean_ph, work, peaks,
                                      "k_deposit_tc_c2"),
         "e2e": {"value": n_all / (t_e2e * 1e-3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d_bytes * world, "d2h_bytes_per_step": d2h_bytes * world,
@@ -565,7 +589,7 @@ def lightcone_4m_section(api, dev, args, peaks):
     for _ in range(3):
         step()
     torch.cuda.synchronize()
-    work = deposit_work(rec, g.nx, g.ny)
+    work = deposit_work(rec, g.nx, g.ny, sspan=small_span_auto(g.nx, g.ny))
     ctx.set_timing(True)
     ctx.phase_times()
     ms, phases = [], []
@@ -584,9 +608,9 @@ def lightcone_4m_section(api, dev, args, peaks):
                        "3000 halos (60% halo / 40% field particles), 1024^2 y and kSZ maps; "
                        "plus HP of the 3000 halos (second stream)",
            "ms_per_step": t_step, "particles_per_s": n / (t_step * 1e-3), "phase_ms": mean_ph,
-           "phase_hbm": phase_bandwidth(mean_ph, n, work[2], g.nx, g.ny,
+           "phase_hbm": phase_bandwidth(mean_ph, n, work["pairs"], g.nx, g.ny,
                                         float(peaks.get("hbm_gbs", 6780.4))),
-           "roofline": deposit_roofline("k_deposit_tc", mean_ph["deposit"], work, peaks,
+           "roofline": deposit_roofline("k_deposit_tc", mean_ph, work, peaks,
                                         "k_deposit_tc_c1")}
     ctx.close()
     ctx_hp.close()

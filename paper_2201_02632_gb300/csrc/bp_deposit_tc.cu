@@ -11,8 +11,8 @@
 // truncated-power form of the piecewise quartic: with a = |u|,
 //   w_left(a) = (2/3) max(1 - a, 0)^4 - (8/3) max(1/2 - a, 0)^4,
 // which is the inner piece 1/2 - (4/3) a + (8/3) a^3 - 2 a^4 below a = 1/2, the outer piece
-// (2/3)(1 - a)^4 above and zero beyond a = 1: no branch and no piece selection (9 FP32
-// instructions).  Products are formed in TF32 with each FP32 operand split into a TF32 head
+// (2/3)(1 - a)^4 above and zero beyond a = 1: no branch and no piece selection (two
+// saturating FMAs, four multiplies and a sign flip).  Products are formed in TF32 with each FP32 operand split into a TF32 head
 // and an exact tail, a b ~ ah bh + ah bt + at bh (three MMAs; about 1e-6 relative error per
 // product).  Each group of TC_G chunks accumulates in FP32 in tensor memory and is then
 // folded into a compensated (sum, compensation) pair by Kahan's summation, also kept in
@@ -20,11 +20,12 @@
 //
 // CTA: 256 threads (8 warps), persistent over work units, 2 CTAs per SM.  Warp w owns the
 // particles 4w .. 4w + 3 of every chunk (K slots 4w .. 4w + 3):
-//  - it gathers their records itself (lanes 0-7, cp.async into a 3-chunk ring, two chunks
-//    ahead), and lanes 0-7 turn them into per-(particle, axis) fields: position relative to
-//    the tile, fraction, kernel scales, the cell holding the centre, the edge value at 64.
-//    h = 0 becomes an infinite kernel scale (a nearest-grid-point weight without a branch)
-//    and a slot past the end of the unit a particle far outside the tile with Y = B = 0;
+//  - it gathers their records itself, TC_BATCH = 4 chunks (16 particles) at a time, one
+//    batch ahead (cp.async, one 16-byte half record per lane), and at the start of a batch
+//    its 32 lanes turn them into per-(particle, axis) fields: position relative to the tile,
+//    fraction, kernel scales, the cell holding the centre, the edge value at 64.  h = 0
+//    becomes an infinite kernel scale (a nearest-grid-point weight without a branch) and a
+//    slot past the end of the unit a particle far outside the tile with Y = B = 0;
 //  - lane l evaluates the kernel at edges l and l + 32 of both axes and takes edges l + 1,
 //    l + 33 from its neighbour, so every edge is evaluated once;
 //  - it writes its 16-byte chunk (4 particles) of rows l, l + 32 (and 64 + l, 96 + l of A)
@@ -54,7 +55,7 @@ constexpr int TC_CH = 32;        // particles per chunk: one 128-byte swizzle ro
 constexpr int TC_G = 4;          // chunks per FP32 accumulation group (128 particles)
 constexpr int TC_WARPS = 8;
 constexpr int TC_THREADS = 32 * TC_WARPS;
-constexpr int TC_RING = 3;       // record ring per warp (chunks)
+constexpr int TC_BATCH = 4;      // chunks whose records and fields a warp prepares at once
 constexpr uint32_t TC_COLS = 256;
 constexpr uint32_t COL_HI = 128, COL_LO = 192;
 constexpr uint32_t TC_IDESC = bptc::idesc_tf32(128, TC_TS);
@@ -84,8 +85,8 @@ struct TcField {
 
 struct TcSmem {
   TcStage st[2];
-  float4 raw[TC_WARPS][TC_RING][4][2];  // records (two 16-byte halves) per warp and chunk
-  TcField fld[TC_WARPS][4];
+  float4 raw[TC_WARPS][4 * TC_BATCH][2];  // records (two 16-byte halves) of the next batch
+  TcField fld[TC_WARPS][4 * TC_BATCH];    // fields of the warp's particles of this batch
   uint64_t mbar[2];     // per stage: the chunk's MMAs completed (tcgen05.commit)
   uint64_t full[2];     // per stage: all eight warps wrote their operands (release arrivals)
   uint32_t arrive[2];   // warps arrived at each stage (cumulative, relaxed; the eighth issues)
@@ -233,82 +234,82 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
       }
       tmem_wait_st();
     }
-    const int nchunks = (int)((U.end - U.begin + TC_CH - 1) / TC_CH);
-    // record pipeline of lanes 0-7: particle gp of this warp's four, record half gh
-    const int gp = lane & 3, gh = (lane >> 2) & 1;
-    const int64_t q0 = U.begin + 4 * w + gp;  // this lane's particle in chunk 0
+    const int len = (int)(U.end - U.begin);  // a unit holds at most 2^30 pairs
+    const uint32_t* uvals = pvals + U.begin;
+    const int nchunks = (len + TC_CH - 1) / TC_CH;
+    // records of this warp's particles, a batch of TC_BATCH chunks at a time: lane l copies
+    // half l & 1 of particle l >> 1 of the batch (chunk (l >> 1) / 4, slot 4 w + (l >> 1) % 4)
+    const int cp_p = lane >> 1, cp_h = lane & 1;
+    const int cp_q0 = (cp_p >> 2) * TC_CH + 4 * w + (cp_p & 3);  // relative to the unit
     uint32_t pv_next = 0;
-    if (lane < 8) {
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const int64_t q = q0 + (int64_t)c * TC_CH;
-        if (q < U.end) cp_async16(&S.raw[w][c][gp][gh], rec + 2 * (int64_t)pvals[q] + gh);
-        cp_async_commit();
-      }
-      const int64_t q2 = q0 + 2 * TC_CH;
-      if (q2 < U.end) pv_next = pvals[q2];
+    {
+      if (cp_q0 < len) cp_async16(&S.raw[w][cp_p][cp_h], rec + 2 * (int64_t)uvals[cp_q0] + cp_h);
+      cp_async_commit();
+      const int q1 = cp_q0 + TC_BATCH * TC_CH;
+      if (q1 < len) pv_next = uvals[q1];
     }
     bool aborted = false;
     for (int c = 0; c < nchunks; ++c, ++gc) {
       const int s = (int)(gc & 1);
-      // 1. records of chunk c + 2 on their way, index of chunk c + 3; chunk c's have landed
-      if (lane < 8) {
-        const int64_t q2 = q0 + (int64_t)(c + 2) * TC_CH;
-        if (q2 < U.end)
-          cp_async16(&S.raw[w][(c + 2) % TC_RING][gp][gh], rec + 2 * (int64_t)pv_next + gh);
+      const int cb = c % TC_BATCH;
+      if (cb == 0) {
+        // 1. the batch's records have landed: its fields, one (particle, axis) per lane
+        cp_async_wait_all();
+        __syncwarp();
+        {
+          const int p = lane & 15, ax = lane >> 4;
+          const int q = (c + (p >> 2)) * TC_CH + 4 * w + (p & 3);
+          TcField& F = S.fld[w][p];
+          float4 a;
+          float e64;
+          int kc;
+          if (q < len) {
+            const float4 r0 = S.raw[w][p][0], r1 = S.raw[w][p][1];
+            float f = ax ? r0.y : r0.x;
+            const int pr = __float_as_int(ax ? r1.w : r1.z) - (ax ? y0 : x0);
+            const bool ngp = !(r0.z > 0.f);
+            const float ih = ngp ? NGP_IH : __frcp_rn(r0.z);
+            if (ngp && !(f > 0.f)) f = 1.0e-30f;  // exactly on an edge: the cell to its right
+            a = make_float4((float)pr, f, KT * ih, KS * ih);
+            kc = pr + (f > 0.f ? 0 : -1);
+            e64 = edge_split(__fsub_rn(__fsub_rn((float)TC_TS, a.x), a.y), a.z, a.w);
+            if (ax == 0) {
+              F.m.z = r0.w;
+              F.m.w = r1.x;
+            }
+          } else {  // empty slot: far outside the tile, no signal
+            a = make_float4(FAR, 0.5f, KT, KS);
+            kc = -(1 << 30);
+            e64 = 0.f;
+            if (ax == 0) {
+              F.m.z = 0.f;
+              F.m.w = 0.f;
+            }
+          }
+          F.ax[ax] = a;
+          if (ax == 0) {
+            F.m.x = e64;
+            F.kc.x = kc;
+          } else {
+            F.m.y = e64;
+            F.kc.y = kc;
+          }
+        }
+        __syncwarp();
+        // 2. the next batch's records on their way (the ring slot is free: its fields are
+        // derived), the index of the one after
+        const int q1 = cp_q0 + (c + TC_BATCH) * TC_CH;
+        if (q1 < len) cp_async16(&S.raw[w][cp_p][cp_h], rec + 2 * (int64_t)pv_next + cp_h);
         cp_async_commit();
-        const int64_t q3 = q2 + TC_CH;
-        pv_next = q3 < U.end ? pvals[q3] : 0u;
-        cp_async_wait_group2();
+        const int q2 = q1 + TC_BATCH * TC_CH;
+        pv_next = q2 < len ? uvals[q2] : 0u;
       }
-      __syncwarp();
-      // 2. fields of this warp's particles of chunk c: lane t < 8 -> particle t & 3, axis t >> 2
-      if (lane < 8) {
-        const int p = lane & 3, ax = lane >> 2;
-        const int64_t q = q0 - gp + p + (int64_t)c * TC_CH;
-        TcField& F = S.fld[w][p];
-        float4 a;
-        float e64;
-        int kc;
-        if (q < U.end) {
-          const float4 r0 = S.raw[w][c % TC_RING][p][0], r1 = S.raw[w][c % TC_RING][p][1];
-          float f = ax ? r0.y : r0.x;
-          const int pr = __float_as_int(ax ? r1.w : r1.z) - (ax ? y0 : x0);
-          const bool ngp = !(r0.z > 0.f);
-          const float ih = ngp ? NGP_IH : __frcp_rn(r0.z);
-          if (ngp && !(f > 0.f)) f = 1.0e-30f;  // exactly on an edge: the cell to its right
-          a = make_float4((float)pr, f, KT * ih, KS * ih);
-          kc = pr + (f > 0.f ? 0 : -1);
-          e64 = edge_split(__fsub_rn(__fsub_rn((float)TC_TS, a.x), a.y), a.z, a.w);
-          if (ax == 0) {
-            F.m.z = r0.w;
-            F.m.w = r1.x;
-          }
-        } else {  // empty slot: far outside the tile, no signal
-          a = make_float4(FAR, 0.5f, KT, KS);
-          kc = -(1 << 30);
-          e64 = 0.f;
-          if (ax == 0) {
-            F.m.z = 0.f;
-            F.m.w = 0.f;
-          }
-        }
-        F.ax[ax] = a;
-        if (ax == 0) {
-          F.m.x = e64;
-          F.kc.x = kc;
-        } else {
-          F.m.y = e64;
-          F.kc.y = kc;
-        }
-      }
-      __syncwarp();
       // 3. weights of particles 4w .. 4w + 3 (in registers: the stage may still be busy)
       TcStage& T = S.st[s];
       float wx0[4], wx1[4], wy0[4], wy1[4], Yk[4], Bk[4];
 #pragma unroll
       for (int p = 0; p < 4; ++p) {
-        const TcField& F = S.fld[w][p];
+        const TcField& F = S.fld[w][4 * cb + p];
         const float4 m = F.m;
         const int2 kc = F.kc;
         axis_weights(lane, lane_f, F.ax[0], m.x, kc.x, wx0[p], wx1[p]);
@@ -390,7 +391,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
       // group (c - 2) / TC_G + 2), which wait for this warp's arrival there
       if (fold_now) fold((c - 2) / TC_G);
     }
-    if (lane < 8) cp_async_wait_all();  // no copy outlives the unit
+    cp_async_wait_all();  // no copy outlives the unit
     if (!aborted) {
       // drain: the last chunks of the unit, folding the last group(s)
       for (int64_t gw = max(gdone, gc - 2); gw < gc; ++gw) {

@@ -213,8 +213,10 @@ __device__ __forceinline__ float bp_wsplit_inv(float dx, float inv_h) {
 constexpr float BP_KT = 0.9036020040512085f;  // (2/3)^(1/4)
 constexpr float BP_KS = 1.277886152267456f;   // (8/3)^(1/4)
 __device__ __forceinline__ float bp_edge_split(float dx, float k1, float k2) {
-  const float t = fmaxf(fmaf(-k1, fabsf(dx), BP_KT), 0.f);            // KT (1 - a), clipped
-  const float s = fmaxf(fmaf(-k2, fabsf(dx), 0.5f * BP_KS), 0.f);     // KS (1/2 - a), clipped
+  // KT (1 - a) and KS (1/2 - a), clipped below at 0 (both stay below 1, so clamping to
+  // [0, 1] is the same clip)
+  const float t = __saturatef(fmaf(-k1, fabsf(dx), BP_KT));
+  const float s = __saturatef(fmaf(-k2, fabsf(dx), 0.5f * BP_KS));
   const float A = t * t, B = s * s;
   const float w = fmaf(A, A, -(B * B));
   return __int_as_float(__float_as_int(w) ^ (~__float_as_int(dx) & (int)0x80000000));
