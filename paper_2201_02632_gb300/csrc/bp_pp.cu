@@ -648,13 +648,18 @@ __global__ void __launch_bounds__(256) k_reduce_tiles(const int64_t* __restrict_
 // bp_edge_split (those of the tensor-core deposit) and adds Y wx wy and B wx wy of every
 // covered cell to the tile's accumulators as 64-bit fixed-point integers, with shared-memory
 // atomics.  Integer sums do not depend on the order of the additions: the result is
-// deterministic.  Each map's scale 2^S is fixed per tile from its largest |Y| (|B|) and the
-// particle count n, so that no cell sum can overflow (a cell's sum is at most n max|Y|) and the
-// quantum is 2^-61 n max|Y|: far below the FP32 rounding of the products.
+// deterministic.  Each map's scale 2^S follows the tile's largest |Y| (|B|) and its particle
+// count n, so that no cell sum can overflow (a cell's sum is at most n max|Y|) and the
+// quantum is 2^-61 n max|Y|: far below the FP32 rounding of the products.  The records are
+// read once: the largest value so far sets the scale, and a larger one later shifts the
+// sums so far down to the new scale.
 constexpr int SMALL_MAX = 8;
 constexpr int SMALL_THREADS = 512;
 struct SmallSmem {
-  unsigned long long acc[2][64 * 64];      // y, b of the 64 x 64 tile
+  // y, b of the 64 x 64 tile as 64-bit two's-complement integers, kept as low and high
+  // 32-bit words (lo[m][q], hi[m][q])
+  uint32_t lo[2][64 * 64];
+  uint32_t hi[2][64 * 64];
   float wx[SMALL_THREADS][SMALL_MAX + 1];  // each thread's column weights (padded rows)
   float amax[2][SMALL_THREADS / 32];
 };
@@ -667,6 +672,16 @@ __device__ __forceinline__ long long small_fix(float v) {
   const long long m = (long long)((b & 0x7fffff) | 0x800000);
   const long long q = e >= 0 ? (m << e) : (e > -24 ? (m >> (-e)) : 0ll);
   return b < 0 ? -q : q;
+}
+
+// acc += v exactly, modulo 2^64, with two 32-bit shared-memory atomics (the pair measured
+// about three times the update rate of one 64-bit shared-memory atomic on this GPU): the
+// low word's previous value tells whether its sum carried into the high word.  The result does not depend on the order of
+// the additions.
+__device__ __forceinline__ void small_add(uint32_t* lo, uint32_t* hi, long long v) {
+  const uint32_t l = (uint32_t)v, h = (uint32_t)((unsigned long long)v >> 32);
+  const uint32_t old = atomicAdd(lo, l);
+  atomicAdd(hi, h + (old + l < old ? 1u : 0u));
 }
 
 // exponent S with n * amax * 2^S < 2^61 (0 when amax is 0)
@@ -688,70 +703,108 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_deposit_small(
   const int64_t b = tstart[4 * (int64_t)t + 1], e = tstart[4 * (int64_t)t + 4];  // classes 1-3
   if (b >= e) return;
   const int x0 = (t % ntx) * 64, y0 = (t / ntx) * 64;
-  for (int q = tid; q < 2 * 64 * 64; q += SMALL_THREADS) (&S.acc[0][0])[q] = 0ull;
-  // 1. the largest |Y| and |B| of the tile's particles
-  float my = 0.f, mb = 0.f;
-  for (int64_t k = b + tid; k < e; k += SMALL_THREADS) {
-    const int64_t pv = pvals[k];
-    my = fmaxf(my, fabsf(rec[2 * pv].w));
-    mb = fmaxf(mb, fabsf(rec[2 * pv + 1].x));
+  for (int q = tid; q < 2 * 64 * 64; q += SMALL_THREADS) {
+    (&S.lo[0][0])[q] = 0u;
+    (&S.hi[0][0])[q] = 0u;
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, o));
-    mb = fmaxf(mb, __shfl_xor_sync(0xffffffffu, mb, o));
-  }
-  if (lane == 0) {
-    S.amax[0][wp] = my;
-    S.amax[1][wp] = mb;
-  }
-  __syncthreads();
-  my = mb = 0.f;
-#pragma unroll
-  for (int q = 0; q < SMALL_THREADS / 32; ++q) {
-    my = fmaxf(my, S.amax[0][q]);
-    mb = fmaxf(mb, S.amax[1][q]);
-  }
-  const int sy = small_scale(my, e - b), sb = small_scale(mb, e - b);
-  // 2. every particle's cells, as fixed-point integers
+  // One pass over the tile's particles, SMALL_THREADS at a time (one per thread, its record
+  // held in registers).  Each map's scale 2^S follows the largest |Y| (|B|) seen so far: it is
+  // set by the first block with a nonzero value and only lowered afterwards, the sums so far
+  // shifted right by the difference (floor: below one quantum per shift).  The order of the
+  // blocks is the sorted order, so the result is still deterministic.
+  const int64_t n = e - b;
+  float run_y = 0.f, run_b = 0.f;  // largest |Y|, |B| so far (the same in every thread)
+  int sy = 0, sb = 0;
   float* wx = S.wx[tid];
-  for (int64_t k = b + tid; k < e; k += SMALL_THREADS) {
-    const int64_t pv = pvals[k];
-    const float4 r0 = rec[2 * pv], r1 = rec[2 * pv + 1];
-    const int ix = __float_as_int(r1.z), iy = __float_as_int(r1.w);
-    int i0, i1, j0, j1;
-    if (!bp_span(ix, r0.x, r0.z, nx, i0, i1) || !bp_span(iy, r0.y, r0.z, ny, j0, j1)) continue;
-    i0 = max(i0, x0);
-    i1 = min(i1, x0 + 63);
-    j0 = max(j0, y0);
-    j1 = min(j1, y0 + 63);
-    if (i0 > i1 || j0 > j1) continue;
-    const bool ngp = !(r0.z > 0.f);
-    const float ih = ngp ? 1.0e38f : __frcp_rn(r0.z);
-    const float k1 = BP_KT * ih, k2 = BP_KS * ih;
-    const float fx = (ngp && !(r0.x > 0.f)) ? 1.0e-30f : r0.x;
-    const float fy = (ngp && !(r0.y > 0.f)) ? 1.0e-30f : r0.y;
-    const int kcx = ix + (fx > 0.f ? 0 : -1), kcy = iy + (fy > 0.f ? 0 : -1);
-    float v = bp_edge_split(__fsub_rn((float)(i0 - ix), fx), k1, k2);
-    for (int i = i0; i <= i1; ++i) {
-      const float vn = bp_edge_split(__fsub_rn((float)(i + 1 - ix), fx), k1, k2);
-      wx[i - i0] = (vn - v) + (i == kcx ? 1.f : 0.f);
-      v = vn;
+  for (int64_t k0 = b; k0 < e; k0 += SMALL_THREADS) {
+    const int64_t k = k0 + tid;
+    const bool valid = k < e;
+    float4 r0 = make_float4(0.f, 0.f, 0.f, 0.f), r1 = r0;
+    if (valid) {
+      const int64_t pv = pvals[k];
+      r0 = rec[2 * pv];
+      r1 = rec[2 * pv + 1];
     }
-    const float Ys = ldexpf(r0.w, sy), Bs = ldexpf(r1.x, sb);
-    const bool has_y = r0.w != 0.f;
-    float u = bp_edge_split(__fsub_rn((float)(j0 - iy), fy), k1, k2);
-    for (int j = j0; j <= j1; ++j) {
-      const float un = bp_edge_split(__fsub_rn((float)(j + 1 - iy), fy), k1, k2);
-      const float wy = (un - u) + (j == kcy ? 1.f : 0.f);
-      u = un;
-      const float ay = Ys * wy, ab = Bs * wy;
-      unsigned long long* ry = &S.acc[0][(j - y0) * 64 + (i0 - x0)];
-      unsigned long long* rb = &S.acc[1][(j - y0) * 64 + (i0 - x0)];
-      for (int c = 0; c <= i1 - i0; ++c) {
-        const float w = wx[c];
-        if (has_y) atomicAdd(ry + c, (unsigned long long)small_fix(ay * w));
-        atomicAdd(rb + c, (unsigned long long)small_fix(ab * w));
+    float my = fabsf(r0.w), mb = fabsf(r1.x);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      my = fmaxf(my, __shfl_xor_sync(0xffffffffu, my, o));
+      mb = fmaxf(mb, __shfl_xor_sync(0xffffffffu, mb, o));
+    }
+    if (lane == 0) {
+      S.amax[0][wp] = my;
+      S.amax[1][wp] = mb;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < SMALL_THREADS / 32; ++q) {
+      my = fmaxf(my, S.amax[0][q]);
+      mb = fmaxf(mb, S.amax[1][q]);
+    }
+    // new scales; a lowered scale shifts the sums so far (uniform across the CTA)
+    int dy = 0, db = 0;
+    if (my > run_y) {
+      const int t2 = small_scale(my, n);
+      if (run_y > 0.f) dy = sy - t2;
+      sy = t2;
+      run_y = my;
+    }
+    if (mb > run_b) {
+      const int t2 = small_scale(mb, n);
+      if (run_b > 0.f) db = sb - t2;
+      sb = t2;
+      run_b = mb;
+    }
+    if (dy > 0 || db > 0) {
+      for (int q = tid; q < 2 * 64 * 64; q += SMALL_THREADS) {
+        const int m = q >> 12, d = m ? db : dy;
+        if (d <= 0) continue;
+        uint32_t* lo = &S.lo[0][0] + q;
+        uint32_t* hi = &S.hi[0][0] + q;
+        const long long a = (long long)(((unsigned long long)*hi << 32) | *lo) >> min(d, 63);
+        *lo = (uint32_t)a;
+        *hi = (uint32_t)((unsigned long long)a >> 32);
+      }
+    }
+    __syncthreads();
+    // every cell of this thread's particle, as fixed-point integers
+    const int ix = __float_as_int(r1.z), iy = __float_as_int(r1.w);
+    int i0 = 0, i1 = -1, j0 = 0, j1 = -1;
+    if (valid && bp_span(ix, r0.x, r0.z, nx, i0, i1) && bp_span(iy, r0.y, r0.z, ny, j0, j1)) {
+      i0 = max(i0, x0);
+      i1 = min(i1, x0 + 63);
+      j0 = max(j0, y0);
+      j1 = min(j1, y0 + 63);
+    } else {
+      i1 = i0 - 1;
+    }
+    if (i0 <= i1 && j0 <= j1) {
+      const bool ngp = !(r0.z > 0.f);
+      const float ih = ngp ? 1.0e38f : __frcp_rn(r0.z);
+      const float k1 = BP_KT * ih, k2 = BP_KS * ih;
+      const float fx = (ngp && !(r0.x > 0.f)) ? 1.0e-30f : r0.x;
+      const float fy = (ngp && !(r0.y > 0.f)) ? 1.0e-30f : r0.y;
+      const int kcx = ix + (fx > 0.f ? 0 : -1), kcy = iy + (fy > 0.f ? 0 : -1);
+      float v = bp_edge_split(__fsub_rn((float)(i0 - ix), fx), k1, k2);
+      for (int i = i0; i <= i1; ++i) {
+        const float vn = bp_edge_split(__fsub_rn((float)(i + 1 - ix), fx), k1, k2);
+        wx[i - i0] = (vn - v) + (i == kcx ? 1.f : 0.f);
+        v = vn;
+      }
+      const float Ys = ldexpf(r0.w, sy), Bs = ldexpf(r1.x, sb);
+      const bool has_y = r0.w != 0.f;
+      float u = bp_edge_split(__fsub_rn((float)(j0 - iy), fy), k1, k2);
+      for (int j = j0; j <= j1; ++j) {
+        const float un = bp_edge_split(__fsub_rn((float)(j + 1 - iy), fy), k1, k2);
+        const float wy = (un - u) + (j == kcy ? 1.f : 0.f);
+        u = un;
+        const float ay = Ys * wy, ab = Bs * wy;
+        const int q0 = (j - y0) * 64 + (i0 - x0);
+        for (int c = 0; c <= i1 - i0; ++c) {
+          const float w = wx[c];
+          if (has_y) small_add(&S.lo[0][q0 + c], &S.hi[0][q0 + c], small_fix(ay * w));
+          small_add(&S.lo[1][q0 + c], &S.hi[1][q0 + c], small_fix(ab * w));
+        }
       }
     }
   }
@@ -763,7 +816,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_deposit_small(
     const int64_t p = (int64_t)gy * nx + gx;
 #pragma unroll
     for (int m = 0; m < 2; ++m) {
-      const long long a = (long long)S.acc[m][q];
+      const long long a = (long long)(((unsigned long long)S.hi[m][q] << 32) | S.lo[m][q]);
       if (a == 0) continue;
       const double vv = ldexp((double)a, -(m ? sb : sy));
       const float hi = (float)vv, lo = (float)(vv - (double)hi);
