@@ -1027,6 +1027,53 @@ def run_ours(args):
     return 0
 
 
+def deposit_only(api, dev, args, peaks):
+    """Profiling mode (not the benchmark line): the particle deposit alone, on the 4e6-particle
+    cone (`4m`) or on a seeded sample of the full-scale cone (`full`, a fraction --sample of its
+    halos with all their particles and the same fraction of the field particles).  Solves,
+    assigns and sorts once, then times --warmup + --steps deposits (pair list rebuilt each
+    time) and prints one JSON line with the phase times and the deposit's algorithmic work."""
+    import torch
+
+    from paper_2201_02632_gb300 import inputs as I
+
+    t = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)
+    if args.deposit_only == "4m":
+        lc = I.lightcone()
+        parts = {k: t(v) for k, v in lc.parts.items()}
+    else:
+        smp = None if args.sample >= 1.0 else (args.sample, args.sample)
+        lc = I.lightcone_device(n_part=args.particles, n_halo=args.halos, npix=args.npix,
+                                device=dev, sample=smp)
+        parts = lc.parts
+    cat = lc.halos
+    ctx = api.Context()
+    model, status = ctx.solve_halos(t(cat.M), t(cat.c), t(cat.z), raise_on_noconv=False)
+    g = api.geom(lc.geom.nx, lc.geom.ny, lc.geom.theta0_x, lc.geom.theta0_y, lc.geom.dtheta)
+    rec = ctx.assign_particles(parts, lc.Mp, t(cat.pos), model, status, g)
+    del parts, lc.parts
+    torch.cuda.empty_cache()
+    maps = api.Maps.zeros(g, dev)
+    work = deposit_work(rec, g.nx, g.ny, sspan=small_span_auto(g.nx, g.ny))
+    ctx.set_timing(True)
+    ph = []
+    for k in range(args.warmup + args.steps):
+        maps.zero_()
+        ctx.pp_prepare(rec, g)
+        ctx.phase_times()
+        ctx.pp_deposit(rec, g, maps)
+        if k >= args.warmup:
+            ph.append(ctx.phase_times())
+    ctx.set_timing(False)
+    mean = {k: sum(p[k] for p in ph) / len(ph) for k in ("deposit", "reduce", "deposit_small")}
+    print(json.dumps({"deposit_only": args.deposit_only, "sample": args.sample,
+                      "particles": int(rec.shape[0]), "maps": f"{g.nx}x{g.ny}",
+                      "phase_ms": mean, "work": work,
+                      "roofline": deposit_roofline("k_deposit_tc", mean, work, peaks, None)}))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1055,11 +1102,25 @@ def main():
     ap.add_argument("--sur-train", type=int, default=2_000_000)
     ap.add_argument("--sur-infer", type=int, default=10_000_000)
     ap.add_argument("--sur-epochs", type=int, default=6)
+    ap.add_argument("--deposit-only", choices=["4m", "full"], default=None,
+                    help="profiling mode: time the particle deposit alone on this workload")
+    ap.add_argument("--sample", type=float, default=1.0,
+                    help="with --deposit-only full: the fraction of the cone's halos (with "
+                         "their particles) and field particles")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.deposit_only:
+        import torch
+
+        from paper_2201_02632_gb300 import api
+        from paper_2201_02632_gb300 import build as B
+
+        B.build()
+        torch.cuda.set_device(0)
+        return deposit_only(api, torch.device("cuda", 0), args, measured_peaks())
     return run_ours(args)
 
 

@@ -390,7 +390,7 @@ int bp_pp_deposit(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_ge
  * synchronise the device.  (The paper has no counterpart: this is a service of the
  * library.)  Same arguments, results and host synchronisation as bp_paste_particles
  * (the call waits once on the context's stream, to read back the pair count), but all
- * scratch lives in one fixed device array inside the library (about 23 MB) and each
+ * scratch lives in one fixed device array inside the library (about 24 MiB) and each
  * tile is deposited by a single CTA.  It calls no cudaMalloc, cudaFree or other
  * allocating routine.  CUDA loads a library's device code and arrays lazily, and that
  * load takes device memory, so bp_create does it: creating a context brings the array

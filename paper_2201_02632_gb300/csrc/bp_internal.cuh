@@ -210,6 +210,9 @@ __device__ __forceinline__ float bp_wsplit_inv(float dx, float inv_h) {
 // (2/3)(1 - a)^4 above, zero beyond a = 1), from |dx| and the scales k1 = BP_KT / h,
 // k2 = BP_KS / h: no branch, no piece selection.  h = 0 is an infinite scale (k1, k2 = BP_KT,
 // BP_KS x 1e38): every edge off the particle is 0.  dx must not be -0 or 0 with h = 0.
+// Items per block of the radix sort (its scratch sizes depend on it).
+constexpr int BP_RS_ITEMS = 2048;
+
 constexpr float BP_KT = 0.9036020040512085f;  // (2/3)^(1/4)
 constexpr float BP_KS = 1.277886152267456f;   // (8/3)^(1/4)
 __device__ __forceinline__ float bp_edge_split(float dx, float k1, float k2) {
@@ -302,9 +305,9 @@ struct BpPasteBuffers {
   uint32_t* counts;   // [n + 1]
   int64_t* offs;      // [n + 1]
   uint32_t *keys0, *vals0, *keys1, *vals1;  // [max_pairs] each
-  uint32_t* hist;     // [256 * ceil(max_pairs / 4096)]
-  int64_t* hoffs;     // [256 * ceil(max_pairs / 4096) + 1]
-  int64_t* bsum;      // [max(n, 256 * ceil(max_pairs / 4096), max_tiles) / 8192 + 2]
+  uint32_t* hist;     // [256 * ceil(max_pairs / BP_RS_ITEMS)]
+  int64_t* hoffs;     // [256 * ceil(max_pairs / BP_RS_ITEMS) + 1]
+  int64_t* bsum;      // [max(n, 256 * ceil(max_pairs / BP_RS_ITEMS), max_tiles) / 8192 + 2]
   int64_t* tstart;    // [max_tiles + 1]
   int64_t* uoff;      // [max_tiles + 1]
   uint32_t* ucount;   // [max_tiles + 1]

@@ -22,7 +22,7 @@ namespace {
 constexpr int64_t NA_MAX_PARTICLES = BP_NOALLOC_MAX_PARTICLES;
 constexpr int64_t NA_MAX_PAIRS = BP_NOALLOC_MAX_PAIRS;
 constexpr int64_t NA_MAX_TILES = BP_NOALLOC_MAX_TILES;
-constexpr int64_t NA_RS_BLOCKS = (NA_MAX_PAIRS + 4095) / 4096;
+constexpr int64_t NA_RS_BLOCKS = (NA_MAX_PAIRS + BP_RS_ITEMS - 1) / BP_RS_ITEMS;
 constexpr int64_t NA_HIST = 256 * NA_RS_BLOCKS;
 constexpr int64_t NA_SCAN_MAX =
     (NA_MAX_PARTICLES > NA_HIST ? NA_MAX_PARTICLES : NA_HIST) > NA_MAX_TILES

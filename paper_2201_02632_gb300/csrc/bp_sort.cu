@@ -90,8 +90,9 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_down(const uint32_t* in, 
 
 // ---------------------------------------------------------------- radix sort
 constexpr int RS_THREADS = 256;
-constexpr int RS_ROUNDS = 16;
-constexpr int RS_ITEMS = RS_THREADS * RS_ROUNDS;
+constexpr int RS_ITEMS = BP_RS_ITEMS;  // items per block (bp_internal.cuh)
+constexpr int RS_ROUNDS = RS_ITEMS / RS_THREADS;
+static_assert(RS_ROUNDS * RS_THREADS == RS_ITEMS, "radix block");
 constexpr int RS_MAXDIG = 256;
 
 __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t* keys, int64_t n,
@@ -111,14 +112,12 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t* keys, in
     hist[(int64_t)d * nblocks + blockIdx.x] = s_h[d];
 }
 
-// Stable scatter of one block of RS_ITEMS items.  Warp w ranks the contiguous slice
-// [w * 512, (w + 1) * 512) of the block in index order (32 items at a time, peers by
-// digit with __match_any_sync, per-warp digit counts in shared memory); the block then
-// places every item at its digit-sorted position in a shared-memory buffer and copies
-// the buffer out, so that the writes of each digit run are contiguous in memory.  Only
-// the ranks stay in registers between the two passes (keys and values are read again for
-// the placement, from L2): this keeps the kernel at about half the registers, twice the
-// resident blocks.
+// Stable scatter of one block of RS_ITEMS items.  Each lane first loads its keys and values
+// (RS_SUB of each, all loads in flight together); warp w then ranks the contiguous slice
+// [w * RS_ITEMS / 8, (w + 1) * RS_ITEMS / 8) of the block in index order (32 items at a
+// time, peers by digit with __match_any_sync, per-warp digit counts in shared memory); the
+// block places every item at its digit-sorted position in a shared-memory buffer and
+// copies the buffer out, so that the writes of each digit run are contiguous in memory.
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_SUB = RS_ITEMS / RS_WARPS / 32;  // items per lane
 
@@ -143,12 +142,19 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* kin,
   const uint32_t lt_mask = (1u << lane) - 1u;
   const int64_t bbase = (int64_t)blockIdx.x * RS_ITEMS;
   const int64_t wbase = bbase + (int64_t)w * (RS_ITEMS / RS_WARPS);
+  uint32_t kk[RS_SUB], vv[RS_SUB];
+#pragma unroll
+  for (int j = 0; j < RS_SUB; ++j) {
+    const int64_t i = wbase + 32 * j + lane;
+    kk[j] = i < n ? kin[i] : 0u;
+    vv[j] = i < n ? vin[i] : 0u;
+  }
   uint32_t rnk[RS_SUB];
 #pragma unroll
   for (int j = 0; j < RS_SUB; ++j) {
     const int64_t i = wbase + 32 * j + lane;
     const bool valid = i < n;
-    const uint32_t key = valid ? kin[i] : 0u;
+    const uint32_t key = kk[j];
     const uint32_t d = (key >> shift) & dmask;
     const uint32_t tag = valid ? d : (0x80000000u | (uint32_t)lane);
     const uint32_t peers = __match_any_sync(0xffffffffu, tag);
@@ -181,11 +187,11 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* kin,
   for (int j = 0; j < RS_SUB; ++j) {
     const int64_t i = wbase + 32 * j + lane;
     if (i < n) {
-      const uint32_t key = kin[i];
+      const uint32_t key = kk[j];
       const uint32_t d = (key >> shift) & dmask;
       const uint32_t pos = s_start[d] + s_cnt[w][d] + rnk[j];
       s_k[pos] = key;
-      s_v[pos] = vin[i];
+      s_v[pos] = vv[j];
     }
   }
   __syncthreads();
@@ -313,7 +319,8 @@ int bp_scan_u32_to_i64_buf(bp_ctx* ctx, const uint32_t* in, int64_t* out, int64_
   return BP_OK;
 }
 
-// hist: >= 256 * ceil(n / 4096) u32; offs: one more int64 than hist entries; bsum as above
+// hist: >= 256 * ceil(n / BP_RS_ITEMS) u32; offs: one more int64 than hist entries; bsum as
+// above
 int bp_radix_sort_pairs_buf(bp_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t* keys_tmp,
                             uint32_t* vals_tmp, int64_t n, int key_bits, uint32_t* hist,
                             int64_t* offs, int64_t* bsum, uint32_t** keys_out,

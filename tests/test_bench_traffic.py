@@ -39,6 +39,12 @@ def test_committed_record_matches_the_current_deposit_sources():
     for f in rec.get("sources", [rec.get("source")]):
         assert os.path.exists(os.path.join(bench.ROOT, "paper_2201_02632_gb300", "csrc", f))
     assert rec["dram_bytes_per_launch_scaled"] == rec["dram_bytes_read"] + rec["dram_bytes_write"]
+    # the full-scale record: captured on a sample, reads scaled by the tile pairs
+    big = d["k_deposit_tc_c2"]
+    assert big["sources"] == rec["sources"]
+    assert big["read_scale"] > 1.0
+    assert big["dram_bytes_per_launch_scaled"] == round(
+        big["dram_bytes_read"] * big["read_scale"]) + big["dram_bytes_write"]
 
 
 def _rec(rows):
