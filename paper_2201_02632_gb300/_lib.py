@@ -13,6 +13,8 @@ LIB_PATH = os.path.join(HERE, "_build", "libbp.so")
 BP_OK, BP_EINVAL, BP_ECUDA, BP_ERANGE, BP_ENOCONV, BP_ETIMEOUT, BP_ENOMEM = 0, -1, -2, -3, -4, -5, -6
 ERR_NAMES = {-1: "BP_EINVAL", -2: "BP_ECUDA", -3: "BP_ERANGE", -4: "BP_ENOCONV",
              -5: "BP_ETIMEOUT", -6: "BP_ENOMEM"}
+# solve modes of bp_solve_halos_ex
+BP_SOLVE_FP64, BP_SOLVE_FP64_SEEDED, BP_SOLVE_FP32_GATED = 0, 1, 2
 
 MODEL_FIELDS = ("Mvir", "c", "z", "r_vir", "r_s", "rho_s", "m_c", "Phi0", "r500", "M500",
                 "M_star", "r_star", "E_gi", "E_dm", "P_s", "T", "rho0", "P0", "r_f", "A_nt",

@@ -160,11 +160,15 @@ class Context:
         return model, status
 
     def solve_halos_ex(self, M, c, z, params=None, guess=None, max_iter=0, gate=0.0, tol=1e-10,
-                       raise_on_noconv=True, seeded=False):
+                       raise_on_noconv=True, seeded=False, gated=False):
         """bp_solve_halos_ex: per-halo (eps_*, f_*, eps_DM) as params [3, n] FP64, starting
         point guess [2, n] FP64 (ln r_f/r_vir, ln T r_vir/GM), iteration cap and gate.
         seeded: the guess starts the FP32 pre-solve (BP_SOLVE_FP64_SEEDED) instead of the
-        FP64 Newton."""
+        FP64 Newton.  gated: BP_SOLVE_FP32_GATED, the FP32 pre-solve's answer where both of
+        its residuals are <= gate (> 0), the full FP64 solve elsewhere."""
+        if seeded and gated:
+            raise ValueError("solve_halos_ex: seeded and gated are exclusive")
+        mode = L.BP_SOLVE_FP32_GATED if gated else (1 if seeded else 0)
         n = M.numel()
         f64 = torch.float64
         model = torch.empty((len(MODEL_FIELDS), n), dtype=f64, device=M.device)
@@ -173,7 +177,7 @@ class Context:
                                        _ptr(z, f64, "z"), _ptr(params, f64, "params"),
                                        _ptr(guess, f64, "guess"), int(max_iter), float(gate),
                                        _ptr(model, f64, "model"),
-                                       _ptr(status, torch.int32, "status"), 1 if seeded else 0,
+                                       _ptr(status, torch.int32, "status"), mode,
                                        float(tol))
         self._check(rc, allow=() if raise_on_noconv else (L.BP_ENOCONV,))
         return model, status

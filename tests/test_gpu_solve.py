@@ -106,3 +106,30 @@ def test_seeded_presolve_reaches_the_same_solutions(orc, api, ctx):
         assert np.abs(mg[F["res_m"]]).max() < 1e-10 and np.abs(mg[F["res_e"]]).max() < 1e-10
         for name in SOLVED:
             np.testing.assert_allclose(mg[F[name]], p[F[name]], rtol=1e-8, err_msg=name)
+
+
+def test_fp32_gated_solve_without_seed(orc, api, ctx):
+    """BP_SOLVE_FP32_GATED from the default start (no guess): the accepted halos carry the
+    FP32 pre-solve's (r_f, T), within 1e-3 of the oracle and with both residuals within the
+    gate; the rest are the FP64 solve's; closed-form fields are those of the plain solve; a
+    gate of 0 is refused."""
+    cat, _ = I.halo_catalog(n=400)
+    M = np.concatenate([cat.M, [1e12, 2e15, 5e14]])
+    c = np.concatenate([cat.c, [12.0, 3.0, 25.0]])
+    z = np.concatenate([cat.z, [3.0, 0.01, 2.5]])
+    mo = orc.solve_halos(M, c, z)
+    gate = 1e-4
+    model, status = ctx.solve_halos_ex(cuda(M), cuda(c), cuda(z), gate=gate, gated=True)
+    nfb = ctx.last_fallback_count()
+    mg = model.cpu().numpy()
+    assert (status.cpu().numpy() == 0).all()
+    assert 0 <= nfb < M.size // 2  # most halos are accepted from the pre-solve
+    F, G = orc.F, api.MF
+    for name in CLOSED:
+        np.testing.assert_allclose(mg[G[ORC_TO_GPU[name]]], mo[:, F[name]], rtol=1e-11,
+                                   err_msg=name)
+    for name in ("r_f", "T", "rho0", "P0"):
+        np.testing.assert_allclose(mg[G[name]], mo[:, F[name]], rtol=1e-3, err_msg=name)
+    assert np.abs(mg[G["res_m"]]).max() <= gate and np.abs(mg[G["res_e"]]).max() <= gate
+    with pytest.raises(api.BpError):
+        ctx.solve_halos_ex(cuda(M), cuda(c), cuda(z), gate=0.0, gated=True)

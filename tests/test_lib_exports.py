@@ -57,3 +57,17 @@ def test_binding_refuses_cpu_tensors():
 
     with pytest.raises(TypeError):
         api._ptr(torch.zeros(3, dtype=torch.float64), torch.float64, "x")
+
+
+def test_binding_constants_match_the_header():
+    """Every BP_* integer constant the binding mirrors has the header's value."""
+    from paper_2201_02632_gb300 import _lib
+
+    text = open(os.path.join(os.path.dirname(__file__), "..", "include", "bp.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in
+            re.finditer(r"^#define (BP_[A-Z0-9_]+) \(?(-?\d+)\)?", text, re.M)}
+    names = [n for n in dir(_lib) if n.startswith("BP_") and isinstance(getattr(_lib, n), int)]
+    assert len(names) >= 10
+    for n in names:
+        assert n in defs, n
+        assert getattr(_lib, n) == defs[n], n
