@@ -188,6 +188,20 @@ int bp_set_small_span(bp_ctx* ctx, int span);
  * context stays usable.  polls = 0 (the default) turns the test off.  BP_EINVAL for polls
  * outside [0, 2^31). */
 int bp_set_wait_test(bp_ctx* ctx, int64_t polls);
+/* Debug build (not in the paper).  A library compiled with -DBP_DEBUG checks, inside the
+ * particle paste's kernels, the index of each store that a wrong index would misplace (pair
+ * emission 101, radix scatter 201-202, small-particle sums 301-302, tensor-core write-out
+ * 401-402, partial-tile reduction 501); a failed check skips that store and records its site
+ * code in the context's debug word (the first failure is kept).  The release build compiles
+ * the checks out.
+ *   bp_debug_build: 1 for a debug build, else 0.
+ *   bp_debug_status: *site = the recorded site code (0: none), then clears the word;
+ *     synchronises the context's stream.  BP_EINVAL for a null argument.
+ *   bp_debug_selftest: records `site` (> 0) as a failed check would (both builds), for
+ *     testing the read-back; asynchronous on the context's stream. */
+int bp_debug_build(void);
+int bp_debug_status(bp_ctx* ctx, int* site);
+int bp_debug_selftest(bp_ctx* ctx, int site);
 /* Bytes of scratch the context currently holds. */
 int64_t bp_workspace_bytes(const bp_ctx* ctx);
 

@@ -8,7 +8,9 @@ import os
 import threading
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libbp.so")
+# the library this binding loads: the release build, or another build of the same sources
+# named by BP_LIB (e.g. the debug build, build.build(debug=True))
+LIB_PATH = os.environ.get("BP_LIB") or os.path.join(HERE, "_build", "libbp.so")
 
 BP_OK, BP_EINVAL, BP_ECUDA, BP_ERANGE, BP_ENOCONV, BP_ETIMEOUT, BP_ENOMEM = 0, -1, -2, -3, -4, -5, -6
 ERR_NAMES = {-1: "BP_EINVAL", -2: "BP_ECUDA", -3: "BP_ERANGE", -4: "BP_ENOCONV",
@@ -38,7 +40,8 @@ EXPORTS = ("bp_create", "bp_destroy", "bp_last_error", "bp_set_stream", "bp_set_
            "bp_solve_halos_ex", "bp_last_fallback_count", "bp_mlp_forward", "bp_mlp_backward",
            "bp_mlp_adam", "bp_mlp_to_bf16", "bp_mlp_infer_bf16", "bp_mlp_features",
            "bp_mlp_targets", "bp_mlp_mse", "bp_solve_halos_surrogate", "bp_hp_plan_create",
-           "bp_hp_plan_execute", "bp_hp_plan_pairs", "bp_hp_plan_destroy")
+           "bp_hp_plan_execute", "bp_hp_plan_pairs", "bp_hp_plan_destroy", "bp_debug_build",
+           "bp_debug_status", "bp_debug_selftest")
 MLP_IN, MLP_HID, MLP_OUT = 6, 128, 3
 MLP_NPARAMS = 128 * 6 + 128 + 2 * (128 * 128 + 128) + 3 * 128 + 3
 MLP_NWEIGHTS = 128 * 6 + 2 * 128 * 128 + 3 * 128
@@ -86,6 +89,9 @@ def load():
                 "bp_set_deposit_kernel": (i32, [P, i32]),
                 "bp_set_wait_test": (i32, [P, i64]),
                 "bp_set_small_span": (i32, [P, i32]),
+                "bp_debug_build": (i32, []),
+                "bp_debug_status": (i32, [P, C.POINTER(C.c_int)]),
+                "bp_debug_selftest": (i32, [P, i32]),
                 "bp_workspace_bytes": (i64, [P]),
                 "bp_set_timing": (i32, [P, i32]),
                 "bp_phase_times": (i32, [P, C.POINTER(C.c_double), i32]),

@@ -242,7 +242,8 @@ int bp_create(bp_ctx** out, const bp_cosmology* cosmo, const bp_icm_params* icm,
     cudaError_t e1 = cudaMalloc(&ctx->d_counter, 64 * sizeof(int64_t));
     cudaError_t e2 = cudaMalloc(&ctx->d_flags, 64 * sizeof(int));
     cudaError_t e3 = cudaMallocHost(&ctx->h_pinned, 64 * sizeof(int64_t));
-    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess)
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess ||
+        cudaMemset(ctx->d_flags, 0, 64 * sizeof(int)) != cudaSuccess)
       r = bp_fail(nullptr, BP_ECUDA, "bp_create: scalar buffers");
     // the allocation-free paste's device array and kernels, loaded now (bp_noalloc.cu)
     if (r == BP_OK && (r = bp_noalloc_setup(ctx)) != BP_OK)
@@ -301,6 +302,39 @@ int bp_set_deposit_kernel(bp_ctx* ctx, int kind) {
   if (kind != BP_DEPOSIT_AUTO && kind != BP_DEPOSIT_SIMT && kind != BP_DEPOSIT_TENSOR)
     return bp_fail(ctx, BP_EINVAL, "bp_set_deposit_kernel: unknown kind %d", kind);
   ctx->pp_kernel = kind;
+  return BP_OK;
+}
+
+namespace {
+// sets the debug word as a failed check would (the plumbing test of bp_debug_selftest)
+__global__ void k_debug_selftest(int* word, int site) {
+  if (threadIdx.x == 0) bp_dbg_fail(word, site);
+}
+}  // namespace
+
+int bp_debug_build(void) {
+#ifdef BP_DEBUG
+  return 1;
+#else
+  return 0;
+#endif
+}
+
+int bp_debug_status(bp_ctx* ctx, int* site) {
+  if (!ctx || !site) return BP_EINVAL;
+  int* h = reinterpret_cast<int*>(ctx->h_pinned + 12);  // slot of this call only
+  BP_CUDA(ctx, cudaMemcpyAsync(h, bp_dbg_word(ctx), sizeof(int), cudaMemcpyDeviceToHost,
+                               ctx->stream));
+  BP_CUDA(ctx, cudaMemsetAsync(bp_dbg_word(ctx), 0, sizeof(int), ctx->stream));
+  BP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+  *site = *h;
+  return BP_OK;
+}
+
+int bp_debug_selftest(bp_ctx* ctx, int site) {
+  if (!ctx || site <= 0) return BP_EINVAL;
+  k_debug_selftest<<<1, 32, 0, ctx->stream>>>(bp_dbg_word(ctx), site);
+  BP_LAUNCH_CHECK(ctx, "debug self-test");
   return BP_OK;
 }
 

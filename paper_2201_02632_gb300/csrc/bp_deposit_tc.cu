@@ -425,6 +425,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
             const int gx = x0 + cx + j;
             if (gx >= nx) continue;
             const int64_t p = (int64_t)gy * nx + gx;
+            if (!BP_DCHECK(p >= 0 && p < (int64_t)nx * ny, err + BP_DBG_SLOT, 401)) continue;
             float sm, e;
             bp_two_sum(map[p], hi[j], sm, e);
             map[p] = sm;
@@ -432,6 +433,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
           }
         }
       } else {
+        if (!BP_DCHECK(jr * TC_TS + cx + 16 <= TC_TS * TC_TS, err + BP_DBG_SLOT, 402)) continue;
         float* P = partials + (int64_t)U.slot * 4 * TC_TS * TC_TS +
                    (is_b ? 2 : 0) * TC_TS * TC_TS + jr * TC_TS + cx;
 #pragma unroll

@@ -108,6 +108,25 @@ struct bp_ctx {
   char msg[512];
 };
 
+// ---- Debug build.  Compiled with -DBP_DEBUG (build.build(debug=True), into _build_debug/),
+// the particle paste's kernels check their index arithmetic before each store that a wrong
+// index would misplace (pair emission, radix scatter, small-particle sums, tensor-core
+// write-out, partial-tile reduction): a failed check skips the store and records the
+// check's site code in the context's debug word, keeping the first failure; bp_debug_status
+// reads and clears the word.  The release build compiles the checks out.
+constexpr int BP_DBG_SLOT = 8;  // the debug word's slot in bp_ctx::d_flags
+__device__ __forceinline__ bool bp_dbg_fail(int* word, int site) {
+  if (word) atomicCAS(word, 0, site);
+  return false;
+}
+#ifdef BP_DEBUG
+#define BP_DCHECK(ok, word, site) ((ok) ? true : bp_dbg_fail((word), (site)))
+#else
+#define BP_DCHECK(ok, word, site) true
+#endif
+inline int* bp_dbg_word(bp_ctx* ctx) { return ctx->d_flags + BP_DBG_SLOT; }
+
+
 // phase timing (no-ops unless bp_set_timing(ctx, 1))
 void bp_phase_begin(bp_ctx* ctx, int ph);
 void bp_phase_end(bp_ctx* ctx, int ph);

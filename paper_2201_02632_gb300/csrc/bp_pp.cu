@@ -315,7 +315,7 @@ __global__ void k_pair_count(const float4* __restrict__ rec, int64_t n, int nx, 
 // tensor-core deposit, 1-3 for the small-particle deposit); with sspan = 0 it is the tile.
 __global__ void k_pair_emit(const float4* __restrict__ rec, int64_t n, int nx, int ny, int ts,
                             int select, int ntx, const int64_t* __restrict__ offs,
-                            uint32_t* keys, uint32_t* vals, int sspan) {
+                            uint32_t* keys, uint32_t* vals, int sspan, int* dbg) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const int64_t i0 = i - lane;
@@ -345,8 +345,13 @@ __global__ void k_pair_emit(const float4* __restrict__ rec, int64_t n, int nx, i
     const int pc = __shfl_sync(0xffffffffu, cls, p);
     if (e < end) {
       const int local = e - prel;
-      keys[base + e] = ((uint32_t)((py0 + local / pw) * ntx + px0 + local % pw) << ks) | pc;
-      vals[base + e] = (uint32_t)(i0 + p);
+      const uint32_t tile = (uint32_t)((py0 + local / pw) * ntx + px0 + local % pw);
+      if (BP_DCHECK(tile < (uint32_t)(ntx * ((ny + ts - 1) / ts)) && local >= 0 &&
+                        base + e < offs[n],
+                    dbg, 101)) {
+        keys[base + e] = (tile << ks) | pc;
+        vals[base + e] = (uint32_t)(i0 + p);
+      }
     }
   }
 }
@@ -601,7 +606,7 @@ __global__ void __launch_bounds__(256) k_reduce_tiles(const int64_t* __restrict_
                                                       int ntx, const float* __restrict__ partials,
                                                       float* ymap, float* bmap, float* ylo,
                                                       float* blo, const int* __restrict__ err,
-                                                      int ks) {
+                                                      int ks, int* dbg) {
   // blockIdx.y: which of REDUCE_SPLIT pixel slices of the tile this CTA sums
   int64_t t = blockIdx.x;
   if (t >= n_tiles) return;
@@ -618,6 +623,7 @@ __global__ void __launch_bounds__(256) k_reduce_tiles(const int64_t* __restrict_
     int gx = x0 + q % TS, gy = y0 + q / TS;
     if (gx >= nx || gy >= ny) continue;
     float hy = 0.f, ly = 0.f, hb = 0.f, lb = 0.f;
+    if (!BP_DCHECK(u0 >= 0 && q >= 0 && q < TS * TS, dbg, 501)) continue;
     for (int64_t k = 0; k < nu; ++k) {
       const float* P = partials + (u0 + k) * 4 * TS * TS;
       float s, e;
@@ -695,7 +701,7 @@ __device__ __forceinline__ int small_scale(float amax, int64_t n) {
 __global__ void __launch_bounds__(SMALL_THREADS) k_deposit_small(
     const float4* __restrict__ rec, const uint32_t* __restrict__ pvals,
     const int64_t* __restrict__ tstart, int ntx, int nx, int ny, float* ymap, float* bmap,
-    float* ylo, float* blo, const int* __restrict__ err) {
+    float* ylo, float* blo, const int* __restrict__ err, int* dbg) {
   extern __shared__ __align__(16) unsigned char small_raw[];
   SmallSmem& S = *reinterpret_cast<SmallSmem*>(small_raw);
   const int t = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
@@ -788,7 +794,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_deposit_small(
       float v = bp_edge_split(__fsub_rn((float)(i0 - ix), fx), k1, k2);
       for (int i = i0; i <= i1; ++i) {
         const float vn = bp_edge_split(__fsub_rn((float)(i + 1 - ix), fx), k1, k2);
-        wx[i - i0] = (vn - v) + (i == kcx ? 1.f : 0.f);
+        if (BP_DCHECK(i - i0 <= SMALL_MAX, dbg, 302)) wx[i - i0] = (vn - v) + (i == kcx ? 1.f : 0.f);
         v = vn;
       }
       const float Ys = ldexpf(r0.w, sy), Bs = ldexpf(r1.x, sb);
@@ -802,6 +808,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_deposit_small(
         const int q0 = (j - y0) * 64 + (i0 - x0);
         for (int c = 0; c <= i1 - i0; ++c) {
           const float w = wx[c];
+          if (!BP_DCHECK(q0 + c >= 0 && q0 + c < 64 * 64 && c <= SMALL_MAX, dbg, 301)) continue;
           if (has_y) small_add(&S.lo[0][q0 + c], &S.hi[0][q0 + c], small_fix(ay * w));
           small_add(&S.lo[1][q0 + c], &S.hi[1][q0 + c], small_fix(ab * w));
         }
@@ -868,7 +875,7 @@ int build_pairs(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_geom
   if ((r = bp_ws(ctx, WS_KEYS1, (size_t)np * 4, (void**)&k1))) return r;
   if ((r = bp_ws(ctx, WS_VALS1, (size_t)np * 4, (void**)&v1))) return r;
   k_pair_emit<<<nb, 256, 0, ctx->stream>>>(rec, n, g->nx, g->ny, ts, select, ntx, offs, k0, v0,
-                                           sspan);
+                                           sspan, bp_dbg_word(ctx));
   BP_LAUNCH_CHECK(ctx, "pair emit");
   bp_phase_end(ctx, BP_PH_PAIRS);
   int key_bits = 0;
@@ -991,7 +998,7 @@ int launch_deposit(bp_ctx* ctx, const float* assigned, const bp_map_geom* g,
   if (P.n_slots > 0) {
     k_reduce_tiles<TS><<<dim3((unsigned)P.n_tiles, REDUCE_SPLIT), 256, 0, ctx->stream>>>(
         P.tstart, P.soff, P.n_tiles, P.unit, g->nx, g->ny, ntx, partials, ymap, bmap, ylo, blo,
-        tc ? ctx->d_flags : nullptr, P.ks);
+        tc ? ctx->d_flags : nullptr, P.ks, bp_dbg_word(ctx));
     BP_LAUNCH_CHECK(ctx, "reduce tiles");
   }
   bp_phase_end(ctx, BP_PH_REDUCE);
@@ -1002,7 +1009,7 @@ int launch_deposit(bp_ctx* ctx, const float* assigned, const bp_map_geom* g,
                                       (int)smem));
     k_deposit_small<<<(unsigned)P.n_tiles, SMALL_THREADS, smem, ctx->stream>>>(
         reinterpret_cast<const float4*>(assigned), P.vals, P.tstart, ntx, g->nx, g->ny, ymap, bmap,
-        ylo, blo, tc ? ctx->d_flags : nullptr);
+        ylo, blo, tc ? ctx->d_flags : nullptr, bp_dbg_word(ctx));
     BP_LAUNCH_CHECK(ctx, "deposit (small particles)");
     bp_phase_end(ctx, BP_PH_DEPOSIT_SMALL);
   }
@@ -1123,7 +1130,7 @@ int bp_pp_paste_buffers(bp_ctx* ctx, int64_t n, const float* assigned, const bp_
                    (long long)np, (long long)B->max_pairs);
   if (np == 0) return BP_OK;
   k_pair_emit<<<nb, 256, 0, ctx->stream>>>(rec, n, g->nx, g->ny, ts, select, ntx, B->offs,
-                                           B->keys0, B->vals0, 0);
+                                           B->keys0, B->vals0, 0, bp_dbg_word(ctx));
   BP_LAUNCH_CHECK(ctx, "pair emit");
   int key_bits = 0;
   while (((int64_t)1 << key_bits) < n_tiles) ++key_bits;

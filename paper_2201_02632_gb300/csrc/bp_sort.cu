@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* kin,
                                                            const uint32_t* vin, uint32_t* kout,
                                                            uint32_t* vout, int64_t n, int shift,
                                                            int nbits, const int64_t* offs,
-                                                           int64_t nblocks) {
+                                                           int64_t nblocks, int* dbg) {
   __shared__ uint32_t s_cnt[RS_WARPS][RS_MAXDIG];  // per-warp digit counts, then offsets
   __shared__ uint32_t s_tot[RS_MAXDIG];
   __shared__ uint32_t s_start[RS_MAXDIG];          // block-local start of each digit
@@ -190,8 +190,10 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* kin,
       const uint32_t key = kk[j];
       const uint32_t d = (key >> shift) & dmask;
       const uint32_t pos = s_start[d] + s_cnt[w][d] + rnk[j];
-      s_k[pos] = key;
-      s_v[pos] = vv[j];
+      if (BP_DCHECK(pos < (uint32_t)RS_ITEMS, dbg, 201)) {
+        s_k[pos] = key;
+        s_v[pos] = vv[j];
+      }
     }
   }
   __syncthreads();
@@ -200,8 +202,10 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_scatter(const uint32_t* kin,
     const uint32_t k = s_k[p];
     const uint32_t d = (k >> shift) & dmask;
     const int64_t g = s_off[d] + (p - (int64_t)s_start[d]);
-    kout[g] = k;
-    vout[g] = s_v[p];
+    if (BP_DCHECK(g >= 0 && g < n, dbg, 202)) {
+      kout[g] = k;
+      vout[g] = s_v[p];
+    }
   }
 }
 
@@ -280,7 +284,8 @@ int bp_radix_sort_pairs(bp_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_t* k
     r = bp_scan_u32_to_i64(ctx, hist, offs, hn);
     if (r) return r;
     k_rs_scatter<<<(unsigned)nblocks, RS_THREADS, 0, ctx->stream>>>(ki, vi, ko, vo, n, shift, nb,
-                                                                    offs, nblocks);
+                                                                    offs, nblocks,
+                                                                    bp_dbg_word(ctx));
     BP_LAUNCH_CHECK(ctx, "radix scatter");
     uint32_t* t;
     t = ki; ki = ko; ko = t;
@@ -342,7 +347,8 @@ int bp_radix_sort_pairs_buf(bp_ctx* ctx, uint32_t* keys, uint32_t* vals, uint32_
     BP_LAUNCH_CHECK(ctx, "radix hist");
     if ((r = bp_scan_u32_to_i64_buf(ctx, hist, offs, hn, bsum))) return r;
     k_rs_scatter<<<(unsigned)nblocks, RS_THREADS, 0, ctx->stream>>>(ki, vi, ko, vo, n, shift, nb,
-                                                                    offs, nblocks);
+                                                                    offs, nblocks,
+                                                                    bp_dbg_word(ctx));
     BP_LAUNCH_CHECK(ctx, "radix scatter");
     uint32_t* t;
     t = ki; ki = ko; ko = t;
