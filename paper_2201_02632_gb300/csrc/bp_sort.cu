@@ -103,9 +103,17 @@ __global__ void __launch_bounds__(RS_THREADS) k_rs_hist(const uint32_t* keys, in
   for (int d = threadIdx.x; d < ndig; d += RS_THREADS) s_h[d] = 0;
   __syncthreads();
   int64_t base = (int64_t)blockIdx.x * RS_ITEMS;
+  // all of this thread's keys in flight at once, then the shared-memory counts
+  uint32_t kk[RS_ROUNDS];
+#pragma unroll
   for (int r = 0; r < RS_ROUNDS; ++r) {
-    int64_t i = base + (int64_t)r * RS_THREADS + threadIdx.x;
-    if (i < n) atomicAdd(&s_h[(keys[i] >> shift) & (ndig - 1)], 1u);
+    const int64_t i = base + (int64_t)r * RS_THREADS + threadIdx.x;
+    kk[r] = i < n ? keys[i] : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < RS_ROUNDS; ++r) {
+    const int64_t i = base + (int64_t)r * RS_THREADS + threadIdx.x;
+    if (i < n) atomicAdd(&s_h[(kk[r] >> shift) & (ndig - 1)], 1u);
   }
   __syncthreads();
   for (int d = threadIdx.x; d < ndig; d += RS_THREADS)
