@@ -74,7 +74,7 @@ struct PpPrepared {
   int64_t n;
   bp_map_geom g;
   int select, ts, unit;
-  int ks;  // 2: keys 4 tile + size class (classes 1-3: the small-particle deposit)
+  int ks;  // 3: keys 8 tile + size class (classes 1-7: the small-particle deposit)
   int64_t np, n_tiles, n_keys, max_units, n_slots;
   const uint32_t* vals;
   int64_t *tstart, *uoff, *soff;

@@ -274,9 +274,13 @@ __global__ void __launch_bounds__(256) k_assign4(AssignArgs a, BpTables T) {
 }
 
 // ---------------------------------------------------------------- pairs
+// Bits of a pair key below the tile when the small-particle deposit is on: the key is
+// 2^SMALL_KS tile + the particle's size class.
+constexpr int SMALL_KS = 3;
 // The tiles a particle's clipped pixel box touches, and its size class: 0 when the box is
-// wider than `sspan` pixels on an axis (or sspan is 0), else 1, 2, 3 for a box at most 2, 4,
-// 8 pixels on both axes (the small-particle deposit takes them grouped by size).
+// wider than `sspan` pixels on an axis (or sspan is 0), else 1 for a box at most 2 pixels on
+// both axes and span - 1 for a largest side of span = 3 .. 8 pixels (the small-particle deposit
+// takes them grouped by size, so that a warp's particles have similar boxes).
 __device__ __forceinline__ bool particle_tiles(const float4 r0, const float4 r1, int nx, int ny,
                                                int ts, int select, int& tx0, int& tx1, int& ty0,
                                                int& ty1, int sspan, int& cls) {
@@ -288,7 +292,7 @@ __device__ __forceinline__ bool particle_tiles(const float4 r0, const float4 r1,
   if (!bp_span(__float_as_int(r1.z), r0.x, r0.z, nx, i0, i1)) return false;
   if (!bp_span(__float_as_int(r1.w), r0.y, r0.z, ny, j0, j1)) return false;
   const int span = max(i1 - i0, j1 - j0) + 1;
-  cls = span > sspan ? 0 : (span <= 2 ? 1 : (span <= 4 ? 2 : 3));
+  cls = span > sspan ? 0 : (span <= 2 ? 1 : span - 1);  // 1 .. 7 (SMALL_KS = 3 bits)
   tx0 = i0 / ts;
   tx1 = i1 / ts;
   ty0 = j0 / ts;
@@ -311,8 +315,8 @@ __global__ void k_pair_count(const float4* __restrict__ rec, int64_t n, int nx, 
 // The warp's particles own one contiguous range of pairs (offs is their exclusive scan):
 // lanes write it 32 consecutive pairs at a time, each finding its particle by a binary
 // search over the warp's 32 offsets (shuffles), so that every store is coalesced.  With
-// sspan > 0 the key is 4 tile + the particle's size class (particle_tiles: 0 for the
-// tensor-core deposit, 1-3 for the small-particle deposit); with sspan = 0 it is the tile.
+// sspan > 0 the key is 2^SMALL_KS tile + the particle's size class (particle_tiles: 0 for the
+// tensor-core deposit, 1-7 for the small-particle deposit); with sspan = 0 it is the tile.
 __global__ void k_pair_emit(const float4* __restrict__ rec, int64_t n, int nx, int ny, int ts,
                             int select, int ntx, const int64_t* __restrict__ offs,
                             uint32_t* keys, uint32_t* vals, int sspan, int* dbg) {
@@ -330,7 +334,7 @@ __global__ void k_pair_emit(const float4* __restrict__ rec, int64_t n, int nx, i
       cls = c;
     }
   }
-  const int ks = sspan > 0 ? 2 : 0;
+  const int ks = sspan > 0 ? SMALL_KS : 0;
   const int64_t base = offs[i0];
   const int rel = (int)(offs[i < n ? i : n] - base);  // past the end: the total
   const int end = __shfl_sync(0xffffffffu, rel + cnt, 31);
@@ -360,7 +364,8 @@ __global__ void k_pair_emit(const float4* __restrict__ rec, int64_t n, int nx, i
 using Unit = BpUnit;
 
 // units per key, and partial-tile slots (only keys split into several units need them); with
-// ks = 2 only the keys 4 tile get units (the others: small particles, k_deposit_small)
+// ks = SMALL_KS only the keys 2^ks tile get units (the others: small particles,
+// k_deposit_small)
 __global__ void k_unit_count(const int64_t* __restrict__ tstart, int64_t n_tiles, int unit,
                              uint32_t* ucount, uint32_t* scount, int ks = 0) {
   int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -706,7 +711,8 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_deposit_small(
   SmallSmem& S = *reinterpret_cast<SmallSmem*>(small_raw);
   const int t = blockIdx.x, tid = threadIdx.x, lane = tid & 31, wp = tid >> 5;
   if (err && *err) return;  // the tensor-core deposit before it gave up
-  const int64_t b = tstart[4 * (int64_t)t + 1], e = tstart[4 * (int64_t)t + 4];  // classes 1-3
+  // classes 1 .. 7 of the tile: keys 8 t + 1 .. 8 t + 7
+  const int64_t b = tstart[((int64_t)t << SMALL_KS) + 1], e = tstart[((int64_t)(t + 1) << SMALL_KS)];
   if (b >= e) return;
   const int x0 = (t % ntx) * 64, y0 = (t / ntx) * 64;
   for (int q = tid; q < 2 * 64 * 64; q += SMALL_THREADS) {
@@ -847,7 +853,7 @@ int check_geom(bp_ctx* ctx, const bp_map_geom* g, const char* who) {
 }
 
 // Builds the sorted (tile, particle) list; returns keys/vals pointers and count.  sspan > 0:
-// keys 4 tile + the particle's size class (see k_pair_emit).
+// keys 2^SMALL_KS tile + the particle's size class (see k_pair_emit).
 int build_pairs(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_geom* g, int select,
                 int ts, uint32_t** keys_out, uint32_t** vals_out, int64_t* npairs_out,
                 int64_t* n_tiles_out, int sspan = 0) {
@@ -879,7 +885,7 @@ int build_pairs(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_geom
   BP_LAUNCH_CHECK(ctx, "pair emit");
   bp_phase_end(ctx, BP_PH_PAIRS);
   int key_bits = 0;
-  while (((int64_t)1 << key_bits) < (n_tiles << (sspan > 0 ? 2 : 0))) ++key_bits;
+  while (((int64_t)1 << key_bits) < (n_tiles << (sspan > 0 ? SMALL_KS : 0))) ++key_bits;
   bp_phase_begin(ctx, BP_PH_SORT);
   if ((r = bp_radix_sort_pairs(ctx, k0, v0, k1, v1, np, key_bits, keys_out, vals_out))) return r;
   *npairs_out = np;
@@ -918,7 +924,7 @@ template <int TS>
 int prepare_units(bp_ctx* ctx, const uint32_t* keys, const uint32_t* vals, int64_t np,
                   int64_t n_tiles, PpPrepared* P, int ks = 0) {
   int r;
-  const int64_t n_keys = n_tiles << ks;  // ks = 2: four keys per tile (size classes)
+  const int64_t n_keys = n_tiles << ks;  // ks = SMALL_KS: 8 keys per tile (size classes)
   // particles per work unit: the context's value, or (auto) about 16 units per
   // resident CTA, at least 2048
   int64_t unit64 = ctx->pp_unit;
@@ -1278,7 +1284,7 @@ int bp_paste_particles(bp_ctx* ctx, int64_t n, const float* assigned, const bp_m
   if ((r = build_pairs(ctx, n, assigned, geom, select, ts, &keys, &vals, &np, &n_tiles, sspan)))
     return r;
   if (np == 0) return BP_OK;
-  const int ks = sspan > 0 ? 2 : 0;
+  const int ks = sspan > 0 ? SMALL_KS : 0;
   if (ts == 64)
     return deposit<64>(ctx, assigned, geom, keys, vals, np, n_tiles, ymap, bmap, ylo, blo, ks);
   return deposit<32>(ctx, assigned, geom, keys, vals, np, n_tiles, ymap, bmap, ylo, blo, ks);
@@ -1315,7 +1321,7 @@ int bp_pp_prepare(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_ge
                          sspan)))
       return r;
     if (np > 0) {
-      const int ks = sspan > 0 ? 2 : 0;
+      const int ks = sspan > 0 ? SMALL_KS : 0;
       r = ts == 64 ? prepare_units<64>(ctx, keys, vals, np, n_tiles, &P, ks)
                    : prepare_units<32>(ctx, keys, vals, np, n_tiles, &P, ks);
       if (r) return r;
@@ -1332,7 +1338,7 @@ int bp_pp_deposit(bp_ctx* ctx, int64_t n, const float* assigned, const bp_map_ge
   const PpPrepared& P = ctx->pp_prep;
   if (!P.valid || P.assigned != assigned || P.n != n || !geom || P.select != select ||
       P.ts != ctx->pp_tile || memcmp(&P.g, geom, sizeof(bp_map_geom)) != 0 ||
-      (P.np > 0 && P.ks != (pp_small_span(ctx, P.ts, geom) > 0 ? 2 : 0)))
+      (P.np > 0 && P.ks != (pp_small_span(ctx, P.ts, geom) > 0 ? SMALL_KS : 0)))
     return bp_fail(ctx, BP_EINVAL, "bp_pp_deposit: no bp_pp_prepare of these records");
   if (P.np == 0 || n == 0) return BP_OK;
   for (int k : {(int)WS_KEYS0, (int)WS_VALS0, (int)WS_KEYS1, (int)WS_VALS1, (int)WS_TILES,
