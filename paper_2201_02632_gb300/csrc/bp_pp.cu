@@ -338,22 +338,38 @@ __global__ void k_pair_emit(const float4* __restrict__ rec, int64_t n, int nx, i
   const int64_t base = offs[i0];
   const int rel = (int)(offs[i < n ? i : n] - base);  // past the end: the total
   const int end = __shfl_sync(0xffffffffu, rel + cnt, 31);
+  // what a lane writing one of this particle's pairs needs, in three words: the first tile
+  // (x, y), the box width and size class, and 1 / width for the division below
+  const uint32_t pxy = (uint32_t)tx0 | ((uint32_t)ty0 << 16);
+  const uint32_t pwc = (uint32_t)w | ((uint32_t)cls << 16);
+  const float rw = __frcp_rn((float)w);
   for (int e0 = 0; e0 < end; e0 += 32) {  // warp-uniform trip count
     const int e = e0 + lane;
     int p = 0;  // the last particle of the warp whose first pair is <= e
 #pragma unroll
     for (int step = 16; step > 0; step >>= 1)
       if (__shfl_sync(0xffffffffu, rel, p + step) <= e) p += step;
-    const int px0 = __shfl_sync(0xffffffffu, tx0, p), py0 = __shfl_sync(0xffffffffu, ty0, p);
-    const int pw = __shfl_sync(0xffffffffu, w, p), prel = __shfl_sync(0xffffffffu, rel, p);
-    const int pc = __shfl_sync(0xffffffffu, cls, p);
+    const uint32_t qxy = __shfl_sync(0xffffffffu, pxy, p), qwc = __shfl_sync(0xffffffffu, pwc, p);
+    const int prel = __shfl_sync(0xffffffffu, rel, p);
+    const float qr = __shfl_sync(0xffffffffu, rw, p);
     if (e < end) {
-      const int local = e - prel;
-      const uint32_t tile = (uint32_t)((py0 + local / pw) * ntx + px0 + local % pw);
-      if (BP_DCHECK(tile < (uint32_t)(ntx * ((ny + ts - 1) / ts)) && local >= 0 &&
-                        base + e < offs[n],
+      // local = row w + col: the quotient from the FP32 reciprocal (exact up to one for
+      // local < 2^22), then one correction step
+      const int local = e - prel, pw = (int)(qwc & 0xffffu);
+      int row = __float2int_rz(__fmul_rn((float)local, qr));
+      int col = local - row * pw;
+      if (col < 0) {
+        --row;
+        col += pw;
+      } else if (col >= pw) {
+        ++row;
+        col -= pw;
+      }
+      const uint32_t tile = (uint32_t)(((int)(qxy >> 16) + row) * ntx + (int)(qxy & 0xffffu) + col);
+      if (BP_DCHECK(tile < (uint32_t)(ntx * ((ny + ts - 1) / ts)) && local >= 0 && col >= 0 &&
+                        col < pw && base + e < offs[n],
                     dbg, 101)) {
-        keys[base + e] = (tile << ks) | pc;
+        keys[base + e] = (tile << ks) | (qwc >> 16);
         vals[base + e] = (uint32_t)(i0 + p);
       }
     }
