@@ -74,7 +74,7 @@ struct alignas(1024) TcStage {
   unsigned char b_lo[TC_TS * 128];
 };
 
-// Per-particle fields of one chunk slot (written by lanes 0-7 of the owning warp).
+// Per-particle fields of one chunk slot (derived by the owning warp at the start of a batch).
 struct TcField {
   float4 ax[2];  // per axis: position of the particle's pixel relative to the tile, fraction,
                  // KT / h, KS / h
@@ -296,7 +296,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2)
           }
         }
         __syncwarp();
-        // 2. the next batch's records on their way (the ring slot is free: its fields are
+        // 2. the next batch's records on their way (the record buffer is free: its fields are
         // derived), the index of the one after
         const int q1 = cp_q0 + (c + TC_BATCH) * TC_CH;
         if (q1 < len) cp_async16(&S.raw[w][cp_p][cp_h], rec + 2 * (int64_t)pv_next + cp_h);

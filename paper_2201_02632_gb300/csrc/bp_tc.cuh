@@ -151,10 +151,6 @@ __device__ __forceinline__ void cp_async_commit() {
 __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_group 0;" ::: "memory");
 }
-// waits for all but this thread's two most recently committed groups of copies
-__device__ __forceinline__ void cp_async_wait_group2() {
-  asm volatile("cp.async.wait_group 2;" ::: "memory");
-}
 
 // ------------------------------------------------------------------ fences
 __device__ __forceinline__ void fence_proxy_async_smem() {
