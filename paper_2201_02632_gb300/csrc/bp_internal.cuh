@@ -185,9 +185,9 @@ __device__ __forceinline__ float bp_hermitef(const float* v, const float* d, int
 }
 
 // z(chi) and tau(chi) of a particle by cubic Hermite interpolation of the interleaved
-// per-node table (two 16-byte loads).
-__device__ __forceinline__ void bp_hermite_ztau(const BpTables& T, float x, float& z,
-                                                float& tau) {
+// per-node table zt (T.zt4, or a copy of it in shared memory; two 16-byte loads).
+__device__ __forceinline__ void bp_hermite_ztau(const BpTables& T, const float4* zt, float x,
+                                                float& z, float& tau) {
   float u = x * T.inv_dchi;
   int i = (int)u;
   if (i < 0) i = 0;
@@ -196,7 +196,7 @@ __device__ __forceinline__ void bp_hermite_ztau(const BpTables& T, float x, floa
   const float t2 = t * t, t3 = t2 * t;
   const float h00 = 2.f * t3 - 3.f * t2 + 1.f, h10 = t3 - 2.f * t2 + t, h01 = -2.f * t3 + 3.f * t2,
               h11 = t3 - t2;
-  const float4 a = __ldg(T.zt4 + i), b = __ldg(T.zt4 + i + 1);
+  const float4 a = zt[i], b = zt[i + 1];
   const float h = T.dchi;
   z = h00 * a.x + h10 * h * a.y + h01 * b.x + h11 * h * b.y;
   tau = h00 * a.z + h10 * h * a.w + h01 * b.z + h11 * h * b.w;

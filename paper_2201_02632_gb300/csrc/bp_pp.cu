@@ -169,11 +169,12 @@ struct AssignArgs {
 // h in pixels, Y = B = 0, and the kind from the halo id alone (a halo particle outside its
 // halo's truncation radius stays HALO, with zero signals later).  MODE 2 (signals): only Y,
 // B and the kind, the same values as MODE 0, into a record whose geometry MODE 1 wrote.
-// The record of particle i from its SoA fields.
+// The record of particle i from its SoA fields, as its two 16-byte halves.
 template <int MODE>
-__device__ __forceinline__ void assign_one(const AssignArgs& a, const BpTables& T, int64_t i,
-                                           float xf, float yf, float zf, float vxf, float vyf,
-                                           float vzf, float hsf, int32_t k) {
+__device__ __forceinline__ void assign_rec(const AssignArgs& a, const BpTables& T,
+                                           const float4* zt, int64_t i, float xf, float yf,
+                                           float zf, float vxf, float vyf, float vzf, float hsf,
+                                           int32_t k, float4& o0, float4& o1) {
   // sky angles and pixel coordinates: double-float FP32 near the axis, else FP64
   int ix = 0, iy = 0;
   float fx = 0.f, fy = 0.f;
@@ -198,7 +199,7 @@ __device__ __forceinline__ void assign_one(const AssignArgs& a, const BpTables& 
   } else if (rh > 0.f) {
     if constexpr (MODE == 0) hp = hsf * a.inv_h_dth / chi;  // exact rounding: the pair list
     float zz, tau;
-    bp_hermite_ztau(T, chi, zz, tau);
+    bp_hermite_ztau(T, zt, chi, zz, tau);
     // FP32 factors of the signals: approximate divisions and exponentials (a few ulps)
     const float DA = __fdividef(chi, 1.0f + zz);
     const float vr = __fdividef(vxf * xf + vyf * yf + vzf * zf, rh);
@@ -229,14 +230,25 @@ __device__ __forceinline__ void assign_one(const AssignArgs& a, const BpTables& 
       }
     }
   }
+  o0 = make_float4(fx, fy, hp, Y);
+  o1 = make_float4(B, __int_as_float(kind), __int_as_float(ix), __int_as_float(iy));
+}
+
+// ... and stored: MODE 2 writes only Y, B and the kind into the record MODE 1 wrote.
+template <int MODE>
+__device__ __forceinline__ void assign_one(const AssignArgs& a, const BpTables& T, int64_t i,
+                                           float xf, float yf, float zf, float vxf, float vyf,
+                                           float vzf, float hsf, int32_t k) {
+  float4 o0, o1;
+  assign_rec<MODE>(a, T, T.zt4, i, xf, yf, zf, vxf, vyf, vzf, hsf, k, o0, o1);
   if constexpr (MODE == 2) {
     float* o = a.out + i * BP_ASSIGNED_STRIDE;
-    o[3] = Y;
-    *reinterpret_cast<float2*>(o + 4) = make_float2(B, __int_as_float(kind));
+    o[3] = o0.w;
+    *reinterpret_cast<float2*>(o + 4) = make_float2(o1.x, o1.y);
   } else {
     float4* o = reinterpret_cast<float4*>(a.out + i * BP_ASSIGNED_STRIDE);
-    o[0] = make_float4(fx, fy, hp, Y);
-    o[1] = make_float4(B, __int_as_float(kind), __int_as_float(ix), __int_as_float(iy));
+    o[0] = o0;
+    o[1] = o1;
   }
 }
 
@@ -250,27 +262,77 @@ __global__ void __launch_bounds__(256) k_assign(AssignArgs a, BpTables T) {
 }
 
 // four consecutive particles per thread, the SoA fields read with 16-byte loads (every array
-// 16-byte aligned); the last n % 4 particles are left to k_assign
+// 16-byte aligned); the last n % 4 particles are left to k_assign.  The whole records (MODE 0)
+// go out through shared memory: a warp's 128 records (4 KB, contiguous in the output) are
+// written by 16-byte stores of 32 consecutive slots each, instead of each lane storing its own
+// 128 bytes at a 128-byte stride (32 cache lines per store instruction).
+constexpr int ASSIGN_THREADS = 256;
 template <int MODE>
-__global__ void __launch_bounds__(256) k_assign4(AssignArgs a, BpTables T) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (4 * q + 3 >= a.n) return;
-  const float4 x = __ldg(reinterpret_cast<const float4*>(a.x) + q);
-  const float4 y = __ldg(reinterpret_cast<const float4*>(a.y) + q);
-  const float4 z = __ldg(reinterpret_cast<const float4*>(a.z) + q);
-  const float4 h = __ldg(reinterpret_cast<const float4*>(a.hs) + q);
-  const int4 k = __ldg(reinterpret_cast<const int4*>(a.hid) + q);
-  float4 vx = make_float4(0.f, 0.f, 0.f, 0.f), vy = vx, vz = vx;
+__global__ void __launch_bounds__(ASSIGN_THREADS) k_assign4(AssignArgs a, BpTables T) {
+  // per warp: the lanes' 8 record halves each, padded to 9 slots (conflict-free both ways)
+  __shared__ float4 stage[MODE == 0 ? ASSIGN_THREADS / 32 : 1][32 * 9];
+  // the z(chi), tau(chi) table (dynamic shared memory, T.nc nodes; not for MODE 1)
+  extern __shared__ float4 s_zt[];
   if constexpr (MODE != 1) {
-    vx = __ldg(reinterpret_cast<const float4*>(a.vx) + q);
-    vy = __ldg(reinterpret_cast<const float4*>(a.vy) + q);
-    vz = __ldg(reinterpret_cast<const float4*>(a.vz) + q);
+    for (int j = threadIdx.x; j < T.nc; j += ASSIGN_THREADS) s_zt[j] = T.zt4[j];
+    __syncthreads();
   }
+  const float4* zt = MODE != 1 ? s_zt : T.zt4;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const bool valid = 4 * q + 3 < a.n;
+  if (MODE != 0 && !valid) return;
+  if (MODE == 0 && (4 * (q - lane) + 3 >= a.n)) return;  // the whole warp past the end
   const int64_t i = 4 * q;
-  assign_one<MODE>(a, T, i, x.x, y.x, z.x, vx.x, vy.x, vz.x, h.x, k.x);
-  assign_one<MODE>(a, T, i + 1, x.y, y.y, z.y, vx.y, vy.y, vz.y, h.y, k.y);
-  assign_one<MODE>(a, T, i + 2, x.z, y.z, z.z, vx.z, vy.z, vz.z, h.z, k.z);
-  assign_one<MODE>(a, T, i + 3, x.w, y.w, z.w, vx.w, vy.w, vz.w, h.w, k.w);
+  float4* st = stage[MODE == 0 ? wp : 0] + lane * 9;  // this lane's 8 record halves
+  if (valid) {
+    const float4 x = __ldg(reinterpret_cast<const float4*>(a.x) + q);
+    const float4 y = __ldg(reinterpret_cast<const float4*>(a.y) + q);
+    const float4 z = __ldg(reinterpret_cast<const float4*>(a.z) + q);
+    const float4 h = __ldg(reinterpret_cast<const float4*>(a.hs) + q);
+    const int4 k = __ldg(reinterpret_cast<const int4*>(a.hid) + q);
+    float4 vx = make_float4(0.f, 0.f, 0.f, 0.f), vy = vx, vz = vx;
+    if constexpr (MODE != 1) {
+      vx = __ldg(reinterpret_cast<const float4*>(a.vx) + q);
+      vy = __ldg(reinterpret_cast<const float4*>(a.vy) + q);
+      vz = __ldg(reinterpret_cast<const float4*>(a.vz) + q);
+    }
+    auto one = [&](int m, float xf, float yf, float zf, float vxf, float vyf, float vzf,
+                   float hf, int32_t kf) {
+      float4 o0, o1;
+      assign_rec<MODE>(a, T, zt, i + m, xf, yf, zf, vxf, vyf, vzf, hf, kf, o0, o1);
+      if constexpr (MODE == 0) {
+        st[2 * m] = o0;
+        st[2 * m + 1] = o1;
+      } else if constexpr (MODE == 2) {
+        float* o = a.out + (i + m) * BP_ASSIGNED_STRIDE;
+        o[3] = o0.w;
+        *reinterpret_cast<float2*>(o + 4) = make_float2(o1.x, o1.y);
+      } else {
+        float4* o = reinterpret_cast<float4*>(a.out + (i + m) * BP_ASSIGNED_STRIDE);
+        o[0] = o0;
+        o[1] = o1;
+      }
+    };
+    one(0, x.x, y.x, z.x, vx.x, vy.x, vz.x, h.x, k.x);
+    one(1, x.y, y.y, z.y, vx.y, vy.y, vz.y, h.y, k.y);
+    one(2, x.z, y.z, z.z, vx.z, vy.z, vz.z, h.z, k.z);
+    one(3, x.w, y.w, z.w, vx.w, vy.w, vz.w, h.w, k.w);
+  }
+  if constexpr (MODE == 0) {
+    __syncwarp();
+    // record half e of the warp (e = 8 lane' + 2 m + half: lane' 's particle m) is at slot
+    // 9 (e / 8) + e % 8; the warp's output starts at particle 4 (q - lane)
+    const int64_t first = 4 * (q - lane);
+    const int64_t n_here = min((int64_t)128, (a.n / 4) * 4 - first);  // particles of the warp
+    float4* out = reinterpret_cast<float4*>(a.out + first * BP_ASSIGNED_STRIDE);
+    const float4* ws = stage[wp];
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+      const int e = 32 * p + lane;
+      if (e / 2 < n_here) out[e] = ws[9 * (e >> 3) + (e & 7)];
+    }
+  }
 }
 
 // ---------------------------------------------------------------- pairs
@@ -1246,13 +1308,21 @@ int bp_assign_particles_part(bp_ctx* ctx, int64_t n, const float* x, const float
                    al16(hsml) && al16(halo_id);
   const int64_t n4 = vec ? n / 4 : 0;  // particles [0, 4 n4) by the vector kernel
   if (n4 > 0) {
-    const unsigned nb4 = (unsigned)((n4 + 255) / 256);
+    const unsigned nb4 = (unsigned)((n4 + ASSIGN_THREADS - 1) / ASSIGN_THREADS);
+    // the z(chi), tau(chi) table in dynamic shared memory (not read by the geometry pass)
+    const size_t zt_smem = part == BP_ASSIGN_GEOMETRY ? 0 : (size_t)ctx->t.nc * sizeof(float4);
+    if (part == BP_ASSIGN_SIGNALS)
+      BP_CUDA(ctx, cudaFuncSetAttribute(k_assign4<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)zt_smem));
+    else if (part != BP_ASSIGN_GEOMETRY)
+      BP_CUDA(ctx, cudaFuncSetAttribute(k_assign4<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)zt_smem));
     if (part == BP_ASSIGN_GEOMETRY)
-      k_assign4<1><<<nb4, 256, 0, ctx->stream>>>(a, ctx->t);
+      k_assign4<1><<<nb4, ASSIGN_THREADS, zt_smem, ctx->stream>>>(a, ctx->t);
     else if (part == BP_ASSIGN_SIGNALS)
-      k_assign4<2><<<nb4, 256, 0, ctx->stream>>>(a, ctx->t);
+      k_assign4<2><<<nb4, ASSIGN_THREADS, zt_smem, ctx->stream>>>(a, ctx->t);
     else
-      k_assign4<0><<<nb4, 256, 0, ctx->stream>>>(a, ctx->t);
+      k_assign4<0><<<nb4, ASSIGN_THREADS, zt_smem, ctx->stream>>>(a, ctx->t);
     BP_LAUNCH_CHECK(ctx, "assign (4 per thread)");
   }
   if (4 * n4 < n) {
