@@ -10,7 +10,8 @@
 // ln(T - T_min)), rho0 from the surface-pressure condition, and the energy
 // condition is driven to zero by safeguarded Newton in ln r_f with the exact
 // derivative of the reduced problem.  The gas integrals over [0, r_f] are
-// composite 16-point Gauss-Legendre rules whose nodes are spread over the lanes.
+// composite 16-point Gauss-Legendre rules whose nodes are spread over the lanes (8 points in
+// the FP32 pre-solve and the FP64 polish).
 //
 // Kernels: k_setup (the scalar set-up, one thread per halo), k_presolve (the reduced
 // problem in FP32 to residuals of ~1e-4: starting points), k_solve (FP64: a
@@ -39,8 +40,11 @@ __constant__ double c_glw[NGL];
 __constant__ double c_glx8[NGL_POLISH];
 __constant__ double c_glw8[NGL_POLISH];
 __constant__ double c_li2[16];  // B_2m / (2m+1)!, m = 1..15
-__constant__ float c_glxf[NGL];  // the same rule in FP32 (pre-solve)
-__constant__ float c_glwf[NGL];
+// The FP32 pre-solve's rule: 8 points per panel (the FP64 solutions agree with the 16-point
+// ones to 5e-11, far below the FP32 floor of the pre-solve), half the nodes per evaluation
+#define NGL_PRE 8
+__constant__ float c_glxf[NGL_PRE];
+__constant__ float c_glwf[NGL_PRE];
 
 namespace {
 
@@ -97,10 +101,14 @@ int upload_constants(bp_ctx* ctx) {
     BP_CUDA(ctx, cudaMemcpyToSymbol(c_glw8, w8, sizeof(w8)));
   }
   BP_CUDA(ctx, cudaMemcpyToSymbol(c_li2, li2, sizeof(li2)));
-  float xf[NGL], wf[NGL];
-  for (int k = 0; k < NGL; ++k) {
-    xf[k] = (float)x[k];
-    wf[k] = (float)w[k];
+  float xf[NGL_PRE], wf[NGL_PRE];
+  {
+    double xp[NGL_PRE], wp[NGL_PRE];
+    gauss_legendre(NGL_PRE, xp, wp);
+    for (int k = 0; k < NGL_PRE; ++k) {
+      xf[k] = (float)xp[k];
+      wf[k] = (float)wp[k];
+    }
   }
   BP_CUDA(ctx, cudaMemcpyToSymbol(c_glxf, xf, sizeof(xf)));
   BP_CUDA(ctx, cudaMemcpyToSymbol(c_glwf, wf, sizeof(wf)));
@@ -971,7 +979,7 @@ struct SolverFT {
   bool full_a;
 
   __device__ SolverFT(const HaloF& hh, float nn, int ni) : h(hh), n_int(ni), n(nn) {}
-  static_assert(NG == NGL, "FP32 rule tabulated for NGL points only");
+  static_assert(NG == NGL_PRE, "FP32 rule tabulated for NGL_PRE points only");
   __device__ static float glx(int j) { return c_glxf[j]; }
   __device__ static float glw(int j) { return c_glwf[j]; }
   __device__ static float group_sum(float v) {
@@ -1076,7 +1084,7 @@ struct SolverFT {
   }
 };
 
-using SolverF = SolverFT<32, NGL>;
+using SolverF = SolverFT<32, NGL_PRE>;
 
 // guess[i] = ln(r_f / r_vir), guess[n + i] = ln(T r_vir / (G M)), or NaN
 __global__ void __launch_bounds__(32 * SOLVE_WARPS) k_presolve(
