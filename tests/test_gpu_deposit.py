@@ -239,3 +239,38 @@ def test_small_span_rejects_out_of_range(api, ctx):
     for bad in (-2, 9):
         with pytest.raises(api.BpError, match="BP_EINVAL"):
             ctx.set_small_span(bad)
+
+
+def test_small_particle_running_scale(orc, api, ctx):
+    """The small-particle deposit reads a tile's records once and sets its fixed-point scale
+    from the largest |Y| (|B|) seen so far: here the first blocks of the tile (1500 particles
+    of the smallest size class) carry |Y|, |B| ~ 1e-3 and the last (600 of the largest class,
+    sorted after them) ~ 1, so the sums of the first blocks are shifted down to the final
+    scale when the bright block arrives.  The maps must still match the oracle, also in the
+    pixels that only the faint particles reach (relative to those pixels' own values)."""
+    rng = np.random.default_rng(12)
+    nx = ny = 64 * 4 * 2  # 8 x 8 tiles: every particle in tile (2, 2) of a 512^2 map
+    n_f, n_b = 1500, 600
+    x0 = y0 = 128.0
+    # faint: sub-pixel kernels spread over the whole tile; bright: 7-8 px boxes in one corner
+    fx = rng.uniform(x0 + 1, x0 + 63, n_f)
+    fy = rng.uniform(y0 + 1, y0 + 63, n_f)
+    bx = rng.uniform(x0 + 5, x0 + 20, n_b)
+    by = rng.uniform(y0 + 5, y0 + 20, n_b)
+    hp = np.concatenate([rng.uniform(0.05, 0.4, n_f), rng.uniform(3.6, 3.9, n_b)])
+    Y = np.concatenate([rng.uniform(0.5e-3, 1e-3, n_f), rng.uniform(0.5, 1.0, n_b)])
+    B = np.concatenate([rng.normal(0, 1e-3, n_f), rng.normal(0, 1.0, n_b)])
+    kind = np.zeros(n_f + n_b, np.int32)
+    a = I.deposit_inputs(np.concatenate([fx, bx]), np.concatenate([fy, by]), hp, Y, B, kind)
+    ctx.set_small_span(8)
+    y, b = _deposit(api, ctx, a, nx, ny)
+    yo, bo = orc.pp_deposit(orc_deposit_inputs(a), orc.geom(nx, ny, 0.0, 0.0, 1.0))
+    assert_map_parity(y[0], yo, what="y")
+    assert_map_parity(b[0], bo, what="b")
+    # the pixels away from the bright corner hold faint particles only: relative error there
+    far = np.zeros_like(yo, bool)
+    far[int(y0) + 30:int(y0) + 64, int(x0) + 30:int(x0) + 64] = True
+    sel = far & (yo > 1e-3 * yo[far].max())
+    assert sel.sum() > 100
+    assert np.abs(y[0][sel] - yo[sel]).max() <= 1e-4 * np.abs(yo[sel]).max()
+    ctx.set_small_span(-1)
