@@ -356,7 +356,7 @@ __global__ void __launch_bounds__(TI_THREADS) k_infer_tc(int64_t n, const float*
           const uint64_t db = desc_sw128(smem_u32(Bw + kb * TI_KB));
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks)  // K step of 16 BF16 = 32 bytes: + 2 in the address
-            mma_bf16(tm, da + 2 * ks, db + 2 * ks, TI_IDESC, (kb | ks) ? 1u : 0u);
+            mma_f16(tm, da + 2 * ks, db + 2 * ks, TI_IDESC, (kb | ks) ? 1u : 0u);
         }
         mma_commit(&S.mbar);
       }

@@ -50,6 +50,12 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
          ((uint32_t)(M >> 4) << 24);
 }
 
+// Instruction descriptor of kind::f16 with FP16 A and B (both K-major), FP32 accumulator,
+// dense, no negation; N in bits 17-22 (N / 8), M in bits 24-28 (M / 16).
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 // FP32 -> TF32, round to nearest (ties away), returned in an FP32 container
 __device__ __forceinline__ float tf32_rna(float x) {
   uint32_t r;
@@ -190,8 +196,9 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint6
       "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
       : "memory");
 }
-// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16 (here BF16 operands), issued by one thread
-__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
+// D[tmem] (+)= A[smem] * B[smem]^T, kind::f16, issued by one thread: FP16 or BF16 operands
+// (both the same type), as the instruction descriptor says
+__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
                                          uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n.reg .pred p;\n"
