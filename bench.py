@@ -52,7 +52,7 @@ def config(args, world):
     """The workload description shared by both arms (and every N)."""
     return {"workload": WORKLOAD, "particles": args.particles, "halos": args.halos,
             "maps": f"{args.npix}x{args.npix}", "pp_tile": 64,
-            "deposit_kernel": "tcgen05 split-TF32",
+            "deposit_kernel": "tcgen05 split-FP16 (power-of-two scaled operands, FP32 accumulation)",
             "l2": "inputs (16 GB of particles) far larger than L2; 256 MB written between "
                   "timed steps as well",
             "parallelism": "single sky, particles and halos partitioned by index, one map "
@@ -82,12 +82,12 @@ def measured_peaks():
         return {}
 
 
-def tf32_peak(peaks, sustained=False):
-    """TF32 dense peak: the measured cuBLAS bf16 rate x the nominal TF32/BF16 dense ratio; the
-    burst rate for a kernel timed alone, the sustained one for a kernel timed inside a long
-    step."""
+def f16_peak(peaks, sustained=False):
+    """FP16 dense peak (FP32 accumulation): the measured cuBLAS bf16 rate (the nominal FP16 and
+    BF16 dense rates are equal); the burst rate for a kernel timed alone, the sustained one for
+    a kernel timed inside a long step."""
     key = "bf16_tflops_sustained" if sustained and "bf16_tflops_sustained" in peaks else "bf16_tflops"
-    return float(peaks.get(key, 1900.0)) * (1.1 / 2.25)
+    return float(peaks.get(key, 1900.0))
 
 
 def fp32_peak(peaks):
@@ -239,14 +239,14 @@ def ncu_traffic(kernel_key):
 
 def deposit_roofline(kernel, ph, work, peaks, traffic_key, sustained=False):
     """Roofline entry of the tensor-core deposit from its live CUDA-event duration and the
-    algorithmic flops of the particles it deposits (against the TF32 tensor peak of
-    measured), plus the MMA work it issues; the small-particle kernel (FP32 ALU and shared
-    memory) beside it."""
+    algorithmic flops of the particles it deposits (against the FP16 tensor peak of
+    measured: its MMAs take FP16 operands), plus the MMA work it issues; the small-particle
+    kernel (FP32 ALU and shared memory) beside it."""
     dep_ms, small_ms = ph["deposit"], ph.get("deposit_small", 0.0)
     achieved = work["flops_tc"] / (dep_ms * 1e-3) / 1e12
-    peak = tf32_peak(peaks, sustained)
+    peak = f16_peak(peaks, sustained)
     # per (tile, particle) pair the kernel issues a 128 x 64 rank-1 update in three
-    # split-TF32 products
+    # split-FP16 products
     mma = work["pairs_tc"] * 128 * 64 * 2 * 3
     out = {"kernel": kernel, "bound": "tensor", "achieved": achieved, "peak": peak,
            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": ncu_traffic(traffic_key),
@@ -256,8 +256,7 @@ def deposit_roofline(kernel, ph, work, peaks, traffic_key, sustained=False):
            "mma_tflops_issued": mma / (dep_ms * 1e-3) / 1e12,
            "frac_fp32_alu_peak": achieved / fp32_peak(peaks),
            "peak_note": ("of measured: bf16 " + ("sustained" if sustained else "burst") +
-                         f" {peak * 2.25 / 1.1:.1f} TFLOP/s x 1.1/2.25 (nominal TF32/BF16 dense "
-                         "ratio)")}
+                         f" {peak:.1f} TFLOP/s (nominal FP16 and BF16 dense rates are equal)")}
     if small_ms > 0:
         fs = work["flops"] - work["flops_tc"]
         out["small"] = {"kernel": "k_deposit_small", "bound": "alu", "ms": small_ms,

@@ -167,7 +167,8 @@ int bp_set_tiling(bp_ctx* ctx, int pp_tile, int hp_tile, int pp_unit);
 /* Which kernel performs the PP deposit (Section 3.4, Eqs. f_ij and the integrated
  * kernel): BP_DEPOSIT_AUTO (the tensor-core kernel when the PP tile is 64, else the
  * SIMT kernel), BP_DEPOSIT_SIMT (FP32 FMAs on the CUDA cores) or BP_DEPOSIT_TENSOR
- * (tcgen05 MMAs in split TF32, tile 64 only; BP_EINVAL at paste time with tile 32).
+ * (tcgen05 MMAs in split FP16 with power-of-two operand scales, tile 64 only; BP_EINVAL
+ * at paste time with tile 32).
  * Both sum every pixel in a fixed order with compensated FP32 accumulators; they
  * differ in the rounding of the products (FP32 against about 1e-6 relative). */
 #define BP_DEPOSIT_AUTO 0

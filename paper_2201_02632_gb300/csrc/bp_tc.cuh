@@ -2,10 +2,10 @@
 // tensor memory (TMEM) and shared-memory mbarriers, as used by the tensor-core deposit and
 // the surrogate's inference.
 //
-// Operand layout: K-major with the 128-byte swizzle.  A row holds 32 TF32 values
+// Operand layout: K-major with the 128-byte swizzle.  A row holds 64 FP16 or BF16 values
 // (128 bytes); 8 rows form a 1024-byte atom; the 16-byte chunk q of row r sits at chunk
 // position q ^ (r % 8).  Atoms are stacked along M (or N) 1024 bytes apart.  One MMA
-// step covers K = 8 (32 bytes); step s starts 32 s bytes into the row.
+// step covers K = 16 (32 bytes); step s starts 32 s bytes into the row.
 #pragma once
 #include <cstdint>
 
@@ -36,13 +36,6 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   return d;
 }
 
-// Instruction descriptor of kind::tf32: FP32 accumulator, TF32 A and B, both K-major,
-// dense, no negation; N in bits 17-22 (N / 8), M in bits 24-28 (M / 16).
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
-}
-
 // Instruction descriptor of kind::f16 with BF16 A and B (both K-major), FP32 accumulator,
 // dense, no negation; N in bits 17-22 (N / 8), M in bits 24-28 (M / 16).
 __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
@@ -54,22 +47,6 @@ __host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
 // dense, no negation; N in bits 17-22 (N / 8), M in bits 24-28 (M / 16).
 __host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
   return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-// FP32 -> TF32, round to nearest (ties away), returned in an FP32 container
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-
-// FP32 -> TF32 head + tail: the head keeps 11 significant bits (the mantissa rounded to
-// nearest, ties away, by an integer add on the bit pattern and a mask: exactly
-// representable in TF32), head + tail == x exactly; the tensor core then drops the tail's
-// bits beyond TF32.  |x| < 2^127.  Two integer instructions and one FP32 subtraction.
-__device__ __forceinline__ void split_tf32(float x, float& hi, float& lo) {
-  hi = __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
-  lo = __fsub_rn(x, hi);
 }
 
 // ------------------------------------------------------------------ mbarrier
@@ -186,16 +163,6 @@ __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
 }
 
 // ------------------------------------------------------------------ MMA
-// D[tmem] (+)= A[smem] * B[smem]^T, kind::tf32, issued by one thread
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
-                                         uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n.reg .pred p;\n"
-      "setp.ne.b32 p, %4, 0;\n"
-      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
 // D[tmem] (+)= A[smem] * B[smem]^T, kind::f16, issued by one thread: FP16 or BF16 operands
 // (both the same type), as the instruction descriptor says
 __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
